@@ -1,0 +1,318 @@
+"""Host-side contraction planner: tree, slicing and cost model.
+
+The paper's subject is the search for good contraction trees; here only a
+plain deterministic planner is kept, whose output (a tree and a set of sliced
+labels) is what the GPU executor runs.
+
+* Tree encoding (Sec. 2): leaves are ids 0..n-1, internal node n+i has
+  children ``pairs[i]``; every id is used once, the root is last.
+* Node incidence (Sec. 2, Eq. incidence) generalised to open labels and
+  hyperedges: a node keeps a label iff the label is open or occurs in a leaf
+  outside the node's subtree.  For a plain graph with no open labels this is
+  the symmetric difference s_l (+) s_r of the paper.
+* Width W = max_v sum_{e in s_v} log2 w(e)   (Eq. edgecon; leaves included)
+  Cost  C = sum_v 2^{vc(v)}, vc = sum_{e in s_l u s_r} log2 w(e)
+  (Eq. vertexcon; summed over contraction vertices).  FLOPs = 8C complex,
+  2C real (Sec. 2, text after Eq. vertexcon).
+* Greedy tree (Sec. 3.4, Eq. greedy-cost-function, Eq. greedy-boltzmann-factor):
+  cost(i,j) = size(k) - alpha (size(i)+size(j)); tau = 0 picks the minimum,
+  ties broken by the smallest (min id, max id); only pairs sharing a label
+  are candidates; when none remain the two smallest tensors are joined by an
+  outer product.  tau > 0 samples pairs with weight exp(-cost/tau).
+* Slicing (Sec. 4.7.1): greedily remove the summed label that minimises the
+  total sliced cost C_s = d_sliced * C(sliced tree) until the sliced width
+  reaches the target.
+"""
+from __future__ import annotations
+
+import dataclasses
+import heapq
+import math
+from typing import Dict, Iterable, List, Optional, Sequence, Set, Tuple
+
+import numpy as np
+
+__all__ = [
+    "TreeInfo",
+    "node_labels",
+    "tree_info",
+    "greedy_tree",
+    "left_deep_tree",
+    "slice_greedy",
+    "plan",
+    "validate_tree",
+]
+
+
+def validate_tree(n_leaves: int, pairs: Sequence[Tuple[int, int]]) -> None:
+    """SSA tree checks: n-1 pairs for n>=1 leaves, ids < own id, each id used once."""
+    if n_leaves < 1:
+        raise ValueError("empty network")
+    if len(pairs) != n_leaves - 1:
+        raise ValueError(f"tree has {len(pairs)} pairs, expected {n_leaves - 1}")
+    used = [False] * (2 * n_leaves - 1)
+    for i, (a, b) in enumerate(pairs):
+        me = n_leaves + i
+        for c in (a, b):
+            if not (0 <= c < me):
+                raise ValueError(f"node {me}: child {c} out of range")
+            if used[c]:
+                raise ValueError(f"id {c} used twice")
+            used[c] = True
+        if a == b:
+            raise ValueError(f"node {me}: children equal")
+
+
+def node_labels(leaf_labels: Sequence[Sequence[int]], pairs: Sequence[Tuple[int, int]],
+                open_labels: Iterable[int] = (), removed: Iterable[int] = ()
+                ) -> List[frozenset]:
+    """Incidence set s_v of every tree vertex (leaves first), Eq. incidence
+    generalised: keep a label iff it is open or still occurs outside the
+    subtree.  Labels in ``removed`` (sliced) are dropped everywhere."""
+    rm = set(removed)
+    opn = set(open_labels)
+    total: Dict[int, int] = {}
+    sets: List[frozenset] = []
+    sub: List[Dict[int, int]] = []
+    for ls in leaf_labels:
+        s = frozenset(l for l in ls if l not in rm)
+        for l in s:
+            total[l] = total.get(l, 0) + 1
+        sets.append(s)
+        sub.append({l: 1 for l in s})
+    for a, b in pairs:
+        sa, sb = sets[a], sets[b]
+        ca, cb = sub[a], sub[b]
+        cnt: Dict[int, int] = {}
+        for l in sa | sb:
+            c = ca.get(l, 0) + cb.get(l, 0)
+            if l in opn or c < total[l]:
+                cnt[l] = c
+        sets.append(frozenset(cnt))
+        sub.append(cnt)
+    return sets
+
+
+@dataclasses.dataclass
+class TreeInfo:
+    n_leaves: int
+    sets: List[frozenset]           # s_v for all tree vertices
+    vc: List[float]                 # vertex congestion of internal nodes (log2)
+    W: float                        # contraction width (Eq. edgecon)
+    C: float                        # contraction cost (Eq. vertexcon), per slice
+    d_sliced: int
+    sliced: Tuple[int, ...]
+
+    @property
+    def C_s(self) -> float:
+        return self.d_sliced * self.C
+
+    def flops(self, is_complex: bool) -> float:
+        return (8.0 if is_complex else 2.0) * self.C_s
+
+    def node_sizes(self) -> List[float]:
+        return []
+
+
+def _log2w(dims: Dict[int, int], labels: Iterable[int]) -> float:
+    return float(sum(math.log2(dims[l]) for l in labels))
+
+
+def tree_info(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
+              pairs: Sequence[Tuple[int, int]], open_labels: Iterable[int] = (),
+              sliced: Sequence[int] = ()) -> TreeInfo:
+    n = len(leaf_labels)
+    validate_tree(n, pairs)
+    sets = node_labels(leaf_labels, pairs, open_labels, sliced)
+    W = max(_log2w(dims, s) for s in sets)
+    vc: List[float] = []
+    C = 0.0
+    for a, b in pairs:
+        v = _log2w(dims, sets[a] | sets[b])
+        vc.append(v)
+        C += 2.0 ** v
+    d = 1
+    for l in sliced:
+        d *= dims[l]
+    return TreeInfo(n, sets, vc, W, C, d, tuple(sliced))
+
+
+# ---------------------------------------------------------------------------
+# Greedy tree (Sec. 3.4)
+# ---------------------------------------------------------------------------
+
+def greedy_tree(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
+                open_labels: Iterable[int] = (), alpha: float = 1.0, tau: float = 0.0,
+                seed: Optional[int] = None) -> List[Tuple[int, int]]:
+    """Agglomerative tree by Eq. greedy-cost-function.
+
+    tau == 0: deterministic minimum with (min id, max id) tie break.
+    tau > 0: Boltzmann sampling (Eq. greedy-boltzmann-factor), seeded.
+    """
+    n = len(leaf_labels)
+    if n == 1:
+        return []
+    opn = set(open_labels)
+    sets: Dict[int, frozenset] = {}
+    users: Dict[int, Set[int]] = {}
+    size: Dict[int, int] = {}
+
+    def tsize(s: Iterable[int]) -> int:
+        p = 1
+        for l in s:
+            p *= dims[l]
+        return p
+
+    for v, ls in enumerate(leaf_labels):
+        sets[v] = frozenset(ls)
+        size[v] = tsize(ls)
+        for l in ls:
+            users.setdefault(l, set()).add(v)
+
+    def out_set(i: int, j: int) -> frozenset:
+        keep = []
+        for l in sets[i] | sets[j]:
+            if l in opn:
+                keep.append(l)
+                continue
+            u = users[l]
+            c = (i in u) + (j in u)
+            if len(u) > c:
+                keep.append(l)
+        return frozenset(keep)
+
+    def cost(i: int, j: int) -> float:
+        return tsize(out_set(i, j)) - alpha * (size[i] + size[j])
+
+    rng = np.random.Generator(np.random.PCG64(seed if seed is not None else 0))
+    alive: Set[int] = set(range(n))
+    heap: List[Tuple[float, int, int]] = []
+    cand: Set[Tuple[int, int]] = set()
+
+    def push(i: int, j: int) -> None:
+        a, b = (i, j) if i < j else (j, i)
+        if (a, b) in cand:
+            return
+        cand.add((a, b))
+        heapq.heappush(heap, (cost(a, b), a, b))
+
+    for l, u in users.items():
+        us = sorted(u)
+        for x in range(len(us)):
+            for y in range(x + 1, len(us)):
+                push(us[x], us[y])
+
+    pairs: List[Tuple[int, int]] = []
+    nxt = n
+    while len(alive) > 1:
+        choice: Optional[Tuple[int, int]] = None
+        if tau > 0.0:
+            live = [(c, a, b) for (c, a, b) in heap if a in alive and b in alive]
+            heap = live
+            heapq.heapify(heap)
+            if live:
+                cs = np.array([c for c, _, _ in live], dtype=np.float64)
+                w = np.exp(-(cs - cs.min()) / tau)
+                k = int(rng.choice(len(live), p=w / w.sum()))
+                _, a, b = live[k]
+                choice = (a, b)
+                heap.remove(live[k])
+                heapq.heapify(heap)
+        else:
+            while heap:
+                c, a, b = heapq.heappop(heap)
+                if a in alive and b in alive:
+                    choice = (a, b)
+                    break
+        if choice is None:
+            # disconnected components: outer product of the two smallest
+            ordered = sorted(alive, key=lambda v: (size[v], v))
+            a, b = sorted(ordered[:2])
+            choice = (a, b)
+        a, b = choice
+        s = out_set(a, b)
+        k = nxt
+        nxt += 1
+        pairs.append((a, b))
+        for l in sets[a] | sets[b]:
+            u = users[l]
+            u.discard(a)
+            u.discard(b)
+            if l in s:
+                u.add(k)
+        alive.discard(a)
+        alive.discard(b)
+        sets[k] = s
+        size[k] = tsize(s)
+        alive.add(k)
+        nbrs: Set[int] = set()
+        for l in s:
+            nbrs |= users[l]
+        nbrs.discard(k)
+        for m in sorted(nbrs):
+            push(m, k)
+    return pairs
+
+
+def left_deep_tree(n_leaves: int, order: Optional[Sequence[int]] = None) -> List[Tuple[int, int]]:
+    """((((t0 t1) t2) t3) ...) in the given leaf order."""
+    order = list(range(n_leaves)) if order is None else list(order)
+    pairs = []
+    cur = order[0]
+    for i, v in enumerate(order[1:]):
+        pairs.append((cur, v))
+        cur = n_leaves + i
+    return pairs
+
+
+# ---------------------------------------------------------------------------
+# Slicing (Sec. 4.7.1)
+# ---------------------------------------------------------------------------
+
+def slice_greedy(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
+                 pairs: Sequence[Tuple[int, int]], open_labels: Iterable[int],
+                 target_width: float, max_sliced: int = 64) -> List[int]:
+    """Greedy index slicing to a target sliced width W_s.
+
+    Each step considers the summed labels of tensors wider than the target
+    and removes the one minimising d_sliced * C(tree without it); ties go to
+    the smallest label id.  Stops when W_s <= target_width.
+    """
+    opn = set(open_labels)
+    sliced: List[int] = []
+    n = len(leaf_labels)
+    while True:
+        info = tree_info(leaf_labels, dims, pairs, opn, sliced)
+        if info.W <= target_width + 1e-9:
+            return sliced
+        if len(sliced) >= max_sliced:
+            raise RuntimeError("slicing did not reach the target width")
+        big = [s for s in info.sets if _log2w(dims, s) > target_width + 1e-9]
+        cands = sorted({l for s in big for l in s if l not in opn})
+        if not cands:
+            raise RuntimeError("only open labels exceed the target width")
+        col = {l: i for i, l in enumerate(cands)}
+        node_cost = np.array([2.0 ** v for v in info.vc])
+        red = np.zeros(len(cands))
+        for k, (a, b) in enumerate(pairs):
+            u = info.sets[a] | info.sets[b]
+            for l in u:
+                i = col.get(l)
+                if i is not None:
+                    red[i] += node_cost[k] * (1.0 - 1.0 / dims[l])
+        w = np.array([dims[l] for l in cands], dtype=np.float64)
+        score = info.d_sliced * w * (info.C - red)
+        best = int(np.flatnonzero(score <= score.min() * (1 + 1e-12))[0])
+        sliced.append(cands[best])
+
+
+def plan(net, target_width: Optional[float] = None, alpha: float = 1.0):
+    """Greedy tree plus optional slicing for a ``inputs.Network``.
+
+    Returns (pairs, sliced, TreeInfo)."""
+    pairs = greedy_tree(net.labels, net.dims, net.open, alpha=alpha)
+    sliced: List[int] = []
+    if target_width is not None:
+        sliced = slice_greedy(net.labels, net.dims, pairs, net.open, target_width)
+    info = tree_info(net.labels, net.dims, pairs, net.open, sliced)
+    return pairs, sliced, info
