@@ -1,0 +1,227 @@
+/*
+ * tn.h -- C-ABI of the GB300 contraction-tree executor (libtn.so).
+ *
+ * Executes a given contraction tree, optionally sliced, over a tensor
+ * network of real or complex tensors on one GPU (sm_103a).  The problem is
+ * the one stated in Sec. 2 of arXiv 2002.01935 (Gray & Kourtis,
+ * "Hyper-optimized tensor network contraction"): a network is a graph whose
+ * vertices carry tensors T_v over ordered index tuples t_v and whose edges
+ * carry discrete labels of size w(e); a rooted binary contraction tree
+ * fixes the order of pairwise contractions; slicing (Sec. 4.7.1) moves the
+ * sums over a chosen set of labels outside and sums the independent sliced
+ * contractions.
+ *
+ * Conventions shared by every call:
+ *   - Labels are arbitrary int64 ids.  A label may occur in any number of
+ *     tensors: in two it is an ordinary edge, in more a hyperedge (Sec. 3.5);
+ *     in one and not open it is summed when that tensor is first contracted.
+ *     A label repeated inside one tensor is rejected (no self loops, Sec. 2).
+ *   - Tensors are dense and row-major over their label order (the last label
+ *     varies fastest).  TN_C64 stores interleaved (re, im) float32 pairs,
+ *     TN_R32 plain float32.
+ *   - Results are returned in FP64 as (mantissa, exponent): value =
+ *     mantissa * 2^exp2.  Every contraction is renormalised by a power of
+ *     two (Sec. 4.2, "actively renormalizing"), so values far outside the
+ *     float range are representable.
+ *   - No call throws.  A non-OK status leaves outputs untouched; the message
+ *     of the last failure on the calling thread is returned by
+ *     tn_last_error().
+ *   - All device work is ordered on the caller's CUDA stream (a
+ *     cudaStream_t passed as void*; NULL = legacy default stream).
+ *   - Power-of-two label sizes run on the tiled kernels; other sizes run on
+ *     the generic kernel (same results, slower).
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tn_net tn_net; /* opaque, library-owned */
+
+typedef enum {
+    TN_OK = 0,
+    TN_EINVAL = 1,        /* malformed network, tree, labels or arguments   */
+    TN_ENOMEM = 2,        /* device or host allocation failed               */
+    TN_ECUDA = 3,         /* a CUDA runtime call failed                     */
+    TN_ETIMEOUT = 4,      /* a bounded device-side wait gave up             */
+    TN_EUNSUPPORTED = 5   /* valid request the executor cannot run          */
+} tn_status;
+
+typedef enum {
+    TN_R32 = 0,           /* real float32 leaves                            */
+    TN_C64 = 1            /* complex64 leaves, interleaved (re, im)         */
+} tn_dtype;
+
+/*
+ * Arithmetic used inside each pairwise contraction (the cross-slice sum is
+ * always FP64).  Complex products are formed from real products (4M), or
+ * from three real products (3M) where named.
+ *   TN_MODE_FP32       : FP32 FMA on CUDA cores (plain complex64 / float32)
+ *   TN_MODE_TF32_3M    : one TF32 tensor-core pass per real product, 3M
+ *   TN_MODE_TF32_SPLIT : operands split hi+lo in TF32, three products
+ *                        (hi*hi + hi*lo + lo*hi), FP32 accumulation
+ *   TN_MODE_BF16_SPLIT : the same split in BF16
+ * Nodes too small for the tensor cores run the FP32 path in every mode.
+ */
+typedef enum {
+    TN_MODE_FP32 = 0,
+    TN_MODE_TF32_3M = 1,
+    TN_MODE_TF32_SPLIT = 2,
+    TN_MODE_BF16_SPLIT = 3
+} tn_mode;
+
+enum { TN_MEM_DEVICE = 0, TN_MEM_HOST = 1 };
+
+/*
+ * tn_create -- build a network handle from tensor shapes and labels
+ * (Sec. 2: the graph G, the tuples t_v and the weights w(e) = |D(e)|).
+ *   dt           storage type of every leaf.
+ *   n_tensors    |V| >= 1.
+ *   ranks[v]     number of labels of tensor v (0 allowed: a scalar).
+ *   labels       the concatenated t_v tuples, sum(ranks) int64 ids.
+ *   n_labels, label_ids[i], label_dims[i]
+ *                every label used, with its size w(e) >= 1.
+ *   n_open, open_labels
+ *                labels left uncontracted, in the order of the output
+ *                tensor's axes (row-major).  n_open = 0: a scalar network.
+ * The arrays are copied; the caller keeps ownership.  On success *out owns a
+ * handle to be released with tn_destroy.  Errors: TN_EINVAL (unknown or
+ * duplicate label, repeated label in a tensor, open label not in any tensor,
+ * size < 1), TN_ENOMEM.
+ */
+tn_status tn_create(tn_net **out, tn_dtype dt, int32_t n_tensors, const int32_t *ranks,
+                    const int64_t *labels, int32_t n_labels, const int64_t *label_ids,
+                    const int64_t *label_dims, int32_t n_open, const int64_t *open_labels);
+
+/*
+ * tn_set_tensor -- attach the entries of leaf v (T_v of Sec. 2).
+ *   ptr   row-major entries in the label order given to tn_create.
+ *   mem   TN_MEM_DEVICE: a device pointer, borrowed (not copied): it must
+ *         stay valid and unchanged until every contraction that reads it
+ *         has completed on its stream.
+ *         TN_MEM_HOST: a host pointer, read by every later tn_contract
+ *         (copied to library-owned device memory on the call's stream;
+ *         page-locked memory makes that copy asynchronous).
+ * Errors: TN_EINVAL (v out of range, ptr NULL for a non-empty tensor).
+ */
+tn_status tn_set_tensor(tn_net *net, int32_t v, const void *ptr, int32_t mem);
+
+/*
+ * Per-call options of tn_contract_ex.  Zero-initialise, then set fields.
+ *   slice_begin, slice_count
+ *       contract only slices [slice_begin, slice_begin + slice_count) of the
+ *       d_sliced = prod w(e) slices (slice_count <= 0: all).  Slice id s
+ *       fixes the sliced labels to the mixed-radix digits of s, the last
+ *       listed label varying fastest (Sec. 4.7.1).
+ *   no_graph
+ *       1: launch the per-slice node sequence directly instead of replaying
+ *       a captured CUDA graph.
+ *   tile_override
+ *       >0: force this tile-table entry for every tiled node (autotuning);
+ *       0: use the built-in choice.
+ *   prof_events, prof_first, prof_count
+ *       timing hooks: prof_events[i] is recorded on the stream just before
+ *       the kernel of node prof_first+i (nodes numbered 0..n_tensors-2 in
+ *       tree order) and prof_events[prof_count] just after node
+ *       prof_first+prof_count-1, in every slice (the last slice's records
+ *       win).  The events are caller-owned timing events.
+ */
+typedef struct {
+    int64_t slice_begin;
+    int64_t slice_count;
+    int32_t no_graph;
+    int32_t tile_override;
+    void *const *prof_events; /* NULL, or prof_count+1 cudaEvent_t (as void*) */
+    int32_t prof_first;
+    int32_t prof_count;
+    int32_t reserved[6];
+} tn_options;
+
+/*
+ * tn_contract -- contract the network with the given tree and slicing.
+ *   tree_pairs   2*(n_tensors-1) int32 ids: internal vertex n_tensors+i has
+ *                children (tree_pairs[2i], tree_pairs[2i+1]); leaves are
+ *                0..n_tensors-1, every id is used exactly once and a child id
+ *                is smaller than its parent's; the root is last (the l(v),
+ *                r(v) tuples of Sec. 2).  A node keeps a label iff it is
+ *                open or occurs in a leaf outside the node's subtree
+ *                (Eq. incidence, generalised to hyperedges and open labels).
+ *   n_sliced, sliced_labels
+ *                labels summed outside the tree (Sec. 4.7.1); they must be
+ *                non-open labels of the network.
+ *   mode         arithmetic of the node contractions (tn_mode).
+ *   out          FP64 mantissa of the result over the open labels in
+ *                tn_create order: complex128 (TN_C64) or float64 (TN_R32),
+ *                prod(open sizes) entries (1 for a scalar network).
+ *   out_mem      TN_MEM_DEVICE or TN_MEM_HOST, for out and out_exp2.
+ *   out_exp2     one int64: value = out * 2^(*out_exp2).
+ *   stream       cudaStream_t (as void*).
+ * Device outputs are written asynchronously on the stream; host outputs
+ * are complete when the call returns (the call synchronises the stream).
+ * The first call with a new (tree, slicing, mode) plans the nodes and
+ * allocates the workspace (cached in the handle; a call during stream
+ * capture must reuse a cached plan).  Errors: TN_EINVAL (malformed tree,
+ * sliced label open or unknown, a leaf without data), TN_ENOMEM, TN_ECUDA,
+ * TN_ETIMEOUT.
+ */
+tn_status tn_contract(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
+                      const int64_t *sliced_labels, tn_mode mode, void *out, int32_t out_mem,
+                      int64_t *out_exp2, void *stream);
+
+/* tn_contract with options (NULL options = tn_contract). */
+tn_status tn_contract_ex(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
+                         const int64_t *sliced_labels, tn_mode mode, const tn_options *opt,
+                         void *out, int32_t out_mem, int64_t *out_exp2, void *stream);
+
+/*
+ * tn_contract_grad -- reverse-mode derivative of the contraction with
+ * respect to every leaf.  The paper states only the forward problem; the
+ * backward pass is the adjoint of each pairwise contraction: for a node
+ * C = A * B with adjoint Cbar, Abar = contract(Cbar, conj(B)) over B's
+ * labels not in A, and Bbar likewise, applied root to leaves.  Forward
+ * intermediates are recomputed per slice, not stored across slices.
+ *   out_adjoint  host FP64 array shaped like tn_contract's out (complex128
+ *                or float64), the adjoint of the result's mantissa:
+ *                the result's adjoint is out_adjoint * 2^(adj_exp2).
+ *   leaf_grads   n_tensors device pointers (NULL to skip a leaf), each
+ *                shaped like the leaf (dtype dt): on return (in stream
+ *                order) leaf_grads[v] = conj(d value / d T_v) * adjoint,
+ *                summed over slices and contracted over the open labels --
+ *                the convention of torch.autograd for complex tensors.
+ *   Other arguments as tn_contract.  Errors as tn_contract.
+ */
+tn_status tn_contract_grad(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
+                           const int64_t *sliced_labels, tn_mode mode, const double *out_adjoint,
+                           int64_t adj_exp2, void *const *leaf_grads, void *stream);
+
+/*
+ * tn_plan_info -- cost figures of a (tree, slicing) for this network, from
+ * Eqs. edgecon and vertexcon: out[0] = W_s (sliced width, log2 of the
+ * largest tensor), out[1] = C (contraction cost of one slice), out[2] =
+ * d_sliced, out[3] = FLOPs of all slices (8 C d_sliced complex, 2 C
+ * d_sliced real), out[4] = workspace bytes per slice, out[5] = number of
+ * nodes run by the tiled kernels, out[6] = by the tensor-core kernel,
+ * out[7] = by the generic kernel.  Host only; no device work.
+ */
+tn_status tn_plan_info(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
+                       const int64_t *sliced_labels, tn_mode mode, double out[8]);
+
+/* Release the handle, its plans and its device memory (synchronises the
+ * device work the handle issued).  NULL is ignored. */
+void tn_destroy(tn_net *net);
+
+/* Message of the last non-OK status on this thread ("" if none). */
+const char *tn_last_error(void);
+
+/* Library version string. */
+const char *tn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TN_H */

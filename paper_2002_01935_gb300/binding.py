@@ -1,0 +1,247 @@
+"""ctypes binding of libtn.so, the C-ABI declared in include/tn.h.
+
+Argument marshalling only: every step of a contraction runs in the
+library's CUDA kernels.  Importing this module loads libtn.so and raises
+ImportError if it has not been built (``paper_2002_01935_gb300.build``);
+there is no fallback.
+
+The functions mirror the C names (tn_create, tn_set_tensor, tn_contract,
+tn_contract_ex, tn_contract_grad, tn_plan_info, tn_destroy, tn_last_error);
+``TensorNetwork`` wraps a handle for use with torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtn.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libtn.so not built ({LIB_PATH}); run paper_2002_01935_gb300.build.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT, TN_EUNSUPPORTED = range(6)
+TN_R32, TN_C64 = 0, 1
+TN_MODE_FP32, TN_MODE_TF32_3M, TN_MODE_TF32_SPLIT, TN_MODE_BF16_SPLIT = range(4)
+TN_MEM_DEVICE, TN_MEM_HOST = 0, 1
+MODES = {"fp32": TN_MODE_FP32, "tf32_3m": TN_MODE_TF32_3M, "tf32_split": TN_MODE_TF32_SPLIT,
+         "bf16_split": TN_MODE_BF16_SPLIT}
+
+
+class tn_options(ctypes.Structure):
+    _fields_ = [("slice_begin", ctypes.c_int64), ("slice_count", ctypes.c_int64),
+                ("no_graph", ctypes.c_int32), ("tile_override", ctypes.c_int32),
+                ("prof_events", ctypes.POINTER(ctypes.c_void_p)), ("prof_first", ctypes.c_int32),
+                ("prof_count", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+
+_lib.tn_create.restype = ctypes.c_int
+_lib.tn_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int32, _i32p, _i64p,
+                           ctypes.c_int32, _i64p, _i64p, ctypes.c_int32, _i64p]
+_lib.tn_set_tensor.restype = ctypes.c_int
+_lib.tn_set_tensor.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_int32]
+_lib.tn_contract.restype = ctypes.c_int
+_lib.tn_contract.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int, _vp, ctypes.c_int32,
+                             _i64p, _vp]
+_lib.tn_contract_ex.restype = ctypes.c_int
+_lib.tn_contract_ex.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int,
+                                ctypes.POINTER(tn_options), _vp, ctypes.c_int32, _i64p, _vp]
+_lib.tn_contract_grad.restype = ctypes.c_int
+_lib.tn_contract_grad.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                                  ctypes.POINTER(_vp), _vp]
+_lib.tn_plan_info.restype = ctypes.c_int
+_lib.tn_plan_info.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int,
+                              ctypes.POINTER(ctypes.c_double)]
+_lib.tn_destroy.restype = None
+_lib.tn_destroy.argtypes = [_vp]
+_lib.tn_last_error.restype = ctypes.c_char_p
+_lib.tn_last_error.argtypes = []
+_lib.tn_version.restype = ctypes.c_char_p
+_lib.tn_version.argtypes = []
+
+EXPORTS = ["tn_create", "tn_set_tensor", "tn_contract", "tn_contract_ex", "tn_contract_grad",
+           "tn_plan_info", "tn_destroy", "tn_last_error", "tn_version"]
+
+
+class TNError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tn status {status}: {msg}")
+        self.status = status
+
+
+def _check(rc: int) -> None:
+    if rc != TN_OK:
+        raise TNError(rc, tn_last_error())
+
+
+def _arr(a, dt):
+    return np.ascontiguousarray(np.asarray(a, dtype=dt))
+
+
+def _p(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def tn_last_error() -> str:
+    return _lib.tn_last_error().decode()
+
+
+def tn_version() -> str:
+    return _lib.tn_version().decode()
+
+
+def tn_create(dtype: int, labels: Sequence[Sequence[int]], dims: Dict[int, int],
+              open_labels: Sequence[int]) -> int:
+    ranks = _arr([len(l) for l in labels], np.int32)
+    flat = _arr([x for l in labels for x in l] or [0], np.int64)
+    ids = sorted(dims)
+    lid = _arr(ids or [0], np.int64)
+    ldim = _arr([dims[i] for i in ids] or [1], np.int64)
+    opn = _arr(list(open_labels) or [0], np.int64)
+    h = _vp()
+    _check(_lib.tn_create(ctypes.byref(h), dtype, len(labels), _p(ranks, ctypes.c_int32),
+                          _p(flat, ctypes.c_int64), len(ids), _p(lid, ctypes.c_int64),
+                          _p(ldim, ctypes.c_int64), len(open_labels), _p(opn, ctypes.c_int64)))
+    return h.value
+
+
+def tn_set_tensor(h: int, v: int, ptr: int, mem: int = TN_MEM_DEVICE) -> None:
+    _check(_lib.tn_set_tensor(h, v, ptr, mem))
+
+
+def _tree(pairs):
+    return _arr([x for p in pairs for x in p] or [0], np.int32)
+
+
+def tn_contract_ex(h: int, pairs, sliced, mode: int, out_ptr: int, out_mem: int, exp_ptr: int,
+                   stream: int = 0, slice_begin: int = 0, slice_count: int = 0,
+                   no_graph: bool = False, tile_override: int = 0,
+                   prof_events: Optional[Sequence[int]] = None, prof_first: int = 0) -> None:
+    tr = _tree(pairs)
+    sl = _arr(list(sliced) or [0], np.int64)
+    opt = tn_options(slice_begin, slice_count, int(no_graph), tile_override)
+    if prof_events:
+        evs = (ctypes.c_void_p * len(prof_events))(*prof_events)
+        opt.prof_events = ctypes.cast(evs, ctypes.POINTER(ctypes.c_void_p))
+        opt.prof_first = prof_first
+        opt.prof_count = len(prof_events) - 1
+    _check(_lib.tn_contract_ex(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
+                               ctypes.byref(opt), out_ptr, out_mem,
+                               ctypes.cast(exp_ptr, _i64p), stream))
+
+
+def tn_contract(h: int, pairs, sliced, mode: int, out_ptr: int, out_mem: int, exp_ptr: int,
+                stream: int = 0) -> None:
+    tr = _tree(pairs)
+    sl = _arr(list(sliced) or [0], np.int64)
+    _check(_lib.tn_contract(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
+                            out_ptr, out_mem, ctypes.cast(exp_ptr, _i64p), stream))
+
+
+def tn_contract_grad(h: int, pairs, sliced, mode: int, adjoint: np.ndarray, adj_exp2: int,
+                     grad_ptrs: Sequence[int], stream: int = 0) -> None:
+    tr = _tree(pairs)
+    sl = _arr(list(sliced) or [0], np.int64)
+    adj = np.ascontiguousarray(adjoint)
+    gp = (_vp * len(grad_ptrs))(*[g or None for g in grad_ptrs])
+    _check(_lib.tn_contract_grad(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64),
+                                 mode, adj.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 int(adj_exp2), gp, stream))
+
+
+def tn_plan_info(h: int, pairs, sliced, mode: int = TN_MODE_FP32) -> Dict[str, float]:
+    tr = _tree(pairs)
+    sl = _arr(list(sliced) or [0], np.int64)
+    out = np.zeros(8, dtype=np.float64)
+    _check(_lib.tn_plan_info(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
+                             _p(out, ctypes.c_double)))
+    keys = ["W", "C", "d_sliced", "flops", "ws_bytes", "n_tiled", "n_tensor_core", "n_generic"]
+    return dict(zip(keys, out.tolist()))
+
+
+def tn_destroy(h: int) -> None:
+    _lib.tn_destroy(h)
+
+
+class TensorNetwork:
+    """A network handle bound to torch leaf tensors.
+
+    ``tensors`` are torch tensors (complex64 or float32), on the GPU for
+    device mode or in (pinned) host memory for host mode.  The handle
+    borrows them: keep them alive while contractions that read them run.
+    """
+
+    def __init__(self, labels, dims, open_labels, tensors=None, complex_=True):
+        import torch  # noqa: F401  (device memory, streams)
+        self.dtype = TN_C64 if complex_ else TN_R32
+        self.labels = [list(l) for l in labels]
+        self.dims = dict(dims)
+        self.open = list(open_labels)
+        self.h = tn_create(self.dtype, self.labels, self.dims, self.open)
+        self._keep: List = []
+        if tensors is not None:
+            self.set_tensors(tensors)
+
+    def close(self):
+        if self.h:
+            tn_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tensors(self, tensors) -> None:
+        import torch
+        want = torch.complex64 if self.dtype == TN_C64 else torch.float32
+        self._keep = []
+        for v, t in enumerate(tensors):
+            if t.dtype != want:
+                raise TypeError(f"leaf {v}: dtype {t.dtype}, expected {want}")
+            if not t.is_contiguous():
+                raise ValueError(f"leaf {v} must be contiguous")
+            mem = TN_MEM_DEVICE if t.is_cuda else TN_MEM_HOST
+            self._keep.append(t)
+            tn_set_tensor(self.h, v, t.data_ptr(), mem)
+
+    @property
+    def out_shape(self) -> Tuple[int, ...]:
+        return tuple(self.dims[l] for l in self.open)
+
+    def contract(self, pairs, sliced=(), mode="fp32", out=None, out_exp=None, stream=None,
+                 slice_begin=0, slice_count=0, no_graph=False, tile_override=0,
+                 prof_events=None, prof_first=0):
+        """Return (mantissa, exp2) torch tensors; value = mantissa * 2**exp2.
+
+        Device outputs by default (asynchronous on ``stream``); pass CPU
+        ``out``/``out_exp`` tensors to receive host outputs (synchronous)."""
+        import torch
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        dev = torch.device("cuda")
+        odt = torch.complex128 if self.dtype == TN_C64 else torch.float64
+        if out is None:
+            out = torch.empty(self.out_shape, dtype=odt, device=dev)
+        if out_exp is None:
+            out_exp = torch.empty((), dtype=torch.int64, device=out.device)
+        mem = TN_MEM_DEVICE if out.is_cuda else TN_MEM_HOST
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        evp = [e.cuda_event for e in prof_events] if prof_events else None
+        tn_contract_ex(self.h, pairs, sliced, m, out.data_ptr(), mem, out_exp.data_ptr(), s,
+                       slice_begin, slice_count, no_graph, tile_override, evp, prof_first)
+        return out, out_exp
+
+    def plan_info(self, pairs, sliced=(), mode="fp32"):
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        return tn_plan_info(self.h, pairs, sliced, m)

@@ -1,0 +1,253 @@
+// tn_api.cpp -- C-ABI entry points and host-side node planning of libtn.so.
+//
+// Planning follows the problem statement of arXiv 2002.01935:
+//   * tree encoding and node incidence: Sec. 2 (Eq. incidence), generalised
+//     so a node keeps a label iff it is open or occurs in a leaf outside the
+//     node's subtree (hyperedges, Sec. 3.5; open labels, Sec. 4.7.3);
+//   * width and cost: Eqs. edgecon and vertexcon; FLOPs 8C / 2C (Sec. 2);
+//   * slicing: Sec. 4.7.1 -- a sliced label is fixed per slice, which only
+//     offsets the leaves that hold it, so no leaf is copied.
+// Each node's labels are grouped into batch (in both operands and kept),
+// K (in both, summed), M / N (in one operand, kept) and summed-only (in one
+// operand, not kept); the node's output is laid out [batch][M][N], each
+// group ordered so its fastest label is the operand's fastest, which keeps
+// every kernel's global accesses coalesced without permutation passes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/tn.h"
+#include "tn_internal.h"
+#include "tn_plan.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+tn_status fail(tn_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define TN_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA,           \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));             \
+    } while (0)
+
+}  // namespace
+
+using tn::Plan;
+using tn::NetDesc;
+
+struct tn_net {
+    NetDesc d;
+    std::vector<std::unique_ptr<Plan>> plans;
+    void* unit = nullptr;  // device scalar 1 for single-tensor networks
+};
+
+extern "C" {
+
+const char* tn_last_error(void) { return g_err.c_str(); }
+
+const char* tn_version(void) { return "tn-gb300 0.1 (sm_103a)"; }
+
+tn_status tn_create(tn_net** out, tn_dtype dt, int32_t n_tensors, const int32_t* ranks,
+                    const int64_t* labels, int32_t n_labels, const int64_t* label_ids,
+                    const int64_t* label_dims, int32_t n_open, const int64_t* open_labels) {
+    if (!out) return fail(TN_EINVAL, "tn_create: out is NULL");
+    *out = nullptr;
+    if (dt != TN_R32 && dt != TN_C64) return fail(TN_EINVAL, "tn_create: bad dtype");
+    if (n_tensors < 1) return fail(TN_EINVAL, "tn_create: n_tensors < 1");
+    if (n_labels < 0 || n_open < 0) return fail(TN_EINVAL, "tn_create: negative count");
+    if (!ranks || (n_labels > 0 && (!label_ids || !label_dims)) || (n_open > 0 && !open_labels))
+        return fail(TN_EINVAL, "tn_create: NULL array");
+    std::unique_ptr<tn_net> net(new (std::nothrow) tn_net);
+    if (!net) return fail(TN_ENOMEM, "tn_create: out of host memory");
+    NetDesc& d = net->d;
+    d.dt = dt;
+    d.n = n_tensors;
+    for (int i = 0; i < n_labels; ++i) {
+        if (label_dims[i] < 1) return fail(TN_EINVAL, "tn_create: label size < 1");
+        if (d.id2d.count(label_ids[i])) return fail(TN_EINVAL, "tn_create: duplicate label id");
+        d.id2d[label_ids[i]] = (int)d.dims.size();
+        d.ids.push_back(label_ids[i]);
+        d.dims.push_back(label_dims[i]);
+    }
+    const int L = (int)d.dims.size();
+    std::vector<int> used(L, 0);
+    int64_t off = 0;
+    d.leaves.resize(n_tensors);
+    for (int v = 0; v < n_tensors; ++v) {
+        if (ranks[v] < 0) return fail(TN_EINVAL, "tn_create: negative rank");
+        if (ranks[v] > 0 && !labels) return fail(TN_EINVAL, "tn_create: labels is NULL");
+        auto& lf = d.leaves[v];
+        for (int i = 0; i < ranks[v]; ++i) {
+            auto it = d.id2d.find(labels[off + i]);
+            if (it == d.id2d.end()) return fail(TN_EINVAL, "tn_create: unknown label in tensor");
+            if (std::find(lf.lab.begin(), lf.lab.end(), it->second) != lf.lab.end())
+                return fail(TN_EINVAL, "tn_create: label repeated within a tensor");
+            lf.lab.push_back(it->second);
+            used[it->second]++;
+        }
+        off += ranks[v];
+        lf.size = 1;
+        lf.stride.assign(lf.lab.size(), 1);
+        for (int i = (int)lf.lab.size() - 1; i >= 0; --i) {
+            lf.stride[i] = lf.size;
+            lf.size *= d.dims[lf.lab[i]];
+        }
+    }
+    for (int i = 0; i < n_open; ++i) {
+        auto it = d.id2d.find(open_labels[i]);
+        if (it == d.id2d.end()) return fail(TN_EINVAL, "tn_create: unknown open label");
+        if (!used[it->second]) return fail(TN_EINVAL, "tn_create: open label in no tensor");
+        if (std::find(d.open.begin(), d.open.end(), it->second) != d.open.end())
+            return fail(TN_EINVAL, "tn_create: open label repeated");
+        d.open.push_back(it->second);
+    }
+    for (int l = 0; l < L; ++l)
+        if (!used[l]) return fail(TN_EINVAL, "tn_create: label used by no tensor");
+    *out = net.release();
+    return TN_OK;
+}
+
+tn_status tn_set_tensor(tn_net* net, int32_t v, const void* ptr, int32_t mem) {
+    if (!net) return fail(TN_EINVAL, "tn_set_tensor: net is NULL");
+    if (v < 0 || v >= net->d.n) return fail(TN_EINVAL, "tn_set_tensor: tensor index out of range");
+    if (mem != TN_MEM_DEVICE && mem != TN_MEM_HOST) return fail(TN_EINVAL, "tn_set_tensor: bad mem");
+    if (!ptr) return fail(TN_EINVAL, "tn_set_tensor: NULL pointer");
+    net->d.leaves[v].ptr = ptr;
+    net->d.leaves[v].mem = mem;
+    return TN_OK;
+}
+
+static tn_status get_plan(tn_net* net, const int32_t* pairs, int32_t n_sliced, const int64_t* sliced,
+                          tn_mode mode, Plan** out) {
+    NetDesc& d = net->d;
+    const int n = d.n;
+    if (n > 1 && !pairs) return fail(TN_EINVAL, "tree_pairs is NULL");
+    if (n_sliced < 0 || (n_sliced > 0 && !sliced)) return fail(TN_EINVAL, "bad sliced labels");
+    if (mode < TN_MODE_FP32 || mode > TN_MODE_BF16_SPLIT) return fail(TN_EINVAL, "bad mode");
+    std::vector<int32_t> pv(pairs, pairs + 2 * (size_t)(n - 1));
+    std::vector<int64_t> sv(sliced, sliced + n_sliced);
+    for (auto& p : net->plans)
+        if (p->mode == mode && p->pairs == pv && p->sliced_ids == sv) {
+            *out = p.get();
+            return TN_OK;
+        }
+    std::unique_ptr<Plan> p(new (std::nothrow) Plan);
+    if (!p) return fail(TN_ENOMEM, "out of host memory");
+    p->mode = mode;
+    p->pairs = pv;
+    p->sliced_ids = sv;
+    std::string err;
+    tn_status st = tn::build_plan(d, *p, err);
+    if (st != TN_OK) return fail(st, err);
+    net->plans.push_back(std::move(p));
+    *out = net->plans.back().get();
+    return TN_OK;
+}
+
+// Device state of a plan is created on its first run (host-only planning
+// stays usable without a GPU, e.g. for tn_plan_info).
+static tn_status ensure_device(tn_net* net, Plan* p) {
+    if (p->ws) return TN_OK;
+    if (net->d.n == 1 && !net->unit) {
+        float one[2] = {1.f, 0.f};
+        TN_CUDA(cudaMalloc(&net->unit, 16));
+        TN_CUDA(cudaMemcpy(net->unit, one, sizeof(one), cudaMemcpyHostToDevice));
+    }
+    std::string err;
+    tn_status st = tn::alloc_plan(net->d, *p, net->unit, err);
+    if (st != TN_OK) {
+        tn::free_device(*p);
+        return fail(st, err);
+    }
+    return TN_OK;
+}
+
+tn_status tn_contract_ex(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
+                         const int64_t* sliced_labels, tn_mode mode, const tn_options* opt, void* out,
+                         int32_t out_mem, int64_t* out_exp2, void* stream) {
+    if (!net) return fail(TN_EINVAL, "tn_contract: net is NULL");
+    if (!out || !out_exp2) return fail(TN_EINVAL, "tn_contract: NULL output");
+    if (out_mem != TN_MEM_DEVICE && out_mem != TN_MEM_HOST) return fail(TN_EINVAL, "bad out_mem");
+    for (int v = 0; v < net->d.n; ++v)
+        if (!net->d.leaves[v].ptr) return fail(TN_EINVAL, "tn_contract: tensor without data");
+    Plan* p = nullptr;
+    tn_status st = get_plan(net, tree_pairs, n_sliced, sliced_labels, mode, &p);
+    if (st != TN_OK) return st;
+    st = ensure_device(net, p);
+    if (st != TN_OK) return st;
+    tn_options o{};
+    if (opt) o = *opt;
+    int64_t begin = o.slice_begin, count = o.slice_count;
+    if (count <= 0) {
+        begin = 0;
+        count = p->d_sliced;
+    }
+    if (begin < 0 || begin + count > p->d_sliced) return fail(TN_EINVAL, "slice range out of bounds");
+    std::string err;
+    st = tn::run_plan(net->d, *p, net->unit, begin, count, o, out, out_mem, out_exp2,
+                      (cudaStream_t)stream, err);
+    if (st != TN_OK) return fail(st, err);
+    return TN_OK;
+}
+
+tn_status tn_contract(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
+                      const int64_t* sliced_labels, tn_mode mode, void* out, int32_t out_mem,
+                      int64_t* out_exp2, void* stream) {
+    return tn_contract_ex(net, tree_pairs, n_sliced, sliced_labels, mode, nullptr, out, out_mem,
+                          out_exp2, stream);
+}
+
+tn_status tn_contract_grad(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
+                           const int64_t* sliced_labels, tn_mode mode, const double* out_adjoint,
+                           int64_t adj_exp2, void* const* leaf_grads, void* stream) {
+    if (!net) return fail(TN_EINVAL, "tn_contract_grad: net is NULL");
+    if (!out_adjoint || !leaf_grads) return fail(TN_EINVAL, "tn_contract_grad: NULL argument");
+    for (int v = 0; v < net->d.n; ++v)
+        if (!net->d.leaves[v].ptr) return fail(TN_EINVAL, "tn_contract_grad: tensor without data");
+    Plan* p = nullptr;
+    tn_status st = get_plan(net, tree_pairs, n_sliced, sliced_labels, mode, &p);
+    if (st != TN_OK) return st;
+    st = ensure_device(net, p);
+    if (st != TN_OK) return st;
+    std::string err;
+    st = tn::run_grad(net->d, *p, net->unit, out_adjoint, adj_exp2, leaf_grads, (cudaStream_t)stream,
+                      err);
+    if (st != TN_OK) return fail(st, err);
+    return TN_OK;
+}
+
+tn_status tn_plan_info(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
+                       const int64_t* sliced_labels, tn_mode mode, double out[8]) {
+    if (!net || !out) return fail(TN_EINVAL, "tn_plan_info: NULL argument");
+    Plan* p = nullptr;
+    tn_status st = get_plan(net, tree_pairs, n_sliced, sliced_labels, mode, &p);
+    if (st != TN_OK) return st;
+    tn::plan_info(net->d, *p, out);
+    return TN_OK;
+}
+
+void tn_destroy(tn_net* net) {
+    if (!net) return;
+    cudaDeviceSynchronize();
+    for (auto& p : net->plans) tn::free_device(*p);
+    for (auto& lf : net->d.leaves)
+        if (lf.staged) cudaFree(lf.staged);
+    if (net->unit) cudaFree(net->unit);
+    delete net;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// tn_internal.h -- structures shared by the host planner and the CUDA kernels
+// of libtn.so.  Not part of the public C-ABI (include/tn.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tn {
+
+// Maximum number of index digits (labels) handled by one generic node launch
+// in each of its output and summed label sets.
+constexpr int kMaxDigits = 40;
+// Maximum number of sliced labels present in one leaf operand.
+constexpr int kMaxSliceDigits = 16;
+// Maximum number of bits per index group of the tiled kernels.
+constexpr int kMaxBits = 40;
+
+// Device-side control block of one contraction call (one per plan).
+struct Control {
+    int64_t slice;        // current slice id
+    int64_t slice_begin;  // first slice id of the call
+    int64_t acc_exp[2];   // double-buffered exponent of the FP64 accumulator
+    int64_t final_exp;    // exponent of the result after the last slice
+    int32_t status;       // 0 ok; TN_ETIMEOUT etc. set by device code
+    int32_t pad;
+};
+
+// Offset of a sliced leaf: sum over its sliced labels of
+// ((slice / div) % dim) * stride.
+struct SliceDigits {
+    int n;
+    int64_t div[kMaxSliceDigits];
+    int64_t dim[kMaxSliceDigits];
+    int64_t stride[kMaxSliceDigits];
+};
+
+// Power-of-two renormalisation bookkeeping of a node (Sec. 4.2 of the
+// paper): the stored tensor times 2^exps[slot] is the true tensor; maxabs
+// holds the largest |component| of the stored tensor (float bits).
+struct ScaleIO {
+    const unsigned* max_a;   // nullptr for a leaf operand (scale 1)
+    const unsigned* max_b;
+    const int64_t* exp_a;    // nullptr for a leaf operand (exponent 0)
+    const int64_t* exp_b;
+    unsigned* max_c;
+    int64_t* exp_c;
+};
+
+// Generic node: out[o] = sum_k A[offA(o,k)] * B[offB(o,k)] with mixed-radix
+// digits; handles any label sizes, batch (hyper) labels and labels summed
+// in one operand only (stride 0 in the other).
+struct GenericArgs {
+    const void* A;
+    const void* B;
+    void* C;
+    int64_t n_out;
+    int64_t n_sum;
+    int n_od;                       // output digits, fastest first
+    int n_kd;                       // summed digits, fastest first
+    int32_t od_dim[kMaxDigits];
+    int64_t od_sa[kMaxDigits];
+    int64_t od_sb[kMaxDigits];
+    int32_t kd_dim[kMaxDigits];
+    int64_t kd_sa[kMaxDigits];
+    int64_t kd_sb[kMaxDigits];
+    SliceDigits sla, slb;
+    const Control* ctl;
+    ScaleIO sc;
+};
+
+// Tiled node (power-of-two label sizes): every index group is a set of bits.
+// offset(group index g) = sum_i bit_i(g) << shift_i ; shift 255 = absent.
+struct BitGroup {
+    int nbits;
+    uint8_t sh[kMaxBits];
+};
+
+// Per-slice FP64 accumulation of the root tensor into the output
+// (Sec. 4.7.1: the sliced contractions are summed), with exponent
+// alignment.  od_*: digits of the output in the user's open-label order,
+// fastest first, with strides into the root tensor.
+struct AccumArgs {
+    const void* R;
+    int64_t n_out;
+    int n_od;
+    int32_t od_dim[kMaxDigits];
+    int64_t od_s[kMaxDigits];
+    const unsigned* max_r;
+    const int64_t* exp_r;
+    double* acc;
+    Control* ctl;
+};
+
+// Launchers (tn_kernels.cu).  is_c: complex64 data.
+cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s);
+cudaError_t launch_accumulate(const AccumArgs& a, bool is_c, cudaStream_t s);
+cudaError_t launch_begin_call(Control* ctl, int64_t slice_begin, double* acc, int64_t n_acc_doubles,
+                              cudaStream_t s);
+cudaError_t launch_begin_slice(unsigned* maxabs, int n_nodes, cudaStream_t s);
+cudaError_t launch_advance(Control* ctl, cudaStream_t s);
+cudaError_t launch_finalize(Control* ctl, int parity, cudaStream_t s);
+
+}  // namespace tn

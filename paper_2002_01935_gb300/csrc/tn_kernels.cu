@@ -1,0 +1,220 @@
+// tn_kernels.cu -- generic node kernel, renormalisation helpers and the FP64
+// cross-slice accumulation of libtn.so (sm_103a).
+//
+// Semantics (arXiv 2002.01935):
+//   * a pairwise contraction takes the inner product over the shared
+//     labels, an outer product if there are none (Sec. 2);
+//   * after each contraction the tensor is renormalised by a power of two
+//     and the exponent is carried along (Sec. 4.2, active renormalisation);
+//     here the scale is applied when the consumer reads the tensor: the
+//     stored tensor S and exponent E mean S * 2^E, and a consumer multiplies
+//     S by 2^-e, e = frexp exponent of max |component| of S, which is exact;
+//   * the sliced contractions are summed in FP64 with exponent alignment
+//     (Sec. 4.7.1).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+__device__ __forceinline__ int exp_of_max(const unsigned* slot) {
+    if (slot == nullptr) return 0;
+    float m = __uint_as_float(*slot);
+    if (!(m > 0.f)) return 0;
+    int e;
+    frexpf(m, &e);
+    return e;
+}
+
+__device__ __forceinline__ int64_t slice_offset(const SliceDigits& d, int64_t slice) {
+    int64_t off = 0;
+    for (int i = 0; i < d.n; ++i) off += ((slice / d.div[i]) % d.dim[i]) * d.stride[i];
+    return off;
+}
+
+// Block-wide max of non-negative floats, folded into *slot with atomicMax
+// on the float bit pattern (order-preserving for non-negative floats).
+__device__ __forceinline__ void block_max_to(float v, unsigned* slot) {
+    __shared__ float red[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        v = lane < nw ? red[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0 && v > 0.f) atomicMax(slot, __float_as_uint(v));
+    }
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(256) k_generic(const GenericArgs a) {
+    const int eA = exp_of_max(a.sc.max_a);
+    const int eB = exp_of_max(a.sc.max_b);
+    const int esum = eA + eB;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int64_t s = (a.sc.exp_a ? *a.sc.exp_a : 0) + (a.sc.exp_b ? *a.sc.exp_b : 0) + esum;
+        *a.sc.exp_c = s;
+    }
+    const int64_t slice = a.ctl->slice;
+    const int64_t baseA = slice_offset(a.sla, slice);
+    const int64_t baseB = slice_offset(a.slb, slice);
+    float lmax = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
+        int64_t ia = baseA, ib = baseB, rem = o;
+        for (int i = 0; i < a.n_od; ++i) {
+            int64_t d = a.od_dim[i];
+            int64_t v = rem % d;
+            rem /= d;
+            ia += v * a.od_sa[i];
+            ib += v * a.od_sb[i];
+        }
+        int cnt[kMaxDigits];
+        for (int i = 0; i < a.n_kd; ++i) cnt[i] = 0;
+        float re = 0.f, im = 0.f;
+        for (int64_t k = 0; k < a.n_sum; ++k) {
+            if (CPLX) {
+                float2 x = reinterpret_cast<const float2*>(a.A)[ia];
+                float2 y = reinterpret_cast<const float2*>(a.B)[ib];
+                re = fmaf(x.x, y.x, re);
+                re = fmaf(-x.y, y.y, re);
+                im = fmaf(x.x, y.y, im);
+                im = fmaf(x.y, y.x, im);
+            } else {
+                re = fmaf(reinterpret_cast<const float*>(a.A)[ia],
+                          reinterpret_cast<const float*>(a.B)[ib], re);
+            }
+            for (int i = 0; i < a.n_kd; ++i) {
+                ia += a.kd_sa[i];
+                ib += a.kd_sb[i];
+                if (++cnt[i] < a.kd_dim[i]) break;
+                ia -= a.kd_sa[i] * a.kd_dim[i];
+                ib -= a.kd_sb[i] * a.kd_dim[i];
+                cnt[i] = 0;
+            }
+        }
+        re = ldexpf(re, -esum);
+        if (CPLX) {
+            im = ldexpf(im, -esum);
+            reinterpret_cast<float2*>(a.C)[o] = make_float2(re, im);
+            lmax = fmaxf(lmax, fmaxf(fabsf(re), fabsf(im)));
+        } else {
+            reinterpret_cast<float*>(a.C)[o] = re;
+            lmax = fmaxf(lmax, fabsf(re));
+        }
+    }
+    block_max_to(lmax, a.sc.max_c);
+}
+
+cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s) {
+    int64_t blocks = (a.n_out + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    if (is_c)
+        k_generic<true><<<(unsigned)blocks, 256, 0, s>>>(a);
+    else
+        k_generic<false><<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// FP64 cross-slice accumulation (Sec. 4.7.1) with exponent alignment
+// --------------------------------------------------------------------------
+
+template <bool CPLX>
+__global__ void __launch_bounds__(256) k_accumulate(const AccumArgs a) {
+    const int64_t step = a.ctl->slice - a.ctl->slice_begin;
+    const int par = (int)(step & 1);
+    const int64_t accE = a.ctl->acc_exp[par];
+    const float rmax = __uint_as_float(*a.max_r);
+    const int64_t S = *a.exp_r;
+    const bool empty = accE == INT64_MIN;
+    const bool zero = !(rmax > 0.f);
+    int64_t newE = zero ? accE : (empty ? S : (S > accE ? S : accE));
+    double fa = 1.0, fr = 0.0;
+    if (!zero) {
+        int64_t da = empty ? 0 : accE - newE;
+        int64_t dr = S - newE;
+        fa = ldexp(1.0, (int)(da < -2000 ? -2000 : da));
+        fr = ldexp(1.0, (int)(dr < -2000 ? -2000 : dr));
+    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
+        int64_t src = 0, rem = o;
+        for (int i = 0; i < a.n_od; ++i) {
+            int64_t d = a.od_dim[i];
+            src += (rem % d) * a.od_s[i];
+            rem /= d;
+        }
+        if (CPLX) {
+            float2 r = reinterpret_cast<const float2*>(a.R)[src];
+            double2* acc = reinterpret_cast<double2*>(a.acc);
+            double2 v = acc[o];
+            v.x = v.x * fa + (double)r.x * fr;
+            v.y = v.y * fa + (double)r.y * fr;
+            acc[o] = v;
+        } else {
+            float r = reinterpret_cast<const float*>(a.R)[src];
+            a.acc[o] = a.acc[o] * fa + (double)r * fr;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->acc_exp[par ^ 1] = newE;
+}
+
+cudaError_t launch_accumulate(const AccumArgs& a, bool is_c, cudaStream_t s) {
+    int64_t blocks = (a.n_out + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    if (is_c)
+        k_accumulate<true><<<(unsigned)blocks, 256, 0, s>>>(a);
+    else
+        k_accumulate<false><<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void k_begin_call(Control* ctl, int64_t slice_begin, double* acc, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        ctl->slice = slice_begin;
+        ctl->slice_begin = slice_begin;
+        ctl->acc_exp[0] = INT64_MIN;
+        ctl->acc_exp[1] = INT64_MIN;
+        ctl->status = 0;
+    }
+    for (; i < n; i += (int64_t)gridDim.x * blockDim.x) acc[i] = 0.0;
+}
+
+cudaError_t launch_begin_call(Control* ctl, int64_t slice_begin, double* acc, int64_t n,
+                              cudaStream_t s) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) blocks = 1;
+    k_begin_call<<<(unsigned)blocks, 256, 0, s>>>(ctl, slice_begin, acc, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_begin_slice(unsigned* maxabs, int n_nodes, cudaStream_t s) {
+    return cudaMemsetAsync(maxabs, 0, sizeof(unsigned) * (size_t)n_nodes, s);
+}
+
+__global__ void k_advance(Control* ctl) { ctl->slice += 1; }
+
+cudaError_t launch_advance(Control* ctl, cudaStream_t s) {
+    k_advance<<<1, 1, 0, s>>>(ctl);
+    return cudaGetLastError();
+}
+
+__global__ void k_finalize(Control* ctl, int parity) {
+    int64_t e = ctl->acc_exp[parity];
+    ctl->final_exp = (e == INT64_MIN) ? 0 : e;
+}
+
+cudaError_t launch_finalize(Control* ctl, int parity, cudaStream_t s) {
+    k_finalize<<<1, 1, 0, s>>>(ctl, parity);
+    return cudaGetLastError();
+}
+
+}  // namespace tn

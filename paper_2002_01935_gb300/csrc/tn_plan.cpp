@@ -1,0 +1,581 @@
+// tn_plan.cpp -- node planning, workspace liveness and the per-call runtime
+// of libtn.so.  See tn_api.cpp for the overview.
+#include "tn_plan.h"
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+namespace tn {
+
+namespace {
+
+struct SubCount {
+    std::vector<std::pair<int, int>> c;  // (label, leaves of the subtree holding it)
+    int get(int l) const {
+        for (auto& x : c)
+            if (x.first == l) return x.second;
+        return 0;
+    }
+};
+
+int64_t stride_in(const std::vector<int>& lab, const std::vector<int64_t>& st, int l) {
+    for (size_t i = 0; i < lab.size(); ++i)
+        if (lab[i] == l) return st[i];
+    return 0;
+}
+
+bool has(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
+
+// Best-fit workspace allocator over element offsets (liveness planning).
+struct Arena {
+    std::map<int64_t, int64_t> free_;  // offset -> length
+    int64_t end = 0;
+    static int64_t round(int64_t n) { return (n + 63) / 64 * 64; }
+    int64_t alloc(int64_t n) {
+        n = round(n);
+        auto best = free_.end();
+        for (auto it = free_.begin(); it != free_.end(); ++it)
+            if (it->second >= n && (best == free_.end() || it->second < best->second)) best = it;
+        if (best != free_.end()) {
+            int64_t off = best->first, len = best->second;
+            free_.erase(best);
+            if (len > n) free_[off + n] = len - n;
+            return off;
+        }
+        // extend, merging a free tail block
+        if (!free_.empty()) {
+            auto last = std::prev(free_.end());
+            if (last->first + last->second == end) {
+                int64_t off = last->first;
+                free_.erase(last);
+                end = off + n;
+                return off;
+            }
+        }
+        int64_t off = end;
+        end += n;
+        return off;
+    }
+    void release(int64_t off, int64_t n) {
+        n = round(n);
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+}  // namespace
+
+tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
+    const int n = d.n;
+    const int L = (int)d.dims.size();
+    // ---- tree validation (Sec. 2: leaves first, children before parents)
+    if ((int64_t)p.pairs.size() != 2 * (int64_t)(n - 1)) {
+        err = "tree must have n_tensors-1 pairs";
+        return TN_EINVAL;
+    }
+    std::vector<char> used(2 * n, 0);
+    for (int k = 0; k < n - 1; ++k) {
+        int me = n + k;
+        for (int j = 0; j < 2; ++j) {
+            int c = p.pairs[2 * k + j];
+            if (c < 0 || c >= me) {
+                err = "tree child id out of range";
+                return TN_EINVAL;
+            }
+            if (used[c]) {
+                err = "tree id used twice";
+                return TN_EINVAL;
+            }
+            used[c] = 1;
+        }
+    }
+    // ---- sliced labels (Sec. 4.7.1)
+    std::vector<char> is_open(L, 0), is_sl(L, 0);
+    for (int l : d.open) is_open[l] = 1;
+    p.sliced.clear();
+    p.d_sliced = 1;
+    for (int64_t id : p.sliced_ids) {
+        auto it = d.id2d.find(id);
+        if (it == d.id2d.end()) {
+            err = "unknown sliced label";
+            return TN_EINVAL;
+        }
+        int l = it->second;
+        if (is_open[l]) {
+            err = "sliced label is open";
+            return TN_EINVAL;
+        }
+        if (is_sl[l]) {
+            err = "sliced label repeated";
+            return TN_EINVAL;
+        }
+        is_sl[l] = 1;
+        p.sliced.push_back(l);
+        if (p.d_sliced > (INT64_MAX / 4) / d.dims[l]) {
+            err = "too many slices";
+            return TN_EUNSUPPORTED;
+        }
+        p.d_sliced *= d.dims[l];
+    }
+    const int ns = (int)p.sliced.size();
+    std::vector<int64_t> sdiv(ns, 1);
+    for (int j = ns - 2; j >= 0; --j) sdiv[j] = sdiv[j + 1] * d.dims[p.sliced[j + 1]];
+
+    // ---- per-vertex labels after slicing
+    const int NV = 2 * n - 1;
+    p.vlab.assign(NV, {});
+    p.vstride.assign(NV, {});
+    p.leaf_sl.assign(n, SliceDigits{});
+    std::vector<int> total(L, 0);
+    std::vector<SubCount> sub(NV);
+    for (int v = 0; v < n; ++v) {
+        const LeafDesc& lf = d.leaves[v];
+        SliceDigits& sd = p.leaf_sl[v];
+        sd.n = 0;
+        for (size_t i = 0; i < lf.lab.size(); ++i) {
+            int l = lf.lab[i];
+            if (is_sl[l]) {
+                if (sd.n >= kMaxSliceDigits) {
+                    err = "too many sliced labels in one tensor";
+                    return TN_EUNSUPPORTED;
+                }
+                int j = (int)(std::find(p.sliced.begin(), p.sliced.end(), l) - p.sliced.begin());
+                sd.div[sd.n] = sdiv[j];
+                sd.dim[sd.n] = d.dims[l];
+                sd.stride[sd.n] = lf.stride[i];
+                sd.n++;
+                continue;
+            }
+            p.vlab[v].push_back(l);
+            p.vstride[v].push_back(lf.stride[i]);
+            total[l]++;
+            sub[v].c.push_back({l, 1});
+        }
+    }
+    // ---- nodes
+    p.nodes.clear();
+    double W = 0, C = 0;
+    auto log2size = [&](const std::vector<int>& lab) {
+        double s = 0;
+        for (int l : lab) s += std::log2((double)d.dims[l]);
+        return s;
+    };
+    for (int v = 0; v < n; ++v) W = std::max(W, log2size(p.vlab[v]));
+    auto make_node = [&](int id, int a, int b, const std::vector<int>& keep) -> Node {
+        // a, b: tree ids or -1 (unit scalar: no labels)
+        static const std::vector<int> none;
+        static const std::vector<int64_t> nones;
+        const std::vector<int>& la = a >= 0 ? p.vlab[a] : none;
+        const std::vector<int>& lb = b >= 0 ? p.vlab[b] : none;
+        const std::vector<int64_t>& sa = a >= 0 ? p.vstride[a] : nones;
+        const std::vector<int64_t>& sb = b >= 0 ? p.vstride[b] : nones;
+        int64_t size_a = 1, size_b = 1;
+        for (int l : la) size_a *= d.dims[l];
+        for (int l : lb) size_b *= d.dims[l];
+        // role: the larger operand takes the B (inner, fastest output) role
+        bool swap = size_a > size_b;
+        Node nd;
+        nd.id = id;
+        nd.ca = swap ? b : a;
+        nd.cb = swap ? a : b;
+        const std::vector<int>& A = swap ? lb : la;
+        const std::vector<int>& B = swap ? la : lb;
+        const std::vector<int64_t>& SA = swap ? sb : sa;
+        const std::vector<int64_t>& SB = swap ? sa : sb;
+        for (int l : A) {
+            bool inb = has(B, l), kept = has(keep, l);
+            if (inb && kept) nd.gb.push_back(l);
+            else if (inb) nd.gk.push_back(l);
+            else if (kept) nd.gm.push_back(l);
+            else nd.gsa.push_back(l);
+        }
+        for (int l : B) {
+            if (has(A, l)) continue;
+            if (has(keep, l)) nd.gn.push_back(l);
+            else nd.gsb.push_back(l);
+        }
+        auto by_desc = [&](const std::vector<int64_t>& S, const std::vector<int>& lab) {
+            return [&](int x, int y) { return stride_in(lab, S, x) > stride_in(lab, S, y); };
+        };
+        std::sort(nd.gb.begin(), nd.gb.end(), by_desc(SA, A));
+        std::sort(nd.gm.begin(), nd.gm.end(), by_desc(SA, A));
+        std::sort(nd.gn.begin(), nd.gn.end(), by_desc(SB, B));
+        std::sort(nd.gk.begin(), nd.gk.end(), by_desc(SB, B));
+        nd.lab = nd.gb;
+        nd.lab.insert(nd.lab.end(), nd.gm.begin(), nd.gm.end());
+        nd.lab.insert(nd.lab.end(), nd.gn.begin(), nd.gn.end());
+        nd.stride.assign(nd.lab.size(), 1);
+        nd.size = 1;
+        for (int i = (int)nd.lab.size() - 1; i >= 0; --i) {
+            nd.stride[i] = nd.size;
+            nd.size *= d.dims[nd.lab[i]];
+        }
+        std::vector<int> uni = A;
+        for (int l : B)
+            if (!has(uni, l)) uni.push_back(l);
+        nd.vc = log2size(uni);
+        return nd;
+    };
+    if (n == 1) {
+        std::vector<int> keep = d.open;
+        Node nd = make_node(n, 0, -1, keep);
+        // the unit operand is smaller: make sure the leaf is an operand
+        p.vlab.push_back(nd.lab);
+        p.vstride.push_back(nd.stride);
+        W = std::max(W, log2size(nd.lab));
+        C += std::pow(2.0, nd.vc);
+        p.nodes.push_back(nd);
+    } else {
+        for (int k = 0; k < n - 1; ++k) {
+            int a = p.pairs[2 * k], b = p.pairs[2 * k + 1], me = n + k;
+            std::vector<int> keep;
+            SubCount sc;
+            auto visit = [&](int c, int other) {
+                for (auto& x : sub[c].c) {
+                    int l = x.first;
+                    if (c == b && sub[a].get(l)) continue;
+                    int cnt = x.second + (c == a ? sub[b].get(l) : 0);
+                    if (is_open[l] || cnt < total[l]) {
+                        keep.push_back(l);
+                        sc.c.push_back({l, cnt});
+                    }
+                }
+                (void)other;
+            };
+            visit(a, b);
+            visit(b, a);
+            sub[me] = sc;
+            sub[a].c.clear();
+            sub[b].c.clear();
+            Node nd = make_node(me, a, b, keep);
+            p.vlab[me] = nd.lab;
+            p.vstride[me] = nd.stride;
+            W = std::max(W, log2size(nd.lab));
+            C += std::pow(2.0, nd.vc);
+            p.nodes.push_back(nd);
+        }
+    }
+    // root labels must be exactly the open labels
+    const Node& root = p.nodes.back();
+    if (root.lab.size() != d.open.size()) {
+        err = "internal: root labels differ from the open labels";
+        return TN_EINVAL;
+    }
+    p.W = W;
+    p.C = C;
+    // ---- workspace liveness: children die when their parent is formed
+    Arena ar;
+    std::vector<int64_t> off(p.nodes.size());
+    for (size_t k = 0; k < p.nodes.size(); ++k) {
+        Node& nd = p.nodes[k];
+        nd.ws_off = ar.alloc(nd.size);
+        for (int c : {nd.ca, nd.cb})
+            if (c >= n) {
+                const Node& ch = p.nodes[c - n];
+                ar.release(ch.ws_off, ch.size);
+            }
+        nd.kind = kGeneric;
+    }
+    p.ws_elems = std::max<int64_t>(ar.end, 64);
+    p.n_out = 1;
+    for (int l : d.open) p.n_out *= d.dims[l];
+    return TN_OK;
+}
+
+static tn_status fill_generic(const NetDesc& d, const Plan& p, const Node& nd, GenericArgs& g,
+                              std::string& err) {
+    memset(&g, 0, sizeof(g));
+    const int n = d.n;
+    static const std::vector<int> none;
+    static const std::vector<int64_t> nones;
+    const std::vector<int>& la = nd.ca >= 0 ? p.vlab[nd.ca] : none;
+    const std::vector<int>& lb = nd.cb >= 0 ? p.vlab[nd.cb] : none;
+    const std::vector<int64_t>& sa = nd.ca >= 0 ? p.vstride[nd.ca] : nones;
+    const std::vector<int64_t>& sb = nd.cb >= 0 ? p.vstride[nd.cb] : nones;
+    if ((int)nd.lab.size() > kMaxDigits) {
+        err = "node rank exceeds the generic kernel limit";
+        return TN_EUNSUPPORTED;
+    }
+    g.n_out = nd.size;
+    g.n_od = (int)nd.lab.size();
+    for (int i = 0; i < g.n_od; ++i) {
+        int l = nd.lab[nd.lab.size() - 1 - i];
+        g.od_dim[i] = (int32_t)d.dims[l];
+        g.od_sa[i] = stride_in(la, sa, l);
+        g.od_sb[i] = stride_in(lb, sb, l);
+    }
+    std::vector<int> ks = nd.gk;
+    ks.insert(ks.end(), nd.gsa.begin(), nd.gsa.end());
+    ks.insert(ks.end(), nd.gsb.begin(), nd.gsb.end());
+    std::sort(ks.begin(), ks.end(), [&](int x, int y) {
+        return stride_in(lb, sb, x) + stride_in(la, sa, x) < stride_in(lb, sb, y) + stride_in(la, sa, y);
+    });
+    if ((int)ks.size() > kMaxDigits) {
+        err = "too many summed labels in one node";
+        return TN_EUNSUPPORTED;
+    }
+    g.n_kd = (int)ks.size();
+    g.n_sum = 1;
+    for (int i = 0; i < g.n_kd; ++i) {
+        int l = ks[i];
+        g.kd_dim[i] = (int32_t)d.dims[l];
+        g.kd_sa[i] = stride_in(la, sa, l);
+        g.kd_sb[i] = stride_in(lb, sb, l);
+        g.n_sum *= d.dims[l];
+    }
+    if (nd.ca >= 0 && nd.ca < n) g.sla = p.leaf_sl[nd.ca];
+    if (nd.cb >= 0 && nd.cb < n) g.slb = p.leaf_sl[nd.cb];
+    return TN_OK;
+}
+
+tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
+    const size_t eb = d.elem_bytes();
+    const int nn = (int)p.nodes.size();
+    auto ck = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess) {
+            err = std::string(what) + ": " + cudaGetErrorString(e);
+            return false;
+        }
+        return true;
+    };
+    if (!ck(cudaMalloc(&p.ws, (size_t)p.ws_elems * eb), "workspace allocation")) return TN_ENOMEM;
+    if (!ck(cudaMalloc(&p.maxabs, sizeof(unsigned) * nn), "cudaMalloc")) return TN_ENOMEM;
+    if (!ck(cudaMalloc(&p.exps, sizeof(int64_t) * nn), "cudaMalloc")) return TN_ENOMEM;
+    if (!ck(cudaMalloc(&p.ctl, sizeof(Control)), "cudaMalloc")) return TN_ENOMEM;
+    size_t acc_doubles = (size_t)p.n_out * (d.is_complex() ? 2 : 1);
+    if (!ck(cudaMalloc(&p.acc, sizeof(double) * acc_doubles), "cudaMalloc")) return TN_ENOMEM;
+    if (!ck(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking), "stream")) return TN_ECUDA;
+    // node launch arguments; leaf pointers are patched per call
+    p.gen.resize(nn);
+    const int n = d.n;
+    for (int k = 0; k < nn; ++k) {
+        const Node& nd = p.nodes[k];
+        GenericArgs& g = p.gen[k];
+        tn_status st = fill_generic(d, p, nd, g, err);
+        if (st != TN_OK) return st;
+        char* ws = (char*)p.ws;
+        g.C = ws + nd.ws_off * eb;
+        g.A = nd.ca >= n ? (const void*)(ws + p.nodes[nd.ca - n].ws_off * eb) : nullptr;
+        g.B = nd.cb >= n ? (const void*)(ws + p.nodes[nd.cb - n].ws_off * eb) : nullptr;
+        if (nd.ca < 0) g.A = unit;
+        if (nd.cb < 0) g.B = unit;
+        g.ctl = p.ctl;
+        g.sc.max_a = nd.ca >= n ? p.maxabs + (nd.ca - n) : nullptr;
+        g.sc.exp_a = nd.ca >= n ? p.exps + (nd.ca - n) : nullptr;
+        g.sc.max_b = nd.cb >= n ? p.maxabs + (nd.cb - n) : nullptr;
+        g.sc.exp_b = nd.cb >= n ? p.exps + (nd.cb - n) : nullptr;
+        g.sc.max_c = p.maxabs + k;
+        g.sc.exp_c = p.exps + k;
+    }
+    // root accumulation: user open-label order -> root layout
+    const Node& root = p.nodes.back();
+    AccumArgs& a = p.acc_args;
+    memset(&a, 0, sizeof(a));
+    a.R = (char*)p.ws + root.ws_off * eb;
+    a.n_out = p.n_out;
+    a.n_od = (int)d.open.size();
+    if (a.n_od > kMaxDigits) {
+        err = "too many open labels";
+        return TN_EUNSUPPORTED;
+    }
+    for (int i = 0; i < a.n_od; ++i) {
+        int l = d.open[d.open.size() - 1 - i];
+        a.od_dim[i] = (int32_t)d.dims[l];
+        a.od_s[i] = stride_in(root.lab, root.stride, l);
+    }
+    a.max_r = p.maxabs + (nn - 1);
+    a.exp_r = p.exps + (nn - 1);
+    a.acc = p.acc;
+    a.ctl = p.ctl;
+    return TN_OK;
+}
+
+// One slice: reset the node maxima, run every node, fold the root into the
+// FP64 accumulator, advance the slice counter.  ev: optional timing events
+// around nodes [pf, pf + pc).
+static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, const cudaEvent_t* ev,
+                                 int pf, int pc) {
+    cudaError_t e = launch_begin_slice(p.maxabs, (int)p.nodes.size(), s);
+    if (e != cudaSuccess) return e;
+    const bool c = d.is_complex();
+    for (int k = 0; k < (int)p.nodes.size(); ++k) {
+        if (ev && k >= pf && k < pf + pc && (e = cudaEventRecord(ev[k - pf], s)) != cudaSuccess)
+            return e;
+        e = launch_generic(p.gen[k], c, s);
+        if (e != cudaSuccess) return e;
+        if (ev && k == pf + pc - 1 && (e = cudaEventRecord(ev[pc], s)) != cudaSuccess) return e;
+    }
+    e = launch_accumulate(p.acc_args, c, s);
+    if (e != cudaSuccess) return e;
+    return launch_advance(p.ctl, s);
+}
+
+tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count,
+                   const tn_options& o, void* out, int out_mem, int64_t* out_exp2,
+                   cudaStream_t stream, std::string& err) {
+    (void)unit;
+    const int n = d.n;
+    const size_t eb = d.elem_bytes();
+#define CK(x)                                                     \
+    do {                                                          \
+        cudaError_t e_ = (x);                                     \
+        if (e_ != cudaSuccess) {                                  \
+            err = std::string(#x) + ": " + cudaGetErrorString(e_); \
+            return e_ == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA; \
+        }                                                         \
+    } while (0)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(stream, &cap));
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    // profiling hooks
+    int pf = 0, pc = 0;
+    const cudaEvent_t* uev = nullptr;
+    if (o.prof_events && o.prof_count > 0) {
+        pf = o.prof_first;
+        pc = o.prof_count;
+        if (pf < 0 || pf + pc > (int)p.nodes.size()) {
+            err = "profiling node range out of bounds";
+            return TN_EINVAL;
+        }
+        uev = reinterpret_cast<const cudaEvent_t*>(o.prof_events);
+    }
+    // leaf pointers (host leaves are staged into library memory)
+    std::vector<const void*> lp(n);
+    for (int v = 0; v < n; ++v) {
+        LeafDesc& lf = d.leaves[v];
+        if (lf.mem == TN_MEM_HOST) {
+            int64_t bytes = std::max<int64_t>(lf.size * (int64_t)eb, 16);
+            if (lf.staged_bytes < bytes) {
+                if (capturing) {
+                    err = "host leaves need a first call outside stream capture";
+                    return TN_EUNSUPPORTED;
+                }
+                if (lf.staged) CK(cudaFree(lf.staged));
+                lf.staged = nullptr;
+                CK(cudaMalloc(&lf.staged, bytes));
+                lf.staged_bytes = bytes;
+            }
+            CK(cudaMemcpyAsync(lf.staged, lf.ptr, lf.size * eb, cudaMemcpyHostToDevice, stream));
+            lp[v] = lf.staged;
+        } else {
+            lp[v] = lf.ptr;
+        }
+    }
+    for (size_t k = 0; k < p.nodes.size(); ++k) {
+        const Node& nd = p.nodes[k];
+        if (nd.ca >= 0 && nd.ca < n) p.gen[k].A = lp[nd.ca];
+        if (nd.cb >= 0 && nd.cb < n) p.gen[k].B = lp[nd.cb];
+    }
+    CK(launch_begin_call(p.ctl, begin, p.acc, p.n_out * (d.is_complex() ? 2 : 1), stream));
+    const bool use_graph = !o.no_graph && !capturing;
+    if (use_graph) {
+        if (!p.gexec || p.graph_ptrs != lp || p.graph_prof_first != pf || p.graph_prof_count != pc) {
+            if (p.gexec) CK(cudaGraphExecDestroy(p.gexec));
+            if (p.graph) CK(cudaGraphDestroy(p.graph));
+            p.gexec = nullptr;
+            p.graph = nullptr;
+            while ((int)p.prof_placeholder.size() < pc + 1) {
+                cudaEvent_t ev;
+                CK(cudaEventCreate(&ev));
+                p.prof_placeholder.push_back(ev);
+            }
+            CK(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_slice(d, p, p.cap_stream, pc ? p.prof_placeholder.data() : nullptr,
+                                          pf, pc);
+            cudaError_t e2 = cudaStreamEndCapture(p.cap_stream, &p.graph);
+            CK(e);
+            CK(e2);
+            CK(cudaGraphInstantiate(&p.gexec, p.graph, 0));
+            p.graph_ptrs = lp;
+            p.graph_prof_first = pf;
+            p.graph_prof_count = pc;
+            p.prof_nodes.assign(pc + 1, nullptr);
+            if (pc) {
+                size_t nn = 0;
+                CK(cudaGraphGetNodes(p.graph, nullptr, &nn));
+                std::vector<cudaGraphNode_t> all(nn);
+                CK(cudaGraphGetNodes(p.graph, all.data(), &nn));
+                for (auto g : all) {
+                    cudaGraphNodeType t;
+                    CK(cudaGraphNodeGetType(g, &t));
+                    if (t != cudaGraphNodeTypeEventRecord) continue;
+                    cudaEvent_t ev;
+                    CK(cudaGraphEventRecordNodeGetEvent(g, &ev));
+                    for (int i = 0; i <= pc; ++i)
+                        if (p.prof_placeholder[i] == ev) p.prof_nodes[i] = g;
+                }
+            }
+        }
+        for (int i = 0; i < pc + (pc ? 1 : 0); ++i)
+            CK(cudaGraphExecEventRecordNodeSetEvent(p.gexec, p.prof_nodes[i], uev[i]));
+        for (int64_t s = 0; s < count; ++s) CK(cudaGraphLaunch(p.gexec, stream));
+    } else {
+        for (int64_t s = 0; s < count; ++s) CK(enqueue_slice(d, p, stream, uev, pf, pc));
+    }
+    CK(launch_finalize(p.ctl, (int)(count & 1), stream));
+    const size_t acc_bytes = sizeof(double) * p.n_out * (d.is_complex() ? 2 : 1);
+    cudaMemcpyKind kind = out_mem == TN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(out, p.acc, acc_bytes, kind, stream));
+    CK(cudaMemcpyAsync(out_exp2, &p.ctl->final_exp, sizeof(int64_t), kind, stream));
+    if (out_mem == TN_MEM_HOST) CK(cudaStreamSynchronize(stream));
+#undef CK
+    return TN_OK;
+}
+
+tn_status run_grad(NetDesc&, Plan&, void*, const double*, int64_t, void* const*, cudaStream_t,
+                   std::string& err) {
+    err = "tn_contract_grad: not available in this build";
+    return TN_EUNSUPPORTED;
+}
+
+void plan_info(const NetDesc& d, const Plan& p, double out[8]) {
+    out[0] = p.W;
+    out[1] = p.C;
+    out[2] = (double)p.d_sliced;
+    out[3] = (d.is_complex() ? 8.0 : 2.0) * p.C * (double)p.d_sliced;
+    out[4] = (double)p.ws_elems * (double)d.elem_bytes();
+    int cnt[3] = {0, 0, 0};
+    for (auto& nd : p.nodes) cnt[nd.kind]++;
+    out[5] = cnt[kTiled];
+    out[6] = cnt[kTensorCore];
+    out[7] = cnt[kGeneric];
+}
+
+void free_device(Plan& p) {
+    if (p.gexec) cudaGraphExecDestroy(p.gexec);
+    if (p.graph) cudaGraphDestroy(p.graph);
+    for (auto ev : p.prof_placeholder) cudaEventDestroy(ev);
+    p.prof_placeholder.clear();
+    p.prof_nodes.clear();
+    p.graph = nullptr;
+    if (p.cap_stream) cudaStreamDestroy(p.cap_stream);
+    if (p.ws) cudaFree(p.ws);
+    if (p.maxabs) cudaFree(p.maxabs);
+    if (p.exps) cudaFree(p.exps);
+    if (p.ctl) cudaFree(p.ctl);
+    if (p.acc) cudaFree(p.acc);
+    p.gexec = nullptr;
+    p.cap_stream = nullptr;
+    p.ws = nullptr;
+    p.maxabs = nullptr;
+    p.exps = nullptr;
+    p.ctl = nullptr;
+    p.acc = nullptr;
+    p.graph_ptrs.clear();
+}
+
+}  // namespace tn

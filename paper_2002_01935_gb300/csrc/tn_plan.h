@@ -1,0 +1,92 @@
+// tn_plan.h -- host-side node plan and runtime of libtn.so (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/tn.h"
+#include "tn_internal.h"
+
+namespace tn {
+
+struct LeafDesc {
+    std::vector<int> lab;         // dense label ids, tensor axis order
+    std::vector<int64_t> stride;  // row-major element strides
+    int64_t size = 1;
+    const void* ptr = nullptr;    // user pointer (device or host)
+    int mem = -1;
+    void* staged = nullptr;       // library copy of a host leaf
+    int64_t staged_bytes = 0;
+};
+
+struct NetDesc {
+    tn_dtype dt = TN_C64;
+    int n = 0;
+    std::vector<int64_t> dims;  // per dense label
+    std::vector<int64_t> ids;   // dense -> user id
+    std::unordered_map<int64_t, int> id2d;
+    std::vector<LeafDesc> leaves;
+    std::vector<int> open;  // dense labels, output axis order
+    bool is_complex() const { return dt == TN_C64; }
+    size_t elem_bytes() const { return dt == TN_C64 ? 8 : 4; }
+};
+
+enum NodeKind { kGeneric = 0, kTiled = 1, kTensorCore = 2 };
+
+struct Node {
+    int id = 0;                  // tree id (n + k)
+    int ca = 0, cb = 0;          // child tree ids in the A and B roles (-1: unit scalar)
+    std::vector<int> lab;        // output labels, slowest first (row-major)
+    std::vector<int64_t> stride;
+    int64_t size = 1;
+    int64_t ws_off = 0;          // element offset in the workspace
+    std::vector<int> gb, gm, gn, gk, gsa, gsb;  // label groups
+    int kind = kGeneric;
+    double vc = 0;               // log2 of 2^vc, Eq. vertexcon
+};
+
+struct Plan {
+    tn_mode mode = TN_MODE_FP32;
+    std::vector<int32_t> pairs;
+    std::vector<int64_t> sliced_ids;
+    std::vector<int> sliced;  // dense
+    int64_t d_sliced = 1;
+    std::vector<Node> nodes;
+    // per tree vertex (leaves then nodes): labels and strides after slicing
+    std::vector<std::vector<int>> vlab;
+    std::vector<std::vector<int64_t>> vstride;
+    std::vector<SliceDigits> leaf_sl;
+    int64_t ws_elems = 0;
+    double W = 0, C = 0;
+    int64_t n_out = 1;
+    // device state
+    void* ws = nullptr;
+    unsigned* maxabs = nullptr;
+    int64_t* exps = nullptr;
+    Control* ctl = nullptr;
+    double* acc = nullptr;
+    std::vector<GenericArgs> gen;
+    AccumArgs acc_args{};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<const void*> graph_ptrs;
+    int graph_prof_first = 0, graph_prof_count = 0;
+    std::vector<cudaEvent_t> prof_placeholder;  // events captured into the graph
+    std::vector<cudaGraphNode_t> prof_nodes;    // their record nodes, in order
+};
+
+tn_status build_plan(const NetDesc& d, Plan& p, std::string& err);
+tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err);
+tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count,
+                   const tn_options& o, void* out, int out_mem, int64_t* out_exp2,
+                   cudaStream_t stream, std::string& err);
+tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int64_t adj_exp2,
+                   void* const* grads, cudaStream_t stream, std::string& err);
+void plan_info(const NetDesc& d, const Plan& p, double out[8]);
+void free_device(Plan& p);  // releases device state; the host plan stays valid
+
+}  // namespace tn

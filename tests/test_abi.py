@@ -1,0 +1,116 @@
+"""The C-ABI library loads, exports every declared symbol, and its host-side
+planning (validation, Eqs. edgecon/vertexcon) agrees with the planner.
+No device work: these run without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2002_01935_gb300 import build
+    build.build()
+    from paper_2002_01935_gb300 import binding
+    return binding
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "tn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tn_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "tn_contract" in names and "tn_create" in names and "tn_contract_grad" in names
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for name in names:
+        assert hasattr(so, name), name
+    assert set(names) <= set(lib.EXPORTS)
+
+
+def test_version(lib):
+    assert "sm_103a" in lib.tn_version()
+
+
+@pytest.mark.parametrize("case", ["repeat", "unknown", "open_missing", "dim0", "unused"])
+def test_create_rejects_malformed_networks(lib, case):
+    dims = {0: 2, 1: 2}
+    labels = [[0, 1], [1]]
+    opn = []
+    if case == "repeat":
+        labels = [[0, 0]]
+        dims = {0: 2}
+    elif case == "unknown":
+        labels = [[0, 7]]
+    elif case == "open_missing":
+        dims = {0: 2, 1: 2, 5: 2}
+        labels = [[0, 1], [1, 5]]
+        opn = [9]
+    elif case == "dim0":
+        dims = {0: 0, 1: 2}
+    elif case == "unused":
+        dims = {0: 2, 1: 2, 3: 2}
+    with pytest.raises(lib.TNError) as e:
+        lib.tn_create(lib.TN_C64, labels, dims, opn)
+    assert e.value.status == lib.TN_EINVAL
+    assert lib.tn_last_error()
+
+
+@pytest.mark.parametrize("pairs", [[(0, 1)], [(0, 1), (1, 3)], [(0, 4), (1, 2)], [(0, 0), (1, 2)]])
+def test_malformed_trees_are_rejected(lib, pairs):
+    h = lib.tn_create(lib.TN_C64, [[0], [0, 1], [1]], {0: 2, 1: 2}, [])
+    try:
+        with pytest.raises(lib.TNError) as e:
+            lib.tn_plan_info(h, pairs, [])
+        assert e.value.status == lib.TN_EINVAL
+    finally:
+        lib.tn_destroy(h)
+
+
+def test_sliced_open_label_is_rejected(lib):
+    h = lib.tn_create(lib.TN_C64, [[0, 1], [1]], {0: 2, 1: 2}, [0])
+    try:
+        with pytest.raises(lib.TNError):
+            lib.tn_plan_info(h, [(0, 1)], [0])
+        with pytest.raises(lib.TNError):
+            lib.tn_plan_info(h, [(0, 1)], [42])
+    finally:
+        lib.tn_destroy(h)
+
+
+@pytest.mark.parametrize("which", ["circuit", "ising", "random"])
+def test_plan_costs_match_planner(lib, which):
+    """W_s, C and FLOPs of the library's node plan equal the Python cost
+    model (Eqs. edgecon, vertexcon; FLOPs 8C/2C) for the same tree."""
+    from paper_2002_01935_gb300 import inputs, planner
+    if which == "circuit":
+        net = inputs.circuit_network(inputs.random_circuit(4, 4, 8, 0),
+                                     inputs.random_bitstrings(16, 1, 1000)[0])
+    elif which == "ising":
+        net = inputs.random_ising(60, 2)
+    else:
+        net = inputs.random_network(9, 14, 3, n_open=2, max_dim=3)
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    for target in (None, 0):
+        sliced = []
+        if target is not None:
+            base = planner.tree_info(net.labels, net.dims, pairs, net.open)
+            sliced = planner.slice_greedy(net.labels, net.dims, pairs, net.open, base.W - 2)
+        ref = planner.tree_info(net.labels, net.dims, pairs, net.open, sliced)
+        h = lib.tn_create(lib.TN_C64 if net.is_complex else lib.TN_R32, net.labels, net.dims,
+                          net.open)
+        try:
+            info = lib.tn_plan_info(h, pairs, sliced)
+        finally:
+            lib.tn_destroy(h)
+        assert info["W"] == pytest.approx(ref.W)
+        assert info["C"] == pytest.approx(ref.C, rel=1e-12)
+        assert info["d_sliced"] == ref.d_sliced
+        assert info["flops"] == pytest.approx(ref.flops(net.is_complex), rel=1e-12)
+        assert info["ws_bytes"] > 0
