@@ -224,7 +224,14 @@ def main():
     # warm-up, then one per-node profile pass to find the dominant kernel
     for _ in range(args.warmup):
         m, e = tnw.contract(pairs, sliced, args.mode)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_nodes + 1)]
+    def events(n):
+        # torch creates the CUDA event lazily: record once so .cuda_event is valid
+        evl = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        for ev in evl:
+            ev.record(stream)
+        return evl
+
+    evs = events(n_nodes + 1)
     flush.zero_()
     tnw.contract(pairs, sliced, args.mode, prof_events=evs, prof_first=0)
     torch.cuda.synchronize()
@@ -234,7 +241,7 @@ def main():
     # timed region: K steps, each bracketed by events; L2 flushed between
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    dom_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    dom_ev = [events(2) for _ in range(args.steps)]
     clk = ClockSampler(local)
     if dist:
         dist.barrier()
@@ -316,7 +323,7 @@ def main():
             rel_err = abs(math.expm1(math.log(abs(result)) + (result_exp - oe) * math.log(2)
                                      - math.log(abs(float(om)))))
 
-    launches_per_step = (n_nodes + 2) * info.d_sliced + 2
+    launches_per_step = (n_nodes + 2) * info.d_sliced + 3
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

@@ -99,5 +99,7 @@ cudaError_t launch_begin_call(Control* ctl, int64_t slice_begin, double* acc, in
 cudaError_t launch_begin_slice(unsigned* maxabs, int n_nodes, cudaStream_t s);
 cudaError_t launch_advance(Control* ctl, cudaStream_t s);
 cudaError_t launch_finalize(Control* ctl, int parity, cudaStream_t s);
+cudaError_t launch_leaf_max(const float* const* ptrs, const int64_t* nfloat, unsigned* out, int n,
+                            cudaStream_t s);
 
 }  // namespace tn

@@ -207,6 +207,35 @@ cudaError_t launch_advance(Control* ctl, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Largest |component| of every leaf (one block per leaf), so that leaves are
+// renormalised like intermediates before their first contraction.
+__global__ void __launch_bounds__(256) k_leaf_max(const float* const* ptrs, const int64_t* nfloat,
+                                                  unsigned* out, int n) {
+    int v = blockIdx.x;
+    if (v >= n) return;
+    const float* p = ptrs[v];
+    int64_t m = nfloat[v];
+    float lmax = 0.f;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) lmax = fmaxf(lmax, fabsf(p[i]));
+    __shared__ float red[32];
+    for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lmax;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int nw = blockDim.x >> 5;
+        lmax = threadIdx.x < nw ? red[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        if (threadIdx.x == 0) out[v] = __float_as_uint(lmax);
+    }
+}
+
+cudaError_t launch_leaf_max(const float* const* ptrs, const int64_t* nfloat, unsigned* out, int n,
+                            cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_leaf_max<<<n, 256, 0, s>>>(ptrs, nfloat, out, n);
+    return cudaGetLastError();
+}
+
 __global__ void k_finalize(Control* ctl, int parity) {
     int64_t e = ctl->acc_exp[parity];
     ctl->final_exp = (e == INT64_MIN) ? 0 : e;

@@ -359,6 +359,16 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
     size_t acc_doubles = (size_t)p.n_out * (d.is_complex() ? 2 : 1);
     if (!ck(cudaMalloc(&p.acc, sizeof(double) * acc_doubles), "cudaMalloc")) return TN_ENOMEM;
     if (!ck(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking), "stream")) return TN_ECUDA;
+    if (!ck(cudaMalloc(&p.leafmax, sizeof(unsigned) * d.n), "cudaMalloc")) return TN_ENOMEM;
+    if (!ck(cudaMalloc((void**)&p.leaf_ptr_dev, sizeof(void*) * d.n), "cudaMalloc")) return TN_ENOMEM;
+    if (!ck(cudaMalloc(&p.leaf_nfloat_dev, sizeof(int64_t) * d.n), "cudaMalloc")) return TN_ENOMEM;
+    {
+        std::vector<int64_t> nf(d.n);
+        for (int v = 0; v < d.n; ++v) nf[v] = d.leaves[v].size * (d.is_complex() ? 2 : 1);
+        if (!ck(cudaMemcpy(p.leaf_nfloat_dev, nf.data(), sizeof(int64_t) * d.n,
+                           cudaMemcpyHostToDevice), "cudaMemcpy"))
+            return TN_ECUDA;
+    }
     // node launch arguments; leaf pointers are patched per call
     p.gen.resize(nn);
     const int n = d.n;
@@ -374,9 +384,10 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
         if (nd.ca < 0) g.A = unit;
         if (nd.cb < 0) g.B = unit;
         g.ctl = p.ctl;
-        g.sc.max_a = nd.ca >= n ? p.maxabs + (nd.ca - n) : nullptr;
+        // leaves: renormalised by their own max, stored exponent 0
+        g.sc.max_a = nd.ca >= n ? p.maxabs + (nd.ca - n) : (nd.ca >= 0 ? p.leafmax + nd.ca : nullptr);
         g.sc.exp_a = nd.ca >= n ? p.exps + (nd.ca - n) : nullptr;
-        g.sc.max_b = nd.cb >= n ? p.maxabs + (nd.cb - n) : nullptr;
+        g.sc.max_b = nd.cb >= n ? p.maxabs + (nd.cb - n) : (nd.cb >= 0 ? p.leafmax + nd.cb : nullptr);
         g.sc.exp_b = nd.cb >= n ? p.exps + (nd.cb - n) : nullptr;
         g.sc.max_c = p.maxabs + k;
         g.sc.exp_c = p.exps + k;
@@ -413,11 +424,15 @@ static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, cons
     if (e != cudaSuccess) return e;
     const bool c = d.is_complex();
     for (int k = 0; k < (int)p.nodes.size(); ++k) {
-        if (ev && k >= pf && k < pf + pc && (e = cudaEventRecord(ev[k - pf], s)) != cudaSuccess)
+        // External records become event-record nodes under stream capture.
+        if (ev && k >= pf && k < pf + pc &&
+            (e = cudaEventRecordWithFlags(ev[k - pf], s, cudaEventRecordExternal)) != cudaSuccess)
             return e;
         e = launch_generic(p.gen[k], c, s);
         if (e != cudaSuccess) return e;
-        if (ev && k == pf + pc - 1 && (e = cudaEventRecord(ev[pc], s)) != cudaSuccess) return e;
+        if (ev && k == pf + pc - 1 &&
+            (e = cudaEventRecordWithFlags(ev[pc], s, cudaEventRecordExternal)) != cudaSuccess)
+            return e;
     }
     e = launch_accumulate(p.acc_args, c, s);
     if (e != cudaSuccess) return e;
@@ -480,6 +495,14 @@ tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count
         if (nd.ca >= 0 && nd.ca < n) p.gen[k].A = lp[nd.ca];
         if (nd.cb >= 0 && nd.cb < n) p.gen[k].B = lp[nd.cb];
     }
+    if (p.leaf_ptr_uploaded != lp) {
+        // pointer table changes only when leaves are re-attached
+        CK(cudaMemcpyAsync(p.leaf_ptr_dev, lp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice,
+                           stream));
+        CK(cudaStreamSynchronize(stream));
+        p.leaf_ptr_uploaded = lp;
+    }
+    CK(launch_leaf_max(p.leaf_ptr_dev, p.leaf_nfloat_dev, p.leafmax, n, stream));
     CK(launch_begin_call(p.ctl, begin, p.acc, p.n_out * (d.is_complex() ? 2 : 1), stream));
     const bool use_graph = !o.no_graph && !capturing;
     if (use_graph) {
@@ -518,6 +541,11 @@ tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count
                     for (int i = 0; i <= pc; ++i)
                         if (p.prof_placeholder[i] == ev) p.prof_nodes[i] = g;
                 }
+                for (auto g : p.prof_nodes)
+                    if (!g) {
+                        err = "internal: timing event node missing from the captured graph";
+                        return TN_ECUDA;
+                    }
             }
         }
         for (int i = 0; i < pc + (pc ? 1 : 0); ++i)
@@ -568,6 +596,13 @@ void free_device(Plan& p) {
     if (p.exps) cudaFree(p.exps);
     if (p.ctl) cudaFree(p.ctl);
     if (p.acc) cudaFree(p.acc);
+    if (p.leafmax) cudaFree(p.leafmax);
+    if (p.leaf_ptr_dev) cudaFree(p.leaf_ptr_dev);
+    if (p.leaf_nfloat_dev) cudaFree(p.leaf_nfloat_dev);
+    p.leafmax = nullptr;
+    p.leaf_ptr_dev = nullptr;
+    p.leaf_nfloat_dev = nullptr;
+    p.leaf_ptr_uploaded.clear();
     p.gexec = nullptr;
     p.cap_stream = nullptr;
     p.ws = nullptr;

@@ -68,6 +68,10 @@ struct Plan {
     int64_t* exps = nullptr;
     Control* ctl = nullptr;
     double* acc = nullptr;
+    unsigned* leafmax = nullptr;           // max |component| of each leaf
+    const float** leaf_ptr_dev = nullptr;  // device copy of the leaf pointers
+    int64_t* leaf_nfloat_dev = nullptr;
+    std::vector<const void*> leaf_ptr_uploaded;
     std::vector<GenericArgs> gen;
     AccumArgs acc_args{};
     cudaStream_t cap_stream = nullptr;
