@@ -199,6 +199,34 @@ tn_status tn_contract_grad(tn_net *net, const int32_t *tree_pairs, int32_t n_sli
                            int64_t adj_exp2, void *const *leaf_grads, void *stream);
 
 /*
+ * tn_contract_noalloc -- tn_contract for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant.
+ * tn_contract obtains its workspace with cudaMalloc on the first run of a
+ * tree; callers that run while a CUDA graph is being captured, hosts that
+ * forbid allocation after start-up, and processes whose device memory is
+ * owned by another allocator cannot let it do so.  This call runs the same
+ * node kernels (FP32 arithmetic, as TN_MODE_FP32) with every piece of scratch
+ * -- intermediate tensors, renormalisation slots, control block, FP64
+ * accumulator -- inside one fixed 8 MiB device array that is part of the
+ * library image; it calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *   Arguments as tn_contract (no mode); the leaves must be device pointers.
+ *   Limit: the tree's workspace plus bookkeeping must fit in 8 MiB
+ *   (tn_plan_info out[4] is the workspace part); larger trees are refused
+ *   with TN_EUNSUPPORTED and a message giving the bytes needed.
+ *   The first call on a device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   Every GPU that loads the library holds the array until the process
+ *   exits.  All calls share it and it keeps the last call's contents; each
+ *   call clears what it needs cleared.  Calls whose GPU work overlaps (other
+ *   streams, other threads) race on the array and must be serialised by the
+ *   caller.
+ */
+tn_status tn_contract_noalloc(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
+                              const int64_t *sliced_labels, void *out, int32_t out_mem,
+                              int64_t *out_exp2, void *stream);
+
+/*
  * tn_plan_info -- cost figures of a (tree, slicing) for this network, from
  * Eqs. edgecon and vertexcon: out[0] = W_s (sliced width, log2 of the
  * largest tensor), out[1] = C (contraction cost of one slice), out[2] =

@@ -59,6 +59,9 @@ _lib.tn_contract_grad.restype = ctypes.c_int
 _lib.tn_contract_grad.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
                                   ctypes.POINTER(_vp), _vp]
+_lib.tn_contract_noalloc.restype = ctypes.c_int
+_lib.tn_contract_noalloc.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, _vp, ctypes.c_int32, _i64p,
+                                     _vp]
 _lib.tn_plan_info.restype = ctypes.c_int
 _lib.tn_plan_info.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int,
                               ctypes.POINTER(ctypes.c_double)]
@@ -70,7 +73,7 @@ _lib.tn_version.restype = ctypes.c_char_p
 _lib.tn_version.argtypes = []
 
 EXPORTS = ["tn_create", "tn_set_tensor", "tn_contract", "tn_contract_ex", "tn_contract_grad",
-           "tn_plan_info", "tn_destroy", "tn_last_error", "tn_version"]
+           "tn_contract_noalloc", "tn_plan_info", "tn_destroy", "tn_last_error", "tn_version"]
 
 
 class TNError(RuntimeError):
@@ -157,6 +160,15 @@ def tn_contract_grad(h: int, pairs, sliced, mode: int, adjoint: np.ndarray, adj_
     _check(_lib.tn_contract_grad(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64),
                                  mode, adj.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                  int(adj_exp2), gp, stream))
+
+
+def tn_contract_noalloc(h: int, pairs, sliced, out_ptr: int, out_mem: int, exp_ptr: int,
+                        stream: int = 0) -> None:
+    """The contraction without any device allocation (fixed 8 MiB scratch)."""
+    tr = _tree(pairs)
+    sl = _arr(list(sliced) or [0], np.int64)
+    _check(_lib.tn_contract_noalloc(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64),
+                                    out_ptr, out_mem, ctypes.cast(exp_ptr, _i64p), stream))
 
 
 def tn_plan_info(h: int, pairs, sliced, mode: int = TN_MODE_FP32) -> Dict[str, float]:

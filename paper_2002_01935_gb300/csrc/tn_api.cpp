@@ -230,6 +230,23 @@ tn_status tn_contract_grad(tn_net* net, const int32_t* tree_pairs, int32_t n_sli
     return TN_OK;
 }
 
+tn_status tn_contract_noalloc(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
+                              const int64_t* sliced_labels, void* out, int32_t out_mem,
+                              int64_t* out_exp2, void* stream) {
+    if (!net) return fail(TN_EINVAL, "tn_contract_noalloc: net is NULL");
+    if (!out || !out_exp2) return fail(TN_EINVAL, "tn_contract_noalloc: NULL output");
+    if (out_mem != TN_MEM_DEVICE && out_mem != TN_MEM_HOST) return fail(TN_EINVAL, "bad out_mem");
+    for (int v = 0; v < net->d.n; ++v)
+        if (!net->d.leaves[v].ptr) return fail(TN_EINVAL, "tn_contract_noalloc: tensor without data");
+    Plan* p = nullptr;  // host-side plan only: no device state is created
+    tn_status st = get_plan(net, tree_pairs, n_sliced, sliced_labels, TN_MODE_FP32, &p);
+    if (st != TN_OK) return st;
+    std::string err;
+    st = tn::run_noalloc(net->d, *p, out, out_mem, out_exp2, (cudaStream_t)stream, err);
+    if (st != TN_OK) return fail(st, err);
+    return TN_OK;
+}
+
 tn_status tn_plan_info(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
                        const int64_t* sliced_labels, tn_mode mode, double out[8]) {
     if (!net || !out) return fail(TN_EINVAL, "tn_plan_info: NULL argument");

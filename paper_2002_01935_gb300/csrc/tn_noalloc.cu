@@ -1,0 +1,210 @@
+// tn_noalloc.cu -- the contraction call for callers that cannot allocate
+// device memory.
+//
+// tn_contract keeps a per-plan workspace that it obtains with cudaMalloc the
+// first time a tree is run.  Some callers cannot allow that: code that runs
+// while another component is capturing a CUDA graph (an allocation there
+// either fails or breaks the capture), hosts that must not allocate after
+// start-up (fixed memory budgets, real-time loops), and processes whose
+// device memory belongs to another allocator's pool.  For them this file
+// offers the same contraction with every piece of scratch -- workspace for
+// the intermediate tensors, node maxima and exponents, leaf maxima, the
+// control block and the FP64 accumulator -- carved out of one fixed array
+// that is part of the library image.  The caller still passes the leaves
+// (device memory) and the outputs.
+//
+// The array costs kNoAllocScratchBytes of device memory on every GPU that
+// loads the library, for as long as the process lives.  Calls share it and
+// it keeps the last call's contents; everything a call relies on starting at
+// zero is cleared by the call itself.  Calls whose GPU work overlaps (on
+// different streams, or from several threads) race on the array.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "tn_internal.h"
+#include "tn_plan.h"
+
+namespace tn {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// In host code g_noalloc_scratch names a host-side shadow, not device
+// memory; the device address is looked up once per device, with that
+// device current.
+bool scratch_address(void** out, std::string& err) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return false;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        err = "device index out of range for the no-allocation scratch table";
+        return false;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            err = std::string("cudaGetSymbolAddress(no-allocation scratch): ") +
+                  cudaGetErrorString(e);
+            return false;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return true;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+tn_status run_noalloc(const NetDesc& d, const Plan& p, void* out, int out_mem, int64_t* out_exp2,
+                      cudaStream_t stream, std::string& err) {
+    const int n = d.n;
+    const int nn = (int)p.nodes.size();
+    const size_t eb = d.elem_bytes();
+    const bool cplx = d.is_complex();
+    for (int v = 0; v < n; ++v)
+        if (d.leaves[v].mem != TN_MEM_DEVICE) {
+            err = "tn_contract_noalloc: leaves must be device pointers (staging a host leaf "
+                  "would need device memory)";
+            return TN_EUNSUPPORTED;
+        }
+    // scratch layout (256-byte aligned sections)
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t o_ctl = take(sizeof(Control));
+    const size_t o_unit = take(16);
+    const size_t o_max = take(sizeof(unsigned) * nn);
+    const size_t o_exp = take(sizeof(int64_t) * nn);
+    const size_t o_lmax = take(sizeof(unsigned) * n);
+    const size_t o_lptr = take(sizeof(void*) * n);
+    const size_t o_lnf = take(sizeof(int64_t) * n);
+    const size_t acc_doubles = (size_t)p.n_out * (cplx ? 2 : 1);
+    const size_t o_acc = take(sizeof(double) * acc_doubles);
+    const size_t o_ws = take((size_t)p.ws_elems * eb);
+    if (off > kNoAllocScratchBytes) {
+        err = "tn_contract_noalloc: this tree needs " + std::to_string(off) +
+              " bytes of scratch; the no-allocation scratch holds " +
+              std::to_string(kNoAllocScratchBytes) + " bytes (8 MiB): use tn_contract";
+        return TN_EUNSUPPORTED;
+    }
+    void* base = nullptr;
+    if (!scratch_address(&base, err)) return TN_ECUDA;
+    char* S = static_cast<char*>(base);
+    Control* ctl = reinterpret_cast<Control*>(S + o_ctl);
+    void* unit = S + o_unit;
+    unsigned* maxabs = reinterpret_cast<unsigned*>(S + o_max);
+    int64_t* exps = reinterpret_cast<int64_t*>(S + o_exp);
+    unsigned* leafmax = reinterpret_cast<unsigned*>(S + o_lmax);
+    const float** lptr = reinterpret_cast<const float**>(S + o_lptr);
+    int64_t* lnf = reinterpret_cast<int64_t*>(S + o_lnf);
+    double* acc = reinterpret_cast<double*>(S + o_acc);
+    char* ws = S + o_ws;
+
+#define CK(x)                                                          \
+    do {                                                               \
+        cudaError_t e_ = (x);                                          \
+        if (e_ != cudaSuccess) {                                       \
+            err = std::string(#x) + ": " + cudaGetErrorString(e_);     \
+            return TN_ECUDA;                                           \
+        }                                                              \
+    } while (0)
+
+    // small host tables go up by copies (pageable: staged before return)
+    std::vector<const void*> lp(n);
+    std::vector<int64_t> nf(n);
+    for (int v = 0; v < n; ++v) {
+        lp[v] = d.leaves[v].ptr;
+        nf[v] = d.leaves[v].size * (cplx ? 2 : 1);
+    }
+    static const float kOne[4] = {1.f, 0.f, 0.f, 0.f};
+    CK(cudaMemcpyAsync(lptr, lp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(lnf, nf.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(unit, kOne, sizeof(kOne), cudaMemcpyHostToDevice, stream));
+
+    // node arguments, pointing into the scratch
+    std::vector<GenericArgs> gen(nn);
+    for (int k = 0; k < nn; ++k) {
+        const Node& nd = p.nodes[k];
+        GenericArgs& g = gen[k];
+        tn_status st = make_generic_args(d, p, k, g, err);
+        if (st != TN_OK) return st;
+        auto operand = [&](int c) -> const void* {
+            if (c < 0) return unit;
+            if (c < n) return d.leaves[c].ptr;
+            return ws + p.nodes[c - n].ws_off * eb;
+        };
+        g.A = operand(nd.ca);
+        g.B = operand(nd.cb);
+        g.C = ws + nd.ws_off * eb;
+        g.ctl = ctl;
+        g.sc.max_a = nd.ca >= n ? maxabs + (nd.ca - n) : (nd.ca >= 0 ? leafmax + nd.ca : nullptr);
+        g.sc.exp_a = nd.ca >= n ? exps + (nd.ca - n) : nullptr;
+        g.sc.max_b = nd.cb >= n ? maxabs + (nd.cb - n) : (nd.cb >= 0 ? leafmax + nd.cb : nullptr);
+        g.sc.exp_b = nd.cb >= n ? exps + (nd.cb - n) : nullptr;
+        g.sc.max_c = maxabs + k;
+        g.sc.exp_c = exps + k;
+    }
+    const Node& root = p.nodes.back();
+    AccumArgs a;
+    memset(&a, 0, sizeof(a));
+    a.R = ws + root.ws_off * eb;
+    a.n_out = p.n_out;
+    a.n_od = (int)d.open.size();
+    if (a.n_od > kMaxDigits) {
+        err = "too many open labels";
+        return TN_EUNSUPPORTED;
+    }
+    for (int i = 0; i < a.n_od; ++i) {
+        int l = d.open[d.open.size() - 1 - i];
+        a.od_dim[i] = (int32_t)d.dims[l];
+        int64_t s = 0;
+        for (size_t j = 0; j < root.lab.size(); ++j)
+            if (root.lab[j] == l) s = root.stride[j];
+        a.od_s[i] = s;
+    }
+    a.max_r = maxabs + (nn - 1);
+    a.exp_r = exps + (nn - 1);
+    a.acc = acc;
+    a.ctl = ctl;
+
+    // the call: leaf maxima, control block and accumulator cleared, then
+    // every slice in order, then the result
+    CK(launch_leaf_max(lptr, lnf, leafmax, n, stream));
+    CK(launch_begin_call(ctl, 0, acc, (int64_t)acc_doubles, stream));
+    for (int64_t s = 0; s < p.d_sliced; ++s) {
+        CK(launch_begin_slice(maxabs, nn, stream));
+        for (int k = 0; k < nn; ++k) CK(launch_generic(gen[k], cplx, stream));
+        CK(launch_accumulate(a, cplx, stream));
+        CK(launch_advance(ctl, stream));
+    }
+    CK(launch_finalize(ctl, (int)(p.d_sliced & 1), stream));
+    cudaMemcpyKind kind = out_mem == TN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(out, acc, sizeof(double) * acc_doubles, kind, stream));
+    CK(cudaMemcpyAsync(out_exp2, &ctl->final_exp, sizeof(int64_t), kind, stream));
+    if (out_mem == TN_MEM_HOST) CK(cudaStreamSynchronize(stream));
+#undef CK
+    return TN_OK;
+}
+
+}  // namespace tn

@@ -570,6 +570,10 @@ tn_status run_grad(NetDesc&, Plan&, void*, const double*, int64_t, void* const*,
     return TN_EUNSUPPORTED;
 }
 
+tn_status make_generic_args(const NetDesc& d, const Plan& p, int k, GenericArgs& g, std::string& err) {
+    return fill_generic(d, p, p.nodes[k], g, err);
+}
+
 void plan_info(const NetDesc& d, const Plan& p, double out[8]) {
     out[0] = p.W;
     out[1] = p.C;

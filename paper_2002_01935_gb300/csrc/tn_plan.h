@@ -92,5 +92,12 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int64_t a
                    void* const* grads, cudaStream_t stream, std::string& err);
 void plan_info(const NetDesc& d, const Plan& p, double out[8]);
 void free_device(Plan& p);  // releases device state; the host plan stays valid
+// Generic-kernel arguments of node k (index digits, slice digits); pointers
+// and bookkeeping slots are left for the caller to fill.
+tn_status make_generic_args(const NetDesc& d, const Plan& p, int k, GenericArgs& g, std::string& err);
+// The contraction with all scratch in the library's fixed device array
+// (tn_noalloc.cu); allocates no device memory.
+tn_status run_noalloc(const NetDesc& d, const Plan& p, void* out, int out_mem, int64_t* out_exp2,
+                      cudaStream_t stream, std::string& err);
 
 }  // namespace tn
