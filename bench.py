@@ -221,9 +221,12 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    # warm-up, then one per-node profile pass to find the dominant kernel
+    # warm-up, then one per-step profile pass to find the dominant launch
+    steps = tnw.plan_steps(pairs, sliced, args.mode)
+    n_steps = len(steps)
     for _ in range(args.warmup):
         m, e = tnw.contract(pairs, sliced, args.mode)
+
     def events(n):
         # torch creates the CUDA event lazily: record once so .cuda_event is valid
         evl = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
@@ -231,12 +234,12 @@ def main():
             ev.record(stream)
         return evl
 
-    evs = events(n_nodes + 1)
+    evs = events(n_steps + 1)
     flush.zero_()
     tnw.contract(pairs, sliced, args.mode, prof_events=evs, prof_first=0)
     torch.cuda.synchronize()
-    node_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(n_nodes)]
-    dom = int(np.argmax(node_ms))
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(n_steps)]
+    dom = int(np.argmax(step_ms))
 
     # timed region: K steps, each bracketed by events; L2 flushed between
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -254,9 +257,9 @@ def main():
         ends[i].record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    step_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
+    call_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
     dom_ms = [a.elapsed_time(b) for a, b in dom_ev]
-    total_ms = sum(step_ms)
+    total_ms = sum(call_ms)
     if dist:
         tt = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -269,7 +272,9 @@ def main():
 
     # roofline of the dominant node kernel
     peaks = load_peaks()
-    dn = nodes[dom]
+    dnodes = steps[dom]["nodes"]
+    dn = {"flops": sum(nodes[k]["flops"] for k in dnodes),
+          "bytes": sum(nodes[k]["bytes"] for k in dnodes)}
     dmean = statistics.mean(dom_ms) / 1e3
     t_hbm = dn["bytes"] / (peaks["hbm_gbs"] * 1e9)
     t_alu = dn["flops"] / (FP32_SIMT_TFLOPS * 1e12)
@@ -281,7 +286,12 @@ def main():
                 "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    roof["kernel"] = f"k_generic (node {dom} of {n_nodes})"
+    cfg_names = {0: "generic", 1: "tile64x64", 2: "tile16x256", 3: "tile4x1024", 4: "tile256x16",
+                 5: "dot"}
+    st = steps[dom]
+    roof["kernel"] = (f"step {dom} of {n_steps}: " +
+                      (f"k_wave over {len(dnodes)} nodes" if st["wave"] else
+                       f"node {dnodes[0]} ({cfg_names.get(st['cfg'], 'generic') if st['kind'] == 1 else 'generic'})"))
     roof["peak_source"] = (peaks["source"] if roof["bound"] == "hbm"
                            else "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz")
     roof["algorithmic"] = {"flops": dn["flops"], "bytes": dn["bytes"]}
@@ -323,7 +333,8 @@ def main():
             rel_err = abs(math.expm1(math.log(abs(result)) + (result_exp - oe) * math.log(2)
                                      - math.log(abs(float(om)))))
 
-    launches_per_step = (n_nodes + 2) * info.d_sliced + 3
+    launches_per_step = sum(1 + (1 if (s["cfg"] in (1, 2, 3, 4, 5) and not s["wave"]) else 0)
+                            for s in steps) * info.d_sliced + 2 * info.d_sliced + 3
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -335,7 +346,9 @@ def main():
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "tree": "greedy (alpha=1, tau=0)",
                    "plan_kernels": {"generic": plan["n_generic"], "tiled": plan["n_tiled"],
-                                    "tensor_core": plan["n_tensor_core"]}},
+                                    "tensor_core": plan["n_tensor_core"]},
+                   "launch_steps": n_steps,
+                   "wave_steps": sum(1 for s in steps if s["wave"])},
         "s_per_network": ms_per_step / 1e3,
         "rel_err_vs_oracle": rel_err,
         "roofline": roof,

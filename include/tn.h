@@ -125,8 +125,8 @@ tn_status tn_set_tensor(tn_net *net, int32_t v, const void *ptr, int32_t mem);
  *       0: use the built-in choice.
  *   prof_events, prof_first, prof_count
  *       timing hooks: prof_events[i] is recorded on the stream just before
- *       the kernel of node prof_first+i (nodes numbered 0..n_tensors-2 in
- *       tree order) and prof_events[prof_count] just after node
+ *       launch step prof_first+i of the per-slice sequence (steps as listed
+ *       by tn_plan_steps) and prof_events[prof_count] just after step
  *       prof_first+prof_count-1, in every slice (the last slice's records
  *       win).  The events are caller-owned timing events.
  */
@@ -237,6 +237,20 @@ tn_status tn_contract_noalloc(tn_net *net, const int32_t *tree_pairs, int32_t n_
  */
 tn_status tn_plan_info(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
                        const int64_t *sliced_labels, tn_mode mode, double out[8]);
+
+/*
+ * tn_plan_steps -- the per-slice launch sequence of a plan (host only).
+ * Nodes (0..n_tensors-2, tree order) run in launch steps: a wave step runs
+ * all small nodes of one tree level in one launch, a single step runs one
+ * node.  *n_steps receives the number of steps; if cap >= *n_steps, then
+ * step_info[4*s..4*s+3] = (is_wave, kernel kind 0 generic / 1 tiled /
+ * 2 tensor core, tile configuration, number of nodes) and step_nodes lists
+ * the nodes of step 0, then step 1, ... (n_tensors-1 entries in all; may be
+ * NULL).  Errors as tn_plan_info.
+ */
+tn_status tn_plan_steps(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
+                        const int64_t *sliced_labels, tn_mode mode, int32_t cap, int32_t *n_steps,
+                        int32_t *step_info, int32_t *step_nodes);
 
 /* Release the handle, its plans and its device memory (synchronises the
  * device work the handle issued).  NULL is ignored. */

@@ -65,6 +65,9 @@ _lib.tn_contract_noalloc.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, _vp, cty
 _lib.tn_plan_info.restype = ctypes.c_int
 _lib.tn_plan_info.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int,
                               ctypes.POINTER(ctypes.c_double)]
+_lib.tn_plan_steps.restype = ctypes.c_int
+_lib.tn_plan_steps.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int, ctypes.c_int32,
+                               _i32p, _i32p, _i32p]
 _lib.tn_destroy.restype = None
 _lib.tn_destroy.argtypes = [_vp]
 _lib.tn_last_error.restype = ctypes.c_char_p
@@ -73,7 +76,8 @@ _lib.tn_version.restype = ctypes.c_char_p
 _lib.tn_version.argtypes = []
 
 EXPORTS = ["tn_create", "tn_set_tensor", "tn_contract", "tn_contract_ex", "tn_contract_grad",
-           "tn_contract_noalloc", "tn_plan_info", "tn_destroy", "tn_last_error", "tn_version"]
+           "tn_contract_noalloc", "tn_plan_info", "tn_plan_steps", "tn_destroy", "tn_last_error",
+           "tn_version"]
 
 
 class TNError(RuntimeError):
@@ -181,6 +185,28 @@ def tn_plan_info(h: int, pairs, sliced, mode: int = TN_MODE_FP32) -> Dict[str, f
     return dict(zip(keys, out.tolist()))
 
 
+def tn_plan_steps(h: int, pairs, sliced, mode: int = TN_MODE_FP32):
+    """Launch steps of the per-slice sequence: list of dicts
+    (wave, kind, cfg, nodes)."""
+    tr = _tree(pairs)
+    sl = _arr(list(sliced) or [0], np.int64)
+    ns = ctypes.c_int32(0)
+    _check(_lib.tn_plan_steps(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
+                              0, ctypes.byref(ns), None, None))
+    n = ns.value
+    info = np.zeros(4 * max(n, 1), dtype=np.int32)
+    nodes = np.zeros(max(len(pairs), 1), dtype=np.int32)
+    _check(_lib.tn_plan_steps(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
+                              n, ctypes.byref(ns), _p(info, ctypes.c_int32), _p(nodes, ctypes.c_int32)))
+    out, pos = [], 0
+    for s in range(n):
+        w, kind, cfg, cnt = info[4 * s:4 * s + 4].tolist()
+        out.append({"wave": bool(w), "kind": kind, "cfg": cfg,
+                    "nodes": nodes[pos:pos + cnt].tolist()})
+        pos += cnt
+    return out
+
+
 def tn_destroy(h: int) -> None:
     _lib.tn_destroy(h)
 
@@ -257,3 +283,7 @@ class TensorNetwork:
     def plan_info(self, pairs, sliced=(), mode="fp32"):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         return tn_plan_info(self.h, pairs, sliced, m)
+
+    def plan_steps(self, pairs, sliced=(), mode="fp32"):
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        return tn_plan_steps(self.h, pairs, sliced, m)

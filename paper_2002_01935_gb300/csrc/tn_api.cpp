@@ -257,6 +257,29 @@ tn_status tn_plan_info(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
     return TN_OK;
 }
 
+tn_status tn_plan_steps(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
+                        const int64_t* sliced_labels, tn_mode mode, int32_t cap, int32_t* n_steps,
+                        int32_t* step_info, int32_t* step_nodes) {
+    if (!net || !n_steps) return fail(TN_EINVAL, "tn_plan_steps: NULL argument");
+    Plan* p = nullptr;
+    tn_status st = get_plan(net, tree_pairs, n_sliced, sliced_labels, mode, &p);
+    if (st != TN_OK) return st;
+    *n_steps = (int32_t)p->steps.size();
+    if (cap < *n_steps || !step_info) return TN_OK;
+    int pos = 0;
+    for (size_t s = 0; s < p->steps.size(); ++s) {
+        const tn::Step& stp = p->steps[s];
+        const tn::Node& first = p->nodes[stp.nodes[0]];
+        step_info[4 * s + 0] = stp.wave;
+        step_info[4 * s + 1] = first.kind;
+        step_info[4 * s + 2] = stp.wave ? 0 : (first.kind == tn::kTiled ? first.tile.cfg : 0);
+        step_info[4 * s + 3] = (int32_t)stp.nodes.size();
+        if (step_nodes)
+            for (int k : stp.nodes) step_nodes[pos++] = k;
+    }
+    return TN_OK;
+}
+
 void tn_destroy(tn_net* net) {
     if (!net) return;
     cudaDeviceSynchronize();

@@ -75,6 +75,41 @@ struct BitGroup {
     uint8_t sh[kMaxBits];
 };
 
+// Tiled node (power-of-two label sizes).  Each index group is a list of
+// bits; bit i of a group index contributes 1 << sh[i] to an operand offset
+// (kNoBit: the operand lacks that label).  Output layout [batch][M][N].
+constexpr uint8_t kNoBit = 255;
+enum TileCfg { kTile64x64 = 1, kTile16x256 = 2, kTile4x1024 = 3, kTile256x16 = 4, kTileDot = 5 };
+
+struct alignas(16) TileArgs {
+    const void* A;
+    const void* B;
+    void* C;
+    void* P;              // K-split partials [split][batch][M][N] (split > 1)
+    int nb, nm, nn, nk;   // bits per group
+    int64_t nbatch;       // 1 << nb
+    uint8_t a_b[kMaxBits], a_m[kMaxBits], a_k[kMaxBits];
+    uint8_t b_b[kMaxBits], b_n[kMaxBits], b_k[kMaxBits];
+    int a_mfast;          // A's fastest tile bit is an M bit: load A along m
+    int b_nfast;          // B's fastest tile bit is an N bit: load B along n
+    int cfg;              // TileCfg
+    int split;            // K splits (grid.z = nbatch * split)
+    int64_t kchunk;       // K entries per split
+    SliceDigits sla, slb;
+    const Control* ctl;
+    ScaleIO sc;
+    int a_leaf, b_leaf;   // leaf index of an operand (its pointer comes from the
+                          // leaf pointer table in wave launches), else -1
+};
+
+// One CTA of a wave launch: outputs [o_begin, o_begin + o_count) of node.
+struct WaveItem {
+    int node;
+    int pad;
+    int64_t o_begin;
+    int64_t o_count;
+};
+
 // Per-slice FP64 accumulation of the root tensor into the output
 // (Sec. 4.7.1: the sliced contractions are summed), with exponent
 // alignment.  od_*: digits of the output in the user's open-label order,
@@ -93,6 +128,10 @@ struct AccumArgs {
 
 // Launchers (tn_kernels.cu).  is_c: complex64 data.
 cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s);
+cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s);  // tn_tiled.cu
+// All small nodes of one tree level in one launch (tn_tiled.cu).
+cudaError_t launch_wave(const WaveItem* items, int n_items, const TileArgs* descs,
+                        const void* const* leaf_ptrs, bool is_c, cudaStream_t s);
 cudaError_t launch_accumulate(const AccumArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_begin_call(Control* ctl, int64_t slice_begin, double* acc, int64_t n_acc_doubles,
                               cudaStream_t s);

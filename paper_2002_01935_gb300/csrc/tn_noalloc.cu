@@ -194,7 +194,9 @@ tn_status run_noalloc(const NetDesc& d, const Plan& p, void* out, int out_mem, i
     CK(launch_begin_call(ctl, 0, acc, (int64_t)acc_doubles, stream));
     for (int64_t s = 0; s < p.d_sliced; ++s) {
         CK(launch_begin_slice(maxabs, nn, stream));
-        for (int k = 0; k < nn; ++k) CK(launch_generic(gen[k], cplx, stream));
+        // the workspace offsets assume the plan's step order
+        for (const Step& st : p.steps)
+            for (int k : st.nodes) CK(launch_generic(gen[k], cplx, stream));
         CK(launch_accumulate(a, cplx, stream));
         CK(launch_advance(ctl, stream));
     }

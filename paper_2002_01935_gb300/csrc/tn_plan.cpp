@@ -6,6 +6,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <map>
 
 namespace tn {
@@ -77,10 +78,143 @@ struct Arena {
     }
 };
 
+bool pow2(int64_t x) { return x >= 1 && (x & (x - 1)) == 0; }
+int ilog2(int64_t x) {
+    int r = 0;
+    while ((int64_t(1) << r) < x) ++r;
+    return r;
+}
+
+// Tiled-kernel plan of a node whose labels and strides are all powers of
+// two: index bits per group, K order, load directions, tile shape and K
+// split.  Returns false (generic kernel) when a limit is exceeded.
+bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems) {
+    static const std::vector<int> none;
+    static const std::vector<int64_t> nones;
+    const std::vector<int>& la = nd.ca >= 0 ? p.vlab[nd.ca] : none;
+    const std::vector<int>& lb = nd.cb >= 0 ? p.vlab[nd.cb] : none;
+    const std::vector<int64_t>& sa = nd.ca >= 0 ? p.vstride[nd.ca] : nones;
+    const std::vector<int64_t>& sb = nd.cb >= 0 ? p.vstride[nd.cb] : nones;
+    for (size_t i = 0; i < la.size(); ++i)
+        if (!pow2(d.dims[la[i]]) || !pow2(sa[i])) return false;
+    for (size_t i = 0; i < lb.size(); ++i)
+        if (!pow2(d.dims[lb[i]]) || !pow2(sb[i])) return false;
+    TileArgs t;
+    memset(&t, 0, sizeof(t));
+    auto push = [&](uint8_t* arr, int& nbits, int l, int64_t stride) -> bool {
+        const int j = ilog2(d.dims[l]);
+        for (int r = 0; r < j; ++r) {
+            if (nbits >= kMaxBits) return false;
+            arr[nbits++] = stride ? (uint8_t)(ilog2(stride) + r) : kNoBit;
+        }
+        return true;
+    };
+    // batch, M, N: fastest label first (the lists are slowest first)
+    int nb2 = 0;
+    for (auto it = nd.gb.rbegin(); it != nd.gb.rend(); ++it) {
+        int tmp = t.nb;
+        if (!push(t.a_b, t.nb, *it, stride_in(la, sa, *it))) return false;
+        if (!push(t.b_b, tmp, *it, stride_in(lb, sb, *it))) return false;
+        nb2 = tmp;
+    }
+    (void)nb2;
+    for (auto it = nd.gm.rbegin(); it != nd.gm.rend(); ++it)
+        if (!push(t.a_m, t.nm, *it, stride_in(la, sa, *it))) return false;
+    for (auto it = nd.gn.rbegin(); it != nd.gn.rend(); ++it)
+        if (!push(t.b_n, t.nn, *it, stride_in(lb, sb, *it))) return false;
+    // K (shared and summed-only labels): order by the stride of the operand
+    // whose fastest label is a K label, so its loads stay contiguous
+    std::vector<int> ks = nd.gk;
+    ks.insert(ks.end(), nd.gsa.begin(), nd.gsa.end());
+    ks.insert(ks.end(), nd.gsb.begin(), nd.gsb.end());
+    auto fastest = [&](const std::vector<int>& lab, const std::vector<int64_t>& st) {
+        int best = -1;
+        int64_t bs = INT64_MAX;
+        for (size_t i = 0; i < lab.size(); ++i)
+            if (d.dims[lab[i]] > 1 && st[i] < bs) {
+                bs = st[i];
+                best = lab[i];
+            }
+        return best;
+    };
+    const int fa = fastest(la, sa), fb = fastest(lb, sb);
+    const bool fa_k = fa >= 0 && has(ks, fa), fb_k = fb >= 0 && has(ks, fb);
+    const bool by_a = fa_k && !fb_k;
+    const int64_t big = INT64_MAX / 4;
+    std::sort(ks.begin(), ks.end(), [&](int x, int y) {
+        int64_t sx = by_a ? stride_in(la, sa, x) : stride_in(lb, sb, x);
+        int64_t sy = by_a ? stride_in(la, sa, y) : stride_in(lb, sb, y);
+        if (!sx) sx = big;
+        if (!sy) sy = big;
+        return sx < sy;
+    });
+    for (int l : ks) {
+        int tmp = t.nk;
+        if (!push(t.a_k, t.nk, l, stride_in(la, sa, l))) return false;
+        if (!push(t.b_k, tmp, l, stride_in(lb, sb, l))) return false;
+    }
+    if (t.nb > 16 || t.nm > 31 || t.nn > 31 || t.nk > 40 || t.nm + t.nn > 40) return false;
+    t.nbatch = int64_t(1) << t.nb;
+    t.a_mfast = fa >= 0 && has(nd.gm, fa);
+    t.b_nfast = fb >= 0 && has(nd.gn, fb);
+    const int64_t M = int64_t(1) << t.nm, N = int64_t(1) << t.nn, K = int64_t(1) << t.nk;
+    int TM = 64, TN = 64, TK = 16;
+    if (M * N <= 64 && K >= 512) {
+        t.cfg = kTileDot;
+        TM = (int)M;
+        TN = (int)N;
+    } else if (t.nm <= 2 && t.nn >= 10) {
+        t.cfg = kTile4x1024;
+        TM = 4;
+        TN = 1024;
+        TK = 4;
+    } else if (t.nm <= 4 && t.nn >= 8) {
+        t.cfg = kTile16x256;
+        TM = 16;
+        TN = 256;
+    } else if (t.nn <= 4 && t.nm >= 8) {
+        t.cfg = kTile256x16;
+        TM = 256;
+        TN = 16;
+    } else {
+        t.cfg = kTile64x64;
+    }
+    t.split = 1;
+    t.kchunk = K;
+    if (t.cfg != kTileDot) {
+        const int64_t tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN) * t.nbatch;
+        const int64_t ktiles = (K + TK - 1) / TK;
+        int split = 1;
+        while (tiles * split < 2 * 152 && split * 4 <= ktiles && split < 64 &&
+               t.nbatch * split * 2 <= 65535)
+            split *= 2;
+        t.split = split;
+        t.kchunk = ((ktiles + split - 1) / split) * TK;
+        if (split > 1) split_elems = std::max(split_elems, (int64_t)split * t.nbatch * M * N);
+    } else {
+        if (t.nbatch > 65535) return false;
+        const int64_t outs = M * N * t.nbatch;
+        int split = 1;
+        while (outs * split < 256 && (K / (split * 2)) >= 1024 && split < 1024) split *= 2;
+        t.split = split;
+        t.kchunk = ((K / split + 255) / 256) * 256;
+        if (split > 1) split_elems = std::max(split_elems, (int64_t)split * outs);
+    }
+    t.a_leaf = nd.ca >= 0 && nd.ca < d.n ? nd.ca : -1;
+    t.b_leaf = nd.cb >= 0 && nd.cb < d.n ? nd.cb : -1;
+    nd.tile = t;
+    nd.kind = kTiled;
+    return true;
+}
+
 }  // namespace
 
 tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
     const int n = d.n;
+    // diagnostics: TN_FORCE_GENERIC=1 runs every node on the generic kernel,
+    // TN_NO_WAVES=1 launches every node separately
+    if (const char* e = getenv("TN_FORCE_GENERIC")) p.force_generic = e[0] == '1';
+    if (const char* e = getenv("TN_NO_WAVES")) p.no_waves = e[0] == '1';
     const int L = (int)d.dims.size();
     // ---- tree validation (Sec. 2: leaves first, children before parents)
     if ((int64_t)p.pairs.size() != 2 * (int64_t)(n - 1)) {
@@ -277,18 +411,72 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
     }
     p.W = W;
     p.C = C;
-    // ---- workspace liveness: children die when their parent is formed
-    Arena ar;
-    std::vector<int64_t> off(p.nodes.size());
+    // ---- kernel choice per node
+    int64_t split_elems = 0;
     for (size_t k = 0; k < p.nodes.size(); ++k) {
         Node& nd = p.nodes[k];
-        nd.ws_off = ar.alloc(nd.size);
-        for (int c : {nd.ca, nd.cb})
-            if (c >= n) {
-                const Node& ch = p.nodes[c - n];
-                ar.release(ch.ws_off, ch.size);
-            }
         nd.kind = kGeneric;
+        if (!p.force_generic) plan_tile(d, p, nd, split_elems);
+    }
+    p.split_bytes = split_elems * (int64_t)d.elem_bytes();
+    // ---- launch schedule: tree levels; per level one wave launch for the
+    // small tiled nodes, then one launch per remaining node
+    std::vector<int> level(2 * n, 0);
+    int max_level = 0;
+    for (size_t k = 0; k < p.nodes.size(); ++k) {
+        const Node& nd = p.nodes[k];
+        int la = nd.ca >= n ? level[nd.ca] : 0, lb = nd.cb >= n ? level[nd.cb] : 0;
+        level[n + k] = 1 + std::max(la, lb);
+        max_level = std::max(max_level, level[n + k]);
+    }
+    p.steps.clear();
+    p.items.clear();
+    for (int L = 1; L <= max_level; ++L) {
+        Step w;
+        w.wave = 1;
+        w.item_begin = (int)p.items.size();
+        std::vector<int> singles;
+        for (size_t k = 0; k < p.nodes.size(); ++k) {
+            if (level[n + k] != L) continue;
+            const Node& nd = p.nodes[k];
+            const TileArgs& t = nd.tile;
+            const bool small = nd.kind == kTiled && t.cfg != kTileDot && nd.size <= (1 << 16) &&
+                               nd.vc <= 20.0 && !p.no_waves;
+            if (!small) {
+                singles.push_back((int)k);
+                continue;
+            }
+            const int64_t chunk = std::min<int64_t>(nd.size, 1024);
+            for (int64_t o = 0; o < nd.size; o += chunk) {
+                WaveItem it;
+                it.node = (int)k;
+                it.pad = 0;
+                it.o_begin = o;
+                it.o_count = chunk;
+                p.items.push_back(it);
+            }
+            w.nodes.push_back((int)k);
+        }
+        w.item_count = (int)p.items.size() - w.item_begin;
+        if (w.item_count > 0) p.steps.push_back(w);
+        for (int k : singles) {
+            Step s;
+            s.node = k;
+            s.nodes.push_back(k);
+            p.steps.push_back(s);
+        }
+    }
+    // ---- workspace liveness in execution order: a step's outputs are all
+    // allocated before any of its operands is released (they run at once)
+    Arena ar;
+    for (const Step& st : p.steps) {
+        for (int k : st.nodes) p.nodes[k].ws_off = ar.alloc(p.nodes[k].size);
+        for (int k : st.nodes)
+            for (int c : {p.nodes[k].ca, p.nodes[k].cb})
+                if (c >= n) {
+                    const Node& ch = p.nodes[c - n];
+                    ar.release(ch.ws_off, ch.size);
+                }
     }
     p.ws_elems = std::max<int64_t>(ar.end, 64);
     p.n_out = 1;
@@ -369,6 +557,8 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
                            cudaMemcpyHostToDevice), "cudaMemcpy"))
             return TN_ECUDA;
     }
+    if (p.split_bytes > 0 && !ck(cudaMalloc(&p.split_buf, p.split_bytes), "split-K buffer"))
+        return TN_ENOMEM;
     // node launch arguments; leaf pointers are patched per call
     p.gen.resize(nn);
     const int n = d.n;
@@ -391,6 +581,32 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
         g.sc.exp_b = nd.cb >= n ? p.exps + (nd.cb - n) : nullptr;
         g.sc.max_c = p.maxabs + k;
         g.sc.exp_c = p.exps + k;
+        Node& ndm = p.nodes[k];
+        if (ndm.kind == kTiled) {
+            TileArgs& t = ndm.tile;
+            t.A = g.A;
+            t.B = g.B;
+            t.C = g.C;
+            t.P = p.split_buf;
+            t.sla = g.sla;
+            t.slb = g.slb;
+            t.ctl = g.ctl;
+            t.sc = g.sc;
+        }
+    }
+    if (!p.items.empty()) {
+        std::vector<TileArgs> descs(nn);
+        for (int k = 0; k < nn; ++k) descs[k] = p.nodes[k].tile;
+        if (!ck(cudaMalloc(&p.descs_dev, sizeof(TileArgs) * nn), "cudaMalloc")) return TN_ENOMEM;
+        if (!ck(cudaMalloc(&p.items_dev, sizeof(WaveItem) * p.items.size()), "cudaMalloc"))
+            return TN_ENOMEM;
+        if (!ck(cudaMemcpy(p.descs_dev, descs.data(), sizeof(TileArgs) * nn, cudaMemcpyHostToDevice),
+                "cudaMemcpy"))
+            return TN_ECUDA;
+        if (!ck(cudaMemcpy(p.items_dev, p.items.data(), sizeof(WaveItem) * p.items.size(),
+                           cudaMemcpyHostToDevice),
+                "cudaMemcpy"))
+            return TN_ECUDA;
     }
     // root accumulation: user open-label order -> root layout
     const Node& root = p.nodes.back();
@@ -423,12 +639,19 @@ static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, cons
     cudaError_t e = launch_begin_slice(p.maxabs, (int)p.nodes.size(), s);
     if (e != cudaSuccess) return e;
     const bool c = d.is_complex();
-    for (int k = 0; k < (int)p.nodes.size(); ++k) {
+    for (int k = 0; k < (int)p.steps.size(); ++k) {
         // External records become event-record nodes under stream capture.
         if (ev && k >= pf && k < pf + pc &&
             (e = cudaEventRecordWithFlags(ev[k - pf], s, cudaEventRecordExternal)) != cudaSuccess)
             return e;
-        e = launch_generic(p.gen[k], c, s);
+        const Step& st = p.steps[k];
+        if (st.wave) {
+            e = launch_wave(p.items_dev + st.item_begin, st.item_count, p.descs_dev,
+                            reinterpret_cast<const void* const*>(p.leaf_ptr_dev), c, s);
+        } else {
+            const Node& nd = p.nodes[st.node];
+            e = nd.kind == kTiled ? launch_tile(nd.tile, c, s) : launch_generic(p.gen[st.node], c, s);
+        }
         if (e != cudaSuccess) return e;
         if (ev && k == pf + pc - 1 &&
             (e = cudaEventRecordWithFlags(ev[pc], s, cudaEventRecordExternal)) != cudaSuccess)
@@ -462,8 +685,8 @@ tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count
     if (o.prof_events && o.prof_count > 0) {
         pf = o.prof_first;
         pc = o.prof_count;
-        if (pf < 0 || pf + pc > (int)p.nodes.size()) {
-            err = "profiling node range out of bounds";
+        if (pf < 0 || pf + pc > (int)p.steps.size()) {
+            err = "profiling step range out of bounds";
             return TN_EINVAL;
         }
         uev = reinterpret_cast<const cudaEvent_t*>(o.prof_events);
@@ -491,9 +714,9 @@ tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count
         }
     }
     for (size_t k = 0; k < p.nodes.size(); ++k) {
-        const Node& nd = p.nodes[k];
-        if (nd.ca >= 0 && nd.ca < n) p.gen[k].A = lp[nd.ca];
-        if (nd.cb >= 0 && nd.cb < n) p.gen[k].B = lp[nd.cb];
+        Node& nd = p.nodes[k];
+        if (nd.ca >= 0 && nd.ca < n) p.gen[k].A = nd.tile.A = lp[nd.ca];
+        if (nd.cb >= 0 && nd.cb < n) p.gen[k].B = nd.tile.B = lp[nd.cb];
     }
     if (p.leaf_ptr_uploaded != lp) {
         // pointer table changes only when leaves are re-attached
@@ -601,6 +824,12 @@ void free_device(Plan& p) {
     if (p.ctl) cudaFree(p.ctl);
     if (p.acc) cudaFree(p.acc);
     if (p.leafmax) cudaFree(p.leafmax);
+    if (p.split_buf) cudaFree(p.split_buf);
+    p.split_buf = nullptr;
+    if (p.descs_dev) cudaFree(p.descs_dev);
+    if (p.items_dev) cudaFree(p.items_dev);
+    p.descs_dev = nullptr;
+    p.items_dev = nullptr;
     if (p.leaf_ptr_dev) cudaFree(p.leaf_ptr_dev);
     if (p.leaf_nfloat_dev) cudaFree(p.leaf_nfloat_dev);
     p.leafmax = nullptr;

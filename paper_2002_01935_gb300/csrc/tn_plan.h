@@ -46,10 +46,22 @@ struct Node {
     std::vector<int> gb, gm, gn, gk, gsa, gsb;  // label groups
     int kind = kGeneric;
     double vc = 0;               // log2 of 2^vc, Eq. vertexcon
+    TileArgs tile{};             // index bits, config and split (kTiled); pointers set at alloc
+};
+
+// One launch of the per-slice sequence: a wave (all small nodes of a tree
+// level, k_wave) or a single node (tiled or generic kernel).
+struct Step {
+    int wave = 0;
+    int node = -1;                 // single-node step
+    int item_begin = 0, item_count = 0;
+    std::vector<int> nodes;        // nodes run by this step
 };
 
 struct Plan {
     tn_mode mode = TN_MODE_FP32;
+    bool force_generic = false;  // every node on the generic kernel
+    bool no_waves = false;       // one launch per node
     std::vector<int32_t> pairs;
     std::vector<int64_t> sliced_ids;
     std::vector<int> sliced;  // dense
@@ -73,6 +85,12 @@ struct Plan {
     int64_t* leaf_nfloat_dev = nullptr;
     std::vector<const void*> leaf_ptr_uploaded;
     std::vector<GenericArgs> gen;
+    std::vector<Step> steps;
+    std::vector<WaveItem> items;
+    WaveItem* items_dev = nullptr;
+    TileArgs* descs_dev = nullptr;
+    void* split_buf = nullptr;      // K-split partials, shared by all split nodes
+    int64_t split_bytes = 0;
     AccumArgs acc_args{};
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;

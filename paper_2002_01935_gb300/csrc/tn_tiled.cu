@@ -1,0 +1,469 @@
+// tn_tiled.cu -- tiled node kernels for power-of-two label sizes (FP32 on
+// CUDA cores).
+//
+// A tree node contracts A and B over the shared labels (Sec. 2 of arXiv
+// 2002.01935).  With every label size a power of two, each group of labels
+// (batch, M, N, K) is a set of index bits and an operand offset is a
+// scatter of those bits to the operand's strides.  The node output is laid
+// out [batch][M][N], i.e. a row-major M x N matrix per batch index, so a
+// node is a batched GEMM whose operands are read through bit scatters:
+//   C[b, m, n] = sum_k A[sA(b) + sA(m) + sA(k)] * B[sB(b) + sB(k) + sB(n)].
+// The index permutation of a classic transpose-transpose-GEMM scheme is
+// folded into the operand loads: each CTA builds tile-local offset tables
+// once, and the planner orders every group's bits by operand stride so
+// that tiles cover the operands' contiguous bits (coalesced loads).
+//
+// Renormalisation (Sec. 4.2): operands are multiplied by 2^-e at load,
+// e = frexp exponent of their max |component|, which is exact; the output
+// max goes to the node's slot for its consumer.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+namespace {
+
+template <bool CPLX>
+struct VT;
+template <>
+struct VT<true> {
+    using T = float2;
+};
+template <>
+struct VT<false> {
+    using T = float;
+};
+
+__device__ __forceinline__ int64_t scatter_bits(uint64_t x, const uint8_t* sh, int nbits) {
+    int64_t o = 0;
+    for (int i = 0; i < nbits; ++i)
+        if (((x >> i) & 1ull) && sh[i] != kNoBit) o += (int64_t)1 << sh[i];
+    return o;
+}
+
+__device__ __forceinline__ int exp_of(const unsigned* slot) {
+    if (slot == nullptr) return 0;
+    float m = __uint_as_float(*slot);
+    if (!(m > 0.f)) return 0;
+    int e;
+    frexpf(m, &e);
+    return e;
+}
+
+__device__ __forceinline__ int64_t slice_off(const SliceDigits& d, int64_t slice) {
+    int64_t off = 0;
+    for (int i = 0; i < d.n; ++i) off += ((slice / d.div[i]) % d.dim[i]) * d.stride[i];
+    return off;
+}
+
+__device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ float2 cmul(float2 x, float f) { return make_float2(x.x * f, x.y * f); }
+__device__ __forceinline__ float cmul(float x, float f) { return x * f; }
+__device__ __forceinline__ float absmax(float2 x) { return fmaxf(fabsf(x.x), fabsf(x.y)); }
+__device__ __forceinline__ float absmax(float x) { return fabsf(x); }
+__device__ __forceinline__ void fma_acc(float2& c, float2 a, float2 b) {
+    c.x = fmaf(a.x, b.x, c.x);
+    c.x = fmaf(-a.y, b.y, c.x);
+    c.y = fmaf(a.x, b.y, c.y);
+    c.y = fmaf(a.y, b.x, c.y);
+}
+__device__ __forceinline__ void fma_acc(float& c, float a, float b) { c = fmaf(a, b, c); }
+template <typename T>
+__device__ __forceinline__ T zero();
+template <>
+__device__ __forceinline__ float2 zero<float2>() {
+    return make_float2(0.f, 0.f);
+}
+template <>
+__device__ __forceinline__ float zero<float>() {
+    return 0.f;
+}
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float add(float a, float b) { return a + b; }
+
+__device__ __forceinline__ void block_max(float v, unsigned* slot) {
+    __shared__ float red[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        v = lane < nw ? red[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0 && v > 0.f) atomicMax(slot, __float_as_uint(v));
+    }
+}
+
+// Operand scales 2^-e (clamped so the float factor stays finite) and the
+// residual exponent applied to the result.
+struct Scales {
+    float fa, fb;
+    int resid;
+};
+
+__device__ __forceinline__ Scales node_scales(const TileArgs& a, bool write_exp) {
+    const int eA = exp_of(a.sc.max_a), eB = exp_of(a.sc.max_b);
+    const int cA = max(-120, min(120, eA)), cB = max(-120, min(120, eB));
+    if (write_exp && a.sc.exp_c)
+        *a.sc.exp_c = (a.sc.exp_a ? *a.sc.exp_a : 0) + (a.sc.exp_b ? *a.sc.exp_b : 0) + eA + eB;
+    Scales s;
+    s.fa = ldexpf(1.f, -cA);
+    s.fb = ldexpf(1.f, -cB);
+    s.resid = (eA - cA) + (eB - cB);
+    return s;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// Register-blocked tile kernel: one CTA = TM x TN outputs of one batch
+// index and one K split; TK-deep steps through shared memory.
+// --------------------------------------------------------------------------
+template <bool CPLX, int TM, int TN, int TK, int RM, int RN>
+__global__ void __launch_bounds__((TM / RM) * (TN / RN))
+    k_tile(const __grid_constant__ TileArgs a) {
+    using T = typename VT<CPLX>::T;
+    constexpr int TX = TN / RN, TY = TM / RM, NT = TX * TY;
+    constexpr int PB = CPLX ? 2 : 4;  // keeps sB rows 16-byte aligned
+    __shared__ T sA[TK][TM + 1];
+    __shared__ __align__(16) T sB[TK][TN + PB];
+    __shared__ int64_t rowA[TM], colB[TN], kA[TK], kB[TK];
+
+    const int tid = threadIdx.x;
+    const int64_t M = 1ll << a.nm, N = 1ll << a.nn, K = 1ll << a.nk;
+    const int64_t tiles_n = (N + TN - 1) / TN;
+    const int64_t m0 = ((int64_t)blockIdx.x / tiles_n) * TM;
+    const int64_t n0 = ((int64_t)blockIdx.x % tiles_n) * TN;
+    const int split_id = blockIdx.z % a.split;
+    const int64_t b = blockIdx.z / a.split;
+    const Scales sc = node_scales(a, blockIdx.x == 0 && blockIdx.z == 0 && tid == 0);
+    const int64_t slice = a.ctl->slice;
+    const int64_t baseA =
+        slice_off(a.sla, slice) + scatter_bits(b, a.a_b, a.nb) + scatter_bits(m0, a.a_m, a.nm);
+    const int64_t baseB =
+        slice_off(a.slb, slice) + scatter_bits(b, a.b_b, a.nb) + scatter_bits(n0, a.b_n, a.nn);
+    for (int i = tid; i < TM; i += NT) rowA[i] = scatter_bits(i, a.a_m, a.nm);
+    for (int j = tid; j < TN; j += NT) colB[j] = scatter_bits(j, a.b_n, a.nn);
+    for (int t = tid; t < TK; t += NT) {
+        kA[t] = scatter_bits(t, a.a_k, a.nk);
+        kB[t] = scatter_bits(t, a.b_k, a.nk);
+    }
+    __syncthreads();
+    const int mlim = (int)min64(M - m0, TM);
+    const int nlim = (int)min64(N - n0, TN);
+    const int64_t kbeg = (int64_t)split_id * a.kchunk;
+    const int64_t kend = min64(K, kbeg + a.kchunk);
+    const T* A = reinterpret_cast<const T*>(a.A);
+    const T* B = reinterpret_cast<const T*>(a.B);
+    const int tx = tid % TX, ty = tid / TX;
+
+    T acc[RM][RN];
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int c = 0; c < RN; ++c) acc[r][c] = zero<T>();
+
+    for (int64_t k0 = kbeg; k0 < kend; k0 += TK) {
+        const int64_t kaA = scatter_bits(k0, a.a_k, a.nk);
+        const int64_t kaB = scatter_bits(k0, a.b_k, a.nk);
+        const int klim = (int)min64(kend - k0, TK);
+        for (int e = tid; e < TM * TK; e += NT) {
+            int i, t;
+            if (a.a_mfast) {
+                i = e % TM;
+                t = e / TM;
+            } else {
+                t = e % TK;
+                i = e / TK;
+            }
+            T v = zero<T>();
+            if (i < mlim && t < klim) v = cmul(A[baseA + rowA[i] + kaA + kA[t]], sc.fa);
+            sA[t][i] = v;
+        }
+        for (int e = tid; e < TN * TK; e += NT) {
+            int j, t;
+            if (a.b_nfast) {
+                j = e % TN;
+                t = e / TN;
+            } else {
+                t = e % TK;
+                j = e / TK;
+            }
+            T v = zero<T>();
+            if (j < nlim && t < klim) v = cmul(B[baseB + colB[j] + kaB + kB[t]], sc.fb);
+            sB[t][j] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int t = 0; t < TK; ++t) {
+            T af[RM], bf[RN];
+#pragma unroll
+            for (int r = 0; r < RM; ++r) af[r] = sA[t][ty * RM + r];
+#pragma unroll
+            for (int c = 0; c < RN; ++c) bf[c] = sB[t][tx * RN + c];
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int c = 0; c < RN; ++c) fma_acc(acc[r][c], af[r], bf[c]);
+        }
+        __syncthreads();
+    }
+
+    // epilogue: direct output (one split) or a partial for the reduce pass
+    float lmax = 0.f;
+    T* out = reinterpret_cast<T*>(a.split > 1 ? a.P : a.C);
+    const int64_t plane = (a.split > 1 ? (int64_t)split_id * ((int64_t)a.nbatch) : 0) + b;
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+        const int i = ty * RM + r;
+        if (i >= mlim) continue;
+        const int64_t rowoff = (plane * M + m0 + i) * N + n0;
+#pragma unroll
+        for (int c = 0; c < RN; ++c) {
+            const int j = tx * RN + c;
+            if (j >= nlim) continue;
+            T v = acc[r][c];
+            if (a.split == 1) {
+                if (sc.resid) {
+                    if constexpr (CPLX) {
+                        v.x = ldexpf(v.x, -sc.resid);
+                        v.y = ldexpf(v.y, -sc.resid);
+                    } else {
+                        v = ldexpf(v, -sc.resid);
+                    }
+                }
+                lmax = fmaxf(lmax, absmax(v));
+            }
+            out[rowoff + j] = v;
+        }
+    }
+    if (a.split == 1) block_max(lmax, a.sc.max_c);
+}
+
+// Fixed-order sum of the K-split partials, then the node epilogue.
+template <bool CPLX>
+__global__ void __launch_bounds__(256) k_split_reduce(const __grid_constant__ TileArgs a) {
+    using T = typename VT<CPLX>::T;
+    const int64_t plane_sz = (int64_t)a.nbatch << (a.nm + a.nn);
+    const Scales sc = node_scales(a, blockIdx.x == 0 && threadIdx.x == 0);
+    const T* P = reinterpret_cast<const T*>(a.P);
+    T* C = reinterpret_cast<T*>(a.C);
+    float lmax = 0.f;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < plane_sz;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        T v = P[o];
+        for (int s = 1; s < a.split; ++s) v = add(v, P[(int64_t)s * plane_sz + o]);
+        if (sc.resid) {
+            if constexpr (CPLX) {
+                v.x = ldexpf(v.x, -sc.resid);
+                v.y = ldexpf(v.y, -sc.resid);
+            } else {
+                v = ldexpf(v, -sc.resid);
+            }
+        }
+        lmax = fmaxf(lmax, absmax(v));
+        C[o] = v;
+    }
+    block_max(lmax, a.sc.max_c);
+}
+
+// Tiny output, long K: grid (outputs, batch, K splits); each CTA reduces its
+// K range in a fixed order; with several splits the partials go to P and
+// k_split_reduce sums them in split order (deterministic).
+template <bool CPLX>
+__global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a) {
+    using T = typename VT<CPLX>::T;
+    const int64_t N = 1ll << a.nn, M = 1ll << a.nm, K = 1ll << a.nk;
+    const int64_t m = (int64_t)blockIdx.x / N, n = (int64_t)blockIdx.x % N;
+    const int64_t b = blockIdx.y;
+    const int sp = blockIdx.z;
+    const Scales sc = node_scales(a, blockIdx.x == 0 && blockIdx.y == 0 && sp == 0 && threadIdx.x == 0);
+    const int64_t slice = a.ctl->slice;
+    const int64_t baseA =
+        slice_off(a.sla, slice) + scatter_bits(b, a.a_b, a.nb) + scatter_bits(m, a.a_m, a.nm);
+    const int64_t baseB =
+        slice_off(a.slb, slice) + scatter_bits(b, a.b_b, a.nb) + scatter_bits(n, a.b_n, a.nn);
+    const T* A = reinterpret_cast<const T*>(a.A);
+    const T* B = reinterpret_cast<const T*>(a.B);
+    const int lo = threadIdx.x;
+    const int64_t loA = scatter_bits(lo, a.a_k, a.nk), loB = scatter_bits(lo, a.b_k, a.nk);
+    const int64_t kb = (int64_t)sp * a.kchunk, ke = min64(K, kb + a.kchunk);
+    T acc0 = zero<T>(), acc1 = zero<T>();
+    int64_t hi = kb;
+    for (; hi + 256 < ke; hi += 512) {
+        const int64_t hA0 = scatter_bits(hi, a.a_k, a.nk), hB0 = scatter_bits(hi, a.b_k, a.nk);
+        const int64_t hA1 = scatter_bits(hi + 256, a.a_k, a.nk), hB1 = scatter_bits(hi + 256, a.b_k, a.nk);
+        const T x0 = A[baseA + hA0 + loA], y0 = B[baseB + hB0 + loB];
+        const T x1 = A[baseA + hA1 + loA], y1 = B[baseB + hB1 + loB];
+        fma_acc(acc0, cmul(x0, sc.fa), cmul(y0, sc.fb));
+        fma_acc(acc1, cmul(x1, sc.fa), cmul(y1, sc.fb));
+    }
+    for (; hi < ke; hi += 256) {
+        if (hi + lo >= ke) break;
+        const int64_t hA = scatter_bits(hi, a.a_k, a.nk), hB = scatter_bits(hi, a.b_k, a.nk);
+        fma_acc(acc0, cmul(A[baseA + hA + loA], sc.fa), cmul(B[baseB + hB + loB], sc.fb));
+    }
+    // fixed-order block reduction
+    __shared__ T red[256];
+    red[threadIdx.x] = add(acc0, acc1);
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = add(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        T v = red[0];
+        const int64_t o = (b * M + m) * N + n;
+        if (a.split > 1) {
+            reinterpret_cast<T*>(a.P)[(int64_t)sp * (a.nbatch * M * N) + o] = v;
+            return;
+        }
+        if (sc.resid) {
+            if constexpr (CPLX) {
+                v.x = ldexpf(v.x, -sc.resid);
+                v.y = ldexpf(v.y, -sc.resid);
+            } else {
+                v = ldexpf(v, -sc.resid);
+            }
+        }
+        reinterpret_cast<T*>(a.C)[o] = v;
+        float mx = absmax(v);
+        if (mx > 0.f) atomicMax(a.sc.max_c, __float_as_uint(mx));
+    }
+}
+
+// One launch for all small nodes of a tree level.  Each CTA computes a
+// chunk of one node's outputs; descriptors live in device memory.  With
+// fewer than 256 outputs in the chunk, g = 256/outputs threads share each
+// output's K range and reduce it in a fixed order.
+template <bool CPLX>
+__global__ void __launch_bounds__(256)
+    k_wave(const WaveItem* items, const TileArgs* descs, const void* const* leaf_ptrs) {
+    using T = typename VT<CPLX>::T;
+    __shared__ TileArgs d;
+    __shared__ int64_t kA[256], kB[256];
+    __shared__ T red[256];
+    const WaveItem it = items[blockIdx.x];
+    {
+        const int4* src = reinterpret_cast<const int4*>(descs + it.node);
+        int4* dst = reinterpret_cast<int4*>(&d);
+        for (int i = threadIdx.x; i < (int)(sizeof(TileArgs) / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int tid = threadIdx.x;
+    const T* A = reinterpret_cast<const T*>(d.a_leaf >= 0 ? leaf_ptrs[d.a_leaf] : d.A);
+    const T* B = reinterpret_cast<const T*>(d.b_leaf >= 0 ? leaf_ptrs[d.b_leaf] : d.B);
+    const Scales sc = node_scales(d, it.o_begin == 0 && tid == 0);
+    const int64_t slice = d.ctl->slice;
+    const int64_t sA = slice_off(d.sla, slice), sB = slice_off(d.slb, slice);
+    const int64_t K = 1ll << d.nk;
+    const int kt = d.nk < 8 ? (int)K : 256;  // table covers k & 255
+    for (int t = tid; t < kt; t += 256) {
+        kA[t] = scatter_bits(t, d.a_k, d.nk);
+        kB[t] = scatter_bits(t, d.b_k, d.nk);
+    }
+    __syncthreads();
+    const int64_t nmask = (1ll << d.nn) - 1, mmask = (1ll << d.nm) - 1;
+    const int O = (int)it.o_count;
+    const int g = O >= 256 ? 1 : 256 / O;
+    float lmax = 0.f;
+    T* C = reinterpret_cast<T*>(d.C);
+    for (int ol = tid / g; ol < O; ol += 256 / g) {
+        const int64_t o = it.o_begin + ol;
+        const int64_t n = o & nmask, m = (o >> d.nn) & mmask, b = o >> (d.nn + d.nm);
+        const int64_t offA = sA + scatter_bits(b, d.a_b, d.nb) + scatter_bits(m, d.a_m, d.nm);
+        const int64_t offB = sB + scatter_bits(b, d.b_b, d.nb) + scatter_bits(n, d.b_n, d.nn);
+        T acc = zero<T>();
+        for (int64_t t = tid % g; t < K; t += g) {
+            int64_t ka, kb2;
+            if (d.nk < 8) {
+                ka = kA[t];
+                kb2 = kB[t];
+            } else {
+                const int64_t hi = t & ~255ll;
+                ka = kA[t & 255] + (hi ? scatter_bits(hi, d.a_k, d.nk) : 0);
+                kb2 = kB[t & 255] + (hi ? scatter_bits(hi, d.b_k, d.nk) : 0);
+            }
+            fma_acc(acc, cmul(A[offA + ka], sc.fa), cmul(B[offB + kb2], sc.fb));
+        }
+        if (g > 1) {
+            red[tid] = acc;
+            __syncthreads();
+            const int j = tid % g;
+            for (int s2 = g / 2; s2 > 0; s2 >>= 1) {
+                if (j < s2) red[tid] = add(red[tid], red[tid + s2]);
+                __syncthreads();
+            }
+            if (j != 0) continue;
+            acc = red[tid];
+        }
+        if (sc.resid) {
+            if constexpr (CPLX) {
+                acc.x = ldexpf(acc.x, -sc.resid);
+                acc.y = ldexpf(acc.y, -sc.resid);
+            } else {
+                acc = ldexpf(acc, -sc.resid);
+            }
+        }
+        lmax = fmaxf(lmax, absmax(acc));
+        C[o] = acc;
+    }
+    block_max(lmax, d.sc.max_c);
+}
+
+// --------------------------------------------------------------------------
+// launchers
+// --------------------------------------------------------------------------
+
+template <bool CPLX, int TM, int TN, int TK, int RM, int RN>
+static cudaError_t launch_cfg(const TileArgs& a, cudaStream_t s) {
+    const int64_t M = 1ll << a.nm, N = 1ll << a.nn;
+    const int64_t tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+    dim3 grid((unsigned)tiles, 1, (unsigned)(a.nbatch * a.split));
+    k_tile<CPLX, TM, TN, TK, RM, RN><<<grid, (TM / RM) * (TN / RN), 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool CPLX>
+static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
+    cudaError_t e;
+    switch (a.cfg) {
+        case kTile64x64: e = launch_cfg<CPLX, 64, 64, 16, 4, 4>(a, s); break;
+        case kTile16x256: e = launch_cfg<CPLX, 16, 256, 16, 4, 4>(a, s); break;
+        case kTile4x1024: e = launch_cfg<CPLX, 4, 1024, 4, 4, 4>(a, s); break;
+        case kTile256x16: e = launch_cfg<CPLX, 256, 16, 16, 4, 4>(a, s); break;
+        case kTileDot: {
+            const int64_t outs = 1ll << (a.nm + a.nn);
+            k_dot<CPLX><<<dim3((unsigned)outs, (unsigned)a.nbatch, (unsigned)a.split), 256, 0, s>>>(a);
+            e = cudaGetLastError();
+            break;
+        }
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess || a.split == 1) return e;
+    const int64_t n = (int64_t)a.nbatch << (a.nm + a.nn);
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_split_reduce<CPLX><<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s) {
+    return is_c ? launch_tile_t<true>(a, s) : launch_tile_t<false>(a, s);
+}
+
+cudaError_t launch_wave(const WaveItem* items, int n_items, const TileArgs* descs,
+                        const void* const* leaf_ptrs, bool is_c, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    if (is_c)
+        k_wave<true><<<n_items, 256, 0, s>>>(items, descs, leaf_ptrs);
+    else
+        k_wave<false><<<n_items, 256, 0, s>>>(items, descs, leaf_ptrs);
+    return cudaGetLastError();
+}
+
+}  // namespace tn
