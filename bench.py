@@ -34,6 +34,10 @@ WORKLOAD = "ising_rr3_n100_beta0.3_greedy_ws24"
 L2_FLUSH_BYTES = 512 << 20
 # FP32 FMA peak of one GB300: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz.
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# nominal dense tensor rates per GPU (TF32 : BF16 = 1.1 : 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
+# real products executed per algorithmic product on the tensor cores
+MODE_PASSES = {"tf32_split": 3, "bf16_split": 3, "tf32_3m": 1}
 
 
 def build_workload(seed: int, n: int = 100, target: float = 24.0):
@@ -187,6 +191,8 @@ def main():
     ap.add_argument("--mode", default="fp32")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare-modes", action="store_true",
+                    help="also time every precision mode (device buffers) and report the error")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -270,30 +276,43 @@ def main():
     result = complex(m.cpu()) if cplx else float(m.cpu())
     result_exp = int(e.cpu())
 
-    # roofline of the dominant node kernel
+    # roofline of the dominant launch step
     peaks = load_peaks()
     dnodes = steps[dom]["nodes"]
     dn = {"flops": sum(nodes[k]["flops"] for k in dnodes),
           "bytes": sum(nodes[k]["bytes"] for k in dnodes)}
     dmean = statistics.mean(dom_ms) / 1e3
+    st = steps[dom]
     t_hbm = dn["bytes"] / (peaks["hbm_gbs"] * 1e9)
-    t_alu = dn["flops"] / (FP32_SIMT_TFLOPS * 1e12)
+    if st["kind"] == 2:
+        tc_peak = peaks["bf16_tflops"] * (1.0 if args.mode == "bf16_split" else TF32_OVER_BF16)
+        passes = MODE_PASSES.get(args.mode, 1)
+        t_alu = dn["flops"] * passes / (tc_peak * 1e12)
+        pipe = {"bound": "tensor", "peak": tc_peak,
+                "peak_source": f"{peaks['source']} bf16 x " +
+                               ("1" if args.mode == "bf16_split" else "1.1/2.25 (nominal TF32:BF16)"),
+                "executed_flops": dn["flops"] * passes}
+    else:
+        t_alu = dn["flops"] / (FP32_SIMT_TFLOPS * 1e12)
+        pipe = {"bound": "alu", "peak": FP32_SIMT_TFLOPS,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"}
     if t_hbm >= t_alu:
         roof = {"bound": "hbm", "achieved": dn["bytes"] / dmean / 1e9, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s"}
+                "unit": "GB/s", "peak_source": peaks["source"]}
     else:
-        roof = {"bound": "alu", "achieved": dn["flops"] / dmean / 1e12, "peak": FP32_SIMT_TFLOPS,
-                "unit": "TFLOP/s"}
+        roof = {"bound": pipe["bound"], "achieved": dn["flops"] / dmean / 1e12, "peak": pipe["peak"],
+                "unit": "TFLOP/s", "peak_source": pipe["peak_source"]}
+        if "executed_flops" in pipe:
+            roof["executed_frac"] = pipe["executed_flops"] / dmean / 1e12 / pipe["peak"]
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
     cfg_names = {0: "generic", 1: "tile64x64", 2: "tile16x256", 3: "tile4x1024", 4: "tile256x16",
                  5: "dot"}
-    st = steps[dom]
+    kname = {0: "k_generic", 1: "k_tile", 2: "k_tc (tcgen05)"}[st["kind"]]
     roof["kernel"] = (f"step {dom} of {n_steps}: " +
                       (f"k_wave over {len(dnodes)} nodes" if st["wave"] else
-                       f"node {dnodes[0]} ({cfg_names.get(st['cfg'], 'generic') if st['kind'] == 1 else 'generic'})"))
-    roof["peak_source"] = (peaks["source"] if roof["bound"] == "hbm"
-                           else "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz")
+                       f"node {dnodes[0]}, {kname}" +
+                       (f" {cfg_names.get(st['cfg'], '')}" if st["kind"] == 1 else "")))
     roof["algorithmic"] = {"flops": dn["flops"], "bytes": dn["bytes"]}
     roof["share_of_step"] = dmean * 1e3 / ms_per_step
 
@@ -333,6 +352,33 @@ def main():
             rel_err = abs(math.expm1(math.log(abs(result)) + (result_exp - oe) * math.log(2)
                                      - math.log(abs(float(om)))))
 
+    modes_cmp = None
+    if args.compare_modes and rank == 0:
+        modes_cmp = {}
+        ref_ln = None
+        if cpu is not None:
+            ref_ln = math.log(abs(float(om))) + oe * math.log(2) if not cplx else None
+        for md in ["fp32", "tf32_split", "bf16_split", "tf32_3m"]:
+            for _ in range(3):
+                mm_, ee_ = tnw.contract(pairs, sliced, md)
+            es, ee2 = events(args.steps), events(args.steps)
+            for i in range(args.steps):
+                flush.zero_()
+                es[i].record(stream)
+                mm_, ee_ = tnw.contract(pairs, sliced, md)
+                ee2[i].record(stream)
+            torch.cuda.synchronize()
+            tms = sum(a.elapsed_time(b2) for a, b2 in zip(es, ee2)) / args.steps
+            entry = {"ms_per_network": tms, "tflops": flops_step / (tms / 1e3) / 1e12}
+            if cpu is not None:
+                if cplx:
+                    ref = complex(om)
+                    entry["rel_err"] = abs(complex(mm_.cpu()) * 2.0 ** (int(ee_.cpu()) - oe) - ref) / abs(ref)
+                else:
+                    entry["rel_err"] = abs(math.expm1(math.log(abs(float(mm_.cpu()))) +
+                                                      int(ee_.cpu()) * math.log(2) - ref_ln))
+            modes_cmp[md] = entry
+
     launches_per_step = sum(1 + (1 if (s["cfg"] in (1, 2, 3, 4, 5) and not s["wave"]) else 0)
                             for s in steps) * info.d_sliced + 2 * info.d_sliced + 3
     line = {
@@ -355,6 +401,10 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
+        "modes": modes_cmp,
+        "step_profile": [{"step": k, "kind": ["generic", "tile", "tcgen05"][s["kind"]],
+                          "wave": s["wave"], "nodes": len(s["nodes"]), "ms": round(step_ms[k], 4)}
+                         for k, s in enumerate(steps)],
         "clocks": clocks,
     }
     if rank == 0:

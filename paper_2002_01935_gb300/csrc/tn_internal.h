@@ -129,6 +129,8 @@ struct AccumArgs {
 // Launchers (tn_kernels.cu).  is_c: complex64 data.
 cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s);  // tn_tiled.cu
+// Tensor-core node (tn_tc.cu): prec 0 TF32, 1 TF32 hi+lo, 2 BF16 hi+lo.
+cudaError_t launch_tc(const TileArgs& a, int prec, bool is_c, cudaStream_t s);
 // All small nodes of one tree level in one launch (tn_tiled.cu).
 cudaError_t launch_wave(const WaveItem* items, int n_items, const TileArgs* descs,
                         const void* const* leaf_ptrs, bool is_c, cudaStream_t s);

@@ -139,7 +139,12 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems) 
     };
     const int fa = fastest(la, sa), fb = fastest(lb, sb);
     const bool fa_k = fa >= 0 && has(ks, fa), fb_k = fb >= 0 && has(ks, fb);
-    const bool by_a = fa_k && !fb_k;
+    // K follows the strides of the operand that needs it for contiguous
+    // loads; when both or neither do, the larger operand wins
+    int64_t size_a = 1, size_b = 1;
+    for (int l : la) size_a *= d.dims[l];
+    for (int l : lb) size_b *= d.dims[l];
+    const bool by_a = (fa_k && !fb_k) || (fa_k == fb_k && size_a > size_b);
     const int64_t big = INT64_MAX / 4;
     std::sort(ks.begin(), ks.end(), [&](int x, int y) {
         int64_t sx = by_a ? stride_in(la, sa, x) : stride_in(lb, sb, x);
@@ -154,6 +159,12 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems) 
         if (!push(t.b_k, tmp, l, stride_in(lb, sb, l))) return false;
     }
     if (t.nb > 16 || t.nm > 31 || t.nn > 31 || t.nk > 40 || t.nm + t.nn > 40) return false;
+    // the kernels keep per-thread operand offsets in 32 bits
+    for (const std::vector<int>* lab : {&la, &lb}) {
+        int64_t sz = 1;
+        for (int l : *lab) sz *= d.dims[l];
+        if (sz >= (int64_t(1) << 31)) return false;
+    }
     t.nbatch = int64_t(1) << t.nb;
     t.a_mfast = fa >= 0 && has(nd.gm, fa);
     t.b_nfast = fb >= 0 && has(nd.gn, fb);
@@ -185,7 +196,7 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems) 
         const int64_t tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN) * t.nbatch;
         const int64_t ktiles = (K + TK - 1) / TK;
         int split = 1;
-        while (tiles * split < 2 * 152 && split * 4 <= ktiles && split < 64 &&
+        while (tiles * split < 2 * 152 && split * 16 <= ktiles && split < 64 &&
                t.nbatch * split * 2 <= 65535)
             split *= 2;
         t.split = split;
@@ -215,6 +226,7 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
     // TN_NO_WAVES=1 launches every node separately
     if (const char* e = getenv("TN_FORCE_GENERIC")) p.force_generic = e[0] == '1';
     if (const char* e = getenv("TN_NO_WAVES")) p.no_waves = e[0] == '1';
+    if (const char* e = getenv("TN_NO_TENSOR_CORES")) p.no_tensor_cores = e[0] == '1';
     const int L = (int)d.dims.size();
     // ---- tree validation (Sec. 2: leaves first, children before parents)
     if ((int64_t)p.pairs.size() != 2 * (int64_t)(n - 1)) {
@@ -411,12 +423,22 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
     }
     p.W = W;
     p.C = C;
-    // ---- kernel choice per node
+    // ---- kernel choice per node: large GEMM-shaped nodes go to the tensor
+    // cores in the reduced-precision modes (M >= 128 rows, N >= 128 real
+    // accumulator columns, K >= 16); everything else on CUDA cores
     int64_t split_elems = 0;
     for (size_t k = 0; k < p.nodes.size(); ++k) {
         Node& nd = p.nodes[k];
         nd.kind = kGeneric;
-        if (!p.force_generic) plan_tile(d, p, nd, split_elems);
+        if (p.force_generic || !plan_tile(d, p, nd, split_elems)) continue;
+        const TileArgs& t = nd.tile;
+        const int nn_min = d.is_complex() ? 6 : 7;
+        if (p.mode != TN_MODE_FP32 && !p.no_tensor_cores && t.cfg != kTileDot && t.nm >= 7 &&
+            t.nn >= nn_min && t.nk >= 4 && t.nbatch <= 65535) {
+            nd.kind = kTensorCore;
+            nd.tile.split = 1;
+            nd.tile.kchunk = int64_t(1) << t.nk;
+        }
     }
     p.split_bytes = split_elems * (int64_t)d.elem_bytes();
     // ---- launch schedule: tree levels; per level one wave launch for the
@@ -582,7 +604,7 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
         g.sc.max_c = p.maxabs + k;
         g.sc.exp_c = p.exps + k;
         Node& ndm = p.nodes[k];
-        if (ndm.kind == kTiled) {
+        if (ndm.kind == kTiled || ndm.kind == kTensorCore) {
             TileArgs& t = ndm.tile;
             t.A = g.A;
             t.B = g.B;
@@ -650,7 +672,13 @@ static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, cons
                             reinterpret_cast<const void* const*>(p.leaf_ptr_dev), c, s);
         } else {
             const Node& nd = p.nodes[st.node];
-            e = nd.kind == kTiled ? launch_tile(nd.tile, c, s) : launch_generic(p.gen[st.node], c, s);
+            if (nd.kind == kTensorCore)
+                e = launch_tc(nd.tile, p.mode == TN_MODE_BF16_SPLIT ? 2 : (p.mode == TN_MODE_TF32_SPLIT ? 1 : 0),
+                              c, s);
+            else if (nd.kind == kTiled)
+                e = launch_tile(nd.tile, c, s);
+            else
+                e = launch_generic(p.gen[st.node], c, s);
         }
         if (e != cudaSuccess) return e;
         if (ev && k == pf + pc - 1 &&

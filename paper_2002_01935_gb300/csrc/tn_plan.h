@@ -62,6 +62,7 @@ struct Plan {
     tn_mode mode = TN_MODE_FP32;
     bool force_generic = false;  // every node on the generic kernel
     bool no_waves = false;       // one launch per node
+    bool no_tensor_cores = false;  // reduced-precision modes on CUDA cores only
     std::vector<int32_t> pairs;
     std::vector<int64_t> sliced_ids;
     std::vector<int> sliced;  // dense

@@ -167,37 +167,52 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
 #pragma unroll
         for (int c = 0; c < RN; ++c) acc[r][c] = zero<T>();
 
-    for (int64_t k0 = kbeg; k0 < kend; k0 += TK) {
+    // global -> registers for one K step (all loads issued back to back)
+    constexpr int LA = (TM * TK + NT - 1) / NT, LB = (TN * TK + NT - 1) / NT;
+    T ra[LA], rb[LB];
+    auto gload = [&](int64_t k0) {
         const int64_t kaA = scatter_bits(k0, a.a_k, a.nk);
         const int64_t kaB = scatter_bits(k0, a.b_k, a.nk);
         const int klim = (int)min64(kend - k0, TK);
-        for (int e = tid; e < TM * TK; e += NT) {
-            int i, t;
-            if (a.a_mfast) {
-                i = e % TM;
-                t = e / TM;
-            } else {
-                t = e % TK;
-                i = e / TK;
-            }
-            T v = zero<T>();
-            if (i < mlim && t < klim) v = cmul(A[baseA + rowA[i] + kaA + kA[t]], sc.fa);
-            sA[t][i] = v;
+#pragma unroll
+        for (int q = 0; q < LA; ++q) {
+            const int e = tid + q * NT;
+            const int i = a.a_mfast ? e % TM : e / TK;
+            const int t = a.a_mfast ? e / TM : e % TK;
+            const bool in = e < TM * TK && i < mlim && t < klim;
+            ra[q] = in ? cmul(A[baseA + rowA[i] + kaA + kA[t]], sc.fa) : zero<T>();
         }
-        for (int e = tid; e < TN * TK; e += NT) {
-            int j, t;
-            if (a.b_nfast) {
-                j = e % TN;
-                t = e / TN;
-            } else {
-                t = e % TK;
-                j = e / TK;
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+            const int e = tid + q * NT;
+            const int j = a.b_nfast ? e % TN : e / TK;
+            const int t = a.b_nfast ? e / TN : e % TK;
+            const bool in = e < TN * TK && j < nlim && t < klim;
+            rb[q] = in ? cmul(B[baseB + colB[j] + kaB + kB[t]], sc.fb) : zero<T>();
+        }
+    };
+    if (kbeg < kend) gload(kbeg);
+    for (int64_t k0 = kbeg; k0 < kend; k0 += TK) {
+#pragma unroll
+        for (int q = 0; q < LA; ++q) {
+            const int e = tid + q * NT;
+            if (e < TM * TK) {
+                const int i = a.a_mfast ? e % TM : e / TK;
+                const int t = a.a_mfast ? e / TM : e % TK;
+                sA[t][i] = ra[q];
             }
-            T v = zero<T>();
-            if (j < nlim && t < klim) v = cmul(B[baseB + colB[j] + kaB + kB[t]], sc.fb);
-            sB[t][j] = v;
+        }
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+            const int e = tid + q * NT;
+            if (e < TN * TK) {
+                const int j = a.b_nfast ? e % TN : e / TK;
+                const int t = a.b_nfast ? e / TN : e % TK;
+                sB[t][j] = rb[q];
+            }
         }
         __syncthreads();
+        if (k0 + TK < kend) gload(k0 + TK);  // next step's loads overlap this step's FMAs
 #pragma unroll 4
         for (int t = 0; t < TK; ++t) {
             T af[RM], bf[RN];
@@ -255,8 +270,17 @@ __global__ void __launch_bounds__(256) k_split_reduce(const __grid_constant__ Ti
     float lmax = 0.f;
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < plane_sz;
          o += (int64_t)gridDim.x * blockDim.x) {
-        T v = P[o];
-        for (int s = 1; s < a.split; ++s) v = add(v, P[(int64_t)s * plane_sz + o]);
+        // fixed order: eight independent partial chains, then combined
+        T part[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) part[q] = zero<T>();
+        int sp = 0;
+        for (; sp + 8 <= a.split; sp += 8)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) part[q] = add(part[q], P[(int64_t)(sp + q) * plane_sz + o]);
+        for (int q = 0; sp < a.split; ++sp, ++q) part[q] = add(part[q], P[(int64_t)sp * plane_sz + o]);
+        T v = add(add(add(part[0], part[1]), add(part[2], part[3])),
+                  add(add(part[4], part[5]), add(part[6], part[7])));
         if (sc.resid) {
             if constexpr (CPLX) {
                 v.x = ldexpf(v.x, -sc.resid);

@@ -1,0 +1,113 @@
+"""Precision modes on the tensor cores against the FP64 oracle.
+
+Large nodes run on tcgen05 tensor cores in the reduced-precision modes:
+TF32 single pass, TF32 hi+lo split and BF16 hi+lo split (three products,
+FP32 accumulation).  Tolerances (relative to the cancellation-free scale,
+i.e. the same contraction on |A|, |B|): 1e-5 for the TF32 split, 1e-4 for
+the BF16 split, 2e-3 for a single TF32 pass (10-bit mantissa).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import brute, tree
+from paper_2002_01935_gb300 import inputs, planner
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"tf32_split": 1e-5, "bf16_split": 1e-4, "tf32_3m": 2e-3, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    if not _t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_01935_gb300 import build
+    build.build()
+    return _t
+
+
+def run(torch, net, pairs, sliced=(), mode="fp32"):
+    from paper_2002_01935_gb300 import binding
+    cplx = net.is_complex
+    dt = torch.complex64 if cplx else torch.float32
+    ts = [torch.from_numpy(np.ascontiguousarray(t)).to(dt).contiguous().cuda() for t in net.tensors]
+    tnw = binding.TensorNetwork(net.labels, net.dims, net.open, ts, complex_=cplx)
+    try:
+        info = tnw.plan_info(pairs, sliced, mode)
+        m, e = tnw.contract(pairs, sliced, mode)
+        torch.cuda.synchronize()
+        return m.cpu().numpy(), int(e.cpu()), info
+    finally:
+        tnw.close()
+
+
+def gemm_net(mb, nb, kb, batch=0, cplx=True, seed=0, interleave=True):
+    """C[b,m,n] = sum_k A[b,m,k] B[b,k,n] with all labels of size 2; the K
+    labels interleave with M and N labels in the operand layouts."""
+    rng = np.random.default_rng(seed)
+    lab = 0
+    bl = list(range(lab, lab + batch)); lab += batch
+    ml = list(range(lab, lab + mb)); lab += mb
+    nl = list(range(lab, lab + nb)); lab += nb
+    kl = list(range(lab, lab + kb)); lab += kb
+    dims = {l: 2 for l in range(lab)}
+    if interleave:
+        la = bl + kl[::2] + ml + kl[1::2]
+        lb = nl[:2] + kl + bl + nl[2:]
+    else:
+        la = bl + ml + kl
+        lb = bl + kl + nl
+    def t(shape):
+        x = rng.standard_normal(shape)
+        return x + 1j * rng.standard_normal(shape) if cplx else x
+    ta, tb = t([2] * len(la)), t([2] * len(lb))
+    return inputs.Network([ta, tb], [la, lb], dims, bl + ml + nl)
+
+
+@pytest.mark.parametrize("mode", ["tf32_split", "bf16_split", "tf32_3m"])
+@pytest.mark.parametrize("shape", [(8, 8, 8, 0, True), (7, 9, 6, 0, False), (9, 7, 10, 0, True),
+                                   (7, 7, 4, 1, True), (8, 8, 7, 0, False), (7, 8, 3, 0, True)])
+def test_single_gemm_node(torch, mode, shape):
+    mb, nb, kb, batch, cplx = shape
+    net = gemm_net(mb, nb, kb, batch, cplx, seed=sum(shape))
+    pairs = [(0, 1)]
+    m, e, info = run(torch, net, pairs, mode=mode)
+    got = m * 2.0 ** e
+    ref = brute.nested_sum(net.tensors, net.labels, net.dims, net.open) if mb + nb + kb + batch <= 22 \
+        else tree.value(net.tensors, net.labels, net.dims, net.open, pairs)
+    scale = tree.value([np.abs(x) for x in net.tensors], net.labels, net.dims, net.open, pairs)
+    if kb >= 4 and mb >= 7:
+        assert info["n_tensor_core"] == 1
+    err = float(np.max(np.abs(got - ref) / scale))
+    assert err <= TOL[mode], err
+
+
+@pytest.mark.parametrize("mode", ["tf32_split", "bf16_split", "tf32_3m"])
+def test_cfg1_ising_modes(torch, mode):
+    net = inputs.random_ising(100, seed=0)
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    m, e, info = run(torch, net, pairs, mode=mode)
+    assert info["n_tensor_core"] >= 1
+    mo, eo = tree.contract_net(net, pairs)
+    d = math.log(float(m)) + e * math.log(2) - (math.log(float(mo)) + eo * math.log(2))
+    assert abs(math.expm1(d)) <= TOL[mode], d
+
+
+@pytest.mark.parametrize("mode", ["tf32_split", "bf16_split", "tf32_3m"])
+def test_circuit_5x5_modes(torch, mode):
+    """Complex 4M on the tensor cores over a whole circuit network; the
+    amplitude's error against the FP64 oracle is within the mode's bound."""
+    circ = inputs.random_circuit(5, 5, 10, seed=0)
+    net = inputs.circuit_network(circ, inputs.random_bitstrings(25, 1, seed=1000)[0])
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    m, e, info = run(torch, net, pairs, mode=mode)
+    assert info["n_tensor_core"] >= 1
+    mo, eo = tree.contract_net(net, pairs)
+    ref = complex(mo) * 2.0 ** eo
+    err = abs(complex(m) * 2.0 ** e - ref) / abs(ref)
+    # the amplitude (~2^-12.5) results from heavy cancellation: allow a
+    # growth factor of 10 over the per-contraction bound
+    assert err <= 10 * TOL[mode], err
