@@ -218,7 +218,7 @@ def main():
     cplx = net.is_complex
     dt = torch.complex64 if cplx else torch.float32
     elem = 8 if cplx else 4
-    leaves = [torch.from_numpy(np.ascontiguousarray(t)).to(dt).contiguous().cuda() for t in net.tensors]
+    leaves = [torch.from_numpy(np.array(t, order="C")).to(dt).contiguous().cuda() for t in net.tensors]
     tnw = binding.TensorNetwork(net.labels, net.dims, net.open, leaves, complex_=cplx)
     plan = tnw.plan_info(pairs, sliced, args.mode)
     flops_step = info.flops(cplx)
@@ -319,7 +319,7 @@ def main():
     # end to end through the C-ABI with host buffers (copies inside the call)
     e2e = None
     if rank == 0:
-        hl = [torch.from_numpy(np.ascontiguousarray(t)).to(dt).contiguous().pin_memory()
+        hl = [torch.from_numpy(np.array(t, order="C")).to(dt).contiguous().pin_memory()
               for t in net.tensors]
         htn = binding.TensorNetwork(net.labels, net.dims, net.open, hl, complex_=cplx)
         odt = torch.complex128 if cplx else torch.float64

@@ -280,6 +280,26 @@ class TensorNetwork:
                        slice_begin, slice_count, no_graph, tile_override, evp, prof_first)
         return out, out_exp
 
+    def grad(self, pairs, sliced, mode, adjoint, adj_exp2=0, grads=None, stream=None):
+        """Leaf gradients conj(d value / d T_v) * adjoint, summed over slices
+        and contracted over the open labels (torch's convention).
+
+        ``adjoint``: array shaped like the output (FP64).  ``grads``: torch
+        tensors shaped like the leaves (device, leaf dtype), or None to
+        allocate.  Returns the list of gradient tensors (asynchronous)."""
+        import torch
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        cplx = self.dtype == TN_C64
+        adj = np.ascontiguousarray(np.asarray(adjoint, dtype=np.complex128 if cplx else np.float64))
+        if adj.size != int(np.prod(self.out_shape)):
+            raise ValueError("adjoint shape does not match the output")
+        if grads is None:
+            grads = [torch.empty_like(t, device="cuda") for t in self._keep]
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        tn_contract_grad(self.h, pairs, sliced, m, adj.view(np.float64), int(adj_exp2),
+                         [g.data_ptr() if g is not None else 0 for g in grads], s)
+        return grads
+
     def plan_info(self, pairs, sliced=(), mode="fp32"):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         return tn_plan_info(self.h, pairs, sliced, m)

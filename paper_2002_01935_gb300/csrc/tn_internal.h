@@ -66,6 +66,7 @@ struct GenericArgs {
     SliceDigits sla, slb;
     const Control* ctl;
     ScaleIO sc;
+    int conj_a, conj_b;  // read the operand complex-conjugated (reverse sweep)
 };
 
 // Tiled node (power-of-two label sizes): every index group is a set of bits.
@@ -100,6 +101,7 @@ struct alignas(16) TileArgs {
     ScaleIO sc;
     int a_leaf, b_leaf;   // leaf index of an operand (its pointer comes from the
                           // leaf pointer table in wave launches), else -1
+    int conj_a, conj_b;   // read the operand complex-conjugated (reverse sweep)
 };
 
 // One CTA of a wave launch: outputs [o_begin, o_begin + o_count) of node.
@@ -126,7 +128,24 @@ struct AccumArgs {
     Control* ctl;
 };
 
+// Reverse sweep: add a leaf's adjoint (times 2^exp) into the caller's
+// gradient buffer at the slice offset; labels absent from the adjoint
+// (summed in one tensor only) broadcast.  Digits fastest first.
+struct LeafGradArgs {
+    void* grad;
+    const void* adj;
+    const int64_t* exp_adj;
+    int64_t n;
+    int n_d;
+    int32_t dim[kMaxDigits];
+    int64_t gstride[kMaxDigits];
+    int64_t astride[kMaxDigits];
+    SliceDigits sl;
+    const Control* ctl;
+};
+
 // Launchers (tn_kernels.cu).  is_c: complex64 data.
+cudaError_t launch_leaf_grad(const LeafGradArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s);  // tn_tiled.cu
 // Tensor-core node (tn_tc.cu): prec 0 TF32, 1 TF32 hi+lo, 2 BF16 hi+lo.

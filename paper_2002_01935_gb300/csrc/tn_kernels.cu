@@ -79,6 +79,8 @@ __global__ void __launch_bounds__(256) k_generic(const GenericArgs a) {
             if (CPLX) {
                 float2 x = reinterpret_cast<const float2*>(a.A)[ia];
                 float2 y = reinterpret_cast<const float2*>(a.B)[ib];
+                if (a.conj_a) x.y = -x.y;
+                if (a.conj_b) y.y = -y.y;
                 re = fmaf(x.x, y.x, re);
                 re = fmaf(-x.y, y.y, re);
                 im = fmaf(x.x, y.y, im);
@@ -233,6 +235,46 @@ cudaError_t launch_leaf_max(const float* const* ptrs, const int64_t* nfloat, uns
                             cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_leaf_max<<<n, 256, 0, s>>>(ptrs, nfloat, out, n);
+    return cudaGetLastError();
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(256) k_leaf_grad(const __grid_constant__ LeafGradArgs a) {
+    const int64_t slice = a.ctl->slice;
+    const int64_t base = slice_offset(a.sl, slice);
+    int64_t e = *a.exp_adj;
+    const int ex = (int)(e < -400 ? -400 : (e > 400 ? 400 : e));
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < a.n; o += stride) {
+        int64_t g = base, s = 0, rem = o;
+        for (int i = 0; i < a.n_d; ++i) {
+            const int64_t d = a.dim[i];
+            const int64_t v = rem % d;
+            rem /= d;
+            g += v * a.gstride[i];
+            s += v * a.astride[i];
+        }
+        if (CPLX) {
+            const float2 x = reinterpret_cast<const float2*>(a.adj)[s];
+            float2* G = reinterpret_cast<float2*>(a.grad);
+            float2 y = G[g];
+            y.x += ldexpf(x.x, ex);
+            y.y += ldexpf(x.y, ex);
+            G[g] = y;
+        } else {
+            reinterpret_cast<float*>(a.grad)[g] += ldexpf(reinterpret_cast<const float*>(a.adj)[s], ex);
+        }
+    }
+}
+
+cudaError_t launch_leaf_grad(const LeafGradArgs& a, bool is_c, cudaStream_t s) {
+    int64_t blocks = (a.n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    if (is_c)
+        k_leaf_grad<true><<<(unsigned)blocks, 256, 0, s>>>(a);
+    else
+        k_leaf_grad<false><<<(unsigned)blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -220,6 +220,70 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems) 
 
 }  // namespace
 
+// A node contracting vertices a and b (tree ids, -1 = the unit scalar) into
+// the labels in keep: label groups and the [batch][M][N] output layout.
+// The larger operand takes the B role (its labels are the fastest).
+Node build_node(const NetDesc& d, const Plan& p, int id, int a, int b, const std::vector<int>& keep) {
+    auto log2size = [&](const std::vector<int>& lab) {
+        double s = 0;
+        for (int l : lab) s += std::log2((double)d.dims[l]);
+        return s;
+    };
+    // a, b: tree ids or -1 (unit scalar: no labels)
+    static const std::vector<int> none;
+    static const std::vector<int64_t> nones;
+    const std::vector<int>& la = a >= 0 ? p.vlab[a] : none;
+    const std::vector<int>& lb = b >= 0 ? p.vlab[b] : none;
+    const std::vector<int64_t>& sa = a >= 0 ? p.vstride[a] : nones;
+    const std::vector<int64_t>& sb = b >= 0 ? p.vstride[b] : nones;
+    int64_t size_a = 1, size_b = 1;
+    for (int l : la) size_a *= d.dims[l];
+    for (int l : lb) size_b *= d.dims[l];
+    // role: the larger operand takes the B (inner, fastest output) role
+    bool swap = size_a > size_b;
+    Node nd;
+    nd.id = id;
+    nd.ca = swap ? b : a;
+    nd.cb = swap ? a : b;
+    const std::vector<int>& A = swap ? lb : la;
+    const std::vector<int>& B = swap ? la : lb;
+    const std::vector<int64_t>& SA = swap ? sb : sa;
+    const std::vector<int64_t>& SB = swap ? sa : sb;
+    for (int l : A) {
+        bool inb = has(B, l), kept = has(keep, l);
+        if (inb && kept) nd.gb.push_back(l);
+        else if (inb) nd.gk.push_back(l);
+        else if (kept) nd.gm.push_back(l);
+        else nd.gsa.push_back(l);
+    }
+    for (int l : B) {
+        if (has(A, l)) continue;
+        if (has(keep, l)) nd.gn.push_back(l);
+        else nd.gsb.push_back(l);
+    }
+    auto by_desc = [&](const std::vector<int64_t>& S, const std::vector<int>& lab) {
+        return [&](int x, int y) { return stride_in(lab, S, x) > stride_in(lab, S, y); };
+    };
+    std::sort(nd.gb.begin(), nd.gb.end(), by_desc(SA, A));
+    std::sort(nd.gm.begin(), nd.gm.end(), by_desc(SA, A));
+    std::sort(nd.gn.begin(), nd.gn.end(), by_desc(SB, B));
+    std::sort(nd.gk.begin(), nd.gk.end(), by_desc(SB, B));
+    nd.lab = nd.gb;
+    nd.lab.insert(nd.lab.end(), nd.gm.begin(), nd.gm.end());
+    nd.lab.insert(nd.lab.end(), nd.gn.begin(), nd.gn.end());
+    nd.stride.assign(nd.lab.size(), 1);
+    nd.size = 1;
+    for (int i = (int)nd.lab.size() - 1; i >= 0; --i) {
+        nd.stride[i] = nd.size;
+        nd.size *= d.dims[nd.lab[i]];
+    }
+    std::vector<int> uni = A;
+    for (int l : B)
+        if (!has(uni, l)) uni.push_back(l);
+    nd.vc = log2size(uni);
+    return nd;
+}
+
 tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
     const int n = d.n;
     // diagnostics: TN_FORCE_GENERIC=1 runs every node on the generic kernel,
@@ -322,59 +386,7 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
     };
     for (int v = 0; v < n; ++v) W = std::max(W, log2size(p.vlab[v]));
     auto make_node = [&](int id, int a, int b, const std::vector<int>& keep) -> Node {
-        // a, b: tree ids or -1 (unit scalar: no labels)
-        static const std::vector<int> none;
-        static const std::vector<int64_t> nones;
-        const std::vector<int>& la = a >= 0 ? p.vlab[a] : none;
-        const std::vector<int>& lb = b >= 0 ? p.vlab[b] : none;
-        const std::vector<int64_t>& sa = a >= 0 ? p.vstride[a] : nones;
-        const std::vector<int64_t>& sb = b >= 0 ? p.vstride[b] : nones;
-        int64_t size_a = 1, size_b = 1;
-        for (int l : la) size_a *= d.dims[l];
-        for (int l : lb) size_b *= d.dims[l];
-        // role: the larger operand takes the B (inner, fastest output) role
-        bool swap = size_a > size_b;
-        Node nd;
-        nd.id = id;
-        nd.ca = swap ? b : a;
-        nd.cb = swap ? a : b;
-        const std::vector<int>& A = swap ? lb : la;
-        const std::vector<int>& B = swap ? la : lb;
-        const std::vector<int64_t>& SA = swap ? sb : sa;
-        const std::vector<int64_t>& SB = swap ? sa : sb;
-        for (int l : A) {
-            bool inb = has(B, l), kept = has(keep, l);
-            if (inb && kept) nd.gb.push_back(l);
-            else if (inb) nd.gk.push_back(l);
-            else if (kept) nd.gm.push_back(l);
-            else nd.gsa.push_back(l);
-        }
-        for (int l : B) {
-            if (has(A, l)) continue;
-            if (has(keep, l)) nd.gn.push_back(l);
-            else nd.gsb.push_back(l);
-        }
-        auto by_desc = [&](const std::vector<int64_t>& S, const std::vector<int>& lab) {
-            return [&](int x, int y) { return stride_in(lab, S, x) > stride_in(lab, S, y); };
-        };
-        std::sort(nd.gb.begin(), nd.gb.end(), by_desc(SA, A));
-        std::sort(nd.gm.begin(), nd.gm.end(), by_desc(SA, A));
-        std::sort(nd.gn.begin(), nd.gn.end(), by_desc(SB, B));
-        std::sort(nd.gk.begin(), nd.gk.end(), by_desc(SB, B));
-        nd.lab = nd.gb;
-        nd.lab.insert(nd.lab.end(), nd.gm.begin(), nd.gm.end());
-        nd.lab.insert(nd.lab.end(), nd.gn.begin(), nd.gn.end());
-        nd.stride.assign(nd.lab.size(), 1);
-        nd.size = 1;
-        for (int i = (int)nd.lab.size() - 1; i >= 0; --i) {
-            nd.stride[i] = nd.size;
-            nd.size *= d.dims[nd.lab[i]];
-        }
-        std::vector<int> uni = A;
-        for (int l : B)
-            if (!has(uni, l)) uni.push_back(l);
-        nd.vc = log2size(uni);
-        return nd;
+        return build_node(d, p, id, a, b, keep);
     };
     if (n == 1) {
         std::vector<int> keep = d.open;
@@ -815,10 +827,13 @@ tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count
     return TN_OK;
 }
 
-tn_status run_grad(NetDesc&, Plan&, void*, const double*, int64_t, void* const*, cudaStream_t,
-                   std::string& err) {
-    err = "tn_contract_grad: not available in this build";
-    return TN_EUNSUPPORTED;
+tn_status make_generic_args_node(const NetDesc& d, const Plan& p, const Node& nd, GenericArgs& g,
+                                 std::string& err) {
+    return fill_generic(d, p, nd, g, err);
+}
+
+bool plan_tile_node(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems) {
+    return plan_tile(d, p, nd, split_elems);
 }
 
 tn_status make_generic_args(const NetDesc& d, const Plan& p, int k, GenericArgs& g, std::string& err) {
@@ -839,6 +854,7 @@ void plan_info(const NetDesc& d, const Plan& p, double out[8]) {
 }
 
 void free_device(Plan& p) {
+    free_grad(p);
     if (p.gexec) cudaGraphExecDestroy(p.gexec);
     if (p.graph) cudaGraphDestroy(p.graph);
     for (auto ev : p.prof_placeholder) cudaEventDestroy(ev);

@@ -58,6 +58,8 @@ struct Step {
     std::vector<int> nodes;        // nodes run by this step
 };
 
+struct GradState;  // reverse-sweep plan and device state (tn_grad.cpp)
+
 struct Plan {
     tn_mode mode = TN_MODE_FP32;
     bool force_generic = false;  // every node on the generic kernel
@@ -86,6 +88,7 @@ struct Plan {
     int64_t* leaf_nfloat_dev = nullptr;
     std::vector<const void*> leaf_ptr_uploaded;
     std::vector<GenericArgs> gen;
+    GradState* grad = nullptr;
     std::vector<Step> steps;
     std::vector<WaveItem> items;
     WaveItem* items_dev = nullptr;
@@ -103,6 +106,10 @@ struct Plan {
 };
 
 tn_status build_plan(const NetDesc& d, Plan& p, std::string& err);
+Node build_node(const NetDesc& d, const Plan& p, int id, int a, int b, const std::vector<int>& keep);
+bool plan_tile_node(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems);
+tn_status make_generic_args_node(const NetDesc& d, const Plan& p, const Node& nd, GenericArgs& g,
+                                 std::string& err);
 tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err);
 tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count,
                    const tn_options& o, void* out, int out_mem, int64_t* out_exp2,
@@ -111,6 +118,7 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int64_t a
                    void* const* grads, cudaStream_t stream, std::string& err);
 void plan_info(const NetDesc& d, const Plan& p, double out[8]);
 void free_device(Plan& p);  // releases device state; the host plan stays valid
+void free_grad(Plan& p);
 // Generic-kernel arguments of node k (index digits, slice digits); pointers
 // and bookkeeping slots are left for the caller to fill.
 tn_status make_generic_args(const NetDesc& d, const Plan& p, int k, GenericArgs& g, std::string& err);

@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc(const __grid_constant__ Tile
                     if constexpr (CPLX) {
                         const float2 z = in ? reinterpret_cast<const float2*>(pa)[oa[i][v]] : make_float2(0.f, 0.f);
                         R.a[i][2 * v] = z.x;
-                        R.a[i][2 * v + 1] = z.y;
+                        R.a[i][2 * v + 1] = a.conj_a ? -z.y : z.y;
                     } else {
                         R.a[i][v] = in ? pa[oa[i][v]] : 0.f;
                     }
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc(const __grid_constant__ Tile
                     if constexpr (CPLX) {
                         const float2 z = in ? reinterpret_cast<const float2*>(pb)[ob[i][v]] : make_float2(0.f, 0.f);
                         R.b[i][2 * v] = z.x;
-                        R.b[i][2 * v + 1] = z.y;
+                        R.b[i][2 * v + 1] = a.conj_b ? -z.y : z.y;
                     } else {
                         R.b[i][v] = in ? pb[ob[i][v]] : 0.f;
                     }

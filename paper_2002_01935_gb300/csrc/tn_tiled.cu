@@ -62,6 +62,11 @@ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? 
 
 __device__ __forceinline__ float2 cmul(float2 x, float f) { return make_float2(x.x * f, x.y * f); }
 __device__ __forceinline__ float cmul(float x, float f) { return x * f; }
+// scaled load value, complex-conjugated when cj != 0 (a sign flip of Im)
+__device__ __forceinline__ float2 cmul(float2 x, float f, int cj) {
+    return make_float2(x.x * f, cj ? -x.y * f : x.y * f);
+}
+__device__ __forceinline__ float cmul(float x, float f, int) { return x * f; }
 __device__ __forceinline__ float absmax(float2 x) { return fmaxf(fabsf(x.x), fabsf(x.y)); }
 __device__ __forceinline__ float absmax(float x) { return fabsf(x); }
 __device__ __forceinline__ void fma_acc(float2& c, float2 a, float2 b) {
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
             const int i = a.a_mfast ? e % TM : e / TK;
             const int t = a.a_mfast ? e / TM : e % TK;
             const bool in = e < TM * TK && i < mlim && t < klim;
-            ra[q] = in ? cmul(A[baseA + rowA[i] + kaA + kA[t]], sc.fa) : zero<T>();
+            ra[q] = in ? cmul(A[baseA + rowA[i] + kaA + kA[t]], sc.fa, a.conj_a) : zero<T>();
         }
 #pragma unroll
         for (int q = 0; q < LB; ++q) {
@@ -188,7 +193,7 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
             const int j = a.b_nfast ? e % TN : e / TK;
             const int t = a.b_nfast ? e / TN : e % TK;
             const bool in = e < TN * TK && j < nlim && t < klim;
-            rb[q] = in ? cmul(B[baseB + colB[j] + kaB + kB[t]], sc.fb) : zero<T>();
+            rb[q] = in ? cmul(B[baseB + colB[j] + kaB + kB[t]], sc.fb, a.conj_b) : zero<T>();
         }
     };
     if (kbeg < kend) gload(kbeg);
@@ -323,13 +328,13 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a)
         const int64_t hA1 = scatter_bits(hi + 256, a.a_k, a.nk), hB1 = scatter_bits(hi + 256, a.b_k, a.nk);
         const T x0 = A[baseA + hA0 + loA], y0 = B[baseB + hB0 + loB];
         const T x1 = A[baseA + hA1 + loA], y1 = B[baseB + hB1 + loB];
-        fma_acc(acc0, cmul(x0, sc.fa), cmul(y0, sc.fb));
-        fma_acc(acc1, cmul(x1, sc.fa), cmul(y1, sc.fb));
+        fma_acc(acc0, cmul(x0, sc.fa, a.conj_a), cmul(y0, sc.fb, a.conj_b));
+        fma_acc(acc1, cmul(x1, sc.fa, a.conj_a), cmul(y1, sc.fb, a.conj_b));
     }
     for (; hi < ke; hi += 256) {
         if (hi + lo >= ke) break;
         const int64_t hA = scatter_bits(hi, a.a_k, a.nk), hB = scatter_bits(hi, a.b_k, a.nk);
-        fma_acc(acc0, cmul(A[baseA + hA + loA], sc.fa), cmul(B[baseB + hB + loB], sc.fb));
+        fma_acc(acc0, cmul(A[baseA + hA + loA], sc.fa, a.conj_a), cmul(B[baseB + hB + loB], sc.fb, a.conj_b));
     }
     // fixed-order block reduction
     __shared__ T red[256];
@@ -412,7 +417,7 @@ __global__ void __launch_bounds__(256)
                 ka = kA[t & 255] + (hi ? scatter_bits(hi, d.a_k, d.nk) : 0);
                 kb2 = kB[t & 255] + (hi ? scatter_bits(hi, d.b_k, d.nk) : 0);
             }
-            fma_acc(acc, cmul(A[offA + ka], sc.fa), cmul(B[offB + kb2], sc.fb));
+            fma_acc(acc, cmul(A[offA + ka], sc.fa, d.conj_a), cmul(B[offB + kb2], sc.fb, d.conj_b));
         }
         if (g > 1) {
             red[tid] = acc;

@@ -33,7 +33,7 @@ def run(torch, net, pairs, sliced=(), mode="fp32"):
     from paper_2002_01935_gb300 import binding
     cplx = net.is_complex
     dt = torch.complex64 if cplx else torch.float32
-    ts = [torch.from_numpy(np.ascontiguousarray(t)).to(dt).contiguous().cuda() for t in net.tensors]
+    ts = [torch.from_numpy(np.array(t, order="C")).to(dt).contiguous().cuda() for t in net.tensors]
     tnw = binding.TensorNetwork(net.labels, net.dims, net.open, ts, complex_=cplx)
     try:
         info = tnw.plan_info(pairs, sliced, mode)

@@ -33,7 +33,7 @@ def gpu_contract(torch, net, pairs, sliced=(), mode="fp32", host=False, **kw):
     from paper_2002_01935_gb300 import binding
     cplx = net.is_complex
     dt = torch.complex64 if cplx else torch.float32
-    ts = [torch.from_numpy(np.ascontiguousarray(t)).to(dt).contiguous() for t in net.tensors]
+    ts = [torch.from_numpy(np.array(t, order="C")).to(dt).contiguous() for t in net.tensors]
     if host:
         ts = [t.pin_memory() for t in ts]
     else:

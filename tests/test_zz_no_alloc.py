@@ -28,7 +28,7 @@ def env():
 
 def _leaves(torch, net):
     dt = torch.complex64 if net.is_complex else torch.float32
-    return [torch.from_numpy(np.ascontiguousarray(t)).to(dt).contiguous().cuda() for t in net.tensors]
+    return [torch.from_numpy(np.array(t, order="C")).to(dt).contiguous().cuda() for t in net.tensors]
 
 
 def test_noalloc_matches_tn_contract_on_two_calls(env):
