@@ -252,6 +252,33 @@ tn_status tn_plan_steps(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced
                         const int64_t *sliced_labels, tn_mode mode, int32_t cap, int32_t *n_steps,
                         int32_t *step_info, int32_t *step_nodes);
 
+/*
+ * Batches of independent networks.  Sec. 4.7.1 of the paper notes that
+ * independent contractions are embarrassingly parallel; a batch runs many
+ * scalar networks (each with its own tree, no slicing) as one captured
+ * launch sequence: per tree level, one launch covers the small nodes of
+ * every network in the batch.
+ *   tn_batch_create   n_nets handles and their trees (tree_pairs[i] as in
+ *                     tn_contract for nets[i]); the handles must outlive the
+ *                     batch and keep their leaves attached (device
+ *                     pointers); allocates the merged device state.
+ *   tn_batch_contract out: 2 doubles per network, the FP64 mantissa
+ *                     (complex (re, im); real networks (x, 0));
+ *                     out_exp2: one int64 per network (value = mantissa *
+ *                     2^exp2); latency_ns (may be NULL): per network, the
+ *                     time from the start of the batch until its root
+ *                     contraction completed (%globaltimer, nanoseconds).
+ *                     out_mem: TN_MEM_DEVICE or TN_MEM_HOST for all three.
+ *   Errors: TN_EINVAL, TN_EUNSUPPORTED (open labels, slicing, host leaves),
+ *   TN_ENOMEM, TN_ECUDA.
+ */
+typedef struct tn_batch tn_batch;
+tn_status tn_batch_create(tn_batch **out, int32_t n_nets, tn_net *const *nets,
+                          const int32_t *const *tree_pairs, tn_mode mode);
+tn_status tn_batch_contract(tn_batch *batch, double *out, int64_t *out_exp2, uint64_t *latency_ns,
+                            int32_t out_mem, void *stream);
+void tn_batch_destroy(tn_batch *batch);
+
 /* Release the handle, its plans and its device memory (synchronises the
  * device work the handle issued).  NULL is ignored. */
 void tn_destroy(tn_net *net);

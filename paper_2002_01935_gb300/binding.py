@@ -68,6 +68,13 @@ _lib.tn_plan_info.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int,
 _lib.tn_plan_steps.restype = ctypes.c_int
 _lib.tn_plan_steps.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int, ctypes.c_int32,
                                _i32p, _i32p, _i32p]
+_lib.tn_batch_create.restype = ctypes.c_int
+_lib.tn_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp),
+                                 ctypes.POINTER(_i32p), ctypes.c_int]
+_lib.tn_batch_contract.restype = ctypes.c_int
+_lib.tn_batch_contract.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, _vp]
+_lib.tn_batch_destroy.restype = None
+_lib.tn_batch_destroy.argtypes = [_vp]
 _lib.tn_destroy.restype = None
 _lib.tn_destroy.argtypes = [_vp]
 _lib.tn_last_error.restype = ctypes.c_char_p
@@ -76,8 +83,8 @@ _lib.tn_version.restype = ctypes.c_char_p
 _lib.tn_version.argtypes = []
 
 EXPORTS = ["tn_create", "tn_set_tensor", "tn_contract", "tn_contract_ex", "tn_contract_grad",
-           "tn_contract_noalloc", "tn_plan_info", "tn_plan_steps", "tn_destroy", "tn_last_error",
-           "tn_version"]
+           "tn_contract_noalloc", "tn_plan_info", "tn_plan_steps", "tn_batch_create",
+           "tn_batch_contract", "tn_batch_destroy", "tn_destroy", "tn_last_error", "tn_version"]
 
 
 class TNError(RuntimeError):
@@ -307,3 +314,43 @@ class TensorNetwork:
     def plan_steps(self, pairs, sliced=(), mode="fp32"):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         return tn_plan_steps(self.h, pairs, sliced, m)
+
+
+class Batch:
+    """Many scalar networks (TensorNetwork handles, each with its tree) run
+    as one captured launch sequence.  ``contract`` returns (mantissa, exp2,
+    latency_ns) device tensors: mantissa (n, 2) float64, exp2 (n,) int64,
+    per-network completion time since the batch started."""
+
+    def __init__(self, networks, trees, mode="fp32"):
+        import torch  # noqa: F401
+        self.nets = list(networks)
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        self._trees = [_tree(t) for t in trees]
+        hs = (_vp * len(self.nets))(*[n.h for n in self.nets])
+        tp = (_i32p * len(self.nets))(*[t.ctypes.data_as(_i32p) for t in self._trees])
+        h = _vp()
+        _check(_lib.tn_batch_create(ctypes.byref(h), len(self.nets), hs, tp, m))
+        self.h = h.value
+
+    def contract(self, stream=None):
+        import torch
+        n = len(self.nets)
+        out = torch.empty((n, 2), dtype=torch.float64, device="cuda")
+        ex = torch.empty(n, dtype=torch.int64, device="cuda")
+        lat = torch.empty(n, dtype=torch.int64, device="cuda")
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        _check(_lib.tn_batch_contract(self.h, out.data_ptr(), ex.data_ptr(), lat.data_ptr(),
+                                      TN_MEM_DEVICE, s))
+        return out, ex, lat
+
+    def close(self):
+        if self.h:
+            _lib.tn_batch_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

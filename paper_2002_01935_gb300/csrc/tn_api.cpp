@@ -25,6 +25,7 @@
 
 #include "../../include/tn.h"
 #include "tn_internal.h"
+#include "tn_batch.h"
 #include "tn_plan.h"
 
 namespace {
@@ -278,6 +279,53 @@ tn_status tn_plan_steps(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced
             for (int k : stp.nodes) step_nodes[pos++] = k;
     }
     return TN_OK;
+}
+
+struct tn_batch {
+    tn::BatchPlan b;
+};
+
+tn_status tn_batch_create(tn_batch** out, int32_t n_nets, tn_net* const* nets,
+                          const int32_t* const* tree_pairs, tn_mode mode) {
+    if (!out || n_nets < 1 || !nets || !tree_pairs) return fail(TN_EINVAL, "tn_batch_create: bad arguments");
+    *out = nullptr;
+    std::unique_ptr<tn_batch> b(new (std::nothrow) tn_batch);
+    if (!b) return fail(TN_ENOMEM, "out of host memory");
+    b->b.mode = mode;
+    for (int i = 0; i < n_nets; ++i) {
+        if (!nets[i]) return fail(TN_EINVAL, "tn_batch_create: NULL network");
+        Plan* p = nullptr;
+        tn_status st = get_plan(nets[i], tree_pairs[i], 0, nullptr, mode, &p);
+        if (st != TN_OK) return st;
+        b->b.nets.push_back(&nets[i]->d);
+        b->b.plans.push_back(p);
+    }
+    std::string err;
+    tn_status st = tn::build_batch(b->b, err);
+    if (st == TN_OK) st = tn::alloc_batch(b->b, err);
+    if (st != TN_OK) {
+        tn::free_batch(b->b);
+        return fail(st, err);
+    }
+    *out = b.release();
+    return TN_OK;
+}
+
+tn_status tn_batch_contract(tn_batch* batch, double* out, int64_t* out_exp2, uint64_t* latency_ns,
+                            int32_t out_mem, void* stream) {
+    if (!batch || !out || !out_exp2) return fail(TN_EINVAL, "tn_batch_contract: NULL argument");
+    if (out_mem != TN_MEM_DEVICE && out_mem != TN_MEM_HOST) return fail(TN_EINVAL, "bad out_mem");
+    std::string err;
+    tn_status st = tn::run_batch(batch->b, out, out_exp2, latency_ns, out_mem, (cudaStream_t)stream, err);
+    if (st != TN_OK) return fail(st, err);
+    return TN_OK;
+}
+
+void tn_batch_destroy(tn_batch* batch) {
+    if (!batch) return;
+    cudaDeviceSynchronize();
+    tn::free_batch(batch->b);
+    delete batch;
 }
 
 void tn_destroy(tn_net* net) {

@@ -67,6 +67,7 @@ struct GenericArgs {
     const Control* ctl;
     ScaleIO sc;
     int conj_a, conj_b;  // read the operand complex-conjugated (reverse sweep)
+    unsigned long long* t_done;  // root of a batched network: completion time (ns)
 };
 
 // Tiled node (power-of-two label sizes): every index group is a set of bits.
@@ -102,6 +103,8 @@ struct alignas(16) TileArgs {
     int a_leaf, b_leaf;   // leaf index of an operand (its pointer comes from the
                           // leaf pointer table in wave launches), else -1
     int conj_a, conj_b;   // read the operand complex-conjugated (reverse sweep)
+    unsigned long long* t_done;  // root of a batched network: completion time (ns)
+    int pad_;
 };
 
 // One CTA of a wave launch: outputs [o_begin, o_begin + o_count) of node.
@@ -144,7 +147,20 @@ struct LeafGradArgs {
     const Control* ctl;
 };
 
+// Batched networks: where each network's root lives and where its result goes.
+struct BatchRoot {
+    const void* root;           // scalar root value (float2 or float)
+    const int64_t* exp;         // root exponent slot
+    const unsigned* max;        // root max slot (0: the value is exactly zero)
+    int is_c;
+    int pad;
+};
+
 // Launchers (tn_kernels.cu).  is_c: complex64 data.
+cudaError_t launch_batch_start(unsigned long long* t_start, cudaStream_t s);
+cudaError_t launch_batch_finish(const BatchRoot* roots, int n, double* out, int64_t* out_exp,
+                                const unsigned long long* t_start, const unsigned long long* t_done,
+                                unsigned long long* latency, cudaStream_t s);
 cudaError_t launch_leaf_grad(const LeafGradArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s);  // tn_tiled.cu

@@ -27,6 +27,12 @@ __device__ __forceinline__ int exp_of_max(const unsigned* slot) {
     return e;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ int64_t slice_offset(const SliceDigits& d, int64_t slice) {
     int64_t off = 0;
     for (int i = 0; i < d.n; ++i) off += ((slice / d.div[i]) % d.dim[i]) * d.stride[i];
@@ -109,6 +115,7 @@ __global__ void __launch_bounds__(256) k_generic(const GenericArgs a) {
         }
     }
     block_max_to(lmax, a.sc.max_c);
+    if (a.t_done && threadIdx.x == 0) atomicMax(a.t_done, global_ns());
 }
 
 cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s) {
@@ -275,6 +282,40 @@ cudaError_t launch_leaf_grad(const LeafGradArgs& a, bool is_c, cudaStream_t s) {
         k_leaf_grad<true><<<(unsigned)blocks, 256, 0, s>>>(a);
     else
         k_leaf_grad<false><<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void k_batch_start(unsigned long long* t_start) { *t_start = global_ns(); }
+
+cudaError_t launch_batch_start(unsigned long long* t_start, cudaStream_t s) {
+    k_batch_start<<<1, 1, 0, s>>>(t_start);
+    return cudaGetLastError();
+}
+
+__global__ void k_batch_finish(const BatchRoot* roots, int n, double* out, int64_t* out_exp,
+                               const unsigned long long* t_start, const unsigned long long* t_done,
+                               unsigned long long* latency) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const BatchRoot r = roots[i];
+    const bool zero = !(__uint_as_float(*r.max) > 0.f);
+    if (r.is_c) {
+        const float2 v = *reinterpret_cast<const float2*>(r.root);
+        out[2 * i] = v.x;
+        out[2 * i + 1] = v.y;
+    } else {
+        out[2 * i] = *reinterpret_cast<const float*>(r.root);
+        out[2 * i + 1] = 0.0;
+    }
+    out_exp[i] = zero ? 0 : *r.exp;
+    if (latency) latency[i] = t_done[i] > *t_start ? t_done[i] - *t_start : 0;
+}
+
+cudaError_t launch_batch_finish(const BatchRoot* roots, int n, double* out, int64_t* out_exp,
+                                const unsigned long long* t_start, const unsigned long long* t_done,
+                                unsigned long long* latency, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_batch_finish<<<(n + 127) / 128, 128, 0, s>>>(roots, n, out, out_exp, t_start, t_done, latency);
     return cudaGetLastError();
 }
 

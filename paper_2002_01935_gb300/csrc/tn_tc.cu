@@ -543,6 +543,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc(const __grid_constant__ Tile
         if (!quiet && (tid & 31) == 0) atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN));
     }
+    if (a.t_done && tid == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        atomicMax(a.t_done, t);
+    }
 }
 
 template <bool CPLX, int PREC>

@@ -89,6 +89,12 @@ __device__ __forceinline__ float zero<float>() {
 __device__ __forceinline__ float2 add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float add(float a, float b) { return a + b; }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ void block_max(float v, unsigned* slot) {
     __shared__ float red[32];
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -261,7 +267,10 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
             out[rowoff + j] = v;
         }
     }
-    if (a.split == 1) block_max(lmax, a.sc.max_c);
+    if (a.split == 1) {
+        block_max(lmax, a.sc.max_c);
+        if (a.t_done && threadIdx.x == 0) atomicMax(a.t_done, global_ns());
+    }
 }
 
 // Fixed-order sum of the K-split partials, then the node epilogue.
@@ -298,6 +307,7 @@ __global__ void __launch_bounds__(256) k_split_reduce(const __grid_constant__ Ti
         C[o] = v;
     }
     block_max(lmax, a.sc.max_c);
+    if (a.t_done && threadIdx.x == 0) atomicMax(a.t_done, global_ns());
 }
 
 // Tiny output, long K: grid (outputs, batch, K splits); each CTA reduces its
@@ -362,6 +372,7 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a)
         reinterpret_cast<T*>(a.C)[o] = v;
         float mx = absmax(v);
         if (mx > 0.f) atomicMax(a.sc.max_c, __float_as_uint(mx));
+        if (a.t_done) atomicMax(a.t_done, global_ns());
     }
 }
 
@@ -442,6 +453,7 @@ __global__ void __launch_bounds__(256)
         C[o] = acc;
     }
     block_max(lmax, d.sc.max_c);
+    if (d.t_done && tid == 0) atomicMax(d.t_done, global_ns());
 }
 
 // --------------------------------------------------------------------------
