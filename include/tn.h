@@ -129,6 +129,12 @@ tn_status tn_set_tensor(tn_net *net, int32_t v, const void *ptr, int32_t mem);
  *       by tn_plan_steps) and prof_events[prof_count] just after step
  *       prof_first+prof_count-1, in every slice (the last slice's records
  *       win).  The events are caller-owned timing events.
+ *   slice_batch
+ *       slice-parallel execution: every node launch runs this many
+ *       consecutive slices side by side (each with its own workspace copy,
+ *       so memory grows by this factor); their results are folded into the
+ *       FP64 sum in slice order, so the result does not depend on it.
+ *       0 or 1: one slice per launch.
  */
 typedef struct {
     int64_t slice_begin;
@@ -138,7 +144,8 @@ typedef struct {
     void *const *prof_events; /* NULL, or prof_count+1 cudaEvent_t (as void*) */
     int32_t prof_first;
     int32_t prof_count;
-    int32_t reserved[6];
+    int32_t slice_batch;      /* slices run side by side per launch (>= 1) */
+    int32_t reserved[5];
 } tn_options;
 
 /*
@@ -225,6 +232,24 @@ tn_status tn_contract_grad(tn_net *net, const int32_t *tree_pairs, int32_t n_sli
 tn_status tn_contract_noalloc(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
                               const int64_t *sliced_labels, void *out, int32_t out_mem,
                               int64_t *out_exp2, void *stream);
+
+/*
+ * tn_contract_instances -- n_inst independent copies of one scalar network
+ * (same labels and tree, unsliced) in one launch sequence: e.g. many output
+ * bitstrings of one circuit (Eq. trans-amp), whose networks differ only in
+ * their output tensors.  Copy i reads leaf v at the pointer attached with
+ * tn_set_tensor plus i * leaf_inst_stride[v] elements (0: shared by all
+ * copies; NULL: all shared); leaves must be device pointers.
+ *   out        2 doubles per copy: FP64 mantissa (complex (re, im); real
+ *              (x, 0)); out_exp2: one int64 per copy; out_mem as
+ *              tn_contract.
+ * The device state grows to n_inst workspace copies.  Errors: TN_EINVAL,
+ * TN_EUNSUPPORTED (open labels, slicing, host leaves, stream capture),
+ * TN_ENOMEM, TN_ECUDA.
+ */
+tn_status tn_contract_instances(tn_net *net, const int32_t *tree_pairs, tn_mode mode, int32_t n_inst,
+                                const int64_t *leaf_inst_stride, double *out, int64_t *out_exp2,
+                                int32_t out_mem, void *stream);
 
 /*
  * tn_plan_info -- cost figures of a (tree, slicing) for this network, from

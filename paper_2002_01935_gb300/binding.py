@@ -37,7 +37,8 @@ class tn_options(ctypes.Structure):
     _fields_ = [("slice_begin", ctypes.c_int64), ("slice_count", ctypes.c_int64),
                 ("no_graph", ctypes.c_int32), ("tile_override", ctypes.c_int32),
                 ("prof_events", ctypes.POINTER(ctypes.c_void_p)), ("prof_first", ctypes.c_int32),
-                ("prof_count", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("prof_count", ctypes.c_int32), ("slice_batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -62,6 +63,9 @@ _lib.tn_contract_grad.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_in
 _lib.tn_contract_noalloc.restype = ctypes.c_int
 _lib.tn_contract_noalloc.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, _vp, ctypes.c_int32, _i64p,
                                      _vp]
+_lib.tn_contract_instances.restype = ctypes.c_int
+_lib.tn_contract_instances.argtypes = [_vp, _i32p, ctypes.c_int, ctypes.c_int32, _i64p, _vp, _vp,
+                                       ctypes.c_int32, _vp]
 _lib.tn_plan_info.restype = ctypes.c_int
 _lib.tn_plan_info.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int,
                               ctypes.POINTER(ctypes.c_double)]
@@ -83,7 +87,7 @@ _lib.tn_version.restype = ctypes.c_char_p
 _lib.tn_version.argtypes = []
 
 EXPORTS = ["tn_create", "tn_set_tensor", "tn_contract", "tn_contract_ex", "tn_contract_grad",
-           "tn_contract_noalloc", "tn_plan_info", "tn_plan_steps", "tn_batch_create",
+           "tn_contract_noalloc", "tn_contract_instances", "tn_plan_info", "tn_plan_steps", "tn_batch_create",
            "tn_batch_contract", "tn_batch_destroy", "tn_destroy", "tn_last_error", "tn_version"]
 
 
@@ -140,10 +144,12 @@ def _tree(pairs):
 def tn_contract_ex(h: int, pairs, sliced, mode: int, out_ptr: int, out_mem: int, exp_ptr: int,
                    stream: int = 0, slice_begin: int = 0, slice_count: int = 0,
                    no_graph: bool = False, tile_override: int = 0,
-                   prof_events: Optional[Sequence[int]] = None, prof_first: int = 0) -> None:
+                   prof_events: Optional[Sequence[int]] = None, prof_first: int = 0,
+                   slice_batch: int = 0) -> None:
     tr = _tree(pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     opt = tn_options(slice_begin, slice_count, int(no_graph), tile_override)
+    opt.slice_batch = slice_batch
     if prof_events:
         evs = (ctypes.c_void_p * len(prof_events))(*prof_events)
         opt.prof_events = ctypes.cast(evs, ctypes.POINTER(ctypes.c_void_p))
@@ -267,7 +273,7 @@ class TensorNetwork:
 
     def contract(self, pairs, sliced=(), mode="fp32", out=None, out_exp=None, stream=None,
                  slice_begin=0, slice_count=0, no_graph=False, tile_override=0,
-                 prof_events=None, prof_first=0):
+                 prof_events=None, prof_first=0, slice_batch=0):
         """Return (mantissa, exp2) torch tensors; value = mantissa * 2**exp2.
 
         Device outputs by default (asynchronous on ``stream``); pass CPU
@@ -284,7 +290,8 @@ class TensorNetwork:
         s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
         evp = [e.cuda_event for e in prof_events] if prof_events else None
         tn_contract_ex(self.h, pairs, sliced, m, out.data_ptr(), mem, out_exp.data_ptr(), s,
-                       slice_begin, slice_count, no_graph, tile_override, evp, prof_first)
+                       slice_begin, slice_count, no_graph, tile_override, evp, prof_first,
+                       slice_batch)
         return out, out_exp
 
     def grad(self, pairs, sliced, mode, adjoint, adj_exp2=0, grads=None, stream=None):
@@ -310,6 +317,24 @@ class TensorNetwork:
     def plan_info(self, pairs, sliced=(), mode="fp32"):
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         return tn_plan_info(self.h, pairs, sliced, m)
+
+    def contract_instances(self, pairs, mode, n_inst, leaf_inst_stride=None, stream=None):
+        """n_inst copies of this scalar network in one launch sequence; copy i
+        reads leaf v at (attached pointer) + i * leaf_inst_stride[v] elements.
+        Returns device tensors (mantissa (n_inst, 2) float64, exp2 (n_inst,))."""
+        import torch
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        out = torch.empty((n_inst, 2), dtype=torch.float64, device="cuda")
+        ex = torch.empty(n_inst, dtype=torch.int64, device="cuda")
+        strides = None
+        if leaf_inst_stride is not None:
+            self._strides = _arr(list(leaf_inst_stride), np.int64)
+            strides = _p(self._strides, ctypes.c_int64)
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        tr = _tree(pairs)
+        _check(_lib.tn_contract_instances(self.h, _p(tr, ctypes.c_int32), m, n_inst, strides,
+                                          out.data_ptr(), ex.data_ptr(), TN_MEM_DEVICE, s))
+        return out, ex
 
     def plan_steps(self, pairs, sliced=(), mode="fp32"):
         m = MODES[mode] if isinstance(mode, str) else int(mode)

@@ -177,6 +177,20 @@ static tn_status ensure_device(tn_net* net, Plan* p) {
     return TN_OK;
 }
 
+// Device state for at least G instances (reallocated outside capture).
+static tn_status ensure_instances(tn_net* net, Plan* p, int G, cudaStream_t stream) {
+    if (p->ws && p->alloc_inst >= G) return TN_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(TN_EUNSUPPORTED, "a plan's first call with more instances must run outside capture");
+    if (p->ws) {
+        cudaDeviceSynchronize();
+        tn::free_device(*p);
+    }
+    p->alloc_inst = std::max(G, p->alloc_inst);
+    return ensure_device(net, p);
+}
+
 tn_status tn_contract_ex(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
                          const int64_t* sliced_labels, tn_mode mode, const tn_options* opt, void* out,
                          int32_t out_mem, int64_t* out_exp2, void* stream) {
@@ -188,8 +202,6 @@ tn_status tn_contract_ex(tn_net* net, const int32_t* tree_pairs, int32_t n_slice
     Plan* p = nullptr;
     tn_status st = get_plan(net, tree_pairs, n_sliced, sliced_labels, mode, &p);
     if (st != TN_OK) return st;
-    st = ensure_device(net, p);
-    if (st != TN_OK) return st;
     tn_options o{};
     if (opt) o = *opt;
     int64_t begin = o.slice_begin, count = o.slice_count;
@@ -198,9 +210,38 @@ tn_status tn_contract_ex(tn_net* net, const int32_t* tree_pairs, int32_t n_slice
         count = p->d_sliced;
     }
     if (begin < 0 || begin + count > p->d_sliced) return fail(TN_EINVAL, "slice range out of bounds");
+    if (o.slice_batch < 0) return fail(TN_EINVAL, "negative slice_batch");
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(o.slice_batch, count));
+    st = ensure_instances(net, p, G, (cudaStream_t)stream);
+    if (st != TN_OK) return st;
     std::string err;
     st = tn::run_plan(net->d, *p, net->unit, begin, count, o, out, out_mem, out_exp2,
                       (cudaStream_t)stream, err);
+    if (st != TN_OK) return fail(st, err);
+    return TN_OK;
+}
+
+tn_status tn_contract_instances(tn_net* net, const int32_t* tree_pairs, tn_mode mode, int32_t n_inst,
+                                const int64_t* leaf_inst_stride, double* out, int64_t* out_exp2,
+                                int32_t out_mem, void* stream) {
+    if (!net) return fail(TN_EINVAL, "tn_contract_instances: net is NULL");
+    if (!out || !out_exp2 || n_inst < 1) return fail(TN_EINVAL, "tn_contract_instances: bad arguments");
+    if (out_mem != TN_MEM_DEVICE && out_mem != TN_MEM_HOST) return fail(TN_EINVAL, "bad out_mem");
+    for (int v = 0; v < net->d.n; ++v) {
+        if (!net->d.leaves[v].ptr) return fail(TN_EINVAL, "tn_contract_instances: tensor without data");
+        if (net->d.leaves[v].mem != TN_MEM_DEVICE)
+            return fail(TN_EUNSUPPORTED, "tn_contract_instances: leaves must be device pointers");
+        if (leaf_inst_stride && leaf_inst_stride[v] < 0)
+            return fail(TN_EINVAL, "tn_contract_instances: negative stride");
+    }
+    Plan* p = nullptr;
+    tn_status st = get_plan(net, tree_pairs, 0, nullptr, mode, &p);
+    if (st != TN_OK) return st;
+    st = ensure_instances(net, p, n_inst, (cudaStream_t)stream);
+    if (st != TN_OK) return st;
+    std::string err;
+    st = tn::run_instances(net->d, *p, net->unit, n_inst, leaf_inst_stride, out, out_exp2, out_mem,
+                           (cudaStream_t)stream, err);
     if (st != TN_OK) return fail(st, err);
     return TN_OK;
 }

@@ -184,6 +184,7 @@ tn_status alloc_batch(BatchPlan& b, std::string& err) {
             g.t_done = root ? b.t_done + i : nullptr;
             TileArgs& t = b.descs[di];
             t = nd.tile;
+            memset(&t.in, 0, sizeof(t.in));  // single instance
             t.A = g.A;
             t.B = g.B;
             t.C = g.C;
@@ -232,7 +233,7 @@ static cudaError_t enqueue_batch(BatchPlan& b, cudaStream_t s) {
     if ((e = launch_batch_start(b.t_start, s)) != cudaSuccess) return e;
     if ((e = launch_leaf_max(b.leaf_ptr_dev, b.leaf_nfloat_dev, b.leafmax, b.n_leaves, s)) != cudaSuccess)
         return e;
-    if ((e = launch_begin_call(b.ctl, 0, nullptr, 0, s)) != cudaSuccess) return e;
+    if ((e = launch_begin_call(b.ctl, 0, 1, nullptr, 0, s)) != cudaSuccess) return e;
     for (const BatchStep& st : b.steps) {
         if (st.wave) {
             e = launch_wave(b.items_dev + st.item_begin, st.item_count, b.descs_dev,

@@ -199,6 +199,7 @@ static tn_status alloc_grad(const NetDesc& d, GradState& G, void* unit, std::str
         g.conj_a = nd.tile.conj_a;
         g.conj_b = nd.tile.conj_b;
         t = nd.tile;
+        memset(&t.in, 0, sizeof(t.in));  // single instance
         t.A = A;
         t.B = B;
         t.C = C;
@@ -348,7 +349,7 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int64_t a
     // zero the outputs, then every slice: forward, reverse sweep, leaf gather
     for (int v = 0; v < n; ++v)
         if (grads[v]) CK(cudaMemsetAsync(grads[v], 0, d.leaves[v].size * eb, stream));
-    CK(launch_begin_call(G.ctl, 0, nullptr, 0, stream));
+    CK(launch_begin_call(G.ctl, 0, p.d_sliced, nullptr, 0, stream));
     std::vector<LeafGradArgs> lg(n);
     for (int v = 0; v < n; ++v) {
         LeafGradArgs& a = lg[v];

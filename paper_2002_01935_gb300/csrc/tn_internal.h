@@ -23,6 +23,19 @@ struct Control {
     int64_t final_exp;    // exponent of the result after the last slice
     int32_t status;       // 0 ok; TN_ETIMEOUT etc. set by device code
     int32_t pad;
+    int64_t slice_end;    // instances whose slice id reaches this are idle
+};
+
+// Instances: one launch runs n_inst copies of a node.  Instance i reads
+// A + i*a_is, B + i*b_is, writes C + i*c_is (elements), uses the
+// renormalisation slots offset by i*s?_is, and works on slice
+// ctl->slice + i*slice_step (instances beyond ctl->slice_end are idle).
+struct InstanceInfo {
+    int32_t n_inst;
+    int32_t slice_step;
+    int64_t a_is, b_is, c_is, p_is;
+    int32_t sa_is, sb_is, sc_is;
+    int32_t pad;
 };
 
 // Offset of a sliced leaf: sum over its sliced labels of
@@ -68,6 +81,7 @@ struct GenericArgs {
     ScaleIO sc;
     int conj_a, conj_b;  // read the operand complex-conjugated (reverse sweep)
     unsigned long long* t_done;  // root of a batched network: completion time (ns)
+    InstanceInfo in;
 };
 
 // Tiled node (power-of-two label sizes): every index group is a set of bits.
@@ -105,6 +119,7 @@ struct alignas(16) TileArgs {
     int conj_a, conj_b;   // read the operand complex-conjugated (reverse sweep)
     unsigned long long* t_done;  // root of a batched network: completion time (ns)
     int pad_;
+    InstanceInfo in;
 };
 
 // One CTA of a wave launch: outputs [o_begin, o_begin + o_count) of node.
@@ -120,6 +135,11 @@ struct WaveItem {
 // alignment.  od_*: digits of the output in the user's open-label order,
 // fastest first, with strides into the root tensor.
 struct AccumArgs {
+    int32_t n_inst;       // roots folded per launch (slice-parallel), in order
+    int32_t pad;
+    int64_t r_is;         // element stride between the instances' roots
+    int32_t s_is;         // slot stride between the instances
+    int32_t pad2;
     const void* R;
     int64_t n_out;
     int n_od;
@@ -170,10 +190,10 @@ cudaError_t launch_tc(const TileArgs& a, int prec, bool is_c, cudaStream_t s);
 cudaError_t launch_wave(const WaveItem* items, int n_items, const TileArgs* descs,
                         const void* const* leaf_ptrs, bool is_c, cudaStream_t s);
 cudaError_t launch_accumulate(const AccumArgs& a, bool is_c, cudaStream_t s);
-cudaError_t launch_begin_call(Control* ctl, int64_t slice_begin, double* acc, int64_t n_acc_doubles,
-                              cudaStream_t s);
+cudaError_t launch_begin_call(Control* ctl, int64_t slice_begin, int64_t slice_end, double* acc,
+                              int64_t n_acc_doubles, cudaStream_t s);
 cudaError_t launch_begin_slice(unsigned* maxabs, int n_nodes, cudaStream_t s);
-cudaError_t launch_advance(Control* ctl, cudaStream_t s);
+cudaError_t launch_advance(Control* ctl, cudaStream_t s, int step = 1);
 cudaError_t launch_finalize(Control* ctl, int parity, cudaStream_t s);
 cudaError_t launch_leaf_max(const float* const* ptrs, const int64_t* nfloat, unsigned* out, int n,
                             cudaStream_t s);

@@ -56,15 +56,30 @@ __device__ __forceinline__ void block_max_to(float v, unsigned* slot) {
 }
 
 template <bool CPLX>
-__global__ void __launch_bounds__(256) k_generic(const GenericArgs a) {
-    const int eA = exp_of_max(a.sc.max_a);
-    const int eB = exp_of_max(a.sc.max_b);
+__global__ void __launch_bounds__(256) k_generic(const __grid_constant__ GenericArgs a) {
+    // instance blockIdx.y: offset pointers, scale slots and slice id
+    const int inst = blockIdx.y;
+    const InstanceInfo& in = a.in;
+    const int64_t slice = a.ctl->slice + (int64_t)inst * in.slice_step;
+    if (slice >= a.ctl->slice_end) return;
+    const int esz = CPLX ? 8 : 4;
+    const void* Ap = (const char*)a.A + (int64_t)inst * in.a_is * esz;
+    const void* Bp = (const char*)a.B + (int64_t)inst * in.b_is * esz;
+    void* Cp = (char*)a.C + (int64_t)inst * in.c_is * esz;
+    ScaleIO sc = a.sc;
+    if (sc.max_a) sc.max_a += (int64_t)inst * in.sa_is;
+    if (sc.exp_a) sc.exp_a += (int64_t)inst * in.sa_is;
+    if (sc.max_b) sc.max_b += (int64_t)inst * in.sb_is;
+    if (sc.exp_b) sc.exp_b += (int64_t)inst * in.sb_is;
+    sc.max_c += (int64_t)inst * in.sc_is;
+    sc.exp_c += (int64_t)inst * in.sc_is;
+    const int eA = exp_of_max(sc.max_a);
+    const int eB = exp_of_max(sc.max_b);
     const int esum = eA + eB;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        int64_t s = (a.sc.exp_a ? *a.sc.exp_a : 0) + (a.sc.exp_b ? *a.sc.exp_b : 0) + esum;
-        *a.sc.exp_c = s;
+        int64_t s = (sc.exp_a ? *sc.exp_a : 0) + (sc.exp_b ? *sc.exp_b : 0) + esum;
+        *sc.exp_c = s;
     }
-    const int64_t slice = a.ctl->slice;
     const int64_t baseA = slice_offset(a.sla, slice);
     const int64_t baseB = slice_offset(a.slb, slice);
     float lmax = 0.f;
@@ -83,8 +98,8 @@ __global__ void __launch_bounds__(256) k_generic(const GenericArgs a) {
         float re = 0.f, im = 0.f;
         for (int64_t k = 0; k < a.n_sum; ++k) {
             if (CPLX) {
-                float2 x = reinterpret_cast<const float2*>(a.A)[ia];
-                float2 y = reinterpret_cast<const float2*>(a.B)[ib];
+                float2 x = reinterpret_cast<const float2*>(Ap)[ia];
+                float2 y = reinterpret_cast<const float2*>(Bp)[ib];
                 if (a.conj_a) x.y = -x.y;
                 if (a.conj_b) y.y = -y.y;
                 re = fmaf(x.x, y.x, re);
@@ -92,8 +107,8 @@ __global__ void __launch_bounds__(256) k_generic(const GenericArgs a) {
                 im = fmaf(x.x, y.y, im);
                 im = fmaf(x.y, y.x, im);
             } else {
-                re = fmaf(reinterpret_cast<const float*>(a.A)[ia],
-                          reinterpret_cast<const float*>(a.B)[ib], re);
+                re = fmaf(reinterpret_cast<const float*>(Ap)[ia],
+                          reinterpret_cast<const float*>(Bp)[ib], re);
             }
             for (int i = 0; i < a.n_kd; ++i) {
                 ia += a.kd_sa[i];
@@ -107,14 +122,14 @@ __global__ void __launch_bounds__(256) k_generic(const GenericArgs a) {
         re = ldexpf(re, -esum);
         if (CPLX) {
             im = ldexpf(im, -esum);
-            reinterpret_cast<float2*>(a.C)[o] = make_float2(re, im);
+            reinterpret_cast<float2*>(Cp)[o] = make_float2(re, im);
             lmax = fmaxf(lmax, fmaxf(fabsf(re), fabsf(im)));
         } else {
-            reinterpret_cast<float*>(a.C)[o] = re;
+            reinterpret_cast<float*>(Cp)[o] = re;
             lmax = fmaxf(lmax, fabsf(re));
         }
     }
-    block_max_to(lmax, a.sc.max_c);
+    block_max_to(lmax, sc.max_c);
     if (a.t_done && threadIdx.x == 0) atomicMax(a.t_done, global_ns());
 }
 
@@ -122,10 +137,11 @@ cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s) {
     int64_t blocks = (a.n_out + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
+    const unsigned ni = a.in.n_inst > 1 ? (unsigned)a.in.n_inst : 1u;
     if (is_c)
-        k_generic<true><<<(unsigned)blocks, 256, 0, s>>>(a);
+        k_generic<true><<<dim3((unsigned)blocks, ni), 256, 0, s>>>(a);
     else
-        k_generic<false><<<(unsigned)blocks, 256, 0, s>>>(a);
+        k_generic<false><<<dim3((unsigned)blocks, ni), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -134,21 +150,28 @@ cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s) {
 // --------------------------------------------------------------------------
 
 template <bool CPLX>
-__global__ void __launch_bounds__(256) k_accumulate(const AccumArgs a) {
-    const int64_t step = a.ctl->slice - a.ctl->slice_begin;
+__global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ AccumArgs a) {
+    // the n_inst roots of this launch are slices ctl->slice + i (i in order);
+    // fold them with one common exponent, skipping zero and idle slices
+    const int ni = a.n_inst > 1 ? a.n_inst : 1;
+    const int64_t step = (a.ctl->slice - a.ctl->slice_begin) / ni;
     const int par = (int)(step & 1);
     const int64_t accE = a.ctl->acc_exp[par];
-    const float rmax = __uint_as_float(*a.max_r);
-    const int64_t S = *a.exp_r;
     const bool empty = accE == INT64_MIN;
-    const bool zero = !(rmax > 0.f);
-    int64_t newE = zero ? accE : (empty ? S : (S > accE ? S : accE));
-    double fa = 1.0, fr = 0.0;
-    if (!zero) {
-        int64_t da = empty ? 0 : accE - newE;
-        int64_t dr = S - newE;
+    int64_t newE = accE;
+    bool any = false;
+    for (int i = 0; i < ni; ++i) {
+        if (a.ctl->slice + i >= a.ctl->slice_end) break;
+        const float rmax = __uint_as_float(a.max_r[(int64_t)i * a.s_is]);
+        if (!(rmax > 0.f)) continue;
+        const int64_t S = a.exp_r[(int64_t)i * a.s_is];
+        newE = (empty && !any) ? S : (S > newE ? S : newE);
+        any = true;
+    }
+    double fa = 1.0;
+    if (any && !empty) {
+        const int64_t da = accE - newE;
         fa = ldexp(1.0, (int)(da < -2000 ? -2000 : da));
-        fr = ldexp(1.0, (int)(dr < -2000 ? -2000 : dr));
     }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
@@ -158,17 +181,34 @@ __global__ void __launch_bounds__(256) k_accumulate(const AccumArgs a) {
             src += (rem % d) * a.od_s[i];
             rem /= d;
         }
+        if (!any) continue;
+        double vr = 0.0, vi = 0.0;
         if (CPLX) {
-            float2 r = reinterpret_cast<const float2*>(a.R)[src];
-            double2* acc = reinterpret_cast<double2*>(a.acc);
-            double2 v = acc[o];
-            v.x = v.x * fa + (double)r.x * fr;
-            v.y = v.y * fa + (double)r.y * fr;
-            acc[o] = v;
+            const double2 v = reinterpret_cast<double2*>(a.acc)[o];
+            vr = v.x * fa;
+            vi = v.y * fa;
         } else {
-            float r = reinterpret_cast<const float*>(a.R)[src];
-            a.acc[o] = a.acc[o] * fa + (double)r * fr;
+            vr = a.acc[o] * fa;
         }
+        for (int i = 0; i < ni; ++i) {
+            if (a.ctl->slice + i >= a.ctl->slice_end) break;
+            const float rmax = __uint_as_float(a.max_r[(int64_t)i * a.s_is]);
+            if (!(rmax > 0.f)) continue;
+            const int64_t dr = a.exp_r[(int64_t)i * a.s_is] - newE;
+            const double fr = ldexp(1.0, (int)(dr < -2000 ? -2000 : dr));
+            const int64_t at = src + (int64_t)i * a.r_is;
+            if (CPLX) {
+                const float2 r = reinterpret_cast<const float2*>(a.R)[at];
+                vr += (double)r.x * fr;
+                vi += (double)r.y * fr;
+            } else {
+                vr += (double)reinterpret_cast<const float*>(a.R)[at] * fr;
+            }
+        }
+        if (CPLX)
+            reinterpret_cast<double2*>(a.acc)[o] = make_double2(vr, vi);
+        else
+            a.acc[o] = vr;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->acc_exp[par ^ 1] = newE;
 }
@@ -184,11 +224,13 @@ cudaError_t launch_accumulate(const AccumArgs& a, bool is_c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-__global__ void k_begin_call(Control* ctl, int64_t slice_begin, double* acc, int64_t n) {
+__global__ void k_begin_call(Control* ctl, int64_t slice_begin, int64_t slice_end, double* acc,
+                             int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         ctl->slice = slice_begin;
         ctl->slice_begin = slice_begin;
+        ctl->slice_end = slice_end;
         ctl->acc_exp[0] = INT64_MIN;
         ctl->acc_exp[1] = INT64_MIN;
         ctl->status = 0;
@@ -196,12 +238,12 @@ __global__ void k_begin_call(Control* ctl, int64_t slice_begin, double* acc, int
     for (; i < n; i += (int64_t)gridDim.x * blockDim.x) acc[i] = 0.0;
 }
 
-cudaError_t launch_begin_call(Control* ctl, int64_t slice_begin, double* acc, int64_t n,
-                              cudaStream_t s) {
+cudaError_t launch_begin_call(Control* ctl, int64_t slice_begin, int64_t slice_end, double* acc,
+                              int64_t n, cudaStream_t s) {
     int64_t blocks = (n + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     if (blocks < 1) blocks = 1;
-    k_begin_call<<<(unsigned)blocks, 256, 0, s>>>(ctl, slice_begin, acc, n);
+    k_begin_call<<<(unsigned)blocks, 256, 0, s>>>(ctl, slice_begin, slice_end, acc, n);
     return cudaGetLastError();
 }
 
@@ -209,10 +251,10 @@ cudaError_t launch_begin_slice(unsigned* maxabs, int n_nodes, cudaStream_t s) {
     return cudaMemsetAsync(maxabs, 0, sizeof(unsigned) * (size_t)n_nodes, s);
 }
 
-__global__ void k_advance(Control* ctl) { ctl->slice += 1; }
+__global__ void k_advance(Control* ctl, int step) { ctl->slice += step; }
 
-cudaError_t launch_advance(Control* ctl, cudaStream_t s) {
-    k_advance<<<1, 1, 0, s>>>(ctl);
+cudaError_t launch_advance(Control* ctl, cudaStream_t s, int step) {
+    k_advance<<<1, 1, 0, s>>>(ctl, step);
     return cudaGetLastError();
 }
 

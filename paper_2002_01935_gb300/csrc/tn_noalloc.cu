@@ -191,7 +191,7 @@ tn_status run_noalloc(const NetDesc& d, const Plan& p, void* out, int out_mem, i
     // the call: leaf maxima, control block and accumulator cleared, then
     // every slice in order, then the result
     CK(launch_leaf_max(lptr, lnf, leafmax, n, stream));
-    CK(launch_begin_call(ctl, 0, acc, (int64_t)acc_doubles, stream));
+    CK(launch_begin_call(ctl, 0, p.d_sliced, acc, (int64_t)acc_doubles, stream));
     for (int64_t s = 0; s < p.d_sliced; ++s) {
         CK(launch_begin_slice(maxabs, nn, stream));
         // the workspace offsets assume the plan's step order

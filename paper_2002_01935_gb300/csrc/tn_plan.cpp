@@ -574,9 +574,13 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
         }
         return true;
     };
-    if (!ck(cudaMalloc(&p.ws, (size_t)p.ws_elems * eb), "workspace allocation")) return TN_ENOMEM;
-    if (!ck(cudaMalloc(&p.maxabs, sizeof(unsigned) * nn), "cudaMalloc")) return TN_ENOMEM;
-    if (!ck(cudaMalloc(&p.exps, sizeof(int64_t) * nn), "cudaMalloc")) return TN_ENOMEM;
+    const int G = std::max(p.alloc_inst, 1);
+    if (!ck(cudaMalloc(&p.ws, (size_t)p.ws_elems * eb * G), "workspace allocation")) return TN_ENOMEM;
+    if (!ck(cudaMalloc(&p.maxabs, sizeof(unsigned) * nn * G), "cudaMalloc")) return TN_ENOMEM;
+    if (!ck(cudaMalloc(&p.exps, sizeof(int64_t) * nn * G), "cudaMalloc")) return TN_ENOMEM;
+    if (!ck(cudaMalloc(&p.inst_roots_dev, sizeof(BatchRoot) * G), "cudaMalloc")) return TN_ENOMEM;
+    if (!ck(cudaMalloc(&p.inst_out_dev, sizeof(double) * 2 * G), "cudaMalloc")) return TN_ENOMEM;
+    if (!ck(cudaMalloc(&p.inst_exp_dev, sizeof(int64_t) * G), "cudaMalloc")) return TN_ENOMEM;
     if (!ck(cudaMalloc(&p.ctl, sizeof(Control)), "cudaMalloc")) return TN_ENOMEM;
     size_t acc_doubles = (size_t)p.n_out * (d.is_complex() ? 2 : 1);
     if (!ck(cudaMalloc(&p.acc, sizeof(double) * acc_doubles), "cudaMalloc")) return TN_ENOMEM;
@@ -590,8 +594,9 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
         if (!ck(cudaMemcpy(p.leaf_nfloat_dev, nf.data(), sizeof(int64_t) * d.n,
                            cudaMemcpyHostToDevice), "cudaMemcpy"))
             return TN_ECUDA;
+        p.leaf_nfloat_uploaded = nf;
     }
-    if (p.split_bytes > 0 && !ck(cudaMalloc(&p.split_buf, p.split_bytes), "split-K buffer"))
+    if (p.split_bytes > 0 && !ck(cudaMalloc(&p.split_buf, p.split_bytes * G), "split-K buffer"))
         return TN_ENOMEM;
     // node launch arguments; leaf pointers are patched per call
     p.gen.resize(nn);
@@ -632,7 +637,7 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
         std::vector<TileArgs> descs(nn);
         for (int k = 0; k < nn; ++k) descs[k] = p.nodes[k].tile;
         if (!ck(cudaMalloc(&p.descs_dev, sizeof(TileArgs) * nn), "cudaMalloc")) return TN_ENOMEM;
-        if (!ck(cudaMalloc(&p.items_dev, sizeof(WaveItem) * p.items.size()), "cudaMalloc"))
+        if (!ck(cudaMalloc(&p.items_dev, sizeof(WaveItem) * p.items.size() * G), "cudaMalloc"))
             return TN_ENOMEM;
         if (!ck(cudaMemcpy(p.descs_dev, descs.data(), sizeof(TileArgs) * nn, cudaMemcpyHostToDevice),
                 "cudaMemcpy"))
@@ -662,15 +667,87 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
     a.exp_r = p.exps + (nn - 1);
     a.acc = p.acc;
     a.ctl = p.ctl;
+    a.n_inst = 1;
+    a.r_is = p.ws_elems;
+    a.s_is = nn;
+    p.cfg_inst = -1;  // instance layout not yet written to the arguments
     return TN_OK;
 }
 
-// One slice: reset the node maxima, run every node, fold the root into the
-// FP64 accumulator, advance the slice counter.  ev: optional timing events
-// around nodes [pf, pf + pc).
+// Write the instance layout (G instances; step 1: instance i = slice s+i,
+// step 0: independent copies whose leaf v sits leaf_is[v] elements apart)
+// into every node's launch arguments, the wave items and the accumulator.
+static tn_status configure_instances(const NetDesc& d, Plan& p, int G, int step,
+                                     const std::vector<int64_t>& leaf_is, std::string& err) {
+    if (p.cfg_inst == G && p.cfg_step == step && p.cfg_leaf_is == leaf_is) return TN_OK;
+    const int n = d.n;
+    const int nn = (int)p.nodes.size();
+    const int64_t p_is = p.split_bytes / (int64_t)d.elem_bytes();
+    for (int k = 0; k < nn; ++k) {
+        Node& nd = p.nodes[k];
+        InstanceInfo in;
+        memset(&in, 0, sizeof(in));
+        in.n_inst = G;
+        in.slice_step = step;
+        in.c_is = p.ws_elems;
+        in.sc_is = nn;
+        in.p_is = p_is;
+        auto set = [&](int c, int64_t& is, int32_t& sis) {
+            if (c >= n) {
+                is = p.ws_elems;
+                sis = nn;
+            } else if (c >= 0) {
+                is = leaf_is.empty() ? 0 : leaf_is[c];
+                sis = 0;
+            }
+        };
+        set(nd.ca, in.a_is, in.sa_is);
+        set(nd.cb, in.b_is, in.sb_is);
+        p.gen[k].in = in;
+        nd.tile.in = in;
+    }
+    if (!p.items.empty()) {
+        std::vector<TileArgs> descs(nn);
+        for (int k = 0; k < nn; ++k) descs[k] = p.nodes[k].tile;
+        std::vector<WaveItem> items;
+        items.reserve(p.items.size() * G);
+        // instance-major within each step keeps every step's items contiguous
+        p.inst_items_begin.assign(p.steps.size(), 0);
+        for (size_t s = 0; s < p.steps.size(); ++s) {
+            const Step& st = p.steps[s];
+            p.inst_items_begin[s] = (int)items.size();
+            if (!st.wave) continue;
+            for (int i = 0; i < G; ++i)
+                for (int j = 0; j < st.item_count; ++j) {
+                    WaveItem it = p.items[st.item_begin + j];
+                    it.pad = i;
+                    items.push_back(it);
+                }
+        }
+        cudaError_t e = cudaMemcpy(p.descs_dev, descs.data(), sizeof(TileArgs) * nn, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p.items_dev, items.data(), sizeof(WaveItem) * items.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            err = std::string("instance layout upload: ") + cudaGetErrorString(e);
+            return TN_ECUDA;
+        }
+    }
+    p.acc_args.n_inst = step == 1 ? G : 1;
+    p.cfg_inst = G;
+    p.cfg_step = step;
+    p.cfg_leaf_is = leaf_is;
+    return TN_OK;
+}
+
+// One launch group: reset the node maxima of all instances, run every node
+// (each launch covers all instances), then either fold the instances' roots
+// (consecutive slices) into the FP64 accumulator and advance the slice
+// counter, or write each independent instance's root to its output.
+// ev: optional timing events around launch steps [pf, pf + pc).
 static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, const cudaEvent_t* ev,
                                  int pf, int pc) {
-    cudaError_t e = launch_begin_slice(p.maxabs, (int)p.nodes.size(), s);
+    const int G = std::max(p.cfg_inst, 1);
+    cudaError_t e = launch_begin_slice(p.maxabs, (int)p.nodes.size() * G, s);
     if (e != cudaSuccess) return e;
     const bool c = d.is_complex();
     for (int k = 0; k < (int)p.steps.size(); ++k) {
@@ -680,7 +757,7 @@ static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, cons
             return e;
         const Step& st = p.steps[k];
         if (st.wave) {
-            e = launch_wave(p.items_dev + st.item_begin, st.item_count, p.descs_dev,
+            e = launch_wave(p.items_dev + p.inst_items_begin[k], st.item_count * G, p.descs_dev,
                             reinterpret_cast<const void* const*>(p.leaf_ptr_dev), c, s);
         } else {
             const Node& nd = p.nodes[st.node];
@@ -697,17 +774,14 @@ static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, cons
             (e = cudaEventRecordWithFlags(ev[pc], s, cudaEventRecordExternal)) != cudaSuccess)
             return e;
     }
+    if (p.cfg_step == 0)
+        return launch_batch_finish(p.inst_roots_dev, G, p.inst_out_dev, p.inst_exp_dev, nullptr, nullptr,
+                                   nullptr, s);
     e = launch_accumulate(p.acc_args, c, s);
     if (e != cudaSuccess) return e;
-    return launch_advance(p.ctl, s);
+    return launch_advance(p.ctl, s, G);
 }
 
-tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count,
-                   const tn_options& o, void* out, int out_mem, int64_t* out_exp2,
-                   cudaStream_t stream, std::string& err) {
-    (void)unit;
-    const int n = d.n;
-    const size_t eb = d.elem_bytes();
 #define CK(x)                                                     \
     do {                                                          \
         cudaError_t e_ = (x);                                     \
@@ -716,23 +790,14 @@ tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count
             return e_ == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA; \
         }                                                         \
     } while (0)
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    CK(cudaStreamIsCapturing(stream, &cap));
-    const bool capturing = cap != cudaStreamCaptureStatusNone;
-    // profiling hooks
-    int pf = 0, pc = 0;
-    const cudaEvent_t* uev = nullptr;
-    if (o.prof_events && o.prof_count > 0) {
-        pf = o.prof_first;
-        pc = o.prof_count;
-        if (pf < 0 || pf + pc > (int)p.steps.size()) {
-            err = "profiling step range out of bounds";
-            return TN_EINVAL;
-        }
-        uev = reinterpret_cast<const cudaEvent_t*>(o.prof_events);
-    }
-    // leaf pointers (host leaves are staged into library memory)
-    std::vector<const void*> lp(n);
+
+// Leaf pointers of this call (host leaves are staged into library memory),
+// patched into the node arguments and the device leaf table.
+static tn_status prepare_leaves(NetDesc& d, Plan& p, bool capturing, std::vector<const void*>& lp,
+                                cudaStream_t stream, std::string& err) {
+    const int n = d.n;
+    const size_t eb = d.elem_bytes();
+    lp.assign(n, nullptr);
     for (int v = 0; v < n; ++v) {
         LeafDesc& lf = d.leaves[v];
         if (lf.mem == TN_MEM_HOST) {
@@ -759,73 +824,198 @@ tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count
         if (nd.cb >= 0 && nd.cb < n) p.gen[k].B = nd.tile.B = lp[nd.cb];
     }
     if (p.leaf_ptr_uploaded != lp) {
-        // pointer table changes only when leaves are re-attached
-        CK(cudaMemcpyAsync(p.leaf_ptr_dev, lp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice,
-                           stream));
+        // the pointer table changes only when leaves are re-attached
+        CK(cudaMemcpyAsync(p.leaf_ptr_dev, lp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, stream));
         CK(cudaStreamSynchronize(stream));
         p.leaf_ptr_uploaded = lp;
     }
+    return TN_OK;
+}
+
+// (Re)capture the per-group graph when the leaves, the timing hooks or the
+// instance layout changed.
+static tn_status ensure_graph(const NetDesc& d, Plan& p, const std::vector<const void*>& lp, int pf,
+                              int pc, std::string& err) {
+    if (p.gexec && p.graph_ptrs == lp && p.graph_prof_first == pf && p.graph_prof_count == pc &&
+        p.graph_inst == p.cfg_inst && p.graph_step == p.cfg_step)
+        return TN_OK;
+    if (p.gexec) CK(cudaGraphExecDestroy(p.gexec));
+    if (p.graph) CK(cudaGraphDestroy(p.graph));
+    p.gexec = nullptr;
+    p.graph = nullptr;
+    while ((int)p.prof_placeholder.size() < pc + 1) {
+        cudaEvent_t ev;
+        CK(cudaEventCreate(&ev));
+        p.prof_placeholder.push_back(ev);
+    }
+    CK(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_slice(d, p, p.cap_stream, pc ? p.prof_placeholder.data() : nullptr, pf, pc);
+    cudaError_t e2 = cudaStreamEndCapture(p.cap_stream, &p.graph);
+    CK(e);
+    CK(e2);
+    CK(cudaGraphInstantiate(&p.gexec, p.graph, 0));
+    p.graph_ptrs = lp;
+    p.graph_prof_first = pf;
+    p.graph_prof_count = pc;
+    p.graph_inst = p.cfg_inst;
+    p.graph_step = p.cfg_step;
+    p.prof_nodes.assign(pc + 1, nullptr);
+    if (pc) {
+        size_t nn = 0;
+        CK(cudaGraphGetNodes(p.graph, nullptr, &nn));
+        std::vector<cudaGraphNode_t> all(nn);
+        CK(cudaGraphGetNodes(p.graph, all.data(), &nn));
+        for (auto g : all) {
+            cudaGraphNodeType t;
+            CK(cudaGraphNodeGetType(g, &t));
+            if (t != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev;
+            CK(cudaGraphEventRecordNodeGetEvent(g, &ev));
+            for (int i = 0; i <= pc; ++i)
+                if (p.prof_placeholder[i] == ev) p.prof_nodes[i] = g;
+        }
+        for (auto g : p.prof_nodes)
+            if (!g) {
+                err = "internal: timing event node missing from the captured graph";
+                return TN_ECUDA;
+            }
+    }
+    return TN_OK;
+}
+
+static tn_status upload_leaf_sizes(const NetDesc& d, Plan& p, int G, const std::vector<int64_t>& leaf_is,
+                                   std::string& err) {
+    std::vector<int64_t> nf(d.n);
+    for (int v = 0; v < d.n; ++v) {
+        const int64_t is = leaf_is.empty() ? 0 : leaf_is[v];
+        nf[v] = ((int64_t)(G - 1) * is + d.leaves[v].size) * (d.is_complex() ? 2 : 1);
+    }
+    if (nf == p.leaf_nfloat_uploaded) return TN_OK;
+    CK(cudaMemcpy(p.leaf_nfloat_dev, nf.data(), sizeof(int64_t) * d.n, cudaMemcpyHostToDevice));
+    p.leaf_nfloat_uploaded = nf;
+    return TN_OK;
+}
+
+tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count,
+                   const tn_options& o, void* out, int out_mem, int64_t* out_exp2,
+                   cudaStream_t stream, std::string& err) {
+    (void)unit;
+    const int n = d.n;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(stream, &cap));
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    // profiling hooks
+    int pf = 0, pc = 0;
+    const cudaEvent_t* uev = nullptr;
+    if (o.prof_events && o.prof_count > 0) {
+        pf = o.prof_first;
+        pc = o.prof_count;
+        if (pf < 0 || pf + pc > (int)p.steps.size()) {
+            err = "profiling step range out of bounds";
+            return TN_EINVAL;
+        }
+        uev = reinterpret_cast<const cudaEvent_t*>(o.prof_events);
+    }
+    // slices per launch group (instances); the device state was sized for it
+    int G = o.slice_batch > 1 ? o.slice_batch : 1;
+    if (G > count) G = (int)count;
+    if (G > p.alloc_inst) {
+        err = "internal: slice batch exceeds the allocated instances";
+        return TN_ECUDA;
+    }
+    if (capturing && (p.cfg_inst != G || p.cfg_step != 1)) {
+        err = "the first call with a new slice batch must run outside stream capture";
+        return TN_EUNSUPPORTED;
+    }
+    tn_status st = configure_instances(d, p, G, 1, std::vector<int64_t>(), err);
+    if (st != TN_OK) return st;
+    if (!capturing) {
+        st = upload_leaf_sizes(d, p, 1, std::vector<int64_t>(), err);
+        if (st != TN_OK) return st;
+    }
+    std::vector<const void*> lp;
+    st = prepare_leaves(d, p, capturing, lp, stream, err);
+    if (st != TN_OK) return st;
     CK(launch_leaf_max(p.leaf_ptr_dev, p.leaf_nfloat_dev, p.leafmax, n, stream));
-    CK(launch_begin_call(p.ctl, begin, p.acc, p.n_out * (d.is_complex() ? 2 : 1), stream));
+    CK(launch_begin_call(p.ctl, begin, begin + count, p.acc, p.n_out * (d.is_complex() ? 2 : 1), stream));
+    const int64_t groups = (count + G - 1) / G;
     const bool use_graph = !o.no_graph && !capturing;
     if (use_graph) {
-        if (!p.gexec || p.graph_ptrs != lp || p.graph_prof_first != pf || p.graph_prof_count != pc) {
-            if (p.gexec) CK(cudaGraphExecDestroy(p.gexec));
-            if (p.graph) CK(cudaGraphDestroy(p.graph));
-            p.gexec = nullptr;
-            p.graph = nullptr;
-            while ((int)p.prof_placeholder.size() < pc + 1) {
-                cudaEvent_t ev;
-                CK(cudaEventCreate(&ev));
-                p.prof_placeholder.push_back(ev);
-            }
-            CK(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = enqueue_slice(d, p, p.cap_stream, pc ? p.prof_placeholder.data() : nullptr,
-                                          pf, pc);
-            cudaError_t e2 = cudaStreamEndCapture(p.cap_stream, &p.graph);
-            CK(e);
-            CK(e2);
-            CK(cudaGraphInstantiate(&p.gexec, p.graph, 0));
-            p.graph_ptrs = lp;
-            p.graph_prof_first = pf;
-            p.graph_prof_count = pc;
-            p.prof_nodes.assign(pc + 1, nullptr);
-            if (pc) {
-                size_t nn = 0;
-                CK(cudaGraphGetNodes(p.graph, nullptr, &nn));
-                std::vector<cudaGraphNode_t> all(nn);
-                CK(cudaGraphGetNodes(p.graph, all.data(), &nn));
-                for (auto g : all) {
-                    cudaGraphNodeType t;
-                    CK(cudaGraphNodeGetType(g, &t));
-                    if (t != cudaGraphNodeTypeEventRecord) continue;
-                    cudaEvent_t ev;
-                    CK(cudaGraphEventRecordNodeGetEvent(g, &ev));
-                    for (int i = 0; i <= pc; ++i)
-                        if (p.prof_placeholder[i] == ev) p.prof_nodes[i] = g;
-                }
-                for (auto g : p.prof_nodes)
-                    if (!g) {
-                        err = "internal: timing event node missing from the captured graph";
-                        return TN_ECUDA;
-                    }
-            }
-        }
+        st = ensure_graph(d, p, lp, pf, pc, err);
+        if (st != TN_OK) return st;
         for (int i = 0; i < pc + (pc ? 1 : 0); ++i)
             CK(cudaGraphExecEventRecordNodeSetEvent(p.gexec, p.prof_nodes[i], uev[i]));
-        for (int64_t s = 0; s < count; ++s) CK(cudaGraphLaunch(p.gexec, stream));
+        for (int64_t s = 0; s < groups; ++s) CK(cudaGraphLaunch(p.gexec, stream));
     } else {
-        for (int64_t s = 0; s < count; ++s) CK(enqueue_slice(d, p, stream, uev, pf, pc));
+        for (int64_t s = 0; s < groups; ++s) CK(enqueue_slice(d, p, stream, uev, pf, pc));
     }
-    CK(launch_finalize(p.ctl, (int)(count & 1), stream));
+    CK(launch_finalize(p.ctl, (int)(groups & 1), stream));
     const size_t acc_bytes = sizeof(double) * p.n_out * (d.is_complex() ? 2 : 1);
     cudaMemcpyKind kind = out_mem == TN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     CK(cudaMemcpyAsync(out, p.acc, acc_bytes, kind, stream));
     CK(cudaMemcpyAsync(out_exp2, &p.ctl->final_exp, sizeof(int64_t), kind, stream));
     if (out_mem == TN_MEM_HOST) CK(cudaStreamSynchronize(stream));
-#undef CK
     return TN_OK;
 }
+
+tn_status run_instances(NetDesc& d, Plan& p, void* unit, int n_inst, const int64_t* leaf_is_arr,
+                        double* out, int64_t* out_exp2, int out_mem, cudaStream_t stream,
+                        std::string& err) {
+    (void)unit;
+    const int n = d.n;
+    const int nn = (int)p.nodes.size();
+    const size_t eb = d.elem_bytes();
+    if (p.d_sliced != 1 || p.n_out != 1) {
+        err = "tn_contract_instances: the network must be scalar and the tree unsliced";
+        return TN_EUNSUPPORTED;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        err = "tn_contract_instances: not available during stream capture";
+        return TN_EUNSUPPORTED;
+    }
+    const int G = n_inst;
+    if (G > p.alloc_inst) {
+        err = "internal: instances exceed the allocation";
+        return TN_ECUDA;
+    }
+    std::vector<int64_t> leaf_is(n, 0);
+    if (leaf_is_arr)
+        for (int v = 0; v < n; ++v) leaf_is[v] = leaf_is_arr[v];
+    tn_status st = configure_instances(d, p, G, 0, leaf_is, err);
+    if (st != TN_OK) return st;
+    st = upload_leaf_sizes(d, p, G, leaf_is, err);
+    if (st != TN_OK) return st;
+    if (p.inst_roots_n != G) {
+        const Node& root = p.nodes.back();
+        std::vector<BatchRoot> roots(G);
+        for (int i = 0; i < G; ++i) {
+            roots[i].root = (char*)p.ws + ((int64_t)i * p.ws_elems + root.ws_off) * eb;
+            roots[i].exp = p.exps + (int64_t)i * nn + (nn - 1);
+            roots[i].max = p.maxabs + (int64_t)i * nn + (nn - 1);
+            roots[i].is_c = d.is_complex();
+            roots[i].pad = 0;
+        }
+        CK(cudaMemcpy(p.inst_roots_dev, roots.data(), sizeof(BatchRoot) * G, cudaMemcpyHostToDevice));
+        p.inst_roots_n = G;
+    }
+    std::vector<const void*> lp;
+    st = prepare_leaves(d, p, false, lp, stream, err);
+    if (st != TN_OK) return st;
+    CK(launch_leaf_max(p.leaf_ptr_dev, p.leaf_nfloat_dev, p.leafmax, n, stream));
+    CK(launch_begin_call(p.ctl, 0, 1, p.acc, 0, stream));
+    st = ensure_graph(d, p, lp, 0, 0, err);
+    if (st != TN_OK) return st;
+    CK(cudaGraphLaunch(p.gexec, stream));
+    cudaMemcpyKind kind = out_mem == TN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(out, p.inst_out_dev, sizeof(double) * 2 * G, kind, stream));
+    CK(cudaMemcpyAsync(out_exp2, p.inst_exp_dev, sizeof(int64_t) * G, kind, stream));
+    if (out_mem == TN_MEM_HOST) CK(cudaStreamSynchronize(stream));
+    return TN_OK;
+}
+#undef CK
+
 
 tn_status make_generic_args_node(const NetDesc& d, const Plan& p, const Node& nd, GenericArgs& g,
                                  std::string& err) {
@@ -872,6 +1062,17 @@ void free_device(Plan& p) {
     p.split_buf = nullptr;
     if (p.descs_dev) cudaFree(p.descs_dev);
     if (p.items_dev) cudaFree(p.items_dev);
+    if (p.inst_roots_dev) cudaFree(p.inst_roots_dev);
+    if (p.inst_out_dev) cudaFree(p.inst_out_dev);
+    if (p.inst_exp_dev) cudaFree(p.inst_exp_dev);
+    p.inst_roots_dev = nullptr;
+    p.inst_out_dev = nullptr;
+    p.inst_exp_dev = nullptr;
+    p.cfg_inst = -1;
+    p.inst_roots_n = 0;
+    p.graph_inst = -1;
+    p.graph_step = -1;
+    p.leaf_nfloat_uploaded.clear();
     p.descs_dev = nullptr;
     p.items_dev = nullptr;
     if (p.leaf_ptr_dev) cudaFree(p.leaf_ptr_dev);

@@ -89,6 +89,17 @@ struct Plan {
     std::vector<const void*> leaf_ptr_uploaded;
     std::vector<GenericArgs> gen;
     GradState* grad = nullptr;
+    // instances (slice-parallel or independent copies)
+    int alloc_inst = 1;                 // instances the device state holds
+    int cfg_inst = -1, cfg_step = 1;    // layout currently in the arguments
+    std::vector<int64_t> cfg_leaf_is;
+    std::vector<int> inst_items_begin;  // per step: first wave item (all instances)
+    BatchRoot* inst_roots_dev = nullptr;
+    double* inst_out_dev = nullptr;
+    int64_t* inst_exp_dev = nullptr;
+    int graph_inst = -1, graph_step = -1;
+    int inst_roots_n = 0;
+    std::vector<int64_t> leaf_nfloat_uploaded;
     std::vector<Step> steps;
     std::vector<WaveItem> items;
     WaveItem* items_dev = nullptr;
@@ -114,6 +125,9 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err);
 tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count,
                    const tn_options& o, void* out, int out_mem, int64_t* out_exp2,
                    cudaStream_t stream, std::string& err);
+tn_status run_instances(NetDesc& d, Plan& p, void* unit, int n_inst, const int64_t* leaf_is,
+                        double* out, int64_t* out_exp2, int out_mem, cudaStream_t stream,
+                        std::string& err);
 tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int64_t adj_exp2,
                    void* const* grads, cudaStream_t stream, std::string& err);
 void plan_info(const NetDesc& d, const Plan& p, double out[8]);

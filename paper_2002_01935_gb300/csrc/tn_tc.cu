@@ -246,16 +246,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc(const __grid_constant__ Tile
     const int64_t tiles_n = (N + NC - 1) / NC;
     const int64_t m0 = ((int64_t)blockIdx.x / tiles_n) * kBM;
     const int64_t n0 = ((int64_t)blockIdx.x % tiles_n) * NC;
-    const int64_t b = blockIdx.z;
+    const int64_t b = blockIdx.z % a.nbatch;
+    const int inst = (int)(blockIdx.z / a.nbatch);
     const int nkb = (int)((K + KC - 1) / KC);
+    // this instance's operands, result, scale slots and slice (an idle
+    // instance leaves before touching barriers or tensor memory)
+    const InstanceInfo& in = a.in;
+    const int64_t slice = a.ctl->slice + (int64_t)inst * in.slice_step;
+    if (slice >= a.ctl->slice_end) return;
+    constexpr int ESZ = CPLX ? 8 : 4;
+    const void* Ainst = (const char*)a.A + (int64_t)inst * in.a_is * ESZ;
+    const void* Binst = (const char*)a.B + (int64_t)inst * in.b_is * ESZ;
+    void* Cinst = (char*)a.C + (int64_t)inst * in.c_is * ESZ;
+    ScaleIO sio = a.sc;
+    if (sio.max_a) sio.max_a += (int64_t)inst * in.sa_is;
+    if (sio.exp_a) sio.exp_a += (int64_t)inst * in.sa_is;
+    if (sio.max_b) sio.max_b += (int64_t)inst * in.sb_is;
+    if (sio.exp_b) sio.exp_b += (int64_t)inst * in.sb_is;
+    sio.max_c += (int64_t)inst * in.sc_is;
+    sio.exp_c += (int64_t)inst * in.sc_is;
 
     // renormalisation of the operands (exact powers of two)
-    const int eA = exp_of(a.sc.max_a), eB = exp_of(a.sc.max_b);
+    const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
     const int cA = max(-120, min(120, eA)), cB = max(-120, min(120, eB));
     const float fa = ldexpf(1.f, -cA), fb = ldexpf(1.f, -cB);
     const int resid = (eA - cA) + (eB - cB);
-    if (blockIdx.x == 0 && blockIdx.z == 0 && tid == 0 && a.sc.exp_c)
-        *a.sc.exp_c = (a.sc.exp_a ? *a.sc.exp_a : 0) + (a.sc.exp_b ? *a.sc.exp_b : 0) + eA + eB;
+    if (blockIdx.x == 0 && b == 0 && tid == 0 && sio.exp_c)
+        *sio.exp_c = (sio.exp_a ? *sio.exp_a : 0) + (sio.exp_b ? *sio.exp_b : 0) + eA + eB;
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -282,7 +299,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc(const __grid_constant__ Tile
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const int64_t slice = a.ctl->slice;
 
     if (warp == kMmaWarp) {
         // ---------------- MMA issuer ----------------
@@ -320,8 +336,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc(const __grid_constant__ Tile
         __syncwarp();
     } else {
         // ---------------- producers ----------------
-        const float* Af = reinterpret_cast<const float*>(a.A);
-        const float* Bf = reinterpret_cast<const float*>(a.B);
+        const float* Af = reinterpret_cast<const float*>(Ainst);
+        const float* Bf = reinterpret_cast<const float*>(Binst);
         const int64_t baseA = slice_offset(a.sla, slice) + scatter(b, a.a_b, a.nb) + scatter(m0, a.a_m, a.nm);
         const int64_t baseB = slice_offset(a.slb, slice) + scatter(b, a.b_b, a.nb) + scatter(n0, a.b_n, a.nn);
         const int mlim = (int)min(M - m0, (int64_t)kBM);
@@ -509,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc(const __grid_constant__ Tile
                     const int nfirst = CPLX ? col / 2 : col;
                     const int ncount = CPLX ? 8 : 16;
                     if (nfirst < nlim) {
-                        float* crow = reinterpret_cast<float*>(a.C) +
+                        float* crow = reinterpret_cast<float*>(Cinst) +
                                       ((b * M + m) * N + n0 + nfirst) * (CPLX ? 2 : 1);
                         if (nfirst + ncount <= nlim) {
 #pragma unroll
@@ -528,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc(const __grid_constant__ Tile
         }
         // block-free max over the producer warps
         for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-        if ((tid & 31) == 0 && lmax > 0.f) atomicMax(a.sc.max_c, __float_as_uint(lmax));
+        if ((tid & 31) == 0 && lmax > 0.f) atomicMax(sio.max_c, __float_as_uint(lmax));
     }
     tc_fence_before();
     __syncthreads();
@@ -565,7 +581,8 @@ static cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     const int64_t M = 1ll << a.nm, N = 1ll << a.nn;
     constexpr int NC = CPLX ? kBN / 2 : kBN;
     const int64_t tiles = ((M + kBM - 1) / kBM) * ((N + NC - 1) / NC);
-    dim3 grid((unsigned)tiles, 1, (unsigned)a.nbatch);
+    const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
+    dim3 grid((unsigned)tiles, 1, (unsigned)(a.nbatch * ni));
     k_tc<CPLX, PREC, STAGES><<<grid, kThreads, SMEM, s>>>(a);
     return cudaGetLastError();
 }

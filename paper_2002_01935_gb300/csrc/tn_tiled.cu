@@ -116,11 +116,44 @@ struct Scales {
     int resid;
 };
 
-__device__ __forceinline__ Scales node_scales(const TileArgs& a, bool write_exp) {
-    const int eA = exp_of(a.sc.max_a), eB = exp_of(a.sc.max_b);
+// One instance's view of a node: operand/result pointers, scale slots and
+// slice id, all offset by the instance index.
+struct View {
+    const void* A;
+    const void* B;
+    void* C;
+    void* P;
+    ScaleIO sc;
+    int64_t slice;
+    bool live;
+};
+
+__device__ __forceinline__ View inst_view(const TileArgs& a, int inst, int esz) {
+    const InstanceInfo& in = a.in;
+    View v;
+    v.A = (const char*)a.A + (int64_t)inst * in.a_is * esz;
+    v.B = (const char*)a.B + (int64_t)inst * in.b_is * esz;
+    v.C = (char*)a.C + (int64_t)inst * in.c_is * esz;
+    v.P = (char*)a.P + (int64_t)inst * in.p_is * esz;
+    v.sc = a.sc;
+    if (v.sc.max_a) v.sc.max_a += (int64_t)inst * in.sa_is;
+    if (v.sc.exp_a) v.sc.exp_a += (int64_t)inst * in.sa_is;
+    if (v.sc.max_b) v.sc.max_b += (int64_t)inst * in.sb_is;
+    if (v.sc.exp_b) v.sc.exp_b += (int64_t)inst * in.sb_is;
+    if (v.sc.max_c) v.sc.max_c += (int64_t)inst * in.sc_is;
+    if (v.sc.exp_c) v.sc.exp_c += (int64_t)inst * in.sc_is;
+    v.slice = a.ctl->slice + (int64_t)inst * in.slice_step;
+    v.live = v.slice < a.ctl->slice_end;
+    return v;
+}
+
+__device__ __forceinline__ int n_inst(const TileArgs& a) { return a.in.n_inst > 1 ? a.in.n_inst : 1; }
+
+__device__ __forceinline__ Scales node_scales(const ScaleIO& sio, bool write_exp) {
+    const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
     const int cA = max(-120, min(120, eA)), cB = max(-120, min(120, eB));
-    if (write_exp && a.sc.exp_c)
-        *a.sc.exp_c = (a.sc.exp_a ? *a.sc.exp_a : 0) + (a.sc.exp_b ? *a.sc.exp_b : 0) + eA + eB;
+    if (write_exp && sio.exp_c)
+        *sio.exp_c = (sio.exp_a ? *sio.exp_a : 0) + (sio.exp_b ? *sio.exp_b : 0) + eA + eB;
     Scales s;
     s.fa = ldexpf(1.f, -cA);
     s.fb = ldexpf(1.f, -cB);
@@ -149,10 +182,15 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
     const int64_t tiles_n = (N + TN - 1) / TN;
     const int64_t m0 = ((int64_t)blockIdx.x / tiles_n) * TM;
     const int64_t n0 = ((int64_t)blockIdx.x % tiles_n) * TN;
-    const int split_id = blockIdx.z % a.split;
-    const int64_t b = blockIdx.z / a.split;
-    const Scales sc = node_scales(a, blockIdx.x == 0 && blockIdx.z == 0 && tid == 0);
-    const int64_t slice = a.ctl->slice;
+    const int per_inst = (int)(a.nbatch * a.split);
+    const int inst = blockIdx.z / per_inst;
+    const int zz = blockIdx.z % per_inst;
+    const int split_id = zz % a.split;
+    const int64_t b = zz / a.split;
+    const View vw = inst_view(a, inst, (int)sizeof(T));
+    if (!vw.live) return;
+    const Scales sc = node_scales(vw.sc, blockIdx.x == 0 && zz == 0 && tid == 0);
+    const int64_t slice = vw.slice;
     const int64_t baseA =
         slice_off(a.sla, slice) + scatter_bits(b, a.a_b, a.nb) + scatter_bits(m0, a.a_m, a.nm);
     const int64_t baseB =
@@ -168,8 +206,8 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
     const int nlim = (int)min64(N - n0, TN);
     const int64_t kbeg = (int64_t)split_id * a.kchunk;
     const int64_t kend = min64(K, kbeg + a.kchunk);
-    const T* A = reinterpret_cast<const T*>(a.A);
-    const T* B = reinterpret_cast<const T*>(a.B);
+    const T* A = reinterpret_cast<const T*>(vw.A);
+    const T* B = reinterpret_cast<const T*>(vw.B);
     const int tx = tid % TX, ty = tid / TX;
 
     T acc[RM][RN];
@@ -241,7 +279,7 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
 
     // epilogue: direct output (one split) or a partial for the reduce pass
     float lmax = 0.f;
-    T* out = reinterpret_cast<T*>(a.split > 1 ? a.P : a.C);
+    T* out = reinterpret_cast<T*>(a.split > 1 ? vw.P : vw.C);
     const int64_t plane = (a.split > 1 ? (int64_t)split_id * ((int64_t)a.nbatch) : 0) + b;
 #pragma unroll
     for (int r = 0; r < RM; ++r) {
@@ -268,7 +306,7 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
         }
     }
     if (a.split == 1) {
-        block_max(lmax, a.sc.max_c);
+        block_max(lmax, vw.sc.max_c);
         if (a.t_done && threadIdx.x == 0) atomicMax(a.t_done, global_ns());
     }
 }
@@ -278,9 +316,11 @@ template <bool CPLX>
 __global__ void __launch_bounds__(256) k_split_reduce(const __grid_constant__ TileArgs a) {
     using T = typename VT<CPLX>::T;
     const int64_t plane_sz = (int64_t)a.nbatch << (a.nm + a.nn);
-    const Scales sc = node_scales(a, blockIdx.x == 0 && threadIdx.x == 0);
-    const T* P = reinterpret_cast<const T*>(a.P);
-    T* C = reinterpret_cast<T*>(a.C);
+    const View vw = inst_view(a, blockIdx.y, (int)sizeof(T));
+    if (!vw.live) return;
+    const Scales sc = node_scales(vw.sc, blockIdx.x == 0 && threadIdx.x == 0);
+    const T* P = reinterpret_cast<const T*>(vw.P);
+    T* C = reinterpret_cast<T*>(vw.C);
     float lmax = 0.f;
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < plane_sz;
          o += (int64_t)gridDim.x * blockDim.x) {
@@ -306,7 +346,7 @@ __global__ void __launch_bounds__(256) k_split_reduce(const __grid_constant__ Ti
         lmax = fmaxf(lmax, absmax(v));
         C[o] = v;
     }
-    block_max(lmax, a.sc.max_c);
+    block_max(lmax, vw.sc.max_c);
     if (a.t_done && threadIdx.x == 0) atomicMax(a.t_done, global_ns());
 }
 
@@ -319,15 +359,17 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a)
     const int64_t N = 1ll << a.nn, M = 1ll << a.nm, K = 1ll << a.nk;
     const int64_t m = (int64_t)blockIdx.x / N, n = (int64_t)blockIdx.x % N;
     const int64_t b = blockIdx.y;
-    const int sp = blockIdx.z;
-    const Scales sc = node_scales(a, blockIdx.x == 0 && blockIdx.y == 0 && sp == 0 && threadIdx.x == 0);
-    const int64_t slice = a.ctl->slice;
+    const int sp = blockIdx.z % a.split;
+    const View vw = inst_view(a, blockIdx.z / a.split, (int)sizeof(T));
+    if (!vw.live) return;
+    const Scales sc = node_scales(vw.sc, blockIdx.x == 0 && blockIdx.y == 0 && sp == 0 && threadIdx.x == 0);
+    const int64_t slice = vw.slice;
     const int64_t baseA =
         slice_off(a.sla, slice) + scatter_bits(b, a.a_b, a.nb) + scatter_bits(m, a.a_m, a.nm);
     const int64_t baseB =
         slice_off(a.slb, slice) + scatter_bits(b, a.b_b, a.nb) + scatter_bits(n, a.b_n, a.nn);
-    const T* A = reinterpret_cast<const T*>(a.A);
-    const T* B = reinterpret_cast<const T*>(a.B);
+    const T* A = reinterpret_cast<const T*>(vw.A);
+    const T* B = reinterpret_cast<const T*>(vw.B);
     const int lo = threadIdx.x;
     const int64_t loA = scatter_bits(lo, a.a_k, a.nk), loB = scatter_bits(lo, a.b_k, a.nk);
     const int64_t kb = (int64_t)sp * a.kchunk, ke = min64(K, kb + a.kchunk);
@@ -358,7 +400,7 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a)
         T v = red[0];
         const int64_t o = (b * M + m) * N + n;
         if (a.split > 1) {
-            reinterpret_cast<T*>(a.P)[(int64_t)sp * (a.nbatch * M * N) + o] = v;
+            reinterpret_cast<T*>(vw.P)[(int64_t)sp * (a.nbatch * M * N) + o] = v;
             return;
         }
         if (sc.resid) {
@@ -369,9 +411,9 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a)
                 v = ldexpf(v, -sc.resid);
             }
         }
-        reinterpret_cast<T*>(a.C)[o] = v;
+        reinterpret_cast<T*>(vw.C)[o] = v;
         float mx = absmax(v);
-        if (mx > 0.f) atomicMax(a.sc.max_c, __float_as_uint(mx));
+        if (mx > 0.f) atomicMax(vw.sc.max_c, __float_as_uint(mx));
         if (a.t_done) atomicMax(a.t_done, global_ns());
     }
 }
@@ -395,10 +437,15 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     const int tid = threadIdx.x;
-    const T* A = reinterpret_cast<const T*>(d.a_leaf >= 0 ? leaf_ptrs[d.a_leaf] : d.A);
-    const T* B = reinterpret_cast<const T*>(d.b_leaf >= 0 ? leaf_ptrs[d.b_leaf] : d.B);
-    const Scales sc = node_scales(d, it.o_begin == 0 && tid == 0);
-    const int64_t slice = d.ctl->slice;
+    const View vw = inst_view(d, it.pad, (int)sizeof(T));
+    if (!vw.live) return;
+    const int64_t isz = (int64_t)sizeof(T);
+    const T* A = reinterpret_cast<const T*>(
+        d.a_leaf >= 0 ? (const char*)leaf_ptrs[d.a_leaf] + (int64_t)it.pad * d.in.a_is * isz : vw.A);
+    const T* B = reinterpret_cast<const T*>(
+        d.b_leaf >= 0 ? (const char*)leaf_ptrs[d.b_leaf] + (int64_t)it.pad * d.in.b_is * isz : vw.B);
+    const Scales sc = node_scales(vw.sc, it.o_begin == 0 && tid == 0);
+    const int64_t slice = vw.slice;
     const int64_t sA = slice_off(d.sla, slice), sB = slice_off(d.slb, slice);
     const int64_t K = 1ll << d.nk;
     const int kt = d.nk < 8 ? (int)K : 256;  // table covers k & 255
@@ -411,7 +458,7 @@ __global__ void __launch_bounds__(256)
     const int O = (int)it.o_count;
     const int g = O >= 256 ? 1 : 256 / O;
     float lmax = 0.f;
-    T* C = reinterpret_cast<T*>(d.C);
+    T* C = reinterpret_cast<T*>(vw.C);
     for (int ol = tid / g; ol < O; ol += 256 / g) {
         const int64_t o = it.o_begin + ol;
         const int64_t n = o & nmask, m = (o >> d.nn) & mmask, b = o >> (d.nn + d.nm);
@@ -452,7 +499,7 @@ __global__ void __launch_bounds__(256)
         lmax = fmaxf(lmax, absmax(acc));
         C[o] = acc;
     }
-    block_max(lmax, d.sc.max_c);
+    block_max(lmax, vw.sc.max_c);
     if (d.t_done && tid == 0) atomicMax(d.t_done, global_ns());
 }
 
@@ -464,7 +511,8 @@ template <bool CPLX, int TM, int TN, int TK, int RM, int RN>
 static cudaError_t launch_cfg(const TileArgs& a, cudaStream_t s) {
     const int64_t M = 1ll << a.nm, N = 1ll << a.nn;
     const int64_t tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
-    dim3 grid((unsigned)tiles, 1, (unsigned)(a.nbatch * a.split));
+    const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
+    dim3 grid((unsigned)tiles, 1, (unsigned)(a.nbatch * a.split * ni));
     k_tile<CPLX, TM, TN, TK, RM, RN><<<grid, (TM / RM) * (TN / RN), 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -479,7 +527,8 @@ static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
         case kTile256x16: e = launch_cfg<CPLX, 256, 16, 16, 4, 4>(a, s); break;
         case kTileDot: {
             const int64_t outs = 1ll << (a.nm + a.nn);
-            k_dot<CPLX><<<dim3((unsigned)outs, (unsigned)a.nbatch, (unsigned)a.split), 256, 0, s>>>(a);
+            const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
+            k_dot<CPLX><<<dim3((unsigned)outs, (unsigned)a.nbatch, (unsigned)(a.split * ni)), 256, 0, s>>>(a);
             e = cudaGetLastError();
             break;
         }
@@ -489,7 +538,8 @@ static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
     const int64_t n = (int64_t)a.nbatch << (a.nm + a.nn);
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    k_split_reduce<CPLX><<<(unsigned)blocks, 256, 0, s>>>(a);
+    const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
+    k_split_reduce<CPLX><<<dim3((unsigned)blocks, (unsigned)ni), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
