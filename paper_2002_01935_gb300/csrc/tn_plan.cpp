@@ -705,6 +705,28 @@ static tn_status configure_instances(const NetDesc& d, Plan& p, int G, int step,
         set(nd.cb, in.b_is, in.sb_is);
         p.gen[k].in = in;
         nd.tile.in = in;
+        // the launch grid's z extent (batch x K splits x instances) is at most
+        // 65535: fewer K splits when many instances run side by side
+        if (nd.kind == kTiled || nd.kind == kTensorCore) {
+            TileArgs& t = nd.tile;
+            if (t.nbatch * (int64_t)G > 65535) {
+                err = "too many instances for a node with " + std::to_string(t.nbatch) + " batch entries";
+                return TN_EUNSUPPORTED;
+            }
+            if (t.split > 1 && t.nbatch * (int64_t)t.split * G > 65535) {
+                int split = t.split;
+                while (split > 1 && t.nbatch * (int64_t)split * G > 65535) split /= 2;
+                const int64_t K = int64_t(1) << t.nk;
+                const int64_t gran = t.cfg == kTileDot ? 256 : (t.cfg == kTile4x1024 ? 4 : 16);
+                const int64_t units = (K + gran - 1) / gran;
+                t.split = split;
+                t.kchunk = ((units + split - 1) / split) * gran;
+            }
+        }
+        if (nd.kind == kGeneric && G > 65535) {
+            err = "too many instances";
+            return TN_EUNSUPPORTED;
+        }
     }
     if (!p.items.empty()) {
         std::vector<TileArgs> descs(nn);

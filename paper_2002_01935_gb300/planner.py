@@ -34,6 +34,8 @@ import numpy as np
 
 __all__ = [
     "TreeInfo",
+    "greedy_tree_sampled",
+    "hyper_greedy",
     "node_labels",
     "tree_info",
     "greedy_tree",
@@ -252,6 +254,135 @@ def greedy_tree(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
         for m in sorted(nbrs):
             push(m, k)
     return pairs
+
+
+def greedy_tree_sampled(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
+                        open_labels: Iterable[int], alpha: float, tau: float,
+                        seed: int) -> List[Tuple[int, int]]:
+    """One Boltzmann-sampled greedy tree (Eq. greedy-boltzmann-factor), fast form.
+
+    The cost of Eq. greedy-cost-function spans many orders of magnitude,
+    so the temperature acts on sign(c) log2(1 + |c|); each candidate pair
+    draws one Gumbel perturbation when it enters the queue (Gumbel-max
+    sampling of exp(-cost/tau) among the queued candidates)."""
+    n = len(leaf_labels)
+    if n == 1:
+        return []
+    opn = set(open_labels)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sets: Dict[int, frozenset] = {}
+    users: Dict[int, Set[int]] = {}
+    lsz: Dict[int, float] = {}
+
+    def lsize(s: Iterable[int]) -> float:
+        return float(sum(math.log2(dims[l]) for l in s))
+
+    for v, ls in enumerate(leaf_labels):
+        sets[v] = frozenset(ls)
+        lsz[v] = lsize(ls)
+        for l in ls:
+            users.setdefault(l, set()).add(v)
+
+    def out_set(i: int, j: int) -> frozenset:
+        keep = []
+        for l in sets[i] | sets[j]:
+            if l in opn:
+                keep.append(l)
+                continue
+            u = users[l]
+            if len(u) > (i in u) + (j in u):
+                keep.append(l)
+        return frozenset(keep)
+
+    heap: List[Tuple[float, int, int]] = []
+    cand: Set[Tuple[int, int]] = set()
+    alive: Set[int] = set(range(n))
+
+    def push(i: int, j: int) -> None:
+        a, b = (i, j) if i < j else (j, i)
+        if (a, b) in cand:
+            return
+        cand.add((a, b))
+        c = 2.0 ** lsize(out_set(a, b)) - alpha * (2.0 ** lsz[a] + 2.0 ** lsz[b])
+        lc = math.copysign(math.log2(1.0 + abs(c)), c)
+        g = -math.log(-math.log(rng.random() + 1e-300) + 1e-300)
+        heapq.heappush(heap, (lc - tau * g, a, b))
+
+    for l, u in users.items():
+        us = sorted(u)
+        for x in range(len(us)):
+            for y in range(x + 1, len(us)):
+                push(us[x], us[y])
+    pairs: List[Tuple[int, int]] = []
+    nxt = n
+    while len(alive) > 1:
+        choice = None
+        while heap:
+            _, a, b = heapq.heappop(heap)
+            if a in alive and b in alive:
+                choice = (a, b)
+                break
+        if choice is None:
+            ordered = sorted(alive, key=lambda v: (lsz[v], v))
+            choice = tuple(sorted(ordered[:2]))
+        a, b = choice
+        s = out_set(a, b)
+        k = nxt
+        nxt += 1
+        pairs.append((a, b))
+        for l in sets[a] | sets[b]:
+            u = users[l]
+            u.discard(a)
+            u.discard(b)
+            if l in s:
+                u.add(k)
+        alive.discard(a)
+        alive.discard(b)
+        sets[k] = s
+        lsz[k] = lsize(s)
+        alive.add(k)
+        nb: Set[int] = set()
+        for l in s:
+            nb |= users[l]
+        nb.discard(k)
+        for m in sorted(nb):
+            push(m, k)
+    return pairs
+
+
+def hyper_greedy(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
+                 open_labels: Iterable[int] = (), trials: int = 32, seed: int = 0,
+                 target_width: Optional[float] = None):
+    """Hyper-Greedy (Sec. 3.4): repeated Boltzmann-sampled greedy trees with
+    alpha ~ U(0, 2) and tau ~ logU(0.01, 3), keeping the lowest cost -- the
+    sliced cost C_s at target_width when given (slicing inside the search,
+    Sec. 4.7.1).  Returns (pairs, sliced, TreeInfo); seeded."""
+    opn = list(open_labels)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    best = None
+    cands = [(1.0, 0.0, None)]
+    for t in range(trials):
+        cands.append((float(rng.uniform(0.0, 2.0)), float(10 ** rng.uniform(-2, math.log10(3))),
+                      int(rng.integers(1 << 31))))
+    for alpha, tau, sd in cands:
+        if sd is None:
+            pairs = greedy_tree(leaf_labels, dims, opn, alpha=1.0)
+        else:
+            pairs = greedy_tree_sampled(leaf_labels, dims, opn, alpha, tau, sd)
+        sliced: List[int] = []
+        if target_width is not None:
+            info0 = tree_info(leaf_labels, dims, pairs, opn)
+            if info0.W > target_width:
+                try:
+                    sliced = slice_greedy(leaf_labels, dims, pairs, opn, target_width)
+                except RuntimeError:
+                    continue  # too wide to slice down: not a candidate
+        info = tree_info(leaf_labels, dims, pairs, opn, sliced)
+        if best is None or info.C_s < best[2].C_s:
+            best = (pairs, sliced, info)
+    if best is None:
+        raise RuntimeError("no sampled tree could be sliced to the target width")
+    return best
 
 
 def left_deep_tree(n_leaves: int, order: Optional[Sequence[int]] = None) -> List[Tuple[int, int]]:
