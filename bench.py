@@ -1,18 +1,31 @@
 #!/usr/bin/env python3
 """Benchmark of the contraction-tree executor; prints one JSON line.
 
-Workload (default): the Ising partition function of a random 3-regular
-graph with N = 100 vertices, beta = 0.3, J = +-1 (one COPY tensor per
-vertex, one Boltzmann matrix per edge), greedy tree sliced to W_s <= 24,
-float32 on the GPU.  One step = one full contraction of the network (all
-slices) through the C-ABI.  Throughput = algorithmic FLOPs 2 C_s per
-network (real; 8 C_s complex) over device time.
+Workloads (``--workload``):
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp32]
+  ising100    (default) Ising partition function of a random 3-regular graph,
+              N = 100, beta = 0.3, J = +-1, greedy tree sliced to W_s <= 24,
+              float32 leaves.  One step = one full contraction (all slices).
+  circuit4x4  one amplitude of a 4x4-qubit, 8-cycle random circuit, greedy
+              tree, no slicing (complex64 leaves).
+  circuit7x7  one amplitude of a 7x7-qubit, 14-cycle random circuit,
+              Hyper-Greedy tree sliced to W_s <= 28; one step = a bounded
+              sample of consecutive slices (``--slices``); the time per
+              amplitude is extrapolated over all 2^k slices.
+  batch       a bounded sample of amplitudes of a 6x6-qubit, 12-cycle circuit
+              (one shared tree) plus 256 Ising networks with N even in
+              [40, 160], all in one captured launch sequence; per-network
+              completion latency p50 / p99.
+
+Throughput = algorithmic FLOPs (8 C complex, 2 C real per slice, Eq.
+vertexcon) over device time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode tf32_split]
   python bench.py --impl reference ...   (the FP64 oracle on host cores)
 
-Under torchrun each rank contracts its own network (seed = rank): weak
-scaling, no collective on the data path; the timing is the max over ranks.
+Under torchrun each rank contracts its own network (seed = rank) or its own
+slice range: weak scaling, no collective on the data path; the timing is the
+max over ranks.
 """
 from __future__ import annotations
 
@@ -30,7 +43,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "contraction FLOP/s & % roofline per tree; s/amplitude; rel. error vs FP64 oracle"
-WORKLOAD = "ising_rr3_n100_beta0.3_greedy_ws24"
+WORKLOAD_NAMES = {
+    "ising100": "ising_rr3_n100_beta0.3_greedy_ws24",
+    "circuit4x4": "circuit_4x4_8cyc_greedy_amplitude",
+    "circuit7x7": "circuit_7x7_14cyc_hypergreedy_ws28_slice_sample",
+    "batch": "batch_6x6_12cyc_amplitudes_plus_256_ising",
+}
+MODES = ["fp32", "tf32_split", "bf16_split", "tf32_3m"]
+# accuracy each mode is held to (relative, against the FP64 oracle)
+MODE_TOL = {"fp32": 1e-5, "tf32_split": 1e-5, "bf16_split": 1e-4, "tf32_3m": 1e-2}
 L2_FLUSH_BYTES = 512 << 20
 # FP32 FMA peak of one GB300: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz.
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -40,14 +61,55 @@ TF32_OVER_BF16 = 1.1 / 2.25
 MODE_PASSES = {"tf32_split": 3, "bf16_split": 3, "tf32_3m": 1}
 
 
-def build_workload(seed: int, n: int = 100, target: float = 24.0):
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+
+def wl_ising(seed: int, n: int = 100, target: float = 24.0):
     from paper_2002_01935_gb300 import inputs, planner
     net = inputs.random_ising(n, seed)
     pairs = planner.greedy_tree(net.labels, net.dims, net.open)
     info = planner.tree_info(net.labels, net.dims, pairs, net.open)
     sliced = planner.slice_greedy(net.labels, net.dims, pairs, net.open, target) if info.W > target else []
     info = planner.tree_info(net.labels, net.dims, pairs, net.open, sliced)
-    return net, pairs, sliced, info
+    return {"net": net, "pairs": pairs, "sliced": sliced, "info": info,
+            "slice_begin": 0, "slice_count": int(info.d_sliced), "oracle": "full",
+            "config": {"n_vertices": n, "beta": 0.3, "J": "+-1", "graph_seed": seed,
+                       "tree": "greedy (alpha=1, tau=0)", "target_W_s": target}}
+
+
+def wl_circuit(rows: int, cols: int, cycles: int, seed: int):
+    from paper_2002_01935_gb300 import inputs, planner
+    circ = inputs.random_circuit(rows, cols, cycles, seed=seed)
+    bits = inputs.random_bitstrings(rows * cols, 1, seed=1000 + seed)[0]
+    net = inputs.circuit_network(circ, bits)
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    info = planner.tree_info(net.labels, net.dims, pairs, net.open)
+    return {"net": net, "pairs": pairs, "sliced": [], "info": info, "slice_begin": 0,
+            "slice_count": 1, "oracle": "full",
+            "config": {"qubits": rows * cols, "grid": f"{rows}x{cols}", "cycles": cycles,
+                       "circuit_seed": seed, "bitstring_seed": 1000 + seed,
+                       "tree": "greedy (alpha=1, tau=0)"}}
+
+
+def wl_circuit7x7(rank: int, slices: int, trials: int = 16, target: float = 28.0):
+    from paper_2002_01935_gb300 import inputs, planner
+    circ = inputs.random_circuit(7, 7, 14, seed=0)
+    bits = inputs.random_bitstrings(49, 1, seed=1000)[0]
+    net = inputs.circuit_network(circ, bits)
+    t0 = time.perf_counter()
+    pairs, sliced, info = planner.hyper_greedy(net.labels, net.dims, net.open, trials=trials,
+                                               seed=0, target_width=target)
+    t_plan = time.perf_counter() - t0
+    count = min(slices, int(info.d_sliced))
+    return {"net": net, "pairs": pairs, "sliced": sliced, "info": info,
+            "slice_begin": rank * count, "slice_count": count, "oracle": "subslice",
+            "config": {"qubits": 49, "grid": "7x7", "cycles": 14, "circuit_seed": 0,
+                       "bitstring_seed": 1000, "target_W_s": target,
+                       "tree": f"Hyper-Greedy, {trials} seeded trials scored by C_s at W_s <= {target:g}",
+                       "planning_s": round(t_plan, 2),
+                       "slice_sample": f"slices [{rank * count}, {rank * count + count}) of "
+                                       f"{int(info.d_sliced)}; time per amplitude extrapolated"}}
 
 
 def node_figures(net, pairs, info, elem_bytes: int):
@@ -132,8 +194,12 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def oracle_baseline(net, pairs, sliced, info, budget_s: float = 12.0, max_runs: int = 40):
-    """Time the FP64 oracle, as it stands, on the host cores."""
+# --------------------------------------------------------------------------
+# oracle legs (host cores, FP64, as it stands)
+# --------------------------------------------------------------------------
+
+def oracle_full(net, pairs, sliced, info, budget_s: float = 12.0, max_runs: int = 40):
+    """Time full oracle contractions of the same network (all slices)."""
     from oracle import tree
     times = []
     val = None
@@ -150,17 +216,50 @@ def oracle_baseline(net, pairs, sliced, info, budget_s: float = 12.0, max_runs: 
             "sample": f"{len(times)} full contractions of the same network (all slices)"}, val
 
 
+def oracle_subslices(net, pairs, target: float = 20.0, budget_s: float = 10.0, max_slices: int = 64):
+    """Time the oracle on consecutive sub-slices of the same tree sliced
+    further, to W_s <= target: a bounded sample of the same contraction."""
+    from oracle import tree
+    from paper_2002_01935_gb300 import planner
+    sl2 = planner.slice_greedy(net.labels, net.dims, pairs, net.open, target)
+    i2 = planner.tree_info(net.labels, net.dims, pairs, net.open, sl2)
+    k, t_sum, acc, acc_e = 0, 0.0, 0.0, None
+    vals = []
+    t_all = time.perf_counter()
+    while k < max_slices and (time.perf_counter() - t_all) < budget_s:
+        t0 = time.perf_counter()
+        m, e = tree.contract_net(net, pairs, sl2, slice_begin=k, slice_count=1)
+        t_sum += time.perf_counter() - t0
+        vals.append((complex(m), int(e)))
+        k += 1
+    e_max = max(e for _, e in vals)
+    ref = sum(m * 2.0 ** (e - e_max) for m, e in vals)
+    per = 8.0 if net.is_complex else 2.0
+    return {"value": per * i2.C * k / t_sum / 1e12, "unit": "TFLOP/s", "cores": tree.max_threads(),
+            "kind": "oracle", "s_per_subslice": t_sum / k,
+            "sample": f"{k} consecutive sub-slices of the same tree sliced to W_s <= {target:g} "
+                      f"(C per sub-slice {i2.C:.3e})"}, (sl2, k, ref, e_max)
+
+
+# --------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# --------------------------------------------------------------------------
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import __graft_entry__  # noqa: F401  (path setup)
     from oracle import build as obuild
-    obuild.build()
-    net, pairs, sliced, info = build_workload(0)
-    # each step: one full oracle contraction, bounded to a few minutes in all
     from oracle import tree
-    for _ in range(max(args.warmup, 0) and 1):
+    obuild.build()
+    if args.workload not in ("ising100", "circuit4x4"):
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"the FP64 oracle needs hours per step on the {args.workload} workload"}))
+        return 0
+    w = wl_ising(0) if args.workload == "ising100" else wl_circuit(4, 4, 8, 0)
+    net, pairs, sliced, info = w["net"], w["pairs"], w["sliced"], w["info"]
+    for _ in range(1 if args.warmup > 0 else 0):
         tree.contract_net(net, pairs, sliced)
     times = []
     for _ in range(args.steps):
@@ -173,8 +272,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "n_vertices": 100, "beta": 0.3, "W_s": info.W,
-                       "C": info.C, "d_sliced": info.d_sliced},
+            "config": dict(workload=WORKLOAD_NAMES[args.workload], W_s=info.W, C=info.C,
+                           d_sliced=info.d_sliced, **w["config"]),
             "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": tree.max_threads(),
                              "kind": "oracle", "sample": f"{args.steps} full contractions"},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -183,101 +282,22 @@ def run_reference(args):
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--mode", default="fp32")
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--compare-modes", action="store_true",
-                    help="also time every precision mode (device buffers) and report the error")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        return run_reference(args)
-    args.warmup = max(args.warmup, 3)
+# --------------------------------------------------------------------------
+# helpers on the GPU side
+# --------------------------------------------------------------------------
 
-    import numpy as np
-    import torch
+def scalar_value(m, e, cplx):
+    """(mantissa tensor, exponent tensor) -> (python scalar mantissa, int exponent)."""
+    return (complex(m.cpu()) if cplx else float(m.cpu())), int(e.cpu())
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2002_01935_gb300 import binding
+def rel_error(got, got_e, ref, ref_e, cplx):
+    if cplx:
+        return abs(got * 2.0 ** (got_e - ref_e) - ref) / abs(ref)
+    return abs(math.expm1(math.log(abs(got)) + (got_e - ref_e) * math.log(2) - math.log(abs(ref))))
 
-    net, pairs, sliced, info = build_workload(rank)
-    cplx = net.is_complex
-    dt = torch.complex64 if cplx else torch.float32
-    elem = 8 if cplx else 4
-    leaves = [torch.from_numpy(np.array(t, order="C")).to(dt).contiguous().cuda() for t in net.tensors]
-    tnw = binding.TensorNetwork(net.labels, net.dims, net.open, leaves, complex_=cplx)
-    plan = tnw.plan_info(pairs, sliced, args.mode)
-    flops_step = info.flops(cplx)
-    nodes = node_figures(net, pairs, info, elem)
-    n_nodes = len(pairs)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    # warm-up, then one per-step profile pass to find the dominant launch
-    steps = tnw.plan_steps(pairs, sliced, args.mode)
-    n_steps = len(steps)
-    for _ in range(args.warmup):
-        m, e = tnw.contract(pairs, sliced, args.mode)
-
-    def events(n):
-        # torch creates the CUDA event lazily: record once so .cuda_event is valid
-        evl = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
-        for ev in evl:
-            ev.record(stream)
-        return evl
-
-    evs = events(n_steps + 1)
-    flush.zero_()
-    tnw.contract(pairs, sliced, args.mode, prof_events=evs, prof_first=0)
-    torch.cuda.synchronize()
-    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(n_steps)]
-    dom = int(np.argmax(step_ms))
-
-    # timed region: K steps, each bracketed by events; L2 flushed between
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    dom_ev = [events(2) for _ in range(args.steps)]
-    clk = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk.start()
-    for i in range(args.steps):
-        flush.zero_()
-        starts[i].record(stream)
-        m, e = tnw.contract(pairs, sliced, args.mode, prof_events=dom_ev[i], prof_first=dom)
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    call_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
-    dom_ms = [a.elapsed_time(b) for a, b in dom_ev]
-    total_ms = sum(call_ms)
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-        dist.barrier()
-    ms_per_step = total_ms / args.steps
-    value = flops_step * world * args.steps / (total_ms / 1e3) / 1e12
-    result = complex(m.cpu()) if cplx else float(m.cpu())
-    result_exp = int(e.cpu())
-
-    # roofline of the dominant launch step
-    peaks = load_peaks()
+def roofline(steps, dom, dom_ms, nodes, mode, ms_per_step, peaks):
     dnodes = steps[dom]["nodes"]
     dn = {"flops": sum(nodes[k]["flops"] for k in dnodes),
           "bytes": sum(nodes[k]["bytes"] for k in dnodes)}
@@ -285,12 +305,12 @@ def main():
     st = steps[dom]
     t_hbm = dn["bytes"] / (peaks["hbm_gbs"] * 1e9)
     if st["kind"] == 2:
-        tc_peak = peaks["bf16_tflops"] * (1.0 if args.mode == "bf16_split" else TF32_OVER_BF16)
-        passes = MODE_PASSES.get(args.mode, 1)
+        tc_peak = peaks["bf16_tflops"] * (1.0 if mode == "bf16_split" else TF32_OVER_BF16)
+        passes = MODE_PASSES.get(mode, 1)
         t_alu = dn["flops"] * passes / (tc_peak * 1e12)
         pipe = {"bound": "tensor", "peak": tc_peak,
                 "peak_source": f"{peaks['source']} bf16 x " +
-                               ("1" if args.mode == "bf16_split" else "1.1/2.25 (nominal TF32:BF16)"),
+                               ("1" if mode == "bf16_split" else "1.1/2.25 (nominal TF32:BF16)"),
                 "executed_flops": dn["flops"] * passes}
     else:
         t_alu = dn["flops"] / (FP32_SIMT_TFLOPS * 1e12)
@@ -309,12 +329,97 @@ def main():
     cfg_names = {0: "generic", 1: "tile64x64", 2: "tile16x256", 3: "tile4x1024", 4: "tile256x16",
                  5: "dot"}
     kname = {0: "k_generic", 1: "k_tile", 2: "k_tc (tcgen05)"}[st["kind"]]
-    roof["kernel"] = (f"step {dom} of {n_steps}: " +
+    roof["kernel"] = (f"step {dom} of {len(steps)}: " +
                       (f"k_wave over {len(dnodes)} nodes" if st["wave"] else
                        f"node {dnodes[0]}, {kname}" +
                        (f" {cfg_names.get(st['cfg'], '')}" if st["kind"] == 1 else "")))
     roof["algorithmic"] = {"flops": dn["flops"], "bytes": dn["bytes"]}
     roof["share_of_step"] = dmean * 1e3 / ms_per_step
+    return roof
+
+
+def device_events(torch, stream, n):
+    # torch creates the CUDA event lazily: record once so .cuda_event is valid
+    evl = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    for ev in evl:
+        ev.record(stream)
+    return evl
+
+
+# --------------------------------------------------------------------------
+# single-network workloads
+# --------------------------------------------------------------------------
+
+def run_network(args, torch, dist, rank, world, local):
+    import numpy as np
+    from paper_2002_01935_gb300 import binding
+
+    if args.workload == "ising100":
+        w = wl_ising(rank)
+    elif args.workload == "circuit4x4":
+        w = wl_circuit(4, 4, 8, rank)
+    else:
+        w = wl_circuit7x7(rank, args.slices)
+    net, pairs, sliced, info = w["net"], w["pairs"], w["sliced"], w["info"]
+    sb, sc = w["slice_begin"], w["slice_count"]
+    mode = args.mode
+    cplx = net.is_complex
+    dt = torch.complex64 if cplx else torch.float32
+    elem = 8 if cplx else 4
+    leaves = [torch.from_numpy(np.array(t, order="C")).to(dt).contiguous().cuda() for t in net.tensors]
+    tnw = binding.TensorNetwork(net.labels, net.dims, net.open, leaves, complex_=cplx)
+    plan = tnw.plan_info(pairs, sliced, mode)
+    per = 8.0 if cplx else 2.0
+    flops_step = per * info.C * sc
+    nodes = node_figures(net, pairs, info, elem)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def call(md=mode, **kw):
+        return tnw.contract(pairs, sliced, md, slice_begin=sb, slice_count=sc, **kw)
+
+    steps = tnw.plan_steps(pairs, sliced, mode)
+    n_steps = len(steps)
+    for _ in range(args.warmup):
+        m, e = call()
+
+    # one per-step profile pass to find the dominant launch step
+    evs = device_events(torch, stream, n_steps + 1)
+    flush.zero_()
+    call(prof_events=evs, prof_first=0)
+    torch.cuda.synchronize()
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(n_steps)]
+    dom = int(np.argmax(step_ms))
+
+    # timed region: K steps, each bracketed by events; L2 flushed between
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    dom_ev = [device_events(torch, stream, 2) for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        m, e = call(prof_events=dom_ev[i], prof_first=dom)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    call_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
+    dom_ms = [a.elapsed_time(b) for a, b in dom_ev]
+    total_ms = sum(call_ms)
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = flops_step * world * args.steps / (total_ms / 1e3) / 1e12
+    result, result_exp = scalar_value(m, e, cplx)
+    peaks = load_peaks()
+    roof = roofline(steps, dom, dom_ms, nodes, mode, ms_per_step, peaks)
 
     # end to end through the C-ABI with host buffers (copies inside the call)
     e2e = None
@@ -326,13 +431,13 @@ def main():
         hout = torch.empty(tnw.out_shape, dtype=odt).pin_memory()
         hexp = torch.empty((), dtype=torch.int64).pin_memory()
         for _ in range(args.warmup):
-            htn.contract(pairs, sliced, args.mode, out=hout, out_exp=hexp)
+            htn.contract(pairs, sliced, mode, out=hout, out_exp=hexp, slice_begin=sb, slice_count=sc)
         t_e2e = 0.0
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            htn.contract(pairs, sliced, args.mode, out=hout, out_exp=hexp)
+            htn.contract(pairs, sliced, mode, out=hout, out_exp=hexp, slice_begin=sb, slice_count=sc)
             t_e2e += time.perf_counter() - t0
         h2d = sum(int(t.numel()) * elem for t in hl)
         d2h = hout.numel() * hout.element_size() + 8
@@ -341,78 +446,285 @@ def main():
                "ms_per_step": t_e2e / args.steps * 1e3}
         htn.close()
 
-    cpu = None
-    rel_err = None
+    # the oracle on the host cores: timing and the reference value
+    cpu, rel_err, ref = None, None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, (om, oe) = oracle_baseline(net, pairs, sliced, info)
-        if cplx:
-            ref = complex(om)
-            rel_err = abs(result * 2.0 ** (result_exp - oe) - ref) / abs(ref)
+        if w["oracle"] == "full":
+            cpu, (om, oe) = oracle_full(net, pairs, sliced, info)
+            ref = (complex(om) if cplx else float(om), int(oe), sliced, 0, sc)
+            rel_err = rel_error(result, result_exp, ref[0], ref[1], cplx)
         else:
-            rel_err = abs(math.expm1(math.log(abs(result)) + (result_exp - oe) * math.log(2)
-                                     - math.log(abs(float(om)))))
+            cpu, (sl2, k, rm, re_) = oracle_subslices(net, pairs)
+            ref = (rm, re_, sl2, 0, k)
+            gm, ge = scalar_value(*tnw.contract(pairs, sl2, mode, slice_begin=0, slice_count=k), cplx)
+            rel_err = rel_error(gm, ge, rm, re_, cplx)
+            cpu["rel_err_sample"] = ("GPU vs oracle on the same sub-slices (the slice sample "
+                                     "itself is beyond the oracle's reach)")
 
+    # every precision mode on the same work (device buffers), with its error
     modes_cmp = None
-    if args.compare_modes and rank == 0:
+    if rank == 0 and not args.no_modes:
         modes_cmp = {}
-        ref_ln = None
-        if cpu is not None:
-            ref_ln = math.log(abs(float(om))) + oe * math.log(2) if not cplx else None
-        for md in ["fp32", "tf32_split", "bf16_split", "tf32_3m"]:
-            for _ in range(3):
-                mm_, ee_ = tnw.contract(pairs, sliced, md)
-            es, ee2 = events(args.steps), events(args.steps)
-            for i in range(args.steps):
+        reps = min(args.steps, 5) if args.workload == "circuit7x7" else args.steps
+        for md in MODES:
+            for _ in range(2):
+                call(md)
+            es, ee2 = device_events(torch, stream, reps), device_events(torch, stream, reps)
+            for i in range(reps):
                 flush.zero_()
                 es[i].record(stream)
-                mm_, ee_ = tnw.contract(pairs, sliced, md)
+                mm_, ee_ = call(md)
                 ee2[i].record(stream)
             torch.cuda.synchronize()
-            tms = sum(a.elapsed_time(b2) for a, b2 in zip(es, ee2)) / args.steps
-            entry = {"ms_per_network": tms, "tflops": flops_step / (tms / 1e3) / 1e12}
-            if cpu is not None:
-                if cplx:
-                    ref = complex(om)
-                    entry["rel_err"] = abs(complex(mm_.cpu()) * 2.0 ** (int(ee_.cpu()) - oe) - ref) / abs(ref)
-                else:
-                    entry["rel_err"] = abs(math.expm1(math.log(abs(float(mm_.cpu()))) +
-                                                      int(ee_.cpu()) * math.log(2) - ref_ln))
+            tms = sum(a.elapsed_time(b2) for a, b2 in zip(es, ee2)) / reps
+            entry = {"ms_per_step": tms, "tflops": flops_step / (tms / 1e3) / 1e12,
+                     "tol": MODE_TOL[md]}
+            if ref is not None:
+                rm, re_, rsl, rb, rc = ref
+                gm, ge = scalar_value(*tnw.contract(pairs, rsl, md, slice_begin=rb, slice_count=rc), cplx)
+                entry["rel_err"] = rel_error(gm, ge, rm, re_, cplx)
+                entry["within_tol"] = entry["rel_err"] <= MODE_TOL[md]
             modes_cmp[md] = entry
 
-    launches_per_step = sum(1 + (1 if (s["cfg"] in (1, 2, 3, 4, 5) and not s["wave"]) else 0)
-                            for s in steps) * info.d_sliced + 2 * info.d_sliced + 3
+    groups = sc
+    launches_per_call = 3 + groups * (3 + sum(s.get("launches", 1) for s in steps))
+    cfg = {"workload": WORKLOAD_NAMES[args.workload], "mode": mode, "W_s": info.W, "C": info.C,
+           "d_sliced": info.d_sliced, "slices_per_step": sc,
+           "flops_per_step": flops_step, "nodes": len(pairs),
+           "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+           "plan_kernels": {"generic": plan["n_generic"], "tiled": plan["n_tiled"],
+                            "tensor_core": plan["n_tensor_core"]},
+           "launch_steps": n_steps, "wave_steps": sum(1 for s in steps if s["wave"]),
+           "workspace_bytes": plan["ws_bytes"]}
+    cfg.update(w["config"])
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_vertices": 100, "beta": 0.3, "J": "+-1",
-                   "mode": args.mode, "W_s": info.W, "C": info.C, "d_sliced": info.d_sliced,
-                   "flops_per_network": flops_step, "nodes": n_nodes,
-                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                   "tree": "greedy (alpha=1, tau=0)",
-                   "plan_kernels": {"generic": plan["n_generic"], "tiled": plan["n_tiled"],
-                                    "tensor_core": plan["n_tensor_core"]},
-                   "launch_steps": n_steps,
-                   "wave_steps": sum(1 for s in steps if s["wave"])},
-        "s_per_network": ms_per_step / 1e3,
+        "dtype": "f32", "data": "synthetic", "config": cfg,
+        "s_per_network": ms_per_step / 1e3 * (info.d_sliced / sc),
         "rel_err_vs_oracle": rel_err,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": launches_per_call * args.steps,
         "modes": modes_cmp,
         "step_profile": [{"step": k, "kind": ["generic", "tile", "tcgen05"][s["kind"]],
                           "wave": s["wave"], "nodes": len(s["nodes"]), "ms": round(step_ms[k], 4)}
                          for k, s in enumerate(steps)],
         "clocks": clocks,
     }
+    if cplx:
+        line["s_per_amplitude"] = line["s_per_network"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     tnw.close()
+    return 0
+
+
+# --------------------------------------------------------------------------
+# batch workload: amplitudes of one circuit + many Ising networks
+# --------------------------------------------------------------------------
+
+def run_batch(args, torch, dist, rank, world, local):
+    import numpy as np
+    from paper_2002_01935_gb300 import binding, inputs, planner
+
+    mode = args.mode
+    t0 = time.perf_counter()
+    circ = inputs.random_circuit(6, 6, 12, seed=0)
+    bits = inputs.random_bitstrings(36, 1024, seed=1000)
+    n_amp = min(args.amplitudes, 1024)
+    sel = bits[rank * n_amp:(rank + 1) * n_amp] if (rank + 1) * n_amp <= 1024 else bits[:n_amp]
+    amp_nets = [inputs.circuit_network(circ, b) for b in sel]
+    a_pairs, _, a_info = planner.hyper_greedy(amp_nets[0].labels, amp_nets[0].dims, amp_nets[0].open,
+                                              trials=32, seed=0, target_width=None)
+    rng = np.random.default_rng(4242 + rank)
+    ising_n = [int(x) for x in rng.choice(np.arange(40, 161, 2), size=args.ising)]
+    ising_nets = [inputs.random_ising(n, seed=7000 + 1000 * rank + j) for j, n in enumerate(ising_n)]
+    ising_trees = [planner.greedy_tree(nt.labels, nt.dims, nt.open) for nt in ising_nets]
+    ising_info = [planner.tree_info(nt.labels, nt.dims, p, nt.open) for nt, p in zip(ising_nets, ising_trees)]
+    t_plan = time.perf_counter() - t0
+    nets = amp_nets + ising_nets
+    trees = [a_pairs] * n_amp + ising_trees
+    flops = [8.0 * a_info.C] * n_amp + [2.0 * i.C for i in ising_info]
+    flops_step = sum(flops)
+    # every leaf of the batch lives in one flat device buffer per dtype (16-byte
+    # aligned views), so the end-to-end leg needs one host->device copy each
+    flat = {}
+    for dt in (torch.complex64, torch.float32):
+        sizes = [-(-int(np.prod(np.shape(t))) // (2 if dt == torch.complex64 else 4)) *
+                 (2 if dt == torch.complex64 else 4)
+                 for nt in nets if (nt.is_complex == (dt == torch.complex64)) for t in nt.tensors]
+        flat[dt] = [torch.zeros(max(sum(sizes), 1), dtype=dt, device="cuda"),
+                    torch.zeros(max(sum(sizes), 1), dtype=dt).pin_memory(), 0]
+    handles, keep = [], []
+    for nt in nets:
+        dt = torch.complex64 if nt.is_complex else torch.float32
+        align = 2 if nt.is_complex else 4
+        dev, host, pos = flat[dt]
+        ts = []
+        for t in nt.tensors:
+            a = np.array(t, order="C")
+            sz = int(a.size)
+            host[pos:pos + sz] = torch.from_numpy(a.reshape(-1)).to(dt)
+            ts.append(dev[pos:pos + sz].view(a.shape))
+            pos += -(-sz // align) * align
+        flat[dt][2] = pos
+        keep.append(ts)
+    for dt in flat:
+        flat[dt][0].copy_(flat[dt][1])
+    for nt, ts in zip(nets, keep):
+        handles.append(binding.TensorNetwork(nt.labels, nt.dims, nt.open, ts, complex_=nt.is_complex))
+    batch = binding.Batch(handles, trees, mode)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        out, ex, lat = batch.contract()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    lats = []
+    clk = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        out, ex, lat = batch.contract()
+        ends[i].record(stream)
+        lats.append(lat)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    total_ms = sum(s.elapsed_time(t) for s, t in zip(starts, ends))
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = flops_step * world * args.steps / (total_ms / 1e3) / 1e12
+    L = np.stack([x.cpu().numpy() for x in lats]).astype(np.float64) / 1e6  # ms
+    la, li = L[:, :n_amp].ravel(), L[:, n_amp:].ravel()
+    pct = lambda x, q: float(np.percentile(x, q)) if x.size else None
+    out, ex = out.cpu().numpy(), ex.cpu().numpy()
+
+    # e2e: the same batch with every leaf copied from pinned host memory per step
+    e2e = None
+    if rank == 0:
+        h2d = sum(int(f[2]) * f[1].element_size() for f in flat.values())
+        t_e2e = 0.0
+        for i in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for dev, host, pos in flat.values():
+                if pos:
+                    dev[:pos].copy_(host[:pos], non_blocking=True)
+            o2, x2, _ = batch.contract()
+            o2h, x2h = o2.cpu(), x2.cpu()
+            if i >= args.warmup:
+                t_e2e += time.perf_counter() - t0
+        e2e = {"value": flops_step * args.steps / t_e2e / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(o2h.numel() * 8 + x2h.numel() * 8),
+               "ms_per_step": t_e2e / args.steps * 1e3,
+               "path": "all leaves copied host->device (one copy per dtype), one batch call, "
+                       "results read back"}
+
+    # the oracle: a sample of the Ising networks in full (amplitudes of 36 qubits
+    # are beyond its reach in a bench run; the sub-slice check covers them)
+    cpu, rel = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import tree
+        errs, t_or, fl_or, k = [], 0.0, 0.0, 0
+        t_all = time.perf_counter()
+        for j in range(len(ising_nets)):
+            if time.perf_counter() - t_all > 10.0:
+                break
+            t1 = time.perf_counter()
+            om, oe = tree.contract_net(ising_nets[j], ising_trees[j])
+            t_or += time.perf_counter() - t1
+            fl_or += flops[n_amp + j]
+            i = n_amp + j
+            errs.append(rel_error(float(out[i, 0]), int(ex[i]), float(om), int(oe), False))
+            k += 1
+        cpu = {"value": fl_or / t_or / 1e12, "unit": "TFLOP/s", "cores": tree.max_threads(),
+               "kind": "oracle", "sample": f"{k} of the {len(ising_nets)} Ising networks, full"}
+        rel = {"ising_max": max(errs) if errs else None, "ising_checked": k}
+        sub, (sl2, kk, rm, re_) = oracle_subslices(amp_nets[0], a_pairs, budget_s=6.0)
+        gm, ge = scalar_value(*handles[0].contract(a_pairs, sl2, mode, slice_begin=0, slice_count=kk), True)
+        rel["amplitude_subslices"] = rel_error(gm, ge, rm, re_, True)
+        rel["amplitude_sample"] = sub["sample"]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES["batch"], "mode": mode,
+                   "amplitudes": n_amp, "amplitude_sample_of": 1024, "circuit": "6x6, 12 cycles",
+                   "amplitude_tree": f"Hyper-Greedy 32 trials, W {a_info.W:g}, C {a_info.C:.3e}",
+                   "ising_networks": len(ising_nets), "ising_N": "even, uniform in [40, 160]",
+                   "flops_per_step": flops_step, "planning_s": round(t_plan, 2),
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+        "s_per_amplitude": (pct(la, 50) / 1e3) if n_amp else None,
+        "latency_ms": {"amplitude_p50": pct(la, 50), "amplitude_p99": pct(la, 99),
+                       "ising_p50": pct(li, 50), "ising_p99": pct(li, 99),
+                       "all_p50": pct(L.ravel(), 50), "all_p99": pct(L.ravel(), 99)},
+        "extrapolated_1024_amplitudes_s": ms_per_step / 1e3 * 1024 / max(n_amp, 1),
+        "rel_err_vs_oracle": rel,
+        "roofline": None,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for h in handles:
+        h.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="ising100", choices=list(WORKLOAD_NAMES))
+    ap.add_argument("--mode", default="tf32_split", choices=MODES)
+    ap.add_argument("--slices", type=int, default=2, help="circuit7x7: slices per step")
+    ap.add_argument("--amplitudes", type=int, default=8, help="batch: amplitudes per step")
+    ap.add_argument("--ising", type=int, default=256, help="batch: Ising networks per step")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-modes", action="store_true", help="skip the per-mode comparison")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    if args.workload == "batch":
+        rc = run_batch(args, torch, dist, rank, world, local)
+    else:
+        rc = run_network(args, torch, dist, rank, world, local)
     if dist:
         dist.destroy_process_group()
-    return 0
+    return rc
 
 
 if __name__ == "__main__":

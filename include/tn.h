@@ -268,8 +268,9 @@ tn_status tn_plan_info(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
  * Nodes (0..n_tensors-2, tree order) run in launch steps: a wave step runs
  * all small nodes of one tree level in one launch, a single step runs one
  * node.  *n_steps receives the number of steps; if cap >= *n_steps, then
- * step_info[4*s..4*s+3] = (is_wave, kernel kind 0 generic / 1 tiled /
- * 2 tensor core, tile configuration, number of nodes) and step_nodes lists
+ * step_info[5*s..5*s+4] = (is_wave, kernel kind 0 generic / 1 tiled /
+ * 2 tensor core, tile configuration, number of nodes, kernel launches of
+ * the step) and step_nodes lists
  * the nodes of step 0, then step 1, ... (n_tensors-1 entries in all; may be
  * NULL).  Errors as tn_plan_info.
  */

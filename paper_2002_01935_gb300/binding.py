@@ -200,21 +200,21 @@ def tn_plan_info(h: int, pairs, sliced, mode: int = TN_MODE_FP32) -> Dict[str, f
 
 def tn_plan_steps(h: int, pairs, sliced, mode: int = TN_MODE_FP32):
     """Launch steps of the per-slice sequence: list of dicts
-    (wave, kind, cfg, nodes)."""
+    (wave, kind, cfg, launches, nodes)."""
     tr = _tree(pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     ns = ctypes.c_int32(0)
     _check(_lib.tn_plan_steps(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
                               0, ctypes.byref(ns), None, None))
     n = ns.value
-    info = np.zeros(4 * max(n, 1), dtype=np.int32)
+    info = np.zeros(5 * max(n, 1), dtype=np.int32)
     nodes = np.zeros(max(len(pairs), 1), dtype=np.int32)
     _check(_lib.tn_plan_steps(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
                               n, ctypes.byref(ns), _p(info, ctypes.c_int32), _p(nodes, ctypes.c_int32)))
     out, pos = [], 0
     for s in range(n):
-        w, kind, cfg, cnt = info[4 * s:4 * s + 4].tolist()
-        out.append({"wave": bool(w), "kind": kind, "cfg": cfg,
+        w, kind, cfg, cnt, nl = info[5 * s:5 * s + 5].tolist()
+        out.append({"wave": bool(w), "kind": kind, "cfg": cfg, "launches": nl,
                     "nodes": nodes[pos:pos + cnt].tolist()})
         pos += cnt
     return out

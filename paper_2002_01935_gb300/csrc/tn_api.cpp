@@ -312,10 +312,12 @@ tn_status tn_plan_steps(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced
     for (size_t s = 0; s < p->steps.size(); ++s) {
         const tn::Step& stp = p->steps[s];
         const tn::Node& first = p->nodes[stp.nodes[0]];
-        step_info[4 * s + 0] = stp.wave;
-        step_info[4 * s + 1] = first.kind;
-        step_info[4 * s + 2] = stp.wave ? 0 : (first.kind == tn::kTiled ? first.tile.cfg : 0);
-        step_info[4 * s + 3] = (int32_t)stp.nodes.size();
+        step_info[5 * s + 0] = stp.wave;
+        step_info[5 * s + 1] = first.kind;
+        step_info[5 * s + 2] = stp.wave ? 0 : (first.kind == tn::kTiled ? first.tile.cfg : 0);
+        step_info[5 * s + 3] = (int32_t)stp.nodes.size();
+        // a split-K tiled node adds its fixed-order reduction launch
+        step_info[5 * s + 4] = 1 + (!stp.wave && first.kind == tn::kTiled && first.tile.split > 1 ? 1 : 0);
         if (step_nodes)
             for (int k : stp.nodes) step_nodes[pos++] = k;
     }
