@@ -1,0 +1,109 @@
+"""Slice sharding across ranks: the block partition and the one exchange
+that sums the partial (mantissa, exponent) results, run as world-size-2
+(and 3) gloo process groups on the host.  Each rank's partial comes from
+the FP64 oracle over its own slice block; the combined value must equal
+the oracle's sum over all slices."""
+import math
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_2002_01935_gb300 import inputs, planner, shard
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("d", [0, 1, 2, 7, 16, 1000])
+def test_slice_range_partitions(world, d):
+    seen = []
+    prev_end = 0
+    for r in range(world):
+        b, c = shard.slice_range(r, world, d)
+        assert b == prev_end and c >= 0
+        prev_end = b + c
+        seen.extend(range(b, b + c))
+    assert seen == list(range(d))
+    counts = [shard.slice_range(r, world, d)[1] for r in range(world)]
+    assert max(counts) - min(counts) <= 1
+
+
+def test_slice_range_rejects_bad_arguments():
+    for args in [(0, 0, 4), (2, 2, 4), (-1, 2, 4), (0, 2, -1)]:
+        with pytest.raises(ValueError):
+            shard.slice_range(*args)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, case, q):
+    import torch
+    import torch.distributed as dist
+    from oracle import tree
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        net, pairs, sliced, d = case()
+        b, c = shard.slice_range(rank, world, d)
+        if c:
+            m, e = tree.contract_net(net, pairs, sliced, slice_begin=b, slice_count=c)
+            m = np.asarray(m)
+        else:  # no slices on this rank: an exact zero
+            m, e = np.zeros([net.dims[l] for l in net.open], dtype=np.complex128), 0
+        mt = torch.from_numpy(np.ascontiguousarray(m, dtype=np.complex128))
+        out, ex = shard.combine(mt, int(e))
+        q.put((rank, out.numpy(), ex))
+    finally:
+        dist.destroy_process_group()
+
+
+def _ising_case():
+    net = inputs.random_ising(24, seed=3)
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    sliced = [l for l in sorted(net.dims) if l not in net.open][:3]
+    return net, pairs, sliced, 8
+
+
+def _open_case():
+    circ = inputs.random_circuit(2, 3, 4, seed=1)
+    net = inputs.circuit_network(circ, open_qubits=[0, 3])
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    sliced = [l for l in sorted(net.dims) if l not in net.open][:2]
+    return net, pairs, sliced, 4
+
+
+def _run(world, case):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, case, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    return sorted(res, key=lambda t: t[0])
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_combine_sums_slices_across_ranks(world):
+    from oracle import tree
+    for case in (_ising_case, _open_case):
+        net, pairs, sliced, d = case()
+        assert d == math.prod(net.dims[l] for l in sliced)
+        mo, eo = tree.contract_net(net, pairs, sliced)
+        ref = np.asarray(mo, dtype=np.complex128) * 2.0 ** eo
+        res = _run(world, case)
+        for rank, m, e in res:
+            got = m * 2.0 ** e
+            np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.max(np.abs(ref)))
+        # every rank ends with the same result
+        assert all(np.array_equal(res[0][1], r[1]) and res[0][2] == r[2] for r in res)
