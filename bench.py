@@ -14,8 +14,8 @@ Workloads (``--workload``):
               amplitude is extrapolated over all 2^k slices.
   batch       a bounded sample of amplitudes of a 6x6-qubit, 12-cycle circuit
               (one shared tree) plus 256 Ising networks with N even in
-              [40, 160], all in one captured launch sequence; per-network
-              completion latency p50 / p99.
+              [40, --ising-max-n], all in one captured launch sequence (unsliced);
+              per-network completion latency p50 / p99.
 
 Throughput = algorithmic FLOPs (8 C complex, 2 C real per slice, Eq.
 vertexcon) over device time.
@@ -540,7 +540,7 @@ def run_batch(args, torch, dist, rank, world, local):
     a_pairs, _, a_info = planner.hyper_greedy(amp_nets[0].labels, amp_nets[0].dims, amp_nets[0].open,
                                               trials=32, seed=0, target_width=None)
     rng = np.random.default_rng(4242 + rank)
-    ising_n = [int(x) for x in rng.choice(np.arange(40, 161, 2), size=args.ising)]
+    ising_n = [int(x) for x in rng.choice(np.arange(40, args.ising_max_n + 1, 2), size=args.ising)]
     ising_nets = [inputs.random_ising(n, seed=7000 + 1000 * rank + j) for j, n in enumerate(ising_n)]
     ising_trees = [planner.greedy_tree(nt.labels, nt.dims, nt.open) for nt in ising_nets]
     ising_info = [planner.tree_info(nt.labels, nt.dims, p, nt.open) for nt, p in zip(ising_nets, ising_trees)]
@@ -664,7 +664,8 @@ def run_batch(args, torch, dist, rank, world, local):
         "config": {"workload": WORKLOAD_NAMES["batch"], "mode": mode,
                    "amplitudes": n_amp, "amplitude_sample_of": 1024, "circuit": "6x6, 12 cycles",
                    "amplitude_tree": f"Hyper-Greedy 32 trials, W {a_info.W:g}, C {a_info.C:.3e}",
-                   "ising_networks": len(ising_nets), "ising_N": "even, uniform in [40, 160]",
+                   "ising_networks": len(ising_nets),
+                   "ising_N": f"even, uniform in [40, {args.ising_max_n}]",
                    "flops_per_step": flops_step, "planning_s": round(t_plan, 2),
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
         "s_per_amplitude": (pct(la, 50) / 1e3) if n_amp else None,
@@ -697,6 +698,8 @@ def main():
     ap.add_argument("--slices", type=int, default=2, help="circuit7x7: slices per step")
     ap.add_argument("--amplitudes", type=int, default=8, help="batch: amplitudes per step")
     ap.add_argument("--ising", type=int, default=256, help="batch: Ising networks per step")
+    ap.add_argument("--ising-max-n", type=int, default=100,
+                    help="batch: largest Ising N (even N uniform in [40, this])")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip the per-mode comparison")

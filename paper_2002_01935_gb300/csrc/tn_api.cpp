@@ -317,7 +317,9 @@ tn_status tn_plan_steps(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced
         step_info[5 * s + 2] = stp.wave ? 0 : (first.kind == tn::kTiled ? first.tile.cfg : 0);
         step_info[5 * s + 3] = (int32_t)stp.nodes.size();
         // a split-K tiled node adds its fixed-order reduction launch
-        step_info[5 * s + 4] = 1 + (!stp.wave && first.kind == tn::kTiled && first.tile.split > 1 ? 1 : 0);
+        step_info[5 * s + 4] = stp.wave ? 1
+                               : first.kind == tn::kTensorCore ? tn::tc_launches(first.tile)
+                               : 1 + (first.kind == tn::kTiled && first.tile.split > 1 ? 1 : 0);
         if (step_nodes)
             for (int k : stp.nodes) step_nodes[pos++] = k;
     }

@@ -205,6 +205,8 @@ tn_status alloc_batch(BatchPlan& b, std::string& err) {
             }
         }
     }
+    b.max_leaf_floats = 0;
+    for (int64_t x : nf) b.max_leaf_floats = std::max(b.max_leaf_floats, x);
     if (!ck(cudaMemcpy(b.leaf_nfloat_dev, nf.data(), sizeof(int64_t) * b.n_leaves, cudaMemcpyHostToDevice),
             "cudaMemcpy"))
         return TN_ECUDA;
@@ -231,7 +233,8 @@ static cudaError_t enqueue_batch(BatchPlan& b, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b.t_done, 0, sizeof(unsigned long long) * N, s)) != cudaSuccess) return e;
     if ((e = launch_batch_start(b.t_start, s)) != cudaSuccess) return e;
-    if ((e = launch_leaf_max(b.leaf_ptr_dev, b.leaf_nfloat_dev, b.leafmax, b.n_leaves, s)) != cudaSuccess)
+    if ((e = launch_leaf_max(b.leaf_ptr_dev, b.leaf_nfloat_dev, b.leafmax, b.n_leaves, s, b.max_leaf_floats)) !=
+        cudaSuccess)
         return e;
     if ((e = launch_begin_call(b.ctl, 0, 1, nullptr, 0, s)) != cudaSuccess) return e;
     for (const BatchStep& st : b.steps) {

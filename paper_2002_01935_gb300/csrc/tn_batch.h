@@ -26,6 +26,7 @@ struct BatchPlan {
     std::vector<int> slot_base, leaf_base, desc_base;
     int64_t ws_bytes = 0, split_bytes = 0;
     int n_slots = 0, n_leaves = 0;
+    int64_t max_leaf_floats = 0;
     std::vector<TileArgs> descs;
     std::vector<GenericArgs> gen;
     std::vector<BatchStep> steps;

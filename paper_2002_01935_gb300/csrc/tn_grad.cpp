@@ -109,16 +109,8 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
             G.g.vstride[NV + child] = nd.stride;
             nd.kind = kGeneric;
             const int ca0 = nd.tile.conj_a, cb0 = nd.tile.conj_b;
-            if (plan_tile_node(d, G.g, nd, split_elems)) {
-                const TileArgs& t = nd.tile;
-                const int nn_min = d.is_complex() ? 6 : 7;
-                if (f.mode != TN_MODE_FP32 && t.cfg != kTileDot && t.nm >= 7 && t.nn >= nn_min &&
-                    t.nk >= 4 && t.nbatch <= 65535) {
-                    nd.kind = kTensorCore;
-                    nd.tile.split = 1;
-                    nd.tile.kchunk = int64_t(1) << t.nk;
-                }
-            }
+            if (plan_tile_node(d, G.g, nd, split_elems) && !f.no_tensor_cores)
+                make_tensor_core(d, f.mode, nd, split_elems);
             nd.tile.conj_a = ca0;
             nd.tile.conj_b = cb0;
             nd.ws_off = take(nd.size);
@@ -128,11 +120,17 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
         }
     }
     // forward split-K buffers count too
-    for (const auto& nd : G.fwd)
+    for (const auto& nd : G.fwd) {
         if (nd.kind == kTiled && nd.tile.split > 1)
             split_elems = std::max(split_elems, (int64_t)nd.tile.split * nd.tile.nbatch *
                                                     (int64_t(1) << (nd.tile.nm + nd.tile.nn)));
-    G.split_bytes = split_elems * (int64_t)d.elem_bytes();
+        if (nd.kind == kTensorCore) {
+            const int prec = f.mode == TN_MODE_BF16_SPLIT ? 2 : (f.mode == TN_MODE_TF32_SPLIT ? 1 : 0);
+            const int64_t eb = d.elem_bytes();
+            split_elems = std::max(split_elems, (tc_geom(nd.tile, d.is_complex(), prec).total + eb - 1) / eb);
+        }
+    }
+    G.split_bytes = (split_elems * (int64_t)d.elem_bytes() + 1023) / 1024 * 1024;
     G.ws_elems = std::max<int64_t>(off, 64);
     // scale slots: forward node k -> k; adjoint of vertex v -> nn + v (root last)
     G.n_slots = nn + NV;
@@ -310,7 +308,9 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int64_t a
         if (nd.cb >= 0 && nd.cb < n) G.gen_b[j].B = G.tile_b[j].B = lp[nd.cb];
     }
     CK(cudaMemcpyAsync(G.leaf_ptr_dev, lp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, stream));
-    CK(launch_leaf_max(G.leaf_ptr_dev, G.leaf_nfloat_dev, G.leafmax, n, stream));
+    int64_t mx_leaf = 0;
+    for (int v = 0; v < n; ++v) mx_leaf = std::max(mx_leaf, d.leaves[v].size * (d.is_complex() ? 2 : 1));
+    CK(launch_leaf_max(G.leaf_ptr_dev, G.leaf_nfloat_dev, G.leafmax, n, stream, mx_leaf));
     // root adjoint: caller's FP64 array (open labels in tn_create order) ->
     // root layout, normalised to a power-of-two scaled float tensor
     const Node& root = G.fwd.back();

@@ -118,9 +118,56 @@ struct alignas(16) TileArgs {
                           // leaf pointer table in wave launches), else -1
     int conj_a, conj_b;   // read the operand complex-conjugated (reverse sweep)
     unsigned long long* t_done;  // root of a batched network: completion time (ns)
-    int pad_;
+    int tc_swap;          // tensor-core node: B plays the row role (see TcGeom)
     InstanceInfo in;
 };
+
+// Packed operands of a tensor-core node, in the shared P buffer (per
+// instance, p_is elements of the node's dtype apart).  The "row" operand R
+// (A, or B when tc_swap) holds [batch x rows] x KR and the "column" operand
+// Q (the other one) [batch x cols] x KR, K-major: a complex R stores
+// (re, im) pairs along K (KR = 2K), a complex Q is expanded to two real rows
+// per column, (re, -im) and (im, re), so that one real GEMM forms the
+// complex product (4M).  Each plane is cut into 16 KB tiles of 128 rows x
+// one 128-byte swizzled row of K (the shared-memory image the MMA reads),
+// stored row tile by row tile and, within one, k-block by k-block, so that
+// one k-block of one operand is a single contiguous bulk copy.  Split
+// precisions store a hi plane then a lo plane.  With a K split (split > 1)
+// the FP32 partial products [split][batch][M][N] follow the packed planes.
+struct TcGeom {
+    int64_t rows_r;    // rows of R per batch entry
+    int64_t cols_q;    // real rows of Q per batch entry
+    int64_t kr;        // packed row length (elements) before padding
+    int ke;            // elements per 128-byte row (32 TF32, 64 BF16)
+    int64_t nkb;       // k-blocks (KR padded up to a multiple of ke)
+    int esz;           // bytes per packed element (4 TF32, 2 BF16)
+    int parts;         // 1, or 2 for hi + lo
+    int64_t plane_r;   // bytes of one R plane
+    int64_t plane_q;   // bytes of one Q plane
+    int64_t region_r;  // bytes of all R planes, 1 KB aligned (Q starts here)
+    int64_t part_off;  // bytes: start of the split-K partials
+    int64_t total;     // bytes per instance, 1 KB aligned
+};
+
+__host__ __device__ inline TcGeom tc_geom(const TileArgs& a, bool cplx, int prec) {
+    TcGeom g;
+    const int c = cplx ? 2 : 1;
+    g.rows_r = int64_t(1) << (a.tc_swap ? a.nn : a.nm);
+    g.cols_q = (int64_t(1) << (a.tc_swap ? a.nm : a.nn)) * c;
+    g.kr = (int64_t(1) << a.nk) * c;
+    g.esz = prec == 2 ? 2 : 4;
+    g.ke = 128 / g.esz;
+    g.nkb = (g.kr + g.ke - 1) / g.ke;
+    g.parts = prec == 0 ? 1 : 2;
+    g.plane_r = a.nbatch * g.rows_r * g.nkb * 128;
+    g.plane_q = a.nbatch * g.cols_q * g.nkb * 128;
+    g.region_r = (g.parts * g.plane_r + 1023) / 1024 * 1024;
+    g.part_off = g.region_r + (g.parts * g.plane_q + 1023) / 1024 * 1024;
+    const int64_t parts_bytes =
+        a.split > 1 ? (int64_t)a.split * a.nbatch * (int64_t(1) << (a.nm + a.nn)) * 4 * c : 0;
+    g.total = g.part_off + (parts_bytes + 1023) / 1024 * 1024;
+    return g;
+}
 
 // One CTA of a wave launch: outputs [o_begin, o_begin + o_count) of node.
 struct WaveItem {
@@ -185,7 +232,10 @@ cudaError_t launch_leaf_grad(const LeafGradArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s);  // tn_tiled.cu
 // Tensor-core node (tn_tc.cu): prec 0 TF32, 1 TF32 hi+lo, 2 BF16 hi+lo.
+// Packs both operands into a.P (TcGeom) and runs the bulk-copy-fed tcgen05
+// GEMM: three launches, plus a fixed-order reduction with a K split.
 cudaError_t launch_tc(const TileArgs& a, int prec, bool is_c, cudaStream_t s);
+inline int tc_launches(const TileArgs& a) { return a.split > 1 ? 4 : 3; }
 // All small nodes of one tree level in one launch (tn_tiled.cu).
 cudaError_t launch_wave(const WaveItem* items, int n_items, const TileArgs* descs,
                         const void* const* leaf_ptrs, bool is_c, cudaStream_t s);
@@ -196,6 +246,6 @@ cudaError_t launch_begin_slice(unsigned* maxabs, int n_nodes, cudaStream_t s);
 cudaError_t launch_advance(Control* ctl, cudaStream_t s, int step = 1);
 cudaError_t launch_finalize(Control* ctl, int parity, cudaStream_t s);
 cudaError_t launch_leaf_max(const float* const* ptrs, const int64_t* nfloat, unsigned* out, int n,
-                            cudaStream_t s);
+                            cudaStream_t s, int64_t max_nfloat);
 
 }  // namespace tn

@@ -175,13 +175,18 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ Accu
     }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
+        if (!any) continue;
         int64_t src = 0, rem = o;
         for (int i = 0; i < a.n_od; ++i) {
-            int64_t d = a.od_dim[i];
-            src += (rem % d) * a.od_s[i];
-            rem /= d;
+            const int64_t d = a.od_dim[i];
+            if ((d & (d - 1)) == 0) {  // power of two: mask and shift
+                src += (rem & (d - 1)) * a.od_s[i];
+                rem >>= __ffsll(d) - 1;
+            } else {
+                src += (rem % d) * a.od_s[i];
+                rem /= d;
+            }
         }
-        if (!any) continue;
         double vr = 0.0, vi = 0.0;
         if (CPLX) {
             const double2 v = reinterpret_cast<double2*>(a.acc)[o];
@@ -258,16 +263,20 @@ cudaError_t launch_advance(Control* ctl, cudaStream_t s, int step) {
     return cudaGetLastError();
 }
 
-// Largest |component| of every leaf (one block per leaf), so that leaves are
-// renormalised like intermediates before their first contraction.
+// Largest |component| of every leaf, so that leaves are renormalised like
+// intermediates before their first contraction.  blockIdx.x: leaf,
+// blockIdx.y: one of gridDim.y interleaved parts of it; parts combine by
+// atomicMax on the float bits (non-negative floats order like unsigned).
 __global__ void __launch_bounds__(256) k_leaf_max(const float* const* ptrs, const int64_t* nfloat,
                                                   unsigned* out, int n) {
     int v = blockIdx.x;
     if (v >= n) return;
     const float* p = ptrs[v];
     int64_t m = nfloat[v];
+    const int64_t first = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    if ((int64_t)blockIdx.y * blockDim.x >= m && blockIdx.y > 0) return;
     float lmax = 0.f;
-    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) lmax = fmaxf(lmax, fabsf(p[i]));
+    for (int64_t i = first; i < m; i += (int64_t)gridDim.y * blockDim.x) lmax = fmaxf(lmax, fabsf(p[i]));
     __shared__ float red[32];
     for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lmax;
@@ -276,14 +285,18 @@ __global__ void __launch_bounds__(256) k_leaf_max(const float* const* ptrs, cons
         int nw = blockDim.x >> 5;
         lmax = threadIdx.x < nw ? red[threadIdx.x] : 0.f;
         for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-        if (threadIdx.x == 0) out[v] = __float_as_uint(lmax);
+        if (threadIdx.x == 0) atomicMax(&out[v], __float_as_uint(lmax));
     }
 }
 
 cudaError_t launch_leaf_max(const float* const* ptrs, const int64_t* nfloat, unsigned* out, int n,
-                            cudaStream_t s) {
+                            cudaStream_t s, int64_t max_nfloat) {
     if (n <= 0) return cudaSuccess;
-    k_leaf_max<<<n, 256, 0, s>>>(ptrs, nfloat, out, n);
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned) * (size_t)n, s);
+    if (e != cudaSuccess) return e;
+    int64_t parts = (max_nfloat + 32767) / 32768;
+    parts = parts < 1 ? 1 : (parts > 256 ? 256 : parts);
+    k_leaf_max<<<dim3((unsigned)n, (unsigned)parts), 256, 0, s>>>(ptrs, nfloat, out, n);
     return cudaGetLastError();
 }
 

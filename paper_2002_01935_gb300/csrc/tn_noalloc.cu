@@ -20,6 +20,7 @@
 // different streams, or from several threads) race on the array.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -190,7 +191,9 @@ tn_status run_noalloc(const NetDesc& d, const Plan& p, void* out, int out_mem, i
 
     // the call: leaf maxima, control block and accumulator cleared, then
     // every slice in order, then the result
-    CK(launch_leaf_max(lptr, lnf, leafmax, n, stream));
+    int64_t mx_leaf = 0;
+    for (int v = 0; v < n; ++v) mx_leaf = std::max(mx_leaf, d.leaves[v].size * (d.is_complex() ? 2 : 1));
+    CK(launch_leaf_max(lptr, lnf, leafmax, n, stream, mx_leaf));
     CK(launch_begin_call(ctl, 0, p.d_sliced, acc, (int64_t)acc_doubles, stream));
     for (int64_t s = 0; s < p.d_sliced; ++s) {
         CK(launch_begin_slice(maxabs, nn, stream));

@@ -443,16 +443,9 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
         Node& nd = p.nodes[k];
         nd.kind = kGeneric;
         if (p.force_generic || !plan_tile(d, p, nd, split_elems)) continue;
-        const TileArgs& t = nd.tile;
-        const int nn_min = d.is_complex() ? 6 : 7;
-        if (p.mode != TN_MODE_FP32 && !p.no_tensor_cores && t.cfg != kTileDot && t.nm >= 7 &&
-            t.nn >= nn_min && t.nk >= 4 && t.nbatch <= 65535) {
-            nd.kind = kTensorCore;
-            nd.tile.split = 1;
-            nd.tile.kchunk = int64_t(1) << t.nk;
-        }
+        if (!p.no_tensor_cores) make_tensor_core(d, p.mode, nd, split_elems);
     }
-    p.split_bytes = split_elems * (int64_t)d.elem_bytes();
+    p.split_bytes = (split_elems * (int64_t)d.elem_bytes() + 1023) / 1024 * 1024;
     // ---- launch schedule: tree levels; per level one wave launch for the
     // small tiled nodes, then one launch per remaining node
     std::vector<int> level(2 * n, 0);
@@ -905,6 +898,12 @@ static tn_status ensure_graph(const NetDesc& d, Plan& p, const std::vector<const
     return TN_OK;
 }
 
+static int64_t max_leaf_floats(const NetDesc& d) {
+    int64_t m = 0;
+    for (int v = 0; v < d.n; ++v) m = std::max(m, d.leaves[v].size * (d.is_complex() ? 2 : 1));
+    return m;
+}
+
 static tn_status upload_leaf_sizes(const NetDesc& d, Plan& p, int G, const std::vector<int64_t>& leaf_is,
                                    std::string& err) {
     std::vector<int64_t> nf(d.n);
@@ -958,7 +957,7 @@ tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count
     std::vector<const void*> lp;
     st = prepare_leaves(d, p, capturing, lp, stream, err);
     if (st != TN_OK) return st;
-    CK(launch_leaf_max(p.leaf_ptr_dev, p.leaf_nfloat_dev, p.leafmax, n, stream));
+    CK(launch_leaf_max(p.leaf_ptr_dev, p.leaf_nfloat_dev, p.leafmax, n, stream, max_leaf_floats(d)));
     CK(launch_begin_call(p.ctl, begin, begin + count, p.acc, p.n_out * (d.is_complex() ? 2 : 1), stream));
     const int64_t groups = (count + G - 1) / G;
     const bool use_graph = !o.no_graph && !capturing;
@@ -1025,7 +1024,7 @@ tn_status run_instances(NetDesc& d, Plan& p, void* unit, int n_inst, const int64
     std::vector<const void*> lp;
     st = prepare_leaves(d, p, false, lp, stream, err);
     if (st != TN_OK) return st;
-    CK(launch_leaf_max(p.leaf_ptr_dev, p.leaf_nfloat_dev, p.leafmax, n, stream));
+    CK(launch_leaf_max(p.leaf_ptr_dev, p.leaf_nfloat_dev, p.leafmax, n, stream, max_leaf_floats(d)));
     CK(launch_begin_call(p.ctl, 0, 1, p.acc, 0, stream));
     st = ensure_graph(d, p, lp, 0, 0, err);
     if (st != TN_OK) return st;
@@ -1042,6 +1041,48 @@ tn_status run_instances(NetDesc& d, Plan& p, void* unit, int n_inst, const int64
 tn_status make_generic_args_node(const NetDesc& d, const Plan& p, const Node& nd, GenericArgs& g,
                                  std::string& err) {
     return fill_generic(d, p, nd, g, err);
+}
+
+// Tensor-core choice for a tiled node in a reduced-precision mode: the
+// GEMM tile needs >= 128 accumulator rows, >= 128 real accumulator columns
+// and K >= 16.  A complex node puts its larger operand in the row role (the
+// column operand is expanded to two real rows per column).  The packed
+// operands live in the shared P buffer, which grows to hold them.
+bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_elems) {
+    TileArgs& t = nd.tile;
+    if (mode == TN_MODE_FP32 || t.cfg == kTileDot || t.nk < 4 || t.nbatch > 65535) return false;
+    const bool c = d.is_complex();
+    int swap = 0;
+    if (c) {
+        if (std::max(t.nm, t.nn) < 7 || std::min(t.nm, t.nn) < 6) return false;
+        swap = t.nn > t.nm ? 1 : 0;
+    } else if (t.nm < 7 || t.nn < 7) {
+        return false;
+    }
+    t.tc_swap = swap;
+    t.split = 1;
+    t.kchunk = int64_t(1) << t.nk;
+    const int prec = mode == TN_MODE_BF16_SPLIT ? 2 : (mode == TN_MODE_TF32_SPLIT ? 1 : 0);
+    // K split: the grid should fill whole waves of the 152 SMs (one CTA
+    // each); split only while every part keeps >= 8 k-blocks
+    {
+        const TcGeom g0 = tc_geom(t, c, prec);
+        const double tiles = (double)t.nbatch * (g0.rows_r / 128) * (g0.cols_q / 128);
+        double best = 0.0;
+        for (int s = 1; s <= 16 && g0.nkb / s >= 8; s *= 2) {
+            const double w = tiles * s / 152.0;
+            const double eff = w / std::ceil(w);
+            if (eff > best + 0.03) {
+                best = eff;
+                t.split = s;
+            }
+        }
+        if (t.nbatch * (int64_t)t.split > 65535) t.split = 1;
+    }
+    const int64_t eb = d.elem_bytes();
+    split_elems = std::max(split_elems, (tc_geom(t, c, prec).total + eb - 1) / eb);
+    nd.kind = kTensorCore;
+    return true;
 }
 
 bool plan_tile_node(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems) {

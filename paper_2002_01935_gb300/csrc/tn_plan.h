@@ -119,6 +119,7 @@ struct Plan {
 tn_status build_plan(const NetDesc& d, Plan& p, std::string& err);
 Node build_node(const NetDesc& d, const Plan& p, int id, int a, int b, const std::vector<int>& keep);
 bool plan_tile_node(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems);
+bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_elems);
 tn_status make_generic_args_node(const NetDesc& d, const Plan& p, const Node& nd, GenericArgs& g,
                                  std::string& err);
 tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err);

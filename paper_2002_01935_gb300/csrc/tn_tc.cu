@@ -1,29 +1,39 @@
-// tn_tc.cu -- tensor-core node kernel (tcgen05 + TMEM) for large nodes.
+// tn_tc.cu -- tensor-core path for large nodes (tcgen05 + TMEM + TMA).
 //
 // A large tree node (Sec. 2 of arXiv 2002.01935: the inner product of two
-// tensors over their shared labels) is a batched GEMM C[b] = A[b] B[b]
-// whose operands are read through the same bit-scatter offsets as the
-// CUDA-core tile kernel.  Here the product runs on the 5th-generation
-// tensor cores:
-//   * four producer warps gather A and B tiles from global memory, split
-//     each value into hi + lo parts (TF32 or BF16, round to nearest), and
-//     store them into shared memory in the K-major, 128-byte-swizzled
-//     layout that tcgen05.mma reads;
-//   * one MMA warp issues tcgen05.mma (kind::tf32 or kind::f16 with BF16)
-//     into an FP32 accumulator tile in tensor memory: hi*hi + hi*lo +
-//     lo*hi for the split modes, a single product otherwise;
-//   * the producer warps then read the accumulator with tcgen05.ld, apply
-//     the power-of-two renormalisation and write C.
-// Complex nodes use one real GEMM with K doubled (4M): A is read as
-// interleaved (re, im) pairs along K, and B is expanded in shared memory
-// into rows (Re B, -Im B) and (Im B, Re B), so the accumulator holds
-// interleaved (re, im) outputs.
-// Every mbarrier wait is bounded; on timeout the kernel records TN_ETIMEOUT
-// in the control block, waits (bounded) for its MMAs, frees its tensor
-// memory and returns.
+// tensors over their shared labels) is a batched GEMM C[b] = A[b] B[b].
+// It runs in three launches:
+//   1. k_pack (row operand R) and 2. k_pack (column operand Q): a bit
+//      permutation of the operand into K-major packed rows (TcGeom), staged
+//      through shared memory so that both the read of the source layout and
+//      the write of the packed layout are coalesced; the same pass applies
+//      the slice offset of a sliced leaf, the power-of-two renormalisation,
+//      the complex conjugation of the reverse sweep, the hi/lo split (TF32
+//      round-to-nearest-away, or BF16 round-to-nearest) and, for a complex Q,
+//      the expansion into the rows (Re, -Im) and (Im, Re).
+//   3. k_umma: a warp-specialised GEMM.  One thread streams 128-row x
+//      128-byte tiles of R and Q into a ring of shared-memory stages with
+//      TMA (cp.async.bulk.tensor, 128-byte swizzle); one thread issues
+//      tcgen05.mma (kind::tf32, or kind::f16 with BF16 operands) into FP32
+//      accumulators in tensor memory -- hi*hi + hi*lo + lo*hi for the split
+//      precisions -- rotating over up to four accumulators along K, which
+//      the epilogue sums in a fixed order; four epilogue warps read them
+//      with tcgen05.ld, undo the residual scale, reduce the node maximum
+//      and write C in the node's [batch][M][N] layout.
+// Complex nodes use one real GEMM with K doubled (4M): R holds interleaved
+// (re, im) pairs along K and Q's expanded rows turn each accumulator column
+// pair into (Re C, Im C).  The larger complex operand plays R (it is not
+// expanded); when that is B the accumulator rows run over N and the
+// epilogue writes the transpose.
+// Every wait is bounded; on timeout the kernel records TN_ETIMEOUT in the
+// control block, waits (bounded) for its copies and MMAs in flight, frees
+// its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
+#include <type_traits>
 
 #include "../../include/tn.h"
 #include "tn_internal.h"
@@ -32,13 +42,17 @@ namespace tn {
 
 namespace {
 
-constexpr int kBM = 128;          // accumulator rows (TMEM lanes)
-constexpr int kBN = 128;          // accumulator columns (real)
-constexpr int kRowBytes = 128;    // one swizzle row per stage and operand
-constexpr int kTileBytes = kBM * kRowBytes;  // 16 KB per operand part
-constexpr int kProducers = 512;   // 16 warps
-constexpr int kThreads = kProducers + 32;
+constexpr int kBM = 128;              // accumulator rows (TMEM lanes) per tile
+constexpr int kBN = 128;              // real accumulator columns per tile
+constexpr int kRowBytes = 128;        // one swizzle row per stage and plane
+constexpr int kTileBytes = kBM * kRowBytes;  // 16 KB per plane and operand
+constexpr int kGemmThreads = 192;     // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kNumAcc = 4;            // TMEM accumulators (128 columns each) in rotation
+constexpr int kGroupRows = 16;        // row tiles per raster group (L2 reuse)
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+constexpr int kPackThreads = 256;
+constexpr int kPackLow = 5;           // lowest bits of each order staged per tile
+constexpr int kPackMaxTile = 1 << (2 * kPackLow);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -143,6 +157,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Add 32 accumulator columns (two x16 loads, one wait) into s[0..31].
+__device__ __forceinline__ void tmem_add32(uint32_t taddr, float* s) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr + 16u));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) s[i] += __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ int64_t scatter(uint64_t x, const uint8_t* sh, int nbits) {
     int64_t o = 0;
     for (int i = 0; i < nbits; ++i)
@@ -165,6 +201,7 @@ __device__ __forceinline__ int exp_of(const unsigned* slot) {
     return e;
 }
 
+
 // Round to TF32 (10 explicit mantissa bits), nearest with ties away.
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;
@@ -172,92 +209,327 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
-// 16-byte chunk position of (row, chunk) in a 128B-swizzled K-major tile.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One contiguous global -> shared bulk copy (TMA engine), completing on bar.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// One packed element: the split parts of a value (TF32 keeps float bit
+// patterns with the low 13 mantissa bits zero; BF16 is round to nearest).
+template <int PREC>
+struct Parts;
+template <>
+struct Parts<0> {
+    using E = float;
+    static __device__ __forceinline__ void split(float x, E& h, E& l) {
+        h = to_tf32(x);
+        l = 0.f;
+    }
+};
+template <>
+struct Parts<1> {
+    using E = float;
+    static __device__ __forceinline__ void split(float x, E& h, E& l) {
+        h = to_tf32(x);
+        l = to_tf32(x - h);
+    }
+};
+template <>
+struct Parts<2> {
+    using E = __nv_bfloat16;
+    static __device__ __forceinline__ void split(float x, E& h, E& l) {
+        h = __float2bfloat16_rn(x);
+        l = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+};
+
+// 16-byte chunk position of (row, chunk) in a 128B-swizzled K-major tile
+// (the layout of a TMA 128-byte swizzle and of the UMMA descriptors below).
 __device__ __forceinline__ uint32_t swz(int row, int chunk) {
     return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
 }
 
-// hi/lo parts of four real values into 16 bytes each (TF32: 4 floats).
-template <bool BF16>
-struct Pack;
-template <>
-struct Pack<false> {
-    // 4 values -> one 16B chunk
-    static __device__ __forceinline__ void split4(const float* x, uint4& hi, uint4& lo, bool split) {
-        float h[4], l[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            h[i] = to_tf32(x[i]);
-            l[i] = split ? to_tf32(x[i] - h[i]) : 0.f;
-        }
-        hi = make_uint4(__float_as_uint(h[0]), __float_as_uint(h[1]), __float_as_uint(h[2]),
-                        __float_as_uint(h[3]));
-        lo = make_uint4(__float_as_uint(l[0]), __float_as_uint(l[1]), __float_as_uint(l[2]),
-                        __float_as_uint(l[3]));
+// Byte position of packed element (row, k) in a plane of 16 KB tiles
+// (128 rows x one 128-byte swizzled row of K each, row tile by row tile,
+// k-block by k-block within one).
+__device__ __forceinline__ int64_t tile_pos(int64_t row, int64_t k, int64_t nkb, int lg_ke, int lg_esz) {
+    const int64_t tile = (row >> 7) * nkb + (k >> lg_ke);
+    const int byte = (int)(k & ((1 << lg_ke) - 1)) << lg_esz;
+    return tile * kTileBytes + swz((int)(row & 127), byte >> 4) + (byte & 15);
+}
+
+// Write the packed elements (x, y) (adjacent along K) at byte position pos
+// of the hi plane and of the lo plane lo_off bytes later.
+template <int PREC>
+__device__ __forceinline__ void put2(char* hi, int64_t lo_off, int64_t pos, float x, float y) {
+    using P = Parts<PREC>;
+    typename P::E hx, lx, hy, ly;
+    P::split(x, hx, lx);
+    P::split(y, hy, ly);
+    if constexpr (PREC == 2) {
+        __nv_bfloat162 h, l;
+        h.x = hx; h.y = hy; l.x = lx; l.y = ly;
+        *reinterpret_cast<__nv_bfloat162*>(hi + pos) = h;
+        *reinterpret_cast<__nv_bfloat162*>(hi + lo_off + pos) = l;
+    } else {
+        *reinterpret_cast<float2*>(hi + pos) = make_float2(hx, hy);
+        if constexpr (PREC == 1) *reinterpret_cast<float2*>(hi + lo_off + pos) = make_float2(lx, ly);
     }
-};
-template <>
-struct Pack<true> {
-    // 8 values -> one 16B chunk
-    static __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
-        uint32_t h[4], l[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]);
-            __nv_bfloat16 h1 = __float2bfloat16_rn(x[2 * i + 1]);
-            __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
-            __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
-            h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-        }
-        hi = make_uint4(h[0], h[1], h[2], h[3]);
-        lo = make_uint4(l[0], l[1], l[2], l[3]);
-    }
-};
+}
+
+template <int PREC>
+__device__ __forceinline__ void put1(char* hi, int64_t lo_off, int64_t pos, float x) {
+    using P = Parts<PREC>;
+    typename P::E h, l;
+    P::split(x, h, l);
+    *reinterpret_cast<typename P::E*>(hi + pos) = h;
+    if constexpr (PREC != 0) *reinterpret_cast<typename P::E*>(hi + lo_off + pos) = l;
+}
 
 }  // namespace
 
-// PREC: 0 = TF32 single product, 1 = TF32 hi+lo (3 products),
-//       2 = BF16 hi+lo (3 products).
+// ---------------------------------------------------------------------------
+// k_pack: operand (role 0 = R, 1 = Q) -> packed K-major planes.
+//
+// Logical element index g (the packed order): K bits fastest, then the
+// row/column bits of the operand, then the batch bits.  The source offset
+// of g scatters each logical bit to the operand's own stride.  A tile is
+// the set of logical bits holding the kPackLow lowest source strides and
+// the kPackLow lowest packed positions; the remaining bits enumerate the
+// tiles.  Each tile is read in source order (consecutive threads read
+// consecutive source addresses), staged in shared memory, and written in
+// packed order (consecutive threads write consecutive packed addresses).
+// ---------------------------------------------------------------------------
+template <bool CPLX, int PREC>
+__global__ void __launch_bounds__(kPackThreads) k_pack(const __grid_constant__ TileArgs a, int role) {
+    using T = typename std::conditional<CPLX, float2, float>::type;
+    __shared__ T stage[kPackMaxTile + kPackMaxTile / 32];  // +1 per 32: no bank conflicts
+    __shared__ int64_t tsrc[kPackMaxTile];
+    __shared__ int64_t tdst[kPackMaxTile];
+    __shared__ uint16_t tidx[kPackMaxTile];
+    __shared__ uint8_t shift[3 * kMaxBits];
+    __shared__ int8_t ts[2 * kPackLow], td[2 * kPackLow];
+    __shared__ int8_t nt[3 * kMaxBits];
+    __shared__ int64_t src_add[2 * kPackLow], dst_add[2 * kPackLow];
+    __shared__ int idx_add[2 * kPackLow];
+    __shared__ int n_tile, n_rest;
+
+    const bool useB = (role == 0) == (a.tc_swap != 0);
+    const int inst = blockIdx.y;
+    const InstanceInfo& in = a.in;
+    const int64_t slice = a.ctl->slice + (int64_t)inst * in.slice_step;
+    if (slice >= a.ctl->slice_end) return;
+    const int nk = a.nk, no = useB ? a.nn : a.nm, nb = a.nb;
+    const int nbits = nk + no + nb;
+    const TcGeom geo = tc_geom(a, CPLX, PREC);
+    constexpr int LG_ESZ = PREC == 2 ? 1 : 2, LG_KE = 7 - LG_ESZ;
+    const int ESZ = CPLX ? 8 : 4;
+    const T* src = reinterpret_cast<const T*>(useB ? a.B : a.A) +
+                   (int64_t)inst * (useB ? in.b_is : in.a_is) +
+                   slice_offset(useB ? a.slb : a.sla, slice);
+    char* pk = reinterpret_cast<char*>(a.P) + (int64_t)inst * in.p_is * ESZ;
+    char* hi = role == 0 ? pk : pk + geo.region_r;
+    const int64_t lo_off = role == 0 ? geo.plane_r : geo.plane_q;
+    const unsigned* mslot = useB ? a.sc.max_b : a.sc.max_a;
+    if (mslot) mslot += (int64_t)inst * (useB ? in.sb_is : in.sa_is);
+    const int e = exp_of(mslot);
+    const float f = ldexpf(1.f, -max(-120, min(120, e)));
+    const bool conj = useB ? a.conj_b : a.conj_a;
+
+    if (threadIdx.x == 0) {
+        const uint8_t* xk = useB ? a.b_k : a.a_k;
+        const uint8_t* xo = useB ? a.b_n : a.a_m;
+        const uint8_t* xb = useB ? a.b_b : a.a_b;
+        for (int p = 0; p < nbits; ++p)
+            shift[p] = p < nk ? xk[p] : (p < nk + no ? xo[p - nk] : xb[p - nk - no]);
+        // tile bits: the kPackLow lowest packed positions and the kPackLow
+        // lowest source strides (strides of distinct labels are distinct)
+        int8_t by_shift[64];
+        for (int s = 0; s < 64; ++s) by_shift[s] = -1;
+        for (int p = 0; p < nbits; ++p)
+            if (shift[p] < 64) by_shift[shift[p]] = (int8_t)p;  // kNoBit: K bit the operand lacks
+        bool in_tile[3 * kMaxBits];
+        for (int p = 0; p < nbits; ++p) in_tile[p] = p < kPackLow;
+        for (int s = 0, r = 0; s < 64 && r < kPackLow; ++s)
+            if (by_shift[s] >= 0) {
+                in_tile[by_shift[s]] = true;
+                ++r;
+            }
+        // where the two sets overlap, fill the tile up with the next packed
+        // positions so that every tile has 2 * kPackLow bits of work
+        {
+            int cnt = 0;
+            for (int p = 0; p < nbits; ++p) cnt += in_tile[p];
+            for (int p = kPackLow; p < nbits && cnt < 2 * kPackLow; ++p)
+                if (!in_tile[p]) {
+                    in_tile[p] = true;
+                    ++cnt;
+                }
+        }
+        int t = 0, u = 0;
+        for (int p = 0; p < nbits; ++p) {
+            if (in_tile[p]) td[t++] = (int8_t)p;
+            else nt[u++] = (int8_t)p;
+        }
+        // the same tile bits in source order (ascending stride; absent bits,
+        // which repeat the same source value, last)
+        int w = 0;
+        for (int s = 0; s < 64; ++s)
+            if (by_shift[s] >= 0 && in_tile[by_shift[s]]) ts[w++] = by_shift[s];
+        for (int i = 0; i < t; ++i)
+            if (shift[td[i]] >= 64) ts[w++] = td[i];
+        for (int j = 0; j < t; ++j) {
+            src_add[j] = shift[ts[j]] < 64 ? int64_t(1) << shift[ts[j]] : 0;
+            dst_add[j] = int64_t(1) << td[j];
+            int r = 0;  // position of td[j] in source order
+            while (ts[r] != td[j]) ++r;
+            idx_add[j] = 1 << r;
+        }
+        n_tile = t;
+        n_rest = u;
+    }
+    __syncthreads();
+    const int t = n_tile, u = n_rest;
+    const int tsz = 1 << t;
+    for (int i = threadIdx.x; i < tsz; i += blockDim.x) {
+        int64_t so = 0, dg = 0;
+        int idx = 0;
+        for (int j = 0; j < t; ++j)
+            if ((i >> j) & 1) {
+                so += src_add[j];
+                dg += dst_add[j];
+                idx += idx_add[j];
+            }
+        tsrc[i] = so;
+        tdst[i] = dg;
+        tidx[i] = (uint16_t)(idx + (idx >> 5));  // padded stage index
+    }
+    __syncthreads();
+    const int64_t n_tiles = int64_t(1) << u;
+    const int64_t K = int64_t(1) << nk;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        int64_t sb = 0, gb = 0;
+        for (int j = 0; j < u; ++j)
+            if ((tile >> j) & 1) {
+                if (shift[nt[j]] < 64) sb += int64_t(1) << shift[nt[j]];
+                gb += int64_t(1) << nt[j];
+            }
+        T ld[kPackMaxTile / kPackThreads];
+#pragma unroll
+        for (int r = 0; r < kPackMaxTile / kPackThreads; ++r) {
+            const int i = threadIdx.x + r * kPackThreads;
+            if (i < tsz) ld[r] = src[sb + tsrc[i]];
+        }
+#pragma unroll
+        for (int r = 0; r < kPackMaxTile / kPackThreads; ++r) {
+            const int i = threadIdx.x + r * kPackThreads;
+            if (i < tsz) stage[i + (i >> 5)] = ld[r];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kPackMaxTile / kPackThreads; ++r) {
+            const int i = threadIdx.x + r * kPackThreads;
+            if (i >= tsz) break;
+            const T v = stage[tidx[i]];
+            const int64_t g = gb + tdst[i];
+            const int64_t row = g >> nk, k = g & (K - 1);
+            if constexpr (CPLX) {
+                const float re = v.x * f, im = (conj ? -v.y : v.y) * f;
+                if (role == 0) {
+                    put2<PREC>(hi, lo_off, tile_pos(row, 2 * k, geo.nkb, LG_KE, LG_ESZ), re, im);
+                } else {
+                    put2<PREC>(hi, lo_off, tile_pos(2 * row, 2 * k, geo.nkb, LG_KE, LG_ESZ), re, -im);
+                    put2<PREC>(hi, lo_off, tile_pos(2 * row + 1, 2 * k, geo.nkb, LG_KE, LG_ESZ), im, re);
+                }
+                // K shorter than one 128-byte row: zero the rest of the row
+                for (int64_t z = 2 * k + geo.kr; z < (int64_t)1 << LG_KE; z += geo.kr) {
+                    if (role == 0) {
+                        put2<PREC>(hi, lo_off, tile_pos(row, z, geo.nkb, LG_KE, LG_ESZ), 0.f, 0.f);
+                    } else {
+                        put2<PREC>(hi, lo_off, tile_pos(2 * row, z, geo.nkb, LG_KE, LG_ESZ), 0.f, 0.f);
+                        put2<PREC>(hi, lo_off, tile_pos(2 * row + 1, z, geo.nkb, LG_KE, LG_ESZ), 0.f, 0.f);
+                    }
+                }
+            } else {
+                put1<PREC>(hi, lo_off, tile_pos(row, k, geo.nkb, LG_KE, LG_ESZ), v * f);
+                for (int64_t z = k + geo.kr; z < (int64_t)1 << LG_KE; z += geo.kr)
+                    put1<PREC>(hi, lo_off, tile_pos(row, z, geo.nkb, LG_KE, LG_ESZ), 0.f);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_umma: bulk-copy-fed tcgen05 GEMM over the packed planes.  blockIdx.x:
+// output tile (grouped raster), blockIdx.y: K split, blockIdx.z: batch entry
+// and instance.
+// ---------------------------------------------------------------------------
 template <bool CPLX, int PREC, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1) k_tc(const __grid_constant__ TileArgs a) {
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    k_umma(const __grid_constant__ TileArgs a, int nacc) {
     constexpr bool BF16 = PREC == 2;
     constexpr bool SPLIT = PREC != 0;
-    constexpr int PARTS = SPLIT ? 2 : 1;                 // hi (+ lo) per operand
-    constexpr int STAGE_BYTES = 2 * PARTS * kTileBytes;  // A and B
-    // real K per stage: a 128-byte row holds 32 TF32 or 64 BF16 values
-    constexpr int KR = BF16 ? 64 : 32;
-    constexpr int KC = CPLX ? KR / 2 : KR;               // source (complex) K per stage
-    constexpr int NC = CPLX ? kBN / 2 : kBN;             // source N per tile
-    constexpr int MMA_K = BF16 ? 16 : 8;                 // real K per instruction
-    constexpr int KSTEPS = KR / MMA_K;                   // instructions per part pair
+    constexpr int PARTS = SPLIT ? 2 : 1;
+    constexpr int STAGE_BYTES = 2 * PARTS * kTileBytes;
+    constexpr int KE = BF16 ? 64 : 32;     // packed elements per 128-byte row
+    constexpr int MMA_K = BF16 ? 16 : 8;   // K per instruction
+    constexpr int KSTEPS = KE / MMA_K;
     constexpr uint32_t FMT = BF16 ? 1u : 2u;
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ uint64_t acc_full[kNumAcc], acc_empty[kNumAcc];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
-    __shared__ int64_t rowA[kBM], colB[NC], kA[KC], kB[KC];
+    __shared__ int consumed;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
-    const int64_t M = 1ll << a.nm, N = 1ll << a.nn, K = 1ll << a.nk;
-    const int64_t tiles_n = (N + NC - 1) / NC;
-    const int64_t m0 = ((int64_t)blockIdx.x / tiles_n) * kBM;
-    const int64_t n0 = ((int64_t)blockIdx.x % tiles_n) * NC;
     const int64_t b = blockIdx.z % a.nbatch;
     const int inst = (int)(blockIdx.z / a.nbatch);
-    const int nkb = (int)((K + KC - 1) / KC);
-    // this instance's operands, result, scale slots and slice (an idle
-    // instance leaves before touching barriers or tensor memory)
+    const int sp = blockIdx.y, nsplit = gridDim.y;
+    // two-level accumulation: a chain of `chain` k-blocks accumulates in one
+    // TMEM accumulator; the epilogue warps add every finished chain into FP32
+    // registers (round to nearest), which keeps the tensor-core adder's long
+    // accumulation error out of the result
+    const int chain = SPLIT ? 1 : 4;
     const InstanceInfo& in = a.in;
     const int64_t slice = a.ctl->slice + (int64_t)inst * in.slice_step;
-    if (slice >= a.ctl->slice_end) return;
-    constexpr int ESZ = CPLX ? 8 : 4;
-    const void* Ainst = (const char*)a.A + (int64_t)inst * in.a_is * ESZ;
-    const void* Binst = (const char*)a.B + (int64_t)inst * in.b_is * ESZ;
-    void* Cinst = (char*)a.C + (int64_t)inst * in.c_is * ESZ;
+    if (slice >= a.ctl->slice_end) return;  // idle instance: before any barrier or TMEM
+    const TcGeom geo = tc_geom(a, CPLX, PREC);
+    const int nkl = (int)(geo.nkb / nsplit);   // k-blocks of this K part
+    const int64_t kb0 = (int64_t)sp * nkl;
+    const int tiles_m = (int)(geo.rows_r / kBM), tiles_n = (int)(geo.cols_q / kBN);
+    // grouped raster: kGroupRows row tiles share the column tiles they stream
+    int tm, tn;
+    {
+        const int per_group = kGroupRows * tiles_n;
+        const int grp = (int)blockIdx.x / per_group;
+        const int first = grp * kGroupRows;
+        const int gsz = min(kGroupRows, tiles_m - first);
+        const int r = (int)blockIdx.x - grp * per_group;
+        tm = first + r % gsz;
+        tn = r / gsz;
+    }
+    const int row0 = tm * kBM, col0 = tn * kBN;
+    const int nchain = (nkl + chain - 1) / chain;
+    const uint32_t alloc_cols = nacc <= 1 ? 128u : (nacc == 2 ? 256u : 512u);
+    const int ESZ = CPLX ? 8 : 4;
+    const char* pk = reinterpret_cast<const char*>(a.P) + (int64_t)inst * in.p_is * ESZ;
+
+    // renormalisation: the pack applied 2^-clamp(e); the rest is undone here
     ScaleIO sio = a.sc;
     if (sio.max_a) sio.max_a += (int64_t)inst * in.sa_is;
     if (sio.exp_a) sio.exp_a += (int64_t)inst * in.sa_is;
@@ -265,34 +537,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc(const __grid_constant__ Tile
     if (sio.exp_b) sio.exp_b += (int64_t)inst * in.sb_is;
     sio.max_c += (int64_t)inst * in.sc_is;
     sio.exp_c += (int64_t)inst * in.sc_is;
-
-    // renormalisation of the operands (exact powers of two)
     const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
-    const int cA = max(-120, min(120, eA)), cB = max(-120, min(120, eB));
-    const float fa = ldexpf(1.f, -cA), fb = ldexpf(1.f, -cB);
-    const int resid = (eA - cA) + (eB - cB);
-    if (blockIdx.x == 0 && b == 0 && tid == 0 && sio.exp_c)
+    const int resid = (eA - max(-120, min(120, eA))) + (eB - max(-120, min(120, eB)));
+    if (blockIdx.x == 0 && sp == 0 && b == 0 && tid == 0 && sio.exp_c)
         *sio.exp_c = (sio.exp_a ? *sio.exp_a : 0) + (sio.exp_b ? *sio.exp_b : 0) + eA + eB;
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full_bar[s], kProducers);
+            mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&done_bar, 1);
+        for (int q = 0; q < kNumAcc; ++q) {
+            mbar_init(&acc_full[q], 1);
+            mbar_init(&acc_empty[q], 4);  // one arrival per epilogue warp
+        }
         abort_flag = 0;
+        consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
     }
-    for (int i = tid; i < kBM; i += kThreads) rowA[i] = scatter(i, a.a_m, a.nm);
-    for (int j = tid; j < NC; j += kThreads) colB[j] = scatter(j, a.b_n, a.nn);
-    for (int t = tid; t < KC; t += kThreads) {
-        kA[t] = scatter(t, a.a_k, a.nk);
-        kB[t] = scatter(t, a.b_k, a.nk);
-    }
-    constexpr int kMmaWarp = kProducers / 32;
-    if (warp == kMmaWarp) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base)),
-                     "r"(kBN));
+                     "r"(alloc_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -300,292 +568,248 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc(const __grid_constant__ Tile
     tc_fence_after();
     const uint32_t tmem = tmem_base;
 
-    if (warp == kMmaWarp) {
+    if (warp == 0) {
+        // ---------------- bulk-copy producer ----------------
+        if (tid == 0) {
+            const char* r_src = pk + ((b * tiles_m + tm) * geo.nkb + kb0) * kTileBytes;
+            const char* q_src = pk + geo.region_r + ((b * tiles_n + tn) * geo.nkb + kb0) * kTileBytes;
+            int issued = 0;
+            for (int j = 0; j < nkl; ++j) {
+                const int s = j % STAGES;
+                if (j >= STAGES &&
+                    !mbar_wait(&empty_bar[s], (uint32_t)(((j / STAGES) + 1) & 1), &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                uint8_t* st = smem + s * STAGE_BYTES;
+                mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+                const int64_t o = (int64_t)j * kTileBytes;
+                bulk_load(st, r_src + o, kTileBytes, &full_bar[s]);
+                if constexpr (SPLIT) bulk_load(st + kTileBytes, r_src + geo.plane_r + o, kTileBytes, &full_bar[s]);
+                uint8_t* sq = st + PARTS * kTileBytes;
+                bulk_load(sq, q_src + o, kTileBytes, &full_bar[s]);
+                if constexpr (SPLIT) bulk_load(sq + kTileBytes, q_src + geo.plane_q + o, kTileBytes, &full_bar[s]);
+                ++issued;
+            }
+            if (abort_flag) {
+                // wait (bounded) for the copies still in flight before leaving
+                int dummy = 0;
+                for (int j = *(volatile int*)&consumed; j < issued; ++j)
+                    mbar_wait(&full_bar[j % STAGES], (uint32_t)((j / STAGES) & 1), &dummy);
+            }
+        }
+    } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
-        if ((tid & 31) == 0) {
+        if (tid == 32) {
             const uint32_t idesc = instr_desc(FMT, kBM, kBN);
-            bool ok = true;
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                const int s = kb % STAGES;
-                if (!mbar_wait(&full_bar[s], (uint32_t)((kb / STAGES) & 1), &abort_flag)) {
-                    ok = false;
+            for (int j = 0; j < nkl; ++j) {
+                const int s = j % STAGES;
+                if (!mbar_wait(&full_bar[s], (uint32_t)((j / STAGES) & 1), &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                const int ch = j / chain, q = ch % nacc;
+                const bool first = j % chain == 0;
+                // a chain reuses accumulator q once the epilogue has drained it
+                if (first && ch >= nacc &&
+                    !mbar_wait(&acc_empty[q], (uint32_t)(((ch / nacc) + 1) & 1), &abort_flag)) {
+                    abort_flag = 1;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-                const uint32_t a_hi = base, b_hi = base + PARTS * kTileBytes;
-                const uint32_t a_lo = base + kTileBytes, b_lo = b_hi + kTileBytes;
+                const uint32_t r_hi = base, q_hi = base + PARTS * kTileBytes;
+                const uint32_t r_lo = base + kTileBytes, q_lo = q_hi + kTileBytes;
+                const uint32_t d = tmem + (uint32_t)(q * kBN);
 #pragma unroll
                 for (int k = 0; k < KSTEPS; ++k) {
                     const uint32_t off = k * MMA_K * (BF16 ? 2 : 4);
-                    const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
-                    mma<BF16>(tmem, smem_desc(a_hi + off), smem_desc(b_hi + off), idesc, acc0);
+                    const uint32_t acc0 = (!first || k > 0) ? 1u : 0u;
+                    mma<BF16>(d, smem_desc(r_hi + off), smem_desc(q_hi + off), idesc, acc0);
                     if constexpr (SPLIT) {
-                        mma<BF16>(tmem, smem_desc(a_hi + off), smem_desc(b_lo + off), idesc, 1u);
-                        mma<BF16>(tmem, smem_desc(a_lo + off), smem_desc(b_hi + off), idesc, 1u);
+                        mma<BF16>(d, smem_desc(r_hi + off), smem_desc(q_lo + off), idesc, 1u);
+                        mma<BF16>(d, smem_desc(r_lo + off), smem_desc(q_hi + off), idesc, 1u);
                     }
                 }
                 mma_commit(&empty_bar[s]);
+                if (j % chain == chain - 1 || j == nkl - 1) mma_commit(&acc_full[q]);
+                *(volatile int*)&consumed = j + 1;
             }
-            if (!ok) {
-                abort_flag = 1;
-                atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
-            }
-            mma_commit(&done_bar);
+            mma_commit(&done_bar);  // arrives once every MMA issued above has completed
         }
-        __syncwarp();
     } else {
-        // ---------------- producers ----------------
-        const float* Af = reinterpret_cast<const float*>(Ainst);
-        const float* Bf = reinterpret_cast<const float*>(Binst);
-        const int64_t baseA = slice_offset(a.sla, slice) + scatter(b, a.a_b, a.nb) + scatter(m0, a.a_m, a.nm);
-        const int64_t baseB = slice_offset(a.slb, slice) + scatter(b, a.b_b, a.nb) + scatter(n0, a.b_n, a.nn);
-        const int mlim = (int)min(M - m0, (int64_t)kBM);
-        const int nlim = (int)min(N - n0, (int64_t)NC);
-        constexpr int VPC = BF16 ? 8 : 4;      // real values per 16B chunk
-        constexpr int CPC = CPLX ? VPC / 2 : VPC;  // source values per chunk (A)
-        constexpr int A_ITEMS = kBM * 8 / kProducers;             // 16B chunks per thread
-        constexpr int BROWS = CPLX ? kBN / 2 : kBN;
-        constexpr int B_ITEMS = BROWS * 8 / kProducers;
-        constexpr int BPC = CPLX ? CPC : VPC;                    // source values per B item
-        constexpr int BV = CPLX ? CPC * 2 : VPC;                 // floats loaded per B item
-        struct Regs {
-            float a[A_ITEMS][VPC];
-            float b[B_ITEMS][BV];
-        };
-        // per-thread operand offsets: an item's rows and K positions are the
-        // same in every k-block (only the k-block base moves)
-        const int kmax = (int)min(K, (int64_t)KC);
-        int32_t oa[A_ITEMS][CPC], ob[B_ITEMS][BPC];
-        uint32_t va = 0, vb = 0;  // validity bits
+        // ---------------- epilogue (warps 2-5) ----------------
+        float lmax = 0.f;
+        const int quad = warp & 3;  // TMEM lanes 32*quad.. belong to this warp
+        float sum[kBN];
 #pragma unroll
-        for (int i = 0; i < A_ITEMS; ++i) {
-            const int it = tid + i * kProducers;
-            const int r = a.a_mfast ? it % kBM : it / 8;
-            const int c = a.a_mfast ? it / kBM : it % 8;
+        for (int i = 0; i < kBN; ++i) sum[i] = 0.f;
+        bool ok = true;
+        for (int ch = 0; ch < nchain && ok; ++ch) {
+            const int q = ch % nacc;
+            const bool got = mbar_wait(&acc_full[q], (uint32_t)((ch / nacc) & 1), &abort_flag);
+            ok = __all_sync(0xffffffffu, got && !abort_flag);  // tcgen05.ld is warp-collective
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(q * kBN);
 #pragma unroll
-            for (int v = 0; v < CPC; ++v) {
-                const int kk = c * CPC + v;
-                const bool in = r < mlim && kk < kmax;
-                oa[i][v] = in ? (int32_t)(rowA[r] + kA[kk]) : 0;
-                va |= (in ? 1u : 0u) << (i * CPC + v);
-            }
+            for (int col = 0; col < kBN; col += 32) tmem_add32(ta + (uint32_t)col, sum + col);
+            tc_fence_before();
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(&acc_empty[q]);
         }
+        if (ok) {
+            const int row = row0 + quad * 32 + (tid & 31);
+            const int64_t M = int64_t(1) << a.nm, N = int64_t(1) << a.nn;
+            // the node's output, or this part's FP32 partial product (same layout)
+            float* C = nsplit > 1
+                           ? reinterpret_cast<float*>(const_cast<char*>(pk) + geo.part_off) +
+                                 (int64_t)sp * a.nbatch * M * N * (CPLX ? 2 : 1)
+                           : reinterpret_cast<float*>(a.C) + (int64_t)inst * in.c_is * (CPLX ? 2 : 1);
+            const int rs = nsplit > 1 ? 0 : resid;
 #pragma unroll
-        for (int i = 0; i < B_ITEMS; ++i) {
-            const int it = tid + i * kProducers;
-            const int j = a.b_nfast ? it % BROWS : it / 8;
-            const int c = a.b_nfast ? it / BROWS : it % 8;
+            for (int col = 0; col < kBN; col += 16) {
+                float* v = sum + col;
 #pragma unroll
-            for (int v = 0; v < BPC; ++v) {
-                const int kk = c * BPC + v;
-                const bool in = j < nlim && kk < kmax;
-                ob[i][v] = in ? (int32_t)(colB[j] + kB[kk]) : 0;
-                vb |= (in ? 1u : 0u) << (i * BPC + v);
-            }
-        }
-        // issue every gather of k-block kb into registers
-        auto gather = [&](int kb, Regs& R) {
-            const int64_t k0 = (int64_t)kb * KC;
-            const float* pa = Af + (baseA + scatter(k0, a.a_k, a.nk)) * (CPLX ? 2 : 1);
-            const float* pb = Bf + (baseB + scatter(k0, a.b_k, a.nk)) * (CPLX ? 2 : 1);
-#pragma unroll
-            for (int i = 0; i < A_ITEMS; ++i)
-#pragma unroll
-                for (int v = 0; v < CPC; ++v) {
-                    const bool in = (va >> (i * CPC + v)) & 1u;
-                    if constexpr (CPLX) {
-                        const float2 z = in ? reinterpret_cast<const float2*>(pa)[oa[i][v]] : make_float2(0.f, 0.f);
-                        R.a[i][2 * v] = z.x;
-                        R.a[i][2 * v + 1] = a.conj_a ? -z.y : z.y;
-                    } else {
-                        R.a[i][v] = in ? pa[oa[i][v]] : 0.f;
-                    }
+                for (int i = 0; i < 16; ++i) {
+                    if (rs) v[i] = ldexpf(v[i], -rs);
+                    lmax = fmaxf(lmax, fabsf(v[i]));
                 }
-#pragma unroll
-            for (int i = 0; i < B_ITEMS; ++i)
-#pragma unroll
-                for (int v = 0; v < BPC; ++v) {
-                    const bool in = (vb >> (i * BPC + v)) & 1u;
-                    if constexpr (CPLX) {
-                        const float2 z = in ? reinterpret_cast<const float2*>(pb)[ob[i][v]] : make_float2(0.f, 0.f);
-                        R.b[i][2 * v] = z.x;
-                        R.b[i][2 * v + 1] = a.conj_b ? -z.y : z.y;
-                    } else {
-                        R.b[i][v] = in ? pb[ob[i][v]] : 0.f;
-                    }
-                }
-        };
-        // scale, split and store k-block kb into its stage, then signal it
-        auto deposit = [&](int kb, const Regs& R) -> bool {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(&empty_bar[s], (uint32_t)(((kb / STAGES) + 1) & 1), &abort_flag))
-                return false;
-            uint8_t* st = smem + s * STAGE_BYTES;
-#pragma unroll
-            for (int i = 0; i < A_ITEMS; ++i) {
-                const int it = tid + i * kProducers;
-                const int r = a.a_mfast ? it % kBM : it / 8;
-                const int c = a.a_mfast ? it / kBM : it % 8;
-                float x[VPC];
-#pragma unroll
-                for (int v = 0; v < VPC; ++v) x[v] = R.a[i][v] * fa;
-                uint4 hi, lo;
-                if constexpr (BF16) Pack<true>::split8(x, hi, lo);
-                else Pack<false>::split4(x, hi, lo, SPLIT);
-                *reinterpret_cast<uint4*>(st + swz(r, c)) = hi;
-                if constexpr (SPLIT) *reinterpret_cast<uint4*>(st + kTileBytes + swz(r, c)) = lo;
-            }
-            uint8_t* sb = st + PARTS * kTileBytes;
-#pragma unroll
-            for (int i = 0; i < B_ITEMS; ++i) {
-                const int it = tid + i * kProducers;
-                const int j = a.b_nfast ? it % BROWS : it / 8;
-                const int c = a.b_nfast ? it / BROWS : it % 8;
                 if constexpr (CPLX) {
-                    float x0[VPC], x1[VPC];  // rows 2j: (re, -im) ; 2j+1: (im, re)
+                    const int64_t j0 = (col0 + col) / 2;  // first complex column of the chunk
+                    if (!a.tc_swap) {
+                        float* crow = C + ((b * M + row) * N + j0) * 2;
 #pragma unroll
-                    for (int v = 0; v < CPC; ++v) {
-                        const float re = R.b[i][2 * v] * fb, im = R.b[i][2 * v + 1] * fb;
-                        x0[2 * v] = re;
-                        x0[2 * v + 1] = -im;
-                        x1[2 * v] = im;
-                        x1[2 * v + 1] = re;
-                    }
-                    uint4 h0, l0, h1, l1;
-                    if constexpr (BF16) {
-                        Pack<true>::split8(x0, h0, l0);
-                        Pack<true>::split8(x1, h1, l1);
+                        for (int i = 0; i < 16; i += 4)
+                            *reinterpret_cast<float4*>(crow + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
                     } else {
-                        Pack<false>::split4(x0, h0, l0, SPLIT);
-                        Pack<false>::split4(x1, h1, l1, SPLIT);
-                    }
-                    *reinterpret_cast<uint4*>(sb + swz(2 * j, c)) = h0;
-                    *reinterpret_cast<uint4*>(sb + swz(2 * j + 1, c)) = h1;
-                    if constexpr (SPLIT) {
-                        *reinterpret_cast<uint4*>(sb + kTileBytes + swz(2 * j, c)) = l0;
-                        *reinterpret_cast<uint4*>(sb + kTileBytes + swz(2 * j + 1, c)) = l1;
+                        // rows run over N, complex columns over M
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            *reinterpret_cast<float2*>(C + ((b * M + j0 + i) * N + row) * 2) =
+                                make_float2(v[2 * i], v[2 * i + 1]);
                     }
                 } else {
-                    float x[VPC];
+                    float* crow = C + (b * M + row) * N + col0 + col;
 #pragma unroll
-                    for (int v = 0; v < VPC; ++v) x[v] = R.b[i][v] * fb;
-                    uint4 hi, lo;
-                    if constexpr (BF16) Pack<true>::split8(x, hi, lo);
-                    else Pack<false>::split4(x, hi, lo, SPLIT);
-                    *reinterpret_cast<uint4*>(sb + swz(j, c)) = hi;
-                    if constexpr (SPLIT) *reinterpret_cast<uint4*>(sb + kTileBytes + swz(j, c)) = lo;
+                    for (int i = 0; i < 16; i += 4)
+                        *reinterpret_cast<float4*>(crow + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
                 }
             }
-            fence_proxy_async();
-            mbar_arrive(&full_bar[s]);
-            return true;
-        };
-        // two register sets: the gathers of k-block kb+1 are in flight while
-        // k-block kb is converted and stored
-        bool ok = true;
-        Regs R0, R1;
-        gather(0, R0);
-        for (int kb = 0; kb < nkb && ok; kb += 2) {
-            if (kb + 1 < nkb) gather(kb + 1, R1);
-            if (!deposit(kb, R0)) {
-                ok = false;
-                break;
-            }
-            if (kb + 1 < nkb) {
-                if (kb + 2 < nkb) gather(kb + 2, R0);
-                if (!deposit(kb + 1, R1)) {
-                    ok = false;
-                    break;
-                }
-            }
-        }
-        if (!ok) abort_flag = 1;
-
-        // ---------------- epilogue ----------------
-        float lmax = 0.f;
-        bool done = mbar_wait(&done_bar, 0u, &abort_flag);
-        tc_fence_after();
-        done = __all_sync(0xffffffffu, done && !abort_flag);  // tcgen05.ld is warp-collective
-        if (done) {
-            const int quad = warp & 3;                // TMEM lanes 32*quad.. belong to this warp
-            const int row = quad * 32 + (tid & 31);   // TMEM lane = tile row
-            const int64_t m = m0 + row;
-            constexpr int kGroups = kProducers / 128;  // warps sharing a lane quadrant
-            const int col0 = (warp >> 2) * (kBN / kGroups);
-            for (int col = col0; col < col0 + kBN / kGroups; col += 16) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col, v);
-                if (m < M) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        if (resid) v[i] = ldexpf(v[i], -resid);
-                        lmax = fmaxf(lmax, fabsf(v[i]));
-                    }
-                    const int nfirst = CPLX ? col / 2 : col;
-                    const int ncount = CPLX ? 8 : 16;
-                    if (nfirst < nlim) {
-                        float* crow = reinterpret_cast<float*>(Cinst) +
-                                      ((b * M + m) * N + n0 + nfirst) * (CPLX ? 2 : 1);
-                        if (nfirst + ncount <= nlim) {
-#pragma unroll
-                            for (int i = 0; i < 16; i += 4)
-                                *reinterpret_cast<float4*>(crow + i) =
-                                    make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-                        } else {
-                            const int vals = (nlim - nfirst) * (CPLX ? 2 : 1);
-                            for (int i = 0; i < vals; ++i) crow[i] = v[i];
-                        }
-                    }
-                }
-            }
-        } else {
+        } else if ((tid & 31) == 0) {
             atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
         }
-        // block-free max over the producer warps
-        for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-        if ((tid & 31) == 0 && lmax > 0.f) atomicMax(sio.max_c, __float_as_uint(lmax));
+        if (nsplit == 1) {
+            for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+            if ((tid & 31) == 0 && lmax > 0.f) atomicMax(sio.max_c, __float_as_uint(lmax));
+        }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == kMmaWarp) {
-        // the MMA thread committed done_bar after its last MMA (also on abort):
-        // wait (bounded) for it so no MMA still writes the accumulator
+    if (warp == 1) {
+        // no MMA may still write the accumulators when they are freed
         int dummy = 0;
         bool quiet = true;
-        if ((tid & 31) == 0) quiet = mbar_wait(&done_bar, 0u, &dummy);
+        if (tid == 32) quiet = mbar_wait(&done_bar, 0u, &dummy);
         quiet = __shfl_sync(0xffffffffu, quiet, 0);
         tc_fence_after();
-        if (!quiet && (tid & 31) == 0) atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN));
+        if (!quiet && tid == 32) atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(alloc_cols));
     }
-    if (a.t_done && tid == 0) {
-        unsigned long long t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        atomicMax(a.t_done, t);
+    if (a.t_done && tid == 0 && nsplit == 1) {
+        unsigned long long tnow;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tnow));
+        atomicMax(a.t_done, tnow);
     }
 }
 
+// ---------------------------------------------------------------------------
+// k_tc_reduce: C = sum of the K parts in part order (FP32), the residual
+// renormalisation and the node maximum.  blockIdx.y: instance.
+// ---------------------------------------------------------------------------
 template <bool CPLX, int PREC>
-static cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
-    constexpr int STAGES = PREC == 0 ? 4 : 3;
+__global__ void __launch_bounds__(256) k_tc_reduce(const __grid_constant__ TileArgs a) {
+    const int inst = blockIdx.y;
+    const InstanceInfo& in = a.in;
+    const int64_t slice = a.ctl->slice + (int64_t)inst * in.slice_step;
+    if (slice >= a.ctl->slice_end) return;
+    const TcGeom geo = tc_geom(a, CPLX, PREC);
+    const int ESZ = CPLX ? 8 : 4;
+    const int64_t n4 = (a.nbatch << (a.nm + a.nn)) * (CPLX ? 2 : 1) / 4;  // float4 per part
+    const float4* P = reinterpret_cast<const float4*>(reinterpret_cast<const char*>(a.P) +
+                                                      (int64_t)inst * in.p_is * ESZ + geo.part_off);
+    float4* C = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.C) + (int64_t)inst * in.c_is * (CPLX ? 2 : 1));
+    ScaleIO sio = a.sc;
+    if (sio.max_a) sio.max_a += (int64_t)inst * in.sa_is;
+    if (sio.max_b) sio.max_b += (int64_t)inst * in.sb_is;
+    sio.max_c += (int64_t)inst * in.sc_is;
+    const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
+    const int resid = (eA - max(-120, min(120, eA))) + (eB - max(-120, min(120, eB)));
+    float lmax = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 s = P[i];
+        for (int p = 1; p < a.split; ++p) {
+            const float4 t = P[p * n4 + i];
+            s.x += t.x; s.y += t.y; s.z += t.z; s.w += t.w;
+        }
+        if (resid) {
+            s.x = ldexpf(s.x, -resid); s.y = ldexpf(s.y, -resid);
+            s.z = ldexpf(s.z, -resid); s.w = ldexpf(s.w, -resid);
+        }
+        lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(s.x), fabsf(s.y)), fmaxf(fabsf(s.z), fabsf(s.w))));
+        C[i] = s;
+    }
+    for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if ((threadIdx.x & 31) == 0 && lmax > 0.f) atomicMax(sio.max_c, __float_as_uint(lmax));
+    if (a.t_done && threadIdx.x == 0) {
+        unsigned long long tnow;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tnow));
+        atomicMax(a.t_done, tnow);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+template <bool CPLX, int PREC>
+cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
+    constexpr int STAGES = PREC == 0 ? 6 : 3;
     constexpr int PARTS = PREC == 0 ? 1 : 2;
     constexpr int SMEM = STAGES * 2 * PARTS * kTileBytes + 1024;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc<CPLX, PREC, STAGES>,
+        cudaError_t e = cudaFuncSetAttribute(k_umma<CPLX, PREC, STAGES>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int64_t M = 1ll << a.nm, N = 1ll << a.nn;
-    constexpr int NC = CPLX ? kBN / 2 : kBN;
-    const int64_t tiles = ((M + kBM - 1) / kBM) * ((N + NC - 1) / NC);
+    const TcGeom g = tc_geom(a, CPLX, PREC);
     const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
-    dim3 grid((unsigned)tiles, 1, (unsigned)(a.nbatch * ni));
-    k_tc<CPLX, PREC, STAGES><<<grid, kThreads, SMEM, s>>>(a);
+    const int split = a.split > 1 ? a.split : 1;
+    if (g.nkb % split) return cudaErrorInvalidValue;
+    const int64_t elems_a = int64_t(1) << (a.nk + a.nm + a.nb);
+    const int64_t elems_b = int64_t(1) << (a.nk + a.nn + a.nb);
+    auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 1024, 1), 152 * 8); };
+    const int64_t n_r = a.tc_swap ? elems_b : elems_a, n_q = a.tc_swap ? elems_a : elems_b;
+    k_pack<CPLX, PREC><<<dim3(blocks(n_r), ni), kPackThreads, 0, s>>>(a, 0);
+    k_pack<CPLX, PREC><<<dim3(blocks(n_q), ni), kPackThreads, 0, s>>>(a, 1);
+    const int nkl = (int)(g.nkb / split);
+    const int chains = PREC == 0 ? (nkl + 3) / 4 : nkl;
+    const int nacc = chains >= kNumAcc ? kNumAcc : (chains >= 2 ? 2 : 1);
+    const int64_t tiles = (g.rows_r / kBM) * (g.cols_q / kBN);
+    dim3 grid((unsigned)tiles, (unsigned)split, (unsigned)(a.nbatch * ni));
+    k_umma<CPLX, PREC, STAGES><<<grid, kGemmThreads, SMEM, s>>>(a, nacc);
+    if (split > 1) {
+        const int64_t n4 = (a.nbatch << (a.nm + a.nn)) * (CPLX ? 2 : 1) / 4;
+        const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>((n4 + 255) / 256, 1), 152 * 8);
+        k_tc_reduce<CPLX, PREC><<<dim3(nb, ni), 256, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
+
+}  // namespace
 
 cudaError_t launch_tc(const TileArgs& a, int prec, bool is_c, cudaStream_t s) {
     if (is_c) {
