@@ -353,16 +353,98 @@ __global__ void __launch_bounds__(256) k_split_reduce(const __grid_constant__ Ti
 // Tiny output, long K: grid (outputs, batch, K splits); each CTA reduces its
 // K range in a fixed order; with several splits the partials go to P and
 // k_split_reduce sums them in split order (deterministic).
+// Inner-product node (few outputs, long K): out[b,m,n] = sum_k A[.., k] B[.., k].
+// The K range is cut into tiles of up to 2^kDotLow2 entries holding the
+// kDotLow lowest strides of A, the kDotLow lowest of B and the next K bits;
+// every tile is read twice in the operands' own orders (consecutive threads,
+// consecutive addresses), staged in shared memory in K order and multiplied
+// there.  blockIdx.x: output, y: batch entry, z: K part x instance.
+constexpr int kDotLow = 5;
+constexpr int kDotTile = 1 << (2 * kDotLow);
+
 template <bool CPLX>
 __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a) {
     using T = typename VT<CPLX>::T;
-    const int64_t N = 1ll << a.nn, M = 1ll << a.nm, K = 1ll << a.nk;
+    __shared__ T sA[kDotTile + kDotTile / 32], sB[kDotTile + kDotTile / 32];
+    __shared__ int64_t offA[kDotTile], offB[kDotTile];
+    __shared__ uint16_t canA[kDotTile], canB[kDotTile];
+    __shared__ int8_t tk[2 * kDotLow], oa[2 * kDotLow], ob[2 * kDotLow], nt[kMaxBits];
+    __shared__ int n_tile, n_rest;
+    __shared__ T red[256];
+    const int64_t N = 1ll << a.nn, M = 1ll << a.nm;
     const int64_t m = (int64_t)blockIdx.x / N, n = (int64_t)blockIdx.x % N;
     const int64_t b = blockIdx.y;
     const int sp = blockIdx.z % a.split;
     const View vw = inst_view(a, blockIdx.z / a.split, (int)sizeof(T));
     if (!vw.live) return;
     const Scales sc = node_scales(vw.sc, blockIdx.x == 0 && blockIdx.y == 0 && sp == 0 && threadIdx.x == 0);
+    const int nk = a.nk;
+    if (threadIdx.x == 0) {
+        // tile bits: the kDotLow lowest strides of each operand, then the
+        // lowest K positions, up to 2 * kDotLow bits
+        bool in[kMaxBits];
+        for (int p = 0; p < nk; ++p) in[p] = false;
+        for (int side = 0; side < 2; ++side) {
+            const uint8_t* sh = side ? a.b_k : a.a_k;
+            for (int r = 0; r < kDotLow; ++r) {
+                int best = -1;
+                for (int p = 0; p < nk; ++p)
+                    if (!in[p] && sh[p] != kNoBit && (best < 0 || sh[p] < sh[best])) best = p;
+                if (best < 0) break;
+                // only bits below the operand's kDotLow-th smallest stride
+                int rank = 0;
+                for (int q = 0; q < nk; ++q) rank += sh[q] != kNoBit && sh[q] < sh[best];
+                if (rank >= kDotLow) break;
+                in[best] = true;
+            }
+        }
+        int cnt = 0;
+        for (int p = 0; p < nk; ++p) cnt += in[p];
+        for (int p = 0; p < nk && cnt < 2 * kDotLow; ++p)
+            if (!in[p]) {
+                in[p] = true;
+                ++cnt;
+            }
+        int t = 0, u = 0;
+        for (int p = 0; p < nk; ++p) {
+            if (in[p]) tk[t++] = (int8_t)p;
+            else nt[u++] = (int8_t)p;
+        }
+        // each operand's order of the tile bits (ascending stride, absent last)
+        for (int side = 0; side < 2; ++side) {
+            const uint8_t* sh = side ? a.b_k : a.a_k;
+            int8_t* o = side ? ob : oa;
+            bool used[2 * kDotLow] = {};
+            for (int w = 0; w < t; ++w) {
+                int best = -1;
+                for (int j = 0; j < t; ++j)
+                    if (!used[j] && (best < 0 || (int)sh[tk[j]] < (int)sh[tk[best]])) best = j;
+                used[best] = true;
+                o[w] = (int8_t)best;  // index into tk
+            }
+        }
+        n_tile = t;
+        n_rest = u;
+    }
+    __syncthreads();
+    const int t = n_tile, u = n_rest, tsz = 1 << t;
+    for (int e = threadIdx.x; e < tsz; e += blockDim.x) {
+        int64_t xa = 0, xb = 0;
+        int ca = 0, cb = 0;
+        for (int w = 0; w < t; ++w)
+            if ((e >> w) & 1) {
+                const int pa = tk[oa[w]], pb = tk[ob[w]];
+                if (a.a_k[pa] != kNoBit) xa += int64_t(1) << a.a_k[pa];
+                if (a.b_k[pb] != kNoBit) xb += int64_t(1) << a.b_k[pb];
+                ca += 1 << oa[w];
+                cb += 1 << ob[w];
+            }
+        offA[e] = xa;
+        offB[e] = xb;
+        canA[e] = (uint16_t)(ca + (ca >> 5));
+        canB[e] = (uint16_t)(cb + (cb >> 5));
+    }
+    __syncthreads();
     const int64_t slice = vw.slice;
     const int64_t baseA =
         slice_off(a.sla, slice) + scatter_bits(b, a.a_b, a.nb) + scatter_bits(m, a.a_m, a.nm);
@@ -370,26 +452,47 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a)
         slice_off(a.slb, slice) + scatter_bits(b, a.b_b, a.nb) + scatter_bits(n, a.b_n, a.nn);
     const T* A = reinterpret_cast<const T*>(vw.A);
     const T* B = reinterpret_cast<const T*>(vw.B);
-    const int lo = threadIdx.x;
-    const int64_t loA = scatter_bits(lo, a.a_k, a.nk), loB = scatter_bits(lo, a.b_k, a.nk);
-    const int64_t kb = (int64_t)sp * a.kchunk, ke = min64(K, kb + a.kchunk);
+    const int64_t n_tiles = int64_t(1) << u;
+    const int64_t per = (n_tiles + a.split - 1) / a.split;
+    const int64_t t0 = (int64_t)sp * per, t1 = min64(n_tiles, t0 + per);
     T acc0 = zero<T>(), acc1 = zero<T>();
-    int64_t hi = kb;
-    for (; hi + 256 < ke; hi += 512) {
-        const int64_t hA0 = scatter_bits(hi, a.a_k, a.nk), hB0 = scatter_bits(hi, a.b_k, a.nk);
-        const int64_t hA1 = scatter_bits(hi + 256, a.a_k, a.nk), hB1 = scatter_bits(hi + 256, a.b_k, a.nk);
-        const T x0 = A[baseA + hA0 + loA], y0 = B[baseB + hB0 + loB];
-        const T x1 = A[baseA + hA1 + loA], y1 = B[baseB + hB1 + loB];
-        fma_acc(acc0, cmul(x0, sc.fa, a.conj_a), cmul(y0, sc.fb, a.conj_b));
-        fma_acc(acc1, cmul(x1, sc.fa, a.conj_a), cmul(y1, sc.fb, a.conj_b));
-    }
-    for (; hi < ke; hi += 256) {
-        if (hi + lo >= ke) break;
-        const int64_t hA = scatter_bits(hi, a.a_k, a.nk), hB = scatter_bits(hi, a.b_k, a.nk);
-        fma_acc(acc0, cmul(A[baseA + hA + loA], sc.fa, a.conj_a), cmul(B[baseB + hB + loB], sc.fb, a.conj_b));
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        int64_t ba = baseA, bb = baseB;
+        for (int j = 0; j < u; ++j)
+            if ((tile >> j) & 1) {
+                if (a.a_k[nt[j]] != kNoBit) ba += int64_t(1) << a.a_k[nt[j]];
+                if (a.b_k[nt[j]] != kNoBit) bb += int64_t(1) << a.b_k[nt[j]];
+            }
+        T xa[kDotTile / 256], xb[kDotTile / 256];
+#pragma unroll
+        for (int r = 0; r < kDotTile / 256; ++r) {
+            const int e = threadIdx.x + r * 256;
+            if (e < tsz) {
+                xa[r] = A[ba + offA[e]];
+                xb[r] = B[bb + offB[e]];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kDotTile / 256; ++r) {
+            const int e = threadIdx.x + r * 256;
+            if (e < tsz) {
+                sA[canA[e]] = xa[r];
+                sB[canB[e]] = xb[r];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kDotTile / 256; ++r) {
+            const int i = threadIdx.x + r * 256;
+            if (i < tsz) {
+                const int ip = i + (i >> 5);
+                if (r & 1) fma_acc(acc1, cmul(sA[ip], sc.fa, a.conj_a), cmul(sB[ip], sc.fb, a.conj_b));
+                else fma_acc(acc0, cmul(sA[ip], sc.fa, a.conj_a), cmul(sB[ip], sc.fb, a.conj_b));
+            }
+        }
+        __syncthreads();
     }
     // fixed-order block reduction
-    __shared__ T red[256];
     red[threadIdx.x] = add(acc0, acc1);
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
