@@ -368,6 +368,13 @@ def run_network(args, torch, dist, rank, world, local):
     elem = 8 if cplx else 4
     leaves = [torch.from_numpy(np.array(t, order="C")).to(dt).contiguous().cuda() for t in net.tensors]
     tnw = binding.TensorNetwork(net.labels, net.dims, net.open, leaves, complex_=cplx)
+    tuned = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        ch = tnw.autotune(pairs, sliced, mode, reps=3)
+        tuned = {"seconds": round(time.perf_counter() - t0, 3), "tensor_core": ch.count(8),
+                 "tile_shapes": {n: ch.count(v) for v, n in
+                                 ((1, "64x64"), (2, "16x256"), (3, "4x1024"), (4, "256x16")) if ch.count(v)}}
     plan = tnw.plan_info(pairs, sliced, mode)
     per = 8.0 if cplx else 2.0
     flops_step = per * info.C * sc
@@ -427,6 +434,8 @@ def run_network(args, torch, dist, rank, world, local):
         hl = [torch.from_numpy(np.array(t, order="C")).to(dt).contiguous().pin_memory()
               for t in net.tensors]
         htn = binding.TensorNetwork(net.labels, net.dims, net.open, hl, complex_=cplx)
+        if not args.no_autotune:
+            htn.autotune(pairs, sliced, mode, reps=3)
         odt = torch.complex128 if cplx else torch.float64
         hout = torch.empty(tnw.out_shape, dtype=odt).pin_memory()
         hexp = torch.empty((), dtype=torch.int64).pin_memory()
@@ -467,6 +476,8 @@ def run_network(args, torch, dist, rank, world, local):
         modes_cmp = {}
         reps = min(args.steps, 5) if args.workload == "circuit7x7" else args.steps
         for md in MODES:
+            if not args.no_autotune:
+                tnw.autotune(pairs, sliced, md, reps=3)
             for _ in range(2):
                 call(md)
             es, ee2 = device_events(torch, stream, reps), device_events(torch, stream, reps)
@@ -495,7 +506,7 @@ def run_network(args, torch, dist, rank, world, local):
            "plan_kernels": {"generic": plan["n_generic"], "tiled": plan["n_tiled"],
                             "tensor_core": plan["n_tensor_core"]},
            "launch_steps": n_steps, "wave_steps": sum(1 for s in steps if s["wave"]),
-           "workspace_bytes": plan["ws_bytes"]}
+           "workspace_bytes": plan["ws_bytes"], "autotune": tuned}
     cfg.update(w["config"])
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
@@ -576,6 +587,9 @@ def run_batch(args, torch, dist, rank, world, local):
         flat[dt][0].copy_(flat[dt][1])
     for nt, ts in zip(nets, keep):
         handles.append(binding.TensorNetwork(nt.labels, nt.dims, nt.open, ts, complex_=nt.is_complex))
+    if not args.no_autotune:
+        for h, tr in zip(handles, trees):
+            h.autotune(tr, [], mode, reps=2)
     batch = binding.Batch(handles, trees, mode)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -703,6 +717,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip the per-mode comparison")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the planner's kernel choices")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -120,9 +120,8 @@ tn_status tn_set_tensor(tn_net *net, int32_t v, const void *ptr, int32_t mem);
  *   no_graph
  *       1: launch the per-slice node sequence directly instead of replaying
  *       a captured CUDA graph.
- *   tile_override
- *       >0: force this tile-table entry for every tiled node (autotuning);
- *       0: use the built-in choice.
+ *   reserved0
+ *       must be 0 (kernel choices come from the plan, see tn_autotune).
  *   prof_events, prof_first, prof_count
  *       timing hooks: prof_events[i] is recorded on the stream just before
  *       launch step prof_first+i of the per-slice sequence (steps as listed
@@ -140,7 +139,7 @@ typedef struct {
     int64_t slice_begin;
     int64_t slice_count;
     int32_t no_graph;
-    int32_t tile_override;
+    int32_t reserved0;
     void *const *prof_events; /* NULL, or prof_count+1 cudaEvent_t (as void*) */
     int32_t prof_first;
     int32_t prof_count;
@@ -262,6 +261,26 @@ tn_status tn_contract_instances(tn_net *net, const int32_t *tree_pairs, tn_mode 
  */
 tn_status tn_plan_info(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
                        const int64_t *sliced_labels, tn_mode mode, double out[8]);
+
+/*
+ * tn_autotune -- per-node kernel choice by measurement.
+ * For every tree node that runs alone in its launch step on a tiled or
+ * tensor-core kernel, each candidate -- the four CUDA-core tile shapes
+ * (64x64, 16x256, 4x1024, 256x16 outputs per block) and, in the reduced-
+ * precision modes, the tensor-core GEMM -- is launched once to warm up and
+ * then reps times between two CUDA events on `stream`; the fastest is kept
+ * in the handle's cached plan for (tree, sliced labels, mode) and used by
+ * every later contraction with that plan (results agree within the mode's
+ * tolerance whatever the choice).  Very large nodes that the tensor cores
+ * can run skip the CUDA-core shapes.  The leaves must be attached; their
+ * values do not matter.  choice (NULL or n_tensors-1 entries) receives per
+ * node 0 (not tuned), 1..4 (tile shape in the order above) or 8 (tensor
+ * core).  Synchronises `stream`.  Errors as tn_contract.
+ * Not in the paper: its executor has no kernel choices to tune.
+ */
+tn_status tn_autotune(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
+                      const int64_t *sliced_labels, tn_mode mode, int32_t reps, int32_t *choice,
+                      void *stream);
 
 /*
  * tn_plan_steps -- the per-slice launch sequence of a plan (host only).

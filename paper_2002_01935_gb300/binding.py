@@ -35,7 +35,7 @@ MODES = {"fp32": TN_MODE_FP32, "tf32_3m": TN_MODE_TF32_3M, "tf32_split": TN_MODE
 
 class tn_options(ctypes.Structure):
     _fields_ = [("slice_begin", ctypes.c_int64), ("slice_count", ctypes.c_int64),
-                ("no_graph", ctypes.c_int32), ("tile_override", ctypes.c_int32),
+                ("no_graph", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("prof_events", ctypes.POINTER(ctypes.c_void_p)), ("prof_first", ctypes.c_int32),
                 ("prof_count", ctypes.c_int32), ("slice_batch", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 5)]
@@ -87,7 +87,8 @@ _lib.tn_version.restype = ctypes.c_char_p
 _lib.tn_version.argtypes = []
 
 EXPORTS = ["tn_create", "tn_set_tensor", "tn_contract", "tn_contract_ex", "tn_contract_grad",
-           "tn_contract_noalloc", "tn_contract_instances", "tn_plan_info", "tn_plan_steps", "tn_batch_create",
+           "tn_contract_noalloc", "tn_contract_instances", "tn_autotune", "tn_plan_info", "tn_plan_steps",
+           "tn_batch_create",
            "tn_batch_contract", "tn_batch_destroy", "tn_destroy", "tn_last_error", "tn_version"]
 
 
@@ -143,12 +144,12 @@ def _tree(pairs):
 
 def tn_contract_ex(h: int, pairs, sliced, mode: int, out_ptr: int, out_mem: int, exp_ptr: int,
                    stream: int = 0, slice_begin: int = 0, slice_count: int = 0,
-                   no_graph: bool = False, tile_override: int = 0,
+                   no_graph: bool = False,
                    prof_events: Optional[Sequence[int]] = None, prof_first: int = 0,
                    slice_batch: int = 0) -> None:
     tr = _tree(pairs)
     sl = _arr(list(sliced) or [0], np.int64)
-    opt = tn_options(slice_begin, slice_count, int(no_graph), tile_override)
+    opt = tn_options(slice_begin, slice_count, int(no_graph), 0)
     opt.slice_batch = slice_batch
     if prof_events:
         evs = (ctypes.c_void_p * len(prof_events))(*prof_events)
@@ -186,6 +187,18 @@ def tn_contract_noalloc(h: int, pairs, sliced, out_ptr: int, out_mem: int, exp_p
     sl = _arr(list(sliced) or [0], np.int64)
     _check(_lib.tn_contract_noalloc(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64),
                                     out_ptr, out_mem, ctypes.cast(exp_ptr, _i64p), stream))
+
+
+def tn_autotune(h: int, pairs, sliced, mode: int, reps: int = 3, stream: int = 0) -> List[int]:
+    """Time every candidate kernel per node and keep the fastest in the
+    cached plan; returns the per-node choice (0 untuned, 1..4 tile shape,
+    8 tensor core)."""
+    tr = _tree(pairs)
+    sl = _arr(list(sliced) or [0], np.int64)
+    ch = np.zeros(max(len(pairs), 1), dtype=np.int32)
+    _check(_lib.tn_autotune(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode, reps,
+                            _p(ch, ctypes.c_int32), stream))
+    return ch[:len(pairs)].tolist()
 
 
 def tn_plan_info(h: int, pairs, sliced, mode: int = TN_MODE_FP32) -> Dict[str, float]:
@@ -272,7 +285,7 @@ class TensorNetwork:
         return tuple(self.dims[l] for l in self.open)
 
     def contract(self, pairs, sliced=(), mode="fp32", out=None, out_exp=None, stream=None,
-                 slice_begin=0, slice_count=0, no_graph=False, tile_override=0,
+                 slice_begin=0, slice_count=0, no_graph=False,
                  prof_events=None, prof_first=0, slice_batch=0):
         """Return (mantissa, exp2) torch tensors; value = mantissa * 2**exp2.
 
@@ -290,8 +303,7 @@ class TensorNetwork:
         s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
         evp = [e.cuda_event for e in prof_events] if prof_events else None
         tn_contract_ex(self.h, pairs, sliced, m, out.data_ptr(), mem, out_exp.data_ptr(), s,
-                       slice_begin, slice_count, no_graph, tile_override, evp, prof_first,
-                       slice_batch)
+                       slice_begin, slice_count, no_graph, evp, prof_first, slice_batch)
         return out, out_exp
 
     def grad(self, pairs, sliced, mode, adjoint, adj_exp2=0, grads=None, stream=None):
@@ -313,6 +325,13 @@ class TensorNetwork:
         tn_contract_grad(self.h, pairs, sliced, m, adj.view(np.float64), int(adj_exp2),
                          [g.data_ptr() if g is not None else 0 for g in grads], s)
         return grads
+
+    def autotune(self, pairs, sliced=(), mode="fp32", reps=3, stream=None):
+        """Per-node kernel choice by measurement (see tn_autotune)."""
+        import torch
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        return tn_autotune(self.h, pairs, sliced, m, reps, s)
 
     def plan_info(self, pairs, sliced=(), mode="fp32"):
         m = MODES[mode] if isinstance(mode, str) else int(mode)

@@ -253,6 +253,22 @@ tn_status tn_contract(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
                           out_exp2, stream);
 }
 
+tn_status tn_autotune(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced, const int64_t* sliced_labels,
+                      tn_mode mode, int32_t reps, int32_t* choice, void* stream) {
+    if (!net) return fail(TN_EINVAL, "tn_autotune: net is NULL");
+    for (int v = 0; v < net->d.n; ++v)
+        if (!net->d.leaves[v].ptr) return fail(TN_EINVAL, "tn_autotune: tensor without data");
+    Plan* p = nullptr;
+    tn_status st = get_plan(net, tree_pairs, n_sliced, sliced_labels, mode, &p);
+    if (st != TN_OK) return st;
+    st = ensure_instances(net, p, 1, (cudaStream_t)stream);
+    if (st != TN_OK) return st;
+    std::string err;
+    st = tn::autotune_plan(net->d, *p, reps, choice, (cudaStream_t)stream, err);
+    if (st != TN_OK) return fail(st, err);
+    return TN_OK;
+}
+
 tn_status tn_contract_grad(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
                            const int64_t* sliced_labels, tn_mode mode, const double* out_adjoint,
                            int64_t adj_exp2, void* const* leaf_grads, void* stream) {

@@ -88,7 +88,7 @@ int ilog2(int64_t x) {
 // Tiled-kernel plan of a node whose labels and strides are all powers of
 // two: index bits per group, K order, load directions, tile shape and K
 // split.  Returns false (generic kernel) when a limit is exceeded.
-bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems) {
+bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems, int force_cfg = 0) {
     static const std::vector<int> none;
     static const std::vector<int64_t> nones;
     const std::vector<int>& la = nd.ca >= 0 ? p.vlab[nd.ca] : none;
@@ -170,7 +170,15 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems) 
     t.b_nfast = fb >= 0 && has(nd.gn, fb);
     const int64_t M = int64_t(1) << t.nm, N = int64_t(1) << t.nn, K = int64_t(1) << t.nk;
     int TM = 64, TN = 64, TK = 16;
-    if (M * N <= 64 && K >= 512) {
+    const bool dot = M * N <= 64 && K >= 512;
+    if (force_cfg >= kTile64x64 && force_cfg <= kTile256x16 && !dot) {
+        // a shape forced by the autotuner (any shape is valid: tiles clip)
+        static const int shapes[5][3] = {{0, 0, 0}, {64, 64, 16}, {16, 256, 16}, {4, 1024, 4}, {256, 16, 16}};
+        t.cfg = force_cfg;
+        TM = shapes[force_cfg][0];
+        TN = shapes[force_cfg][1];
+        TK = shapes[force_cfg][2];
+    } else if (dot) {
         t.cfg = kTileDot;
         TM = (int)M;
         TN = (int)N;
@@ -206,6 +214,7 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems) 
         if (t.nbatch > 65535) return false;
         const int64_t outs = M * N * t.nbatch;
         int split = 1;
+        // one K tile (1024 entries) or more per part; about 256 parts in all
         while (outs * split < 256 && (K / (split * 2)) >= 1024 && split < 1024) split *= 2;
         t.split = split;
         t.kchunk = ((K / split + 255) / 256) * 256;
@@ -1035,7 +1044,6 @@ tn_status run_instances(NetDesc& d, Plan& p, void* unit, int n_inst, const int64
     if (out_mem == TN_MEM_HOST) CK(cudaStreamSynchronize(stream));
     return TN_OK;
 }
-#undef CK
 
 
 tn_status make_generic_args_node(const NetDesc& d, const Plan& p, const Node& nd, GenericArgs& g,
@@ -1084,6 +1092,145 @@ bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_e
     nd.kind = kTensorCore;
     return true;
 }
+
+// ---- autotuner: the kernel of every node that runs alone in its launch
+// step is chosen by timing each candidate on the device.
+static cudaError_t launch_node(const NetDesc& d, const Plan& p, const Node& nd, cudaStream_t s) {
+    if (nd.kind == kTensorCore)
+        return launch_tc(nd.tile, p.mode == TN_MODE_BF16_SPLIT ? 2 : (p.mode == TN_MODE_TF32_SPLIT ? 1 : 0),
+                         d.is_complex(), s);
+    return launch_tile(nd.tile, d.is_complex(), s);
+}
+
+// Node k rebuilt as variant v (1..4: tile shape, kVariantTC: tensor core),
+// keeping its device bindings; false if the variant does not apply.
+static bool make_variant(const NetDesc& d, const Plan& p, int k, int v, Node& out, int64_t& split_elems) {
+    const Node& nd = p.nodes[k];
+    Node t = nd;
+    if (!plan_tile(d, p, t, split_elems, v == kVariantTC ? 0 : v)) return false;
+    if (t.tile.cfg == kTileDot) return false;
+    t.kind = kTiled;
+    if (v == kVariantTC && !make_tensor_core(d, p.mode, t, split_elems)) return false;
+    TileArgs& a = t.tile;
+    const TileArgs& o = nd.tile;
+    a.A = o.A;
+    a.B = o.B;
+    a.C = o.C;
+    a.P = o.P;
+    a.sla = o.sla;
+    a.slb = o.slb;
+    a.ctl = o.ctl;
+    a.sc = o.sc;
+    a.conj_a = o.conj_a;
+    a.conj_b = o.conj_b;
+    a.t_done = o.t_done;
+    a.in = o.in;
+    out = t;
+    return true;
+}
+
+tn_status autotune_plan(NetDesc& d, Plan& p, int reps, int32_t* choice, cudaStream_t s, std::string& err) {
+    const int nn = (int)p.nodes.size();
+    if (choice)
+        for (int k = 0; k < nn; ++k) choice[k] = 0;
+    if (reps < 1) reps = 1;
+    // nodes that run alone in their step, on a tiled or tensor-core kernel
+    std::vector<int> tune;
+    for (const Step& st : p.steps)
+        if (!st.wave) {
+            const Node& nd = p.nodes[st.node];
+            if ((nd.kind == kTiled && nd.tile.cfg != kTileDot) || nd.kind == kTensorCore) tune.push_back(st.node);
+        }
+    if (tune.empty()) return TN_OK;
+    // bind this call's leaves (their values do not matter for timing)
+    tn_status st = configure_instances(d, p, 1, 1, std::vector<int64_t>(), err);
+    if (st != TN_OK) return st;
+    st = upload_leaf_sizes(d, p, 1, std::vector<int64_t>(), err);
+    if (st != TN_OK) return st;
+    std::vector<const void*> lp;
+    st = prepare_leaves(d, p, false, lp, s, err);
+    if (st != TN_OK) return st;
+    CK(launch_leaf_max(p.leaf_ptr_dev, p.leaf_nfloat_dev, p.leafmax, d.n, s, max_leaf_floats(d)));
+    // candidates and the shared P buffer they need
+    std::vector<std::vector<std::pair<int, Node>>> cand(nn);
+    int64_t split_elems = 0;
+    for (int k : tune) {
+        const Node& nd = p.nodes[k];
+        const int vc = nd.tile.nm + nd.tile.nn + nd.tile.nk + nd.tile.nb;  // log2 of the products
+        Node tc;
+        const bool has_tc = !p.no_tensor_cores && make_variant(d, p, k, kVariantTC, tc, split_elems);
+        if (has_tc) cand[k].push_back({kVariantTC, tc});
+        // CUDA-core shapes, unless the node is so large that they cannot win
+        if (!has_tc || vc < 32)
+            for (int v = kTile64x64; v <= kTile256x16; ++v) {
+                Node t;
+                if (make_variant(d, p, k, v, t, split_elems)) cand[k].push_back({v, t});
+            }
+    }
+    const int64_t need = (split_elems * (int64_t)d.elem_bytes() + 1023) / 1024 * 1024;
+    const int G = std::max(p.alloc_inst, 1);
+    if (need > p.split_bytes) {
+        CK(cudaStreamSynchronize(s));
+        if (p.split_buf) CK(cudaFree(p.split_buf));
+        p.split_buf = nullptr;
+        CK(cudaMalloc(&p.split_buf, need * G));
+        p.split_bytes = need;
+        for (auto& nd : p.nodes) nd.tile.P = p.split_buf;
+        for (auto& cs : cand)
+            for (auto& c : cs) c.second.tile.P = p.split_buf;
+    }
+    // a valid control block (slice 0 of the range) for the single-node launches
+    CK(launch_begin_call(p.ctl, 0, p.d_sliced, p.acc, 0, s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int k : tune) {
+        float best = 1e30f;
+        int best_v = 0;
+        Node best_node = p.nodes[k];
+        for (auto& c : cand[k]) {
+            c.second.tile.in = p.nodes[k].tile.in;
+            cudaError_t e = launch_node(d, p, c.second, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_node(d, p, c.second, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                err = std::string("autotune: ") + cudaGetErrorString(e);
+                return TN_ECUDA;
+            }
+            if (ms < best) {
+                best = ms;
+                best_v = c.first;
+                best_node = c.second;
+            }
+        }
+        p.nodes[k] = best_node;
+        if (choice) choice[k] = best_v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the control block must not look like a finished call; the next call
+    // rebuilds the instance configuration and the captured graph
+    CK(cudaStreamSynchronize(s));
+    Control zero{};
+    CK(cudaMemcpy(p.ctl, &zero, sizeof(Control), cudaMemcpyHostToDevice));
+    if (p.descs_dev) {
+        std::vector<TileArgs> descs(nn);
+        for (int k = 0; k < nn; ++k) descs[k] = p.nodes[k].tile;
+        CK(cudaMemcpy(p.descs_dev, descs.data(), sizeof(TileArgs) * nn, cudaMemcpyHostToDevice));
+    }
+    p.cfg_inst = -1;
+    p.graph_ptrs.clear();
+    p.tuned = true;
+    return TN_OK;
+}
+
+#undef CK
 
 bool plan_tile_node(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems) {
     return plan_tile(d, p, nd, split_elems);

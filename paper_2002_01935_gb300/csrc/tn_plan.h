@@ -62,6 +62,7 @@ struct GradState;  // reverse-sweep plan and device state (tn_grad.cpp)
 
 struct Plan {
     tn_mode mode = TN_MODE_FP32;
+    bool tuned = false;             // kernels chosen by autotune_plan
     bool force_generic = false;  // every node on the generic kernel
     bool no_waves = false;       // one launch per node
     bool no_tensor_cores = false;  // reduced-precision modes on CUDA cores only
@@ -120,6 +121,11 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err);
 Node build_node(const NetDesc& d, const Plan& p, int id, int a, int b, const std::vector<int>& keep);
 bool plan_tile_node(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems);
 bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_elems);
+// Autotuner variant code of the tensor-core kernel (tile shapes use TileCfg).
+constexpr int kVariantTC = 8;
+// Times every candidate kernel of the nodes that run alone in a launch step
+// and keeps the fastest in the plan (device state must be allocated).
+tn_status autotune_plan(NetDesc& d, Plan& p, int reps, int32_t* choice, cudaStream_t s, std::string& err);
 tn_status make_generic_args_node(const NetDesc& d, const Plan& p, const Node& nd, GenericArgs& g,
                                  std::string& err);
 tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err);

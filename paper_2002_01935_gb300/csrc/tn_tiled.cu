@@ -381,47 +381,48 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a)
     const int nk = a.nk;
     if (threadIdx.x == 0) {
         // tile bits: the kDotLow lowest strides of each operand, then the
-        // lowest K positions, up to 2 * kDotLow bits
+        // lowest K positions, up to 2 * kDotLow bits (strides of one
+        // operand's labels are distinct powers of two)
+        int8_t by[2][64];
+        for (int q = 0; q < 64; ++q) by[0][q] = by[1][q] = -1;
         bool in[kMaxBits];
-        for (int p = 0; p < nk; ++p) in[p] = false;
-        for (int side = 0; side < 2; ++side) {
-            const uint8_t* sh = side ? a.b_k : a.a_k;
-            for (int r = 0; r < kDotLow; ++r) {
-                int best = -1;
-                for (int p = 0; p < nk; ++p)
-                    if (!in[p] && sh[p] != kNoBit && (best < 0 || sh[p] < sh[best])) best = p;
-                if (best < 0) break;
-                // only bits below the operand's kDotLow-th smallest stride
-                int rank = 0;
-                for (int q = 0; q < nk; ++q) rank += sh[q] != kNoBit && sh[q] < sh[best];
-                if (rank >= kDotLow) break;
-                in[best] = true;
-            }
+        for (int p = 0; p < nk; ++p) {
+            in[p] = false;
+            if (a.a_k[p] < 64) by[0][a.a_k[p]] = (int8_t)p;
+            if (a.b_k[p] < 64) by[1][a.b_k[p]] = (int8_t)p;
         }
         int cnt = 0;
-        for (int p = 0; p < nk; ++p) cnt += in[p];
+        for (int side = 0; side < 2; ++side)
+            for (int q = 0, r = 0; q < 64 && r < kDotLow; ++q)
+                if (by[side][q] >= 0) {
+                    if (!in[by[side][q]]) ++cnt;
+                    in[by[side][q]] = true;
+                    ++r;
+                }
         for (int p = 0; p < nk && cnt < 2 * kDotLow; ++p)
             if (!in[p]) {
                 in[p] = true;
                 ++cnt;
             }
         int t = 0, u = 0;
+        int8_t pos[kMaxBits];
         for (int p = 0; p < nk; ++p) {
-            if (in[p]) tk[t++] = (int8_t)p;
-            else nt[u++] = (int8_t)p;
+            if (in[p]) {
+                pos[p] = (int8_t)t;
+                tk[t++] = (int8_t)p;
+            } else {
+                nt[u++] = (int8_t)p;
+            }
         }
         // each operand's order of the tile bits (ascending stride, absent last)
         for (int side = 0; side < 2; ++side) {
             const uint8_t* sh = side ? a.b_k : a.a_k;
             int8_t* o = side ? ob : oa;
-            bool used[2 * kDotLow] = {};
-            for (int w = 0; w < t; ++w) {
-                int best = -1;
-                for (int j = 0; j < t; ++j)
-                    if (!used[j] && (best < 0 || (int)sh[tk[j]] < (int)sh[tk[best]])) best = j;
-                used[best] = true;
-                o[w] = (int8_t)best;  // index into tk
-            }
+            int w = 0;
+            for (int q = 0; q < 64; ++q)
+                if (by[side][q] >= 0 && in[by[side][q]]) o[w++] = pos[by[side][q]];
+            for (int j = 0; j < t; ++j)
+                if (sh[tk[j]] >= 64) o[w++] = (int8_t)j;
         }
         n_tile = t;
         n_rest = u;
