@@ -8,6 +8,8 @@ Workloads (``--workload``):
               float32 leaves.  One step = one full contraction (all slices).
   circuit4x4  one amplitude of a 4x4-qubit, 8-cycle random circuit, greedy
               tree, no slicing (complex64 leaves).
+  circuit5x5  one amplitude of a 5x5-qubit, 10-cycle random circuit (the
+              smaller circuit that is checked in full), greedy tree.
   circuit7x7  one amplitude of a 7x7-qubit, 14-cycle random circuit,
               Hyper-Greedy tree sliced to W_s <= 28; one step = a bounded
               sample of consecutive slices (``--slices``); the time per
@@ -46,6 +48,7 @@ METRIC = "contraction FLOP/s & % roofline per tree; s/amplitude; rel. error vs F
 WORKLOAD_NAMES = {
     "ising100": "ising_rr3_n100_beta0.3_greedy_ws24",
     "circuit4x4": "circuit_4x4_8cyc_greedy_amplitude",
+    "circuit5x5": "circuit_5x5_10cyc_greedy_amplitude",
     "circuit7x7": "circuit_7x7_14cyc_hypergreedy_ws28_slice_sample",
     "batch": "batch_6x6_12cyc_amplitudes_plus_256_ising",
 }
@@ -253,11 +256,12 @@ def run_reference(args):
     from oracle import build as obuild
     from oracle import tree
     obuild.build()
-    if args.workload not in ("ising100", "circuit4x4"):
+    if args.workload not in ("ising100", "circuit4x4", "circuit5x5"):
         print(json.dumps({"impl": "reference", "unavailable":
                           f"the FP64 oracle needs hours per step on the {args.workload} workload"}))
         return 0
-    w = wl_ising(0) if args.workload == "ising100" else wl_circuit(4, 4, 8, 0)
+    w = (wl_ising(0) if args.workload == "ising100" else
+         wl_circuit(4, 4, 8, 0) if args.workload == "circuit4x4" else wl_circuit(5, 5, 10, 0))
     net, pairs, sliced, info = w["net"], w["pairs"], w["sliced"], w["info"]
     for _ in range(1 if args.warmup > 0 else 0):
         tree.contract_net(net, pairs, sliced)
@@ -358,6 +362,8 @@ def run_network(args, torch, dist, rank, world, local):
         w = wl_ising(rank)
     elif args.workload == "circuit4x4":
         w = wl_circuit(4, 4, 8, rank)
+    elif args.workload == "circuit5x5":
+        w = wl_circuit(5, 5, 10, rank)
     else:
         w = wl_circuit7x7(rank, args.slices)
     net, pairs, sliced, info = w["net"], w["pairs"], w["sliced"], w["info"]
@@ -407,11 +413,13 @@ def run_network(args, torch, dist, rank, world, local):
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
+    torch.cuda.nvtx.range_push("timed")  # ncu --nvtx --nvtx-include timed/ profiles just this
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
         m, e = call(prof_events=dom_ev[i], prof_first=dom)
         ends[i].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clocks = clk.stop()
     call_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
@@ -603,12 +611,14 @@ def run_batch(args, torch, dist, rank, world, local):
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
+    torch.cuda.nvtx.range_push("timed")
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
         out, ex, lat = batch.contract()
         ends[i].record(stream)
         lats.append(lat)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clocks = clk.stop()
     total_ms = sum(s.elapsed_time(t) for s, t in zip(starts, ends))
