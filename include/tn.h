@@ -58,12 +58,15 @@ typedef enum {
 
 /*
  * Arithmetic used inside each pairwise contraction (the cross-slice sum is
- * always FP64).  Complex products are formed from real products (4M), or
- * from three real products (3M) where named.
+ * always FP64).  Complex products are formed from four real products (4M)
+ * or, where named, three (3M: Re A Re B, Im A Im B and (Re A + Im A)(Re B +
+ * Im B)).
  *   TN_MODE_FP32       : FP32 FMA on CUDA cores (plain complex64 / float32)
- *   TN_MODE_TF32_3M    : one TF32 tensor-core pass per real product, 3M
+ *   TN_MODE_TF32_3M    : operands rounded to TF32, one tensor-core pass,
+ *                        3M for complex nodes with >= 128 columns on both
+ *                        sides (4M otherwise), FP32 accumulation
  *   TN_MODE_TF32_SPLIT : operands split hi+lo in TF32, three products
- *                        (hi*hi + hi*lo + lo*hi), FP32 accumulation
+ *                        (hi*hi + hi*lo + lo*hi), 4M, FP32 accumulation
  *   TN_MODE_BF16_SPLIT : the same split in BF16
  * Nodes too small for the tensor cores run the FP32 path in every mode.
  */

@@ -246,7 +246,7 @@ static cudaError_t enqueue_batch(BatchPlan& b, cudaStream_t s) {
             const Node& nd = p.nodes[st.node];
             const int di = b.desc_base[st.net] + st.node;
             if (nd.kind == kTensorCore)
-                e = launch_tc(b.descs[di], b.mode == TN_MODE_BF16_SPLIT ? 2 : (b.mode == TN_MODE_TF32_SPLIT ? 1 : 0),
+                e = launch_tc(b.descs[di], tc_prec_of_mode(b.mode),
                               st.cplx, s);
             else if (nd.kind == kTiled)
                 e = launch_tile(b.descs[di], st.cplx, s);

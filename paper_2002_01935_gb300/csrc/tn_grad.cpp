@@ -125,7 +125,7 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
             split_elems = std::max(split_elems, (int64_t)nd.tile.split * nd.tile.nbatch *
                                                     (int64_t(1) << (nd.tile.nm + nd.tile.nn)));
         if (nd.kind == kTensorCore) {
-            const int prec = f.mode == TN_MODE_BF16_SPLIT ? 2 : (f.mode == TN_MODE_TF32_SPLIT ? 1 : 0);
+            const int prec = tc_prec_of_mode(f.mode);
             const int64_t eb = d.elem_bytes();
             split_elems = std::max(split_elems, (tc_geom(nd.tile, d.is_complex(), prec).total + eb - 1) / eb);
         }
@@ -250,7 +250,7 @@ void free_grad(Plan& p) {
 static cudaError_t launch_node(const Node& nd, const GenericArgs& g, const TileArgs& t, tn_mode mode,
                                bool c, cudaStream_t s) {
     if (nd.kind == kTensorCore)
-        return launch_tc(t, mode == TN_MODE_BF16_SPLIT ? 2 : (mode == TN_MODE_TF32_SPLIT ? 1 : 0), c, s);
+        return launch_tc(t, tc_prec_of_mode(mode), c, s);
     if (nd.kind == kTiled) return launch_tile(t, c, s);
     return launch_generic(g, c, s);
 }

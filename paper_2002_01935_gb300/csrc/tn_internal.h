@@ -149,22 +149,40 @@ struct TcGeom {
     int64_t total;     // bytes per instance, 1 KB aligned
 };
 
+// Tensor-core precision of a mode (tn_mode values): 0 TF32 single product
+// (4M), 1 TF32 hi+lo, 2 BF16 hi+lo, 3 TF32 single product (3M).
+__host__ __device__ inline int tc_prec_of_mode(int mode) {
+    return mode == 3 ? 2 : (mode == 2 ? 1 : (mode == 1 ? 3 : 0));
+}
+
+// 3M needs a complex node with >= 128 complex columns; otherwise the node
+// runs the single-product 4M form.
+__host__ __device__ inline int tc_prec_of_node(const TileArgs& a, bool cplx, int prec) {
+    if (prec == 3 && (!cplx || a.nm < 7 || a.nn < 7)) return 0;
+    return prec;
+}
+
+// With prec 3 (3M), R and Q are not interleaved or expanded: both hold three
+// real planes [rows] x K -- Re, Im and Re + Im -- and the GEMM forms
+// T1 = Re A Re B, T2 = Im A Im B, T3 = (Re A + Im A)(Re B + Im B), so that
+// Re C = T1 - T2 and Im C = T3 - T1 - T2.
 __host__ __device__ inline TcGeom tc_geom(const TileArgs& a, bool cplx, int prec) {
     TcGeom g;
-    const int c = cplx ? 2 : 1;
+    prec = tc_prec_of_node(a, cplx, prec);
+    const int c = cplx && prec != 3 ? 2 : 1;
     g.rows_r = int64_t(1) << (a.tc_swap ? a.nn : a.nm);
     g.cols_q = (int64_t(1) << (a.tc_swap ? a.nm : a.nn)) * c;
     g.kr = (int64_t(1) << a.nk) * c;
     g.esz = prec == 2 ? 2 : 4;
     g.ke = 128 / g.esz;
     g.nkb = (g.kr + g.ke - 1) / g.ke;
-    g.parts = prec == 0 ? 1 : 2;
+    g.parts = prec == 0 ? 1 : (prec == 3 ? 3 : 2);
     g.plane_r = a.nbatch * g.rows_r * g.nkb * 128;
     g.plane_q = a.nbatch * g.cols_q * g.nkb * 128;
     g.region_r = (g.parts * g.plane_r + 1023) / 1024 * 1024;
     g.part_off = g.region_r + (g.parts * g.plane_q + 1023) / 1024 * 1024;
     const int64_t parts_bytes =
-        a.split > 1 ? (int64_t)a.split * a.nbatch * (int64_t(1) << (a.nm + a.nn)) * 4 * c : 0;
+        a.split > 1 ? (int64_t)a.split * a.nbatch * (int64_t(1) << (a.nm + a.nn)) * 4 * (cplx ? 2 : 1) : 0;
     g.total = g.part_off + (parts_bytes + 1023) / 1024 * 1024;
     return g;
 }
@@ -231,7 +249,7 @@ cudaError_t launch_batch_finish(const BatchRoot* roots, int n, double* out, int6
 cudaError_t launch_leaf_grad(const LeafGradArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s);  // tn_tiled.cu
-// Tensor-core node (tn_tc.cu): prec 0 TF32, 1 TF32 hi+lo, 2 BF16 hi+lo.
+// Tensor-core node (tn_tc.cu): prec as tc_prec_of_mode.
 // Packs both operands into a.P (TcGeom) and runs the bulk-copy-fed tcgen05
 // GEMM: three launches, plus a fixed-order reduction with a K split.
 cudaError_t launch_tc(const TileArgs& a, int prec, bool is_c, cudaStream_t s);

@@ -786,7 +786,7 @@ static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, cons
         } else {
             const Node& nd = p.nodes[st.node];
             if (nd.kind == kTensorCore)
-                e = launch_tc(nd.tile, p.mode == TN_MODE_BF16_SPLIT ? 2 : (p.mode == TN_MODE_TF32_SPLIT ? 1 : 0),
+                e = launch_tc(nd.tile, tc_prec_of_mode(p.mode),
                               c, s);
             else if (nd.kind == kTiled)
                 e = launch_tile(nd.tile, c, s);
@@ -1070,7 +1070,7 @@ bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_e
     t.tc_swap = swap;
     t.split = 1;
     t.kchunk = int64_t(1) << t.nk;
-    const int prec = mode == TN_MODE_BF16_SPLIT ? 2 : (mode == TN_MODE_TF32_SPLIT ? 1 : 0);
+    const int prec = tc_prec_of_mode(mode);
     // K split: the grid should fill whole waves of the 152 SMs (one CTA
     // each); split only while every part keeps >= 8 k-blocks
     {
@@ -1097,7 +1097,7 @@ bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_e
 // step is chosen by timing each candidate on the device.
 static cudaError_t launch_node(const NetDesc& d, const Plan& p, const Node& nd, cudaStream_t s) {
     if (nd.kind == kTensorCore)
-        return launch_tc(nd.tile, p.mode == TN_MODE_BF16_SPLIT ? 2 : (p.mode == TN_MODE_TF32_SPLIT ? 1 : 0),
+        return launch_tc(nd.tile, tc_prec_of_mode(p.mode),
                          d.is_complex(), s);
     return launch_tile(nd.tile, d.is_complex(), s);
 }

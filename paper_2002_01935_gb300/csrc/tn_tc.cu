@@ -245,6 +245,8 @@ struct Parts<1> {
     }
 };
 template <>
+struct Parts<3> : Parts<0> {};
+template <>
 struct Parts<2> {
     using E = __nv_bfloat16;
     static __device__ __forceinline__ void split(float x, E& h, E& l) {
@@ -443,7 +445,20 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const __grid_constant__ T
             const T v = stage[tidx[i]];
             const int64_t g = gb + tdst[i];
             const int64_t row = g >> nk, k = g & (K - 1);
-            if constexpr (CPLX) {
+            if constexpr (CPLX && PREC == 3) {
+                // 3M: planes Re, Im, Re + Im of either operand, K not doubled
+                const float re = v.x * f, im = (conj ? -v.y : v.y) * f;
+                const int64_t pos = tile_pos(row, k, geo.nkb, LG_KE, LG_ESZ);
+                put1<0>(hi, 0, pos, re);
+                put1<0>(hi + lo_off, 0, pos, im);
+                put1<0>(hi + 2 * lo_off, 0, pos, re + im);
+                for (int64_t z = k + geo.kr; z < (int64_t)1 << LG_KE; z += geo.kr) {
+                    const int64_t pz = tile_pos(row, z, geo.nkb, LG_KE, LG_ESZ);
+                    put1<0>(hi, 0, pz, 0.f);
+                    put1<0>(hi + lo_off, 0, pz, 0.f);
+                    put1<0>(hi + 2 * lo_off, 0, pz, 0.f);
+                }
+            } else if constexpr (CPLX) {
                 const float re = v.x * f, im = (conj ? -v.y : v.y) * f;
                 if (role == 0) {
                     put2<PREC>(hi, lo_off, tile_pos(row, 2 * k, geo.nkb, LG_KE, LG_ESZ), re, im);
@@ -724,6 +739,203 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
+// k_umma3m: complex node as three real TF32 GEMMs (3M) over the Re, Im and
+// Re + Im planes of R and Q, one accumulator each (128 complex columns per
+// tile); the epilogue forms Re C = T1 - T2 and Im C = T3 - T1 - T2.
+// ---------------------------------------------------------------------------
+template <int STAGES>
+__global__ void __launch_bounds__(kGemmThreads, 1) k_umma3m(const __grid_constant__ TileArgs a) {
+    constexpr int STAGE_BYTES = 6 * kTileBytes;
+    constexpr int KE = 32, MMA_K = 8, KSTEPS = KE / MMA_K;
+    constexpr uint32_t ALLOC = 512;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ int consumed;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int64_t b = blockIdx.z % a.nbatch;
+    const int inst = (int)(blockIdx.z / a.nbatch);
+    const int sp = blockIdx.y, nsplit = gridDim.y;
+    const InstanceInfo& in = a.in;
+    const int64_t slice = a.ctl->slice + (int64_t)inst * in.slice_step;
+    if (slice >= a.ctl->slice_end) return;
+    const TcGeom geo = tc_geom(a, true, 3);
+    const int nkl = (int)(geo.nkb / nsplit);
+    const int64_t kb0 = (int64_t)sp * nkl;
+    const int tiles_m = (int)(geo.rows_r / kBM), tiles_n = (int)(geo.cols_q / kBN);
+    int tm, tn;
+    {
+        const int per_group = kGroupRows * tiles_n;
+        const int grp = (int)blockIdx.x / per_group;
+        const int first = grp * kGroupRows;
+        const int gsz = min(kGroupRows, tiles_m - first);
+        const int r = (int)blockIdx.x - grp * per_group;
+        tm = first + r % gsz;
+        tn = r / gsz;
+    }
+    const int row0 = tm * kBM, col0 = tn * kBN;
+    const char* pk = reinterpret_cast<const char*>(a.P) + (int64_t)inst * in.p_is * 8;
+    ScaleIO sio = a.sc;
+    if (sio.max_a) sio.max_a += (int64_t)inst * in.sa_is;
+    if (sio.exp_a) sio.exp_a += (int64_t)inst * in.sa_is;
+    if (sio.max_b) sio.max_b += (int64_t)inst * in.sb_is;
+    if (sio.exp_b) sio.exp_b += (int64_t)inst * in.sb_is;
+    sio.max_c += (int64_t)inst * in.sc_is;
+    sio.exp_c += (int64_t)inst * in.sc_is;
+    const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
+    const int resid = (eA - max(-120, min(120, eA))) + (eB - max(-120, min(120, eB)));
+    if (blockIdx.x == 0 && sp == 0 && b == 0 && tid == 0 && sio.exp_c)
+        *sio.exp_c = (sio.exp_a ? *sio.exp_a : 0) + (sio.exp_b ? *sio.exp_b : 0) + eA + eB;
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(ALLOC));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (tid == 0) {
+            const char* r_src = pk + ((b * tiles_m + tm) * geo.nkb + kb0) * kTileBytes;
+            const char* q_src = pk + geo.region_r + ((b * tiles_n + tn) * geo.nkb + kb0) * kTileBytes;
+            int issued = 0;
+            for (int j = 0; j < nkl; ++j) {
+                const int s = j % STAGES;
+                if (j >= STAGES &&
+                    !mbar_wait(&empty_bar[s], (uint32_t)(((j / STAGES) + 1) & 1), &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                uint8_t* st = smem + s * STAGE_BYTES;
+                mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+                const int64_t o = (int64_t)j * kTileBytes;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    bulk_load(st + q * kTileBytes, r_src + q * geo.plane_r + o, kTileBytes, &full_bar[s]);
+                    bulk_load(st + (3 + q) * kTileBytes, q_src + q * geo.plane_q + o, kTileBytes, &full_bar[s]);
+                }
+                ++issued;
+            }
+            if (abort_flag) {
+                int dummy = 0;
+                for (int j = *(volatile int*)&consumed; j < issued; ++j)
+                    mbar_wait(&full_bar[j % STAGES], (uint32_t)((j / STAGES) & 1), &dummy);
+            }
+        }
+    } else if (warp == 1) {
+        if (tid == 32) {
+            const uint32_t idesc = instr_desc(2u, kBM, kBN);
+            for (int j = 0; j < nkl; ++j) {
+                const int s = j % STAGES;
+                if (!mbar_wait(&full_bar[s], (uint32_t)((j / STAGES) & 1), &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+                for (int k = 0; k < KSTEPS; ++k) {
+                    const uint32_t off = k * MMA_K * 4;
+                    const uint32_t acc = (j > 0 || k > 0) ? 1u : 0u;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        mma<false>(tmem + (uint32_t)(q * kBN), smem_desc(base + q * kTileBytes + off),
+                                   smem_desc(base + (3 + q) * kTileBytes + off), idesc, acc);
+                }
+                mma_commit(&empty_bar[s]);
+                *(volatile int*)&consumed = j + 1;
+            }
+            mma_commit(&done_bar);
+        }
+    } else {
+        float lmax = 0.f;
+        const bool done0 = mbar_wait(&done_bar, 0u, &abort_flag);
+        tc_fence_after();
+        const bool done = __all_sync(0xffffffffu, done0 && !abort_flag);
+        if (done) {
+            const int quad = warp & 3;
+            const int row = row0 + quad * 32 + (tid & 31);
+            const int64_t M = int64_t(1) << a.nm, N = int64_t(1) << a.nn;
+            float* C = nsplit > 1
+                           ? reinterpret_cast<float*>(const_cast<char*>(pk) + geo.part_off) +
+                                 (int64_t)sp * a.nbatch * M * N * 2
+                           : reinterpret_cast<float*>(a.C) + (int64_t)inst * in.c_is * 2;
+            const int rs = nsplit > 1 ? 0 : resid;
+            for (int col = 0; col < kBN; col += 16) {
+                float t1[16], t2[16], t3[16];
+                const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col;
+                tmem_ld16(ta, t1);
+                tmem_ld16(ta + kBN, t2);
+                tmem_ld16(ta + 2 * kBN, t3);
+                float re[16], im[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    re[i] = t1[i] - t2[i];
+                    im[i] = t3[i] - t1[i] - t2[i];
+                    if (rs) {
+                        re[i] = ldexpf(re[i], -rs);
+                        im[i] = ldexpf(im[i], -rs);
+                    }
+                    lmax = fmaxf(lmax, fmaxf(fabsf(re[i]), fabsf(im[i])));
+                }
+                const int64_t j0 = col0 + col;  // first complex column of the chunk
+                if (!a.tc_swap) {
+                    float* crow = C + ((b * M + row) * N + j0) * 2;
+#pragma unroll
+                    for (int i = 0; i < 16; i += 2)
+                        *reinterpret_cast<float4*>(crow + 2 * i) = make_float4(re[i], im[i], re[i + 1], im[i + 1]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        *reinterpret_cast<float2*>(C + ((b * M + j0 + i) * N + row) * 2) = make_float2(re[i], im[i]);
+                }
+            }
+        } else if ((tid & 31) == 0) {
+            atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
+        }
+        if (nsplit == 1) {
+            for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+            if ((tid & 31) == 0 && lmax > 0.f) atomicMax(sio.max_c, __float_as_uint(lmax));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        int dummy = 0;
+        bool quiet = true;
+        if (tid == 32) quiet = mbar_wait(&done_bar, 0u, &dummy);
+        quiet = __shfl_sync(0xffffffffu, quiet, 0);
+        tc_fence_after();
+        if (!quiet && tid == 32) atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ALLOC));
+    }
+    if (a.t_done && tid == 0 && nsplit == 1) {
+        unsigned long long tnow;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tnow));
+        atomicMax(a.t_done, tnow);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_tc_reduce: C = sum of the K parts in part order (FP32), the residual
 // renormalisation and the node maximum.  blockIdx.y: instance.
 // ---------------------------------------------------------------------------
@@ -773,6 +985,34 @@ __global__ void __launch_bounds__(256) k_tc_reduce(const __grid_constant__ TileA
 // ---------------------------------------------------------------------------
 namespace {
 
+cudaError_t launch_tc_3m(const TileArgs& a, cudaStream_t s) {
+    constexpr int STAGES = 2;
+    constexpr int SMEM = STAGES * 6 * kTileBytes + 1024;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_umma3m<STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const TcGeom g = tc_geom(a, true, 3);
+    const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
+    const int split = a.split > 1 ? a.split : 1;
+    if (g.nkb % split) return cudaErrorInvalidValue;
+    auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 1024, 1), 152 * 8); };
+    const int64_t elems_a = int64_t(1) << (a.nk + a.nm + a.nb);
+    const int64_t elems_b = int64_t(1) << (a.nk + a.nn + a.nb);
+    k_pack<true, 3><<<dim3(blocks(a.tc_swap ? elems_b : elems_a), ni), kPackThreads, 0, s>>>(a, 0);
+    k_pack<true, 3><<<dim3(blocks(a.tc_swap ? elems_a : elems_b), ni), kPackThreads, 0, s>>>(a, 1);
+    const int64_t tiles = (g.rows_r / kBM) * (g.cols_q / kBN);
+    k_umma3m<STAGES><<<dim3((unsigned)tiles, (unsigned)split, (unsigned)(a.nbatch * ni)), kGemmThreads, SMEM, s>>>(a);
+    if (split > 1) {
+        const int64_t n4 = (a.nbatch << (a.nm + a.nn)) * 2 / 4;
+        const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>((n4 + 255) / 256, 1), 152 * 8);
+        k_tc_reduce<true, 3><<<dim3(nb, ni), 256, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 template <bool CPLX, int PREC>
 cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     constexpr int STAGES = PREC == 0 ? 6 : 3;
@@ -812,6 +1052,8 @@ cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_tc(const TileArgs& a, int prec, bool is_c, cudaStream_t s) {
+    prec = tc_prec_of_node(a, is_c, prec);
+    if (prec == 3) return launch_tc_3m(a, s);
     if (is_c) {
         if (prec == 0) return launch_tc_t<true, 0>(a, s);
         if (prec == 1) return launch_tc_t<true, 1>(a, s);
