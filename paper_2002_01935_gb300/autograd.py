@@ -32,7 +32,10 @@ class _Contract(torch.autograd.Function):
         ctx.tnw.set_tensors(list(ctx.saved_tensors))
         adj = grad_out.detach().to(torch.complex128 if ctx.tnw.dtype == binding.TN_C64
                                    else torch.float64).cpu().numpy()
-        grads = ctx.tnw.grad(ctx.pairs, ctx.sliced, ctx.mode, adj)
+        # leaves that need no gradient get none (NULL: skipped by the sweep)
+        need = ctx.needs_input_grad[4:]
+        grads = [torch.empty_like(t) if nd else None for t, nd in zip(ctx.saved_tensors, need)]
+        grads = ctx.tnw.grad(ctx.pairs, ctx.sliced, ctx.mode, adj, grads=grads)
         return (None, None, None, None, *grads)
 
 

@@ -271,6 +271,7 @@ class TensorNetwork:
         import torch
         want = torch.complex64 if self.dtype == TN_C64 else torch.float32
         self._keep = []
+        attached = getattr(self, "_attached", None) or [None] * len(tensors)
         for v, t in enumerate(tensors):
             if t.dtype != want:
                 raise TypeError(f"leaf {v}: dtype {t.dtype}, expected {want}")
@@ -278,7 +279,11 @@ class TensorNetwork:
                 raise ValueError(f"leaf {v} must be contiguous")
             mem = TN_MEM_DEVICE if t.is_cuda else TN_MEM_HOST
             self._keep.append(t)
-            tn_set_tensor(self.h, v, t.data_ptr(), mem)
+            key = (t.data_ptr(), mem)
+            if attached[v] != key:  # unchanged pointers need no call
+                tn_set_tensor(self.h, v, key[0], mem)
+                attached[v] = key
+        self._attached = attached
 
     @property
     def out_shape(self) -> Tuple[int, ...]:

@@ -147,6 +147,7 @@ struct TcGeom {
     int64_t region_r;  // bytes of all R planes, 1 KB aligned (Q starts here)
     int64_t part_off;  // bytes: start of the split-K partials
     int64_t total;     // bytes per instance, 1 KB aligned
+    int bn;            // GEMM tile columns: 256 where the columns allow, else 128
 };
 
 // Tensor-core precision of a mode (tn_mode values): 0 TF32 single product
@@ -184,6 +185,7 @@ __host__ __device__ inline TcGeom tc_geom(const TileArgs& a, bool cplx, int prec
     const int64_t parts_bytes =
         a.split > 1 ? (int64_t)a.split * a.nbatch * (int64_t(1) << (a.nm + a.nn)) * 4 * (cplx ? 2 : 1) : 0;
     g.total = g.part_off + (parts_bytes + 1023) / 1024 * 1024;
+    g.bn = (prec != 3 && g.cols_q % 256 == 0) ? 256 : 128;
     return g;
 }
 

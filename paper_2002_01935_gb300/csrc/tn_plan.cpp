@@ -1075,7 +1075,7 @@ bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_e
     // each); split only while every part keeps >= 8 k-blocks
     {
         const TcGeom g0 = tc_geom(t, c, prec);
-        const double tiles = (double)t.nbatch * (g0.rows_r / 128) * (g0.cols_q / 128);
+        const double tiles = (double)t.nbatch * (g0.rows_r / 128) * (g0.cols_q / g0.bn);
         double best = 0.0;
         for (int s = 1; s <= 16 && g0.nkb / s >= 8; s *= 2) {
             const double w = tiles * s / 152.0;

@@ -490,13 +490,16 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const __grid_constant__ T
 // output tile (grouped raster), blockIdx.y: K split, blockIdx.z: batch entry
 // and instance.
 // ---------------------------------------------------------------------------
-template <bool CPLX, int PREC, int STAGES>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+template <bool CPLX, int PREC, int STAGES, int BN>
+__global__ void __launch_bounds__(64 + BN, 1)
     k_umma(const __grid_constant__ TileArgs a, int nacc) {
     constexpr bool BF16 = PREC == 2;
     constexpr bool SPLIT = PREC != 0;
     constexpr int PARTS = SPLIT ? 2 : 1;
-    constexpr int STAGE_BYTES = 2 * PARTS * kTileBytes;
+    constexpr int QB = BN * kRowBytes;                    // one Q part per stage
+    constexpr int QT = BN / kBM;                           // packed 128-row Q tiles per part
+    constexpr int EPI_WARPS = BN / 32;                     // 128 rows x BN columns, 128 each
+    constexpr int STAGE_BYTES = PARTS * (kTileBytes + QB);
     constexpr int KE = BF16 ? 64 : 32;     // packed elements per 128-byte row
     constexpr int MMA_K = BF16 ? 16 : 8;   // K per instruction
     constexpr int KSTEPS = KE / MMA_K;
@@ -526,7 +529,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const TcGeom geo = tc_geom(a, CPLX, PREC);
     const int nkl = (int)(geo.nkb / nsplit);   // k-blocks of this K part
     const int64_t kb0 = (int64_t)sp * nkl;
-    const int tiles_m = (int)(geo.rows_r / kBM), tiles_n = (int)(geo.cols_q / kBN);
+    const int tiles_m = (int)(geo.rows_r / kBM), tiles_n = (int)(geo.cols_q / BN);
     // grouped raster: kGroupRows row tiles share the column tiles they stream
     int tm, tn;
     {
@@ -538,9 +541,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         tm = first + r % gsz;
         tn = r / gsz;
     }
-    const int row0 = tm * kBM, col0 = tn * kBN;
+    const int row0 = tm * kBM, col0 = tn * BN;
     const int nchain = (nkl + chain - 1) / chain;
-    const uint32_t alloc_cols = nacc <= 1 ? 128u : (nacc == 2 ? 256u : 512u);
+    const int acc_cols = nacc * BN;
+    const uint32_t alloc_cols = acc_cols <= 128 ? 128u : (acc_cols <= 256 ? 256u : 512u);
     const int ESZ = CPLX ? 8 : 4;
     const char* pk = reinterpret_cast<const char*>(a.P) + (int64_t)inst * in.p_is * ESZ;
 
@@ -565,7 +569,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         mbar_init(&done_bar, 1);
         for (int q = 0; q < kNumAcc; ++q) {
             mbar_init(&acc_full[q], 1);
-            mbar_init(&acc_empty[q], 4);  // one arrival per epilogue warp
+            mbar_init(&acc_empty[q], EPI_WARPS);  // one arrival per epilogue warp
         }
         abort_flag = 0;
         consumed = 0;
@@ -587,7 +591,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         // ---------------- bulk-copy producer ----------------
         if (tid == 0) {
             const char* r_src = pk + ((b * tiles_m + tm) * geo.nkb + kb0) * kTileBytes;
-            const char* q_src = pk + geo.region_r + ((b * tiles_n + tn) * geo.nkb + kb0) * kTileBytes;
+            const char* q_src = pk + geo.region_r + ((b * tiles_n + tn) * QT * geo.nkb + kb0) * kTileBytes;
             int issued = 0;
             for (int j = 0; j < nkl; ++j) {
                 const int s = j % STAGES;
@@ -602,8 +606,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 bulk_load(st, r_src + o, kTileBytes, &full_bar[s]);
                 if constexpr (SPLIT) bulk_load(st + kTileBytes, r_src + geo.plane_r + o, kTileBytes, &full_bar[s]);
                 uint8_t* sq = st + PARTS * kTileBytes;
-                bulk_load(sq, q_src + o, kTileBytes, &full_bar[s]);
-                if constexpr (SPLIT) bulk_load(sq + kTileBytes, q_src + geo.plane_q + o, kTileBytes, &full_bar[s]);
+                // BN columns: QT consecutive 128-row packed tiles, one after the other in smem
+#pragma unroll
+                for (int h = 0; h < QT; ++h) {
+                    const int64_t oh = o + (int64_t)h * geo.nkb * kTileBytes;
+                    bulk_load(sq + h * kTileBytes, q_src + oh, kTileBytes, &full_bar[s]);
+                    if constexpr (SPLIT)
+                        bulk_load(sq + QB + h * kTileBytes, q_src + geo.plane_q + oh, kTileBytes, &full_bar[s]);
+                }
                 ++issued;
             }
             if (abort_flag) {
@@ -616,7 +626,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (tid == 32) {
-            const uint32_t idesc = instr_desc(FMT, kBM, kBN);
+            const uint32_t idesc = instr_desc(FMT, kBM, BN);
             for (int j = 0; j < nkl; ++j) {
                 const int s = j % STAGES;
                 if (!mbar_wait(&full_bar[s], (uint32_t)((j / STAGES) & 1), &abort_flag)) {
@@ -634,8 +644,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 tc_fence_after();
                 const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
                 const uint32_t r_hi = base, q_hi = base + PARTS * kTileBytes;
-                const uint32_t r_lo = base + kTileBytes, q_lo = q_hi + kTileBytes;
-                const uint32_t d = tmem + (uint32_t)(q * kBN);
+                const uint32_t r_lo = base + kTileBytes, q_lo = q_hi + QB;
+                const uint32_t d = tmem + (uint32_t)(q * BN);
 #pragma unroll
                 for (int k = 0; k < KSTEPS; ++k) {
                     const uint32_t off = k * MMA_K * (BF16 ? 2 : 4);
@@ -653,12 +663,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             mma_commit(&done_bar);  // arrives once every MMA issued above has completed
         }
     } else {
-        // ---------------- epilogue (warps 2-5) ----------------
+        // ---------------- epilogue (warps 2..) ----------------
         float lmax = 0.f;
-        const int quad = warp & 3;  // TMEM lanes 32*quad.. belong to this warp
-        float sum[kBN];
+        const int quad = warp & 3;                   // TMEM lanes 32*quad.. belong to this warp
+        const int cbase = ((warp - 2) >> 2) * kBM;   // this warp's 128 of the BN columns
+        float sum[kBM];
 #pragma unroll
-        for (int i = 0; i < kBN; ++i) sum[i] = 0.f;
+        for (int i = 0; i < kBM; ++i) sum[i] = 0.f;
         bool ok = true;
         for (int ch = 0; ch < nchain && ok; ++ch) {
             const int q = ch % nacc;
@@ -666,9 +677,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             ok = __all_sync(0xffffffffu, got && !abort_flag);  // tcgen05.ld is warp-collective
             if (!ok) break;
             tc_fence_after();
-            const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(q * kBN);
+            const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(q * BN + cbase);
 #pragma unroll
-            for (int col = 0; col < kBN; col += 32) tmem_add32(ta + (uint32_t)col, sum + col);
+            for (int col = 0; col < kBM; col += 32) tmem_add32(ta + (uint32_t)col, sum + col);
             tc_fence_before();
             __syncwarp();
             if ((tid & 31) == 0) mbar_arrive(&acc_empty[q]);
@@ -683,8 +694,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                            : reinterpret_cast<float*>(a.C) + (int64_t)inst * in.c_is * (CPLX ? 2 : 1);
             const int rs = nsplit > 1 ? 0 : resid;
 #pragma unroll
-            for (int col = 0; col < kBN; col += 16) {
-                float* v = sum + col;
+            for (int cc = 0; cc < kBM; cc += 16) {
+                float* v = sum + cc;
+                const int col = cbase + cc;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     if (rs) v[i] = ldexpf(v[i], -rs);
@@ -1013,18 +1025,29 @@ cudaError_t launch_tc_3m(const TileArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <bool CPLX, int PREC>
-cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
-    constexpr int STAGES = PREC == 0 ? 6 : 3;
-    constexpr int PARTS = PREC == 0 ? 1 : 2;
-    constexpr int SMEM = STAGES * 2 * PARTS * kTileBytes + 1024;
+// pipeline depth: as many stages as fit in 192 KB
+template <int PREC, int BN>
+constexpr int stages_of() {
+    return (192 * 1024) / ((PREC == 0 ? 1 : 2) * (kTileBytes + BN * kRowBytes));
+}
+
+template <bool CPLX, int PREC, int BN>
+cudaError_t launch_umma(const TileArgs& a, dim3 grid, int nacc, cudaStream_t s) {
+    constexpr int STAGES = stages_of<PREC, BN>();
+    constexpr int SMEM = STAGES * (PREC == 0 ? 1 : 2) * (kTileBytes + BN * kRowBytes) + 1024;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_umma<CPLX, PREC, STAGES>,
+        cudaError_t e = cudaFuncSetAttribute(k_umma<CPLX, PREC, STAGES, BN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess) return e;
         configured = true;
     }
+    k_umma<CPLX, PREC, STAGES, BN><<<grid, 64 + BN, SMEM, s>>>(a, nacc);
+    return cudaGetLastError();
+}
+
+template <bool CPLX, int PREC>
+cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     const TcGeom g = tc_geom(a, CPLX, PREC);
     const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
     const int split = a.split > 1 ? a.split : 1;
@@ -1037,10 +1060,13 @@ cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     k_pack<CPLX, PREC><<<dim3(blocks(n_q), ni), kPackThreads, 0, s>>>(a, 1);
     const int nkl = (int)(g.nkb / split);
     const int chains = PREC == 0 ? (nkl + 3) / 4 : nkl;
-    const int nacc = chains >= kNumAcc ? kNumAcc : (chains >= 2 ? 2 : 1);
-    const int64_t tiles = (g.rows_r / kBM) * (g.cols_q / kBN);
+    const int max_acc = 512 / g.bn;
+    const int nacc = chains >= max_acc ? max_acc : (chains >= 2 ? 2 : 1);
+    const int64_t tiles = (g.rows_r / kBM) * (g.cols_q / g.bn);
     dim3 grid((unsigned)tiles, (unsigned)split, (unsigned)(a.nbatch * ni));
-    k_umma<CPLX, PREC, STAGES><<<grid, kGemmThreads, SMEM, s>>>(a, nacc);
+    cudaError_t e = g.bn == 256 ? launch_umma<CPLX, PREC, 256>(a, grid, nacc, s)
+                                : launch_umma<CPLX, PREC, 128>(a, grid, nacc, s);
+    if (e != cudaSuccess) return e;
     if (split > 1) {
         const int64_t n4 = (a.nbatch << (a.nm + a.nn)) * (CPLX ? 2 : 1) / 4;
         const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>((n4 + 255) / 256, 1), 152 * 8);
