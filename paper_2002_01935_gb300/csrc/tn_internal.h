@@ -150,6 +150,30 @@ struct TcGeom {
     int bn;            // GEMM tile columns: 256 where the columns allow, else 128
 };
 
+// Tile plan of one operand pack (tensor-core path), computed on the host:
+// a tile is 2^t entries (t <= 10), enumerated in source order by the
+// src_add offsets and in packed order by dst_add (packed index) and
+// idx_add (stage index); the u remaining bits step between tiles.
+struct PackPlan {
+    int t, u;
+    int64_t src_add[10];
+    int64_t dst_add[10];
+    int32_t idx_add[10];
+    int64_t rest_src[3 * kMaxBits];
+    int64_t rest_dst[3 * kMaxBits];
+};
+
+// Tile plan of an inner-product node (k_dot), computed on the host: a tile
+// is 2^t K entries; entry e in A's order is at A offset sum of a_add and
+// K-order index sum of ca_add over its set bits (likewise for B); the u
+// remaining K bits step between tiles.
+struct DotPlan {
+    int t, u;
+    int64_t a_add[10], b_add[10];
+    int32_t ca_add[10], cb_add[10];
+    int64_t rest_a[kMaxBits], rest_b[kMaxBits];
+};
+
 // Tensor-core precision of a mode (tn_mode values): 0 TF32 single product
 // (4M), 1 TF32 hi+lo, 2 BF16 hi+lo, 3 TF32 single product (3M).
 __host__ __device__ inline int tc_prec_of_mode(int mode) {

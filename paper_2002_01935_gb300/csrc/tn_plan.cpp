@@ -1072,12 +1072,12 @@ bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_e
     t.kchunk = int64_t(1) << t.nk;
     const int prec = tc_prec_of_mode(mode);
     // K split: the grid should fill whole waves of the 152 SMs (one CTA
-    // each); split only while every part keeps >= 8 k-blocks
+    // each); split only while every part keeps >= 4 k-blocks
     {
         const TcGeom g0 = tc_geom(t, c, prec);
         const double tiles = (double)t.nbatch * (g0.rows_r / 128) * (g0.cols_q / g0.bn);
         double best = 0.0;
-        for (int s = 1; s <= 16 && g0.nkb / s >= 8; s *= 2) {
+        for (int s = 1; s <= 16 && g0.nkb / s >= 4; s *= 2) {
             const double w = tiles * s / 152.0;
             const double eff = w / std::ceil(w);
             if (eff > best + 0.03) {
@@ -1203,8 +1203,12 @@ tn_status autotune_plan(NetDesc& d, Plan& p, int reps, int32_t* choice, cudaStre
                 err = std::string("autotune: ") + cudaGetErrorString(e);
                 return TN_ECUDA;
             }
-            if (ms < best) {
-                best = ms;
+            // the planner's choice stays unless another is clearly faster
+            const bool planned = c.second.kind == p.nodes[k].kind &&
+                                 (c.second.kind == kTensorCore || c.second.tile.cfg == p.nodes[k].tile.cfg);
+            const float eff = planned ? ms * 0.95f : ms;
+            if (eff < best) {
+                best = eff;
                 best_v = c.first;
                 best_node = c.second;
             }

@@ -33,6 +33,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "../../include/tn.h"
@@ -313,26 +314,20 @@ __device__ __forceinline__ void put1(char* hi, int64_t lo_off, int64_t pos, floa
 // packed order (consecutive threads write consecutive packed addresses).
 // ---------------------------------------------------------------------------
 template <bool CPLX, int PREC>
-__global__ void __launch_bounds__(kPackThreads) k_pack(const __grid_constant__ TileArgs a, int role) {
+__global__ void __launch_bounds__(kPackThreads)
+    k_pack(const __grid_constant__ TileArgs a, const __grid_constant__ PackPlan pp, int role) {
     using T = typename std::conditional<CPLX, float2, float>::type;
     __shared__ T stage[kPackMaxTile + kPackMaxTile / 32];  // +1 per 32: no bank conflicts
     __shared__ int64_t tsrc[kPackMaxTile];
     __shared__ int64_t tdst[kPackMaxTile];
     __shared__ uint16_t tidx[kPackMaxTile];
-    __shared__ uint8_t shift[3 * kMaxBits];
-    __shared__ int8_t ts[2 * kPackLow], td[2 * kPackLow];
-    __shared__ int8_t nt[3 * kMaxBits];
-    __shared__ int64_t src_add[2 * kPackLow], dst_add[2 * kPackLow];
-    __shared__ int idx_add[2 * kPackLow];
-    __shared__ int n_tile, n_rest;
 
     const bool useB = (role == 0) == (a.tc_swap != 0);
     const int inst = blockIdx.y;
     const InstanceInfo& in = a.in;
     const int64_t slice = a.ctl->slice + (int64_t)inst * in.slice_step;
     if (slice >= a.ctl->slice_end) return;
-    const int nk = a.nk, no = useB ? a.nn : a.nm, nb = a.nb;
-    const int nbits = nk + no + nb;
+    const int nk = a.nk;
     const TcGeom geo = tc_geom(a, CPLX, PREC);
     constexpr int LG_ESZ = PREC == 2 ? 1 : 2, LG_KE = 7 - LG_ESZ;
     const int ESZ = CPLX ? 8 : 4;
@@ -348,73 +343,22 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const __grid_constant__ T
     const float f = ldexpf(1.f, -max(-120, min(120, e)));
     const bool conj = useB ? a.conj_b : a.conj_a;
 
-    if (threadIdx.x == 0) {
-        const uint8_t* xk = useB ? a.b_k : a.a_k;
-        const uint8_t* xo = useB ? a.b_n : a.a_m;
-        const uint8_t* xb = useB ? a.b_b : a.a_b;
-        for (int p = 0; p < nbits; ++p)
-            shift[p] = p < nk ? xk[p] : (p < nk + no ? xo[p - nk] : xb[p - nk - no]);
-        // tile bits: the kPackLow lowest packed positions and the kPackLow
-        // lowest source strides (strides of distinct labels are distinct)
-        int8_t by_shift[64];
-        for (int s = 0; s < 64; ++s) by_shift[s] = -1;
-        for (int p = 0; p < nbits; ++p)
-            if (shift[p] < 64) by_shift[shift[p]] = (int8_t)p;  // kNoBit: K bit the operand lacks
-        bool in_tile[3 * kMaxBits];
-        for (int p = 0; p < nbits; ++p) in_tile[p] = p < kPackLow;
-        for (int s = 0, r = 0; s < 64 && r < kPackLow; ++s)
-            if (by_shift[s] >= 0) {
-                in_tile[by_shift[s]] = true;
-                ++r;
-            }
-        // where the two sets overlap, fill the tile up with the next packed
-        // positions so that every tile has 2 * kPackLow bits of work
-        {
-            int cnt = 0;
-            for (int p = 0; p < nbits; ++p) cnt += in_tile[p];
-            for (int p = kPackLow; p < nbits && cnt < 2 * kPackLow; ++p)
-                if (!in_tile[p]) {
-                    in_tile[p] = true;
-                    ++cnt;
-                }
-        }
-        int t = 0, u = 0;
-        for (int p = 0; p < nbits; ++p) {
-            if (in_tile[p]) td[t++] = (int8_t)p;
-            else nt[u++] = (int8_t)p;
-        }
-        // the same tile bits in source order (ascending stride; absent bits,
-        // which repeat the same source value, last)
-        int w = 0;
-        for (int s = 0; s < 64; ++s)
-            if (by_shift[s] >= 0 && in_tile[by_shift[s]]) ts[w++] = by_shift[s];
-        for (int i = 0; i < t; ++i)
-            if (shift[td[i]] >= 64) ts[w++] = td[i];
-        for (int j = 0; j < t; ++j) {
-            src_add[j] = shift[ts[j]] < 64 ? int64_t(1) << shift[ts[j]] : 0;
-            dst_add[j] = int64_t(1) << td[j];
-            int r = 0;  // position of td[j] in source order
-            while (ts[r] != td[j]) ++r;
-            idx_add[j] = 1 << r;
-        }
-        n_tile = t;
-        n_rest = u;
-    }
-    __syncthreads();
-    const int t = n_tile, u = n_rest;
+    // the tile tables: source offset of each source-order index, packed
+    // index and (padded) stage index of each packed-order index
+    const int t = pp.t, u = pp.u;
     const int tsz = 1 << t;
     for (int i = threadIdx.x; i < tsz; i += blockDim.x) {
         int64_t so = 0, dg = 0;
         int idx = 0;
         for (int j = 0; j < t; ++j)
             if ((i >> j) & 1) {
-                so += src_add[j];
-                dg += dst_add[j];
-                idx += idx_add[j];
+                so += pp.src_add[j];
+                dg += pp.dst_add[j];
+                idx += pp.idx_add[j];
             }
         tsrc[i] = so;
         tdst[i] = dg;
-        tidx[i] = (uint16_t)(idx + (idx >> 5));  // padded stage index
+        tidx[i] = (uint16_t)(idx + (idx >> 5));
     }
     __syncthreads();
     const int64_t n_tiles = int64_t(1) << u;
@@ -423,8 +367,8 @@ __global__ void __launch_bounds__(kPackThreads) k_pack(const __grid_constant__ T
         int64_t sb = 0, gb = 0;
         for (int j = 0; j < u; ++j)
             if ((tile >> j) & 1) {
-                if (shift[nt[j]] < 64) sb += int64_t(1) << shift[nt[j]];
-                gb += int64_t(1) << nt[j];
+                sb += pp.rest_src[j];
+                gb += pp.rest_dst[j];
             }
         T ld[kPackMaxTile / kPackThreads];
 #pragma unroll
@@ -997,6 +941,68 @@ __global__ void __launch_bounds__(256) k_tc_reduce(const __grid_constant__ TileA
 // ---------------------------------------------------------------------------
 namespace {
 
+// Tile bits of a pack (role 0: R, 1: Q): the kPackLow lowest packed
+// positions and the kPackLow lowest source strides, filled up with the next
+// packed positions to 2 * kPackLow bits; the other bits enumerate tiles.
+PackPlan make_pack_plan(const TileArgs& a, int role) {
+    PackPlan pp;
+    memset(&pp, 0, sizeof(pp));
+    const bool useB = (role == 0) == (a.tc_swap != 0);
+    const int nk = a.nk, no = useB ? a.nn : a.nm, nb = a.nb;
+    const int nbits = nk + no + nb;
+    const uint8_t* xk = useB ? a.b_k : a.a_k;
+    const uint8_t* xo = useB ? a.b_n : a.a_m;
+    const uint8_t* xb = useB ? a.b_b : a.a_b;
+    uint8_t shift[3 * kMaxBits];
+    for (int p = 0; p < nbits; ++p) shift[p] = p < nk ? xk[p] : (p < nk + no ? xo[p - nk] : xb[p - nk - no]);
+    int by_shift[64];
+    for (int s = 0; s < 64; ++s) by_shift[s] = -1;
+    for (int p = 0; p < nbits; ++p)
+        if (shift[p] < 64) by_shift[shift[p]] = p;  // kNoBit: a K bit the operand lacks
+    bool in_tile[3 * kMaxBits];
+    for (int p = 0; p < nbits; ++p) in_tile[p] = p < kPackLow;
+    for (int s = 0, r = 0; s < 64 && r < kPackLow; ++s)
+        if (by_shift[s] >= 0) {
+            in_tile[by_shift[s]] = true;
+            ++r;
+        }
+    int cnt = 0;
+    for (int p = 0; p < nbits; ++p) cnt += in_tile[p];
+    for (int p = kPackLow; p < nbits && cnt < 2 * kPackLow; ++p)
+        if (!in_tile[p]) {
+            in_tile[p] = true;
+            ++cnt;
+        }
+    int td[2 * kPackLow], ts[2 * kPackLow];
+    int t = 0, u = 0;
+    for (int p = 0; p < nbits; ++p) {
+        if (in_tile[p]) {
+            td[t++] = p;
+        } else {
+            pp.rest_src[u] = shift[p] < 64 ? int64_t(1) << shift[p] : 0;
+            pp.rest_dst[u] = int64_t(1) << p;
+            ++u;
+        }
+    }
+    // the same tile bits in source order (ascending stride; absent bits,
+    // which repeat the same source value, last)
+    int w = 0;
+    for (int s = 0; s < 64; ++s)
+        if (by_shift[s] >= 0 && in_tile[by_shift[s]]) ts[w++] = by_shift[s];
+    for (int i = 0; i < t; ++i)
+        if (shift[td[i]] >= 64) ts[w++] = td[i];
+    for (int j = 0; j < t; ++j) {
+        pp.src_add[j] = shift[ts[j]] < 64 ? int64_t(1) << shift[ts[j]] : 0;
+        pp.dst_add[j] = int64_t(1) << td[j];
+        int r = 0;
+        while (ts[r] != td[j]) ++r;
+        pp.idx_add[j] = 1 << r;
+    }
+    pp.t = t;
+    pp.u = u;
+    return pp;
+}
+
 cudaError_t launch_tc_3m(const TileArgs& a, cudaStream_t s) {
     constexpr int STAGES = 2;
     constexpr int SMEM = STAGES * 6 * kTileBytes + 1024;
@@ -1010,11 +1016,12 @@ cudaError_t launch_tc_3m(const TileArgs& a, cudaStream_t s) {
     const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
     const int split = a.split > 1 ? a.split : 1;
     if (g.nkb % split) return cudaErrorInvalidValue;
-    auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 1024, 1), 152 * 8); };
+    // every pack CTA stages several 1024-entry tiles (its setup is amortised)
+    auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), 152 * 4); };
     const int64_t elems_a = int64_t(1) << (a.nk + a.nm + a.nb);
     const int64_t elems_b = int64_t(1) << (a.nk + a.nn + a.nb);
-    k_pack<true, 3><<<dim3(blocks(a.tc_swap ? elems_b : elems_a), ni), kPackThreads, 0, s>>>(a, 0);
-    k_pack<true, 3><<<dim3(blocks(a.tc_swap ? elems_a : elems_b), ni), kPackThreads, 0, s>>>(a, 1);
+    k_pack<true, 3><<<dim3(blocks(a.tc_swap ? elems_b : elems_a), ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 0), 0);
+    k_pack<true, 3><<<dim3(blocks(a.tc_swap ? elems_a : elems_b), ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 1), 1);
     const int64_t tiles = (g.rows_r / kBM) * (g.cols_q / kBN);
     k_umma3m<STAGES><<<dim3((unsigned)tiles, (unsigned)split, (unsigned)(a.nbatch * ni)), kGemmThreads, SMEM, s>>>(a);
     if (split > 1) {
@@ -1054,10 +1061,11 @@ cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     if (g.nkb % split) return cudaErrorInvalidValue;
     const int64_t elems_a = int64_t(1) << (a.nk + a.nm + a.nb);
     const int64_t elems_b = int64_t(1) << (a.nk + a.nn + a.nb);
-    auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 1024, 1), 152 * 8); };
+    // every pack CTA stages several 1024-entry tiles (its setup is amortised)
+    auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), 152 * 4); };
     const int64_t n_r = a.tc_swap ? elems_b : elems_a, n_q = a.tc_swap ? elems_a : elems_b;
-    k_pack<CPLX, PREC><<<dim3(blocks(n_r), ni), kPackThreads, 0, s>>>(a, 0);
-    k_pack<CPLX, PREC><<<dim3(blocks(n_q), ni), kPackThreads, 0, s>>>(a, 1);
+    k_pack<CPLX, PREC><<<dim3(blocks(n_r), ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 0), 0);
+    k_pack<CPLX, PREC><<<dim3(blocks(n_q), ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 1), 1);
     const int nkl = (int)(g.nkb / split);
     const int chains = PREC == 0 ? (nkl + 3) / 4 : nkl;
     const int max_acc = 512 / g.bn;

@@ -17,6 +17,7 @@
 // e = frexp exponent of their max |component|, which is exact; the output
 // max goes to the node's slot for its consumer.
 #include <cuda_runtime.h>
+#include <cstring>
 #include <stdint.h>
 
 #include "tn_internal.h"
@@ -363,13 +364,11 @@ constexpr int kDotLow = 5;
 constexpr int kDotTile = 1 << (2 * kDotLow);
 
 template <bool CPLX>
-__global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a) {
+__global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a, const __grid_constant__ DotPlan dp) {
     using T = typename VT<CPLX>::T;
     __shared__ T sA[kDotTile + kDotTile / 32], sB[kDotTile + kDotTile / 32];
     __shared__ int64_t offA[kDotTile], offB[kDotTile];
     __shared__ uint16_t canA[kDotTile], canB[kDotTile];
-    __shared__ int8_t tk[2 * kDotLow], oa[2 * kDotLow], ob[2 * kDotLow], nt[kMaxBits];
-    __shared__ int n_tile, n_rest;
     __shared__ T red[256];
     const int64_t N = 1ll << a.nn, M = 1ll << a.nm;
     const int64_t m = (int64_t)blockIdx.x / N, n = (int64_t)blockIdx.x % N;
@@ -378,67 +377,16 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a)
     const View vw = inst_view(a, blockIdx.z / a.split, (int)sizeof(T));
     if (!vw.live) return;
     const Scales sc = node_scales(vw.sc, blockIdx.x == 0 && blockIdx.y == 0 && sp == 0 && threadIdx.x == 0);
-    const int nk = a.nk;
-    if (threadIdx.x == 0) {
-        // tile bits: the kDotLow lowest strides of each operand, then the
-        // lowest K positions, up to 2 * kDotLow bits (strides of one
-        // operand's labels are distinct powers of two)
-        int8_t by[2][64];
-        for (int q = 0; q < 64; ++q) by[0][q] = by[1][q] = -1;
-        bool in[kMaxBits];
-        for (int p = 0; p < nk; ++p) {
-            in[p] = false;
-            if (a.a_k[p] < 64) by[0][a.a_k[p]] = (int8_t)p;
-            if (a.b_k[p] < 64) by[1][a.b_k[p]] = (int8_t)p;
-        }
-        int cnt = 0;
-        for (int side = 0; side < 2; ++side)
-            for (int q = 0, r = 0; q < 64 && r < kDotLow; ++q)
-                if (by[side][q] >= 0) {
-                    if (!in[by[side][q]]) ++cnt;
-                    in[by[side][q]] = true;
-                    ++r;
-                }
-        for (int p = 0; p < nk && cnt < 2 * kDotLow; ++p)
-            if (!in[p]) {
-                in[p] = true;
-                ++cnt;
-            }
-        int t = 0, u = 0;
-        int8_t pos[kMaxBits];
-        for (int p = 0; p < nk; ++p) {
-            if (in[p]) {
-                pos[p] = (int8_t)t;
-                tk[t++] = (int8_t)p;
-            } else {
-                nt[u++] = (int8_t)p;
-            }
-        }
-        // each operand's order of the tile bits (ascending stride, absent last)
-        for (int side = 0; side < 2; ++side) {
-            const uint8_t* sh = side ? a.b_k : a.a_k;
-            int8_t* o = side ? ob : oa;
-            int w = 0;
-            for (int q = 0; q < 64; ++q)
-                if (by[side][q] >= 0 && in[by[side][q]]) o[w++] = pos[by[side][q]];
-            for (int j = 0; j < t; ++j)
-                if (sh[tk[j]] >= 64) o[w++] = (int8_t)j;
-        }
-        n_tile = t;
-        n_rest = u;
-    }
-    __syncthreads();
-    const int t = n_tile, u = n_rest, tsz = 1 << t;
+    const int t = dp.t, u = dp.u, tsz = 1 << t;
     for (int e = threadIdx.x; e < tsz; e += blockDim.x) {
         int64_t xa = 0, xb = 0;
         int ca = 0, cb = 0;
         for (int w = 0; w < t; ++w)
             if ((e >> w) & 1) {
-                const int pa = tk[oa[w]], pb = tk[ob[w]];
-                if (a.a_k[pa] != kNoBit) xa += int64_t(1) << a.a_k[pa];
-                if (a.b_k[pb] != kNoBit) xb += int64_t(1) << a.b_k[pb];
-                ca += 1 << oa[w];
-                cb += 1 << ob[w];
+                xa += dp.a_add[w];
+                xb += dp.b_add[w];
+                ca += dp.ca_add[w];
+                cb += dp.cb_add[w];
             }
         offA[e] = xa;
         offB[e] = xb;
@@ -461,8 +409,8 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a)
         int64_t ba = baseA, bb = baseB;
         for (int j = 0; j < u; ++j)
             if ((tile >> j) & 1) {
-                if (a.a_k[nt[j]] != kNoBit) ba += int64_t(1) << a.a_k[nt[j]];
-                if (a.b_k[nt[j]] != kNoBit) bb += int64_t(1) << a.b_k[nt[j]];
+                ba += dp.rest_a[j];
+                bb += dp.rest_b[j];
             }
         T xa[kDotTile / 256], xb[kDotTile / 256];
 #pragma unroll
@@ -621,6 +569,65 @@ static cudaError_t launch_cfg(const TileArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Tile bits of an inner-product node: the kDotLow lowest strides of each
+// operand, then the lowest K positions, up to 2 * kDotLow bits; each
+// operand's order of them (ascending stride, absent bits last).
+static DotPlan make_dot_plan(const TileArgs& a) {
+    DotPlan dp;
+    memset(&dp, 0, sizeof(dp));
+    const int nk = a.nk;
+    int by[2][64];
+    for (int q = 0; q < 64; ++q) by[0][q] = by[1][q] = -1;
+    bool in[kMaxBits] = {};
+    for (int p = 0; p < nk; ++p) {
+        if (a.a_k[p] < 64) by[0][a.a_k[p]] = p;
+        if (a.b_k[p] < 64) by[1][a.b_k[p]] = p;
+    }
+    int cnt = 0;
+    for (int side = 0; side < 2; ++side)
+        for (int q = 0, r = 0; q < 64 && r < kDotLow; ++q)
+            if (by[side][q] >= 0) {
+                if (!in[by[side][q]]) ++cnt;
+                in[by[side][q]] = true;
+                ++r;
+            }
+    for (int p = 0; p < nk && cnt < 2 * kDotLow; ++p)
+        if (!in[p]) {
+            in[p] = true;
+            ++cnt;
+        }
+    int tk[2 * kDotLow], pos[kMaxBits];
+    int t = 0, u = 0;
+    for (int p = 0; p < nk; ++p) {
+        if (in[p]) {
+            pos[p] = t;
+            tk[t++] = p;
+        } else {
+            dp.rest_a[u] = a.a_k[p] != kNoBit ? int64_t(1) << a.a_k[p] : 0;
+            dp.rest_b[u] = a.b_k[p] != kNoBit ? int64_t(1) << a.b_k[p] : 0;
+            ++u;
+        }
+    }
+    for (int side = 0; side < 2; ++side) {
+        const uint8_t* sh = side ? a.b_k : a.a_k;
+        int order[2 * kDotLow];
+        int w = 0;
+        for (int q = 0; q < 64; ++q)
+            if (by[side][q] >= 0 && in[by[side][q]]) order[w++] = pos[by[side][q]];
+        for (int j = 0; j < t; ++j)
+            if (sh[tk[j]] >= 64) order[w++] = j;
+        for (int i = 0; i < t; ++i) {
+            const int p = tk[order[i]];
+            const int64_t add = sh[p] != kNoBit ? int64_t(1) << sh[p] : 0;
+            (side ? dp.b_add : dp.a_add)[i] = add;
+            (side ? dp.cb_add : dp.ca_add)[i] = 1 << order[i];
+        }
+    }
+    dp.t = t;
+    dp.u = u;
+    return dp;
+}
+
 template <bool CPLX>
 static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
     cudaError_t e;
@@ -632,7 +639,8 @@ static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
         case kTileDot: {
             const int64_t outs = 1ll << (a.nm + a.nn);
             const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
-            k_dot<CPLX><<<dim3((unsigned)outs, (unsigned)a.nbatch, (unsigned)(a.split * ni)), 256, 0, s>>>(a);
+            k_dot<CPLX><<<dim3((unsigned)outs, (unsigned)a.nbatch, (unsigned)(a.split * ni)), 256, 0, s>>>(
+                a, make_dot_plan(a));
             e = cudaGetLastError();
             break;
         }
