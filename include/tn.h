@@ -106,9 +106,11 @@ tn_status tn_create(tn_net **out, tn_dtype dt, int32_t n_tensors, const int32_t 
  *   mem   TN_MEM_DEVICE: a device pointer, borrowed (not copied): it must
  *         stay valid and unchanged until every contraction that reads it
  *         has completed on its stream.
- *         TN_MEM_HOST: a host pointer, read by every later tn_contract
- *         (copied to library-owned device memory on the call's stream;
- *         page-locked memory makes that copy asynchronous).
+ *         TN_MEM_HOST: a host pointer, read by every later tn_contract:
+ *         during the call all host leaves are gathered into one library-
+ *         owned page-locked image, which goes to the device as one copy on
+ *         the call's stream (under stream capture: one copy per leaf, read
+ *         when the graph runs).
  * Errors: TN_EINVAL (v out of range, ptr NULL for a non-empty tensor).
  */
 tn_status tn_set_tensor(tn_net *net, int32_t v, const void *ptr, int32_t mem);

@@ -395,6 +395,10 @@ void tn_destroy(tn_net* net) {
     for (auto& p : net->plans) tn::free_device(*p);
     for (auto& lf : net->d.leaves)
         if (lf.staged) cudaFree(lf.staged);
+    tn::NetDesc& d = net->d;
+    if (d.stage_host) cudaFreeHost(d.stage_host);
+    if (d.stage_dev) cudaFree(d.stage_dev);
+    if (d.stage_done) cudaEventDestroy(d.stage_done);
     if (net->unit) cudaFree(net->unit);
     delete net;
 }

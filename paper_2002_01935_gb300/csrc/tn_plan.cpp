@@ -822,8 +822,47 @@ static tn_status prepare_leaves(NetDesc& d, Plan& p, bool capturing, std::vector
     const int n = d.n;
     const size_t eb = d.elem_bytes();
     lp.assign(n, nullptr);
+    // several host leaves outside capture: one page-locked image, one copy
+    int n_host = 0;
+    int64_t total = 0;
+    for (int v = 0; v < n; ++v)
+        if (d.leaves[v].mem == TN_MEM_HOST) {
+            ++n_host;
+            total += (d.leaves[v].size * (int64_t)eb + 15) / 16 * 16;
+        }
+    if (!capturing && n_host > 1) {
+        if (d.stage_bytes < total) {
+            if (d.stage_pending) CK(cudaEventSynchronize(d.stage_done));
+            d.stage_pending = false;
+            if (d.stage_host) CK(cudaFreeHost(d.stage_host));
+            if (d.stage_dev) CK(cudaFree(d.stage_dev));
+            d.stage_host = d.stage_dev = nullptr;
+            d.stage_bytes = 0;
+            CK(cudaMallocHost(&d.stage_host, total));
+            CK(cudaMalloc(&d.stage_dev, total));
+            d.stage_bytes = total;
+            if (!d.stage_done) CK(cudaEventCreateWithFlags(&d.stage_done, cudaEventDisableTiming));
+        }
+        // the image may still be read by the previous call's copy
+        if (d.stage_pending) CK(cudaEventSynchronize(d.stage_done));
+        int64_t off = 0;
+        for (int v = 0; v < n; ++v) {
+            LeafDesc& lf = d.leaves[v];
+            if (lf.mem == TN_MEM_HOST) {
+                memcpy((char*)d.stage_host + off, lf.ptr, lf.size * eb);
+                lp[v] = (char*)d.stage_dev + off;
+                off += (lf.size * (int64_t)eb + 15) / 16 * 16;
+            } else {
+                lp[v] = lf.ptr;
+            }
+        }
+        CK(cudaMemcpyAsync(d.stage_dev, d.stage_host, off, cudaMemcpyHostToDevice, stream));
+        CK(cudaEventRecord(d.stage_done, stream));
+        d.stage_pending = true;
+    }
     for (int v = 0; v < n; ++v) {
         LeafDesc& lf = d.leaves[v];
+        if (lf.mem == TN_MEM_HOST && lp[v]) continue;  // staged above
         if (lf.mem == TN_MEM_HOST) {
             int64_t bytes = std::max<int64_t>(lf.size * (int64_t)eb, 16);
             if (lf.staged_bytes < bytes) {
@@ -1072,12 +1111,12 @@ bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_e
     t.kchunk = int64_t(1) << t.nk;
     const int prec = tc_prec_of_mode(mode);
     // K split: the grid should fill whole waves of the 152 SMs (one CTA
-    // each); split only while every part keeps >= 4 k-blocks
+    // each); split only while every part keeps >= 8 k-blocks
     {
         const TcGeom g0 = tc_geom(t, c, prec);
         const double tiles = (double)t.nbatch * (g0.rows_r / 128) * (g0.cols_q / g0.bn);
         double best = 0.0;
-        for (int s = 1; s <= 16 && g0.nkb / s >= 4; s *= 2) {
+        for (int s = 1; s <= 16 && g0.nkb / s >= 8; s *= 2) {
             const double w = tiles * s / 152.0;
             const double eff = w / std::ceil(w);
             if (eff > best + 0.03) {
@@ -1159,7 +1198,14 @@ tn_status autotune_plan(NetDesc& d, Plan& p, int reps, int32_t* choice, cudaStre
         const int vc = nd.tile.nm + nd.tile.nn + nd.tile.nk + nd.tile.nb;  // log2 of the products
         Node tc;
         const bool has_tc = !p.no_tensor_cores && make_variant(d, p, k, kVariantTC, tc, split_elems);
-        if (has_tc) cand[k].push_back({kVariantTC, tc});
+        if (has_tc) {
+            cand[k].push_back({kVariantTC, tc});
+            if (tc.tile.split > 1) {  // the same GEMM without its K split (no reduction launch)
+                Node t1 = tc;
+                t1.tile.split = 1;
+                cand[k].push_back({kVariantTC, t1});
+            }
+        }
         // CUDA-core shapes, unless the node is so large that they cannot win
         if (!has_tc || vc < 32)
             for (int v = kTile64x64; v <= kTile256x16; ++v) {

@@ -30,6 +30,13 @@ struct NetDesc {
     std::unordered_map<int64_t, int> id2d;
     std::vector<LeafDesc> leaves;
     std::vector<int> open;  // dense labels, output axis order
+    // host leaves of one call go to the device as one copy: a page-locked
+    // image of all of them, its device twin, and the event of the last copy
+    void* stage_host = nullptr;
+    void* stage_dev = nullptr;
+    int64_t stage_bytes = 0;
+    cudaEvent_t stage_done = nullptr;
+    bool stage_pending = false;
     bool is_complex() const { return dt == TN_C64; }
     size_t elem_bytes() const { return dt == TN_C64 ? 8 : 4; }
 };
