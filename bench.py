@@ -14,6 +14,10 @@ Workloads (``--workload``):
               Hyper-Greedy tree sliced to W_s <= 28; one step = a bounded
               sample of consecutive slices (``--slices``); the time per
               amplitude is extrapolated over all 2^k slices.
+  grad5x4     loss = mean over 64 bitstrings of ln|c_x|^2 of a 5x4-qubit,
+              12-cycle circuit and its gradient with respect to the (theta, phi)
+              of all 93 fSim gates, through the autograd Function (forward tree
+              and reverse sweep on the GPU); one step = loss + gradient.
   batch       a bounded sample of amplitudes of a 6x6-qubit, 12-cycle circuit
               (one shared tree) plus 256 Ising networks with N even in
               [40, --ising-max-n], all in one captured launch sequence (unsliced);
@@ -51,6 +55,7 @@ WORKLOAD_NAMES = {
     "circuit5x5": "circuit_5x5_10cyc_greedy_amplitude",
     "circuit7x7": "circuit_7x7_14cyc_hypergreedy_ws28_slice_sample",
     "batch": "batch_6x6_12cyc_amplitudes_plus_256_ising",
+    "grad5x4": "grad_5x4_12cyc_fsim_params_64_bitstrings",
 }
 MODES = ["fp32", "tf32_split", "bf16_split", "tf32_3m"]
 # accuracy each mode is held to (relative, against the FP64 oracle)
@@ -407,7 +412,10 @@ def run_network(args, torch, dist, rank, world, local):
     # timed region: K steps, each bracketed by events; L2 flushed between
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    dom_ev = [device_events(torch, stream, 2) for _ in range(args.steps)]
+    # every 4th timed step also records events around the dominant launch step
+    # (the roofline's live duration); the hooks cost a little device time
+    hooked = [i for i in range(args.steps) if i % 4 == 3] or [args.steps - 1]
+    dom_ev = {i: device_events(torch, stream, 2) for i in hooked}
     clk = ClockSampler(local)
     if dist:
         dist.barrier()
@@ -417,13 +425,16 @@ def run_network(args, torch, dist, rank, world, local):
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
-        m, e = call(prof_events=dom_ev[i], prof_first=dom)
+        if i in dom_ev:
+            m, e = call(prof_events=dom_ev[i], prof_first=dom)
+        else:
+            m, e = call()
         ends[i].record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clocks = clk.stop()
     call_ms = [s.elapsed_time(t) for s, t in zip(starts, ends)]
-    dom_ms = [a.elapsed_time(b) for a, b in dom_ev]
+    dom_ms = [a.elapsed_time(b) for a, b in dom_ev.values()]
     total_ms = sum(call_ms)
     if dist:
         tt = torch.tensor([total_ms], device="cuda")
@@ -712,6 +723,143 @@ def run_batch(args, torch, dist, rank, world, local):
     return 0
 
 
+def fsim_batch(torch, theta, phi):
+    """fSim(theta, phi) for vectors of angles: [n, 2, 2, 2, 2] complex64 (the
+    circuit model that produces the leaves, not part of the contraction)."""
+    n = theta.shape[0]
+    c, s = torch.cos(theta).to(torch.complex128), torch.sin(theta).to(torch.complex128)
+    g = torch.zeros((n, 4, 4), dtype=torch.complex128, device=theta.device)
+    g[:, 0, 0] = 1
+    g[:, 1, 1] = c
+    g[:, 2, 2] = c
+    g[:, 1, 2] = -1j * s
+    g[:, 2, 1] = -1j * s
+    g[:, 3, 3] = torch.exp(-1j * phi.to(torch.complex128))
+    return g.to(torch.complex64).reshape(n, 2, 2, 2, 2)
+
+
+def run_grad(args, torch, dist, rank, world, local):
+    import numpy as np
+    from paper_2002_01935_gb300 import autograd, binding, inputs, planner
+
+    mode = args.mode
+    R, C, T = 5, 4, 12
+    circ = inputs.random_circuit(R, C, T, seed=0)
+    bits = inputs.random_bitstrings(R * C, 64, seed=1000 + rank)
+    fs = circ.fsim_gates()
+    nets = [inputs.circuit_network(circ, b) for b in bits]
+    net0 = nets[0]
+    pairs = planner.greedy_tree(net0.labels, net0.dims, net0.open)
+    info = planner.tree_info(net0.labels, net0.dims, pairs, net0.open)
+    n = net0.n_tensors
+    first_out = n - R * C  # output states are the last leaves
+    base = [torch.from_numpy(np.array(t, order="C")).to(torch.complex64).cuda() for t in net0.tensors]
+    outs = [[torch.from_numpy(np.array(nt.tensors[v], order="C")).to(torch.complex64).cuda()
+             for v in range(first_out, n)] for nt in nets]
+    leaf_of = [net0.meta["gate_leaf"][g] for g in fs]
+    theta = torch.tensor([circ.gates[g].params[0] for g in fs], dtype=torch.float64, device="cuda",
+                         requires_grad=True)
+    phi = torch.tensor([circ.gates[g].params[1] for g in fs], dtype=torch.float64, device="cuda",
+                       requires_grad=True)
+    tnw = binding.TensorNetwork(net0.labels, net0.dims, net0.open, base, complex_=True)
+    if not args.no_autotune:
+        tnw.autotune(pairs, [], mode, reps=3)
+
+    def step():
+        theta.grad = None
+        phi.grad = None
+        G = fsim_batch(torch, theta, phi)
+        leaves = list(base)
+        for i, v in enumerate(leaf_of):
+            leaves[v] = G[i]
+        loss = 0.0
+        for x in range(len(bits)):
+            lx = leaves[:first_out] + outs[x]
+            cval = autograd.contract(tnw, pairs, [], mode, *lx)
+            loss = loss + torch.log(torch.abs(cval) ** 2) / len(bits)
+        loss.backward()
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    clk.start()
+    times = []
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = step()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    torch.cuda.nvtx.range_pop()
+    clocks = clk.stop()
+    total = sum(times)
+    if dist:
+        tt = torch.tensor([total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = float(tt.item())
+    ms_per_step = total / args.steps * 1e3
+    # algorithmic work: forward 8 C, reverse sweep 2 x 8 C per bitstring
+    flops_step = 24.0 * info.C * len(bits)
+    value = flops_step * world / (ms_per_step / 1e3) / 1e12
+
+    # parity sample: leaf derivatives of bitstring 0 against the oracle's
+    # environments (the exact derivative), and the oracle's time for them
+    cpu, rel = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import gradient, tree
+        G = fsim_batch(torch, theta.detach(), phi.detach())
+        lv = list(base)
+        for i, v in enumerate(leaf_of):
+            lv[v] = G[i]
+        lv = lv[:first_out] + outs[0]
+        tnw.set_tensors(lv)
+        grads = tnw.grad(pairs, [], mode, np.array(1.0 + 0j))
+        host = [t.detach().cpu().numpy().astype(np.complex128) for t in lv]
+        sample = [leaf_of[0], leaf_of[len(leaf_of) // 2], leaf_of[-1]]
+        errs, t_or = [], 0.0
+        tf = lambda l, d, o: planner.greedy_tree(l, d, o)
+        for v in sample:
+            t1 = time.perf_counter()
+            env = gradient.environment(host, net0.labels, net0.dims, v, tf)
+            t_or += time.perf_counter() - t1
+            got = np.conj(grads[v].detach().cpu().numpy().astype(np.complex128))
+            errs.append(float(np.linalg.norm(got - env) / np.linalg.norm(env)))
+        t1 = time.perf_counter()
+        tree.contract(host, net0.labels, net0.dims, net0.open, pairs)
+        t_fwd = time.perf_counter() - t1
+        cpu = {"value": 8.0 * info.C / t_fwd / 1e12, "unit": "TFLOP/s", "cores": tree.max_threads(),
+               "kind": "oracle", "s_per_gradient_step_extrapolated": 64 * (t_fwd + (n - 1) * t_or / len(sample)),
+               "sample": "one forward contraction and the environments of 3 fSim leaves of bitstring 0"}
+        rel = {"leaf_gradient_max": max(errs), "leaves_checked": len(sample)}
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES["grad5x4"], "mode": mode, "qubits": R * C, "cycles": T,
+                   "parameters": 2 * len(fs), "bitstrings": len(bits), "W": info.W, "C": info.C,
+                   "flops_per_step": flops_step, "tree": "greedy (alpha=1, tau=0)",
+                   "flops_convention": "24 C per bitstring: forward 8 C + reverse sweep 16 C"},
+        "loss": float(loss.detach().cpu()),
+        "s_per_gradient_step": ms_per_step / 1e3,
+        "rel_err_vs_oracle": rel,
+        "roofline": None,
+        "cpu_baseline": cpu,
+        "e2e": None,
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tnw.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -748,6 +896,8 @@ def main():
     __graft_entry__.build()
     if args.workload == "batch":
         rc = run_batch(args, torch, dist, rank, world, local)
+    elif args.workload == "grad5x4":
+        rc = run_grad(args, torch, dist, rank, world, local)
     else:
         rc = run_network(args, torch, dist, rank, world, local)
     if dist:
