@@ -899,13 +899,20 @@ static tn_status prepare_leaves(NetDesc& d, Plan& p, bool capturing, std::vector
 // instance layout changed.
 static tn_status ensure_graph(const NetDesc& d, Plan& p, const std::vector<const void*>& lp, int pf,
                               int pc, std::string& err) {
-    if (p.gexec && p.graph_ptrs == lp && p.graph_prof_first == pf && p.graph_prof_count == pc &&
-        p.graph_inst == p.cfg_inst && p.graph_step == p.cfg_step)
+    const bool h = pc > 0;
+    cudaGraph_t& graph = h ? p.graph_h : p.graph;
+    cudaGraphExec_t& gexec = h ? p.gexec_h : p.gexec;
+    std::vector<const void*>& gptrs = h ? p.graph_ptrs_h : p.graph_ptrs;
+    int& gpf = h ? p.graph_prof_first_h : p.graph_prof_first;
+    int& gpc = h ? p.graph_prof_count_h : p.graph_prof_count;
+    int& ginst = h ? p.graph_inst_h : p.graph_inst;
+    int& gstep = h ? p.graph_step_h : p.graph_step;
+    if (gexec && gptrs == lp && gpf == pf && gpc == pc && ginst == p.cfg_inst && gstep == p.cfg_step)
         return TN_OK;
-    if (p.gexec) CK(cudaGraphExecDestroy(p.gexec));
-    if (p.graph) CK(cudaGraphDestroy(p.graph));
-    p.gexec = nullptr;
-    p.graph = nullptr;
+    if (gexec) CK(cudaGraphExecDestroy(gexec));
+    if (graph) CK(cudaGraphDestroy(graph));
+    gexec = nullptr;
+    graph = nullptr;
     while ((int)p.prof_placeholder.size() < pc + 1) {
         cudaEvent_t ev;
         CK(cudaEventCreate(&ev));
@@ -913,21 +920,22 @@ static tn_status ensure_graph(const NetDesc& d, Plan& p, const std::vector<const
     }
     CK(cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_slice(d, p, p.cap_stream, pc ? p.prof_placeholder.data() : nullptr, pf, pc);
-    cudaError_t e2 = cudaStreamEndCapture(p.cap_stream, &p.graph);
+    cudaError_t e2 = cudaStreamEndCapture(p.cap_stream, &graph);
     CK(e);
     CK(e2);
-    CK(cudaGraphInstantiate(&p.gexec, p.graph, 0));
-    p.graph_ptrs = lp;
-    p.graph_prof_first = pf;
-    p.graph_prof_count = pc;
-    p.graph_inst = p.cfg_inst;
-    p.graph_step = p.cfg_step;
+    CK(cudaGraphInstantiate(&gexec, graph, 0));
+    gptrs = lp;
+    gpf = pf;
+    gpc = pc;
+    ginst = p.cfg_inst;
+    gstep = p.cfg_step;
+    if (!h) return TN_OK;
     p.prof_nodes.assign(pc + 1, nullptr);
     if (pc) {
         size_t nn = 0;
-        CK(cudaGraphGetNodes(p.graph, nullptr, &nn));
+        CK(cudaGraphGetNodes(graph, nullptr, &nn));
         std::vector<cudaGraphNode_t> all(nn);
-        CK(cudaGraphGetNodes(p.graph, all.data(), &nn));
+        CK(cudaGraphGetNodes(graph, all.data(), &nn));
         for (auto g : all) {
             cudaGraphNodeType t;
             CK(cudaGraphNodeGetType(g, &t));
@@ -1012,9 +1020,10 @@ tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count
     if (use_graph) {
         st = ensure_graph(d, p, lp, pf, pc, err);
         if (st != TN_OK) return st;
+        cudaGraphExec_t gx = pc ? p.gexec_h : p.gexec;
         for (int i = 0; i < pc + (pc ? 1 : 0); ++i)
-            CK(cudaGraphExecEventRecordNodeSetEvent(p.gexec, p.prof_nodes[i], uev[i]));
-        for (int64_t s = 0; s < groups; ++s) CK(cudaGraphLaunch(p.gexec, stream));
+            CK(cudaGraphExecEventRecordNodeSetEvent(gx, p.prof_nodes[i], uev[i]));
+        for (int64_t s = 0; s < groups; ++s) CK(cudaGraphLaunch(gx, stream));
     } else {
         for (int64_t s = 0; s < groups; ++s) CK(enqueue_slice(d, p, stream, uev, pf, pc));
     }
@@ -1276,6 +1285,7 @@ tn_status autotune_plan(NetDesc& d, Plan& p, int reps, int32_t* choice, cudaStre
     }
     p.cfg_inst = -1;
     p.graph_ptrs.clear();
+    p.graph_ptrs_h.clear();
     p.tuned = true;
     return TN_OK;
 }
@@ -1307,6 +1317,12 @@ void free_device(Plan& p) {
     free_grad(p);
     if (p.gexec) cudaGraphExecDestroy(p.gexec);
     if (p.graph) cudaGraphDestroy(p.graph);
+    if (p.gexec_h) cudaGraphExecDestroy(p.gexec_h);
+    if (p.graph_h) cudaGraphDestroy(p.graph_h);
+    p.gexec_h = nullptr;
+    p.graph_h = nullptr;
+    p.graph_ptrs_h.clear();
+    p.graph_inst_h = p.graph_step_h = -1;
     for (auto ev : p.prof_placeholder) cudaEventDestroy(ev);
     p.prof_placeholder.clear();
     p.prof_nodes.clear();

@@ -116,10 +116,17 @@ struct Plan {
     int64_t split_bytes = 0;
     AccumArgs acc_args{};
     cudaStream_t cap_stream = nullptr;
-    cudaGraph_t graph = nullptr;
+    cudaGraph_t graph = nullptr;         // per-slice sequence without timing hooks
     cudaGraphExec_t gexec = nullptr;
     std::vector<const void*> graph_ptrs;
     int graph_prof_first = 0, graph_prof_count = 0;
+    // the same sequence with timing hooks (kept beside the plain one, so
+    // that calls with and without hooks do not recapture)
+    cudaGraph_t graph_h = nullptr;
+    cudaGraphExec_t gexec_h = nullptr;
+    std::vector<const void*> graph_ptrs_h;
+    int graph_prof_first_h = 0, graph_prof_count_h = 0;
+    int graph_inst_h = -1, graph_step_h = -1;
     std::vector<cudaEvent_t> prof_placeholder;  // events captured into the graph
     std::vector<cudaGraphNode_t> prof_nodes;    // their record nodes, in order
 };
