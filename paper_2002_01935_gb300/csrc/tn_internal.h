@@ -280,9 +280,14 @@ cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s);  // tn_ti
 // GEMM: three launches, plus a fixed-order reduction with a K split.
 cudaError_t launch_tc(const TileArgs& a, int prec, bool is_c, cudaStream_t s);
 inline int tc_launches(const TileArgs& a) { return a.split > 1 ? 4 : 3; }
-// All small nodes of one tree level in one launch (tn_tiled.cu).
+// Small nodes of one or more tree levels in one launch (tn_tiled.cu).  deps
+// (per node: child a, its chunk count, child b, its chunk count; -1 = none)
+// makes it a dataflow over levels with completion counters done[node * G +
+// instance] and the item counter head, all zero at launch.
 cudaError_t launch_wave(const WaveItem* items, int n_items, const TileArgs* descs,
-                        const void* const* leaf_ptrs, bool is_c, cudaStream_t s);
+                        const void* const* leaf_ptrs, bool is_c, cudaStream_t s,
+                        const int4* deps = nullptr, unsigned* done = nullptr, unsigned* head = nullptr,
+                        int G = 1);
 cudaError_t launch_accumulate(const AccumArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_begin_call(Control* ctl, int64_t slice_begin, int64_t slice_end, double* acc,
                               int64_t n_acc_doubles, cudaStream_t s);

@@ -296,9 +296,11 @@ Node build_node(const NetDesc& d, const Plan& p, int id, int a, int b, const std
 tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
     const int n = d.n;
     // diagnostics: TN_FORCE_GENERIC=1 runs every node on the generic kernel,
-    // TN_NO_WAVES=1 launches every node separately
+    // TN_NO_WAVES=1 launches every node separately, TN_NO_FLOW=1 one launch
+    // per wave level
     if (const char* e = getenv("TN_FORCE_GENERIC")) p.force_generic = e[0] == '1';
     if (const char* e = getenv("TN_NO_WAVES")) p.no_waves = e[0] == '1';
+    if (const char* e = getenv("TN_NO_FLOW")) p.no_flow = e[0] == '1';
     if (const char* e = getenv("TN_NO_TENSOR_CORES")) p.no_tensor_cores = e[0] == '1';
     const int L = (int)d.dims.size();
     // ---- tree validation (Sec. 2: leaves first, children before parents)
@@ -502,6 +504,42 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
             p.steps.push_back(s);
         }
     }
+    // ---- consecutive wave levels become one dataflow launch (their items
+    // are contiguous); a node waits for its children in the same launch
+    if (!p.no_flow) {
+        std::vector<Step> merged;
+        for (Step& st : p.steps) {
+            if (st.wave && !merged.empty() && merged.back().wave &&
+                merged.back().item_begin + merged.back().item_count == st.item_begin) {
+                Step& m = merged.back();
+                m.item_count += st.item_count;
+                m.nodes.insert(m.nodes.end(), st.nodes.begin(), st.nodes.end());
+                m.flow = 1;
+            } else {
+                merged.push_back(st);
+            }
+        }
+        p.steps = merged;
+    }
+    p.flow_deps.assign(4 * p.nodes.size(), -1);
+    for (const Step& st : p.steps) {
+        if (!st.flow) continue;
+        std::vector<char> in_step(p.nodes.size(), 0);
+        for (int k : st.nodes) in_step[k] = 1;
+        for (int k : st.nodes) {
+            const Node& nd = p.nodes[k];
+            int slot = 0;
+            for (int c : {nd.ca, nd.cb}) {
+                if (c >= n && in_step[c - n]) {
+                    const Node& ch = p.nodes[c - n];
+                    const int64_t chunk = std::min<int64_t>(ch.size, 1024);
+                    p.flow_deps[4 * k + 2 * slot] = c - n;
+                    p.flow_deps[4 * k + 2 * slot + 1] = (int)((ch.size + chunk - 1) / chunk);
+                }
+                ++slot;
+            }
+        }
+    }
     // ---- workspace liveness in execution order: a step's outputs are all
     // allocated before any of its operands is released (they run at once)
     Arena ar;
@@ -634,6 +672,15 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
             t.ctl = g.ctl;
             t.sc = g.sc;
         }
+    }
+    {
+        // dataflow waves: dependencies, and completion / item counters
+        if (!ck(cudaMalloc(&p.flow_deps_dev, sizeof(int) * 4 * std::max(nn, 1)), "cudaMalloc")) return TN_ENOMEM;
+        if (!ck(cudaMemcpy(p.flow_deps_dev, p.flow_deps.data(), sizeof(int) * p.flow_deps.size(),
+                           cudaMemcpyHostToDevice), "cudaMemcpy"))
+            return TN_ECUDA;
+        const size_t cnt = (size_t)nn * G + p.steps.size() + 1;
+        if (!ck(cudaMalloc(&p.flow_cnt_dev, sizeof(unsigned) * cnt), "cudaMalloc")) return TN_ENOMEM;
     }
     if (!p.items.empty()) {
         std::vector<TileArgs> descs(nn);
@@ -771,8 +818,15 @@ static tn_status configure_instances(const NetDesc& d, Plan& p, int G, int step,
 static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, const cudaEvent_t* ev,
                                  int pf, int pc) {
     const int G = std::max(p.cfg_inst, 1);
-    cudaError_t e = launch_begin_slice(p.maxabs, (int)p.nodes.size() * G, s);
+    const int nn = (int)p.nodes.size();
+    cudaError_t e = launch_begin_slice(p.maxabs, nn * G, s);
     if (e != cudaSuccess) return e;
+    bool any_flow = false;
+    for (const Step& st : p.steps) any_flow |= st.flow != 0;
+    if (any_flow &&
+        (e = cudaMemsetAsync(p.flow_cnt_dev, 0, sizeof(unsigned) * ((size_t)nn * G + p.steps.size()), s)) !=
+            cudaSuccess)
+        return e;
     const bool c = d.is_complex();
     for (int k = 0; k < (int)p.steps.size(); ++k) {
         // External records become event-record nodes under stream capture.
@@ -781,8 +835,14 @@ static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, cons
             return e;
         const Step& st = p.steps[k];
         if (st.wave) {
-            e = launch_wave(p.items_dev + p.inst_items_begin[k], st.item_count * G, p.descs_dev,
-                            reinterpret_cast<const void* const*>(p.leaf_ptr_dev), c, s);
+            if (st.flow)
+                e = launch_wave(p.items_dev + p.inst_items_begin[k], st.item_count * G, p.descs_dev,
+                                reinterpret_cast<const void* const*>(p.leaf_ptr_dev), c, s,
+                                reinterpret_cast<const int4*>(p.flow_deps_dev), p.flow_cnt_dev,
+                                p.flow_cnt_dev + (size_t)nn * G + k, G);
+            else
+                e = launch_wave(p.items_dev + p.inst_items_begin[k], st.item_count * G, p.descs_dev,
+                                reinterpret_cast<const void* const*>(p.leaf_ptr_dev), c, s);
         } else {
             const Node& nd = p.nodes[st.node];
             if (nd.kind == kTensorCore)
@@ -1338,6 +1398,10 @@ void free_device(Plan& p) {
     p.split_buf = nullptr;
     if (p.descs_dev) cudaFree(p.descs_dev);
     if (p.items_dev) cudaFree(p.items_dev);
+    if (p.flow_deps_dev) cudaFree(p.flow_deps_dev);
+    if (p.flow_cnt_dev) cudaFree(p.flow_cnt_dev);
+    p.flow_deps_dev = nullptr;
+    p.flow_cnt_dev = nullptr;
     if (p.inst_roots_dev) cudaFree(p.inst_roots_dev);
     if (p.inst_out_dev) cudaFree(p.inst_out_dev);
     if (p.inst_exp_dev) cudaFree(p.inst_exp_dev);

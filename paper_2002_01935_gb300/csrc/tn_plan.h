@@ -60,6 +60,7 @@ struct Node {
 // level, k_wave) or a single node (tiled or generic kernel).
 struct Step {
     int wave = 0;
+    int flow = 0;                  // wave over several levels run as one dataflow
     int node = -1;                 // single-node step
     int item_begin = 0, item_count = 0;
     std::vector<int> nodes;        // nodes run by this step
@@ -70,6 +71,10 @@ struct GradState;  // reverse-sweep plan and device state (tn_grad.cpp)
 struct Plan {
     tn_mode mode = TN_MODE_FP32;
     bool tuned = false;             // kernels chosen by autotune_plan
+    bool no_flow = false;           // one launch per wave level (env TN_NO_FLOW)
+    std::vector<int> flow_deps;     // per node: child a, its chunks, child b, its chunks
+    int* flow_deps_dev = nullptr;
+    unsigned* flow_cnt_dev = nullptr;  // done[node * G + inst], then one head per step
     bool force_generic = false;  // every node on the generic kernel
     bool no_waves = false;       // one launch per node
     bool no_tensor_cores = false;  // reduced-precision modes on CUDA cores only

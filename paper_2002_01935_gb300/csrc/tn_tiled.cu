@@ -17,9 +17,11 @@
 // e = frexp exponent of their max |component|, which is exact; the output
 // max goes to the node's slot for its consumer.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstring>
 #include <stdint.h>
 
+#include "../../include/tn.h"
 #include "tn_internal.h"
 
 namespace tn {
@@ -470,89 +472,150 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a,
     }
 }
 
-// One launch for all small nodes of a tree level.  Each CTA computes a
-// chunk of one node's outputs; descriptors live in device memory.  With
-// fewer than 256 outputs in the chunk, g = 256/outputs threads share each
-// output's K range and reduce it in a fixed order.
+// One launch for the small nodes of one or more consecutive tree levels.
+// Each work item is a chunk of one node's outputs; descriptors live in
+// device memory.  With fewer than 256 outputs in the chunk, g = 256/outputs
+// threads share each output's K range and reduce it in a fixed order.
+//
+// Without dependencies (deps == nullptr) item i is CTA i.  With them, the
+// launch covers several levels as one dataflow: persistent CTAs take items
+// in order from a counter; before an item runs, the chunks of its children
+// that belong to the same launch must have finished (per node and instance
+// completion counters; a bounded wait that records TN_ETIMEOUT); after it,
+// its own counter is raised.  Items only depend on earlier items, and every
+// taken item belongs to a running CTA, so the waits always end.  Inputs that
+// other CTAs of the launch produced are read through L2 (ld.global.cg).
+constexpr long long kFlowWaitCycles = 4000000000ll;  // ~2 s
+
+template <bool CPLX>
+__device__ __forceinline__ typename VT<CPLX>::T ld_cg(const typename VT<CPLX>::T* p) {
+    if constexpr (CPLX) return __ldcg(reinterpret_cast<const float2*>(p));
+    else return __ldcg(reinterpret_cast<const float*>(p));
+}
+
 template <bool CPLX>
 __global__ void __launch_bounds__(256)
-    k_wave(const WaveItem* items, const TileArgs* descs, const void* const* leaf_ptrs) {
+    k_wave(const WaveItem* items, int n_items, const TileArgs* descs, const void* const* leaf_ptrs,
+           const int4* deps, unsigned* done, unsigned* head, int G) {
     using T = typename VT<CPLX>::T;
     __shared__ TileArgs d;
     __shared__ int64_t kA[256], kB[256];
     __shared__ T red[256];
-    const WaveItem it = items[blockIdx.x];
-    {
-        const int4* src = reinterpret_cast<const int4*>(descs + it.node);
-        int4* dst = reinterpret_cast<int4*>(&d);
-        for (int i = threadIdx.x; i < (int)(sizeof(TileArgs) / 16); i += blockDim.x) dst[i] = src[i];
-    }
-    __syncthreads();
+    __shared__ int cur;
     const int tid = threadIdx.x;
-    const View vw = inst_view(d, it.pad, (int)sizeof(T));
-    if (!vw.live) return;
-    const int64_t isz = (int64_t)sizeof(T);
-    const T* A = reinterpret_cast<const T*>(
-        d.a_leaf >= 0 ? (const char*)leaf_ptrs[d.a_leaf] + (int64_t)it.pad * d.in.a_is * isz : vw.A);
-    const T* B = reinterpret_cast<const T*>(
-        d.b_leaf >= 0 ? (const char*)leaf_ptrs[d.b_leaf] + (int64_t)it.pad * d.in.b_is * isz : vw.B);
-    const Scales sc = node_scales(vw.sc, it.o_begin == 0 && tid == 0);
-    const int64_t slice = vw.slice;
-    const int64_t sA = slice_off(d.sla, slice), sB = slice_off(d.slb, slice);
-    const int64_t K = 1ll << d.nk;
-    const int kt = d.nk < 8 ? (int)K : 256;  // table covers k & 255
-    for (int t = tid; t < kt; t += 256) {
-        kA[t] = scatter_bits(t, d.a_k, d.nk);
-        kB[t] = scatter_bits(t, d.b_k, d.nk);
+    for (int pass = 0;; ++pass) {
+        // ---- take an item
+        if (deps == nullptr) {
+            if (pass > 0) break;
+            if (tid == 0) cur = blockIdx.x;
+        } else if (tid == 0) {
+            cur = (int)atomicAdd(head, 1u);
+        }
+        __syncthreads();
+        const int idx = cur;
+        if (idx >= n_items) break;
+        const WaveItem it = items[idx];
+        // ---- everything that does not depend on the children first: the
+        // descriptor, the instance view and the K offset tables
+        {
+            const int4* src = reinterpret_cast<const int4*>(descs + it.node);
+            int4* dst = reinterpret_cast<int4*>(&d);
+            for (int i = tid; i < (int)(sizeof(TileArgs) / 16); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        const View vw = inst_view(d, it.pad, (int)sizeof(T));
+        const int kt = d.nk < 8 ? (int)(1ll << d.nk) : 256;  // table covers k & 255
+        if (vw.live)
+            for (int t = tid; t < kt; t += 256) {
+                kA[t] = scatter_bits(t, d.a_k, d.nk);
+                kB[t] = scatter_bits(t, d.b_k, d.nk);
+            }
+        // ---- then wait for children computed in this launch
+        if (deps != nullptr && tid == 0) {
+            const int4 dp = deps[it.node];
+            const long long t0 = clock64();
+            for (int side = 0; side < 2; ++side) {
+                const int child = side ? dp.z : dp.x;
+                const unsigned need = (unsigned)(side ? dp.w : dp.y);
+                if (child < 0) continue;
+                const volatile unsigned* cnt = done + (int64_t)child * G + it.pad;
+                while (*cnt < need) {
+                    if (clock64() - t0 > kFlowWaitCycles) {
+                        atomicExch(const_cast<int32_t*>(&d.ctl->status), (int32_t)TN_ETIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (vw.live) {
+            const int64_t isz = (int64_t)sizeof(T);
+            const T* A = reinterpret_cast<const T*>(
+                d.a_leaf >= 0 ? (const char*)leaf_ptrs[d.a_leaf] + (int64_t)it.pad * d.in.a_is * isz : vw.A);
+            const T* B = reinterpret_cast<const T*>(
+                d.b_leaf >= 0 ? (const char*)leaf_ptrs[d.b_leaf] + (int64_t)it.pad * d.in.b_is * isz : vw.B);
+            const Scales sc = node_scales(vw.sc, it.o_begin == 0 && tid == 0);
+            const int64_t slice = vw.slice;
+            const int64_t sA = slice_off(d.sla, slice), sB = slice_off(d.slb, slice);
+            const int64_t K = 1ll << d.nk;
+            const int64_t nmask = (1ll << d.nn) - 1, mmask = (1ll << d.nm) - 1;
+            const int O = (int)it.o_count;
+            const int g = O >= 256 ? 1 : 256 / O;
+            float lmax = 0.f;
+            T* C = reinterpret_cast<T*>(vw.C);
+            for (int ol = tid / g; ol < O; ol += 256 / g) {
+                const int64_t o = it.o_begin + ol;
+                const int64_t n = o & nmask, m = (o >> d.nn) & mmask, b = o >> (d.nn + d.nm);
+                const int64_t offA = sA + scatter_bits(b, d.a_b, d.nb) + scatter_bits(m, d.a_m, d.nm);
+                const int64_t offB = sB + scatter_bits(b, d.b_b, d.nb) + scatter_bits(n, d.b_n, d.nn);
+                T acc = zero<T>();
+                for (int64_t t = tid % g; t < K; t += g) {
+                    int64_t ka, kb2;
+                    if (d.nk < 8) {
+                        ka = kA[t];
+                        kb2 = kB[t];
+                    } else {
+                        const int64_t hi = t & ~255ll;
+                        ka = kA[t & 255] + (hi ? scatter_bits(hi, d.a_k, d.nk) : 0);
+                        kb2 = kB[t & 255] + (hi ? scatter_bits(hi, d.b_k, d.nk) : 0);
+                    }
+                    fma_acc(acc, cmul(ld_cg<CPLX>(A + offA + ka), sc.fa, d.conj_a),
+                            cmul(ld_cg<CPLX>(B + offB + kb2), sc.fb, d.conj_b));
+                }
+                if (g > 1) {
+                    red[tid] = acc;
+                    __syncthreads();
+                    const int j = tid % g;
+                    for (int s2 = g / 2; s2 > 0; s2 >>= 1) {
+                        if (j < s2) red[tid] = add(red[tid], red[tid + s2]);
+                        __syncthreads();
+                    }
+                    if (j != 0) continue;
+                    acc = red[tid];
+                }
+                if (sc.resid) {
+                    if constexpr (CPLX) {
+                        acc.x = ldexpf(acc.x, -sc.resid);
+                        acc.y = ldexpf(acc.y, -sc.resid);
+                    } else {
+                        acc = ldexpf(acc, -sc.resid);
+                    }
+                }
+                lmax = fmaxf(lmax, absmax(acc));
+                C[o] = acc;
+            }
+            block_max(lmax, vw.sc.max_c);
+            if (d.t_done && tid == 0) atomicMax(d.t_done, global_ns());
+        }
+        // ---- publish: outputs, maximum and exponent before the counter
+        __syncthreads();
+        if (deps != nullptr && tid == 0) {
+            __threadfence();
+            atomicAdd(done + (int64_t)it.node * G + it.pad, 1u);
+        }
     }
-    __syncthreads();
-    const int64_t nmask = (1ll << d.nn) - 1, mmask = (1ll << d.nm) - 1;
-    const int O = (int)it.o_count;
-    const int g = O >= 256 ? 1 : 256 / O;
-    float lmax = 0.f;
-    T* C = reinterpret_cast<T*>(vw.C);
-    for (int ol = tid / g; ol < O; ol += 256 / g) {
-        const int64_t o = it.o_begin + ol;
-        const int64_t n = o & nmask, m = (o >> d.nn) & mmask, b = o >> (d.nn + d.nm);
-        const int64_t offA = sA + scatter_bits(b, d.a_b, d.nb) + scatter_bits(m, d.a_m, d.nm);
-        const int64_t offB = sB + scatter_bits(b, d.b_b, d.nb) + scatter_bits(n, d.b_n, d.nn);
-        T acc = zero<T>();
-        for (int64_t t = tid % g; t < K; t += g) {
-            int64_t ka, kb2;
-            if (d.nk < 8) {
-                ka = kA[t];
-                kb2 = kB[t];
-            } else {
-                const int64_t hi = t & ~255ll;
-                ka = kA[t & 255] + (hi ? scatter_bits(hi, d.a_k, d.nk) : 0);
-                kb2 = kB[t & 255] + (hi ? scatter_bits(hi, d.b_k, d.nk) : 0);
-            }
-            fma_acc(acc, cmul(A[offA + ka], sc.fa, d.conj_a), cmul(B[offB + kb2], sc.fb, d.conj_b));
-        }
-        if (g > 1) {
-            red[tid] = acc;
-            __syncthreads();
-            const int j = tid % g;
-            for (int s2 = g / 2; s2 > 0; s2 >>= 1) {
-                if (j < s2) red[tid] = add(red[tid], red[tid + s2]);
-                __syncthreads();
-            }
-            if (j != 0) continue;
-            acc = red[tid];
-        }
-        if (sc.resid) {
-            if constexpr (CPLX) {
-                acc.x = ldexpf(acc.x, -sc.resid);
-                acc.y = ldexpf(acc.y, -sc.resid);
-            } else {
-                acc = ldexpf(acc, -sc.resid);
-            }
-        }
-        lmax = fmaxf(lmax, absmax(acc));
-        C[o] = acc;
-    }
-    block_max(lmax, vw.sc.max_c);
-    if (d.t_done && tid == 0) atomicMax(d.t_done, global_ns());
 }
 
 // --------------------------------------------------------------------------
@@ -660,12 +723,15 @@ cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s) {
 }
 
 cudaError_t launch_wave(const WaveItem* items, int n_items, const TileArgs* descs,
-                        const void* const* leaf_ptrs, bool is_c, cudaStream_t s) {
+                        const void* const* leaf_ptrs, bool is_c, cudaStream_t s, const int4* deps,
+                        unsigned* done, unsigned* head, int G) {
     if (n_items <= 0) return cudaSuccess;
+    // dataflow: persistent CTAs (all resident: 8 per SM fit), else one per item
+    const int grid = deps ? std::min(n_items, 152 * 8) : n_items;
     if (is_c)
-        k_wave<true><<<n_items, 256, 0, s>>>(items, descs, leaf_ptrs);
+        k_wave<true><<<grid, 256, 0, s>>>(items, n_items, descs, leaf_ptrs, deps, done, head, G);
     else
-        k_wave<false><<<n_items, 256, 0, s>>>(items, descs, leaf_ptrs);
+        k_wave<false><<<grid, 256, 0, s>>>(items, n_items, descs, leaf_ptrs, deps, done, head, G);
     return cudaGetLastError();
 }
 
