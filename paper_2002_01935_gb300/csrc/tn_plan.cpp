@@ -1212,13 +1212,25 @@ static cudaError_t launch_node(const NetDesc& d, const Plan& p, const Node& nd, 
 
 // Node k rebuilt as variant v (1..4: tile shape, kVariantTC: tensor core),
 // keeping its device bindings; false if the variant does not apply.
-static bool make_variant(const NetDesc& d, const Plan& p, int k, int v, Node& out, int64_t& split_elems) {
+static bool make_variant(const NetDesc& d, const Plan& p, int k, int v, Node& out, int64_t& split_elems,
+                         int split_mult = 1) {
     const Node& nd = p.nodes[k];
     Node t = nd;
     if (!plan_tile(d, p, t, split_elems, v == kVariantTC ? 0 : v)) return false;
     if (t.tile.cfg == kTileDot) return false;
     t.kind = kTiled;
     if (v == kVariantTC && !make_tensor_core(d, p.mode, t, split_elems)) return false;
+    if (v != kVariantTC && split_mult > 1) {
+        // finer K split: more blocks for short grids over long K (>= 2 K tiles each)
+        TileArgs& a = t.tile;
+        const int TK = a.cfg == kTile4x1024 ? 4 : 16;
+        const int64_t K = int64_t(1) << a.nk, ktiles = (K + TK - 1) / TK;
+        const int split = a.split * split_mult;
+        if (split > 256 || ktiles / split < 2 || a.nbatch * (int64_t)split > 65535) return false;
+        a.split = split;
+        a.kchunk = ((ktiles + split - 1) / split) * TK;
+        split_elems = std::max(split_elems, (int64_t)split * a.nbatch * (int64_t(1) << (a.nm + a.nn)));
+    }
     TileArgs& a = t.tile;
     const TileArgs& o = nd.tile;
     a.A = o.A;
@@ -1277,10 +1289,11 @@ tn_status autotune_plan(NetDesc& d, Plan& p, int reps, int32_t* choice, cudaStre
         }
         // CUDA-core shapes, unless the node is so large that they cannot win
         if (!has_tc || vc < 32)
-            for (int v = kTile64x64; v <= kTile256x16; ++v) {
-                Node t;
-                if (make_variant(d, p, k, v, t, split_elems)) cand[k].push_back({v, t});
-            }
+            for (int v = kTile64x64; v <= kTile256x16; ++v)
+                for (int mult : {1, 4}) {
+                    Node t;
+                    if (make_variant(d, p, k, v, t, split_elems, mult)) cand[k].push_back({v, t});
+                }
     }
     const int64_t need = (split_elems * (int64_t)d.elem_bytes() + 1023) / 1024 * 1024;
     const int G = std::max(p.alloc_inst, 1);
