@@ -363,31 +363,52 @@ __global__ void __launch_bounds__(kPackThreads)
     __syncthreads();
     const int64_t n_tiles = int64_t(1) << u;
     const int64_t K = int64_t(1) << nk;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        int64_t sb = 0, gb = 0;
+    // tile bases by their bits; the loads of the next tile are issued before
+    // the current one is written out (two tiles of reads in flight)
+    auto bases = [&](int64_t tile, int64_t& sb, int64_t& gb) {
+        sb = 0;
+        gb = 0;
         for (int j = 0; j < u; ++j)
             if ((tile >> j) & 1) {
                 sb += pp.rest_src[j];
                 gb += pp.rest_dst[j];
             }
-        T ld[kPackMaxTile / kPackThreads];
+    };
+    constexpr int R = kPackMaxTile / kPackThreads;
+    T ld[R];
+    int64_t sb, gb;
+    if ((int64_t)blockIdx.x < n_tiles) {
+        bases(blockIdx.x, sb, gb);
 #pragma unroll
-        for (int r = 0; r < kPackMaxTile / kPackThreads; ++r) {
+        for (int r = 0; r < R; ++r) {
             const int i = threadIdx.x + r * kPackThreads;
             if (i < tsz) ld[r] = src[sb + tsrc[i]];
         }
+    }
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t gb_cur = gb;
 #pragma unroll
-        for (int r = 0; r < kPackMaxTile / kPackThreads; ++r) {
+        for (int r = 0; r < R; ++r) {
             const int i = threadIdx.x + r * kPackThreads;
             if (i < tsz) stage[i + (i >> 5)] = ld[r];
         }
         __syncthreads();
+        const int64_t next = tile + gridDim.x;
+        if (next < n_tiles) {
+            bases(next, sb, gb);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = threadIdx.x + r * kPackThreads;
+                if (i < tsz) ld[r] = src[sb + tsrc[i]];
+            }
+        }
+        const int64_t gbase = gb_cur;
 #pragma unroll
         for (int r = 0; r < kPackMaxTile / kPackThreads; ++r) {
             const int i = threadIdx.x + r * kPackThreads;
             if (i >= tsz) break;
             const T v = stage[tidx[i]];
-            const int64_t g = gb + tdst[i];
+            const int64_t g = gbase + tdst[i];
             const int64_t row = g >> nk, k = g & (K - 1);
             if constexpr (CPLX && PREC == 3) {
                 // 3M: planes Re, Im, Re + Im of either operand, K not doubled
@@ -1017,7 +1038,7 @@ cudaError_t launch_tc_3m(const TileArgs& a, cudaStream_t s) {
     const int split = a.split > 1 ? a.split : 1;
     if (g.nkb % split) return cudaErrorInvalidValue;
     // every pack CTA stages several 1024-entry tiles (its setup is amortised)
-    auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), 152 * 4); };
+    auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), 152 * 8); };
     const int64_t elems_a = int64_t(1) << (a.nk + a.nm + a.nb);
     const int64_t elems_b = int64_t(1) << (a.nk + a.nn + a.nb);
     k_pack<true, 3><<<dim3(blocks(a.tc_swap ? elems_b : elems_a), ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 0), 0);
@@ -1062,7 +1083,7 @@ cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     const int64_t elems_a = int64_t(1) << (a.nk + a.nm + a.nb);
     const int64_t elems_b = int64_t(1) << (a.nk + a.nn + a.nb);
     // every pack CTA stages several 1024-entry tiles (its setup is amortised)
-    auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), 152 * 4); };
+    auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), 152 * 8); };
     const int64_t n_r = a.tc_swap ? elems_b : elems_a, n_q = a.tc_swap ? elems_a : elems_b;
     k_pack<CPLX, PREC><<<dim3(blocks(n_r), ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 0), 0);
     k_pack<CPLX, PREC><<<dim3(blocks(n_q), ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 1), 1);
