@@ -219,12 +219,29 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
 #pragma unroll
         for (int c = 0; c < RN; ++c) acc[r][c] = zero<T>();
 
-    // global -> registers for one K step (all loads issued back to back)
+    // global -> registers for one K step (all loads issued back to back).
+    // The operand offsets of the K step's base k0 are kept incrementally:
+    // k0 advances by TK, so only the bits of its carry chain change.
     constexpr int LA = (TM * TK + NT - 1) / NT, LB = (TN * TK + NT - 1) / NT;
+    constexpr int LG_TK = TK == 16 ? 4 : (TK == 8 ? 3 : (TK == 4 ? 2 : 0));
+    static_assert((1 << LG_TK) == TK, "TK must be a power of two");
     T ra[LA], rb[LB];
+    int64_t cur_k = kbeg;
+    int64_t kaA = scatter_bits(kbeg, a.a_k, a.nk), kaB = scatter_bits(kbeg, a.b_k, a.nk);
+    auto step_k = [&]() {  // cur_k += TK, offsets follow
+        int i = LG_TK;
+        while (i < a.nk && ((cur_k >> i) & 1)) {
+            if (a.a_k[i] != kNoBit) kaA -= int64_t(1) << a.a_k[i];
+            if (a.b_k[i] != kNoBit) kaB -= int64_t(1) << a.b_k[i];
+            ++i;
+        }
+        if (i < a.nk) {
+            if (a.a_k[i] != kNoBit) kaA += int64_t(1) << a.a_k[i];
+            if (a.b_k[i] != kNoBit) kaB += int64_t(1) << a.b_k[i];
+        }
+        cur_k += TK;
+    };
     auto gload = [&](int64_t k0) {
-        const int64_t kaA = scatter_bits(k0, a.a_k, a.nk);
-        const int64_t kaB = scatter_bits(k0, a.b_k, a.nk);
         const int klim = (int)min64(kend - k0, TK);
 #pragma unroll
         for (int q = 0; q < LA; ++q) {
@@ -245,6 +262,7 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
     };
     if (kbeg < kend) gload(kbeg);
     for (int64_t k0 = kbeg; k0 < kend; k0 += TK) {
+        // kaA/kaB describe k0 here; gload of k0 + TK needs them advanced
 #pragma unroll
         for (int q = 0; q < LA; ++q) {
             const int e = tid + q * NT;
@@ -264,14 +282,17 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
             }
         }
         __syncthreads();
-        if (k0 + TK < kend) gload(k0 + TK);  // next step's loads overlap this step's FMAs
+        if (k0 + TK < kend) {
+            step_k();
+            gload(k0 + TK);  // next step's loads overlap this step's FMAs
+        }
 #pragma unroll 4
         for (int t = 0; t < TK; ++t) {
             T af[RM], bf[RN];
 #pragma unroll
             for (int r = 0; r < RM; ++r) af[r] = sA[t][ty * RM + r];
 #pragma unroll
-            for (int c = 0; c < RN; ++c) bf[c] = sB[t][tx * RN + c];
+            for (int c = 0; c < RN; ++c) bf[c] = sB[t][tx + c * TX];  // conflict-free
 #pragma unroll
             for (int r = 0; r < RM; ++r)
 #pragma unroll
@@ -291,7 +312,7 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
         const int64_t rowoff = (plane * M + m0 + i) * N + n0;
 #pragma unroll
         for (int c = 0; c < RN; ++c) {
-            const int j = tx * RN + c;
+            const int j = tx + c * TX;
             if (j >= nlim) continue;
             T v = acc[r][c];
             if (a.split == 1) {
