@@ -159,8 +159,8 @@ struct PackPlan {
     int64_t src_add[10];
     int64_t dst_add[10];
     int32_t idx_add[10];
-    int64_t rest_src[3 * kMaxBits];
-    int64_t rest_dst[3 * kMaxBits];
+    int64_t rest_src[kMaxBits];  // an operand has at most 2^40 entries
+    int64_t rest_dst[kMaxBits];
 };
 
 // Tile plan of an inner-product node (k_dot), computed on the host: a tile
@@ -276,10 +276,10 @@ cudaError_t launch_leaf_grad(const LeafGradArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s);  // tn_tiled.cu
 // Tensor-core node (tn_tc.cu): prec as tc_prec_of_mode.
-// Packs both operands into a.P (TcGeom) and runs the bulk-copy-fed tcgen05
-// GEMM: three launches, plus a fixed-order reduction with a K split.
+// Packs both operands into a.P (TcGeom, one launch) and runs the bulk-copy-
+// fed tcgen05 GEMM: two launches, plus a fixed-order reduction with a K split.
 cudaError_t launch_tc(const TileArgs& a, int prec, bool is_c, cudaStream_t s);
-inline int tc_launches(const TileArgs& a) { return a.split > 1 ? 4 : 3; }
+inline int tc_launches(const TileArgs& a) { return a.split > 1 ? 3 : 2; }
 // Small nodes of one or more tree levels in one launch (tn_tiled.cu).  deps
 // (per node: child a, its chunk count, child b, its chunk count; -1 = none)
 // makes it a dataflow over levels with completion counters done[node * G +

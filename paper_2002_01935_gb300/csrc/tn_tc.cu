@@ -315,7 +315,13 @@ __device__ __forceinline__ void put1(char* hi, int64_t lo_off, int64_t pos, floa
 // ---------------------------------------------------------------------------
 template <bool CPLX, int PREC>
 __global__ void __launch_bounds__(kPackThreads)
-    k_pack(const __grid_constant__ TileArgs a, const __grid_constant__ PackPlan pp, int role) {
+    k_pack(const __grid_constant__ TileArgs a, const __grid_constant__ PackPlan pr,
+           const __grid_constant__ PackPlan pq, int blocks_r) {
+    // blocks [0, blocks_r) pack R, the others Q (one launch for both operands)
+    const int role = (int)blockIdx.x < blocks_r ? 0 : 1;
+    const PackPlan& pp = role == 0 ? pr : pq;
+    const int bx = role == 0 ? (int)blockIdx.x : (int)blockIdx.x - blocks_r;
+    const int nbx = role == 0 ? blocks_r : (int)gridDim.x - blocks_r;
     using T = typename std::conditional<CPLX, float2, float>::type;
     __shared__ T stage[kPackMaxTile + kPackMaxTile / 32];  // +1 per 32: no bank conflicts
     __shared__ int64_t tsrc[kPackMaxTile];
@@ -377,15 +383,15 @@ __global__ void __launch_bounds__(kPackThreads)
     constexpr int R = kPackMaxTile / kPackThreads;
     T ld[R];
     int64_t sb, gb;
-    if ((int64_t)blockIdx.x < n_tiles) {
-        bases(blockIdx.x, sb, gb);
+    if ((int64_t)bx < n_tiles) {
+        bases(bx, sb, gb);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int i = threadIdx.x + r * kPackThreads;
             if (i < tsz) ld[r] = src[sb + tsrc[i]];
         }
     }
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    for (int64_t tile = bx; tile < n_tiles; tile += nbx) {
         const int64_t gb_cur = gb;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -393,7 +399,7 @@ __global__ void __launch_bounds__(kPackThreads)
             if (i < tsz) stage[i + (i >> 5)] = ld[r];
         }
         __syncthreads();
-        const int64_t next = tile + gridDim.x;
+        const int64_t next = tile + nbx;
         if (next < n_tiles) {
             bases(next, sb, gb);
 #pragma unroll
@@ -1041,8 +1047,11 @@ cudaError_t launch_tc_3m(const TileArgs& a, cudaStream_t s) {
     auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), 152 * 8); };
     const int64_t elems_a = int64_t(1) << (a.nk + a.nm + a.nb);
     const int64_t elems_b = int64_t(1) << (a.nk + a.nn + a.nb);
-    k_pack<true, 3><<<dim3(blocks(a.tc_swap ? elems_b : elems_a), ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 0), 0);
-    k_pack<true, 3><<<dim3(blocks(a.tc_swap ? elems_a : elems_b), ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 1), 1);
+    {
+        const unsigned br = blocks(a.tc_swap ? elems_b : elems_a), bq = blocks(a.tc_swap ? elems_a : elems_b);
+        k_pack<true, 3><<<dim3(br + bq, ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 0), make_pack_plan(a, 1),
+                                                                 (int)br);
+    }
     const int64_t tiles = (g.rows_r / kBM) * (g.cols_q / kBN);
     k_umma3m<STAGES><<<dim3((unsigned)tiles, (unsigned)split, (unsigned)(a.nbatch * ni)), kGemmThreads, SMEM, s>>>(a);
     if (split > 1) {
@@ -1085,8 +1094,8 @@ cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     // every pack CTA stages several 1024-entry tiles (its setup is amortised)
     auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), 152 * 8); };
     const int64_t n_r = a.tc_swap ? elems_b : elems_a, n_q = a.tc_swap ? elems_a : elems_b;
-    k_pack<CPLX, PREC><<<dim3(blocks(n_r), ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 0), 0);
-    k_pack<CPLX, PREC><<<dim3(blocks(n_q), ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 1), 1);
+    k_pack<CPLX, PREC><<<dim3(blocks(n_r) + blocks(n_q), ni), kPackThreads, 0, s>>>(
+        a, make_pack_plan(a, 0), make_pack_plan(a, 1), (int)blocks(n_r));
     const int nkl = (int)(g.nkb / split);
     const int chains = PREC == 0 ? (nkl + 3) / 4 : nkl;
     const int max_acc = 512 / g.bn;

@@ -114,3 +114,38 @@ def test_plan_costs_match_planner(lib, which):
         assert info["d_sliced"] == ref.d_sliced
         assert info["flops"] == pytest.approx(ref.flops(net.is_complex), rel=1e-12)
         assert info["ws_bytes"] > 0
+
+
+def _steps(lib, net, pairs, sliced=(), mode="fp32"):
+    h = lib.TensorNetwork(net.labels, net.dims, net.open, None, complex_=net.is_complex)
+    try:
+        return h.plan_steps(pairs, sliced, mode), h.plan_info(pairs, sliced, mode)
+    finally:
+        h.close()
+
+
+def test_launch_schedule_covers_every_node_once_in_dependency_order(lib):
+    """Host plan only: every tree node is in exactly one launch step, and a
+    node's children run in an earlier step or earlier in the same (dataflow)
+    step; consecutive wave levels are merged into one dataflow step."""
+    from paper_2002_01935_gb300 import inputs, planner
+    for net in (inputs.random_ising(60, seed=2),
+                inputs.circuit_network(inputs.random_circuit(4, 4, 8, seed=0),
+                                       inputs.random_bitstrings(16, 1, seed=1000)[0])):
+        pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+        steps, info = _steps(lib, net, pairs)
+        n = net.n_tensors
+        seen = {}
+        for s, st in enumerate(steps):
+            for pos, k in enumerate(st["nodes"]):
+                assert k not in seen
+                seen[k] = (s, pos)
+        assert sorted(seen) == list(range(len(pairs)))
+        for k, (a, b) in enumerate(pairs):
+            for c in (a, b):
+                if c >= n:
+                    assert seen[c - n] < seen[k], (k, c - n)
+        # no two wave steps in a row: they would have been merged
+        for s0, s1 in zip(steps, steps[1:]):
+            assert not (s0["wave"] and s1["wave"])
+        assert sum(s["launches"] for s in steps) >= len(steps)

@@ -255,3 +255,29 @@ def test_cfg2_variant_5x5_10_cycles(torch):
     sl = planner.slice_greedy(net.labels, net.dims, pairs, net.open, 20)
     m, e = gpu_contract(torch, net, pairs, sl)
     assert abs(complex(m) * 2.0 ** e - ref) <= TOL * abs(ref)
+
+
+def test_dataflow_waves_match_level_launches(torch, monkeypatch):
+    """The same contraction with the small nodes of consecutive tree levels
+    in one dataflow launch and with one launch per level: identical bits."""
+    from paper_2002_01935_gb300 import binding
+    res = []
+    for flow in ("0", "1"):
+        monkeypatch.setenv("TN_NO_FLOW", flow)
+        for net in (inputs.random_ising(100, seed=0),
+                    inputs.circuit_network(inputs.random_circuit(4, 4, 8, seed=0),
+                                           inputs.random_bitstrings(16, 1, seed=1000)[0])):
+            pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+            dt = torch.complex64 if net.is_complex else torch.float32
+            ts = [torch.from_numpy(np.array(t, order="C")).to(dt).cuda() for t in net.tensors]
+            h = binding.TensorNetwork(net.labels, net.dims, net.open, ts, complex_=net.is_complex)
+            try:
+                steps = h.plan_steps(pairs, [], "fp32")
+                m, e = h.contract(pairs, [], "fp32")
+                torch.cuda.synchronize()
+                res.append((len(steps), m.cpu().numpy().tobytes(), int(e.cpu())))
+            finally:
+                h.close()
+    (s0a, m0a, e0a), (s0b, m0b, e0b), (s1a, m1a, e1a), (s1b, m1b, e1b) = res
+    assert s0a < s1a and s0b < s1b  # fewer launch steps with the dataflow
+    assert (m0a, e0a) == (m1a, e1a) and (m0b, e0b) == (m1b, e1b)
