@@ -335,7 +335,7 @@ def roofline(steps, dom, dom_ms, nodes, mode, ms_per_step, peaks):
             roof["executed_frac"] = pipe["executed_flops"] / dmean / 1e12 / pipe["peak"]
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    cfg_names = {0: "generic", 1: "tile64x64", 2: "tile16x256", 3: "tile4x1024", 4: "tile256x16",
+    cfg_names = {0: "generic", 1: "tile64x64", 2: "tile16x256", 3: "tile4x1024", 4: "tile256x16", 6: "tile128x64",
                  5: "dot"}
     kname = {0: "k_generic", 1: "k_tile", 2: "k_tc (tcgen05)"}[st["kind"]]
     roof["kernel"] = (f"step {dom} of {len(steps)}: " +
@@ -385,7 +385,8 @@ def run_network(args, torch, dist, rank, world, local):
         ch = tnw.autotune(pairs, sliced, mode, reps=3)
         tuned = {"seconds": round(time.perf_counter() - t0, 3), "tensor_core": ch.count(8),
                  "tile_shapes": {n: ch.count(v) for v, n in
-                                 ((1, "64x64"), (2, "16x256"), (3, "4x1024"), (4, "256x16")) if ch.count(v)}}
+                                 ((1, "64x64"), (2, "16x256"), (3, "4x1024"), (4, "256x16"), (6, "128x64"))
+                                 if ch.count(v)}}
     plan = tnw.plan_info(pairs, sliced, mode)
     per = 8.0 if cplx else 2.0
     flops_step = per * info.C * sc

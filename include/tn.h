@@ -270,8 +270,9 @@ tn_status tn_plan_info(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
 /*
  * tn_autotune -- per-node kernel choice by measurement.
  * For every tree node that runs alone in its launch step on a tiled or
- * tensor-core kernel, each candidate -- the four CUDA-core tile shapes
- * (64x64, 16x256, 4x1024, 256x16 outputs per block) and, in the reduced-
+ * tensor-core kernel, each candidate -- the five CUDA-core tile shapes
+ * (64x64, 16x256, 4x1024, 256x16, 128x64 outputs per block, each with two
+ * K splits) and, in the reduced-
  * precision modes, the tensor-core GEMM -- is launched once to warm up and
  * then reps times between two CUDA events on `stream`; the fastest is kept
  * in the handle's cached plan for (tree, sliced labels, mode) and used by
@@ -279,7 +280,8 @@ tn_status tn_plan_info(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
  * tolerance whatever the choice).  Very large nodes that the tensor cores
  * can run skip the CUDA-core shapes.  The leaves must be attached; their
  * values do not matter.  choice (NULL or n_tensors-1 entries) receives per
- * node 0 (not tuned), 1..4 (tile shape in the order above) or 8 (tensor
+ * node 0 (not tuned), 1..4 or 6 (tile shapes 64x64, 16x256, 4x1024,
+ * 256x16, 128x64) or 8 (tensor
  * core).  Synchronises `stream`.  Errors as tn_contract.
  * Not in the paper: its executor has no kernel choices to tune.
  */

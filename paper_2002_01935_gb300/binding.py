@@ -191,7 +191,7 @@ def tn_contract_noalloc(h: int, pairs, sliced, out_ptr: int, out_mem: int, exp_p
 
 def tn_autotune(h: int, pairs, sliced, mode: int, reps: int = 3, stream: int = 0) -> List[int]:
     """Time every candidate kernel per node and keep the fastest in the
-    cached plan; returns the per-node choice (0 untuned, 1..4 tile shape,
+    cached plan; returns the per-node choice (0 untuned, 1..4 and 6 tile shape,
     8 tensor core)."""
     tr = _tree(pairs)
     sl = _arr(list(sliced) or [0], np.int64)

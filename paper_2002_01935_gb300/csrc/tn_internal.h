@@ -95,7 +95,7 @@ struct BitGroup {
 // bits; bit i of a group index contributes 1 << sh[i] to an operand offset
 // (kNoBit: the operand lacks that label).  Output layout [batch][M][N].
 constexpr uint8_t kNoBit = 255;
-enum TileCfg { kTile64x64 = 1, kTile16x256 = 2, kTile4x1024 = 3, kTile256x16 = 4, kTileDot = 5 };
+enum TileCfg { kTile64x64 = 1, kTile16x256 = 2, kTile4x1024 = 3, kTile256x16 = 4, kTileDot = 5, kTile128x64 = 6 };
 
 struct alignas(16) TileArgs {
     const void* A;

@@ -171,9 +171,10 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems, 
     const int64_t M = int64_t(1) << t.nm, N = int64_t(1) << t.nn, K = int64_t(1) << t.nk;
     int TM = 64, TN = 64, TK = 16;
     const bool dot = M * N <= 64 && K >= 512;
-    if (force_cfg >= kTile64x64 && force_cfg <= kTile256x16 && !dot) {
+    if (force_cfg >= kTile64x64 && force_cfg <= kTile128x64 && force_cfg != kTileDot && !dot) {
         // a shape forced by the autotuner (any shape is valid: tiles clip)
-        static const int shapes[5][3] = {{0, 0, 0}, {64, 64, 16}, {16, 256, 16}, {4, 1024, 4}, {256, 16, 16}};
+        static const int shapes[7][3] = {{0, 0, 0},    {64, 64, 16},   {16, 256, 16}, {4, 1024, 4},
+                                         {256, 16, 16}, {0, 0, 0},      {128, 64, 16}};
         t.cfg = force_cfg;
         TM = shapes[force_cfg][0];
         TN = shapes[force_cfg][1];
@@ -1289,7 +1290,7 @@ tn_status autotune_plan(NetDesc& d, Plan& p, int reps, int32_t* choice, cudaStre
         }
         // CUDA-core shapes, unless the node is so large that they cannot win
         if (!has_tc || vc < 32)
-            for (int v = kTile64x64; v <= kTile256x16; ++v)
+            for (int v : {int(kTile64x64), int(kTile16x256), int(kTile4x1024), int(kTile256x16), int(kTile128x64)})
                 for (int mult : {1, 4}) {
                     Node t;
                     if (make_variant(d, p, k, v, t, split_elems, mult)) cand[k].push_back({v, t});

@@ -720,6 +720,7 @@ static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
         case kTile16x256: e = launch_cfg<CPLX, 16, 256, 16, 4, 4>(a, s); break;
         case kTile4x1024: e = launch_cfg<CPLX, 4, 1024, 4, 4, 4>(a, s); break;
         case kTile256x16: e = launch_cfg<CPLX, 256, 16, 16, 4, 4>(a, s); break;
+        case kTile128x64: e = launch_cfg<CPLX, 128, 64, 16, 8, 4>(a, s); break;
         case kTileDot: {
             const int64_t outs = 1ll << (a.nm + a.nn);
             const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;

@@ -12,7 +12,7 @@ from paper_2002_01935_gb300 import inputs, planner
 
 pytestmark = pytest.mark.gpu
 
-VALID = {0, 1, 2, 3, 4, 8}
+VALID = {0, 1, 2, 3, 4, 6, 8}
 
 
 @pytest.fixture(scope="module")
