@@ -18,6 +18,10 @@ Workloads (``--workload``):
               12-cycle circuit and its gradient with respect to the (theta, phi)
               of all 93 fSim gates, through the autograd Function (forward tree
               and reverse sweep on the GPU); one step = loss + gradient.
+  node        one large complex node alone (two random tensors, M x K and
+              K x N by --node-bits, default 15,13,10 = the largest node of
+              the 7x7x14 slice), open M x N output: the tensor-core kernel
+              measured on its own; sampled outputs checked in FP64.
   batch       a bounded sample of amplitudes of a 6x6-qubit, 12-cycle circuit
               (one shared tree) plus 256 Ising networks with N even in
               [40, --ising-max-n], all in one captured launch sequence (unsliced);
@@ -56,6 +60,7 @@ WORKLOAD_NAMES = {
     "circuit7x7": "circuit_7x7_14cyc_hypergreedy_ws28_slice_sample",
     "batch": "batch_6x6_12cyc_amplitudes_plus_256_ising",
     "grad5x4": "grad_5x4_12cyc_fsim_params_64_bitstrings",
+    "node": "single_complex_node",
 }
 MODES = ["fp32", "tf32_split", "bf16_split", "tf32_3m"]
 # accuracy each mode is held to (relative, against the FP64 oracle)
@@ -861,6 +866,93 @@ def run_grad(args, torch, dist, rank, world, local):
     return 0
 
 
+def run_node(args, torch, dist, rank, world, local):
+    import numpy as np
+    from paper_2002_01935_gb300 import binding, inputs
+
+    mb, nb, kb = (int(x) for x in args.node_bits.split(","))
+    mode = args.mode
+    rng = np.random.default_rng(11 + rank)
+    ml = list(range(mb))
+    nl = list(range(mb, mb + nb))
+    kl = list(range(mb + nb, mb + nb + kb))
+    dims = {l: 2 for l in ml + nl + kl}
+    # K labels interleaved with M / N labels, as in a contraction tree
+    la = kl[::2] + ml + kl[1::2]
+    lb = nl[:3] + kl + nl[3:]
+    f = lambda s: (rng.standard_normal(s) + 1j * rng.standard_normal(s)).astype(np.complex64)
+    ta, tb = f([2] * len(la)), f([2] * len(lb))
+    net = inputs.Network([ta, tb], [la, lb], dims, ml + nl)
+    pairs = [(0, 1)]
+    leaves = [torch.from_numpy(t).cuda() for t in (ta, tb)]
+    tnw = binding.TensorNetwork(net.labels, net.dims, net.open, leaves, complex_=True)
+    plan = tnw.plan_info(pairs, [], mode)
+    steps = tnw.plan_steps(pairs, [], mode)
+    flops = 8.0 * 2.0 ** (mb + nb + kb)
+    stream = torch.cuda.current_stream()
+    out = torch.empty([2] * (mb + nb), dtype=torch.complex128, device="cuda")
+    ex = torch.empty((), dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        tnw.contract(pairs, [], mode, out=out, out_exp=ex)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    node_ev = [device_events(torch, stream, 2) for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    torch.cuda.synchronize()
+    clk.start()
+    torch.cuda.nvtx.range_push("timed")
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        tnw.contract(pairs, [], mode, out=out, out_exp=ex, prof_events=node_ev[i], prof_first=0)
+        ends[i].record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms_step = sum(s.elapsed_time(t) for s, t in zip(starts, ends)) / args.steps
+    ms_node = statistics.mean(a.elapsed_time(b) for a, b in node_ev)
+    peaks = load_peaks()
+    tc = steps[0]["kind"] == 2
+    passes = MODE_PASSES.get(mode, 1) if tc else 1
+    if mode == "tf32_3m" and tc:
+        passes = 0.75  # three real products per complex one instead of four
+    peak = (peaks["bf16_tflops"] * (1.0 if mode == "bf16_split" else TF32_OVER_BF16)) if tc else FP32_SIMT_TFLOPS
+    achieved = flops / (ms_node / 1e3) / 1e12
+    roof = {"bound": "tensor" if tc else "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "executed_frac": achieved * passes / peak, "traffic": None,
+            "peak_source": (f"{peaks['source']} bf16" + ("" if mode == "bf16_split" else " x 1.1/2.25")) if tc
+            else "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+            "kernel": f"node ({mb}, {nb}, {kb}) bits, {'pack + tcgen05 GEMM' if tc else 'k_tile'}",
+            "share_of_step": ms_node / ms_step}
+    # sampled outputs against the definition, in FP64
+    res = out.cpu().numpy().reshape(2 ** mb, 2 ** nb) * 2.0 ** int(ex.cpu())
+    A = ta.astype(np.complex128).transpose([la.index(l) for l in ml + kl]).reshape(2 ** mb, 2 ** kb)
+    B = tb.astype(np.complex128).transpose([lb.index(l) for l in kl + nl]).reshape(2 ** kb, 2 ** nb)
+    ii = rng.integers(0, 2 ** mb, 64)
+    jj = rng.integers(0, 2 ** nb, 64)
+    ref = np.einsum("sk,ks->s", A[ii], B[:, jj])
+    scale = np.einsum("sk,ks->s", np.abs(A[ii]), np.abs(B[:, jj]))
+    err = float(np.max(np.abs(res[ii, jj] - ref) / scale))
+    line = {
+        "metric": METRIC, "value": flops / (ms_step / 1e3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES["node"], "mode": mode, "bits_m_n_k": [mb, nb, kb],
+                   "plan_kernels": {"tensor_core": plan["n_tensor_core"], "tiled": plan["n_tiled"]},
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "step": "the node, its FP64 output accumulation and the copy to the caller's tensor"},
+        "node_ms": ms_node,
+        "rel_err_vs_fp64_sample": err,
+        "rel_err_definition": "64 sampled outputs, |got - exact| / (sum over k of |A||B|)",
+        "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tnw.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -871,6 +963,7 @@ def main():
     ap.add_argument("--slices", type=int, default=2, help="circuit7x7: slices per step")
     ap.add_argument("--amplitudes", type=int, default=8, help="batch: amplitudes per step")
     ap.add_argument("--ising", type=int, default=256, help="batch: Ising networks per step")
+    ap.add_argument("--node-bits", default="15,13,10", help="node: M,N,K label bits")
     ap.add_argument("--ising-max-n", type=int, default=100,
                     help="batch: largest Ising N (even N uniform in [40, this])")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -899,6 +992,8 @@ def main():
         rc = run_batch(args, torch, dist, rank, world, local)
     elif args.workload == "grad5x4":
         rc = run_grad(args, torch, dist, rank, world, local)
+    elif args.workload == "node":
+        rc = run_node(args, torch, dist, rank, world, local)
     else:
         rc = run_network(args, torch, dist, rank, world, local)
     if dist:
