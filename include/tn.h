@@ -209,6 +209,41 @@ tn_status tn_contract_grad(tn_net *net, const int32_t *tree_pairs, int32_t n_sli
                            const int64_t *sliced_labels, tn_mode mode, const double *out_adjoint,
                            int64_t adj_exp2, void *const *leaf_grads, void *stream);
 
+/* tn_contract_grad_ex flag: add the gradients into leaf_grads (which then
+ * hold the caller's running sums) instead of overwriting them. */
+#define TN_GRAD_ACCUMULATE 1u
+
+/*
+ * tn_contract_grad_ex -- tn_contract_grad with the adjoint in device memory
+ * and/or accumulation into the gradient buffers, for loops over many
+ * networks of one shape (e.g. the bitstrings of a circuit sharing a tree)
+ * that sum their gradients without host round trips.
+ *   out_adjoint   FP64 adjoint as in tn_contract_grad, in host memory
+ *                 (adj_mem = TN_MEM_HOST: copied before the call returns)
+ *                 or device memory (TN_MEM_DEVICE: read in stream order, so
+ *                 it may come from earlier work on the stream, e.g. the
+ *                 forward result, without a host synchronisation).
+ *   adj_exp2      power-of-two exponent of the adjoint (host value).
+ *   adj_exp2_dev  NULL, or (device adjoints only) a device int64 added to
+ *                 adj_exp2 in stream order -- e.g. the negated exponent of
+ *                 a tn_contract result, for adjoints such as 1 / value.
+ *   flags         0 or TN_GRAD_ACCUMULATE.
+ *   Other arguments as tn_contract_grad.
+ * Both calls keep, per (tree, slicing, mode), a library image of the leaves
+ * (refreshed from the attached pointers at the start of every call) and of
+ * the gradients, so that the per-slice launch sequence -- forward recompute,
+ * reverse sweep, leaf gathers -- is one CUDA graph captured on the first
+ * call and replayed by later calls whatever their pointers.  Neither call
+ * may be made while the stream is being captured (TN_EUNSUPPORTED).  Calls
+ * on one network must be ordered (one stream): they share that state.
+ * Errors: as tn_contract; TN_EINVAL for a bad adj_mem, unknown flags, or
+ * adj_exp2_dev with a host adjoint.
+ */
+tn_status tn_contract_grad_ex(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
+                              const int64_t *sliced_labels, tn_mode mode, const double *out_adjoint,
+                              int32_t adj_mem, int64_t adj_exp2, const int64_t *adj_exp2_dev,
+                              void *const *leaf_grads, uint32_t flags, void *stream);
+
 /*
  * tn_contract_noalloc -- tn_contract for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a deployment variant.

@@ -30,8 +30,10 @@ class _Contract(torch.autograd.Function):
     def backward(ctx, grad_out):
         # one handle may serve several forward calls: re-attach this call's leaves
         ctx.tnw.set_tensors(list(ctx.saved_tensors))
-        adj = grad_out.detach().to(torch.complex128 if ctx.tnw.dtype == binding.TN_C64
-                                   else torch.float64).cpu().numpy()
+        # the adjoint stays on the device: no host synchronisation
+        adj = grad_out.detach().to(device=ctx.saved_tensors[0].device,
+                                   dtype=torch.complex128 if ctx.tnw.dtype == binding.TN_C64
+                                   else torch.float64).contiguous()
         # leaves that need no gradient get none (NULL: skipped by the sweep)
         need = ctx.needs_input_grad[4:]
         grads = [torch.empty_like(t) if nd else None for t, nd in zip(ctx.saved_tensors, need)]

@@ -6,8 +6,8 @@ ImportError if it has not been built (``paper_2002_01935_gb300.build``);
 there is no fallback.
 
 The functions mirror the C names (tn_create, tn_set_tensor, tn_contract,
-tn_contract_ex, tn_contract_grad, tn_plan_info, tn_destroy, tn_last_error);
-``TensorNetwork`` wraps a handle for use with torch tensors.
+tn_contract_ex, tn_contract_grad, tn_contract_grad_ex, tn_plan_info, tn_destroy,
+tn_last_error); ``TensorNetwork`` wraps a handle for use with torch tensors.
 """
 from __future__ import annotations
 
@@ -60,6 +60,9 @@ _lib.tn_contract_grad.restype = ctypes.c_int
 _lib.tn_contract_grad.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
                                   ctypes.POINTER(_vp), _vp]
+_lib.tn_contract_grad_ex.restype = ctypes.c_int
+_lib.tn_contract_grad_ex.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int, _vp, ctypes.c_int32,
+                                     ctypes.c_int64, _vp, ctypes.POINTER(_vp), ctypes.c_uint32, _vp]
 _lib.tn_contract_noalloc.restype = ctypes.c_int
 _lib.tn_contract_noalloc.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, _vp, ctypes.c_int32, _i64p,
                                      _vp]
@@ -87,6 +90,7 @@ _lib.tn_version.restype = ctypes.c_char_p
 _lib.tn_version.argtypes = []
 
 EXPORTS = ["tn_create", "tn_set_tensor", "tn_contract", "tn_contract_ex", "tn_contract_grad",
+           "tn_contract_grad_ex",
            "tn_contract_noalloc", "tn_contract_instances", "tn_autotune", "tn_plan_info", "tn_plan_steps",
            "tn_batch_create",
            "tn_batch_contract", "tn_batch_destroy", "tn_destroy", "tn_last_error", "tn_version"]
@@ -178,6 +182,22 @@ def tn_contract_grad(h: int, pairs, sliced, mode: int, adjoint: np.ndarray, adj_
     _check(_lib.tn_contract_grad(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64),
                                  mode, adj.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                  int(adj_exp2), gp, stream))
+
+
+TN_GRAD_ACCUMULATE = 1
+
+
+def tn_contract_grad_ex(h: int, pairs, sliced, mode: int, adj_ptr: int, adj_mem: int, adj_exp2: int,
+                        adj_exp2_dev: int, grad_ptrs: Sequence[int], flags: int = 0,
+                        stream: int = 0) -> None:
+    """tn_contract_grad with a host or device adjoint (pointer to FP64) and
+    optional accumulation (flags = TN_GRAD_ACCUMULATE)."""
+    tr = _tree(pairs)
+    sl = _arr(list(sliced) or [0], np.int64)
+    gp = (_vp * len(grad_ptrs))(*[g or None for g in grad_ptrs])
+    _check(_lib.tn_contract_grad_ex(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
+                                    adj_ptr, adj_mem, int(adj_exp2), adj_exp2_dev or None, gp, flags,
+                                    stream))
 
 
 def tn_contract_noalloc(h: int, pairs, sliced, out_ptr: int, out_mem: int, exp_ptr: int,
@@ -311,24 +331,54 @@ class TensorNetwork:
                        slice_begin, slice_count, no_graph, evp, prof_first, slice_batch)
         return out, out_exp
 
-    def grad(self, pairs, sliced, mode, adjoint, adj_exp2=0, grads=None, stream=None):
+    def grad(self, pairs, sliced, mode, adjoint, adj_exp2=0, grads=None, stream=None,
+             accumulate=False):
         """Leaf gradients conj(d value / d T_v) * adjoint, summed over slices
         and contracted over the open labels (torch's convention).
 
-        ``adjoint``: array shaped like the output (FP64).  ``grads``: torch
-        tensors shaped like the leaves (device, leaf dtype), or None to
-        allocate.  Returns the list of gradient tensors (asynchronous)."""
+        ``adjoint``: shaped like the output, FP64 (complex128 for complex
+        networks): a host array, or a CUDA torch tensor (read in stream
+        order, no host synchronisation).  ``adj_exp2``: an int, or (with a
+        CUDA adjoint) a CUDA int64 scalar tensor; the adjoint is
+        adjoint * 2**adj_exp2.  ``grads``: torch tensors shaped like the
+        leaves (device, leaf dtype; None entries are skipped), or None to
+        allocate.  ``accumulate``: add into ``grads`` instead of overwriting.
+        Returns the list of gradient tensors (asynchronous)."""
         import torch
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         cplx = self.dtype == TN_C64
-        adj = np.ascontiguousarray(np.asarray(adjoint, dtype=np.complex128 if cplx else np.float64))
-        if adj.size != int(np.prod(self.out_shape)):
-            raise ValueError("adjoint shape does not match the output")
+        n_out = int(np.prod(self.out_shape))
+        keep = None
+        if isinstance(adjoint, torch.Tensor) and adjoint.is_cuda:
+            want = torch.complex128 if cplx else torch.float64
+            if adjoint.dtype != want:
+                raise TypeError(f"adjoint dtype {adjoint.dtype}, expected {want}")
+            if adjoint.numel() != n_out:
+                raise ValueError("adjoint shape does not match the output")
+            keep = adjoint.contiguous()
+            adj_ptr, adj_mem = keep.data_ptr(), TN_MEM_DEVICE
+        else:
+            if isinstance(adjoint, torch.Tensor):
+                adjoint = adjoint.detach().numpy()
+            adj = np.ascontiguousarray(np.asarray(adjoint, dtype=np.complex128 if cplx else np.float64))
+            if adj.size != n_out:
+                raise ValueError("adjoint shape does not match the output")
+            keep = adj
+            adj_ptr, adj_mem = adj.ctypes.data, TN_MEM_HOST
+        exp_host, exp_dev = 0, 0
+        if isinstance(adj_exp2, torch.Tensor):
+            if adj_mem != TN_MEM_DEVICE or not adj_exp2.is_cuda or adj_exp2.dtype != torch.int64:
+                raise TypeError("a tensor adj_exp2 must be a CUDA int64 scalar, with a CUDA adjoint")
+            exp_dev = adj_exp2.data_ptr()
+        else:
+            exp_host = int(adj_exp2)
         if grads is None:
             grads = [torch.empty_like(t, device="cuda") for t in self._keep]
         s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
-        tn_contract_grad(self.h, pairs, sliced, m, adj.view(np.float64), int(adj_exp2),
-                         [g.data_ptr() if g is not None else 0 for g in grads], s)
+        tn_contract_grad_ex(self.h, pairs, sliced, m, adj_ptr, adj_mem, exp_host, exp_dev,
+                            [g.data_ptr() if g is not None else 0 for g in grads],
+                            TN_GRAD_ACCUMULATE if accumulate else 0, s)
+        del keep
         return grads
 
     def autotune(self, pairs, sliced=(), mode="fp32", reps=3, stream=None):

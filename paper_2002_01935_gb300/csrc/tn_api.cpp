@@ -269,11 +269,16 @@ tn_status tn_autotune(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced, 
     return TN_OK;
 }
 
-tn_status tn_contract_grad(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
-                           const int64_t* sliced_labels, tn_mode mode, const double* out_adjoint,
-                           int64_t adj_exp2, void* const* leaf_grads, void* stream) {
+tn_status tn_contract_grad_ex(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
+                              const int64_t* sliced_labels, tn_mode mode, const double* out_adjoint,
+                              int32_t adj_mem, int64_t adj_exp2, const int64_t* adj_exp2_dev,
+                              void* const* leaf_grads, uint32_t flags, void* stream) {
     if (!net) return fail(TN_EINVAL, "tn_contract_grad: net is NULL");
     if (!out_adjoint || !leaf_grads) return fail(TN_EINVAL, "tn_contract_grad: NULL argument");
+    if (adj_mem != TN_MEM_DEVICE && adj_mem != TN_MEM_HOST) return fail(TN_EINVAL, "bad adj_mem");
+    if (adj_exp2_dev && adj_mem != TN_MEM_DEVICE)
+        return fail(TN_EINVAL, "tn_contract_grad: adj_exp2_dev needs a device adjoint");
+    if (flags & ~(uint32_t)TN_GRAD_ACCUMULATE) return fail(TN_EINVAL, "tn_contract_grad: unknown flags");
     for (int v = 0; v < net->d.n; ++v)
         if (!net->d.leaves[v].ptr) return fail(TN_EINVAL, "tn_contract_grad: tensor without data");
     Plan* p = nullptr;
@@ -282,10 +287,17 @@ tn_status tn_contract_grad(tn_net* net, const int32_t* tree_pairs, int32_t n_sli
     st = ensure_device(net, p);
     if (st != TN_OK) return st;
     std::string err;
-    st = tn::run_grad(net->d, *p, net->unit, out_adjoint, adj_exp2, leaf_grads, (cudaStream_t)stream,
-                      err);
+    st = tn::run_grad(net->d, *p, net->unit, out_adjoint, adj_mem, adj_exp2, adj_exp2_dev, leaf_grads,
+                      (flags & TN_GRAD_ACCUMULATE) != 0, (cudaStream_t)stream, err);
     if (st != TN_OK) return fail(st, err);
     return TN_OK;
+}
+
+tn_status tn_contract_grad(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
+                           const int64_t* sliced_labels, tn_mode mode, const double* out_adjoint,
+                           int64_t adj_exp2, void* const* leaf_grads, void* stream) {
+    return tn_contract_grad_ex(net, tree_pairs, n_sliced, sliced_labels, mode, out_adjoint, TN_MEM_HOST,
+                               adj_exp2, nullptr, leaf_grads, 0u, stream);
 }
 
 tn_status tn_contract_noalloc(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,

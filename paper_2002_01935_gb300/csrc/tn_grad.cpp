@@ -13,6 +13,16 @@
 // occurs in that tensor only (summed at its first contraction) gives an
 // adjoint constant along it: the gather broadcasts.  Renormalisation
 // exponents are tracked exactly as in the forward pass.
+//
+// Launch structure.  The forward recompute and the sweep form one list of
+// nodes (forward nodes, then adjoint nodes root to leaves) scheduled like
+// the forward pass: by dependency level, the small nodes of consecutive
+// levels as one dataflow wave launch, the others one launch each.  All of
+// it reads the leaves from a library-owned image (refreshed by one gather
+// launch per call) and adds the leaf adjoints into library-owned
+// accumulators (copied, or added, to the caller's buffers by one launch at
+// the end), so the per-slice sequence has no per-call pointer in it: it is
+// captured once as a CUDA graph and replayed by every later call.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,6 +45,18 @@ struct GradState {
     int64_t ws_elems = 0;
     int64_t split_bytes = 0;
     int n_slots = 0;
+    // schedule over the combined node list: forward node k is k, adjoint
+    // node j is nn + j (Step.node / Step.nodes / WaveItem.node use these)
+    std::vector<Step> steps;
+    std::vector<WaveItem> items;
+    std::vector<int> flow_deps;  // per combined node: child a, chunks, child b, chunks
+    bool any_flow = false;
+    // leaf images (floats): leaf v at leaf_off[v] in both the leaf copy and
+    // the gradient accumulator
+    std::vector<int64_t> leaf_off;
+    int64_t leaf_floats = 0;
+    int64_t max_leaf_floats = 0;
+    int64_t max_grad_n = 0;
     // device
     void* ws = nullptr;
     void* split_buf = nullptr;
@@ -42,10 +64,24 @@ struct GradState {
     int64_t* exps = nullptr;
     Control* ctl = nullptr;
     unsigned* leafmax = nullptr;
-    const float** leaf_ptr_dev = nullptr;
+    float* leaf_img = nullptr;
+    float* gacc = nullptr;
+    const float** img_ptr_dev = nullptr;   // leaf image pointers (fixed)
     int64_t* leaf_nfloat_dev = nullptr;
+    TileArgs* descs_dev = nullptr;
+    WaveItem* items_dev = nullptr;
+    int* flow_deps_dev = nullptr;
+    unsigned* flow_cnt_dev = nullptr;      // done[combined node], then one head per step
+    LeafGradArgs* lg_dev = nullptr;        // one entry per leaf
+    CopyEntry* copy_dev = nullptr;         // per call: gather entries, then scatter entries
+    double* adj_dev = nullptr;             // host adjoints are staged here
+    int64_t* perm_dev = nullptr;           // root offset of each output
     std::vector<GenericArgs> gen_f, gen_b;
     std::vector<TileArgs> tile_f, tile_b;
+    // the per-slice sequence as a captured graph (built on the first call)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
 };
 
 static bool has_label(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
@@ -134,15 +170,126 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
     G.ws_elems = std::max<int64_t>(off, 64);
     // scale slots: forward node k -> k; adjoint of vertex v -> nn + v (root last)
     G.n_slots = nn + NV;
+    // ---- schedule of the combined list (forward nodes, then adjoints)
+    const int nb = (int)G.bwd.size();
+    const int ncomb = nn + nb;
+    std::vector<int> adj_prod(NV, -1);  // adjoint node of each vertex
+    for (int j = 0; j < nb; ++j) adj_prod[G.bwd_target[j]] = nn + j;
+    auto producer = [&](int v) -> int {  // combined node that writes vertex v, -1 if none
+        if (v < n) return -1;            // unit, leaf
+        if (v < NV) return v - n;        // forward node
+        return adj_prod[v - NV];         // adjoint (-1: the root's, set per call)
+    };
+    auto cnode = [&](int c) -> const Node& { return c < nn ? G.fwd[c] : G.bwd[c - nn]; };
+    std::vector<int> order(G.fwd_order);
+    for (int j = 0; j < nb; ++j) order.push_back(nn + j);
+    std::vector<int> level(ncomb, 0);
+    int max_level = 0;
+    for (int c : order) {
+        const Node& nd = cnode(c);
+        int l = 0;
+        for (int v : {nd.ca, nd.cb}) {
+            const int pr = producer(v);
+            if (pr >= 0) l = std::max(l, level[pr]);
+        }
+        level[c] = l + 1;
+        max_level = std::max(max_level, level[c]);
+    }
+    std::vector<std::vector<int>> at(max_level + 1);
+    for (int c : order) at[level[c]].push_back(c);
+    G.steps.clear();
+    G.items.clear();
+    for (int L = 1; L <= max_level; ++L) {
+        Step w;
+        w.wave = 1;
+        w.item_begin = (int)G.items.size();
+        std::vector<int> singles;
+        for (int c : at[L]) {
+            const Node& nd = cnode(c);
+            const bool small = nd.kind == kTiled && nd.tile.cfg != kTileDot && nd.size <= (1 << 16) &&
+                               nd.vc <= 20.0 && !f.no_waves;
+            if (!small) {
+                singles.push_back(c);
+                continue;
+            }
+            const int64_t chunk = std::min<int64_t>(nd.size, 1024);
+            for (int64_t o = 0; o < nd.size; o += chunk) {
+                WaveItem it;
+                it.node = c;
+                it.pad = 0;
+                it.o_begin = o;
+                it.o_count = chunk;
+                G.items.push_back(it);
+            }
+            w.nodes.push_back(c);
+        }
+        w.item_count = (int)G.items.size() - w.item_begin;
+        if (w.item_count > 0) G.steps.push_back(w);
+        for (int c : singles) {
+            Step s;
+            s.node = c;
+            s.nodes.push_back(c);
+            G.steps.push_back(s);
+        }
+    }
+    if (!f.no_flow) {  // consecutive waves: one dataflow launch
+        std::vector<Step> merged;
+        for (Step& st : G.steps) {
+            if (st.wave && !merged.empty() && merged.back().wave &&
+                merged.back().item_begin + merged.back().item_count == st.item_begin) {
+                Step& m = merged.back();
+                m.item_count += st.item_count;
+                m.nodes.insert(m.nodes.end(), st.nodes.begin(), st.nodes.end());
+                m.flow = 1;
+            } else {
+                merged.push_back(st);
+            }
+        }
+        G.steps = merged;
+    }
+    G.flow_deps.assign(4 * (size_t)std::max(ncomb, 1), -1);
+    G.any_flow = false;
+    for (const Step& st : G.steps) {
+        if (!st.flow) continue;
+        G.any_flow = true;
+        std::vector<char> in_step(ncomb, 0);
+        for (int c : st.nodes) in_step[c] = 1;
+        for (int c : st.nodes) {
+            const Node& nd = cnode(c);
+            int slot = 0;
+            for (int v : {nd.ca, nd.cb}) {
+                const int pr = producer(v);
+                if (pr >= 0 && in_step[pr]) {
+                    const Node& ch = cnode(pr);
+                    const int64_t chunk = std::min<int64_t>(ch.size, 1024);
+                    G.flow_deps[4 * c + 2 * slot] = pr;
+                    G.flow_deps[4 * c + 2 * slot + 1] = (int)((ch.size + chunk - 1) / chunk);
+                }
+                ++slot;
+            }
+        }
+    }
+    // ---- leaf images
+    G.leaf_off.assign(n, 0);
+    G.leaf_floats = 0;
+    G.max_leaf_floats = 0;
+    for (int v = 0; v < n; ++v) {
+        const int64_t nf = d.leaves[v].size * (d.is_complex() ? 2 : 1);
+        G.leaf_off[v] = G.leaf_floats;
+        G.leaf_floats += (nf + 63) / 64 * 64;  // 256-byte aligned leaves
+        G.max_leaf_floats = std::max(G.max_leaf_floats, nf);
+    }
     (void)err;
     return TN_OK;
 }
 
-static tn_status alloc_grad(const NetDesc& d, GradState& G, void* unit, std::string& err) {
+static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void* unit, std::string& err) {
     const size_t eb = d.elem_bytes();
     const int n = d.n;
     const int nn = (int)G.fwd.size();
+    const int nb = (int)G.bwd.size();
     const int NV = G.NV;
+    const bool cplx = d.is_complex();
     auto ck = [&](cudaError_t e, const char* what) {
         if (e != cudaSuccess) {
             err = std::string(what) + ": " + cudaGetErrorString(e);
@@ -150,23 +297,44 @@ static tn_status alloc_grad(const NetDesc& d, GradState& G, void* unit, std::str
         }
         return true;
     };
-    if (!ck(cudaMalloc(&G.ws, (size_t)G.ws_elems * eb), "gradient workspace")) return TN_ENOMEM;
-    if (G.split_bytes && !ck(cudaMalloc(&G.split_buf, G.split_bytes), "cudaMalloc")) return TN_ENOMEM;
-    if (!ck(cudaMalloc(&G.maxabs, sizeof(unsigned) * G.n_slots), "cudaMalloc")) return TN_ENOMEM;
-    if (!ck(cudaMalloc(&G.exps, sizeof(int64_t) * G.n_slots), "cudaMalloc")) return TN_ENOMEM;
-    if (!ck(cudaMalloc(&G.ctl, sizeof(Control)), "cudaMalloc")) return TN_ENOMEM;
-    if (!ck(cudaMalloc(&G.leafmax, sizeof(unsigned) * n), "cudaMalloc")) return TN_ENOMEM;
-    if (!ck(cudaMalloc((void**)&G.leaf_ptr_dev, sizeof(void*) * n), "cudaMalloc")) return TN_ENOMEM;
-    if (!ck(cudaMalloc(&G.leaf_nfloat_dev, sizeof(int64_t) * n), "cudaMalloc")) return TN_ENOMEM;
-    std::vector<int64_t> nf(n);
-    for (int v = 0; v < n; ++v) nf[v] = d.leaves[v].size * (d.is_complex() ? 2 : 1);
-    if (!ck(cudaMemcpy(G.leaf_nfloat_dev, nf.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice),
-            "cudaMemcpy"))
-        return TN_ECUDA;
+#define AL(ptr, bytes, what) \
+    if (!ck(cudaMalloc((void**)&(ptr), (size_t)(bytes)), what)) return TN_ENOMEM
+#define UP(dst, src, bytes) \
+    if (!ck(cudaMemcpy((void*)(dst), (const void*)(src), (size_t)(bytes), cudaMemcpyHostToDevice), "cudaMemcpy")) \
+        return TN_ECUDA
+    AL(G.ws, (size_t)G.ws_elems * eb, "gradient workspace");
+    if (G.split_bytes) AL(G.split_buf, G.split_bytes, "cudaMalloc");
+    AL(G.maxabs, sizeof(unsigned) * G.n_slots, "cudaMalloc");
+    AL(G.exps, sizeof(int64_t) * G.n_slots, "cudaMalloc");
+    AL(G.ctl, sizeof(Control), "cudaMalloc");
+    AL(G.leafmax, sizeof(unsigned) * n, "cudaMalloc");
+    AL(G.leaf_img, sizeof(float) * std::max<int64_t>(G.leaf_floats, 64), "leaf image");
+    AL(G.gacc, sizeof(float) * std::max<int64_t>(G.leaf_floats, 64), "gradient accumulators");
+    AL(G.img_ptr_dev, sizeof(void*) * n, "cudaMalloc");
+    AL(G.leaf_nfloat_dev, sizeof(int64_t) * n, "cudaMalloc");
+    AL(G.lg_dev, sizeof(LeafGradArgs) * n, "cudaMalloc");
+    AL(G.copy_dev, sizeof(CopyEntry) * 2 * n, "cudaMalloc");
+    const int64_t n_out = f.n_out;
+    AL(G.adj_dev, sizeof(double) * n_out * (cplx ? 2 : 1), "cudaMalloc");
+    AL(G.perm_dev, sizeof(int64_t) * n_out, "cudaMalloc");
+    const int ncomb = nn + nb;
+    AL(G.flow_deps_dev, sizeof(int) * G.flow_deps.size(), "cudaMalloc");
+    AL(G.flow_cnt_dev, sizeof(unsigned) * ((size_t)ncomb + G.steps.size() + 1), "cudaMalloc");
+    UP(G.flow_deps_dev, G.flow_deps.data(), sizeof(int) * G.flow_deps.size());
+    {
+        std::vector<const float*> ip(n);
+        std::vector<int64_t> nf(n);
+        for (int v = 0; v < n; ++v) {
+            ip[v] = G.leaf_img + G.leaf_off[v];
+            nf[v] = d.leaves[v].size * (cplx ? 2 : 1);
+        }
+        UP(G.img_ptr_dev, ip.data(), sizeof(void*) * n);
+        UP(G.leaf_nfloat_dev, nf.data(), sizeof(int64_t) * n);
+    }
     char* ws = (char*)G.ws;
     auto fwd_ptr = [&](int v) -> const void* {
         if (v < 0) return unit;
-        if (v < n) return nullptr;  // leaf: patched per call
+        if (v < n) return G.leaf_img + G.leaf_off[v];
         return ws + G.fwd[v - n].ws_off * eb;
     };
     auto slot_max = [&](int v) -> const unsigned* {
@@ -216,9 +384,9 @@ static tn_status alloc_grad(const NetDesc& d, GradState& G, void* unit, std::str
                             ws + nd.ws_off * eb, G.maxabs + k, G.exps + k);
         if (st != TN_OK) return st;
     }
-    G.gen_b.assign(G.bwd.size(), GenericArgs{});
-    G.tile_b.assign(G.bwd.size(), TileArgs{});
-    for (size_t j = 0; j < G.bwd.size(); ++j) {
+    G.gen_b.assign(nb, GenericArgs{});
+    G.tile_b.assign(nb, TileArgs{});
+    for (int j = 0; j < nb; ++j) {
         Node& nd = G.bwd[j];
         auto operand = [&](int v) -> const void* {
             if (v >= NV) return ws + G.adj_off[v - NV] * eb;
@@ -229,20 +397,85 @@ static tn_status alloc_grad(const NetDesc& d, GradState& G, void* unit, std::str
                             ws + nd.ws_off * eb, G.maxabs + nn + target, G.exps + nn + target);
         if (st != TN_OK) return st;
     }
+    if (!G.items.empty()) {
+        std::vector<TileArgs> descs(ncomb);
+        for (int k = 0; k < nn; ++k) descs[k] = G.tile_f[k];
+        for (int j = 0; j < nb; ++j) descs[nn + j] = G.tile_b[j];
+        AL(G.descs_dev, sizeof(TileArgs) * ncomb, "cudaMalloc");
+        AL(G.items_dev, sizeof(WaveItem) * G.items.size(), "cudaMalloc");
+        UP(G.descs_dev, descs.data(), sizeof(TileArgs) * ncomb);
+        UP(G.items_dev, G.items.data(), sizeof(WaveItem) * G.items.size());
+    }
+    // leaf gathers: adjoint of leaf v -> its accumulator
+    std::vector<LeafGradArgs> lg(n);
+    G.max_grad_n = 0;
+    for (int v = 0; v < n; ++v) {
+        LeafGradArgs& a = lg[v];
+        memset(&a, 0, sizeof(a));
+        const LeafDesc& lf = d.leaves[v];
+        a.grad = G.gacc + G.leaf_off[v];
+        a.adj = ws + G.adj_off[v] * eb;
+        a.exp_adj = G.exps + nn + v;
+        a.ctl = G.ctl;
+        a.sl = f.leaf_sl[v];
+        const std::vector<int>& al = G.g.vlab[NV + v];
+        const std::vector<int64_t>& as = G.g.vstride[NV + v];
+        a.n = 1;
+        int nd_ = 0;
+        for (int i = (int)lf.lab.size() - 1; i >= 0; --i) {
+            const int l = lf.lab[i];
+            if (std::find(f.sliced.begin(), f.sliced.end(), l) != f.sliced.end()) continue;
+            if (nd_ >= kMaxDigits) {
+                err = "leaf rank exceeds the gradient gather limit";
+                return TN_EUNSUPPORTED;
+            }
+            a.dim[nd_] = (int32_t)d.dims[l];
+            a.gstride[nd_] = lf.stride[i];
+            int64_t s = 0;
+            for (size_t j = 0; j < al.size(); ++j)
+                if (al[j] == l) s = as[j];
+            a.astride[nd_] = s;
+            a.n *= d.dims[l];
+            ++nd_;
+        }
+        a.n_d = nd_;
+        G.max_grad_n = std::max(G.max_grad_n, a.n);
+    }
+    UP(G.lg_dev, lg.data(), sizeof(LeafGradArgs) * n);
+    // root layout of each output (open labels in tn_create order, last fastest)
+    {
+        const Node& root = G.fwd.back();
+        std::vector<int64_t> perm(n_out);
+        for (int64_t o = 0; o < n_out; ++o) {
+            int64_t rem = o, dst = 0;
+            for (int i = (int)d.open.size() - 1; i >= 0; --i) {
+                const int l = d.open[i];
+                const int64_t v = rem % d.dims[l];
+                rem /= d.dims[l];
+                for (size_t j = 0; j < root.lab.size(); ++j)
+                    if (root.lab[j] == l) dst += v * root.stride[j];
+            }
+            perm[o] = dst;
+        }
+        UP(G.perm_dev, perm.data(), sizeof(int64_t) * n_out);
+    }
+#undef AL
+#undef UP
     return TN_OK;
 }
 
 void free_grad(Plan& p) {
     GradState* G = p.grad;
     if (!G) return;
-    cudaFree(G->ws);
-    if (G->split_buf) cudaFree(G->split_buf);
-    cudaFree(G->maxabs);
-    cudaFree(G->exps);
-    cudaFree(G->ctl);
-    cudaFree(G->leafmax);
-    cudaFree(G->leaf_ptr_dev);
-    cudaFree(G->leaf_nfloat_dev);
+    for (void* q : {(void*)G->ws, G->split_buf, (void*)G->maxabs, (void*)G->exps, (void*)G->ctl,
+                    (void*)G->leafmax, (void*)G->leaf_img, (void*)G->gacc, (void*)G->img_ptr_dev,
+                    (void*)G->leaf_nfloat_dev, (void*)G->descs_dev, (void*)G->items_dev,
+                    (void*)G->flow_deps_dev, (void*)G->flow_cnt_dev, (void*)G->lg_dev,
+                    (void*)G->copy_dev, (void*)G->adj_dev, (void*)G->perm_dev})
+        if (q) cudaFree(q);
+    if (G->gexec) cudaGraphExecDestroy(G->gexec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    if (G->cap_stream) cudaStreamDestroy(G->cap_stream);
     delete G;
     p.grad = nullptr;
 }
@@ -255,11 +488,41 @@ static cudaError_t launch_node(const Node& nd, const GenericArgs& g, const TileA
     return launch_generic(g, c, s);
 }
 
-tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int64_t adj_exp2,
-                   void* const* grads, cudaStream_t stream, std::string& err) {
+// One slice: scale slots and dataflow counters cleared, the schedule's
+// steps, the leaf gathers, and the slice counter advanced.
+static cudaError_t enqueue_grad_slice(const GradState& G, tn_mode mode, bool cplx, cudaStream_t s) {
+    const int nn = (int)G.fwd.size();
+    const int ncomb = nn + (int)G.bwd.size();
+    cudaError_t e = cudaMemsetAsync(G.maxabs, 0, sizeof(unsigned) * (G.n_slots - 1), s);
+    if (e == cudaSuccess && G.any_flow)
+        e = cudaMemsetAsync(G.flow_cnt_dev, 0, sizeof(unsigned) * ((size_t)ncomb + G.steps.size()), s);
+    const void* const* leaf_tab = reinterpret_cast<const void* const*>(G.img_ptr_dev);
+    for (size_t k = 0; k < G.steps.size() && e == cudaSuccess; ++k) {
+        const Step& st = G.steps[k];
+        if (st.wave) {
+            if (st.flow)
+                e = launch_wave(G.items_dev + st.item_begin, st.item_count, G.descs_dev, leaf_tab, cplx, s,
+                                reinterpret_cast<const int4*>(G.flow_deps_dev), G.flow_cnt_dev,
+                                G.flow_cnt_dev + ncomb + k, 1);
+            else
+                e = launch_wave(G.items_dev + st.item_begin, st.item_count, G.descs_dev, leaf_tab, cplx, s);
+        } else if (st.node < nn) {
+            e = launch_node(G.fwd[st.node], G.gen_f[st.node], G.tile_f[st.node], mode, cplx, s);
+        } else {
+            const int j = st.node - nn;
+            e = launch_node(G.bwd[j], G.gen_b[j], G.tile_b[j], mode, cplx, s);
+        }
+    }
+    if (e == cudaSuccess) e = launch_leaf_grads(G.lg_dev, (int)G.leaf_off.size(), G.max_grad_n, cplx, s);
+    if (e == cudaSuccess) e = launch_advance(G.ctl, s);
+    return e;
+}
+
+tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_mem, int64_t adj_exp2,
+                   const int64_t* adj_exp2_dev, void* const* grads, bool accumulate, cudaStream_t stream,
+                   std::string& err) {
     const int n = d.n;
     const bool cplx = d.is_complex();
-    const size_t eb = d.elem_bytes();
 #define CK(x)                                                          \
     do {                                                               \
         cudaError_t e_ = (x);                                          \
@@ -275,14 +538,15 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int64_t a
         }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        err = "tn_contract_grad: not available under stream capture (it uploads per-call tables; "
+              "its per-slice work is already a CUDA graph)";
+        return TN_EUNSUPPORTED;
+    }
     if (!p.grad) {
-        if (cap != cudaStreamCaptureStatusNone) {
-            err = "tn_contract_grad: the first call for a tree must run outside stream capture";
-            return TN_EUNSUPPORTED;
-        }
         GradState* G = new GradState;
         tn_status st = build_grad(d, p, *G, err);
-        if (st == TN_OK) st = alloc_grad(d, *G, unit, err);
+        if (st == TN_OK) st = alloc_grad(d, p, *G, unit, err);
         if (st != TN_OK) {
             p.grad = G;
             free_grad(p);
@@ -292,107 +556,56 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int64_t a
     }
     GradState& G = *p.grad;
     const int nn = (int)G.fwd.size();
-    const int NV = G.NV;
     const int root_v = n + nn - 1;
-    // leaf pointers into the forward arguments
-    std::vector<const void*> lp(n);
-    for (int v = 0; v < n; ++v) lp[v] = d.leaves[v].ptr;
-    for (int k = 0; k < nn; ++k) {
-        const Node& nd = G.fwd[k];
-        if (nd.ca >= 0 && nd.ca < n) G.gen_f[k].A = G.tile_f[k].A = lp[nd.ca];
-        if (nd.cb >= 0 && nd.cb < n) G.gen_f[k].B = G.tile_f[k].B = lp[nd.cb];
-    }
-    for (size_t j = 0; j < G.bwd.size(); ++j) {
-        const Node& nd = G.bwd[j];
-        if (nd.ca >= 0 && nd.ca < n) G.gen_b[j].A = G.tile_b[j].A = lp[nd.ca];
-        if (nd.cb >= 0 && nd.cb < n) G.gen_b[j].B = G.tile_b[j].B = lp[nd.cb];
-    }
-    CK(cudaMemcpyAsync(G.leaf_ptr_dev, lp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, stream));
-    int64_t mx_leaf = 0;
-    for (int v = 0; v < n; ++v) mx_leaf = std::max(mx_leaf, d.leaves[v].size * (d.is_complex() ? 2 : 1));
-    CK(launch_leaf_max(G.leaf_ptr_dev, G.leaf_nfloat_dev, G.leafmax, n, stream, mx_leaf));
-    // root adjoint: caller's FP64 array (open labels in tn_create order) ->
-    // root layout, normalised to a power-of-two scaled float tensor
-    const Node& root = G.fwd.back();
-    const int64_t n_out = p.n_out;
-    std::vector<double> perm((size_t)n_out * (cplx ? 2 : 1), 0.0);
-    double amax = 0;
-    for (int64_t o = 0; o < n_out; ++o) {
-        int64_t rem = o, dst = 0;
-        for (int i = (int)d.open.size() - 1; i >= 0; --i) {
-            const int l = d.open[i];
-            const int64_t v = rem % d.dims[l];
-            rem /= d.dims[l];
-            for (size_t j = 0; j < root.lab.size(); ++j)
-                if (root.lab[j] == l) dst += v * root.stride[j];
-        }
-        for (int c = 0; c < (cplx ? 2 : 1); ++c) {
-            const double x = adj[o * (cplx ? 2 : 1) + c];
-            perm[dst * (cplx ? 2 : 1) + c] = x;
-            amax = std::max(amax, std::fabs(x));
-        }
-    }
-    int eadj = 0;
-    if (amax > 0) std::frexp(amax, &eadj);
-    std::vector<float> rootadj(perm.size());
-    for (size_t i = 0; i < perm.size(); ++i) rootadj[i] = (float)std::ldexp(perm[i], -eadj);
-    const float rmax = amax > 0 ? (float)std::ldexp(amax, -eadj) : 0.f;
-    unsigned rmax_bits;
-    std::memcpy(&rmax_bits, &rmax, 4);
-    const int64_t rexp = (int64_t)eadj + adj_exp2;
-    char* ws = (char*)G.ws;
-    CK(cudaMemcpyAsync(ws + G.adj_off[root_v] * eb, rootadj.data(), rootadj.size() * sizeof(float),
-                       cudaMemcpyHostToDevice, stream));
-    const int root_slot = nn + root_v;
-    CK(cudaMemcpyAsync(G.maxabs + root_slot, &rmax_bits, sizeof(unsigned), cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(G.exps + root_slot, &rexp, sizeof(int64_t), cudaMemcpyHostToDevice, stream));
-    // zero the outputs, then every slice: forward, reverse sweep, leaf gather
+    const size_t eb = d.elem_bytes();
+    // per-call table: the leaves into the image, then the gradients out
+    std::vector<CopyEntry> tab;
+    tab.reserve(2 * n);
     for (int v = 0; v < n; ++v)
-        if (grads[v]) CK(cudaMemsetAsync(grads[v], 0, d.leaves[v].size * eb, stream));
+        tab.push_back(CopyEntry{static_cast<const float*>(d.leaves[v].ptr), G.leaf_img + G.leaf_off[v],
+                                d.leaves[v].size * (cplx ? 2 : 1), 0, 0});
+    for (int v = 0; v < n; ++v)
+        if (grads[v])
+            tab.push_back(CopyEntry{G.gacc + G.leaf_off[v], static_cast<float*>(grads[v]),
+                                    d.leaves[v].size * (cplx ? 2 : 1), accumulate ? 1 : 0, 0});
+    const int n_scatter = (int)tab.size() - n;
+    // pageable source: the copy is staged before the call returns
+    CK(cudaMemcpyAsync(G.copy_dev, tab.data(), sizeof(CopyEntry) * tab.size(), cudaMemcpyHostToDevice,
+                       stream));
+    CK(launch_copy_table(G.copy_dev, n, G.max_leaf_floats, stream));
+    CK(launch_leaf_max(G.img_ptr_dev, G.leaf_nfloat_dev, G.leafmax, n, stream, G.max_leaf_floats));
+    // root adjoint
+    const double* adj_src = adj;
+    if (adj_mem == TN_MEM_HOST) {
+        CK(cudaMemcpyAsync(G.adj_dev, adj, sizeof(double) * p.n_out * (cplx ? 2 : 1), cudaMemcpyHostToDevice,
+                           stream));
+        adj_src = G.adj_dev;
+    }
+    RootAdjArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.adj = adj_src;
+    ra.exp_dev = adj_mem == TN_MEM_HOST ? nullptr : adj_exp2_dev;
+    ra.exp_host = adj_exp2;
+    ra.perm = G.perm_dev;
+    ra.n_out = p.n_out;
+    ra.cplx = cplx ? 1 : 0;
+    ra.dst = reinterpret_cast<float*>(static_cast<char*>(G.ws) + G.adj_off[root_v] * eb);
+    ra.max_slot = G.maxabs + (G.n_slots - 1);
+    ra.exp_slot = G.exps + (G.n_slots - 1);
+    CK(launch_root_adjoint(ra, stream));
+    CK(cudaMemsetAsync(G.gacc, 0, sizeof(float) * G.leaf_floats, stream));
     CK(launch_begin_call(G.ctl, 0, p.d_sliced, nullptr, 0, stream));
-    std::vector<LeafGradArgs> lg(n);
-    for (int v = 0; v < n; ++v) {
-        LeafGradArgs& a = lg[v];
-        memset(&a, 0, sizeof(a));
-        if (!grads[v]) continue;
-        const LeafDesc& lf = d.leaves[v];
-        a.grad = grads[v];
-        a.adj = ws + G.adj_off[v] * eb;
-        a.exp_adj = G.exps + nn + v;
-        a.ctl = G.ctl;
-        a.sl = p.leaf_sl[v];
-        const std::vector<int>& al = G.g.vlab[NV + v];
-        const std::vector<int64_t>& as = G.g.vstride[NV + v];
-        a.n = 1;
-        int nd_ = 0;
-        for (int i = (int)lf.lab.size() - 1; i >= 0; --i) {
-            const int l = lf.lab[i];
-            if (std::find(p.sliced.begin(), p.sliced.end(), l) != p.sliced.end()) continue;
-            if (nd_ >= kMaxDigits) {
-                err = "leaf rank exceeds the gradient gather limit";
-                return TN_EUNSUPPORTED;
-            }
-            a.dim[nd_] = (int32_t)d.dims[l];
-            a.gstride[nd_] = lf.stride[i];
-            int64_t s = 0;
-            for (size_t j = 0; j < al.size(); ++j)
-                if (al[j] == l) s = as[j];
-            a.astride[nd_] = s;
-            a.n *= d.dims[l];
-            ++nd_;
-        }
-        a.n_d = nd_;
+    if (!G.gexec) {
+        if (!G.cap_stream) CK(cudaStreamCreateWithFlags(&G.cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(G.cap_stream, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t e1 = enqueue_grad_slice(G, p.mode, cplx, G.cap_stream);
+        const cudaError_t e2 = cudaStreamEndCapture(G.cap_stream, &G.graph);
+        CK(e1);
+        CK(e2);
+        CK(cudaGraphInstantiate(&G.gexec, G.graph, 0));
     }
-    for (int64_t s = 0; s < p.d_sliced; ++s) {
-        CK(cudaMemsetAsync(G.maxabs, 0, sizeof(unsigned) * (G.n_slots - 1), stream));
-        for (int k : G.fwd_order)
-            CK(launch_node(G.fwd[k], G.gen_f[k], G.tile_f[k], p.mode, cplx, stream));
-        for (size_t j = 0; j < G.bwd.size(); ++j)
-            CK(launch_node(G.bwd[j], G.gen_b[j], G.tile_b[j], p.mode, cplx, stream));
-        for (int v = 0; v < n; ++v)
-            if (grads[v]) CK(launch_leaf_grad(lg[v], cplx, stream));
-        CK(launch_advance(G.ctl, stream));
-    }
+    for (int64_t s = 0; s < p.d_sliced; ++s) CK(cudaGraphLaunch(G.gexec, stream));
+    if (n_scatter > 0) CK(launch_copy_table(G.copy_dev + n, n_scatter, G.max_leaf_floats, stream));
 #undef CK
     return TN_OK;
 }

@@ -242,8 +242,8 @@ struct AccumArgs {
     Control* ctl;
 };
 
-// Reverse sweep: add a leaf's adjoint (times 2^exp) into the caller's
-// gradient buffer at the slice offset; labels absent from the adjoint
+// Reverse sweep: add a leaf's adjoint (times 2^exp) into its gradient
+// accumulator at the slice offset; labels absent from the adjoint
 // (summed in one tensor only) broadcast.  Digits fastest first.
 struct LeafGradArgs {
     void* grad;
@@ -256,6 +256,35 @@ struct LeafGradArgs {
     int64_t astride[kMaxDigits];
     SliceDigits sl;
     const Control* ctl;
+};
+
+// Reverse sweep, per call: copies between the caller's tensors and the
+// library's images of them (the leaves in, the leaf gradients out), one
+// entry per tensor.
+struct CopyEntry {
+    const float* src;
+    float* dst;
+    int64_t nfloat;
+    int32_t add;  // dst += src instead of dst = src
+    int32_t pad;
+};
+
+// Root adjoint of the reverse sweep: FP64 adjoint in the user's open-label
+// order -> float mantissas in the root layout (perm[o] = root offset of
+// output o), renormalised by its largest |component|; the exponent (plus
+// exp_host and, when not NULL, *exp_dev) and the max go to the root's
+// scale slots.
+struct RootAdjArgs {
+    const double* adj;
+    const int64_t* exp_dev;
+    int64_t exp_host;
+    const int64_t* perm;
+    int64_t n_out;
+    int32_t cplx;
+    int32_t pad;
+    float* dst;
+    unsigned* max_slot;
+    int64_t* exp_slot;
 };
 
 // Batched networks: where each network's root lives and where its result goes.
@@ -272,7 +301,12 @@ cudaError_t launch_batch_start(unsigned long long* t_start, cudaStream_t s);
 cudaError_t launch_batch_finish(const BatchRoot* roots, int n, double* out, int64_t* out_exp,
                                 const unsigned long long* t_start, const unsigned long long* t_done,
                                 unsigned long long* latency, cudaStream_t s);
-cudaError_t launch_leaf_grad(const LeafGradArgs& a, bool is_c, cudaStream_t s);
+// Leaf adjoints of the current slice for every entry of the device table
+// (max_n: the largest entry's n).
+cudaError_t launch_leaf_grads(const LeafGradArgs* tab, int n_entries, int64_t max_n, bool is_c,
+                              cudaStream_t s);
+cudaError_t launch_copy_table(const CopyEntry* tab, int n_entries, int64_t max_nfloat, cudaStream_t s);
+cudaError_t launch_root_adjoint(const RootAdjArgs& a, cudaStream_t s);
 cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s);  // tn_tiled.cu
 // Tensor-core node (tn_tc.cu): prec as tc_prec_of_mode.

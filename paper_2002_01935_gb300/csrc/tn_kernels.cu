@@ -300,8 +300,19 @@ cudaError_t launch_leaf_max(const float* const* ptrs, const int64_t* nfloat, uns
     return cudaGetLastError();
 }
 
+// Leaf adjoints of one slice, all leaves in one launch: blockIdx.y picks
+// the table entry, blockIdx.x a chunk of its elements.
 template <bool CPLX>
-__global__ void __launch_bounds__(256) k_leaf_grad(const __grid_constant__ LeafGradArgs a) {
+__global__ void __launch_bounds__(256) k_leaf_grads(const LeafGradArgs* tab, int n_entries) {
+    __shared__ LeafGradArgs a;
+    if ((int)blockIdx.y >= n_entries) return;
+    {
+        const int* src = reinterpret_cast<const int*>(tab + blockIdx.y);
+        int* dst = reinterpret_cast<int*>(&a);
+        for (int i = threadIdx.x; i < (int)(sizeof(LeafGradArgs) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    if ((int64_t)blockIdx.x * blockDim.x >= a.n) return;
     const int64_t slice = a.ctl->slice;
     const int64_t base = slice_offset(a.sl, slice);
     int64_t e = *a.exp_adj;
@@ -329,14 +340,70 @@ __global__ void __launch_bounds__(256) k_leaf_grad(const __grid_constant__ LeafG
     }
 }
 
-cudaError_t launch_leaf_grad(const LeafGradArgs& a, bool is_c, cudaStream_t s) {
-    int64_t blocks = (a.n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    if (blocks < 1) blocks = 1;
+cudaError_t launch_leaf_grads(const LeafGradArgs* tab, int n_entries, int64_t max_n, bool is_c,
+                              cudaStream_t s) {
+    if (n_entries <= 0) return cudaSuccess;
+    int64_t blocks = (max_n + 255) / 256;
+    blocks = blocks < 1 ? 1 : (blocks > 152 * 8 ? 152 * 8 : blocks);
+    const dim3 grid((unsigned)blocks, (unsigned)n_entries);
     if (is_c)
-        k_leaf_grad<true><<<(unsigned)blocks, 256, 0, s>>>(a);
+        k_leaf_grads<true><<<grid, 256, 0, s>>>(tab, n_entries);
     else
-        k_leaf_grad<false><<<(unsigned)blocks, 256, 0, s>>>(a);
+        k_leaf_grads<false><<<grid, 256, 0, s>>>(tab, n_entries);
+    return cudaGetLastError();
+}
+
+// dst = src (or dst += src) for every entry of the table: blockIdx.y picks
+// the entry, blockIdx.x a chunk.
+__global__ void __launch_bounds__(256) k_copy_table(const CopyEntry* tab, int n_entries) {
+    if ((int)blockIdx.y >= n_entries) return;
+    const CopyEntry e = tab[blockIdx.y];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e.nfloat; i += stride)
+        e.dst[i] = e.add ? e.dst[i] + e.src[i] : e.src[i];
+}
+
+cudaError_t launch_copy_table(const CopyEntry* tab, int n_entries, int64_t max_nfloat, cudaStream_t s) {
+    if (n_entries <= 0) return cudaSuccess;
+    int64_t blocks = (max_nfloat + 255) / 256;
+    blocks = blocks < 1 ? 1 : (blocks > 152 * 4 ? 152 * 4 : blocks);
+    k_copy_table<<<dim3((unsigned)blocks, (unsigned)n_entries), 256, 0, s>>>(tab, n_entries);
+    return cudaGetLastError();
+}
+
+// The root adjoint in the form the sweep reads: largest |component| m of
+// the FP64 adjoint, m = f * 2^e with f in [0.5, 1) (frexp), every component
+// scaled by 2^-e (exact) and rounded to float into the root's layout; the
+// root's scale slots get f and e plus the adjoint's own exponent.  One block.
+__global__ void __launch_bounds__(1024) k_root_adjoint(const RootAdjArgs a) {
+    __shared__ double red[32];
+    const int c = a.cplx ? 2 : 1;
+    const int64_t nd = a.n_out * c;
+    double m = 0.0;
+    for (int64_t i = threadIdx.x; i < nd; i += blockDim.x) m = fmax(m, fabs(a.adj[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) red[0] = m;
+    }
+    __syncthreads();
+    m = red[0];
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);
+    for (int64_t i = threadIdx.x; i < nd; i += blockDim.x)
+        a.dst[a.perm[i / c] * c + (i % c)] = (float)ldexp(a.adj[i], -e);
+    if (threadIdx.x == 0) {
+        const float f = m > 0.0 ? (float)ldexp(m, -e) : 0.f;
+        *a.max_slot = __float_as_uint(f);
+        *a.exp_slot = (int64_t)e + a.exp_host + (a.exp_dev ? *a.exp_dev : 0);
+    }
+}
+
+cudaError_t launch_root_adjoint(const RootAdjArgs& a, cudaStream_t s) {
+    k_root_adjoint<<<1, 1024, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -154,8 +154,11 @@ tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count
 tn_status run_instances(NetDesc& d, Plan& p, void* unit, int n_inst, const int64_t* leaf_is,
                         double* out, int64_t* out_exp2, int out_mem, cudaStream_t stream,
                         std::string& err);
-tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int64_t adj_exp2,
-                   void* const* grads, cudaStream_t stream, std::string& err);
+// adj: FP64 adjoint in host (adj_mem TN_MEM_HOST) or device memory; its
+// exponent is adj_exp2 plus, for a device adjoint, *adj_exp2_dev (if set).
+tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_mem, int64_t adj_exp2,
+                   const int64_t* adj_exp2_dev, void* const* grads, bool accumulate, cudaStream_t stream,
+                   std::string& err);
 void plan_info(const NetDesc& d, const Plan& p, double out[8]);
 void free_device(Plan& p);  // releases device state; the host plan stays valid
 void free_grad(Plan& p);

@@ -1,0 +1,233 @@
+"""tn_contract_grad_ex: device adjoints, device exponents, accumulation,
+and the reuse of the captured reverse-sweep graph across calls whose leaf
+and gradient pointers change.  Every result is checked against either the
+FP64 oracle (environments of the leaves) or the host-adjoint call, which the
+oracle tests pin."""
+import numpy as np
+import pytest
+
+from oracle import gradient
+from paper_2002_01935_gb300 import inputs, planner
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    if not _t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_01935_gb300 import build
+    build.build()
+    return _t
+
+
+def _tree(l, d, o):
+    return planner.greedy_tree(l, d, o)
+
+
+def _setup(torch, seed=11, n_open=1, complex_=True, sliced_n=0):
+    from paper_2002_01935_gb300 import binding
+    net = inputs.random_network(7, 12, 900 + seed, n_open=n_open, complex_=complex_)
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    dt = torch.complex64 if complex_ else torch.float32
+    ts = [torch.from_numpy(np.array(t, order="C")).to(dt).cuda() for t in net.tensors]
+    tnw = binding.TensorNetwork(net.labels, net.dims, net.open, ts, complex_=complex_)
+    summed = [l for l in sorted(net.dims) if l not in net.open]
+    return net, pairs, summed[:sliced_n], ts, tnw
+
+
+def _adjoint(net, seed):
+    rng = np.random.default_rng(seed)
+    shape = tuple(net.dims[l] for l in net.open)
+    a = rng.standard_normal(shape)
+    if net.is_complex:
+        a = a + 1j * rng.standard_normal(shape)
+    return a
+
+
+def _oracle(net, adj):
+    ts, ls = list(net.tensors), [list(x) for x in net.labels]
+    ts.append(np.conj(np.asarray(adj)))
+    ls.append(list(net.open))
+    return [np.conj(gradient.environment(ts, ls, net.dims, v, _tree)) for v in range(net.n_tensors)]
+
+
+@pytest.mark.parametrize("sliced_n", [0, 2])
+def test_device_adjoint_matches_host_adjoint(torch, sliced_n):
+    net, pairs, sliced, ts, tnw = _setup(torch, sliced_n=sliced_n)
+    adj = _adjoint(net, 1)
+    g_host = [g.cpu().numpy() for g in tnw.grad(pairs, sliced, "fp32", adj)]
+    adj_dev = torch.from_numpy(np.ascontiguousarray(adj)).cuda()
+    g_dev = tnw.grad(pairs, sliced, "fp32", adj_dev)
+    torch.cuda.synchronize()
+    for a, b in zip(g_host, g_dev):
+        assert np.array_equal(a, b.cpu().numpy())
+    ref = _oracle(net, adj)
+    for v in range(net.n_tensors):
+        assert np.linalg.norm(g_host[v] - ref[v]) <= 1e-5 * (np.linalg.norm(ref[v]) + 1e-30), v
+    tnw.close()
+
+
+def test_device_exponent_scales_exactly(torch):
+    net, pairs, sliced, ts, tnw = _setup(torch, seed=12)
+    adj = _adjoint(net, 2)
+    adj_dev = torch.from_numpy(np.ascontiguousarray(adj)).cuda()
+    base = [g.cpu().numpy() for g in tnw.grad(pairs, sliced, "fp32", adj_dev)]
+    for k in (-7, 5):
+        e = torch.tensor(k, dtype=torch.int64, device="cuda")
+        got = tnw.grad(pairs, sliced, "fp32", adj_dev, adj_exp2=e)
+        torch.cuda.synchronize()
+        for a, b in zip(base, got):
+            assert np.array_equal(np.ldexp(a.real, k) + 1j * np.ldexp(a.imag, k), b.cpu().numpy())
+    tnw.close()
+
+
+def test_accumulate_adds_into_buffers(torch):
+    net, pairs, sliced, ts, tnw = _setup(torch, seed=13, sliced_n=1)
+    adj1, adj2 = _adjoint(net, 3), _adjoint(net, 4)
+    g1 = [g.cpu().numpy() for g in tnw.grad(pairs, sliced, "fp32", adj1)]
+    g2 = [g.cpu().numpy() for g in tnw.grad(pairs, sliced, "fp32", adj2)]
+    acc = [torch.full_like(t, 0.25 + 0.5j) for t in ts]
+    acc[1] = None  # skipped leaf
+    tnw.grad(pairs, sliced, "fp32", adj1, grads=acc, accumulate=True)
+    tnw.grad(pairs, sliced, "fp32", adj2, grads=acc, accumulate=True)
+    torch.cuda.synchronize()
+    for v, a in enumerate(acc):
+        if a is None:
+            continue
+        want = (np.complex64(0.25 + 0.5j) + g1[v]) + g2[v]  # float32 adds, in call order
+        assert np.array_equal(a.cpu().numpy(), want.astype(np.complex64)), v
+    tnw.close()
+
+
+def test_graph_reuse_with_new_pointers(torch):
+    """Second and later calls replay the captured sweep: new leaf tensors
+    (other addresses, other values) and new gradient buffers must give the
+    oracle's gradients for the new values."""
+    net, pairs, sliced, ts, tnw = _setup(torch, seed=14, sliced_n=1)
+    adj = _adjoint(net, 5)
+    tnw.grad(pairs, sliced, "fp32", adj)  # captures
+    rng = np.random.default_rng(6)
+    for rep in range(3):
+        new = [t * np.float32(1.0 + 0.1 * rng.standard_normal()) for t in net.tensors]
+        net2 = net.with_tensors(new)
+        ts2 = [torch.from_numpy(np.array(t, order="C")).to(torch.complex64).cuda() for t in new]
+        tnw.set_tensors(ts2)
+        got = [g.cpu().numpy() for g in tnw.grad(pairs, sliced, "fp32", adj)]
+        ref = _oracle(net2, adj)
+        for v in range(net.n_tensors):
+            assert np.linalg.norm(got[v] - ref[v]) <= 1e-5 * (np.linalg.norm(ref[v]) + 1e-30), (rep, v)
+    tnw.close()
+
+
+def test_bad_arguments_are_refused(torch):
+    from paper_2002_01935_gb300 import binding
+    net, pairs, sliced, ts, tnw = _setup(torch, seed=15)
+    adj = _adjoint(net, 7)
+    e = torch.tensor(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(TypeError):  # device exponent with a host adjoint
+        tnw.grad(pairs, sliced, "fp32", adj, adj_exp2=e)
+    gp = [torch.empty_like(t).data_ptr() for t in ts]
+    adj_np = np.ascontiguousarray(adj)
+    with pytest.raises(binding.TNError):  # same, at the C-ABI
+        binding.tn_contract_grad_ex(tnw.h, pairs, sliced, 0, adj_np.ctypes.data, binding.TN_MEM_HOST, 0,
+                                    e.data_ptr(), gp, 0, 0)
+    with pytest.raises(binding.TNError):  # unknown flag
+        binding.tn_contract_grad_ex(tnw.h, pairs, sliced, 0, adj_np.ctypes.data, binding.TN_MEM_HOST, 0,
+                                    0, gp, 2, 0)
+    tnw.close()
+
+
+def test_refused_under_stream_capture(torch):
+    from paper_2002_01935_gb300 import binding
+    net, pairs, sliced, ts, tnw = _setup(torch, seed=16)
+    adj_dev = torch.from_numpy(np.ascontiguousarray(_adjoint(net, 8))).cuda()
+    tnw.grad(pairs, sliced, "fp32", adj_dev)
+    torch.cuda.synchronize()
+    grads = [torch.empty_like(t) for t in ts]
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(binding.TNError):
+        with torch.cuda.graph(g, stream=s):
+            tnw.grad(pairs, sliced, "fp32", adj_dev, grads=grads, stream=s)
+    tnw.close()
+
+
+def test_accumulated_step_matches_autograd(torch):
+    """The loop the gradient benchmark runs (device adjoint 2 / (B conj(A))
+    from the forward result, accumulation over bitstrings, one torch
+    backward to the fSim parameters) against the autograd Function."""
+    from paper_2002_01935_gb300 import autograd, binding
+    R, C, T = 3, 3, 6
+    circ = inputs.random_circuit(R, C, T, seed=2)
+    bits = inputs.random_bitstrings(R * C, 6, seed=3)
+    fs = circ.fsim_gates()
+    nets = [inputs.circuit_network(circ, b) for b in bits]
+    net0 = nets[0]
+    n = net0.n_tensors
+    first_out = n - R * C
+    pairs = planner.greedy_tree(net0.labels, net0.dims, net0.open)
+    leaf_of = [net0.meta["gate_leaf"][g] for g in fs]
+    base = [torch.from_numpy(np.array(t, order="C")).to(torch.complex64).cuda() for t in net0.tensors]
+    outs = [torch.stack([torch.from_numpy(np.array(nt.tensors[v], order="C")).to(torch.complex64)
+                         for v in range(first_out, n)]).cuda() for nt in nets]
+
+    def params():
+        th = torch.tensor([circ.gates[g].params[0] for g in fs], dtype=torch.float64, device="cuda",
+                          requires_grad=True)
+        ph = torch.tensor([circ.gates[g].params[1] for g in fs], dtype=torch.float64, device="cuda",
+                          requires_grad=True)
+        return th, ph
+
+    def fsim_batch(th, ph):
+        c, s = torch.cos(th).to(torch.complex128), torch.sin(th).to(torch.complex128)
+        g = torch.zeros((th.shape[0], 4, 4), dtype=torch.complex128, device="cuda")
+        g[:, 0, 0] = 1
+        g[:, 1, 1] = c
+        g[:, 2, 2] = c
+        g[:, 1, 2] = -1j * s
+        g[:, 2, 1] = -1j * s
+        g[:, 3, 3] = torch.exp(-1j * ph.to(torch.complex128))
+        return g.to(torch.complex64).reshape(-1, 2, 2, 2, 2)
+
+    # autograd Function
+    th, ph = params()
+    G = fsim_batch(th, ph)
+    tnw = binding.TensorNetwork(net0.labels, net0.dims, net0.open, None, complex_=True)
+    loss = 0.0
+    for x in range(len(bits)):
+        lv = list(base)
+        for i, v in enumerate(leaf_of):
+            lv[v] = G[i]
+        lv = lv[:first_out] + [outs[x][q] for q in range(R * C)]
+        loss = loss + torch.log(torch.abs(autograd.contract(tnw, pairs, [], "fp32", *lv)) ** 2) / len(bits)
+    loss.backward()
+    ref_th, ref_ph = th.grad.cpu().numpy(), ph.grad.cpu().numpy()
+    tnw.close()
+
+    # accumulation through tn_contract_grad_ex
+    th, ph = params()
+    tnw = binding.TensorNetwork(net0.labels, net0.dims, net0.open, None, complex_=True)
+    dG = torch.zeros((len(fs), 2, 2, 2, 2), dtype=torch.complex64, device="cuda")
+    gbuf = [None] * n
+    for i, v in enumerate(leaf_of):
+        gbuf[v] = dG[i]
+    out_buf = torch.empty_like(outs[0])
+    with torch.no_grad():
+        Gd = fsim_batch(th.detach(), ph.detach())
+        lv = list(base)
+        for i, v in enumerate(leaf_of):
+            lv[v] = Gd[i]
+        tnw.set_tensors(lv[:first_out] + [out_buf[q] for q in range(R * C)])
+        for x in range(len(bits)):
+            out_buf.copy_(outs[x])
+            m, e = tnw.contract(pairs, [], "fp32")
+            adj = 2.0 / (len(bits) * torch.conj(m))
+            tnw.grad(pairs, [], "fp32", adj, adj_exp2=torch.neg(e), grads=gbuf, accumulate=True)
+    torch.autograd.backward(fsim_batch(th, ph), dG)
+    got_th, got_ph = th.grad.cpu().numpy(), ph.grad.cpu().numpy()
+    tnw.close()
+    scale = max(np.max(np.abs(ref_th)), np.max(np.abs(ref_ph)))
+    assert np.max(np.abs(got_th - ref_th)) <= 1e-5 * scale
+    assert np.max(np.abs(got_ph - ref_ph)) <= 1e-5 * scale
