@@ -84,7 +84,7 @@ tn_status build_batch(BatchPlan& b, std::string& err) {
                 for (size_t k = 0; k < p.nodes.size(); ++k) {
                     if (b.level[i][k] != L || !b.small[i][k]) continue;
                     const int64_t size = p.nodes[k].size;
-                    const int64_t chunk = std::min<int64_t>(size, 1024);
+                    const int64_t chunk = wave_chunk(p.nodes[k]);
                     for (int64_t o = 0; o < size; o += chunk) {
                         WaveItem it;
                         it.node = b.desc_base[i] + (int)k;

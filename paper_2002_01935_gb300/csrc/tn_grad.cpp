@@ -206,13 +206,12 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
         std::vector<int> singles;
         for (int c : at[L]) {
             const Node& nd = cnode(c);
-            const bool small = nd.kind == kTiled && nd.tile.cfg != kTileDot && nd.size <= (1 << 16) &&
-                               nd.vc <= 20.0 && !f.no_waves;
+            const bool small = wave_node(nd) && !f.no_waves;
             if (!small) {
                 singles.push_back(c);
                 continue;
             }
-            const int64_t chunk = std::min<int64_t>(nd.size, 1024);
+            const int64_t chunk = wave_chunk(nd);
             for (int64_t o = 0; o < nd.size; o += chunk) {
                 WaveItem it;
                 it.node = c;
@@ -261,7 +260,7 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
                 const int pr = producer(v);
                 if (pr >= 0 && in_step[pr]) {
                     const Node& ch = cnode(pr);
-                    const int64_t chunk = std::min<int64_t>(ch.size, 1024);
+                    const int64_t chunk = wave_chunk(ch);
                     G.flow_deps[4 * c + 2 * slot] = pr;
                     G.flow_deps[4 * c + 2 * slot + 1] = (int)((ch.size + chunk - 1) / chunk);
                 }

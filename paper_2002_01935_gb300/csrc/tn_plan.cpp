@@ -478,14 +478,12 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
         for (size_t k = 0; k < p.nodes.size(); ++k) {
             if (level[n + k] != L) continue;
             const Node& nd = p.nodes[k];
-            const TileArgs& t = nd.tile;
-            const bool small = nd.kind == kTiled && t.cfg != kTileDot && nd.size <= (1 << 16) &&
-                               nd.vc <= 20.0 && !p.no_waves;
+            const bool small = wave_node(nd) && !p.no_waves;
             if (!small) {
                 singles.push_back((int)k);
                 continue;
             }
-            const int64_t chunk = std::min<int64_t>(nd.size, 1024);
+            const int64_t chunk = wave_chunk(nd);
             for (int64_t o = 0; o < nd.size; o += chunk) {
                 WaveItem it;
                 it.node = (int)k;
@@ -533,7 +531,7 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
             for (int c : {nd.ca, nd.cb}) {
                 if (c >= n && in_step[c - n]) {
                     const Node& ch = p.nodes[c - n];
-                    const int64_t chunk = std::min<int64_t>(ch.size, 1024);
+                    const int64_t chunk = wave_chunk(ch);
                     p.flow_deps[4 * k + 2 * slot] = c - n;
                     p.flow_deps[4 * k + 2 * slot + 1] = (int)((ch.size + chunk - 1) / chunk);
                 }

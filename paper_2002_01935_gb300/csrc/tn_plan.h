@@ -66,6 +66,24 @@ struct Step {
     std::vector<int> nodes;        // nodes run by this step
 };
 
+// Wave items (k_wave: one CTA of 256 threads per item, every output summed
+// over all 2^nk entries of K by that CTA).  A tiled node joins a wave when
+// it is small: at most 2^16 outputs, 2^20 multiply-adds, 2^14 summed
+// entries per output.  Its items hold at most 2^12 multiply-adds (16 per
+// thread), so that an item's chain of dependent loads does not grow with K
+// -- on the dataflow's critical path every item counts -- and at most 1024
+// outputs.
+inline bool wave_node(const Node& nd) {
+    return nd.kind == kTiled && nd.tile.cfg != kTileDot && nd.size <= (1 << 16) && nd.vc <= 20.0 &&
+           nd.tile.nk <= 14;
+}
+inline int64_t wave_chunk(const Node& nd) {
+    const int sh = nd.tile.nk >= 12 ? 0 : 12 - nd.tile.nk;
+    int64_t c = int64_t(1) << sh;
+    if (c > 1024) c = 1024;
+    return nd.size < c ? nd.size : c;
+}
+
 struct GradState;  // reverse-sweep plan and device state (tn_grad.cpp)
 
 struct Plan {

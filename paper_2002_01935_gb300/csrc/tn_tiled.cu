@@ -592,6 +592,7 @@ __global__ void __launch_bounds__(256)
                 const int64_t offA = sA + scatter_bits(b, d.a_b, d.nb) + scatter_bits(m, d.a_m, d.nm);
                 const int64_t offB = sB + scatter_bits(b, d.b_b, d.nb) + scatter_bits(n, d.b_n, d.nn);
                 T acc = zero<T>();
+#pragma unroll 4
                 for (int64_t t = tid % g; t < K; t += g) {
                     int64_t ka, kb2;
                     if (d.nk < 8) {
