@@ -771,43 +771,26 @@ def run_grad(args, torch, dist, rank, world, local):
     if not args.no_autotune:
         tnw.autotune(pairs, [], mode, reps=3)
 
-    # One gradient step: the fSim leaves from the parameters (torch), then per
-    # bitstring the forward contraction and the reverse sweep, whose leaf
-    # gradients the library adds into one buffer (TN_GRAD_ACCUMULATE), then
-    # one torch backward from those leaf gradients to (theta, phi).  The
-    # adjoint of log|A|^2 / B is 2 / (B conj(A)): it is formed on the device
-    # from the forward result (mantissa m, exponent e: 2 / (B conj(m)) times
-    # 2^-e), so no step waits for the host.  The output-state leaves of the
-    # current bitstring are copied into one fixed buffer.
+    # One gradient step through the batched autograd Function: the fSim
+    # leaves from the parameters (torch), the 64 amplitudes in one launch
+    # sequence (instances), L = mean log|A_x|^2 (torch), and its backward: one
+    # reverse sweep per bitstring with the adjoint on the device, the fSim
+    # leaves' gradients summed over the bitstrings in the library, then torch
+    # from those leaves to (theta, phi).
     nb = len(bits)
     outs_all = torch.stack([torch.stack(o) for o in outs])          # [B, R*C, 2]
-    out_buf = torch.empty_like(outs_all[0])
-    n_fs = len(leaf_of)
-    dG = torch.zeros((n_fs, 2, 2, 2, 2), dtype=torch.complex64, device="cuda")
-    gbuf = [None] * n
-    for i, v in enumerate(leaf_of):
-        gbuf[v] = dG[i]
-    ln2 = math.log(2.0)
+    batch = {first_out + q: outs_all[:, q].contiguous() for q in range(R * C)}
 
     def step():
-        with torch.no_grad():
-            Gd = fsim_batch(torch, theta.detach(), phi.detach())
-            leaves = list(base)
-            for i, v in enumerate(leaf_of):
-                leaves[v] = Gd[i]
-            tnw.set_tensors(leaves[:first_out] + [out_buf[q] for q in range(R * C)])
-            dG.zero_()
-            loss = torch.zeros((), dtype=torch.float64, device="cuda")
-            for x in range(nb):
-                out_buf.copy_(outs_all[x])
-                m, e = tnw.contract(pairs, [], mode)
-                adj = 2.0 / (nb * torch.conj(m))
-                tnw.grad(pairs, [], mode, adj, adj_exp2=torch.neg(e), grads=gbuf, accumulate=True)
-                loss += (torch.log(torch.abs(m) ** 2) + (2.0 * ln2) * e.double()) / nb
         theta.grad = None
         phi.grad = None
         G = fsim_batch(torch, theta, phi)
-        torch.autograd.backward(G, dG)
+        leaves = list(base)
+        for i, v in enumerate(leaf_of):
+            leaves[v] = G[i]
+        vals = autograd.contract_batch(tnw, pairs, mode, leaves[:first_out] + [None] * (R * C), batch)
+        loss = torch.mean(torch.log(torch.abs(vals) ** 2))
+        loss.backward()
         return loss
 
     for _ in range(args.warmup):

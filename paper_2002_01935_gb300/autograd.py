@@ -7,6 +7,14 @@ backward calls tn_contract_grad: every leaf's gradient is computed by the
 hand-written reverse tree sweep on the GPU (per-slice recomputation of the
 forward intermediates), with the holomorphic convention of torch:
 grad_leaf = conj(d value / d leaf) * grad_output.
+
+``contract_batch(tnw, pairs, mode, leaves, batch)`` is the same for B
+scalar networks that share the tree and every leaf except those in
+``batch`` (e.g. the output-state leaves of B bitstrings of one circuit,
+Eq. trans-amp): the forward runs the B copies in one launch sequence
+(tn_contract_instances), the backward runs one reverse sweep per network
+with its adjoint on the device and adds the shared leaves' gradients over
+the batch in the library (TN_GRAD_ACCUMULATE).
 """
 from __future__ import annotations
 
@@ -43,3 +51,70 @@ class _Contract(torch.autograd.Function):
 
 def contract(tnw: "binding.TensorNetwork", pairs, sliced, mode, *leaves) -> torch.Tensor:
     return _Contract.apply(tnw, pairs, list(sliced), mode, *leaves)
+
+
+class _ContractBatch(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, tnw, pairs, mode, batch_ids, n_batch, *tensors):
+        n = len(tensors) - len(batch_ids)
+        shared = [t.detach().contiguous() for t in tensors[:n]]
+        stacks = [t.detach().contiguous() for t in tensors[n:]]
+        leaves = list(shared)
+        strides = [0] * n
+        for v, st in zip(batch_ids, stacks):
+            if st.shape[0] != n_batch:
+                raise ValueError(f"batch leaf {v}: leading dimension {st.shape[0]}, expected {n_batch}")
+            leaves[v] = st
+            strides[v] = st[0].numel()
+        tnw.set_tensors(leaves)
+        mant, ex = tnw.contract_instances(pairs, mode, n_batch, strides)
+        value = mant * torch.pow(torch.tensor(2.0, dtype=torch.float64, device=mant.device),
+                                 ex.double()).unsqueeze(1)
+        if tnw.dtype == binding.TN_C64:
+            value = torch.complex(value[:, 0], value[:, 1])
+        else:
+            value = value[:, 0].contiguous()
+        ctx.tnw, ctx.pairs, ctx.mode, ctx.batch_ids = tnw, pairs, mode, list(batch_ids)
+        ctx.save_for_backward(*shared, *stacks)
+        return value
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        tnw = ctx.tnw
+        saved = ctx.saved_tensors
+        nb = len(ctx.batch_ids)
+        n = len(saved) - nb
+        shared, stacks = list(saved[:n]), list(saved[n:])
+        need = ctx.needs_input_grad[5:]
+        cplx = tnw.dtype == binding.TN_C64
+        adj = grad_out.detach().to(device=shared[0].device,
+                                   dtype=torch.complex128 if cplx else torch.float64).contiguous()
+        # shared leaves: one buffer each, summed over the batch; batch
+        # leaves: a slot per network (zero, then added once)
+        g_shared = [torch.zeros_like(t) if nd else None for t, nd in zip(shared, need[:n])]
+        g_stack = [torch.zeros_like(st) if nd else None for st, nd in zip(stacks, need[n:])]
+        n_batch = adj.shape[0]
+        for b in range(n_batch):
+            leaves = list(shared)
+            grads = list(g_shared)
+            for j, v in enumerate(ctx.batch_ids):
+                leaves[v] = stacks[j][b]
+                grads[v] = g_stack[j][b] if g_stack[j] is not None else None
+            tnw.set_tensors(leaves)
+            tnw.grad(ctx.pairs, [], ctx.mode, adj[b:b + 1], grads=grads, accumulate=True)
+        return (None, None, None, None, None, *g_shared, *g_stack)
+
+
+def contract_batch(tnw: "binding.TensorNetwork", pairs, mode, leaves, batch) -> torch.Tensor:
+    """Values of B scalar networks sharing a tree: ``leaves`` gives every
+    leaf (those replaced per network may be None), ``batch`` maps leaf
+    index -> tensor [B, *leaf shape].  Returns a [B] complex128 / float64
+    tensor, differentiable in every leaf tensor (unsliced trees)."""
+    ids = sorted(batch)
+    stacks = [batch[v] for v in ids]
+    if not stacks:
+        raise ValueError("contract_batch needs at least one batch leaf")
+    n_batch = stacks[0].shape[0]
+    # placeholders for the batch positions (never read: detached, no gradient)
+    shared = [l if l is not None else batch[v][0].detach() for v, l in enumerate(leaves)]
+    return _ContractBatch.apply(tnw, pairs, mode, ids, n_batch, *shared, *stacks)

@@ -68,13 +68,15 @@ struct Step {
 
 // Wave items (k_wave: one CTA of 256 threads per item, every output summed
 // over all 2^nk entries of K by that CTA).  A tiled node joins a wave when
-// it is small: at most 2^16 outputs, 2^20 multiply-adds, 2^14 summed
-// entries per output.  Its items hold at most 2^12 multiply-adds (16 per
+// it is small: at most 2^16 outputs, 2^22 multiply-adds (1024 items), 2^14
+// summed entries per output.  Narrow mid-size nodes (a few thousand outputs,
+// 2^21..2^22 multiply-adds) fill the GPU better as items than as a tiled
+// launch, whose tiles they cover only in part.  Its items hold at most 2^12 multiply-adds (16 per
 // thread), so that an item's chain of dependent loads does not grow with K
 // -- on the dataflow's critical path every item counts -- and at most 1024
 // outputs.
 inline bool wave_node(const Node& nd) {
-    return nd.kind == kTiled && nd.tile.cfg != kTileDot && nd.size <= (1 << 16) && nd.vc <= 20.0 &&
+    return nd.kind == kTiled && nd.tile.cfg != kTileDot && nd.size <= (1 << 16) && nd.vc <= 22.0 &&
            nd.tile.nk <= 14;
 }
 inline int64_t wave_chunk(const Node& nd) {

@@ -155,9 +155,10 @@ def test_refused_under_stream_capture(torch):
 
 
 def test_accumulated_step_matches_autograd(torch):
-    """The loop the gradient benchmark runs (device adjoint 2 / (B conj(A))
-    from the forward result, accumulation over bitstrings, one torch
-    backward to the fSim parameters) against the autograd Function."""
+    """A loop over bitstrings at the C-ABI level (device adjoint 2 / (B
+    conj(A)) formed from each forward result, accumulation over the
+    bitstrings, one torch backward to the fSim parameters) against the
+    autograd Function."""
     from paper_2002_01935_gb300 import autograd, binding
     R, C, T = 3, 3, 6
     circ = inputs.random_circuit(R, C, T, seed=2)
@@ -231,3 +232,52 @@ def test_accumulated_step_matches_autograd(torch):
     scale = max(np.max(np.abs(ref_th)), np.max(np.abs(ref_ph)))
     assert np.max(np.abs(got_th - ref_th)) <= 1e-5 * scale
     assert np.max(np.abs(got_ph - ref_ph)) <= 1e-5 * scale
+
+
+def test_contract_batch_matches_per_network_function(torch):
+    """contract_batch (instances forward, per-network sweeps with summed
+    shared-leaf gradients) against autograd.contract called per network:
+    values, fSim-leaf gradients and output-leaf gradients."""
+    from paper_2002_01935_gb300 import autograd, binding
+    R, C, T = 3, 3, 6
+    circ = inputs.random_circuit(R, C, T, seed=7)
+    bits = inputs.random_bitstrings(R * C, 5, seed=8)
+    nets = [inputs.circuit_network(circ, b) for b in bits]
+    net0 = nets[0]
+    n = net0.n_tensors
+    first_out = n - R * C
+    pairs = planner.greedy_tree(net0.labels, net0.dims, net0.open)
+
+    def leaves_of(req):
+        base = [torch.from_numpy(np.array(t, order="C")).to(torch.complex64).cuda() for t in net0.tensors]
+        for v in (0, 5, first_out - 1):
+            base[v].requires_grad_(req)
+        outs = torch.stack([torch.stack([torch.from_numpy(np.array(nt.tensors[v], order="C")).to(torch.complex64)
+                                         for v in range(first_out, n)]) for nt in nets]).cuda()
+        outs.requires_grad_(req)
+        return base, outs
+
+    base, outs = leaves_of(True)
+    tnw = binding.TensorNetwork(net0.labels, net0.dims, net0.open, None, complex_=True)
+    vals = []
+    for x in range(len(bits)):
+        lv = base[:first_out] + [outs[x, q] for q in range(R * C)]
+        vals.append(autograd.contract(tnw, pairs, [], "fp32", *lv))
+    ref_v = torch.stack(vals)
+    loss = torch.sum(torch.log(torch.abs(ref_v) ** 2))
+    loss.backward()
+    ref = [base[v].grad.cpu().numpy() for v in (0, 5, first_out - 1)] + [outs.grad.cpu().numpy()]
+    tnw.close()
+
+    base, outs = leaves_of(True)
+    tnw = binding.TensorNetwork(net0.labels, net0.dims, net0.open, None, complex_=True)
+    batch = {first_out + q: outs[:, q] for q in range(R * C)}
+    got_v = autograd.contract_batch(tnw, pairs, "fp32", base[:first_out] + [None] * (R * C), batch)
+    loss = torch.sum(torch.log(torch.abs(got_v) ** 2))
+    loss.backward()
+    got = [base[v].grad.cpu().numpy() for v in (0, 5, first_out - 1)] + [outs.grad.cpu().numpy()]
+    tnw.close()
+    rv, gv = ref_v.detach().cpu().numpy(), got_v.detach().cpu().numpy()
+    assert np.max(np.abs(gv - rv)) <= 1e-5 * np.max(np.abs(rv))
+    for a, b in zip(got, ref):
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
