@@ -352,6 +352,40 @@ def roofline(steps, dom, dom_ms, nodes, mode, ms_per_step, peaks):
     return roof
 
 
+def tree_roofline(steps, nodes, mode, ms_per_step, slices_per_step, peaks, step_ms):
+    """Per-tree roofline: the sum over nodes of max(executed FLOPs / pipe
+    peak, algorithmic bytes / HBM bandwidth) -- the pipe being the tensor
+    cores for tensor-core nodes, FP32 SIMT for the rest -- over the measured
+    time; nodes whose bound is under 2 us are latency-bound, and the steps
+    that hold only such nodes are reported with their share of the time."""
+    t_roof = 0.0
+    tiny, tiny_steps_ms = 0, 0.0
+    for k, st in enumerate(steps):
+        all_tiny = True
+        for j in st["nodes"]:
+            nd = nodes[j]
+            t_hbm = nd["bytes"] / (peaks["hbm_gbs"] * 1e9)
+            if st["kind"] == 2:
+                tc = peaks["bf16_tflops"] * (1.0 if mode == "bf16_split" else TF32_OVER_BF16)
+                t_alu = nd["flops"] * MODE_PASSES.get(mode, 1) / (tc * 1e12)
+            else:
+                t_alu = nd["flops"] / (FP32_SIMT_TFLOPS * 1e12)
+            t = max(t_hbm, t_alu)
+            t_roof += t
+            if t < 2e-6:
+                tiny += 1
+            else:
+                all_tiny = False
+        if all_tiny and k < len(step_ms):
+            tiny_steps_ms += step_ms[k]
+    t_ms = t_roof * slices_per_step * 1e3
+    return {"t_roof_ms": t_ms, "measured_ms": ms_per_step, "frac": t_ms / ms_per_step,
+            "peaks": "measured HBM and bf16 (TF32 = bf16 x 1.1/2.25), derived FP32 SIMT",
+            "latency_bound_nodes": tiny, "nodes": sum(len(s["nodes"]) for s in steps),
+            "latency_bound_step_ms": tiny_steps_ms * slices_per_step,
+            "latency_bound_time_frac": tiny_steps_ms * slices_per_step / ms_per_step}
+
+
 def device_events(torch, stream, n):
     # torch creates the CUDA event lazily: record once so .cuda_event is valid
     evl = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
@@ -541,6 +575,7 @@ def run_network(args, torch, dist, rank, world, local):
         "s_per_network": ms_per_step / 1e3 * (info.d_sliced / sc),
         "rel_err_vs_oracle": rel_err,
         "roofline": roof,
+        "tree_roofline": tree_roofline(steps, nodes, mode, ms_per_step, sc, peaks, step_ms),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_call * args.steps,

@@ -245,6 +245,39 @@ tn_status tn_contract_grad_ex(tn_net *net, const int32_t *tree_pairs, int32_t n_
                               void *const *leaf_grads, uint32_t flags, void *stream);
 
 /*
+ * tn_contract_grad_instances -- the reverse sweep of n_inst copies of the
+ * network in one launch sequence, the gradient counterpart of
+ * tn_contract_instances (e.g. the bitstrings of one circuit: their networks
+ * differ only in the output-state leaves).  Copy i reads leaf v at the
+ * attached pointer plus i * leaf_inst_stride[v] elements (0, or NULL for
+ * all: shared by every copy; otherwise at least the leaf's size).  Every
+ * node launch covers all copies (each copy has its own workspace, packing
+ * buffer and scale slots); slicing is allowed (every copy runs every
+ * slice).
+ *   out_adjoint   n_inst adjoints, each shaped like tn_contract's out (FP64,
+ *                 complex (re, im) pairs), copy after copy; host or device
+ *                 memory as adj_mem.
+ *   adj_exp2      exponent added to every copy's adjoint.
+ *   adj_exp2_dev  NULL, or (device adjoints only) n_inst device int64s,
+ *                 copy i's adjoint exponent is adj_exp2 + adj_exp2_dev[i].
+ *   leaf_grads    n_tensors device pointers (NULL: skipped): for a shared
+ *                 leaf the sum over the copies of their gradients (added in
+ *                 copy order); for a varying leaf copy i's gradient at
+ *                 + i * leaf_inst_stride[v] elements.
+ *   flags         0 or TN_GRAD_ACCUMULATE.
+ * The device state grows to n_inst copies of the sweep's workspace; a
+ * different (n_inst, shared/varying pattern) rebuilds it (and synchronises
+ * the stream).  Errors: as tn_contract_grad_ex; TN_EINVAL for n_inst < 1
+ * or overlapping copies; TN_EUNSUPPORTED when a node's launch grid would
+ * exceed the CUDA limit for this many copies.
+ */
+tn_status tn_contract_grad_instances(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
+                                     const int64_t *sliced_labels, tn_mode mode, int32_t n_inst,
+                                     const int64_t *leaf_inst_stride, const double *out_adjoint,
+                                     int32_t adj_mem, int64_t adj_exp2, const int64_t *adj_exp2_dev,
+                                     void *const *leaf_grads, uint32_t flags, void *stream);
+
+/*
  * tn_contract_noalloc -- tn_contract for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a deployment variant.
  * tn_contract obtains its workspace with cudaMalloc on the first run of a

@@ -12,9 +12,10 @@ grad_leaf = conj(d value / d leaf) * grad_output.
 scalar networks that share the tree and every leaf except those in
 ``batch`` (e.g. the output-state leaves of B bitstrings of one circuit,
 Eq. trans-amp): the forward runs the B copies in one launch sequence
-(tn_contract_instances), the backward runs one reverse sweep per network
-with its adjoint on the device and adds the shared leaves' gradients over
-the batch in the library (TN_GRAD_ACCUMULATE).
+(tn_contract_instances), the backward runs the reverse sweeps of all B
+networks in one launch sequence (tn_contract_grad_instances) with the
+adjoints on the device; the shared leaves' gradients are summed over the
+batch in the library.
 """
 from __future__ import annotations
 
@@ -89,19 +90,20 @@ class _ContractBatch(torch.autograd.Function):
         cplx = tnw.dtype == binding.TN_C64
         adj = grad_out.detach().to(device=shared[0].device,
                                    dtype=torch.complex128 if cplx else torch.float64).contiguous()
-        # shared leaves: one buffer each, summed over the batch; batch
-        # leaves: a slot per network (zero, then added once)
-        g_shared = [torch.zeros_like(t) if nd else None for t, nd in zip(shared, need[:n])]
-        g_stack = [torch.zeros_like(st) if nd else None for st, nd in zip(stacks, need[n:])]
+        # one reverse sweep over all networks: shared leaves' gradients
+        # summed over the batch, batch leaves' per network
+        g_shared = [torch.empty_like(t) if nd else None for t, nd in zip(shared, need[:n])]
+        g_stack = [torch.empty_like(st) if nd else None for st, nd in zip(stacks, need[n:])]
         n_batch = adj.shape[0]
-        for b in range(n_batch):
-            leaves = list(shared)
-            grads = list(g_shared)
-            for j, v in enumerate(ctx.batch_ids):
-                leaves[v] = stacks[j][b]
-                grads[v] = g_stack[j][b] if g_stack[j] is not None else None
-            tnw.set_tensors(leaves)
-            tnw.grad(ctx.pairs, [], ctx.mode, adj[b:b + 1], grads=grads, accumulate=True)
+        leaves = list(shared)
+        grads = list(g_shared)
+        strides = [0] * n
+        for j, v in enumerate(ctx.batch_ids):
+            leaves[v] = stacks[j]
+            grads[v] = g_stack[j]
+            strides[v] = stacks[j][0].numel()
+        tnw.set_tensors(leaves)
+        tnw.grad_instances(ctx.pairs, [], ctx.mode, n_batch, strides, adj, grads=grads)
         return (None, None, None, None, None, *g_shared, *g_stack)
 
 

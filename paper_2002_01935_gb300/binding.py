@@ -63,6 +63,10 @@ _lib.tn_contract_grad.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_in
 _lib.tn_contract_grad_ex.restype = ctypes.c_int
 _lib.tn_contract_grad_ex.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int, _vp, ctypes.c_int32,
                                      ctypes.c_int64, _vp, ctypes.POINTER(_vp), ctypes.c_uint32, _vp]
+_lib.tn_contract_grad_instances.restype = ctypes.c_int
+_lib.tn_contract_grad_instances.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int, ctypes.c_int32,
+                                            _i64p, _vp, ctypes.c_int32, ctypes.c_int64, _vp,
+                                            ctypes.POINTER(_vp), ctypes.c_uint32, _vp]
 _lib.tn_contract_noalloc.restype = ctypes.c_int
 _lib.tn_contract_noalloc.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, _vp, ctypes.c_int32, _i64p,
                                      _vp]
@@ -90,7 +94,7 @@ _lib.tn_version.restype = ctypes.c_char_p
 _lib.tn_version.argtypes = []
 
 EXPORTS = ["tn_create", "tn_set_tensor", "tn_contract", "tn_contract_ex", "tn_contract_grad",
-           "tn_contract_grad_ex",
+           "tn_contract_grad_ex", "tn_contract_grad_instances",
            "tn_contract_noalloc", "tn_contract_instances", "tn_autotune", "tn_plan_info", "tn_plan_steps",
            "tn_batch_create",
            "tn_batch_contract", "tn_batch_destroy", "tn_destroy", "tn_last_error", "tn_version"]
@@ -198,6 +202,21 @@ def tn_contract_grad_ex(h: int, pairs, sliced, mode: int, adj_ptr: int, adj_mem:
     _check(_lib.tn_contract_grad_ex(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
                                     adj_ptr, adj_mem, int(adj_exp2), adj_exp2_dev or None, gp, flags,
                                     stream))
+
+
+def tn_contract_grad_instances(h: int, pairs, sliced, mode: int, n_inst: int, leaf_inst_stride,
+                               adj_ptr: int, adj_mem: int, adj_exp2: int, adj_exp2_dev: int,
+                               grad_ptrs: Sequence[int], flags: int = 0, stream: int = 0) -> None:
+    """Reverse sweep of n_inst copies (leaf v of copy i at + i *
+    leaf_inst_stride[v] elements; None: all shared) in one launch sequence."""
+    tr = _tree(pairs)
+    sl = _arr(list(sliced) or [0], np.int64)
+    st = _arr(list(leaf_inst_stride), np.int64) if leaf_inst_stride is not None else None
+    gp = (_vp * len(grad_ptrs))(*[g or None for g in grad_ptrs])
+    _check(_lib.tn_contract_grad_instances(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64),
+                                           mode, n_inst, _p(st, ctypes.c_int64) if st is not None else None,
+                                           adj_ptr, adj_mem, int(adj_exp2), adj_exp2_dev or None, gp, flags,
+                                           stream))
 
 
 def tn_contract_noalloc(h: int, pairs, sliced, out_ptr: int, out_mem: int, exp_ptr: int,
@@ -378,6 +397,51 @@ class TensorNetwork:
         tn_contract_grad_ex(self.h, pairs, sliced, m, adj_ptr, adj_mem, exp_host, exp_dev,
                             [g.data_ptr() if g is not None else 0 for g in grads],
                             TN_GRAD_ACCUMULATE if accumulate else 0, s)
+        del keep
+        return grads
+
+    def grad_instances(self, pairs, sliced, mode, n_inst, leaf_inst_stride, adjoint, adj_exp2=0,
+                       grads=None, stream=None, accumulate=False):
+        """Reverse sweep of n_inst copies in one launch sequence (see
+        tn_contract_grad_instances).  ``adjoint``: [n_inst, *output shape]
+        FP64 (complex128 for complex networks), host array or CUDA tensor;
+        ``adj_exp2``: int, or a CUDA int64 tensor of n_inst exponents (CUDA
+        adjoint only).  ``grads``: per leaf a tensor shaped like the leaf
+        (shared leaves: summed over the copies) or like the stacked copies
+        (varying leaves), or None to skip.  Returns ``grads``."""
+        import torch
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        cplx = self.dtype == TN_C64
+        n_out = int(np.prod(self.out_shape))
+        if isinstance(adjoint, torch.Tensor) and adjoint.is_cuda:
+            want = torch.complex128 if cplx else torch.float64
+            if adjoint.dtype != want:
+                raise TypeError(f"adjoint dtype {adjoint.dtype}, expected {want}")
+            if adjoint.numel() != n_out * n_inst:
+                raise ValueError("adjoint must hold n_inst outputs")
+            keep = adjoint.contiguous()
+            adj_ptr, adj_mem = keep.data_ptr(), TN_MEM_DEVICE
+        else:
+            if isinstance(adjoint, torch.Tensor):
+                adjoint = adjoint.detach().numpy()
+            keep = np.ascontiguousarray(np.asarray(adjoint, dtype=np.complex128 if cplx else np.float64))
+            if keep.size != n_out * n_inst:
+                raise ValueError("adjoint must hold n_inst outputs")
+            adj_ptr, adj_mem = keep.ctypes.data, TN_MEM_HOST
+        exp_host, exp_dev = 0, 0
+        if isinstance(adj_exp2, torch.Tensor):
+            if adj_mem != TN_MEM_DEVICE or not adj_exp2.is_cuda or adj_exp2.dtype != torch.int64 \
+                    or adj_exp2.numel() != n_inst:
+                raise TypeError("a tensor adj_exp2 must hold n_inst CUDA int64s, with a CUDA adjoint")
+            exp_dev = adj_exp2.contiguous().data_ptr()
+        else:
+            exp_host = int(adj_exp2)
+        if grads is None:  # attached tensors: stacked copies for varying leaves
+            grads = [torch.empty_like(t, device="cuda") for t in self._keep]
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        tn_contract_grad_instances(self.h, pairs, sliced, m, n_inst, leaf_inst_stride, adj_ptr, adj_mem,
+                                   exp_host, exp_dev, [g.data_ptr() if g is not None else 0 for g in grads],
+                                   TN_GRAD_ACCUMULATE if accumulate else 0, s)
         del keep
         return grads
 

@@ -288,7 +288,34 @@ tn_status tn_contract_grad_ex(tn_net* net, const int32_t* tree_pairs, int32_t n_
     if (st != TN_OK) return st;
     std::string err;
     st = tn::run_grad(net->d, *p, net->unit, out_adjoint, adj_mem, adj_exp2, adj_exp2_dev, leaf_grads,
-                      (flags & TN_GRAD_ACCUMULATE) != 0, (cudaStream_t)stream, err);
+                      (flags & TN_GRAD_ACCUMULATE) != 0, 1, nullptr, (cudaStream_t)stream, err);
+    if (st != TN_OK) return fail(st, err);
+    return TN_OK;
+}
+
+tn_status tn_contract_grad_instances(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
+                                     const int64_t* sliced_labels, tn_mode mode, int32_t n_inst,
+                                     const int64_t* leaf_inst_stride, const double* out_adjoint,
+                                     int32_t adj_mem, int64_t adj_exp2, const int64_t* adj_exp2_dev,
+                                     void* const* leaf_grads, uint32_t flags, void* stream) {
+    if (!net) return fail(TN_EINVAL, "tn_contract_grad_instances: net is NULL");
+    if (!out_adjoint || !leaf_grads) return fail(TN_EINVAL, "tn_contract_grad_instances: NULL argument");
+    if (n_inst < 1) return fail(TN_EINVAL, "tn_contract_grad_instances: n_inst < 1");
+    if (adj_mem != TN_MEM_DEVICE && adj_mem != TN_MEM_HOST) return fail(TN_EINVAL, "bad adj_mem");
+    if (adj_exp2_dev && adj_mem != TN_MEM_DEVICE)
+        return fail(TN_EINVAL, "tn_contract_grad_instances: adj_exp2_dev needs a device adjoint");
+    if (flags & ~(uint32_t)TN_GRAD_ACCUMULATE)
+        return fail(TN_EINVAL, "tn_contract_grad_instances: unknown flags");
+    for (int v = 0; v < net->d.n; ++v)
+        if (!net->d.leaves[v].ptr) return fail(TN_EINVAL, "tn_contract_grad_instances: tensor without data");
+    Plan* p = nullptr;
+    tn_status st = get_plan(net, tree_pairs, n_sliced, sliced_labels, mode, &p);
+    if (st != TN_OK) return st;
+    st = ensure_device(net, p);
+    if (st != TN_OK) return st;
+    std::string err;
+    st = tn::run_grad(net->d, *p, net->unit, out_adjoint, adj_mem, adj_exp2, adj_exp2_dev, leaf_grads,
+                      (flags & TN_GRAD_ACCUMULATE) != 0, n_inst, leaf_inst_stride, (cudaStream_t)stream, err);
     if (st != TN_OK) return fail(st, err);
     return TN_OK;
 }

@@ -51,12 +51,21 @@ struct GradState {
     std::vector<WaveItem> items;
     std::vector<int> flow_deps;  // per combined node: child a, chunks, child b, chunks
     bool any_flow = false;
-    // leaf images (floats): leaf v at leaf_off[v] in both the leaf copy and
-    // the gradient accumulator
-    std::vector<int64_t> leaf_off;
-    int64_t leaf_floats = 0;
+    // gradient accumulators (floats): leaf v at acc_off[v], one such block
+    // of acc_floats per instance
+    std::vector<int64_t> acc_off;
+    int64_t acc_floats = 0;
     int64_t max_leaf_floats = 0;
     int64_t max_grad_n = 0;
+    // instance layout of the device state (n_inst = 0: not allocated).
+    // Leaves either are shared by all instances or have one copy each
+    // (varying); the leaf image holds leaf v at img_off[v], its instance
+    // copies img_is[v] floats apart (0: shared).
+    int n_inst = 0;
+    std::vector<char> varying;
+    std::vector<int64_t> img_off, img_is;
+    int64_t img_floats = 0;
+    std::vector<int> inst_item_begin;  // per step: first item of the instance-replicated list
     // device
     void* ws = nullptr;
     void* split_buf = nullptr;
@@ -268,27 +277,35 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
             }
         }
     }
-    // ---- leaf images
-    G.leaf_off.assign(n, 0);
-    G.leaf_floats = 0;
+    // ---- gradient accumulator layout
+    G.acc_off.assign(n, 0);
+    G.acc_floats = 0;
     G.max_leaf_floats = 0;
     for (int v = 0; v < n; ++v) {
         const int64_t nf = d.leaves[v].size * (d.is_complex() ? 2 : 1);
-        G.leaf_off[v] = G.leaf_floats;
-        G.leaf_floats += (nf + 63) / 64 * 64;  // 256-byte aligned leaves
+        G.acc_off[v] = G.acc_floats;
+        G.acc_floats += (nf + 63) / 64 * 64;  // 256-byte aligned leaves
         G.max_leaf_floats = std::max(G.max_leaf_floats, nf);
     }
     (void)err;
     return TN_OK;
 }
 
-static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void* unit, std::string& err) {
+// Device state of the sweep for n_inst instances whose leaves are shared or
+// varying (one copy per instance).  Everything holds one region per
+// instance: workspace, packed-operand / split buffer, scale slots, gradient
+// accumulators, dataflow counters; the node arguments carry the instance
+// strides (InstanceInfo) and wave items are replicated per instance.
+static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void* unit, int n_inst,
+                            const std::vector<char>& varying, std::string& err) {
     const size_t eb = d.elem_bytes();
     const int n = d.n;
     const int nn = (int)G.fwd.size();
     const int nb = (int)G.bwd.size();
     const int NV = G.NV;
     const bool cplx = d.is_complex();
+    const int cf = cplx ? 2 : 1;
+    const int64_t NI = n_inst;
     auto ck = [&](cudaError_t e, const char* what) {
         if (e != cudaSuccess) {
             err = std::string(what) + ": " + cudaGetErrorString(e);
@@ -301,31 +318,47 @@ static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void*
 #define UP(dst, src, bytes) \
     if (!ck(cudaMemcpy((void*)(dst), (const void*)(src), (size_t)(bytes), cudaMemcpyHostToDevice), "cudaMemcpy")) \
         return TN_ECUDA
-    AL(G.ws, (size_t)G.ws_elems * eb, "gradient workspace");
-    if (G.split_bytes) AL(G.split_buf, G.split_bytes, "cudaMalloc");
-    AL(G.maxabs, sizeof(unsigned) * G.n_slots, "cudaMalloc");
-    AL(G.exps, sizeof(int64_t) * G.n_slots, "cudaMalloc");
+    G.n_inst = n_inst;
+    G.varying = varying;
+    // leaf image layout
+    G.img_off.assign(n, 0);
+    G.img_is.assign(n, 0);
+    G.img_floats = 0;
+    for (int v = 0; v < n; ++v) {
+        const int64_t pad = (d.leaves[v].size * cf + 63) / 64 * 64;
+        G.img_off[v] = G.img_floats;
+        G.img_is[v] = varying[v] ? pad : 0;
+        G.img_floats += varying[v] ? pad * NI : pad;
+    }
+    AL(G.ws, (size_t)G.ws_elems * eb * NI, "gradient workspace");
+    if (G.split_bytes) AL(G.split_buf, G.split_bytes * NI, "cudaMalloc");
+    AL(G.maxabs, sizeof(unsigned) * G.n_slots * NI, "cudaMalloc");
+    AL(G.exps, sizeof(int64_t) * G.n_slots * NI, "cudaMalloc");
     AL(G.ctl, sizeof(Control), "cudaMalloc");
     AL(G.leafmax, sizeof(unsigned) * n, "cudaMalloc");
-    AL(G.leaf_img, sizeof(float) * std::max<int64_t>(G.leaf_floats, 64), "leaf image");
-    AL(G.gacc, sizeof(float) * std::max<int64_t>(G.leaf_floats, 64), "gradient accumulators");
+    AL(G.leaf_img, sizeof(float) * std::max<int64_t>(G.img_floats, 64), "leaf image");
+    AL(G.gacc, sizeof(float) * std::max<int64_t>(G.acc_floats * NI, 64), "gradient accumulators");
     AL(G.img_ptr_dev, sizeof(void*) * n, "cudaMalloc");
     AL(G.leaf_nfloat_dev, sizeof(int64_t) * n, "cudaMalloc");
     AL(G.lg_dev, sizeof(LeafGradArgs) * n, "cudaMalloc");
-    AL(G.copy_dev, sizeof(CopyEntry) * 2 * n, "cudaMalloc");
+    AL(G.copy_dev, sizeof(CopyEntry) * 2 * n * NI, "cudaMalloc");
     const int64_t n_out = f.n_out;
-    AL(G.adj_dev, sizeof(double) * n_out * (cplx ? 2 : 1), "cudaMalloc");
+    AL(G.adj_dev, sizeof(double) * n_out * cf * NI, "cudaMalloc");
     AL(G.perm_dev, sizeof(int64_t) * n_out, "cudaMalloc");
     const int ncomb = nn + nb;
     AL(G.flow_deps_dev, sizeof(int) * G.flow_deps.size(), "cudaMalloc");
-    AL(G.flow_cnt_dev, sizeof(unsigned) * ((size_t)ncomb + G.steps.size() + 1), "cudaMalloc");
+    AL(G.flow_cnt_dev, sizeof(unsigned) * ((size_t)ncomb * NI + G.steps.size() + 1), "cudaMalloc");
     UP(G.flow_deps_dev, G.flow_deps.data(), sizeof(int) * G.flow_deps.size());
+    // the padding between image entries stays zero (leaf maxima read it)
+    if (!ck(cudaMemset(G.leaf_img, 0, sizeof(float) * std::max<int64_t>(G.img_floats, 64)), "cudaMemset"))
+        return TN_ECUDA;
     {
         std::vector<const float*> ip(n);
         std::vector<int64_t> nf(n);
         for (int v = 0; v < n; ++v) {
-            ip[v] = G.leaf_img + G.leaf_off[v];
-            nf[v] = d.leaves[v].size * (cplx ? 2 : 1);
+            ip[v] = G.leaf_img + G.img_off[v];
+            const int64_t one = d.leaves[v].size * cf;
+            nf[v] = varying[v] ? G.img_is[v] * (NI - 1) + one : one;  // all copies
         }
         UP(G.img_ptr_dev, ip.data(), sizeof(void*) * n);
         UP(G.leaf_nfloat_dev, nf.data(), sizeof(int64_t) * n);
@@ -333,7 +366,7 @@ static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void*
     char* ws = (char*)G.ws;
     auto fwd_ptr = [&](int v) -> const void* {
         if (v < 0) return unit;
-        if (v < n) return G.leaf_img + G.leaf_off[v];
+        if (v < n) return G.leaf_img + G.img_off[v];
         return ws + G.fwd[v - n].ws_off * eb;
     };
     auto slot_max = [&](int v) -> const unsigned* {
@@ -346,6 +379,19 @@ static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void*
         if (v < n) return nullptr;
         if (v < NV) return G.exps + (v - n);
         return G.exps + nn + (v - NV);
+    };
+    // instance strides of an operand vertex (elements, slots)
+    auto op_is = [&](int v, int64_t& is, int32_t& sis) {
+        if (v < 0) {
+            is = 0;
+            sis = 0;
+        } else if (v < n) {
+            is = G.img_is[v] / cf;
+            sis = 0;  // leaf maxima are over all copies
+        } else {
+            is = G.ws_elems;
+            sis = G.n_slots;
+        }
     };
     auto wire = [&](Node& nd, GenericArgs& g, TileArgs& t, const void* A, const void* B, void* C,
                     unsigned* max_c, int64_t* exp_c) -> tn_status {
@@ -363,8 +409,18 @@ static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void*
         g.sc.exp_c = exp_c;
         g.conj_a = nd.tile.conj_a;
         g.conj_b = nd.tile.conj_b;
+        InstanceInfo in;
+        memset(&in, 0, sizeof(in));
+        in.n_inst = n_inst;
+        in.slice_step = 0;  // every instance works on the current slice
+        in.c_is = G.ws_elems;
+        in.sc_is = G.n_slots;
+        in.p_is = G.split_bytes / (int64_t)eb;
+        op_is(nd.ca, in.a_is, in.sa_is);
+        op_is(nd.cb, in.b_is, in.sb_is);
+        g.in = in;
         t = nd.tile;
-        memset(&t.in, 0, sizeof(t.in));  // single instance
+        t.in = in;
         t.A = A;
         t.B = B;
         t.C = C;
@@ -373,6 +429,30 @@ static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void*
         t.slb = g.slb;
         t.ctl = G.ctl;
         t.sc = g.sc;
+        // grid z = batch x K splits x instances is at most 65535
+        if (nd.kind == kTiled || nd.kind == kTensorCore) {
+            if (t.nbatch * NI > 65535) {
+                err = "tn_contract_grad: too many instances for a node with " + std::to_string(t.nbatch) +
+                      " batch entries";
+                return TN_EUNSUPPORTED;
+            }
+            if (t.split > 1 && t.nbatch * (int64_t)t.split * NI > 65535) {
+                if (nd.kind == kTensorCore) {
+                    err = "tn_contract_grad: too many instances for a K-split tensor-core node";
+                    return TN_EUNSUPPORTED;
+                }
+                int split = t.split;
+                while (split > 1 && t.nbatch * (int64_t)split * NI > 65535) split /= 2;
+                const int64_t K = int64_t(1) << t.nk;
+                const int64_t gran = t.cfg == kTileDot ? 256 : (t.cfg == kTile4x1024 ? 4 : 16);
+                const int64_t units = (K + gran - 1) / gran;
+                t.split = split;
+                t.kchunk = ((units + split - 1) / split) * gran;
+            }
+        } else if (NI > 65535) {
+            err = "tn_contract_grad: too many instances";
+            return TN_EUNSUPPORTED;
+        }
         return TN_OK;
     };
     G.gen_f.assign(nn, GenericArgs{});
@@ -396,14 +476,29 @@ static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void*
                             ws + nd.ws_off * eb, G.maxabs + nn + target, G.exps + nn + target);
         if (st != TN_OK) return st;
     }
+    G.inst_item_begin.assign(G.steps.size(), 0);
     if (!G.items.empty()) {
         std::vector<TileArgs> descs(ncomb);
         for (int k = 0; k < nn; ++k) descs[k] = G.tile_f[k];
         for (int j = 0; j < nb; ++j) descs[nn + j] = G.tile_b[j];
+        // instance-major within each step keeps every step's items contiguous
+        std::vector<WaveItem> items;
+        items.reserve(G.items.size() * NI);
+        for (size_t s = 0; s < G.steps.size(); ++s) {
+            const Step& st = G.steps[s];
+            G.inst_item_begin[s] = (int)items.size();
+            if (!st.wave) continue;
+            for (int i = 0; i < n_inst; ++i)
+                for (int j = 0; j < st.item_count; ++j) {
+                    WaveItem it = G.items[st.item_begin + j];
+                    it.pad = i;
+                    items.push_back(it);
+                }
+        }
         AL(G.descs_dev, sizeof(TileArgs) * ncomb, "cudaMalloc");
-        AL(G.items_dev, sizeof(WaveItem) * G.items.size(), "cudaMalloc");
+        AL(G.items_dev, sizeof(WaveItem) * std::max<size_t>(items.size(), 1), "cudaMalloc");
         UP(G.descs_dev, descs.data(), sizeof(TileArgs) * ncomb);
-        UP(G.items_dev, G.items.data(), sizeof(WaveItem) * G.items.size());
+        UP(G.items_dev, items.data(), sizeof(WaveItem) * items.size());
     }
     // leaf gathers: adjoint of leaf v -> its accumulator
     std::vector<LeafGradArgs> lg(n);
@@ -412,9 +507,12 @@ static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void*
         LeafGradArgs& a = lg[v];
         memset(&a, 0, sizeof(a));
         const LeafDesc& lf = d.leaves[v];
-        a.grad = G.gacc + G.leaf_off[v];
+        a.grad = G.gacc + G.acc_off[v];
+        a.grad_is = G.acc_floats / cf;
         a.adj = ws + G.adj_off[v] * eb;
+        a.adj_is = G.ws_elems;
         a.exp_adj = G.exps + nn + v;
+        a.exp_is = G.n_slots;
         a.ctl = G.ctl;
         a.sl = f.leaf_sl[v];
         const std::vector<int>& al = G.g.vlab[NV + v];
@@ -463,17 +561,41 @@ static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void*
     return TN_OK;
 }
 
+// Releases the device state (the host plan of the sweep stays).
+static void free_grad_device(GradState& G) {
+    for (void* q : {(void*)G.ws, G.split_buf, (void*)G.maxabs, (void*)G.exps, (void*)G.ctl,
+                    (void*)G.leafmax, (void*)G.leaf_img, (void*)G.gacc, (void*)G.img_ptr_dev,
+                    (void*)G.leaf_nfloat_dev, (void*)G.descs_dev, (void*)G.items_dev,
+                    (void*)G.flow_deps_dev, (void*)G.flow_cnt_dev, (void*)G.lg_dev,
+                    (void*)G.copy_dev, (void*)G.adj_dev, (void*)G.perm_dev})
+        if (q) cudaFree(q);
+    G.ws = G.split_buf = nullptr;
+    G.maxabs = nullptr;
+    G.exps = nullptr;
+    G.ctl = nullptr;
+    G.leafmax = nullptr;
+    G.leaf_img = G.gacc = nullptr;
+    G.img_ptr_dev = nullptr;
+    G.leaf_nfloat_dev = nullptr;
+    G.descs_dev = nullptr;
+    G.items_dev = nullptr;
+    G.flow_deps_dev = nullptr;
+    G.flow_cnt_dev = nullptr;
+    G.lg_dev = nullptr;
+    G.copy_dev = nullptr;
+    G.adj_dev = nullptr;
+    G.perm_dev = nullptr;
+    if (G.gexec) cudaGraphExecDestroy(G.gexec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G.gexec = nullptr;
+    G.graph = nullptr;
+    G.n_inst = 0;
+}
+
 void free_grad(Plan& p) {
     GradState* G = p.grad;
     if (!G) return;
-    for (void* q : {(void*)G->ws, G->split_buf, (void*)G->maxabs, (void*)G->exps, (void*)G->ctl,
-                    (void*)G->leafmax, (void*)G->leaf_img, (void*)G->gacc, (void*)G->img_ptr_dev,
-                    (void*)G->leaf_nfloat_dev, (void*)G->descs_dev, (void*)G->items_dev,
-                    (void*)G->flow_deps_dev, (void*)G->flow_cnt_dev, (void*)G->lg_dev,
-                    (void*)G->copy_dev, (void*)G->adj_dev, (void*)G->perm_dev})
-        if (q) cudaFree(q);
-    if (G->gexec) cudaGraphExecDestroy(G->gexec);
-    if (G->graph) cudaGraphDestroy(G->graph);
+    free_grad_device(*G);
     if (G->cap_stream) cudaStreamDestroy(G->cap_stream);
     delete G;
     p.grad = nullptr;
@@ -487,24 +609,28 @@ static cudaError_t launch_node(const Node& nd, const GenericArgs& g, const TileA
     return launch_generic(g, c, s);
 }
 
-// One slice: scale slots and dataflow counters cleared, the schedule's
-// steps, the leaf gathers, and the slice counter advanced.
+// One slice for every instance: scale slots and dataflow counters cleared,
+// the schedule's steps, the leaf gathers, and the slice counter advanced.
 static cudaError_t enqueue_grad_slice(const GradState& G, tn_mode mode, bool cplx, cudaStream_t s) {
     const int nn = (int)G.fwd.size();
     const int ncomb = nn + (int)G.bwd.size();
-    cudaError_t e = cudaMemsetAsync(G.maxabs, 0, sizeof(unsigned) * (G.n_slots - 1), s);
+    const int NI = G.n_inst;
+    // every instance's slots but its root-adjoint slot (set per call)
+    cudaError_t e = NI == 1 ? cudaMemsetAsync(G.maxabs, 0, sizeof(unsigned) * (G.n_slots - 1), s)
+                            : launch_zero_strided(G.maxabs, G.n_slots - 1, G.n_slots, NI, s);
     if (e == cudaSuccess && G.any_flow)
-        e = cudaMemsetAsync(G.flow_cnt_dev, 0, sizeof(unsigned) * ((size_t)ncomb + G.steps.size()), s);
+        e = cudaMemsetAsync(G.flow_cnt_dev, 0, sizeof(unsigned) * ((size_t)ncomb * NI + G.steps.size()), s);
     const void* const* leaf_tab = reinterpret_cast<const void* const*>(G.img_ptr_dev);
     for (size_t k = 0; k < G.steps.size() && e == cudaSuccess; ++k) {
         const Step& st = G.steps[k];
         if (st.wave) {
+            const WaveItem* it = G.items_dev + G.inst_item_begin[k];
             if (st.flow)
-                e = launch_wave(G.items_dev + st.item_begin, st.item_count, G.descs_dev, leaf_tab, cplx, s,
+                e = launch_wave(it, st.item_count * NI, G.descs_dev, leaf_tab, cplx, s,
                                 reinterpret_cast<const int4*>(G.flow_deps_dev), G.flow_cnt_dev,
-                                G.flow_cnt_dev + ncomb + k, 1);
+                                G.flow_cnt_dev + (size_t)ncomb * NI + k, NI);
             else
-                e = launch_wave(G.items_dev + st.item_begin, st.item_count, G.descs_dev, leaf_tab, cplx, s);
+                e = launch_wave(it, st.item_count * NI, G.descs_dev, leaf_tab, cplx, s);
         } else if (st.node < nn) {
             e = launch_node(G.fwd[st.node], G.gen_f[st.node], G.tile_f[st.node], mode, cplx, s);
         } else {
@@ -512,16 +638,18 @@ static cudaError_t enqueue_grad_slice(const GradState& G, tn_mode mode, bool cpl
             e = launch_node(G.bwd[j], G.gen_b[j], G.tile_b[j], mode, cplx, s);
         }
     }
-    if (e == cudaSuccess) e = launch_leaf_grads(G.lg_dev, (int)G.leaf_off.size(), G.max_grad_n, cplx, s);
+    if (e == cudaSuccess)
+        e = launch_leaf_grads(G.lg_dev, (int)G.acc_off.size(), G.max_grad_n, NI, cplx, s);
     if (e == cudaSuccess) e = launch_advance(G.ctl, s);
     return e;
 }
 
 tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_mem, int64_t adj_exp2,
-                   const int64_t* adj_exp2_dev, void* const* grads, bool accumulate, cudaStream_t stream,
-                   std::string& err) {
+                   const int64_t* adj_exp2_dev, void* const* grads, bool accumulate, int n_inst,
+                   const int64_t* leaf_inst_stride, cudaStream_t stream, std::string& err) {
     const int n = d.n;
     const bool cplx = d.is_complex();
+    const int cf = cplx ? 2 : 1;
 #define CK(x)                                                          \
     do {                                                               \
         cudaError_t e_ = (x);                                          \
@@ -530,10 +658,24 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
             return e_ == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA; \
         }                                                              \
     } while (0)
+    if (n_inst < 1) {
+        err = "tn_contract_grad: n_inst < 1";
+        return TN_EINVAL;
+    }
     for (int v = 0; v < n; ++v)
         if (d.leaves[v].mem != TN_MEM_DEVICE) {
             err = "tn_contract_grad: leaves must be device pointers";
             return TN_EUNSUPPORTED;
+        }
+    std::vector<char> varying(n, 0);
+    if (n_inst > 1 && leaf_inst_stride)
+        for (int v = 0; v < n; ++v) {
+            if (leaf_inst_stride[v] < 0 || (leaf_inst_stride[v] > 0 && leaf_inst_stride[v] < d.leaves[v].size)) {
+                err = "tn_contract_grad: leaf_inst_stride[" + std::to_string(v) +
+                      "] must be 0 or at least the leaf's size (copies may not overlap)";
+                return TN_EINVAL;
+            }
+            varying[v] = leaf_inst_stride[v] > 0;
         }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(stream, &cap));
@@ -545,38 +687,68 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
     if (!p.grad) {
         GradState* G = new GradState;
         tn_status st = build_grad(d, p, *G, err);
-        if (st == TN_OK) st = alloc_grad(d, p, *G, unit, err);
         if (st != TN_OK) {
-            p.grad = G;
-            free_grad(p);
+            delete G;
             return st;
         }
         p.grad = G;
     }
     GradState& G = *p.grad;
+    if (G.n_inst != n_inst || G.varying != varying) {
+        // another instance layout: the device state and graph are rebuilt
+        CK(cudaStreamSynchronize(stream));
+        free_grad_device(G);
+        tn_status st = alloc_grad(d, p, G, unit, n_inst, varying, err);
+        if (st != TN_OK) {
+            free_grad_device(G);
+            return st;
+        }
+    }
     const int nn = (int)G.fwd.size();
     const int root_v = n + nn - 1;
     const size_t eb = d.elem_bytes();
     // per-call table: the leaves into the image, then the gradients out
     std::vector<CopyEntry> tab;
-    tab.reserve(2 * n);
-    for (int v = 0; v < n; ++v)
-        tab.push_back(CopyEntry{static_cast<const float*>(d.leaves[v].ptr), G.leaf_img + G.leaf_off[v],
-                                d.leaves[v].size * (cplx ? 2 : 1), 0, 0});
-    for (int v = 0; v < n; ++v)
-        if (grads[v])
-            tab.push_back(CopyEntry{G.gacc + G.leaf_off[v], static_cast<float*>(grads[v]),
-                                    d.leaves[v].size * (cplx ? 2 : 1), accumulate ? 1 : 0, 0});
-    const int n_scatter = (int)tab.size() - n;
+    tab.reserve((size_t)2 * n * n_inst);
+    for (int v = 0; v < n; ++v) {
+        const int64_t nf = d.leaves[v].size * cf;
+        const float* src = static_cast<const float*>(d.leaves[v].ptr);
+        float* dst = G.leaf_img + G.img_off[v];
+        if (!varying[v]) {
+            tab.push_back(CopyEntry{src, dst, nf, 0, 1, 0});
+        } else {
+            for (int i = 0; i < n_inst; ++i)
+                tab.push_back(CopyEntry{src + (int64_t)i * leaf_inst_stride[v] * cf, dst + i * G.img_is[v], nf, 0,
+                                        1, 0});
+        }
+    }
+    const int n_gather = (int)tab.size();
+    for (int v = 0; v < n; ++v) {
+        if (!grads[v]) continue;
+        const int64_t nf = d.leaves[v].size * cf;
+        float* dst = static_cast<float*>(grads[v]);
+        const float* src = G.gacc + G.acc_off[v];
+        if (!varying[v]) {
+            tab.push_back(CopyEntry{src, dst, nf, G.acc_floats, n_inst, accumulate ? 1 : 0});
+        } else {
+            for (int i = 0; i < n_inst; ++i)
+                tab.push_back(CopyEntry{src + i * G.acc_floats, dst + (int64_t)i * leaf_inst_stride[v] * cf, nf, 0, 1,
+                                        accumulate ? 1 : 0});
+        }
+    }
+    const int n_scatter = (int)tab.size() - n_gather;
     // pageable source: the copy is staged before the call returns
     CK(cudaMemcpyAsync(G.copy_dev, tab.data(), sizeof(CopyEntry) * tab.size(), cudaMemcpyHostToDevice,
                        stream));
-    CK(launch_copy_table(G.copy_dev, n, G.max_leaf_floats, stream));
-    CK(launch_leaf_max(G.img_ptr_dev, G.leaf_nfloat_dev, G.leafmax, n, stream, G.max_leaf_floats));
-    // root adjoint
+    CK(launch_copy_table(G.copy_dev, n_gather, G.max_leaf_floats, stream));
+    int64_t mx = 0;
+    for (int v = 0; v < n; ++v)
+        mx = std::max(mx, varying[v] ? G.img_is[v] * (n_inst - 1) + d.leaves[v].size * cf : d.leaves[v].size * cf);
+    CK(launch_leaf_max(G.img_ptr_dev, G.leaf_nfloat_dev, G.leafmax, n, stream, mx));
+    // root adjoints
     const double* adj_src = adj;
     if (adj_mem == TN_MEM_HOST) {
-        CK(cudaMemcpyAsync(G.adj_dev, adj, sizeof(double) * p.n_out * (cplx ? 2 : 1), cudaMemcpyHostToDevice,
+        CK(cudaMemcpyAsync(G.adj_dev, adj, sizeof(double) * p.n_out * cf * n_inst, cudaMemcpyHostToDevice,
                            stream));
         adj_src = G.adj_dev;
     }
@@ -591,8 +763,10 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
     ra.dst = reinterpret_cast<float*>(static_cast<char*>(G.ws) + G.adj_off[root_v] * eb);
     ra.max_slot = G.maxabs + (G.n_slots - 1);
     ra.exp_slot = G.exps + (G.n_slots - 1);
-    CK(launch_root_adjoint(ra, stream));
-    CK(cudaMemsetAsync(G.gacc, 0, sizeof(float) * G.leaf_floats, stream));
+    ra.dst_is = G.ws_elems * cf;
+    ra.slot_is = G.n_slots;
+    CK(launch_root_adjoint(ra, n_inst, stream));
+    CK(cudaMemsetAsync(G.gacc, 0, sizeof(float) * G.acc_floats * n_inst, stream));
     CK(launch_begin_call(G.ctl, 0, p.d_sliced, nullptr, 0, stream));
     if (!G.gexec) {
         if (!G.cap_stream) CK(cudaStreamCreateWithFlags(&G.cap_stream, cudaStreamNonBlocking));
@@ -604,7 +778,7 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
         CK(cudaGraphInstantiate(&G.gexec, G.graph, 0));
     }
     for (int64_t s = 0; s < p.d_sliced; ++s) CK(cudaGraphLaunch(G.gexec, stream));
-    if (n_scatter > 0) CK(launch_copy_table(G.copy_dev + n, n_scatter, G.max_leaf_floats, stream));
+    if (n_scatter > 0) CK(launch_copy_table(G.copy_dev + n_gather, n_scatter, G.max_leaf_floats, stream));
 #undef CK
     return TN_OK;
 }

@@ -249,6 +249,8 @@ struct LeafGradArgs {
     void* grad;
     const void* adj;
     const int64_t* exp_adj;
+    int64_t grad_is, adj_is;  // elements between instances (grid z)
+    int64_t exp_is;           // scale slots between instances
     int64_t n;
     int n_d;
     int32_t dim[kMaxDigits];
@@ -265,8 +267,9 @@ struct CopyEntry {
     const float* src;
     float* dst;
     int64_t nfloat;
-    int32_t add;  // dst += src instead of dst = src
-    int32_t pad;
+    int64_t src_is;  // floats between the n_sum source copies
+    int32_t n_sum;   // dst (+)= sum over i < n_sum of src[i * src_is + j], i ascending
+    int32_t add;     // dst += ... instead of dst = ...
 };
 
 // Root adjoint of the reverse sweep: FP64 adjoint in the user's open-label
@@ -285,6 +288,10 @@ struct RootAdjArgs {
     float* dst;
     unsigned* max_slot;
     int64_t* exp_slot;
+    // instances (one block each): adjoint i at adj + i * n_out * (1|2),
+    // exponent exp_dev[i], root dst + i * dst_is floats, slots + i * slot_is
+    int64_t dst_is;
+    int64_t slot_is;
 };
 
 // Batched networks: where each network's root lives and where its result goes.
@@ -303,10 +310,12 @@ cudaError_t launch_batch_finish(const BatchRoot* roots, int n, double* out, int6
                                 unsigned long long* latency, cudaStream_t s);
 // Leaf adjoints of the current slice for every entry of the device table
 // (max_n: the largest entry's n).
-cudaError_t launch_leaf_grads(const LeafGradArgs* tab, int n_entries, int64_t max_n, bool is_c,
+cudaError_t launch_leaf_grads(const LeafGradArgs* tab, int n_entries, int64_t max_n, int n_inst, bool is_c,
                               cudaStream_t s);
 cudaError_t launch_copy_table(const CopyEntry* tab, int n_entries, int64_t max_nfloat, cudaStream_t s);
-cudaError_t launch_root_adjoint(const RootAdjArgs& a, cudaStream_t s);
+// p[i * stride + j] = 0 for i < n, j < count (per-instance scale slots).
+cudaError_t launch_zero_strided(unsigned* p, int64_t count, int64_t stride, int n, cudaStream_t s);
+cudaError_t launch_root_adjoint(const RootAdjArgs& a, int n_inst, cudaStream_t s);
 cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s);  // tn_tiled.cu
 // Tensor-core node (tn_tc.cu): prec as tc_prec_of_mode.

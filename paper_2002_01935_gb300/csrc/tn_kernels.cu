@@ -313,9 +313,10 @@ __global__ void __launch_bounds__(256) k_leaf_grads(const LeafGradArgs* tab, int
     }
     __syncthreads();
     if ((int64_t)blockIdx.x * blockDim.x >= a.n) return;
+    const int64_t inst = blockIdx.z;
     const int64_t slice = a.ctl->slice;
     const int64_t base = slice_offset(a.sl, slice);
-    int64_t e = *a.exp_adj;
+    int64_t e = a.exp_adj[inst * a.exp_is];
     const int ex = (int)(e < -400 ? -400 : (e > 400 ? 400 : e));
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < a.n; o += stride) {
@@ -327,6 +328,8 @@ __global__ void __launch_bounds__(256) k_leaf_grads(const LeafGradArgs* tab, int
             g += v * a.gstride[i];
             s += v * a.astride[i];
         }
+        s += inst * a.adj_is;
+        g += inst * a.grad_is;
         if (CPLX) {
             const float2 x = reinterpret_cast<const float2*>(a.adj)[s];
             float2* G = reinterpret_cast<float2*>(a.grad);
@@ -340,12 +343,12 @@ __global__ void __launch_bounds__(256) k_leaf_grads(const LeafGradArgs* tab, int
     }
 }
 
-cudaError_t launch_leaf_grads(const LeafGradArgs* tab, int n_entries, int64_t max_n, bool is_c,
+cudaError_t launch_leaf_grads(const LeafGradArgs* tab, int n_entries, int64_t max_n, int n_inst, bool is_c,
                               cudaStream_t s) {
     if (n_entries <= 0) return cudaSuccess;
     int64_t blocks = (max_n + 255) / 256;
     blocks = blocks < 1 ? 1 : (blocks > 152 * 8 ? 152 * 8 : blocks);
-    const dim3 grid((unsigned)blocks, (unsigned)n_entries);
+    const dim3 grid((unsigned)blocks, (unsigned)n_entries, (unsigned)(n_inst > 1 ? n_inst : 1));
     if (is_c)
         k_leaf_grads<true><<<grid, 256, 0, s>>>(tab, n_entries);
     else
@@ -359,15 +362,38 @@ __global__ void __launch_bounds__(256) k_copy_table(const CopyEntry* tab, int n_
     if ((int)blockIdx.y >= n_entries) return;
     const CopyEntry e = tab[blockIdx.y];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e.nfloat; i += stride)
-        e.dst[i] = e.add ? e.dst[i] + e.src[i] : e.src[i];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e.nfloat; i += stride) {
+        float v = e.src[i];
+        for (int r = 1; r < e.n_sum; ++r) v += e.src[r * e.src_is + i];
+        e.dst[i] = e.add ? e.dst[i] + v : v;
+    }
 }
 
 cudaError_t launch_copy_table(const CopyEntry* tab, int n_entries, int64_t max_nfloat, cudaStream_t s) {
-    if (n_entries <= 0) return cudaSuccess;
     int64_t blocks = (max_nfloat + 255) / 256;
     blocks = blocks < 1 ? 1 : (blocks > 152 * 4 ? 152 * 4 : blocks);
-    k_copy_table<<<dim3((unsigned)blocks, (unsigned)n_entries), 256, 0, s>>>(tab, n_entries);
+    for (int first = 0; first < n_entries; first += 65535) {  // grid y limit
+        const int cnt = n_entries - first < 65535 ? n_entries - first : 65535;
+        k_copy_table<<<dim3((unsigned)blocks, (unsigned)cnt), 256, 0, s>>>(tab + first, cnt);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// p[i * stride + j] = 0 for i < n, j < count.
+__global__ void k_zero_strided(unsigned* p, int64_t count, int64_t stride, int n) {
+    const int64_t total = count * n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+        p[(t / count) * stride + t % count] = 0u;
+}
+
+cudaError_t launch_zero_strided(unsigned* p, int64_t count, int64_t stride, int n, cudaStream_t s) {
+    const int64_t total = count * n;
+    if (total <= 0) return cudaSuccess;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    k_zero_strided<<<(unsigned)blocks, 256, 0, s>>>(p, count, stride, n);
     return cudaGetLastError();
 }
 
@@ -375,10 +401,16 @@ cudaError_t launch_copy_table(const CopyEntry* tab, int n_entries, int64_t max_n
 // the FP64 adjoint, m = f * 2^e with f in [0.5, 1) (frexp), every component
 // scaled by 2^-e (exact) and rounded to float into the root's layout; the
 // root's scale slots get f and e plus the adjoint's own exponent.  One block.
-__global__ void __launch_bounds__(1024) k_root_adjoint(const RootAdjArgs a) {
+__global__ void __launch_bounds__(1024) k_root_adjoint(RootAdjArgs a) {
     __shared__ double red[32];
     const int c = a.cplx ? 2 : 1;
     const int64_t nd = a.n_out * c;
+    const int64_t inst = blockIdx.x;
+    a.adj += inst * nd;
+    a.dst += inst * a.dst_is;
+    a.max_slot += inst * a.slot_is;
+    a.exp_slot += inst * a.slot_is;
+    if (a.exp_dev) a.exp_dev += inst;
     double m = 0.0;
     for (int64_t i = threadIdx.x; i < nd; i += blockDim.x) m = fmax(m, fabs(a.adj[i]));
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -402,8 +434,8 @@ __global__ void __launch_bounds__(1024) k_root_adjoint(const RootAdjArgs a) {
     }
 }
 
-cudaError_t launch_root_adjoint(const RootAdjArgs& a, cudaStream_t s) {
-    k_root_adjoint<<<1, 1024, 0, s>>>(a);
+cudaError_t launch_root_adjoint(const RootAdjArgs& a, int n_inst, cudaStream_t s) {
+    k_root_adjoint<<<(unsigned)(n_inst > 1 ? n_inst : 1), 1024, 0, s>>>(a);
     return cudaGetLastError();
 }
 

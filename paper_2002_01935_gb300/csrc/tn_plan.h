@@ -176,9 +176,13 @@ tn_status run_instances(NetDesc& d, Plan& p, void* unit, int n_inst, const int64
                         std::string& err);
 // adj: FP64 adjoint in host (adj_mem TN_MEM_HOST) or device memory; its
 // exponent is adj_exp2 plus, for a device adjoint, *adj_exp2_dev (if set).
+// n_inst instances: leaf v of instance i at its pointer + i *
+// leaf_inst_stride[v] elements (NULL or 0: shared), adjoint i at adj + i *
+// (output size), exponent adj_exp2 + adj_exp2_dev[i]; a shared leaf's
+// gradient is the sum over the instances, a varying leaf's is per instance.
 tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_mem, int64_t adj_exp2,
-                   const int64_t* adj_exp2_dev, void* const* grads, bool accumulate, cudaStream_t stream,
-                   std::string& err);
+                   const int64_t* adj_exp2_dev, void* const* grads, bool accumulate, int n_inst,
+                   const int64_t* leaf_inst_stride, cudaStream_t stream, std::string& err);
 void plan_info(const NetDesc& d, const Plan& p, double out[8]);
 void free_device(Plan& p);  // releases device state; the host plan stays valid
 void free_grad(Plan& p);

@@ -281,3 +281,58 @@ def test_contract_batch_matches_per_network_function(torch):
     assert np.max(np.abs(gv - rv)) <= 1e-5 * np.max(np.abs(rv))
     for a, b in zip(got, ref):
         assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("sliced_n,mode", [(0, "fp32"), (1, "fp32"), (0, "tf32_split")])
+def test_grad_instances_match_single_sweeps(torch, sliced_n, mode):
+    """n copies in one sweep (two leaves varying per copy, the rest shared)
+    against one tn_contract_grad call per copy: shared leaves get the sum
+    over the copies, varying leaves each copy's gradient."""
+    net, pairs, sliced, ts, tnw = _setup(torch, seed=21, sliced_n=sliced_n)
+    B = 5
+    rng = np.random.default_rng(9)
+    var = [1, 4]
+    stacks = {v: torch.stack([ts[v] * np.float32(1.0 + 0.2 * rng.standard_normal()) for _ in range(B)])
+              for v in var}
+    adjs = np.stack([_adjoint(net, 30 + i) for i in range(B)])
+    singles = []
+    for i in range(B):
+        lv = list(ts)
+        for v in var:
+            lv[v] = stacks[v][i].contiguous()
+        tnw.set_tensors(lv)
+        singles.append([g.cpu().numpy() for g in tnw.grad(pairs, sliced, mode, adjs[i])])
+    lv = list(ts)
+    strides = [0] * len(ts)
+    for v in var:
+        lv[v] = stacks[v]
+        strides[v] = ts[v].numel()
+    tnw.set_tensors(lv)
+    adj_dev = torch.from_numpy(np.ascontiguousarray(adjs)).cuda()
+    got = [g.cpu().numpy() for g in tnw.grad_instances(pairs, sliced, mode, B, strides, adj_dev)]
+    for v in range(len(ts)):
+        if v in var:
+            ref = np.stack([singles[i][v] for i in range(B)])
+        else:
+            ref = sum(singles[i][v].astype(np.complex128) for i in range(B))
+        assert got[v].shape == ref.shape, v
+        assert np.linalg.norm(got[v] - ref) <= 1e-5 * (np.linalg.norm(ref) + 1e-30), v
+    # accumulation into the same buffers doubles them
+    acc = [torch.from_numpy(g.copy()).cuda() for g in got]
+    tnw.grad_instances(pairs, sliced, mode, B, strides, adj_dev, grads=acc, accumulate=True)
+    for v in range(len(ts)):
+        assert np.array_equal(acc[v].cpu().numpy(), (got[v] + got[v]).astype(got[v].dtype)), v
+    tnw.close()
+
+
+def test_grad_instances_refuses_overlapping_copies(torch):
+    from paper_2002_01935_gb300 import binding
+    net, pairs, sliced, ts, tnw = _setup(torch, seed=22)
+    strides = [0] * len(ts)
+    v = int(np.argmax([t.numel() for t in ts]))
+    assert ts[v].numel() >= 2
+    strides[v] = ts[v].numel() // 2  # copies would overlap
+    adj = np.stack([_adjoint(net, 1), _adjoint(net, 2)])
+    with pytest.raises(binding.TNError):
+        tnw.grad_instances(pairs, sliced, "fp32", 2, strides, adj)
+    tnw.close()
