@@ -836,13 +836,21 @@ def run_grad(args, torch, dist, rank, world, local):
         dist.barrier()
     clk.start()
     times = []
+    stream = torch.cuda.current_stream()
+    # the backward runs on autograd's own thread, outside a thread-scoped
+    # NVTX range: the profiler start/stop marks the timed region for
+    # ncu --profile-from-start off
     torch.cuda.nvtx.range_push("timed")
+    torch.cuda.profiler.start()
     for _ in range(args.steps):
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
         loss = step()
+        ev1.record(stream)
         torch.cuda.synchronize()
-        times.append(time.perf_counter() - t0)
+        times.append(ev0.elapsed_time(ev1) / 1e3)
+    torch.cuda.profiler.stop()
     torch.cuda.nvtx.range_pop()
     clocks = clk.stop()
     total = sum(times)

@@ -212,6 +212,10 @@ tn_status tn_contract_grad(tn_net *net, const int32_t *tree_pairs, int32_t n_sli
 /* tn_contract_grad_ex flag: add the gradients into leaf_grads (which then
  * hold the caller's running sums) instead of overwriting them. */
 #define TN_GRAD_ACCUMULATE 1u
+/* tn_contract_grad_instances flag: the forward intermediates are those of the
+ * last tn_contract_instances_keep call (same tree, mode, copies, strides and
+ * leaf data): the sweep runs without recomputing them. */
+#define TN_GRAD_KEPT_FORWARD 2u
 
 /*
  * tn_contract_grad_ex -- tn_contract_grad with the adjoint in device memory
@@ -264,7 +268,7 @@ tn_status tn_contract_grad_ex(tn_net *net, const int32_t *tree_pairs, int32_t n_
  *                 leaf the sum over the copies of their gradients (added in
  *                 copy order); for a varying leaf copy i's gradient at
  *                 + i * leaf_inst_stride[v] elements.
- *   flags         0 or TN_GRAD_ACCUMULATE.
+ *   flags         TN_GRAD_ACCUMULATE and/or TN_GRAD_KEPT_FORWARD (below).
  * The device state grows to n_inst copies of the sweep's workspace; a
  * different (n_inst, shared/varying pattern) rebuilds it (and synchronises
  * the stream).  Errors: as tn_contract_grad_ex; TN_EINVAL for n_inst < 1
@@ -276,6 +280,24 @@ tn_status tn_contract_grad_instances(tn_net *net, const int32_t *tree_pairs, int
                                      const int64_t *leaf_inst_stride, const double *out_adjoint,
                                      int32_t adj_mem, int64_t adj_exp2, const int64_t *adj_exp2_dev,
                                      void *const *leaf_grads, uint32_t flags, void *stream);
+
+/*
+ * tn_contract_instances_keep -- tn_contract_instances (unsliced scalar
+ * networks, same arguments and outputs) computed in the state of the
+ * reverse sweep of (tree, unsliced, mode) for n_inst copies, with every
+ * intermediate kept.  A following tn_contract_grad_instances call with the
+ * same tree, mode, n_inst and leaf strides, no slicing, and flag
+ * TN_GRAD_KEPT_FORWARD then runs only the sweep: for an unsliced tree the
+ * forward is computed once per gradient step instead of twice.  The library
+ * refuses the flag (TN_EINVAL) when the kept state is gone (another
+ * gradient call of that tree and mode ran in between, or another copy
+ * count); it cannot see changes of the leaf data, which the caller must
+ * not make in between.  Errors as tn_contract_instances; TN_EUNSUPPORTED
+ * for sliced trees or open outputs.
+ */
+tn_status tn_contract_instances_keep(tn_net *net, const int32_t *tree_pairs, tn_mode mode, int32_t n_inst,
+                                     const int64_t *leaf_inst_stride, double *out, int64_t *out_exp2,
+                                     int32_t out_mem, void *stream);
 
 /*
  * tn_contract_noalloc -- tn_contract for callers that cannot allocate device

@@ -12,10 +12,10 @@ grad_leaf = conj(d value / d leaf) * grad_output.
 scalar networks that share the tree and every leaf except those in
 ``batch`` (e.g. the output-state leaves of B bitstrings of one circuit,
 Eq. trans-amp): the forward runs the B copies in one launch sequence
-(tn_contract_instances), the backward runs the reverse sweeps of all B
-networks in one launch sequence (tn_contract_grad_instances) with the
-adjoints on the device; the shared leaves' gradients are summed over the
-batch in the library.
+keeping the intermediates (tn_contract_instances_keep), the backward runs
+the reverse sweeps of all B networks in one launch sequence
+(tn_contract_grad_instances) on them, with the adjoints on the device; the
+shared leaves' gradients are summed over the batch in the library.
 """
 from __future__ import annotations
 
@@ -68,14 +68,16 @@ class _ContractBatch(torch.autograd.Function):
             leaves[v] = st
             strides[v] = st[0].numel()
         tnw.set_tensors(leaves)
-        mant, ex = tnw.contract_instances(pairs, mode, n_batch, strides)
+        # forward in the sweep's state with the intermediates kept: the
+        # backward reuses them unless another gradient call intervened
+        mant, ex, token = tnw.contract_instances_keep(pairs, mode, n_batch, strides)
         value = mant * torch.pow(torch.tensor(2.0, dtype=torch.float64, device=mant.device),
                                  ex.double()).unsqueeze(1)
         if tnw.dtype == binding.TN_C64:
             value = torch.complex(value[:, 0], value[:, 1])
         else:
             value = value[:, 0].contiguous()
-        ctx.tnw, ctx.pairs, ctx.mode, ctx.batch_ids = tnw, pairs, mode, list(batch_ids)
+        ctx.tnw, ctx.pairs, ctx.mode, ctx.batch_ids, ctx.token = tnw, pairs, mode, list(batch_ids), token
         ctx.save_for_backward(*shared, *stacks)
         return value
 
@@ -103,7 +105,7 @@ class _ContractBatch(torch.autograd.Function):
             grads[v] = g_stack[j]
             strides[v] = stacks[j][0].numel()
         tnw.set_tensors(leaves)
-        tnw.grad_instances(ctx.pairs, [], ctx.mode, n_batch, strides, adj, grads=grads)
+        tnw.grad_instances(ctx.pairs, [], ctx.mode, n_batch, strides, adj, grads=grads, kept_forward=ctx.token)
         return (None, None, None, None, None, *g_shared, *g_stack)
 
 

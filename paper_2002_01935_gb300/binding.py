@@ -67,6 +67,9 @@ _lib.tn_contract_grad_instances.restype = ctypes.c_int
 _lib.tn_contract_grad_instances.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int, ctypes.c_int32,
                                             _i64p, _vp, ctypes.c_int32, ctypes.c_int64, _vp,
                                             ctypes.POINTER(_vp), ctypes.c_uint32, _vp]
+_lib.tn_contract_instances_keep.restype = ctypes.c_int
+_lib.tn_contract_instances_keep.argtypes = [_vp, _i32p, ctypes.c_int, ctypes.c_int32, _i64p, _vp, _vp,
+                                            ctypes.c_int32, _vp]
 _lib.tn_contract_noalloc.restype = ctypes.c_int
 _lib.tn_contract_noalloc.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, _vp, ctypes.c_int32, _i64p,
                                      _vp]
@@ -94,7 +97,7 @@ _lib.tn_version.restype = ctypes.c_char_p
 _lib.tn_version.argtypes = []
 
 EXPORTS = ["tn_create", "tn_set_tensor", "tn_contract", "tn_contract_ex", "tn_contract_grad",
-           "tn_contract_grad_ex", "tn_contract_grad_instances",
+           "tn_contract_grad_ex", "tn_contract_grad_instances", "tn_contract_instances_keep",
            "tn_contract_noalloc", "tn_contract_instances", "tn_autotune", "tn_plan_info", "tn_plan_steps",
            "tn_batch_create",
            "tn_batch_contract", "tn_batch_destroy", "tn_destroy", "tn_last_error", "tn_version"]
@@ -189,6 +192,7 @@ def tn_contract_grad(h: int, pairs, sliced, mode: int, adjoint: np.ndarray, adj_
 
 
 TN_GRAD_ACCUMULATE = 1
+TN_GRAD_KEPT_FORWARD = 2
 
 
 def tn_contract_grad_ex(h: int, pairs, sliced, mode: int, adj_ptr: int, adj_mem: int, adj_exp2: int,
@@ -397,18 +401,39 @@ class TensorNetwork:
         tn_contract_grad_ex(self.h, pairs, sliced, m, adj_ptr, adj_mem, exp_host, exp_dev,
                             [g.data_ptr() if g is not None else 0 for g in grads],
                             TN_GRAD_ACCUMULATE if accumulate else 0, s)
+        self._grad_epoch = getattr(self, "_grad_epoch", 0) + 1
         del keep
         return grads
 
+    def contract_instances_keep(self, pairs, mode, n_inst, leaf_inst_stride=None, stream=None):
+        """contract_instances computed in the reverse sweep's state with the
+        intermediates kept (tn_contract_instances_keep).  Returns (mantissa
+        (n_inst, 2) float64, exp2 (n_inst,)) device tensors and a token for
+        grad_instances(kept_forward=token)."""
+        import torch
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        out = torch.empty((n_inst, 2), dtype=torch.float64, device="cuda")
+        ex = torch.empty(n_inst, dtype=torch.int64, device="cuda")
+        st = _arr(list(leaf_inst_stride), np.int64) if leaf_inst_stride is not None else None
+        s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        _check(_lib.tn_contract_instances_keep(self.h, _p(_tree(pairs), ctypes.c_int32), m, n_inst,
+                                               _p(st, ctypes.c_int64) if st is not None else None,
+                                               out.data_ptr(), ex.data_ptr(), TN_MEM_DEVICE, s))
+        self._grad_epoch = getattr(self, "_grad_epoch", 0) + 1
+        return out, ex, self._grad_epoch
+
     def grad_instances(self, pairs, sliced, mode, n_inst, leaf_inst_stride, adjoint, adj_exp2=0,
-                       grads=None, stream=None, accumulate=False):
+                       grads=None, stream=None, accumulate=False, kept_forward=None):
         """Reverse sweep of n_inst copies in one launch sequence (see
         tn_contract_grad_instances).  ``adjoint``: [n_inst, *output shape]
         FP64 (complex128 for complex networks), host array or CUDA tensor;
         ``adj_exp2``: int, or a CUDA int64 tensor of n_inst exponents (CUDA
         adjoint only).  ``grads``: per leaf a tensor shaped like the leaf
         (shared leaves: summed over the copies) or like the stacked copies
-        (varying leaves), or None to skip.  Returns ``grads``."""
+        (varying leaves), or None to skip.  ``kept_forward``: the token of a
+        contract_instances_keep call; when no other gradient call ran on this
+        handle since, the sweep reuses that forward (TN_GRAD_KEPT_FORWARD).
+        Returns ``grads``."""
         import torch
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         cplx = self.dtype == TN_C64
@@ -439,9 +464,14 @@ class TensorNetwork:
         if grads is None:  # attached tensors: stacked copies for varying leaves
             grads = [torch.empty_like(t, device="cuda") for t in self._keep]
         s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        flags = TN_GRAD_ACCUMULATE if accumulate else 0
+        if kept_forward is not None and kept_forward == getattr(self, "_grad_epoch", 0) and not sliced:
+            flags |= TN_GRAD_KEPT_FORWARD
         tn_contract_grad_instances(self.h, pairs, sliced, m, n_inst, leaf_inst_stride, adj_ptr, adj_mem,
                                    exp_host, exp_dev, [g.data_ptr() if g is not None else 0 for g in grads],
-                                   TN_GRAD_ACCUMULATE if accumulate else 0, s)
+                                   flags, s)
+        if not flags & TN_GRAD_KEPT_FORWARD:  # the sweep's workspace now holds another forward
+            self._grad_epoch = getattr(self, "_grad_epoch", 0) + 1
         del keep
         return grads
 

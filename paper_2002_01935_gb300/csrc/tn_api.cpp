@@ -132,8 +132,12 @@ tn_status tn_set_tensor(tn_net* net, int32_t v, const void* ptr, int32_t mem) {
     return TN_OK;
 }
 
+// Plans are kept per (tree, slicing, mode, copies): copies > 1 is the plan of
+// tn_contract_instances with that many copies per launch, whose kernel
+// choices and K splits count the copies (and which the autotuner, timing
+// single copies, leaves alone).
 static tn_status get_plan(tn_net* net, const int32_t* pairs, int32_t n_sliced, const int64_t* sliced,
-                          tn_mode mode, Plan** out) {
+                          tn_mode mode, Plan** out, int copies = 1) {
     NetDesc& d = net->d;
     const int n = d.n;
     if (n > 1 && !pairs) return fail(TN_EINVAL, "tree_pairs is NULL");
@@ -142,7 +146,7 @@ static tn_status get_plan(tn_net* net, const int32_t* pairs, int32_t n_sliced, c
     std::vector<int32_t> pv(pairs, pairs + 2 * (size_t)(n - 1));
     std::vector<int64_t> sv(sliced, sliced + n_sliced);
     for (auto& p : net->plans)
-        if (p->mode == mode && p->pairs == pv && p->sliced_ids == sv) {
+        if (p->mode == mode && p->pairs == pv && p->sliced_ids == sv && p->copies == copies) {
             *out = p.get();
             return TN_OK;
         }
@@ -151,6 +155,7 @@ static tn_status get_plan(tn_net* net, const int32_t* pairs, int32_t n_sliced, c
     p->mode = mode;
     p->pairs = pv;
     p->sliced_ids = sv;
+    p->copies = copies;
     std::string err;
     tn_status st = tn::build_plan(d, *p, err);
     if (st != TN_OK) return fail(st, err);
@@ -235,7 +240,7 @@ tn_status tn_contract_instances(tn_net* net, const int32_t* tree_pairs, tn_mode 
             return fail(TN_EINVAL, "tn_contract_instances: negative stride");
     }
     Plan* p = nullptr;
-    tn_status st = get_plan(net, tree_pairs, 0, nullptr, mode, &p);
+    tn_status st = get_plan(net, tree_pairs, 0, nullptr, mode, &p, n_inst);
     if (st != TN_OK) return st;
     st = ensure_instances(net, p, n_inst, (cudaStream_t)stream);
     if (st != TN_OK) return st;
@@ -288,7 +293,7 @@ tn_status tn_contract_grad_ex(tn_net* net, const int32_t* tree_pairs, int32_t n_
     if (st != TN_OK) return st;
     std::string err;
     st = tn::run_grad(net->d, *p, net->unit, out_adjoint, adj_mem, adj_exp2, adj_exp2_dev, leaf_grads,
-                      (flags & TN_GRAD_ACCUMULATE) != 0, 1, nullptr, (cudaStream_t)stream, err);
+                      (flags & TN_GRAD_ACCUMULATE) != 0, false, 1, nullptr, (cudaStream_t)stream, err);
     if (st != TN_OK) return fail(st, err);
     return TN_OK;
 }
@@ -304,7 +309,7 @@ tn_status tn_contract_grad_instances(tn_net* net, const int32_t* tree_pairs, int
     if (adj_mem != TN_MEM_DEVICE && adj_mem != TN_MEM_HOST) return fail(TN_EINVAL, "bad adj_mem");
     if (adj_exp2_dev && adj_mem != TN_MEM_DEVICE)
         return fail(TN_EINVAL, "tn_contract_grad_instances: adj_exp2_dev needs a device adjoint");
-    if (flags & ~(uint32_t)TN_GRAD_ACCUMULATE)
+    if (flags & ~(uint32_t)(TN_GRAD_ACCUMULATE | TN_GRAD_KEPT_FORWARD))
         return fail(TN_EINVAL, "tn_contract_grad_instances: unknown flags");
     for (int v = 0; v < net->d.n; ++v)
         if (!net->d.leaves[v].ptr) return fail(TN_EINVAL, "tn_contract_grad_instances: tensor without data");
@@ -315,7 +320,28 @@ tn_status tn_contract_grad_instances(tn_net* net, const int32_t* tree_pairs, int
     if (st != TN_OK) return st;
     std::string err;
     st = tn::run_grad(net->d, *p, net->unit, out_adjoint, adj_mem, adj_exp2, adj_exp2_dev, leaf_grads,
-                      (flags & TN_GRAD_ACCUMULATE) != 0, n_inst, leaf_inst_stride, (cudaStream_t)stream, err);
+                      (flags & TN_GRAD_ACCUMULATE) != 0, (flags & TN_GRAD_KEPT_FORWARD) != 0, n_inst,
+                      leaf_inst_stride, (cudaStream_t)stream, err);
+    if (st != TN_OK) return fail(st, err);
+    return TN_OK;
+}
+
+tn_status tn_contract_instances_keep(tn_net* net, const int32_t* tree_pairs, tn_mode mode, int32_t n_inst,
+                                     const int64_t* leaf_inst_stride, double* out, int64_t* out_exp2,
+                                     int32_t out_mem, void* stream) {
+    if (!net) return fail(TN_EINVAL, "tn_contract_instances_keep: net is NULL");
+    if (!out || !out_exp2 || n_inst < 1) return fail(TN_EINVAL, "tn_contract_instances_keep: bad arguments");
+    if (out_mem != TN_MEM_DEVICE && out_mem != TN_MEM_HOST) return fail(TN_EINVAL, "bad out_mem");
+    for (int v = 0; v < net->d.n; ++v)
+        if (!net->d.leaves[v].ptr) return fail(TN_EINVAL, "tn_contract_instances_keep: tensor without data");
+    Plan* p = nullptr;
+    tn_status st = get_plan(net, tree_pairs, 0, nullptr, mode, &p);
+    if (st != TN_OK) return st;
+    st = ensure_device(net, p);
+    if (st != TN_OK) return st;
+    std::string err;
+    st = tn::run_grad_forward(net->d, *p, net->unit, n_inst, leaf_inst_stride, out, out_exp2, out_mem,
+                              (cudaStream_t)stream, err);
     if (st != TN_OK) return fail(st, err);
     return TN_OK;
 }

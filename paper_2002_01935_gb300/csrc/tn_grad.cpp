@@ -66,6 +66,13 @@ struct GradState {
     std::vector<int64_t> img_off, img_is;
     int64_t img_floats = 0;
     std::vector<int> inst_item_begin;  // per step: first item of the instance-replicated list
+    int plan_inst = 1;                 // copies the node kernels and K splits were planned for
+    int n_fwd_steps = 0;               // steps [0, n_fwd_steps) hold the forward nodes
+    bool kept = false;                 // the workspace holds the forward of the last keep call
+    BatchRoot* roots_dev = nullptr;    // per copy: root value and its scale slots
+    double* val_dev = nullptr;         // per copy: FP64 value (2 doubles) ...
+    int64_t* val_exp_dev = nullptr;    // ... and exponent, for host outputs
+    std::vector<int> level;            // dependency level of each combined node
     // device
     void* ws = nullptr;
     void* split_buf = nullptr;
@@ -87,19 +94,22 @@ struct GradState {
     int64_t* perm_dev = nullptr;           // root offset of each output
     std::vector<GenericArgs> gen_f, gen_b;
     std::vector<TileArgs> tile_f, tile_b;
-    // the per-slice sequence as a captured graph (built on the first call)
+    // the per-slice sequence as two captured graphs (built on the first
+    // call): the forward steps, then the sweep
     cudaStream_t cap_stream = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph_f = nullptr, graph_b = nullptr;
+    cudaGraphExec_t gexec_f = nullptr, gexec_b = nullptr;
 };
 
 static bool has_label(const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); }
 
-static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::string& err) {
+static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, int copies, std::string& err) {
     const int n = d.n;
     const int nn = (int)f.nodes.size();
     G.g = Plan();
     G.g.mode = f.mode;
+    G.g.copies = copies;
+    G.plan_inst = copies;
     G.g.vlab = f.vlab;
     G.g.vstride = f.vstride;
     G.g.leaf_sl = f.leaf_sl;
@@ -117,6 +127,17 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
         return o;
     };
     G.fwd = f.nodes;
+    if (copies > 1) {
+        // many copies per launch: the single-copy kernel choices (autotuned,
+        // K splits sized for one copy) give way to the planner's rule with
+        // the copies counted
+        int64_t se = 0;
+        for (Node& nd : G.fwd) {
+            nd.kind = kGeneric;
+            if (f.force_generic || !plan_tile_node(d, G.g, nd, se)) continue;
+            if (!f.no_tensor_cores) make_tensor_core(d, f.mode, nd, se, copies);
+        }
+    }
     G.fwd_order.clear();
     for (const Step& st : f.steps)
         for (int k : st.nodes) G.fwd_order.push_back(k);
@@ -155,7 +176,7 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
             nd.kind = kGeneric;
             const int ca0 = nd.tile.conj_a, cb0 = nd.tile.conj_b;
             if (plan_tile_node(d, G.g, nd, split_elems) && !f.no_tensor_cores)
-                make_tensor_core(d, f.mode, nd, split_elems);
+                make_tensor_core(d, f.mode, nd, split_elems, copies);
             nd.tile.conj_a = ca0;
             nd.tile.conj_b = cb0;
             nd.ws_off = take(nd.size);
@@ -192,18 +213,23 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
     auto cnode = [&](int c) -> const Node& { return c < nn ? G.fwd[c] : G.bwd[c - nn]; };
     std::vector<int> order(G.fwd_order);
     for (int j = 0; j < nb; ++j) order.push_back(nn + j);
+    // levels: the adjoint nodes come after every forward node (the forward
+    // steps form one graph, the sweep another: a caller that just ran the
+    // forward keeps its intermediates and runs the sweep alone)
     std::vector<int> level(ncomb, 0);
-    int max_level = 0;
+    int max_level = 0, fwd_levels = 0;
     for (int c : order) {
         const Node& nd = cnode(c);
-        int l = 0;
+        int l = c < nn ? 0 : fwd_levels;
         for (int v : {nd.ca, nd.cb}) {
             const int pr = producer(v);
             if (pr >= 0) l = std::max(l, level[pr]);
         }
         level[c] = l + 1;
         max_level = std::max(max_level, level[c]);
+        if (c < nn) fwd_levels = max_level;
     }
+    G.level = level;
     std::vector<std::vector<int>> at(max_level + 1);
     for (int c : order) at[level[c]].push_back(c);
     G.steps.clear();
@@ -215,7 +241,7 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
         std::vector<int> singles;
         for (int c : at[L]) {
             const Node& nd = cnode(c);
-            const bool small = wave_node(nd) && !f.no_waves;
+            const bool small = wave_node(nd, G.plan_inst) && !f.no_waves;
             if (!small) {
                 singles.push_back(c);
                 continue;
@@ -244,7 +270,8 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
         std::vector<Step> merged;
         for (Step& st : G.steps) {
             if (st.wave && !merged.empty() && merged.back().wave &&
-                merged.back().item_begin + merged.back().item_count == st.item_begin) {
+                merged.back().item_begin + merged.back().item_count == st.item_begin &&
+                (merged.back().nodes[0] < nn) == (st.nodes[0] < nn)) {  // same phase
                 Step& m = merged.back();
                 m.item_count += st.item_count;
                 m.nodes.insert(m.nodes.end(), st.nodes.begin(), st.nodes.end());
@@ -255,6 +282,8 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, std::
         }
         G.steps = merged;
     }
+    G.n_fwd_steps = 0;
+    while (G.n_fwd_steps < (int)G.steps.size() && G.steps[G.n_fwd_steps].nodes[0] < nn) ++G.n_fwd_steps;
     G.flow_deps.assign(4 * (size_t)std::max(ncomb, 1), -1);
     G.any_flow = false;
     for (const Step& st : G.steps) {
@@ -481,19 +510,28 @@ static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void*
         std::vector<TileArgs> descs(ncomb);
         for (int k = 0; k < nn; ++k) descs[k] = G.tile_f[k];
         for (int j = 0; j < nb; ++j) descs[nn + j] = G.tile_b[j];
-        // instance-major within each step keeps every step's items contiguous
+        // within each step: level by level, every copy's items of a level
+        // before the next level, so that the copies' dependency chains
+        // advance together (a node's children always come earlier)
         std::vector<WaveItem> items;
         items.reserve(G.items.size() * NI);
         for (size_t s = 0; s < G.steps.size(); ++s) {
             const Step& st = G.steps[s];
             G.inst_item_begin[s] = (int)items.size();
             if (!st.wave) continue;
-            for (int i = 0; i < n_inst; ++i)
-                for (int j = 0; j < st.item_count; ++j) {
-                    WaveItem it = G.items[st.item_begin + j];
-                    it.pad = i;
-                    items.push_back(it);
-                }
+            int j0 = 0;
+            while (j0 < st.item_count) {
+                const int L = G.level[G.items[st.item_begin + j0].node];
+                int j1 = j0;
+                while (j1 < st.item_count && G.level[G.items[st.item_begin + j1].node] == L) ++j1;
+                for (int i = 0; i < n_inst; ++i)
+                    for (int j = j0; j < j1; ++j) {
+                        WaveItem it = G.items[st.item_begin + j];
+                        it.pad = i;
+                        items.push_back(it);
+                    }
+                j0 = j1;
+            }
         }
         AL(G.descs_dev, sizeof(TileArgs) * ncomb, "cudaMalloc");
         AL(G.items_dev, sizeof(WaveItem) * std::max<size_t>(items.size(), 1), "cudaMalloc");
@@ -556,6 +594,22 @@ static tn_status alloc_grad(const NetDesc& d, const Plan& f, GradState& G, void*
         }
         UP(G.perm_dev, perm.data(), sizeof(int64_t) * n_out);
     }
+    // root value of every copy (scalar networks), for the keeping forward
+    if (n_out == 1) {
+        const Node& root = G.fwd.back();
+        std::vector<BatchRoot> roots(n_inst);
+        for (int i = 0; i < n_inst; ++i) {
+            roots[i].root = ws + (root.ws_off + (int64_t)i * G.ws_elems) * eb;
+            roots[i].exp = G.exps + (nn - 1) + (int64_t)i * G.n_slots;
+            roots[i].max = G.maxabs + (nn - 1) + (int64_t)i * G.n_slots;
+            roots[i].is_c = cplx ? 1 : 0;
+            roots[i].pad = 0;
+        }
+        AL(G.roots_dev, sizeof(BatchRoot) * n_inst, "cudaMalloc");
+        AL(G.val_dev, sizeof(double) * 2 * n_inst, "cudaMalloc");
+        AL(G.val_exp_dev, sizeof(int64_t) * n_inst, "cudaMalloc");
+        UP(G.roots_dev, roots.data(), sizeof(BatchRoot) * n_inst);
+    }
 #undef AL
 #undef UP
     return TN_OK;
@@ -585,11 +639,19 @@ static void free_grad_device(GradState& G) {
     G.copy_dev = nullptr;
     G.adj_dev = nullptr;
     G.perm_dev = nullptr;
-    if (G.gexec) cudaGraphExecDestroy(G.gexec);
-    if (G.graph) cudaGraphDestroy(G.graph);
-    G.gexec = nullptr;
-    G.graph = nullptr;
+    for (void* q : {(void*)G.roots_dev, (void*)G.val_dev, (void*)G.val_exp_dev})
+        if (q) cudaFree(q);
+    G.roots_dev = nullptr;
+    G.val_dev = nullptr;
+    G.val_exp_dev = nullptr;
+    if (G.gexec_f) cudaGraphExecDestroy(G.gexec_f);
+    if (G.gexec_b) cudaGraphExecDestroy(G.gexec_b);
+    if (G.graph_f) cudaGraphDestroy(G.graph_f);
+    if (G.graph_b) cudaGraphDestroy(G.graph_b);
+    G.gexec_f = G.gexec_b = nullptr;
+    G.graph_f = G.graph_b = nullptr;
     G.n_inst = 0;
+    G.kept = false;
 }
 
 void free_grad(Plan& p) {
@@ -609,19 +671,14 @@ static cudaError_t launch_node(const Node& nd, const GenericArgs& g, const TileA
     return launch_generic(g, c, s);
 }
 
-// One slice for every instance: scale slots and dataflow counters cleared,
-// the schedule's steps, the leaf gathers, and the slice counter advanced.
-static cudaError_t enqueue_grad_slice(const GradState& G, tn_mode mode, bool cplx, cudaStream_t s) {
+// The steps [k0, k1) of the schedule for every instance.
+static cudaError_t enqueue_steps(const GradState& G, int k0, int k1, tn_mode mode, bool cplx, cudaStream_t s) {
     const int nn = (int)G.fwd.size();
     const int ncomb = nn + (int)G.bwd.size();
     const int NI = G.n_inst;
-    // every instance's slots but its root-adjoint slot (set per call)
-    cudaError_t e = NI == 1 ? cudaMemsetAsync(G.maxabs, 0, sizeof(unsigned) * (G.n_slots - 1), s)
-                            : launch_zero_strided(G.maxabs, G.n_slots - 1, G.n_slots, NI, s);
-    if (e == cudaSuccess && G.any_flow)
-        e = cudaMemsetAsync(G.flow_cnt_dev, 0, sizeof(unsigned) * ((size_t)ncomb * NI + G.steps.size()), s);
     const void* const* leaf_tab = reinterpret_cast<const void* const*>(G.img_ptr_dev);
-    for (size_t k = 0; k < G.steps.size() && e == cudaSuccess; ++k) {
+    cudaError_t e = cudaSuccess;
+    for (int k = k0; k < k1 && e == cudaSuccess; ++k) {
         const Step& st = G.steps[k];
         if (st.wave) {
             const WaveItem* it = G.items_dev + G.inst_item_begin[k];
@@ -638,18 +695,64 @@ static cudaError_t enqueue_grad_slice(const GradState& G, tn_mode mode, bool cpl
             e = launch_node(G.bwd[j], G.gen_b[j], G.tile_b[j], mode, cplx, s);
         }
     }
+    return e;
+}
+
+// Zero scale slots [j0, j1) of every instance.
+static cudaError_t zero_slots(const GradState& G, int j0, int j1, cudaStream_t s) {
+    if (j1 <= j0) return cudaSuccess;
+    if (G.n_inst == 1) return cudaMemsetAsync(G.maxabs + j0, 0, sizeof(unsigned) * (j1 - j0), s);
+    return launch_zero_strided(G.maxabs + j0, j1 - j0, G.n_slots, G.n_inst, s);
+}
+
+// Forward half of one slice: forward scale slots and dataflow counters
+// cleared, the forward steps.
+static cudaError_t enqueue_forward(const GradState& G, tn_mode mode, bool cplx, cudaStream_t s) {
+    const int nn = (int)G.fwd.size();
+    const size_t ncomb = (size_t)nn + G.bwd.size();
+    const size_t NI = (size_t)G.n_inst;
+    cudaError_t e = zero_slots(G, 0, nn, s);
+    if (e == cudaSuccess && G.any_flow) e = cudaMemsetAsync(G.flow_cnt_dev, 0, sizeof(unsigned) * nn * NI, s);
+    if (e == cudaSuccess && G.any_flow)
+        e = cudaMemsetAsync(G.flow_cnt_dev + ncomb * NI, 0, sizeof(unsigned) * G.n_fwd_steps, s);
+    if (e == cudaSuccess) e = enqueue_steps(G, 0, G.n_fwd_steps, mode, cplx, s);
+    return e;
+}
+
+// Sweep half of one slice: adjoint scale slots (all but the root's, set
+// per call) and counters cleared, the adjoint steps, the leaf gathers, and
+// the slice counter advanced.
+static cudaError_t enqueue_sweep(const GradState& G, tn_mode mode, bool cplx, cudaStream_t s) {
+    const int nn = (int)G.fwd.size();
+    const size_t ncomb = (size_t)nn + G.bwd.size();
+    const size_t NI = (size_t)G.n_inst;
+    cudaError_t e = zero_slots(G, nn, G.n_slots - 1, s);
+    if (e == cudaSuccess && G.any_flow)
+        e = cudaMemsetAsync(G.flow_cnt_dev + nn * NI, 0, sizeof(unsigned) * (ncomb - nn) * NI, s);
+    if (e == cudaSuccess && G.any_flow)
+        e = cudaMemsetAsync(G.flow_cnt_dev + ncomb * NI + G.n_fwd_steps, 0,
+                            sizeof(unsigned) * (G.steps.size() - G.n_fwd_steps), s);
+    if (e == cudaSuccess) e = enqueue_steps(G, G.n_fwd_steps, (int)G.steps.size(), mode, cplx, s);
     if (e == cudaSuccess)
-        e = launch_leaf_grads(G.lg_dev, (int)G.acc_off.size(), G.max_grad_n, NI, cplx, s);
+        e = launch_leaf_grads(G.lg_dev, (int)G.acc_off.size(), G.max_grad_n, G.n_inst, cplx, s);
     if (e == cudaSuccess) e = launch_advance(G.ctl, s);
     return e;
 }
 
-tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_mem, int64_t adj_exp2,
-                   const int64_t* adj_exp2_dev, void* const* grads, bool accumulate, int n_inst,
-                   const int64_t* leaf_inst_stride, cudaStream_t stream, std::string& err) {
-    const int n = d.n;
-    const bool cplx = d.is_complex();
-    const int cf = cplx ? 2 : 1;
+static cudaError_t capture(GradState& G, bool fwd, tn_mode mode, bool cplx) {
+    cudaGraph_t& g = fwd ? G.graph_f : G.graph_b;
+    cudaGraphExec_t& x = fwd ? G.gexec_f : G.gexec_b;
+    cudaError_t e = cudaSuccess;
+    if (!G.cap_stream) e = cudaStreamCreateWithFlags(&G.cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(G.cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t e1 = fwd ? enqueue_forward(G, mode, cplx, G.cap_stream) : enqueue_sweep(G, mode, cplx, G.cap_stream);
+    const cudaError_t e2 = cudaStreamEndCapture(G.cap_stream, &g);
+    if (e1 != cudaSuccess) return e1;
+    if (e2 != cudaSuccess) return e2;
+    return cudaGraphInstantiate(&x, g, 0);
+}
+
 #define CK(x)                                                          \
     do {                                                               \
         cudaError_t e_ = (x);                                          \
@@ -658,6 +761,12 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
             return e_ == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA; \
         }                                                              \
     } while (0)
+
+// Checks the call, (re)builds the sweep's plan and device state for this
+// copy count and shared/varying pattern, and captures the two graphs.
+static tn_status prepare(NetDesc& d, Plan& p, void* unit, int n_inst, const int64_t* leaf_inst_stride,
+                         cudaStream_t stream, std::vector<char>& varying, std::string& err) {
+    const int n = d.n;
     if (n_inst < 1) {
         err = "tn_contract_grad: n_inst < 1";
         return TN_EINVAL;
@@ -667,7 +776,7 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
             err = "tn_contract_grad: leaves must be device pointers";
             return TN_EUNSUPPORTED;
         }
-    std::vector<char> varying(n, 0);
+    varying.assign(n, 0);
     if (n_inst > 1 && leaf_inst_stride)
         for (int v = 0; v < n; ++v) {
             if (leaf_inst_stride[v] < 0 || (leaf_inst_stride[v] > 0 && leaf_inst_stride[v] < d.leaves[v].size)) {
@@ -684,9 +793,13 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
               "its per-slice work is already a CUDA graph)";
         return TN_EUNSUPPORTED;
     }
+    if (p.grad && p.grad->plan_inst != n_inst) {
+        CK(cudaStreamSynchronize(stream));
+        free_grad(p);  // kernels and K splits are planned per copy count
+    }
     if (!p.grad) {
         GradState* G = new GradState;
-        tn_status st = build_grad(d, p, *G, err);
+        tn_status st = build_grad(d, p, *G, n_inst, err);
         if (st != TN_OK) {
             delete G;
             return st;
@@ -695,7 +808,7 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
     }
     GradState& G = *p.grad;
     if (G.n_inst != n_inst || G.varying != varying) {
-        // another instance layout: the device state and graph are rebuilt
+        // another instance layout: the device state and graphs are rebuilt
         CK(cudaStreamSynchronize(stream));
         free_grad_device(G);
         tn_status st = alloc_grad(d, p, G, unit, n_inst, varying, err);
@@ -704,17 +817,22 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
             return st;
         }
     }
-    const int nn = (int)G.fwd.size();
-    const int root_v = n + nn - 1;
-    const size_t eb = d.elem_bytes();
-    // per-call table: the leaves into the image, then the gradients out
-    std::vector<CopyEntry> tab;
-    tab.reserve((size_t)2 * n * n_inst);
-    for (int v = 0; v < n; ++v) {
+    const bool cplx = d.is_complex();
+    if (!G.gexec_f) CK(capture(G, true, p.mode, cplx));
+    if (!G.gexec_b) CK(capture(G, false, p.mode, cplx));
+    return TN_OK;
+}
+
+// Gather entries of the per-call copy table: the caller's leaves (copy i of
+// a varying leaf at + i * stride) into the leaf image.
+static void gather_entries(const NetDesc& d, const GradState& G, int n_inst, const int64_t* leaf_inst_stride,
+                           std::vector<CopyEntry>& tab) {
+    const int cf = d.is_complex() ? 2 : 1;
+    for (int v = 0; v < d.n; ++v) {
         const int64_t nf = d.leaves[v].size * cf;
         const float* src = static_cast<const float*>(d.leaves[v].ptr);
         float* dst = G.leaf_img + G.img_off[v];
-        if (!varying[v]) {
+        if (!G.varying[v]) {
             tab.push_back(CopyEntry{src, dst, nf, 0, 1, 0});
         } else {
             for (int i = 0; i < n_inst; ++i)
@@ -722,6 +840,73 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
                                         1, 0});
         }
     }
+}
+
+static int64_t image_max_floats(const NetDesc& d, const GradState& G, int n_inst) {
+    const int cf = d.is_complex() ? 2 : 1;
+    int64_t mx = 0;
+    for (int v = 0; v < d.n; ++v)
+        mx = std::max(mx, G.varying[v] ? G.img_is[v] * (n_inst - 1) + d.leaves[v].size * cf : d.leaves[v].size * cf);
+    return mx;
+}
+
+tn_status run_grad_forward(NetDesc& d, Plan& p, void* unit, int n_inst, const int64_t* leaf_inst_stride,
+                           double* out, int64_t* out_exp2, int out_mem, cudaStream_t stream, std::string& err) {
+    if (p.d_sliced != 1 || p.n_out != 1) {
+        err = "tn_contract_instances_keep: unsliced scalar networks only";
+        return TN_EUNSUPPORTED;
+    }
+    std::vector<char> varying;
+    tn_status st = prepare(d, p, unit, n_inst, leaf_inst_stride, stream, varying, err);
+    if (st != TN_OK) return st;
+    GradState& G = *p.grad;
+    G.kept = false;
+    std::vector<CopyEntry> tab;
+    gather_entries(d, G, n_inst, leaf_inst_stride, tab);
+    CK(cudaMemcpyAsync(G.copy_dev, tab.data(), sizeof(CopyEntry) * tab.size(), cudaMemcpyHostToDevice, stream));
+    CK(launch_copy_table(G.copy_dev, (int)tab.size(), G.max_leaf_floats, stream));
+    CK(launch_leaf_max(G.img_ptr_dev, G.leaf_nfloat_dev, G.leafmax, d.n, stream, image_max_floats(d, G, n_inst)));
+    CK(launch_begin_call(G.ctl, 0, 1, nullptr, 0, stream));
+    CK(cudaGraphLaunch(G.gexec_f, stream));
+    const bool host = out_mem == TN_MEM_HOST;
+    CK(launch_batch_finish(G.roots_dev, n_inst, host ? G.val_dev : out, host ? G.val_exp_dev : out_exp2, nullptr,
+                           nullptr, nullptr, stream));
+    if (host) {
+        CK(cudaMemcpyAsync(out, G.val_dev, sizeof(double) * 2 * n_inst, cudaMemcpyDeviceToHost, stream));
+        CK(cudaMemcpyAsync(out_exp2, G.val_exp_dev, sizeof(int64_t) * n_inst, cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+    }
+    G.kept = true;
+    return TN_OK;
+}
+
+tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_mem, int64_t adj_exp2,
+                   const int64_t* adj_exp2_dev, void* const* grads, bool accumulate, bool kept_forward,
+                   int n_inst, const int64_t* leaf_inst_stride, cudaStream_t stream, std::string& err) {
+    const int n = d.n;
+    const bool cplx = d.is_complex();
+    const int cf = cplx ? 2 : 1;
+    if (kept_forward && (!p.grad || !p.grad->kept || p.grad->n_inst != n_inst)) {
+        err = "tn_contract_grad: TN_GRAD_KEPT_FORWARD without a preceding tn_contract_instances_keep "
+              "of this tree, mode and copy count";
+        return TN_EINVAL;
+    }
+    std::vector<char> varying;
+    tn_status st = prepare(d, p, unit, n_inst, leaf_inst_stride, stream, varying, err);
+    if (st != TN_OK) return st;
+    GradState& G = *p.grad;
+    if (kept_forward && G.varying != varying) {
+        err = "tn_contract_grad: TN_GRAD_KEPT_FORWARD with other leaf strides than the kept forward";
+        return TN_EINVAL;
+    }
+    const int nn = (int)G.fwd.size();
+    const int root_v = n + nn - 1;
+    const size_t eb = d.elem_bytes();
+    // per-call table: the leaves into the image (unless kept), then the
+    // gradients out
+    std::vector<CopyEntry> tab;
+    tab.reserve((size_t)2 * n * n_inst);
+    if (!kept_forward) gather_entries(d, G, n_inst, leaf_inst_stride, tab);
     const int n_gather = (int)tab.size();
     for (int v = 0; v < n; ++v) {
         if (!grads[v]) continue;
@@ -738,13 +923,13 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
     }
     const int n_scatter = (int)tab.size() - n_gather;
     // pageable source: the copy is staged before the call returns
-    CK(cudaMemcpyAsync(G.copy_dev, tab.data(), sizeof(CopyEntry) * tab.size(), cudaMemcpyHostToDevice,
-                       stream));
-    CK(launch_copy_table(G.copy_dev, n_gather, G.max_leaf_floats, stream));
-    int64_t mx = 0;
-    for (int v = 0; v < n; ++v)
-        mx = std::max(mx, varying[v] ? G.img_is[v] * (n_inst - 1) + d.leaves[v].size * cf : d.leaves[v].size * cf);
-    CK(launch_leaf_max(G.img_ptr_dev, G.leaf_nfloat_dev, G.leafmax, n, stream, mx));
+    if (!tab.empty())
+        CK(cudaMemcpyAsync(G.copy_dev, tab.data(), sizeof(CopyEntry) * tab.size(), cudaMemcpyHostToDevice,
+                           stream));
+    if (!kept_forward) {
+        CK(launch_copy_table(G.copy_dev, n_gather, G.max_leaf_floats, stream));
+        CK(launch_leaf_max(G.img_ptr_dev, G.leaf_nfloat_dev, G.leafmax, n, stream, image_max_floats(d, G, n_inst)));
+    }
     // root adjoints
     const double* adj_src = adj;
     if (adj_mem == TN_MEM_HOST) {
@@ -768,19 +953,18 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
     CK(launch_root_adjoint(ra, n_inst, stream));
     CK(cudaMemsetAsync(G.gacc, 0, sizeof(float) * G.acc_floats * n_inst, stream));
     CK(launch_begin_call(G.ctl, 0, p.d_sliced, nullptr, 0, stream));
-    if (!G.gexec) {
-        if (!G.cap_stream) CK(cudaStreamCreateWithFlags(&G.cap_stream, cudaStreamNonBlocking));
-        CK(cudaStreamBeginCapture(G.cap_stream, cudaStreamCaptureModeThreadLocal));
-        const cudaError_t e1 = enqueue_grad_slice(G, p.mode, cplx, G.cap_stream);
-        const cudaError_t e2 = cudaStreamEndCapture(G.cap_stream, &G.graph);
-        CK(e1);
-        CK(e2);
-        CK(cudaGraphInstantiate(&G.gexec, G.graph, 0));
+    if (kept_forward) {
+        CK(cudaGraphLaunch(G.gexec_b, stream));
+    } else {
+        G.kept = false;  // the workspace is rewritten slice by slice
+        for (int64_t s = 0; s < p.d_sliced; ++s) {
+            CK(cudaGraphLaunch(G.gexec_f, stream));
+            CK(cudaGraphLaunch(G.gexec_b, stream));
+        }
     }
-    for (int64_t s = 0; s < p.d_sliced; ++s) CK(cudaGraphLaunch(G.gexec, stream));
     if (n_scatter > 0) CK(launch_copy_table(G.copy_dev + n_gather, n_scatter, G.max_leaf_floats, stream));
-#undef CK
     return TN_OK;
 }
+#undef CK
 
 }  // namespace tn

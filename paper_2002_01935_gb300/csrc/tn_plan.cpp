@@ -188,11 +188,11 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems, 
         TM = 4;
         TN = 1024;
         TK = 4;
-    } else if (t.nm <= 4 && t.nn >= 8) {
+    } else if (t.nm <= 5 && t.nn >= 8) {  // 64-row tiles would run half empty at M = 32
         t.cfg = kTile16x256;
         TM = 16;
         TN = 256;
-    } else if (t.nn <= 4 && t.nm >= 8) {
+    } else if (t.nn <= 5 && t.nm >= 8) {
         t.cfg = kTile256x16;
         TM = 256;
         TN = 16;
@@ -205,7 +205,7 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems, 
         const int64_t tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN) * t.nbatch;
         const int64_t ktiles = (K + TK - 1) / TK;
         int split = 1;
-        while (tiles * split < 2 * 152 && split * 16 <= ktiles && split < 64 &&
+        while (tiles * p.copies * split < 2 * 152 && split * 16 <= ktiles && split < 64 &&
                t.nbatch * split * 2 <= 65535)
             split *= 2;
         t.split = split;
@@ -216,7 +216,7 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems, 
         const int64_t outs = M * N * t.nbatch;
         int split = 1;
         // one K tile (1024 entries) or more per part; about 256 parts in all
-        while (outs * split < 256 && (K / (split * 2)) >= 1024 && split < 1024) split *= 2;
+        while (outs * p.copies * split < 256 && (K / (split * 2)) >= 1024 && split < 1024) split *= 2;
         t.split = split;
         t.kchunk = ((K / split + 255) / 256) * 256;
         if (split > 1) split_elems = std::max(split_elems, (int64_t)split * outs);
@@ -455,7 +455,7 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
         Node& nd = p.nodes[k];
         nd.kind = kGeneric;
         if (p.force_generic || !plan_tile(d, p, nd, split_elems)) continue;
-        if (!p.no_tensor_cores) make_tensor_core(d, p.mode, nd, split_elems);
+        if (!p.no_tensor_cores) make_tensor_core(d, p.mode, nd, split_elems, p.copies);
     }
     p.split_bytes = (split_elems * (int64_t)d.elem_bytes() + 1023) / 1024 * 1024;
     // ---- launch schedule: tree levels; per level one wave launch for the
@@ -478,7 +478,7 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
         for (size_t k = 0; k < p.nodes.size(); ++k) {
             if (level[n + k] != L) continue;
             const Node& nd = p.nodes[k];
-            const bool small = wave_node(nd) && !p.no_waves;
+            const bool small = wave_node(nd, p.copies) && !p.no_waves;
             if (!small) {
                 singles.push_back((int)k);
                 continue;
@@ -781,18 +781,33 @@ static tn_status configure_instances(const NetDesc& d, Plan& p, int G, int step,
         for (int k = 0; k < nn; ++k) descs[k] = p.nodes[k].tile;
         std::vector<WaveItem> items;
         items.reserve(p.items.size() * G);
-        // instance-major within each step keeps every step's items contiguous
+        // within each step: level by level, every instance's items of a
+        // level before the next level (the instances' dependency chains
+        // advance together; a node's children always come earlier)
+        std::vector<int> level(nn, 0);
+        for (int k = 0; k < nn; ++k) {
+            const Node& nd = p.nodes[k];
+            const int la = nd.ca >= n ? level[nd.ca - n] : 0, lb = nd.cb >= n ? level[nd.cb - n] : 0;
+            level[k] = 1 + std::max(la, lb);
+        }
         p.inst_items_begin.assign(p.steps.size(), 0);
         for (size_t s = 0; s < p.steps.size(); ++s) {
             const Step& st = p.steps[s];
             p.inst_items_begin[s] = (int)items.size();
             if (!st.wave) continue;
-            for (int i = 0; i < G; ++i)
-                for (int j = 0; j < st.item_count; ++j) {
-                    WaveItem it = p.items[st.item_begin + j];
-                    it.pad = i;
-                    items.push_back(it);
-                }
+            int j0 = 0;
+            while (j0 < st.item_count) {
+                const int L = level[p.items[st.item_begin + j0].node];
+                int j1 = j0;
+                while (j1 < st.item_count && level[p.items[st.item_begin + j1].node] == L) ++j1;
+                for (int i = 0; i < G; ++i)
+                    for (int j = j0; j < j1; ++j) {
+                        WaveItem it = p.items[st.item_begin + j];
+                        it.pad = i;
+                        items.push_back(it);
+                    }
+                j0 = j1;
+            }
         }
         cudaError_t e = cudaMemcpy(p.descs_dev, descs.data(), sizeof(TileArgs) * nn, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
@@ -1163,7 +1178,7 @@ tn_status make_generic_args_node(const NetDesc& d, const Plan& p, const Node& nd
 // and K >= 16.  A complex node puts its larger operand in the row role (the
 // column operand is expanded to two real rows per column).  The packed
 // operands live in the shared P buffer, which grows to hold them.
-bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_elems) {
+bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_elems, int copies) {
     TileArgs& t = nd.tile;
     if (mode == TN_MODE_FP32 || t.cfg == kTileDot || t.nk < 4 || t.nbatch > 65535) return false;
     const bool c = d.is_complex();
@@ -1182,7 +1197,7 @@ bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_e
     // each); split only while every part keeps >= 8 k-blocks
     {
         const TcGeom g0 = tc_geom(t, c, prec);
-        const double tiles = (double)t.nbatch * (g0.rows_r / 128) * (g0.cols_q / g0.bn);
+        const double tiles = (double)t.nbatch * (g0.rows_r / 128) * (g0.cols_q / g0.bn) * copies;
         double best = 0.0;
         for (int s = 1; s <= 16 && g0.nkb / s >= 8; s *= 2) {
             const double w = tiles * s / 152.0;

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -75,9 +76,11 @@ struct Step {
 // thread), so that an item's chain of dependent loads does not grow with K
 // -- on the dataflow's critical path every item counts -- and at most 1024
 // outputs.
-inline bool wave_node(const Node& nd) {
-    return nd.kind == kTiled && nd.tile.cfg != kTileDot && nd.size <= (1 << 16) && nd.vc <= 22.0 &&
-           nd.tile.nk <= 14;
+inline bool wave_node(const Node& nd, int copies = 1) {
+    // with several copies per launch the 2^22 bound is on all copies together:
+    // bigger launches belong to the tiled and tensor-core kernels
+    return nd.kind == kTiled && nd.tile.cfg != kTileDot && nd.size <= (1 << 16) &&
+           nd.vc + std::log2((double)copies) <= 22.0 && nd.tile.nk <= 14;
 }
 inline int64_t wave_chunk(const Node& nd) {
     const int sh = nd.tile.nk >= 12 ? 0 : 12 - nd.tile.nk;
@@ -98,6 +101,7 @@ struct Plan {
     bool force_generic = false;  // every node on the generic kernel
     bool no_waves = false;       // one launch per node
     bool no_tensor_cores = false;  // reduced-precision modes on CUDA cores only
+    int copies = 1;  // copies sharing every node launch: K splits fill the GPU with tiles x copies
     std::vector<int32_t> pairs;
     std::vector<int64_t> sliced_ids;
     std::vector<int> sliced;  // dense
@@ -159,7 +163,7 @@ struct Plan {
 tn_status build_plan(const NetDesc& d, Plan& p, std::string& err);
 Node build_node(const NetDesc& d, const Plan& p, int id, int a, int b, const std::vector<int>& keep);
 bool plan_tile_node(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems);
-bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_elems);
+bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_elems, int copies = 1);
 // Autotuner variant code of the tensor-core kernel (tile shapes use TileCfg).
 constexpr int kVariantTC = 8;
 // Times every candidate kernel of the nodes that run alone in a launch step
@@ -180,9 +184,15 @@ tn_status run_instances(NetDesc& d, Plan& p, void* unit, int n_inst, const int64
 // leaf_inst_stride[v] elements (NULL or 0: shared), adjoint i at adj + i *
 // (output size), exponent adj_exp2 + adj_exp2_dev[i]; a shared leaf's
 // gradient is the sum over the instances, a varying leaf's is per instance.
+// kept_forward: the workspace holds the forward of the last
+// run_grad_forward (same copies and leaves): only the sweep runs.
 tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_mem, int64_t adj_exp2,
-                   const int64_t* adj_exp2_dev, void* const* grads, bool accumulate, int n_inst,
-                   const int64_t* leaf_inst_stride, cudaStream_t stream, std::string& err);
+                   const int64_t* adj_exp2_dev, void* const* grads, bool accumulate, bool kept_forward,
+                   int n_inst, const int64_t* leaf_inst_stride, cudaStream_t stream, std::string& err);
+// Forward of n_inst copies (unsliced scalar networks) in the sweep's state,
+// every intermediate kept; values as tn_contract_instances.
+tn_status run_grad_forward(NetDesc& d, Plan& p, void* unit, int n_inst, const int64_t* leaf_inst_stride,
+                           double* out, int64_t* out_exp2, int out_mem, cudaStream_t stream, std::string& err);
 void plan_info(const NetDesc& d, const Plan& p, double out[8]);
 void free_device(Plan& p);  // releases device state; the host plan stays valid
 void free_grad(Plan& p);

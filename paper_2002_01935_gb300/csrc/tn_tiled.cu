@@ -520,7 +520,9 @@ __global__ void __launch_bounds__(256)
            const int4* deps, unsigned* done, unsigned* head, int G) {
     using T = typename VT<CPLX>::T;
     __shared__ TileArgs d;
-    __shared__ int64_t kA[256], kB[256];
+    // K offsets: low 8 bits of the K index from kA / kB, the rest (at most
+    // 6 more bits: wave nodes have nk <= 14) from kAh / kBh
+    __shared__ int64_t kA[256], kB[256], kAh[64], kBh[64];
     __shared__ T red[256];
     __shared__ int cur;
     const int tid = threadIdx.x;
@@ -546,11 +548,17 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
         const View vw = inst_view(d, it.pad, (int)sizeof(T));
         const int kt = d.nk < 8 ? (int)(1ll << d.nk) : 256;  // table covers k & 255
-        if (vw.live)
+        const int kh = d.nk > 8 && d.nk <= 14 ? (int)(1ll << (d.nk - 8)) : 0;  // k >> 8
+        if (vw.live) {
             for (int t = tid; t < kt; t += 256) {
                 kA[t] = scatter_bits(t, d.a_k, d.nk);
                 kB[t] = scatter_bits(t, d.b_k, d.nk);
             }
+            for (int h = tid; h < kh; h += 256) {
+                kAh[h] = scatter_bits((int64_t)h << 8, d.a_k, d.nk);
+                kBh[h] = scatter_bits((int64_t)h << 8, d.b_k, d.nk);
+            }
+        }
         // ---- then wait for children computed in this launch
         if (deps != nullptr && tid == 0) {
             const int4 dp = deps[it.node];
@@ -598,6 +606,9 @@ __global__ void __launch_bounds__(256)
                     if (d.nk < 8) {
                         ka = kA[t];
                         kb2 = kB[t];
+                    } else if (kh > 0) {
+                        ka = kA[t & 255] + kAh[t >> 8];
+                        kb2 = kB[t & 255] + kBh[t >> 8];
                     } else {
                         const int64_t hi = t & ~255ll;
                         ka = kA[t & 255] + (hi ? scatter_bits(hi, d.a_k, d.nk) : 0);

@@ -336,3 +336,56 @@ def test_grad_instances_refuses_overlapping_copies(torch):
     with pytest.raises(binding.TNError):
         tnw.grad_instances(pairs, sliced, "fp32", 2, strides, adj)
     tnw.close()
+
+
+def _stacked_setup(torch, seed, B):
+    net, pairs, sliced, ts, tnw = _setup(torch, seed=seed, n_open=0)
+    rng = np.random.default_rng(seed)
+    var = [0, 3]
+    lv = list(ts)
+    strides = [0] * len(ts)
+    for v in var:
+        lv[v] = torch.stack([ts[v] * np.float32(1.0 + 0.2 * rng.standard_normal()) for _ in range(B)])
+        strides[v] = ts[v].numel()
+    tnw.set_tensors(lv)
+    adjs = torch.from_numpy(rng.standard_normal((B, 2)).view(np.complex128).reshape(B)).cuda()
+    return net, pairs, tnw, lv, strides, adjs
+
+
+def test_kept_forward_matches_recompute(torch):
+    """grad_instances after contract_instances_keep (sweep only) against the
+    full call (forward recomputed): identical gradients; the kept values
+    against tn_contract_instances."""
+    B = 4
+    net, pairs, tnw, lv, strides, adjs = _stacked_setup(torch, 23, B)
+    for mode in ("fp32", "tf32_split"):
+        full = [g.cpu().numpy() for g in tnw.grad_instances(pairs, [], mode, B, strides, adjs)]
+        m, e, token = tnw.contract_instances_keep(pairs, mode, B, strides)
+        kept = [g.cpu().numpy() for g in tnw.grad_instances(pairs, [], mode, B, strides, adjs, kept_forward=token)]
+        for a, b in zip(full, kept):
+            assert np.array_equal(a, b)
+        m2, e2 = tnw.contract_instances(pairs, mode, B, strides)
+        v1 = (m[:, 0] + 1j * m[:, 1]).cpu().numpy() * np.exp2(e.cpu().numpy().astype(float))
+        v2 = (m2[:, 0] + 1j * m2[:, 1]).cpu().numpy() * np.exp2(e2.cpu().numpy().astype(float))
+        assert np.max(np.abs(v1 - v2)) <= 1e-5 * np.max(np.abs(v2))
+    tnw.close()
+
+
+def test_kept_forward_refused_when_stale(torch):
+    """After another gradient call the kept forward is gone: the C-ABI
+    refuses the flag, and the binding falls back to the full call."""
+    from paper_2002_01935_gb300 import binding
+    B = 3
+    net, pairs, tnw, lv, strides, adjs = _stacked_setup(torch, 24, B)
+    ref = [g.cpu().numpy() for g in tnw.grad_instances(pairs, [], "fp32", B, strides, adjs)]
+    m, e, token = tnw.contract_instances_keep(pairs, "fp32", B, strides)
+    tnw.grad_instances(pairs, [], "fp32", B, strides, adjs * 2)  # rewrites the sweep's workspace
+    gp = [torch.empty_like(t).data_ptr() for t in lv]
+    with pytest.raises(binding.TNError):
+        binding.tn_contract_grad_instances(tnw.h, pairs, [], 0, B, strides, adjs.data_ptr(), binding.TN_MEM_DEVICE,
+                                           0, 0, gp, binding.TN_GRAD_KEPT_FORWARD,
+                                           torch.cuda.current_stream().cuda_stream)
+    got = [g.cpu().numpy() for g in tnw.grad_instances(pairs, [], "fp32", B, strides, adjs, kept_forward=token)]
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+    tnw.close()
