@@ -421,7 +421,7 @@ def run_network(args, torch, dist, rank, world, local):
     tuned = None
     if not args.no_autotune:
         t0 = time.perf_counter()
-        ch = tnw.autotune(pairs, sliced, mode, reps=3)
+        ch = tnw.autotune(pairs, sliced, mode, reps=10)
         tuned = {"seconds": round(time.perf_counter() - t0, 3), "tensor_core": ch.count(8),
                  "tile_shapes": {n: ch.count(v) for v, n in
                                  ((1, "64x64"), (2, "16x256"), (3, "4x1024"), (4, "256x16"), (6, "128x64"))
@@ -494,7 +494,7 @@ def run_network(args, torch, dist, rank, world, local):
               for t in net.tensors]
         htn = binding.TensorNetwork(net.labels, net.dims, net.open, hl, complex_=cplx)
         if not args.no_autotune:
-            htn.autotune(pairs, sliced, mode, reps=3)
+            htn.autotune(pairs, sliced, mode, reps=10)
         odt = torch.complex128 if cplx else torch.float64
         hout = torch.empty(tnw.out_shape, dtype=odt).pin_memory()
         hexp = torch.empty((), dtype=torch.int64).pin_memory()
@@ -536,7 +536,7 @@ def run_network(args, torch, dist, rank, world, local):
         reps = min(args.steps, 5) if args.workload == "circuit7x7" else args.steps
         for md in MODES:
             if not args.no_autotune:
-                tnw.autotune(pairs, sliced, md, reps=3)
+                tnw.autotune(pairs, sliced, md, reps=10)
             for _ in range(2):
                 call(md)
             es, ee2 = device_events(torch, stream, reps), device_events(torch, stream, reps)

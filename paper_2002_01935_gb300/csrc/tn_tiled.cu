@@ -46,9 +46,12 @@ __device__ __forceinline__ int64_t scatter_bits(uint64_t x, const uint8_t* sh, i
     return o;
 }
 
+// Scale slots are read through L2 (ld.global.cg): inside a dataflow launch
+// other CTAs write them, and a line an earlier item left in this SM's L1
+// could be stale.
 __device__ __forceinline__ int exp_of(const unsigned* slot) {
     if (slot == nullptr) return 0;
-    float m = __uint_as_float(*slot);
+    float m = __uint_as_float(__ldcg(slot));
     if (!(m > 0.f)) return 0;
     int e;
     frexpf(m, &e);
@@ -156,7 +159,28 @@ __device__ __forceinline__ Scales node_scales(const ScaleIO& sio, bool write_exp
     const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
     const int cA = max(-120, min(120, eA)), cB = max(-120, min(120, eB));
     if (write_exp && sio.exp_c)
-        *sio.exp_c = (sio.exp_a ? *sio.exp_a : 0) + (sio.exp_b ? *sio.exp_b : 0) + eA + eB;
+        *sio.exp_c = (sio.exp_a ? __ldcg(sio.exp_a) : 0) + (sio.exp_b ? __ldcg(sio.exp_b) : 0) + eA + eB;
+    Scales s;
+    s.fa = ldexpf(1.f, -cA);
+    s.fb = ldexpf(1.f, -cB);
+    s.resid = (eA - cA) + (eB - cB);
+    return s;
+}
+
+// node_scales from values already read: the children's max bits and
+// exponents (0 where absent); exp_c (may be null) receives the node's
+// exponent.
+__device__ __forceinline__ Scales scales_from(unsigned ma, unsigned mb, int64_t ea, int64_t eb, int64_t* exp_c) {
+    auto ex = [](unsigned bits) {
+        const float m = __uint_as_float(bits);
+        if (!(m > 0.f)) return 0;
+        int e;
+        frexpf(m, &e);
+        return e;
+    };
+    const int eA = ex(ma), eB = ex(mb);
+    const int cA = max(-120, min(120, eA)), cB = max(-120, min(120, eB));
+    if (exp_c) *exp_c = ea + eb + eA + eB;
     Scales s;
     s.fa = ldexpf(1.f, -cA);
     s.fb = ldexpf(1.f, -cB);
@@ -335,30 +359,46 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
     }
 }
 
-// Fixed-order sum of the K-split partials, then the node epilogue.
+// Sums the K-split partials of a node in a fixed order and applies its
+// epilogue.  G threads share one output (G = 1 when the outputs alone fill
+// the GPU): thread g sums splits [g*split/G, (g+1)*split/G) in eight
+// independent chains, then the G sums are added in g order.
 template <bool CPLX>
-__global__ void __launch_bounds__(256) k_split_reduce(const __grid_constant__ TileArgs a) {
+__global__ void __launch_bounds__(256) k_split_reduce(const __grid_constant__ TileArgs a, int G) {
     using T = typename VT<CPLX>::T;
+    __shared__ T red[256];
     const int64_t plane_sz = (int64_t)a.nbatch << (a.nm + a.nn);
     const View vw = inst_view(a, blockIdx.y, (int)sizeof(T));
     if (!vw.live) return;
     const Scales sc = node_scales(vw.sc, blockIdx.x == 0 && threadIdx.x == 0);
     const T* P = reinterpret_cast<const T*>(vw.P);
     T* C = reinterpret_cast<T*>(vw.C);
+    const int tid = threadIdx.x, g = tid % G, per_blk = 256 / G;
+    const int s0 = (int)((int64_t)a.split * g / G), s1 = (int)((int64_t)a.split * (g + 1) / G);
     float lmax = 0.f;
-    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < plane_sz;
-         o += (int64_t)gridDim.x * blockDim.x) {
-        // fixed order: eight independent partial chains, then combined
-        T part[8];
+    for (int64_t ob = (int64_t)blockIdx.x * per_blk; ob < plane_sz; ob += (int64_t)gridDim.x * per_blk) {
+        const int64_t o = ob + tid / G;
+        T v = zero<T>();
+        if (o < plane_sz) {
+            T part[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) part[q] = zero<T>();
-        int sp = 0;
-        for (; sp + 8 <= a.split; sp += 8)
+            for (int q = 0; q < 8; ++q) part[q] = zero<T>();
+            int sp = s0;
+            for (; sp + 8 <= s1; sp += 8)
 #pragma unroll
-            for (int q = 0; q < 8; ++q) part[q] = add(part[q], P[(int64_t)(sp + q) * plane_sz + o]);
-        for (int q = 0; sp < a.split; ++sp, ++q) part[q] = add(part[q], P[(int64_t)sp * plane_sz + o]);
-        T v = add(add(add(part[0], part[1]), add(part[2], part[3])),
-                  add(add(part[4], part[5]), add(part[6], part[7])));
+                for (int q = 0; q < 8; ++q) part[q] = add(part[q], P[(int64_t)(sp + q) * plane_sz + o]);
+            for (int q = 0; sp < s1; ++sp, ++q) part[q] = add(part[q], P[(int64_t)sp * plane_sz + o]);
+            v = add(add(add(part[0], part[1]), add(part[2], part[3])),
+                    add(add(part[4], part[5]), add(part[6], part[7])));
+        }
+        if (G > 1) {  // uniform over the block: every thread runs the same iterations
+            red[tid] = v;
+            __syncthreads();
+            if (g == 0)
+                for (int q = 1; q < G; ++q) v = add(v, red[tid + q]);
+            __syncthreads();
+        }
+        if (g != 0 || o >= plane_sz) continue;
         if (sc.resid) {
             if constexpr (CPLX) {
                 v.x = ldexpf(v.x, -sc.resid);
@@ -508,6 +548,17 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a,
 // other CTAs of the launch produced are read through L2 (ld.global.cg).
 constexpr long long kFlowWaitCycles = 4000000000ll;  // ~2 s
 
+// Completion counters: the producer's release add (after a CTA barrier, so
+// it covers the whole CTA's writes) pairs with the consumer's acquire load.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 template <bool CPLX>
 __device__ __forceinline__ typename VT<CPLX>::T ld_cg(const typename VT<CPLX>::T* p) {
     if constexpr (CPLX) return __ldcg(reinterpret_cast<const float2*>(p));
@@ -559,6 +610,19 @@ __global__ void __launch_bounds__(256)
                 kBh[h] = scatter_bits((int64_t)h << 8, d.b_k, d.nk);
             }
         }
+        // operand bases need only the descriptor and the leaf table
+        const int64_t isz = (int64_t)sizeof(T);
+        const T* A = nullptr;
+        const T* B = nullptr;
+        int64_t sA = 0, sB = 0;
+        if (vw.live) {
+            A = reinterpret_cast<const T*>(
+                d.a_leaf >= 0 ? (const char*)leaf_ptrs[d.a_leaf] + (int64_t)it.pad * d.in.a_is * isz : vw.A);
+            B = reinterpret_cast<const T*>(
+                d.b_leaf >= 0 ? (const char*)leaf_ptrs[d.b_leaf] + (int64_t)it.pad * d.in.b_is * isz : vw.B);
+            sA = slice_off(d.sla, vw.slice);
+            sB = slice_off(d.slb, vw.slice);
+        }
         // ---- then wait for children computed in this launch
         if (deps != nullptr && tid == 0) {
             const int4 dp = deps[it.node];
@@ -567,8 +631,8 @@ __global__ void __launch_bounds__(256)
                 const int child = side ? dp.z : dp.x;
                 const unsigned need = (unsigned)(side ? dp.w : dp.y);
                 if (child < 0) continue;
-                const volatile unsigned* cnt = done + (int64_t)child * G + it.pad;
-                while (*cnt < need) {
+                const unsigned* cnt = done + (int64_t)child * G + it.pad;
+                while (ld_acquire_gpu(cnt) < need) {
                     if (clock64() - t0 > kFlowWaitCycles) {
                         atomicExch(const_cast<int32_t*>(&d.ctl->status), (int32_t)TN_ETIMEOUT);
                         break;
@@ -576,46 +640,68 @@ __global__ void __launch_bounds__(256)
                     __nanosleep(32);
                 }
             }
-            __threadfence();
         }
         __syncthreads();
         if (vw.live) {
-            const int64_t isz = (int64_t)sizeof(T);
-            const T* A = reinterpret_cast<const T*>(
-                d.a_leaf >= 0 ? (const char*)leaf_ptrs[d.a_leaf] + (int64_t)it.pad * d.in.a_is * isz : vw.A);
-            const T* B = reinterpret_cast<const T*>(
-                d.b_leaf >= 0 ? (const char*)leaf_ptrs[d.b_leaf] + (int64_t)it.pad * d.in.b_is * isz : vw.B);
-            const Scales sc = node_scales(vw.sc, it.o_begin == 0 && tid == 0);
-            const int64_t slice = vw.slice;
-            const int64_t sA = slice_off(d.sla, slice), sB = slice_off(d.slb, slice);
             const int64_t K = 1ll << d.nk;
             const int64_t nmask = (1ll << d.nn) - 1, mmask = (1ll << d.nm) - 1;
             const int O = (int)it.o_count;
             const int g = O >= 256 ? 1 : 256 / O;
+            auto k_off = [&](int64_t t, int64_t& ka, int64_t& kb2) {
+                if (d.nk < 8) {
+                    ka = kA[t];
+                    kb2 = kB[t];
+                } else if (kh > 0) {
+                    ka = kA[t & 255] + kAh[t >> 8];
+                    kb2 = kB[t & 255] + kBh[t >> 8];
+                } else {
+                    const int64_t hi = t & ~255ll;
+                    ka = kA[t & 255] + (hi ? scatter_bits(hi, d.a_k, d.nk) : 0);
+                    kb2 = kB[t & 255] + (hi ? scatter_bits(hi, d.b_k, d.nk) : 0);
+                }
+            };
+            auto o_off = [&](int64_t o, int64_t& offA, int64_t& offB) {
+                const int64_t n = o & nmask, m = (o >> d.nn) & mmask, b = o >> (d.nn + d.nm);
+                offA = sA + scatter_bits(b, d.a_b, d.nb) + scatter_bits(m, d.a_m, d.nm);
+                offB = sB + scatter_bits(b, d.b_b, d.nb) + scatter_bits(n, d.b_n, d.nn);
+            };
+            // the children's scale slots and this thread's first operand
+            // pair are read together (one L2 round trip, not two)
+            const unsigned rma = vw.sc.max_a ? __ldcg(vw.sc.max_a) : 0u;
+            const unsigned rmb = vw.sc.max_b ? __ldcg(vw.sc.max_b) : 0u;
+            const int64_t rea = vw.sc.exp_a ? __ldcg(vw.sc.exp_a) : 0;
+            const int64_t reb = vw.sc.exp_b ? __ldcg(vw.sc.exp_b) : 0;
+            bool first = tid / g < O && (int64_t)(tid % g) < K;
+            T a0 = zero<T>(), b0 = zero<T>();
+            if (first) {
+                int64_t offA, offB, ka, kb2;
+                o_off(it.o_begin + tid / g, offA, offB);
+                k_off(tid % g, ka, kb2);
+                a0 = ld_cg<CPLX>(A + offA + ka);
+                b0 = ld_cg<CPLX>(B + offB + kb2);
+            }
+            const Scales sc = scales_from(rma, rmb, rea, reb, it.o_begin == 0 && tid == 0 ? vw.sc.exp_c : nullptr);
             float lmax = 0.f;
             T* C = reinterpret_cast<T*>(vw.C);
             for (int ol = tid / g; ol < O; ol += 256 / g) {
                 const int64_t o = it.o_begin + ol;
-                const int64_t n = o & nmask, m = (o >> d.nn) & mmask, b = o >> (d.nn + d.nm);
-                const int64_t offA = sA + scatter_bits(b, d.a_b, d.nb) + scatter_bits(m, d.a_m, d.nm);
-                const int64_t offB = sB + scatter_bits(b, d.b_b, d.nb) + scatter_bits(n, d.b_n, d.nn);
+                int64_t offA, offB;
+                o_off(o, offA, offB);
                 T acc = zero<T>();
 #pragma unroll 4
                 for (int64_t t = tid % g; t < K; t += g) {
-                    int64_t ka, kb2;
-                    if (d.nk < 8) {
-                        ka = kA[t];
-                        kb2 = kB[t];
-                    } else if (kh > 0) {
-                        ka = kA[t & 255] + kAh[t >> 8];
-                        kb2 = kB[t & 255] + kBh[t >> 8];
+                    T va, vb;
+                    if (first) {
+                        va = a0;
+                        vb = b0;
+                        first = false;
                     } else {
-                        const int64_t hi = t & ~255ll;
-                        ka = kA[t & 255] + (hi ? scatter_bits(hi, d.a_k, d.nk) : 0);
-                        kb2 = kB[t & 255] + (hi ? scatter_bits(hi, d.b_k, d.nk) : 0);
+                        int64_t ka, kb2;
+                        k_off(t, ka, kb2);
+                        va = ld_cg<CPLX>(A + offA + ka);
+                        vb = ld_cg<CPLX>(B + offB + kb2);
                     }
-                    fma_acc(acc, cmul(ld_cg<CPLX>(A + offA + ka), sc.fa, d.conj_a),
-                            cmul(ld_cg<CPLX>(B + offB + kb2), sc.fb, d.conj_b));
+                    fma_acc(acc, cmul(va, sc.fa, d.conj_a), cmul(vb, sc.fb, d.conj_b));
                 }
                 if (g > 1) {
                     red[tid] = acc;
@@ -644,10 +730,7 @@ __global__ void __launch_bounds__(256)
         }
         // ---- publish: outputs, maximum and exponent before the counter
         __syncthreads();
-        if (deps != nullptr && tid == 0) {
-            __threadfence();
-            atomicAdd(done + (int64_t)it.node * G + it.pad, 1u);
-        }
+        if (deps != nullptr && tid == 0) red_release_gpu_add(done + (int64_t)it.node * G + it.pad, 1u);
     }
 }
 
@@ -745,10 +828,13 @@ static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
     }
     if (e != cudaSuccess || a.split == 1) return e;
     const int64_t n = (int64_t)a.nbatch << (a.nm + a.nn);
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
     const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
-    k_split_reduce<CPLX><<<dim3((unsigned)blocks, (unsigned)ni), 256, 0, s>>>(a);
+    // threads per output: enough that outputs x G fill the GPU's threads
+    int G = 1;
+    while (G < 32 && G * 2 <= a.split && n * ni * G < (int64_t)152 * 256 * 4) G *= 2;
+    int64_t blocks = (n + 256 / G - 1) / (256 / G);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_split_reduce<CPLX><<<dim3((unsigned)blocks, (unsigned)ni), 256, 0, s>>>(a, G);
     return cudaGetLastError();
 }
 
