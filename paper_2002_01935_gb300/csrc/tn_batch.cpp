@@ -84,7 +84,7 @@ tn_status build_batch(BatchPlan& b, std::string& err) {
                 for (size_t k = 0; k < p.nodes.size(); ++k) {
                     if (b.level[i][k] != L || !b.small[i][k]) continue;
                     const int64_t size = p.nodes[k].size;
-                    const int64_t chunk = wave_chunk(p.nodes[k]);
+                    const int64_t chunk = wave_chunk(p.nodes[k], N);  // many networks: throughput
                     for (int64_t o = 0; o < size; o += chunk) {
                         WaveItem it;
                         it.node = b.desc_base[i] + (int)k;

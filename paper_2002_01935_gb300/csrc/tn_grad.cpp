@@ -246,7 +246,7 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, int c
                 singles.push_back(c);
                 continue;
             }
-            const int64_t chunk = wave_chunk(nd);
+            const int64_t chunk = wave_chunk(nd, G.plan_inst);
             for (int64_t o = 0; o < nd.size; o += chunk) {
                 WaveItem it;
                 it.node = c;
@@ -298,7 +298,7 @@ static tn_status build_grad(const NetDesc& d, const Plan& f, GradState& G, int c
                 const int pr = producer(v);
                 if (pr >= 0 && in_step[pr]) {
                     const Node& ch = cnode(pr);
-                    const int64_t chunk = wave_chunk(ch);
+                    const int64_t chunk = wave_chunk(ch, G.plan_inst);
                     G.flow_deps[4 * c + 2 * slot] = pr;
                     G.flow_deps[4 * c + 2 * slot + 1] = (int)((ch.size + chunk - 1) / chunk);
                 }

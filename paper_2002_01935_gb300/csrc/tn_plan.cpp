@@ -483,7 +483,7 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
                 singles.push_back((int)k);
                 continue;
             }
-            const int64_t chunk = wave_chunk(nd);
+            const int64_t chunk = wave_chunk(nd, p.copies);
             for (int64_t o = 0; o < nd.size; o += chunk) {
                 WaveItem it;
                 it.node = (int)k;
@@ -531,7 +531,7 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
             for (int c : {nd.ca, nd.cb}) {
                 if (c >= n && in_step[c - n]) {
                     const Node& ch = p.nodes[c - n];
-                    const int64_t chunk = wave_chunk(ch);
+                    const int64_t chunk = wave_chunk(ch, p.copies);
                     p.flow_deps[4 * k + 2 * slot] = c - n;
                     p.flow_deps[4 * k + 2 * slot + 1] = (int)((ch.size + chunk - 1) / chunk);
                 }

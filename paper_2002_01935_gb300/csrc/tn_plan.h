@@ -69,21 +69,22 @@ struct Step {
 
 // Wave items (k_wave: one CTA of 256 threads per item, every output summed
 // over all 2^nk entries of K by that CTA).  A tiled node joins a wave when
-// it is small: at most 2^16 outputs, 2^22 multiply-adds (1024 items), 2^14
-// summed entries per output.  Narrow mid-size nodes (a few thousand outputs,
-// 2^21..2^22 multiply-adds) fill the GPU better as items than as a tiled
-// launch, whose tiles they cover only in part.  Its items hold at most 2^12 multiply-adds (16 per
-// thread), so that an item's chain of dependent loads does not grow with K
-// -- on the dataflow's critical path every item counts -- and at most 1024
-// outputs.
+// it is small: at most 2^16 outputs, 2^22 multiply-adds counted over all
+// copies that share the launch, 2^14 summed entries per output.  Narrow
+// mid-size nodes (a few thousand outputs, 2^21..2^22 multiply-adds) fill
+// the GPU better as items than as a tiled launch, whose tiles they cover
+// only in part; bigger launches belong to the tiled and tensor-core kernels.
 inline bool wave_node(const Node& nd, int copies = 1) {
-    // with several copies per launch the 2^22 bound is on all copies together:
-    // bigger launches belong to the tiled and tensor-core kernels
     return nd.kind == kTiled && nd.tile.cfg != kTileDot && nd.size <= (1 << 16) &&
            nd.vc + std::log2((double)copies) <= 22.0 && nd.tile.nk <= 14;
 }
-inline int64_t wave_chunk(const Node& nd) {
-    const int sh = nd.tile.nk >= 12 ? 0 : 12 - nd.tile.nk;
+// Outputs per item: at most 2^10 multiply-adds (4 per thread, one batch of
+// independent loads: on the dataflow's critical path an item's latency must
+// not grow with K), 2^12 when several copies share the launch (there
+// throughput counts), and at most 1024 outputs.
+inline int64_t wave_chunk(const Node& nd, int copies = 1) {
+    const int bits = copies > 1 ? 12 : 10;
+    const int sh = nd.tile.nk >= bits ? 0 : bits - nd.tile.nk;
     int64_t c = int64_t(1) << sh;
     if (c > 1024) c = 1024;
     return nd.size < c ? nd.size : c;

@@ -576,7 +576,9 @@ __global__ void __launch_bounds__(256)
     __shared__ int64_t kA[256], kB[256], kAh[64], kBh[64];
     __shared__ T red[256];
     __shared__ int cur;
+    __shared__ int loaded;  // node whose descriptor and K tables are in shared memory
     const int tid = threadIdx.x;
+    if (tid == 0) loaded = -1;
     for (int pass = 0;; ++pass) {
         // ---- take an item
         if (deps == nullptr) {
@@ -590,17 +592,20 @@ __global__ void __launch_bounds__(256)
         if (idx >= n_items) break;
         const WaveItem it = items[idx];
         // ---- everything that does not depend on the children first: the
-        // descriptor, the instance view and the K offset tables
-        {
+        // descriptor and the K offset tables (kept from the previous item
+        // when it was of the same node), the instance view
+        const bool fresh = it.node != loaded;
+        if (fresh) {
             const int4* src = reinterpret_cast<const int4*>(descs + it.node);
             int4* dst = reinterpret_cast<int4*>(&d);
             for (int i = tid; i < (int)(sizeof(TileArgs) / 16); i += blockDim.x) dst[i] = src[i];
         }
         __syncthreads();
+        if (tid == 0) loaded = it.node;  // every thread has read the old value
         const View vw = inst_view(d, it.pad, (int)sizeof(T));
         const int kt = d.nk < 8 ? (int)(1ll << d.nk) : 256;  // table covers k & 255
         const int kh = d.nk > 8 && d.nk <= 14 ? (int)(1ll << (d.nk - 8)) : 0;  // k >> 8
-        if (vw.live) {
+        if (fresh) {
             for (int t = tid; t < kt; t += 256) {
                 kA[t] = scatter_bits(t, d.a_k, d.nk);
                 kB[t] = scatter_bits(t, d.b_k, d.nk);
