@@ -557,7 +557,11 @@ def run_network(args, torch, dist, rank, world, local):
             modes_cmp[md] = entry
 
     groups = sc
-    launches_per_call = 3 + groups * (3 + sum(s.get("launches", 1) for s in steps))
+    # our kernels per call: call setup (leaf maxima + control block) and the
+    # result copy; per slice group the steps' launches and the accumulation
+    # (which also advances the slice counter when it is one block)
+    n_out = math.prod(net.dims[l] for l in net.open)
+    launches_per_call = 2 + groups * (1 + (n_out > 256) + sum(s.get("launches", 1) for s in steps))
     cfg = {"workload": WORKLOAD_NAMES[args.workload], "mode": mode, "W_s": info.W, "C": info.C,
            "d_sliced": info.d_sliced, "slices_per_step": sc,
            "flops_per_step": flops_step, "nodes": len(pairs),

@@ -240,6 +240,8 @@ struct AccumArgs {
     const int64_t* exp_r;
     double* acc;
     Control* ctl;
+    int32_t advance;  // one-block launches: slices to advance ctl->slice by (set by the launcher)
+    int32_t pad3;
 };
 
 // Reverse sweep: add a leaf's adjoint (times 2^exp) into its gradient
@@ -331,12 +333,22 @@ cudaError_t launch_wave(const WaveItem* items, int n_items, const TileArgs* desc
                         const void* const* leaf_ptrs, bool is_c, cudaStream_t s,
                         const int4* deps = nullptr, unsigned* done = nullptr, unsigned* head = nullptr,
                         int G = 1);
-cudaError_t launch_accumulate(const AccumArgs& a, bool is_c, cudaStream_t s);
+// Folds the slice group's roots into the FP64 accumulator, leaves the
+// result's exponent after the last group, and advances the slice counter by
+// `advance` (in the same launch when it is one block).
+cudaError_t launch_accumulate(const AccumArgs& a, bool is_c, cudaStream_t s, int advance);
+// Leaf maxima (as launch_leaf_max) and the call's control block and
+// accumulator (as launch_begin_call) in one launch after one memset.
+cudaError_t launch_call_begin(const float* const* ptrs, const int64_t* nfloat, unsigned* out, int n,
+                              int64_t max_nfloat, Control* ctl, int64_t slice_begin, int64_t slice_end,
+                              double* acc, int64_t n_acc, cudaStream_t s);
+// Copies the accumulator (n doubles) and the final exponent to out / out_exp.
+cudaError_t launch_result(const double* acc, int64_t n, const Control* ctl, double* out, int64_t* out_exp,
+                          cudaStream_t s);
 cudaError_t launch_begin_call(Control* ctl, int64_t slice_begin, int64_t slice_end, double* acc,
                               int64_t n_acc_doubles, cudaStream_t s);
 cudaError_t launch_begin_slice(unsigned* maxabs, int n_nodes, cudaStream_t s);
 cudaError_t launch_advance(Control* ctl, cudaStream_t s, int step = 1);
-cudaError_t launch_finalize(Control* ctl, int parity, cudaStream_t s);
 cudaError_t launch_leaf_max(const float* const* ptrs, const int64_t* nfloat, unsigned* out, int n,
                             cudaStream_t s, int64_t max_nfloat);
 

@@ -215,18 +215,28 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ Accu
         else
             a.acc[o] = vr;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->acc_exp[par ^ 1] = newE;
+    if (gridDim.x == 1 && a.advance) __syncthreads();  // every thread has read ctl->slice
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->acc_exp[par ^ 1] = newE;
+        // the last group of the call leaves the result's exponent
+        if (a.ctl->slice + ni >= a.ctl->slice_end) a.ctl->final_exp = newE == INT64_MIN ? 0 : newE;
+        if (gridDim.x == 1 && a.advance) a.ctl->slice += a.advance;
+    }
 }
 
-cudaError_t launch_accumulate(const AccumArgs& a, bool is_c, cudaStream_t s) {
-    int64_t blocks = (a.n_out + 255) / 256;
+cudaError_t launch_accumulate(const AccumArgs& a0, bool is_c, cudaStream_t s, int advance) {
+    int64_t blocks = (a0.n_out + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
+    AccumArgs a = a0;
+    a.advance = blocks == 1 ? advance : 0;  // one block advances the slice counter itself
     if (is_c)
         k_accumulate<true><<<(unsigned)blocks, 256, 0, s>>>(a);
     else
         k_accumulate<false><<<(unsigned)blocks, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && blocks > 1 && advance) e = launch_advance(a.ctl, s, advance);
+    return e;
 }
 
 __global__ void k_begin_call(Control* ctl, int64_t slice_begin, int64_t slice_end, double* acc,
@@ -287,6 +297,74 @@ __global__ void __launch_bounds__(256) k_leaf_max(const float* const* ptrs, cons
         for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
         if (threadIdx.x == 0) atomicMax(&out[v], __float_as_uint(lmax));
     }
+}
+
+// The start of a call: leaf maxima as k_leaf_max, and (block 0) the control
+// block and the FP64 accumulator as k_begin_call.
+__global__ void __launch_bounds__(256) k_call_begin(const float* const* ptrs, const int64_t* nfloat,
+                                                    unsigned* out, int n, Control* ctl, int64_t slice_begin,
+                                                    int64_t slice_end, double* acc, int64_t n_acc) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        ctl->slice = slice_begin;
+        ctl->slice_begin = slice_begin;
+        ctl->slice_end = slice_end;
+        ctl->acc_exp[0] = INT64_MIN;
+        ctl->acc_exp[1] = INT64_MIN;
+        ctl->status = 0;
+    }
+    {
+        const int64_t nblk = (int64_t)gridDim.x * gridDim.y, bid = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        for (int64_t i = bid * blockDim.x + threadIdx.x; i < n_acc; i += nblk * blockDim.x) acc[i] = 0.0;
+    }
+    const int v = blockIdx.x;
+    if (v >= n) return;
+    const float* p = ptrs[v];
+    const int64_t m = nfloat[v];
+    const int64_t first = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    if ((int64_t)blockIdx.y * blockDim.x >= m && blockIdx.y > 0) return;
+    float lmax = 0.f;
+    for (int64_t i = first; i < m; i += (int64_t)gridDim.y * blockDim.x) lmax = fmaxf(lmax, fabsf(p[i]));
+    __shared__ float red[32];
+    for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lmax;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int nw = blockDim.x >> 5;
+        lmax = threadIdx.x < nw ? red[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        if (threadIdx.x == 0) atomicMax(&out[v], __float_as_uint(lmax));
+    }
+}
+
+cudaError_t launch_call_begin(const float* const* ptrs, const int64_t* nfloat, unsigned* out, int n,
+                              int64_t max_nfloat, Control* ctl, int64_t slice_begin, int64_t slice_end,
+                              double* acc, int64_t n_acc, cudaStream_t s) {
+    if (n > 0) {
+        const cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned) * (size_t)n, s);
+        if (e != cudaSuccess) return e;
+    }
+    int64_t parts = (max_nfloat + 32767) / 32768;
+    parts = parts < 1 ? 1 : (parts > 256 ? 256 : parts);
+    const unsigned gx = (unsigned)(n > 0 ? n : 1);
+    k_call_begin<<<dim3(gx, (unsigned)parts), 256, 0, s>>>(ptrs, nfloat, out, n, ctl, slice_begin, slice_end, acc,
+                                                          n_acc);
+    return cudaGetLastError();
+}
+
+// The call's result: the FP64 accumulator and the exponent, to the caller's
+// device buffers (or a staging buffer for one host copy: exp after acc).
+__global__ void k_result(const double* acc, int64_t n, const Control* ctl, double* out, int64_t* out_exp) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = acc[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *out_exp = ctl->final_exp;
+}
+
+cudaError_t launch_result(const double* acc, int64_t n, const Control* ctl, double* out, int64_t* out_exp,
+                          cudaStream_t s) {
+    int64_t blocks = (n + 255) / 256;
+    blocks = blocks < 1 ? 1 : (blocks > 152 * 4 ? 152 * 4 : blocks);
+    k_result<<<(unsigned)blocks, 256, 0, s>>>(acc, n, ctl, out, out_exp);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_leaf_max(const float* const* ptrs, const int64_t* nfloat, unsigned* out, int n,
@@ -470,16 +548,6 @@ cudaError_t launch_batch_finish(const BatchRoot* roots, int n, double* out, int6
                                 unsigned long long* latency, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_batch_finish<<<(n + 127) / 128, 128, 0, s>>>(roots, n, out, out_exp, t_start, t_done, latency);
-    return cudaGetLastError();
-}
-
-__global__ void k_finalize(Control* ctl, int parity) {
-    int64_t e = ctl->acc_exp[parity];
-    ctl->final_exp = (e == INT64_MIN) ? 0 : e;
-}
-
-cudaError_t launch_finalize(Control* ctl, int parity, cudaStream_t s) {
-    k_finalize<<<1, 1, 0, s>>>(ctl, parity);
     return cudaGetLastError();
 }
 

@@ -193,17 +193,14 @@ tn_status run_noalloc(const NetDesc& d, const Plan& p, void* out, int out_mem, i
     // every slice in order, then the result
     int64_t mx_leaf = 0;
     for (int v = 0; v < n; ++v) mx_leaf = std::max(mx_leaf, d.leaves[v].size * (d.is_complex() ? 2 : 1));
-    CK(launch_leaf_max(lptr, lnf, leafmax, n, stream, mx_leaf));
-    CK(launch_begin_call(ctl, 0, p.d_sliced, acc, (int64_t)acc_doubles, stream));
+    CK(launch_call_begin(lptr, lnf, leafmax, n, mx_leaf, ctl, 0, p.d_sliced, acc, (int64_t)acc_doubles, stream));
     for (int64_t s = 0; s < p.d_sliced; ++s) {
         CK(launch_begin_slice(maxabs, nn, stream));
         // the workspace offsets assume the plan's step order
         for (const Step& st : p.steps)
             for (int k : st.nodes) CK(launch_generic(gen[k], cplx, stream));
-        CK(launch_accumulate(a, cplx, stream));
-        CK(launch_advance(ctl, stream));
+        CK(launch_accumulate(a, cplx, stream, 1));
     }
-    CK(launch_finalize(ctl, (int)(p.d_sliced & 1), stream));
     cudaMemcpyKind kind = out_mem == TN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     CK(cudaMemcpyAsync(out, acc, sizeof(double) * acc_doubles, kind, stream));
     CK(cudaMemcpyAsync(out_exp2, &ctl->final_exp, sizeof(int64_t), kind, stream));

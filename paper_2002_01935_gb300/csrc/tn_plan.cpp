@@ -623,6 +623,7 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
     if (!ck(cudaMalloc(&p.ctl, sizeof(Control)), "cudaMalloc")) return TN_ENOMEM;
     size_t acc_doubles = (size_t)p.n_out * (d.is_complex() ? 2 : 1);
     if (!ck(cudaMalloc(&p.acc, sizeof(double) * acc_doubles), "cudaMalloc")) return TN_ENOMEM;
+    if (!ck(cudaMalloc(&p.out_stage, sizeof(double) * (acc_doubles + 1)), "cudaMalloc")) return TN_ENOMEM;
     if (!ck(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking), "stream")) return TN_ECUDA;
     if (!ck(cudaMalloc(&p.leafmax, sizeof(unsigned) * d.n), "cudaMalloc")) return TN_ENOMEM;
     if (!ck(cudaMalloc((void**)&p.leaf_ptr_dev, sizeof(void*) * d.n), "cudaMalloc")) return TN_ENOMEM;
@@ -875,9 +876,7 @@ static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, cons
     if (p.cfg_step == 0)
         return launch_batch_finish(p.inst_roots_dev, G, p.inst_out_dev, p.inst_exp_dev, nullptr, nullptr,
                                    nullptr, s);
-    e = launch_accumulate(p.acc_args, c, s);
-    if (e != cudaSuccess) return e;
-    return launch_advance(p.ctl, s, G);
+    return launch_accumulate(p.acc_args, c, s, G);
 }
 
 #define CK(x)                                                     \
@@ -1087,8 +1086,9 @@ tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count
     std::vector<const void*> lp;
     st = prepare_leaves(d, p, capturing, lp, stream, err);
     if (st != TN_OK) return st;
-    CK(launch_leaf_max(p.leaf_ptr_dev, p.leaf_nfloat_dev, p.leafmax, n, stream, max_leaf_floats(d)));
-    CK(launch_begin_call(p.ctl, begin, begin + count, p.acc, p.n_out * (d.is_complex() ? 2 : 1), stream));
+    const int64_t n_acc = p.n_out * (d.is_complex() ? 2 : 1);
+    CK(launch_call_begin(p.leaf_ptr_dev, p.leaf_nfloat_dev, p.leafmax, n, max_leaf_floats(d), p.ctl, begin,
+                         begin + count, p.acc, n_acc, stream));
     const int64_t groups = (count + G - 1) / G;
     const bool use_graph = !o.no_graph && !capturing;
     if (use_graph) {
@@ -1101,12 +1101,18 @@ tn_status run_plan(NetDesc& d, Plan& p, void* unit, int64_t begin, int64_t count
     } else {
         for (int64_t s = 0; s < groups; ++s) CK(enqueue_slice(d, p, stream, uev, pf, pc));
     }
-    CK(launch_finalize(p.ctl, (int)(groups & 1), stream));
-    const size_t acc_bytes = sizeof(double) * p.n_out * (d.is_complex() ? 2 : 1);
-    cudaMemcpyKind kind = out_mem == TN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    CK(cudaMemcpyAsync(out, p.acc, acc_bytes, kind, stream));
-    CK(cudaMemcpyAsync(out_exp2, &p.ctl->final_exp, sizeof(int64_t), kind, stream));
-    if (out_mem == TN_MEM_HOST) CK(cudaStreamSynchronize(stream));
+    // the result: one launch to device outputs; to host outputs, one copy of
+    // [accumulator | exponent] staged on the device
+    if (out_mem == TN_MEM_HOST) {
+        CK(launch_result(p.acc, n_acc, p.ctl, p.out_stage, reinterpret_cast<int64_t*>(p.out_stage + n_acc), stream));
+        std::vector<double> host((size_t)n_acc + 1);
+        CK(cudaMemcpyAsync(host.data(), p.out_stage, sizeof(double) * (n_acc + 1), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        std::memcpy(out, host.data(), sizeof(double) * n_acc);
+        std::memcpy(out_exp2, host.data() + n_acc, sizeof(int64_t));
+    } else {
+        CK(launch_result(p.acc, n_acc, p.ctl, static_cast<double*>(out), out_exp2, stream));
+    }
     return TN_OK;
 }
 
@@ -1155,8 +1161,8 @@ tn_status run_instances(NetDesc& d, Plan& p, void* unit, int n_inst, const int64
     std::vector<const void*> lp;
     st = prepare_leaves(d, p, false, lp, stream, err);
     if (st != TN_OK) return st;
-    CK(launch_leaf_max(p.leaf_ptr_dev, p.leaf_nfloat_dev, p.leafmax, n, stream, max_leaf_floats(d)));
-    CK(launch_begin_call(p.ctl, 0, 1, p.acc, 0, stream));
+    CK(launch_call_begin(p.leaf_ptr_dev, p.leaf_nfloat_dev, p.leafmax, n, max_leaf_floats(d), p.ctl, 0, 1, p.acc,
+                         0, stream));
     st = ensure_graph(d, p, lp, 0, 0, err);
     if (st != TN_OK) return st;
     CK(cudaGraphLaunch(p.gexec, stream));
@@ -1420,6 +1426,8 @@ void free_device(Plan& p) {
     if (p.exps) cudaFree(p.exps);
     if (p.ctl) cudaFree(p.ctl);
     if (p.acc) cudaFree(p.acc);
+    if (p.out_stage) cudaFree(p.out_stage);
+    p.out_stage = nullptr;
     if (p.leafmax) cudaFree(p.leafmax);
     if (p.split_buf) cudaFree(p.split_buf);
     p.split_buf = nullptr;

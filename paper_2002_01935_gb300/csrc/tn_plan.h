@@ -121,6 +121,7 @@ struct Plan {
     int64_t* exps = nullptr;
     Control* ctl = nullptr;
     double* acc = nullptr;
+    double* out_stage = nullptr;           // [accumulator | exponent] for host outputs
     unsigned* leafmax = nullptr;           // max |component| of each leaf
     const float** leaf_ptr_dev = nullptr;  // device copy of the leaf pointers
     int64_t* leaf_nfloat_dev = nullptr;
