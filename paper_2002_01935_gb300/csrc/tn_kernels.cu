@@ -332,19 +332,24 @@ __global__ void __launch_bounds__(256) k_call_begin(const float* const* ptrs, co
         const int nw = blockDim.x >> 5;
         lmax = threadIdx.x < nw ? red[threadIdx.x] : 0.f;
         for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-        if (threadIdx.x == 0) atomicMax(&out[v], __float_as_uint(lmax));
+        if (threadIdx.x == 0) {
+            if (gridDim.y == 1)
+                out[v] = __float_as_uint(lmax);  // one block per leaf: no zeroing needed
+            else
+                atomicMax(&out[v], __float_as_uint(lmax));
+        }
     }
 }
 
 cudaError_t launch_call_begin(const float* const* ptrs, const int64_t* nfloat, unsigned* out, int n,
                               int64_t max_nfloat, Control* ctl, int64_t slice_begin, int64_t slice_end,
                               double* acc, int64_t n_acc, cudaStream_t s) {
-    if (n > 0) {
+    int64_t parts = (max_nfloat + 32767) / 32768;
+    parts = parts < 1 ? 1 : (parts > 256 ? 256 : parts);
+    if (n > 0 && parts > 1) {  // several blocks per leaf combine by atomicMax from zero
         const cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned) * (size_t)n, s);
         if (e != cudaSuccess) return e;
     }
-    int64_t parts = (max_nfloat + 32767) / 32768;
-    parts = parts < 1 ? 1 : (parts > 256 ? 256 : parts);
     const unsigned gx = (unsigned)(n > 0 ? n : 1);
     k_call_begin<<<dim3(gx, (unsigned)parts), 256, 0, s>>>(ptrs, nfloat, out, n, ctl, slice_begin, slice_end, acc,
                                                           n_acc);

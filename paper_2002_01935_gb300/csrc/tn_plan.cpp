@@ -615,7 +615,13 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
     };
     const int G = std::max(p.alloc_inst, 1);
     if (!ck(cudaMalloc(&p.ws, (size_t)p.ws_elems * eb * G), "workspace allocation")) return TN_ENOMEM;
-    if (!ck(cudaMalloc(&p.maxabs, sizeof(unsigned) * nn * G), "cudaMalloc")) return TN_ENOMEM;
+    // node maxima of every instance, then the dataflow counters (done per
+    // node and instance, one item head per step): one region, cleared by one
+    // memset per slice
+    const size_t flow_cnt = (size_t)nn * G + p.steps.size() + 1;
+    if (!ck(cudaMalloc(&p.maxabs, sizeof(unsigned) * ((size_t)nn * G + flow_cnt)), "cudaMalloc"))
+        return TN_ENOMEM;
+    p.flow_cnt_dev = p.maxabs + (size_t)nn * G;
     if (!ck(cudaMalloc(&p.exps, sizeof(int64_t) * nn * G), "cudaMalloc")) return TN_ENOMEM;
     if (!ck(cudaMalloc(&p.inst_roots_dev, sizeof(BatchRoot) * G), "cudaMalloc")) return TN_ENOMEM;
     if (!ck(cudaMalloc(&p.inst_out_dev, sizeof(double) * 2 * G), "cudaMalloc")) return TN_ENOMEM;
@@ -679,8 +685,6 @@ tn_status alloc_plan(NetDesc& d, Plan& p, void* unit, std::string& err) {
         if (!ck(cudaMemcpy(p.flow_deps_dev, p.flow_deps.data(), sizeof(int) * p.flow_deps.size(),
                            cudaMemcpyHostToDevice), "cudaMemcpy"))
             return TN_ECUDA;
-        const size_t cnt = (size_t)nn * G + p.steps.size() + 1;
-        if (!ck(cudaMalloc(&p.flow_cnt_dev, sizeof(unsigned) * cnt), "cudaMalloc")) return TN_ENOMEM;
     }
     if (!p.items.empty()) {
         std::vector<TileArgs> descs(nn);
@@ -834,14 +838,13 @@ static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, cons
                                  int pf, int pc) {
     const int G = std::max(p.cfg_inst, 1);
     const int nn = (int)p.nodes.size();
-    cudaError_t e = launch_begin_slice(p.maxabs, nn * G, s);
-    if (e != cudaSuccess) return e;
     bool any_flow = false;
     for (const Step& st : p.steps) any_flow |= st.flow != 0;
-    if (any_flow &&
-        (e = cudaMemsetAsync(p.flow_cnt_dev, 0, sizeof(unsigned) * ((size_t)nn * G + p.steps.size()), s)) !=
-            cudaSuccess)
-        return e;
+    // the node maxima and (dataflow) the counters that follow them
+    const size_t n_zero = any_flow ? (size_t)(p.flow_cnt_dev - p.maxabs) + (size_t)nn * G + p.steps.size()
+                                   : (size_t)nn * G;
+    cudaError_t e = cudaMemsetAsync(p.maxabs, 0, sizeof(unsigned) * n_zero, s);
+    if (e != cudaSuccess) return e;
     const bool c = d.is_complex();
     for (int k = 0; k < (int)p.steps.size(); ++k) {
         // External records become event-record nodes under stream capture.
@@ -1434,7 +1437,6 @@ void free_device(Plan& p) {
     if (p.descs_dev) cudaFree(p.descs_dev);
     if (p.items_dev) cudaFree(p.items_dev);
     if (p.flow_deps_dev) cudaFree(p.flow_deps_dev);
-    if (p.flow_cnt_dev) cudaFree(p.flow_cnt_dev);
     p.flow_deps_dev = nullptr;
     p.flow_cnt_dev = nullptr;
     if (p.inst_roots_dev) cudaFree(p.inst_roots_dev);
