@@ -55,6 +55,14 @@ constexpr int kPackThreads = 256;
 constexpr int kPackLow = 5;           // lowest bits of each order staged per tile
 constexpr int kPackMaxTile = 1 << (2 * kPackLow);
 
+// Pack CTAs for an operand of n entries: every CTA stages several 1024-entry
+// tiles, so that its setup is amortised (measured: one tile per CTA made the
+// packs of mid-size nodes slower, not faster).
+inline unsigned pack_blocks(int64_t n, int ni) {
+    (void)ni;
+    return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), 152 * 8);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -1043,10 +1051,9 @@ cudaError_t launch_tc_3m(const TileArgs& a, cudaStream_t s) {
     const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
     const int split = a.split > 1 ? a.split : 1;
     if (g.nkb % split) return cudaErrorInvalidValue;
-    // every pack CTA stages several 1024-entry tiles (its setup is amortised)
-    auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), 152 * 8); };
     const int64_t elems_a = int64_t(1) << (a.nk + a.nm + a.nb);
     const int64_t elems_b = int64_t(1) << (a.nk + a.nn + a.nb);
+    auto blocks = [ni](int64_t n) { return pack_blocks(n, ni); };
     {
         const unsigned br = blocks(a.tc_swap ? elems_b : elems_a), bq = blocks(a.tc_swap ? elems_a : elems_b);
         k_pack<true, 3><<<dim3(br + bq, ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 0), make_pack_plan(a, 1),
@@ -1091,8 +1098,7 @@ cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     if (g.nkb % split) return cudaErrorInvalidValue;
     const int64_t elems_a = int64_t(1) << (a.nk + a.nm + a.nb);
     const int64_t elems_b = int64_t(1) << (a.nk + a.nn + a.nb);
-    // every pack CTA stages several 1024-entry tiles (its setup is amortised)
-    auto blocks = [](int64_t n) { return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), 152 * 8); };
+    auto blocks = [ni](int64_t n) { return pack_blocks(n, ni); };
     const int64_t n_r = a.tc_swap ? elems_b : elems_a, n_q = a.tc_swap ? elems_a : elems_b;
     k_pack<CPLX, PREC><<<dim3(blocks(n_r) + blocks(n_q), ni), kPackThreads, 0, s>>>(
         a, make_pack_plan(a, 0), make_pack_plan(a, 1), (int)blocks(n_r));

@@ -834,9 +834,12 @@ static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
     if (e != cudaSuccess || a.split == 1) return e;
     const int64_t n = (int64_t)a.nbatch << (a.nm + a.nn);
     const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
-    // threads per output: enough that outputs x G fill the GPU's threads
+    // threads per output: enough that outputs x G fill the GPU's threads;
+    // chosen from one instance's outputs, so that every instance sums in the
+    // same order however many run side by side (results independent of the
+    // slice batch)
     int G = 1;
-    while (G < 32 && G * 2 <= a.split && n * ni * G < (int64_t)152 * 256 * 4) G *= 2;
+    while (G < 32 && G * 2 <= a.split && n * G < (int64_t)152 * 256 * 4) G *= 2;
     int64_t blocks = (n + 256 / G - 1) / (256 / G);
     if (blocks > 152 * 8) blocks = 152 * 8;
     k_split_reduce<CPLX><<<dim3((unsigned)blocks, (unsigned)ni), 256, 0, s>>>(a, G);
