@@ -422,7 +422,7 @@ def run_network(args, torch, dist, rank, world, local):
     if not args.no_autotune:
         t0 = time.perf_counter()
         ch = tnw.autotune(pairs, sliced, mode, reps=10)
-        tuned = {"seconds": round(time.perf_counter() - t0, 3), "tensor_core": ch.count(8),
+        tuned = {"seconds": round(time.perf_counter() - t0, 3), "tensor_core": ch.count(8) + ch.count(9), "tensor_core_128col": ch.count(9),
                  "tile_shapes": {n: ch.count(v) for v, n in
                                  ((1, "64x64"), (2, "16x256"), (3, "4x1024"), (4, "256x16"), (6, "128x64"))
                                  if ch.count(v)}}

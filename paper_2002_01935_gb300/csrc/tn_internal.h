@@ -119,6 +119,7 @@ struct alignas(16) TileArgs {
     int conj_a, conj_b;   // read the operand complex-conjugated (reverse sweep)
     unsigned long long* t_done;  // root of a batched network: completion time (ns)
     int tc_swap;          // tensor-core node: B plays the row role (see TcGeom)
+    int tc_bn128;         // tensor-core node: 128-column GEMM tiles even where 256 fit
     InstanceInfo in;
 };
 
@@ -209,7 +210,7 @@ __host__ __device__ inline TcGeom tc_geom(const TileArgs& a, bool cplx, int prec
     const int64_t parts_bytes =
         a.split > 1 ? (int64_t)a.split * a.nbatch * (int64_t(1) << (a.nm + a.nn)) * 4 * (cplx ? 2 : 1) : 0;
     g.total = g.part_off + (parts_bytes + 1023) / 1024 * 1024;
-    g.bn = (prec != 3 && g.cols_q % 256 == 0) ? 256 : 128;
+    g.bn = (prec != 3 && g.cols_q % 256 == 0 && !a.tc_bn128) ? 256 : 128;
     return g;
 }
 

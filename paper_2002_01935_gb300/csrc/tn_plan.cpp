@@ -1239,11 +1239,13 @@ static bool make_variant(const NetDesc& d, const Plan& p, int k, int v, Node& ou
                          int split_mult = 1) {
     const Node& nd = p.nodes[k];
     Node t = nd;
-    if (!plan_tile(d, p, t, split_elems, v == kVariantTC ? 0 : v)) return false;
+    const bool tcv = v == kVariantTC || v == kVariantTC128;
+    if (!plan_tile(d, p, t, split_elems, tcv ? 0 : v)) return false;
+    if (v == kVariantTC128) t.tile.tc_bn128 = 1;
     if (t.tile.cfg == kTileDot) return false;
     t.kind = kTiled;
-    if (v == kVariantTC && !make_tensor_core(d, p.mode, t, split_elems)) return false;
-    if (v != kVariantTC && split_mult > 1) {
+    if (tcv && !make_tensor_core(d, p.mode, t, split_elems)) return false;
+    if (!tcv && split_mult > 1) {
         // finer K split: more blocks for short grids over long K (>= 2 K tiles each)
         TileArgs& a = t.tile;
         const int TK = a.cfg == kTile4x1024 ? 4 : 16;
@@ -1308,6 +1310,17 @@ tn_status autotune_plan(NetDesc& d, Plan& p, int reps, int32_t* choice, cudaStre
                 Node t1 = tc;
                 t1.tile.split = 1;
                 cand[k].push_back({kVariantTC, t1});
+            }
+            // 128-column tiles where 256 were chosen: twice the CTAs
+            Node tn;
+            if (tc_geom(tc.tile, d.is_complex(), tc_prec_of_mode(p.mode)).bn == 256 &&
+                make_variant(d, p, k, kVariantTC128, tn, split_elems)) {
+                cand[k].push_back({kVariantTC128, tn});
+                if (tn.tile.split > 1) {
+                    Node t1 = tn;
+                    t1.tile.split = 1;
+                    cand[k].push_back({kVariantTC128, t1});
+                }
             }
         }
         // CUDA-core shapes, unless the node is so large that they cannot win

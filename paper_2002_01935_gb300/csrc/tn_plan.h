@@ -168,6 +168,9 @@ bool plan_tile_node(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_el
 bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_elems, int copies = 1);
 // Autotuner variant code of the tensor-core kernel (tile shapes use TileCfg).
 constexpr int kVariantTC = 8;
+// ... and of the tensor-core kernel with 128-column tiles (twice the tiles:
+// a fuller grid for nodes with few).
+constexpr int kVariantTC128 = 9;
 // Times every candidate kernel of the nodes that run alone in a launch step
 // and keeps the fastest in the plan (device state must be allocated).
 tn_status autotune_plan(NetDesc& d, Plan& p, int reps, int32_t* choice, cudaStream_t s, std::string& err);
