@@ -785,7 +785,7 @@ def fsim_batch(torch, theta, phi):
 
 def run_grad(args, torch, dist, rank, world, local):
     import numpy as np
-    from paper_2002_01935_gb300 import autograd, binding, inputs, planner
+    from paper_2002_01935_gb300 import autograd, binding, inputs, planner, shard
 
     mode = args.mode
     R, C, T = 5, 4, 12
@@ -830,6 +830,8 @@ def run_grad(args, torch, dist, rank, world, local):
         vals = autograd.contract_batch(tnw, pairs, mode, leaves[:first_out] + [None] * (R * C), batch)
         loss = torch.mean(torch.log(torch.abs(vals) ** 2))
         loss.backward()
+        if dist:  # data parallel over bitstrings: the parameter gradients summed over the ranks
+            shard.combine_grads([theta.grad, phi.grad])
         return loss
 
     for _ in range(args.warmup):

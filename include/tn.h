@@ -232,6 +232,11 @@ tn_status tn_contract_grad(tn_net *net, const int32_t *tree_pairs, int32_t n_sli
  *                 adj_exp2 in stream order -- e.g. the negated exponent of
  *                 a tn_contract result, for adjoints such as 1 / value.
  *   flags         0 or TN_GRAD_ACCUMULATE.
+ *   slice_begin, slice_count
+ *                 the slices swept: [slice_begin, slice_begin + slice_count)
+ *                 of the d_sliced slices (slice_count <= 0: all).  Partial
+ *                 ranges give the gradient of that part of the sum: ranks
+ *                 sharing the slices add their gradients (one all-reduce).
  *   Other arguments as tn_contract_grad.
  * Both calls keep, per (tree, slicing, mode), a library image of the leaves
  * (refreshed from the attached pointers at the start of every call) and of
@@ -246,7 +251,8 @@ tn_status tn_contract_grad(tn_net *net, const int32_t *tree_pairs, int32_t n_sli
 tn_status tn_contract_grad_ex(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
                               const int64_t *sliced_labels, tn_mode mode, const double *out_adjoint,
                               int32_t adj_mem, int64_t adj_exp2, const int64_t *adj_exp2_dev,
-                              void *const *leaf_grads, uint32_t flags, void *stream);
+                              void *const *leaf_grads, uint32_t flags, int64_t slice_begin,
+                              int64_t slice_count, void *stream);
 
 /*
  * tn_contract_grad_instances -- the reverse sweep of n_inst copies of the
@@ -269,6 +275,7 @@ tn_status tn_contract_grad_ex(tn_net *net, const int32_t *tree_pairs, int32_t n_
  *                 copy order); for a varying leaf copy i's gradient at
  *                 + i * leaf_inst_stride[v] elements.
  *   flags         TN_GRAD_ACCUMULATE and/or TN_GRAD_KEPT_FORWARD (below).
+ *   slice_begin, slice_count  as tn_contract_grad_ex.
  * The device state grows to n_inst copies of the sweep's workspace; a
  * different (n_inst, shared/varying pattern) rebuilds it (and synchronises
  * the stream).  Errors: as tn_contract_grad_ex; TN_EINVAL for n_inst < 1
@@ -279,7 +286,8 @@ tn_status tn_contract_grad_instances(tn_net *net, const int32_t *tree_pairs, int
                                      const int64_t *sliced_labels, tn_mode mode, int32_t n_inst,
                                      const int64_t *leaf_inst_stride, const double *out_adjoint,
                                      int32_t adj_mem, int64_t adj_exp2, const int64_t *adj_exp2_dev,
-                                     void *const *leaf_grads, uint32_t flags, void *stream);
+                                     void *const *leaf_grads, uint32_t flags, int64_t slice_begin,
+                                     int64_t slice_count, void *stream);
 
 /*
  * tn_contract_instances_keep -- tn_contract_instances (unsliced scalar

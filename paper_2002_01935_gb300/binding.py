@@ -62,11 +62,13 @@ _lib.tn_contract_grad.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_in
                                   ctypes.POINTER(_vp), _vp]
 _lib.tn_contract_grad_ex.restype = ctypes.c_int
 _lib.tn_contract_grad_ex.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int, _vp, ctypes.c_int32,
-                                     ctypes.c_int64, _vp, ctypes.POINTER(_vp), ctypes.c_uint32, _vp]
+                                     ctypes.c_int64, _vp, ctypes.POINTER(_vp), ctypes.c_uint32,
+                                     ctypes.c_int64, ctypes.c_int64, _vp]
 _lib.tn_contract_grad_instances.restype = ctypes.c_int
 _lib.tn_contract_grad_instances.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int, ctypes.c_int32,
                                             _i64p, _vp, ctypes.c_int32, ctypes.c_int64, _vp,
-                                            ctypes.POINTER(_vp), ctypes.c_uint32, _vp]
+                                            ctypes.POINTER(_vp), ctypes.c_uint32, ctypes.c_int64,
+                                            ctypes.c_int64, _vp]
 _lib.tn_contract_instances_keep.restype = ctypes.c_int
 _lib.tn_contract_instances_keep.argtypes = [_vp, _i32p, ctypes.c_int, ctypes.c_int32, _i64p, _vp, _vp,
                                             ctypes.c_int32, _vp]
@@ -197,7 +199,7 @@ TN_GRAD_KEPT_FORWARD = 2
 
 def tn_contract_grad_ex(h: int, pairs, sliced, mode: int, adj_ptr: int, adj_mem: int, adj_exp2: int,
                         adj_exp2_dev: int, grad_ptrs: Sequence[int], flags: int = 0,
-                        stream: int = 0) -> None:
+                        stream: int = 0, slice_begin: int = 0, slice_count: int = 0) -> None:
     """tn_contract_grad with a host or device adjoint (pointer to FP64) and
     optional accumulation (flags = TN_GRAD_ACCUMULATE)."""
     tr = _tree(pairs)
@@ -205,12 +207,13 @@ def tn_contract_grad_ex(h: int, pairs, sliced, mode: int, adj_ptr: int, adj_mem:
     gp = (_vp * len(grad_ptrs))(*[g or None for g in grad_ptrs])
     _check(_lib.tn_contract_grad_ex(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
                                     adj_ptr, adj_mem, int(adj_exp2), adj_exp2_dev or None, gp, flags,
-                                    stream))
+                                    int(slice_begin), int(slice_count), stream))
 
 
 def tn_contract_grad_instances(h: int, pairs, sliced, mode: int, n_inst: int, leaf_inst_stride,
                                adj_ptr: int, adj_mem: int, adj_exp2: int, adj_exp2_dev: int,
-                               grad_ptrs: Sequence[int], flags: int = 0, stream: int = 0) -> None:
+                               grad_ptrs: Sequence[int], flags: int = 0, stream: int = 0,
+                               slice_begin: int = 0, slice_count: int = 0) -> None:
     """Reverse sweep of n_inst copies (leaf v of copy i at + i *
     leaf_inst_stride[v] elements; None: all shared) in one launch sequence."""
     tr = _tree(pairs)
@@ -220,7 +223,7 @@ def tn_contract_grad_instances(h: int, pairs, sliced, mode: int, n_inst: int, le
     _check(_lib.tn_contract_grad_instances(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64),
                                            mode, n_inst, _p(st, ctypes.c_int64) if st is not None else None,
                                            adj_ptr, adj_mem, int(adj_exp2), adj_exp2_dev or None, gp, flags,
-                                           stream))
+                                           int(slice_begin), int(slice_count), stream))
 
 
 def tn_contract_noalloc(h: int, pairs, sliced, out_ptr: int, out_mem: int, exp_ptr: int,
@@ -355,7 +358,7 @@ class TensorNetwork:
         return out, out_exp
 
     def grad(self, pairs, sliced, mode, adjoint, adj_exp2=0, grads=None, stream=None,
-             accumulate=False):
+             accumulate=False, slice_begin=0, slice_count=0):
         """Leaf gradients conj(d value / d T_v) * adjoint, summed over slices
         and contracted over the open labels (torch's convention).
 
@@ -366,7 +369,8 @@ class TensorNetwork:
         adjoint * 2**adj_exp2.  ``grads``: torch tensors shaped like the
         leaves (device, leaf dtype; None entries are skipped), or None to
         allocate.  ``accumulate``: add into ``grads`` instead of overwriting.
-        Returns the list of gradient tensors (asynchronous)."""
+        ``slice_begin``/``slice_count``: sweep only those slices (count 0:
+        all).  Returns the list of gradient tensors (asynchronous)."""
         import torch
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         cplx = self.dtype == TN_C64
@@ -400,7 +404,7 @@ class TensorNetwork:
         s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
         tn_contract_grad_ex(self.h, pairs, sliced, m, adj_ptr, adj_mem, exp_host, exp_dev,
                             [g.data_ptr() if g is not None else 0 for g in grads],
-                            TN_GRAD_ACCUMULATE if accumulate else 0, s)
+                            TN_GRAD_ACCUMULATE if accumulate else 0, s, slice_begin, slice_count)
         self._grad_epoch = getattr(self, "_grad_epoch", 0) + 1
         del keep
         return grads
@@ -423,7 +427,8 @@ class TensorNetwork:
         return out, ex, self._grad_epoch
 
     def grad_instances(self, pairs, sliced, mode, n_inst, leaf_inst_stride, adjoint, adj_exp2=0,
-                       grads=None, stream=None, accumulate=False, kept_forward=None):
+                       grads=None, stream=None, accumulate=False, kept_forward=None,
+                       slice_begin=0, slice_count=0):
         """Reverse sweep of n_inst copies in one launch sequence (see
         tn_contract_grad_instances).  ``adjoint``: [n_inst, *output shape]
         FP64 (complex128 for complex networks), host array or CUDA tensor;
@@ -469,7 +474,7 @@ class TensorNetwork:
             flags |= TN_GRAD_KEPT_FORWARD
         tn_contract_grad_instances(self.h, pairs, sliced, m, n_inst, leaf_inst_stride, adj_ptr, adj_mem,
                                    exp_host, exp_dev, [g.data_ptr() if g is not None else 0 for g in grads],
-                                   flags, s)
+                                   flags, s, slice_begin, slice_count)
         if not flags & TN_GRAD_KEPT_FORWARD:  # the sweep's workspace now holds another forward
             self._grad_epoch = getattr(self, "_grad_epoch", 0) + 1
         del keep

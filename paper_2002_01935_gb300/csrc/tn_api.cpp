@@ -277,7 +277,8 @@ tn_status tn_autotune(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced, 
 tn_status tn_contract_grad_ex(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
                               const int64_t* sliced_labels, tn_mode mode, const double* out_adjoint,
                               int32_t adj_mem, int64_t adj_exp2, const int64_t* adj_exp2_dev,
-                              void* const* leaf_grads, uint32_t flags, void* stream) {
+                              void* const* leaf_grads, uint32_t flags, int64_t slice_begin,
+                              int64_t slice_count, void* stream) {
     if (!net) return fail(TN_EINVAL, "tn_contract_grad: net is NULL");
     if (!out_adjoint || !leaf_grads) return fail(TN_EINVAL, "tn_contract_grad: NULL argument");
     if (adj_mem != TN_MEM_DEVICE && adj_mem != TN_MEM_HOST) return fail(TN_EINVAL, "bad adj_mem");
@@ -293,7 +294,8 @@ tn_status tn_contract_grad_ex(tn_net* net, const int32_t* tree_pairs, int32_t n_
     if (st != TN_OK) return st;
     std::string err;
     st = tn::run_grad(net->d, *p, net->unit, out_adjoint, adj_mem, adj_exp2, adj_exp2_dev, leaf_grads,
-                      (flags & TN_GRAD_ACCUMULATE) != 0, false, 1, nullptr, (cudaStream_t)stream, err);
+                      (flags & TN_GRAD_ACCUMULATE) != 0, false, 1, nullptr, slice_begin, slice_count,
+                      (cudaStream_t)stream, err);
     if (st != TN_OK) return fail(st, err);
     return TN_OK;
 }
@@ -302,7 +304,8 @@ tn_status tn_contract_grad_instances(tn_net* net, const int32_t* tree_pairs, int
                                      const int64_t* sliced_labels, tn_mode mode, int32_t n_inst,
                                      const int64_t* leaf_inst_stride, const double* out_adjoint,
                                      int32_t adj_mem, int64_t adj_exp2, const int64_t* adj_exp2_dev,
-                                     void* const* leaf_grads, uint32_t flags, void* stream) {
+                                     void* const* leaf_grads, uint32_t flags, int64_t slice_begin,
+                                     int64_t slice_count, void* stream) {
     if (!net) return fail(TN_EINVAL, "tn_contract_grad_instances: net is NULL");
     if (!out_adjoint || !leaf_grads) return fail(TN_EINVAL, "tn_contract_grad_instances: NULL argument");
     if (n_inst < 1) return fail(TN_EINVAL, "tn_contract_grad_instances: n_inst < 1");
@@ -321,7 +324,7 @@ tn_status tn_contract_grad_instances(tn_net* net, const int32_t* tree_pairs, int
     std::string err;
     st = tn::run_grad(net->d, *p, net->unit, out_adjoint, adj_mem, adj_exp2, adj_exp2_dev, leaf_grads,
                       (flags & TN_GRAD_ACCUMULATE) != 0, (flags & TN_GRAD_KEPT_FORWARD) != 0, n_inst,
-                      leaf_inst_stride, (cudaStream_t)stream, err);
+                      leaf_inst_stride, slice_begin, slice_count, (cudaStream_t)stream, err);
     if (st != TN_OK) return fail(st, err);
     return TN_OK;
 }
@@ -350,7 +353,7 @@ tn_status tn_contract_grad(tn_net* net, const int32_t* tree_pairs, int32_t n_sli
                            const int64_t* sliced_labels, tn_mode mode, const double* out_adjoint,
                            int64_t adj_exp2, void* const* leaf_grads, void* stream) {
     return tn_contract_grad_ex(net, tree_pairs, n_sliced, sliced_labels, mode, out_adjoint, TN_MEM_HOST,
-                               adj_exp2, nullptr, leaf_grads, 0u, stream);
+                               adj_exp2, nullptr, leaf_grads, 0u, 0, 0, stream);
 }
 
 tn_status tn_contract_noalloc(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,

@@ -882,8 +882,17 @@ tn_status run_grad_forward(NetDesc& d, Plan& p, void* unit, int n_inst, const in
 
 tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_mem, int64_t adj_exp2,
                    const int64_t* adj_exp2_dev, void* const* grads, bool accumulate, bool kept_forward,
-                   int n_inst, const int64_t* leaf_inst_stride, cudaStream_t stream, std::string& err) {
+                   int n_inst, const int64_t* leaf_inst_stride, int64_t slice_begin, int64_t slice_count,
+                   cudaStream_t stream, std::string& err) {
     const int n = d.n;
+    if (slice_count <= 0) {
+        slice_begin = 0;
+        slice_count = p.d_sliced;
+    }
+    if (slice_begin < 0 || slice_begin + slice_count > p.d_sliced) {
+        err = "tn_contract_grad: slice range out of bounds";
+        return TN_EINVAL;
+    }
     const bool cplx = d.is_complex();
     const int cf = cplx ? 2 : 1;
     if (kept_forward && (!p.grad || !p.grad->kept || p.grad->n_inst != n_inst)) {
@@ -952,12 +961,12 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
     ra.slot_is = G.n_slots;
     CK(launch_root_adjoint(ra, n_inst, stream));
     CK(cudaMemsetAsync(G.gacc, 0, sizeof(float) * G.acc_floats * n_inst, stream));
-    CK(launch_begin_call(G.ctl, 0, p.d_sliced, nullptr, 0, stream));
+    CK(launch_begin_call(G.ctl, slice_begin, slice_begin + slice_count, nullptr, 0, stream));
     if (kept_forward) {
         CK(cudaGraphLaunch(G.gexec_b, stream));
     } else {
         G.kept = false;  // the workspace is rewritten slice by slice
-        for (int64_t s = 0; s < p.d_sliced; ++s) {
+        for (int64_t s = 0; s < slice_count; ++s) {
             CK(cudaGraphLaunch(G.gexec_f, stream));
             CK(cudaGraphLaunch(G.gexec_b, stream));
         }

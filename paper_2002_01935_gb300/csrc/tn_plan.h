@@ -193,7 +193,8 @@ tn_status run_instances(NetDesc& d, Plan& p, void* unit, int n_inst, const int64
 // run_grad_forward (same copies and leaves): only the sweep runs.
 tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_mem, int64_t adj_exp2,
                    const int64_t* adj_exp2_dev, void* const* grads, bool accumulate, bool kept_forward,
-                   int n_inst, const int64_t* leaf_inst_stride, cudaStream_t stream, std::string& err);
+                   int n_inst, const int64_t* leaf_inst_stride, int64_t slice_begin, int64_t slice_count,
+                   cudaStream_t stream, std::string& err);
 // Forward of n_inst copies (unsliced scalar networks) in the sweep's state,
 // every intermediate kept; values as tn_contract_instances.
 tn_status run_grad_forward(NetDesc& d, Plan& p, void* unit, int n_inst, const int64_t* leaf_inst_stride,

@@ -52,3 +52,35 @@ def combine(mantissa, exp2: int, group=None):
     dist.all_reduce(part, op=dist.ReduceOp.SUM, group=group)
     out = torch.view_as_complex(part) if mantissa.is_complex() else part
     return out, e_max
+
+
+def combine_grads(grads, group=None):
+    """Sum gradient buffers over the ranks, in place: each rank swept its own
+    block of slices (tn_contract_grad_ex with a slice range) or its own
+    networks (e.g. a block of bitstrings), and the gradient of the whole sum
+    is the sum of the parts -- one all-reduce of all buffers together.  The
+    sum is taken in float64 (rounded once back to the buffers' dtype), so
+    that it does not depend on the backend's reduction order beyond FP64
+    rounding.  ``grads``: tensors (None entries are skipped), on the device
+    the backend expects."""
+    import torch
+    import torch.distributed as dist
+
+    live = [g for g in grads if g is not None]
+    if not live:
+        return grads
+    if not all(g.is_contiguous() for g in live):
+        raise ValueError("gradient buffers must be contiguous")
+    parts = [torch.view_as_real(g).reshape(-1) if g.is_complex() else g.reshape(-1) for g in live]
+    flat = torch.cat([p.to(torch.float64) for p in parts])
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+    off = 0
+    for g, p in zip(live, parts):
+        n = p.numel()
+        src = flat[off:off + n].to(p.dtype)
+        if g.is_complex():
+            torch.view_as_real(g).reshape(-1).copy_(src)
+        else:
+            g.reshape(-1).copy_(src)
+        off += n
+    return grads

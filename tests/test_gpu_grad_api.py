@@ -389,3 +389,26 @@ def test_kept_forward_refused_when_stale(torch):
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
     tnw.close()
+
+
+@pytest.mark.parametrize("parts", [2, 3])
+def test_slice_ranges_sum_to_the_full_gradient(torch, parts):
+    """Gradients over disjoint slice ranges (as ranks sharing the slices
+    compute them) add up to the gradient over all slices."""
+    from paper_2002_01935_gb300 import shard
+    net, pairs, sliced, ts, tnw = _setup(torch, seed=31, sliced_n=3)
+    d = int(np.prod([net.dims[l] for l in sliced]))
+    adj = _adjoint(net, 9)
+    full = [g.cpu().numpy() for g in tnw.grad(pairs, sliced, "fp32", adj)]
+    acc = [np.zeros_like(g) for g in full]
+    for r in range(parts):
+        b, cnt = shard.slice_range(r, parts, d)
+        part = tnw.grad(pairs, sliced, "fp32", adj, slice_begin=b, slice_count=cnt)
+        for a, g in zip(acc, part):
+            a += g.cpu().numpy()
+    for a, f in zip(acc, full):
+        assert np.linalg.norm(a - f) <= 1e-6 * (np.linalg.norm(f) + 1e-30)
+    from paper_2002_01935_gb300 import binding
+    with pytest.raises(binding.TNError):
+        tnw.grad(pairs, sliced, "fp32", adj, slice_begin=d - 1, slice_count=2)
+    tnw.close()

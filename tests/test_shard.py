@@ -107,3 +107,79 @@ def test_combine_sums_slices_across_ranks(world):
             np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.max(np.abs(ref)))
         # every rank ends with the same result
         assert all(np.array_equal(res[0][1], r[1]) and res[0][2] == r[2] for r in res)
+
+
+def _slice_env_grads(net, pairs_fn, sliced, begin, count):
+    """Leaf gradients (conj of the environments, adjoint 1) of the slices
+    [begin, begin + count) of a closed network, from the oracle: each slice
+    fixes the sliced labels (last listed fastest) and contributes its
+    environments at those index values."""
+    from oracle import gradient
+    dims = net.dims
+    grads = [np.zeros(np.shape(t), dtype=np.complex128) for t in net.tensors]
+    radix = [dims[l] for l in sliced]
+    for s in range(begin, begin + count):
+        val, rem = {}, s
+        for l, d in zip(reversed(sliced), reversed(radix)):
+            val[l] = rem % d
+            rem //= d
+        ts, ls, idx = [], [], []
+        for t, lab in zip(net.tensors, net.labels):
+            sel = tuple(val[l] if l in val else slice(None) for l in lab)
+            ts.append(np.asarray(t)[sel])
+            ls.append([l for l in lab if l not in val])
+            idx.append(sel)
+        for v in range(net.n_tensors):
+            env = gradient.environment(ts, ls, dims, v, pairs_fn)
+            grads[v][idx[v]] += np.conj(env)
+    return grads
+
+
+def _grad_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        net = inputs.random_network(6, 9, 812, n_open=0, complex_=True)
+        sliced = sorted(net.dims)[:3]
+        d = math.prod(net.dims[l] for l in sliced)
+        b, c = shard.slice_range(rank, world, d)
+        part = _slice_env_grads(net, planner.greedy_tree, sliced, b, c)
+        ts = [torch.from_numpy(g.copy()) for g in part]
+        shard.combine_grads(ts + [None])
+        q.put((rank, [t.numpy() for t in ts]))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_combine_grads_sums_slice_blocks(world):
+    """Per-rank gradients over blocks of slices, summed by combine_grads,
+    equal the gradient of the whole (unsliced) network."""
+    from oracle import gradient
+    import torch.multiprocessing as mp
+    net = inputs.random_network(6, 9, 812, n_open=0, complex_=True)
+    full = [np.conj(gradient.environment(net.tensors, net.labels, net.dims, v, planner.greedy_tree))
+            for v in range(net.n_tensors)]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_grad_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=180) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, gs in res:
+        for g, ref in zip(gs, full):
+            np.testing.assert_allclose(g, ref, rtol=1e-11, atol=1e-12 * np.max(np.abs(ref)))
+
+
+def test_combine_grads_rejects_strided_buffers():
+    import torch
+    with pytest.raises(ValueError):
+        shard.combine_grads([torch.zeros(4, 4)[:, 1]])
