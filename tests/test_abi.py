@@ -149,3 +149,24 @@ def test_launch_schedule_covers_every_node_once_in_dependency_order(lib):
         for s0, s1 in zip(steps, steps[1:]):
             assert not (s0["wave"] and s1["wave"])
         assert sum(s["launches"] for s in steps) >= len(steps)
+
+
+def test_wave_steps_hold_only_small_nodes(lib):
+    """Host plan only: a node runs inside a wave launch only when it is small
+    (at most 2^16 outputs, 2^22 multiply-adds, 2^14 summed entries per
+    output); the largest nodes of these trees run alone."""
+    from paper_2002_01935_gb300 import inputs, planner
+    for net in (inputs.random_ising(100, seed=0),
+                inputs.circuit_network(inputs.random_circuit(5, 4, 12, seed=0),
+                                       inputs.random_bitstrings(20, 1, seed=1000)[0])):
+        pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+        info = planner.tree_info(net.labels, net.dims, pairs, net.open)
+        steps, _ = _steps(lib, net, pairs)
+        n = net.n_tensors
+        in_wave = {k for st in steps if st["wave"] for k in st["nodes"]}
+        for k in in_wave:
+            size = len(info.sets[n + k])          # log2 of the outputs (all dims 2)
+            vc = info.vc[k]                       # log2 of the multiply-adds
+            assert size <= 16 and vc <= 22 and vc - size <= 14, (k, size, vc)
+        biggest = max(range(len(pairs)), key=lambda k: info.vc[k])
+        assert biggest not in in_wave
