@@ -275,14 +275,17 @@ cudaError_t launch_advance(Control* ctl, cudaStream_t s, int step) {
 
 // Largest |component| of every leaf, so that leaves are renormalised like
 // intermediates before their first contraction.  blockIdx.x: leaf,
-// blockIdx.y: one of gridDim.y interleaved parts of it; parts combine by
-// atomicMax on the float bits (non-negative floats order like unsigned).
-__global__ void __launch_bounds__(256) k_leaf_max(const float* const* ptrs, const int64_t* nfloat,
-                                                  unsigned* out, int n) {
-    int v = blockIdx.x;
+// blockIdx.y: one of gridDim.y interleaved parts of it.
+// Part blockIdx.y of leaf blockIdx.x: the largest |component| over its
+// entries, combined over the parts by atomicMax on the float bits
+// (non-negative floats order like unsigned), or stored directly when one
+// block covers the leaf and `direct` allows it (no zeroing needed then).
+__device__ __forceinline__ void leaf_max_part(const float* const* ptrs, const int64_t* nfloat, unsigned* out,
+                                              int n, bool direct) {
+    const int v = blockIdx.x;
     if (v >= n) return;
     const float* p = ptrs[v];
-    int64_t m = nfloat[v];
+    const int64_t m = nfloat[v];
     const int64_t first = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     if ((int64_t)blockIdx.y * blockDim.x >= m && blockIdx.y > 0) return;
     float lmax = 0.f;
@@ -292,11 +295,21 @@ __global__ void __launch_bounds__(256) k_leaf_max(const float* const* ptrs, cons
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lmax;
     __syncthreads();
     if (threadIdx.x < 32) {
-        int nw = blockDim.x >> 5;
+        const int nw = blockDim.x >> 5;
         lmax = threadIdx.x < nw ? red[threadIdx.x] : 0.f;
         for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-        if (threadIdx.x == 0) atomicMax(&out[v], __float_as_uint(lmax));
+        if (threadIdx.x == 0) {
+            if (direct && gridDim.y == 1)
+                out[v] = __float_as_uint(lmax);
+            else
+                atomicMax(&out[v], __float_as_uint(lmax));
+        }
     }
+}
+
+__global__ void __launch_bounds__(256) k_leaf_max(const float* const* ptrs, const int64_t* nfloat,
+                                                  unsigned* out, int n) {
+    leaf_max_part(ptrs, nfloat, out, n, false);
 }
 
 // The start of a call: leaf maxima as k_leaf_max, and (block 0) the control
@@ -316,29 +329,7 @@ __global__ void __launch_bounds__(256) k_call_begin(const float* const* ptrs, co
         const int64_t nblk = (int64_t)gridDim.x * gridDim.y, bid = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
         for (int64_t i = bid * blockDim.x + threadIdx.x; i < n_acc; i += nblk * blockDim.x) acc[i] = 0.0;
     }
-    const int v = blockIdx.x;
-    if (v >= n) return;
-    const float* p = ptrs[v];
-    const int64_t m = nfloat[v];
-    const int64_t first = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
-    if ((int64_t)blockIdx.y * blockDim.x >= m && blockIdx.y > 0) return;
-    float lmax = 0.f;
-    for (int64_t i = first; i < m; i += (int64_t)gridDim.y * blockDim.x) lmax = fmaxf(lmax, fabsf(p[i]));
-    __shared__ float red[32];
-    for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lmax;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int nw = blockDim.x >> 5;
-        lmax = threadIdx.x < nw ? red[threadIdx.x] : 0.f;
-        for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-        if (threadIdx.x == 0) {
-            if (gridDim.y == 1)
-                out[v] = __float_as_uint(lmax);  // one block per leaf: no zeroing needed
-            else
-                atomicMax(&out[v], __float_as_uint(lmax));
-        }
-    }
+    leaf_max_part(ptrs, nfloat, out, n, true);
 }
 
 cudaError_t launch_call_begin(const float* const* ptrs, const int64_t* nfloat, unsigned* out, int n,
