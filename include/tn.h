@@ -389,6 +389,17 @@ tn_status tn_autotune(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
                       void *stream);
 
 /*
+ * tn_selftest_flow_timeout -- failure-detection self-test of the bounded
+ * device waits.  Launches one dataflow wave whose only item waits for a
+ * completion counter that nothing raises; after its bound (about 2 s) the
+ * wait gives up, the kernel records TN_ETIMEOUT in its control block and
+ * returns, and the CUDA context stays usable.  Returns that status
+ * (TN_ETIMEOUT; TN_OK would mean the wait did not run out) after
+ * synchronising `stream`.  Uses 4 KB of device memory for the call.
+ */
+tn_status tn_selftest_flow_timeout(void *stream);
+
+/*
  * tn_plan_steps -- the per-slice launch sequence of a plan (host only).
  * Nodes (0..n_tensors-2, tree order) run in launch steps: a wave step runs
  * all small nodes of one tree level in one launch, a single step runs one

@@ -72,6 +72,8 @@ _lib.tn_contract_grad_instances.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, c
 _lib.tn_contract_instances_keep.restype = ctypes.c_int
 _lib.tn_contract_instances_keep.argtypes = [_vp, _i32p, ctypes.c_int, ctypes.c_int32, _i64p, _vp, _vp,
                                             ctypes.c_int32, _vp]
+_lib.tn_selftest_flow_timeout.restype = ctypes.c_int
+_lib.tn_selftest_flow_timeout.argtypes = [_vp]
 _lib.tn_contract_noalloc.restype = ctypes.c_int
 _lib.tn_contract_noalloc.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, _vp, ctypes.c_int32, _i64p,
                                      _vp]
@@ -100,6 +102,7 @@ _lib.tn_version.argtypes = []
 
 EXPORTS = ["tn_create", "tn_set_tensor", "tn_contract", "tn_contract_ex", "tn_contract_grad",
            "tn_contract_grad_ex", "tn_contract_grad_instances", "tn_contract_instances_keep",
+           "tn_selftest_flow_timeout",
            "tn_contract_noalloc", "tn_contract_instances", "tn_autotune", "tn_plan_info", "tn_plan_steps",
            "tn_batch_create",
            "tn_batch_contract", "tn_batch_destroy", "tn_destroy", "tn_last_error", "tn_version"]
@@ -224,6 +227,12 @@ def tn_contract_grad_instances(h: int, pairs, sliced, mode: int, n_inst: int, le
                                            mode, n_inst, _p(st, ctypes.c_int64) if st is not None else None,
                                            adj_ptr, adj_mem, int(adj_exp2), adj_exp2_dev or None, gp, flags,
                                            int(slice_begin), int(slice_count), stream))
+
+
+def tn_selftest_flow_timeout(stream: int = 0) -> int:
+    """Failure-detection self-test: the status of a dataflow wait that is
+    made to run out (TN_ETIMEOUT expected).  Does not raise for it."""
+    return int(_lib.tn_selftest_flow_timeout(stream))
 
 
 def tn_contract_noalloc(h: int, pairs, sliced, out_ptr: int, out_mem: int, exp_ptr: int,

@@ -383,6 +383,64 @@ tn_status tn_plan_info(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
     return TN_OK;
 }
 
+tn_status tn_selftest_flow_timeout(void* stream) {
+    // one dataflow item (a one-output node) whose child counter nothing
+    // raises: every index below stays inside these small buffers
+    cudaStream_t s = (cudaStream_t)stream;
+    char* buf = nullptr;
+    const size_t kBytes = 4096;
+    TN_CUDA(cudaMalloc(&buf, kBytes));
+    tn::Control* ctl = reinterpret_cast<tn::Control*>(buf);
+    float* A = reinterpret_cast<float*>(buf + 256);
+    float* B = A + 16;
+    float* C = A + 32;
+    unsigned* max_c = reinterpret_cast<unsigned*>(buf + 512);
+    int64_t* exp_c = reinterpret_cast<int64_t*>(buf + 520);
+    unsigned* done = reinterpret_cast<unsigned*>(buf + 576);  // done[0..3]
+    unsigned* head = reinterpret_cast<unsigned*>(buf + 640);
+    int4* deps = reinterpret_cast<int4*>(buf + 704);          // one entry
+    tn::WaveItem* item = reinterpret_cast<tn::WaveItem*>(buf + 768);
+    tn::TileArgs* desc = reinterpret_cast<tn::TileArgs*>(buf + 1024);
+    if (sizeof(tn::TileArgs) > kBytes - 1024) {
+        cudaFree(buf);
+        return fail(TN_EINVAL, "selftest: descriptor larger than its buffer");
+    }
+    tn::Control hc{};
+    hc.slice = 0;
+    hc.slice_begin = 0;
+    hc.slice_end = 1;
+    tn::TileArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.A = A;
+    t.B = B;
+    t.C = C;
+    t.nbatch = 1;
+    t.cfg = tn::kTile64x64;
+    t.split = 1;
+    t.kchunk = 1;
+    t.ctl = ctl;
+    t.sc.max_c = max_c;
+    t.sc.exp_c = exp_c;
+    t.a_leaf = -1;
+    t.b_leaf = -1;
+    const int4 dep = make_int4(1, 1, -1, 0);  // waits for one chunk of node 1: not in the launch
+    tn::WaveItem it{0, 0, 0, 1};
+    cudaError_t e = cudaMemsetAsync(buf, 0, kBytes, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(desc, &t, sizeof(t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(deps, &dep, sizeof(dep), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(item, &it, sizeof(it), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = tn::launch_wave(item, 1, desc, nullptr, false, s, deps, done, head, 1);
+    int32_t status = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&status, &ctl->status, sizeof(status), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (e != cudaSuccess) return fail(TN_ECUDA, std::string("selftest: ") + cudaGetErrorString(e));
+    if (status != TN_OK) return fail((tn_status)status, "selftest: a bounded dataflow wait gave up (as intended)");
+    return TN_OK;
+}
+
 tn_status tn_plan_steps(tn_net* net, const int32_t* tree_pairs, int32_t n_sliced,
                         const int64_t* sliced_labels, tn_mode mode, int32_t cap, int32_t* n_steps,
                         int32_t* step_info, int32_t* step_nodes) {
