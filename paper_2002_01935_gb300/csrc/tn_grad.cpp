@@ -8,8 +8,8 @@
 // and Bbar likewise (holomorphic derivative, conjugated as torch.autograd
 // expects).  Per slice the forward intermediates are recomputed and all kept
 // (no workspace reuse), then the tree is swept from the root to the
-// leaves; leaf adjoints are added into the caller's gradient buffers at the
-// slice's offset, so the result is summed over slices.  A leaf label that
+// leaves; leaf adjoints are added into gradient accumulators at the slice's
+// offset, so the result is summed over slices.  A leaf label that
 // occurs in that tensor only (summed at its first contraction) gives an
 // adjoint constant along it: the gather broadcasts.  Renormalisation
 // exponents are tracked exactly as in the forward pass.
@@ -17,12 +17,16 @@
 // Launch structure.  The forward recompute and the sweep form one list of
 // nodes (forward nodes, then adjoint nodes root to leaves) scheduled like
 // the forward pass: by dependency level, the small nodes of consecutive
-// levels as one dataflow wave launch, the others one launch each.  All of
-// it reads the leaves from a library-owned image (refreshed by one gather
-// launch per call) and adds the leaf adjoints into library-owned
-// accumulators (copied, or added, to the caller's buffers by one launch at
-// the end), so the per-slice sequence has no per-call pointer in it: it is
-// captured once as a CUDA graph and replayed by every later call.
+// levels as one dataflow wave launch, the others one launch each; every
+// adjoint node comes after every forward node, so the per-slice sequence
+// is two CUDA graphs (forward, sweep).  Both read the leaves from a
+// library-owned image (refreshed by one gather launch per call) and the
+// sweep adds the leaf adjoints into library-owned accumulators (copied, or
+// added, to the caller's buffers by one launch at the end), so neither
+// graph holds a per-call pointer: they are captured once and replayed by
+// every later call.  n copies of the network (shared or per-copy leaves)
+// run in every launch; a caller that ran the forward of those copies in
+// this state (run_grad_forward) can run the sweep alone.
 #include <cuda_runtime.h>
 
 #include <algorithm>
