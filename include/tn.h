@@ -345,9 +345,11 @@ tn_status tn_contract_noalloc(tn_net *net, const int32_t *tree_pairs, int32_t n_
  *   out        2 doubles per copy: FP64 mantissa (complex (re, im); real
  *              (x, 0)); out_exp2: one int64 per copy; out_mem as
  *              tn_contract.
- * The device state grows to n_inst workspace copies.  Errors: TN_EINVAL,
- * TN_EUNSUPPORTED (open labels, slicing, host leaves, stream capture),
- * TN_ENOMEM, TN_ECUDA.
+ * Each copy count has its own plan, kept in the handle: its kernel choices
+ * and K splits count the copies that share every launch (tn_autotune, which
+ * times single copies, does not touch it), and its device state holds
+ * n_inst workspace copies.  Errors: TN_EINVAL, TN_EUNSUPPORTED (open
+ * labels, slicing, host leaves, stream capture), TN_ENOMEM, TN_ECUDA.
  */
 tn_status tn_contract_instances(tn_net *net, const int32_t *tree_pairs, tn_mode mode, int32_t n_inst,
                                 const int64_t *leaf_inst_stride, double *out, int64_t *out_exp2,
