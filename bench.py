@@ -168,15 +168,21 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                 "--format=csv,noheader,nounits", "-lms", "50", "-f", self.path],
                 stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            # the timed region starts once sampling runs (first row written)
+            t0 = time.time()
+            while time.time() - t0 < 3.0 and self.proc.poll() is None:
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
     def stop(self):
         if self.proc is None:
             return None
-        time.sleep(0.25)
+        time.sleep(0.06)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -1012,7 +1018,9 @@ def run_node(args, torch, dist, rank, world, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 400 for the sub-millisecond workloads, so that the "
+                         "timed region spans several clock samples; 5 otherwise; 20 for --impl reference)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="ising100", choices=list(WORKLOAD_NAMES))
     ap.add_argument("--mode", default="tf32_split", choices=MODES)
@@ -1027,6 +1035,9 @@ def main():
     ap.add_argument("--no-modes", action="store_true", help="skip the per-mode comparison")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planner's kernel choices")
     args = ap.parse_args()
+    if args.steps is None:
+        short = args.workload in ("ising100", "circuit4x4", "circuit5x5")
+        args.steps = 20 if args.impl == "reference" else (400 if short else 5)
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(args.warmup, 3)
