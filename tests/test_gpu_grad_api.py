@@ -412,3 +412,60 @@ def test_slice_ranges_sum_to_the_full_gradient(torch, parts):
     with pytest.raises(binding.TNError):
         tnw.grad(pairs, sliced, "fp32", adj, slice_begin=d - 1, slice_count=2)
     tnw.close()
+
+
+def test_keep_forward_refuses_open_outputs(torch):
+    """The keeping forward serves scalar networks (one value per copy)."""
+    from paper_2002_01935_gb300 import binding
+    net, pairs, sliced, ts, tnw = _setup(torch, seed=41, n_open=1)
+    lv = list(ts)
+    strides = [0] * len(ts)
+    lv[0] = torch.stack([ts[0], ts[0]])
+    strides[0] = ts[0].numel()
+    tnw.set_tensors(lv)
+    with pytest.raises(binding.TNError):
+        tnw.contract_instances_keep(pairs, "fp32", 2, strides)
+    tnw.close()
+
+
+def test_single_tensor_network_gradient(torch):
+    """A network of one tensor: its value is the sum of its entries over the
+    summed labels, the gradient of a leaf is conj(adjoint) broadcast."""
+    from paper_2002_01935_gb300 import binding
+    rng = np.random.default_rng(3)
+    t = (rng.standard_normal((2, 2, 2)) + 1j * rng.standard_normal((2, 2, 2))).astype(np.complex64)
+    labels, dims = [[1, 2, 3]], {1: 2, 2: 2, 3: 2}
+    tt = torch.from_numpy(t).cuda()
+    tnw = binding.TensorNetwork(labels, dims, [2], [tt], complex_=True)
+    adj = np.array([0.5 - 1.0j, 2.0 + 0.25j])
+    g = tnw.grad([], [], "fp32", adj)[0].cpu().numpy()
+    # value[o] = sum over a, c of T[a, o, c]: d value[o] / d T[a, o, c] = 1, so
+    # the gradient (conj(derivative) * adjoint) is adj[o] along every a, c
+    ref = np.broadcast_to(adj[None, :, None], (2, 2, 2))
+    assert np.allclose(g, ref, rtol=1e-6, atol=1e-6)
+    tnw.close()
+
+
+@pytest.mark.parametrize("parts", [2])
+def test_grad_instances_slice_ranges(torch, parts):
+    """Copies and slice ranges together: the ranges add up to the full sweep."""
+    from paper_2002_01935_gb300 import shard
+    net, pairs, sliced, ts, tnw = _setup(torch, seed=42, n_open=0, sliced_n=2)
+    B = 3
+    lv = list(ts)
+    strides = [0] * len(ts)
+    lv[2] = torch.stack([ts[2] * np.float32(1.0 + 0.1 * i) for i in range(B)])
+    strides[2] = ts[2].numel()
+    tnw.set_tensors(lv)
+    adjs = torch.from_numpy(np.array([1.0 + 0.5j, -0.5 + 0.25j, 0.75 - 1.0j])).cuda()
+    d = int(np.prod([net.dims[l] for l in sliced]))
+    full = [g.cpu().numpy() for g in tnw.grad_instances(pairs, sliced, "fp32", B, strides, adjs)]
+    acc = [np.zeros_like(g) for g in full]
+    for r in range(parts):
+        b, cnt = shard.slice_range(r, parts, d)
+        part = tnw.grad_instances(pairs, sliced, "fp32", B, strides, adjs, slice_begin=b, slice_count=cnt)
+        for a, g in zip(acc, part):
+            a += g.cpu().numpy()
+    for a, f in zip(acc, full):
+        assert np.linalg.norm(a - f) <= 1e-6 * (np.linalg.norm(f) + 1e-30)
+    tnw.close()
