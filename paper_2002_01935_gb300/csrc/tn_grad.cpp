@@ -908,7 +908,7 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
     tn_status st = prepare(d, p, unit, n_inst, leaf_inst_stride, stream, varying, err);
     if (st != TN_OK) return st;
     GradState& G = *p.grad;
-    if (kept_forward && G.varying != varying) {
+    if (kept_forward && (G.varying != varying || !G.kept)) {
         err = "tn_contract_grad: TN_GRAD_KEPT_FORWARD with other leaf strides than the kept forward";
         return TN_EINVAL;
     }
