@@ -55,6 +55,7 @@ sys.path.insert(0, ROOT)
 METRIC = "contraction FLOP/s & % roofline per tree; s/amplitude; rel. error vs FP64 oracle"
 WORKLOAD_NAMES = {
     "ising100": "ising_rr3_n100_beta0.3_greedy_ws24",
+    "ising100_hyper": "ising_rr3_n100_beta0.3_hyperedge_form_greedy_ws24",
     "circuit4x4": "circuit_4x4_8cyc_greedy_amplitude",
     "circuit5x5": "circuit_5x5_10cyc_greedy_amplitude",
     "circuit7x7": "circuit_7x7_14cyc_hypergreedy_ws28_slice_sample",
@@ -78,9 +79,9 @@ MODE_PASSES = {"tf32_split": 3, "bf16_split": 3, "tf32_3m": 1}
 # workloads
 # --------------------------------------------------------------------------
 
-def wl_ising(seed: int, n: int = 100, target: float = 24.0):
+def wl_ising(seed: int, n: int = 100, target: float = 24.0, hyper: bool = False):
     from paper_2002_01935_gb300 import inputs, planner
-    net = inputs.random_ising(n, seed)
+    net = inputs.random_ising_hyper(n, seed) if hyper else inputs.random_ising(n, seed)
     pairs = planner.greedy_tree(net.labels, net.dims, net.open)
     info = planner.tree_info(net.labels, net.dims, pairs, net.open)
     sliced = planner.slice_greedy(net.labels, net.dims, pairs, net.open, target) if info.W > target else []
@@ -88,6 +89,7 @@ def wl_ising(seed: int, n: int = 100, target: float = 24.0):
     return {"net": net, "pairs": pairs, "sliced": sliced, "info": info,
             "slice_begin": 0, "slice_count": int(info.d_sliced), "oracle": "full",
             "config": {"n_vertices": n, "beta": 0.3, "J": "+-1", "graph_seed": seed,
+                       "form": "hyperedge (one label per spin)" if hyper else "COPY tensor per vertex",
                        "tree": "greedy (alpha=1, tau=0)", "target_W_s": target}}
 
 
@@ -272,11 +274,12 @@ def run_reference(args):
     from oracle import build as obuild
     from oracle import tree
     obuild.build()
-    if args.workload not in ("ising100", "circuit4x4", "circuit5x5"):
+    if args.workload not in ("ising100", "ising100_hyper", "circuit4x4", "circuit5x5"):
         print(json.dumps({"impl": "reference", "unavailable":
                           f"the FP64 oracle needs hours per step on the {args.workload} workload"}))
         return 0
     w = (wl_ising(0) if args.workload == "ising100" else
+         wl_ising(0, hyper=True) if args.workload == "ising100_hyper" else
          wl_circuit(4, 4, 8, 0) if args.workload == "circuit4x4" else wl_circuit(5, 5, 10, 0))
     net, pairs, sliced, info = w["net"], w["pairs"], w["sliced"], w["info"]
     for _ in range(1 if args.warmup > 0 else 0):
@@ -410,6 +413,8 @@ def run_network(args, torch, dist, rank, world, local):
 
     if args.workload == "ising100":
         w = wl_ising(rank)
+    elif args.workload == "ising100_hyper":
+        w = wl_ising(rank, hyper=True)
     elif args.workload == "circuit4x4":
         w = wl_circuit(4, 4, 8, rank)
     elif args.workload == "circuit5x5":
@@ -1036,7 +1041,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the planner's kernel choices")
     args = ap.parse_args()
     if args.steps is None:
-        short = args.workload in ("ising100", "circuit4x4", "circuit5x5")
+        short = args.workload in ("ising100", "ising100_hyper", "circuit4x4", "circuit5x5")
         args.steps = 20 if args.impl == "reference" else (400 if short else 5)
     if args.impl == "reference":
         return run_reference(args)

@@ -332,6 +332,41 @@ def random_ising(n_vertices: int, seed: int, beta: float = 0.3, degree: int = 3)
     return ising_network(n_vertices, edges, J, beta)
 
 
+def ising_hyper_network(n_vertices: int, edges: Sequence[Tuple[int, int]], J: Sequence[float],
+                        beta: float) -> Network:
+    """Hyperedge form of the same Z (Sec. 3.5: a COPY tensor is a hyperedge):
+    the spin of vertex v is one label (id v) shared by the matrices of all
+    its edges, M_e[s_u, s_v] = exp(beta J_e s(a) s(b)) over labels (u, v); a
+    vertex without edges gets a vector of ones.  Leaves: the edge matrices
+    in edge order, then those vectors."""
+    spin = np.array([1.0, -1.0])
+    tensors: List[np.ndarray] = []
+    labels: List[List[int]] = []
+    deg = [0] * n_vertices
+    for ei, (u, v) in enumerate(edges):
+        tensors.append(np.exp(beta * float(J[ei]) * np.outer(spin, spin)))
+        labels.append([int(u), int(v)])
+        deg[u] += 1
+        deg[v] += 1
+    for v in range(n_vertices):
+        if deg[v] == 0:
+            tensors.append(np.ones(2))
+            labels.append([v])
+    dims = {v: 2 for v in range(n_vertices)}
+    net = Network(tensors, labels, dims, [],
+                  meta={"kind": "ising_hyper", "edges": [tuple(e) for e in edges],
+                        "J": [float(j) for j in J], "beta": beta, "n": n_vertices})
+    net.validate()
+    return net
+
+
+def random_ising_hyper(n_vertices: int, seed: int, beta: float = 0.3, degree: int = 3) -> Network:
+    """random_ising's graph and couplings (same seed) in the hyperedge form."""
+    edges = random_regular_graph(n_vertices, degree, seed)
+    J = ising_couplings(len(edges), seed + 1_000_003)
+    return ising_hyper_network(n_vertices, edges, J, beta)
+
+
 # ---------------------------------------------------------------------------
 # Small random networks for brute-force checks
 # ---------------------------------------------------------------------------

@@ -235,6 +235,20 @@ def test_ising_matches_enumeration(n, seed):
     assert abs(log_z(net, pairs) - ref) < 1e-12
 
 
+@pytest.mark.parametrize("n,seed", [(8, 0), (12, 4), (16, 9)])
+def test_ising_hyperedge_form_matches_enumeration(n, seed):
+    """The hyperedge form (one label per spin, shared by the matrices of its
+    three edges) gives the same Z as the enumeration and as the COPY form."""
+    net = inputs.random_ising_hyper(n, seed)
+    edges, J = net.meta["edges"], net.meta["J"]
+    assert all(sum(l in ls for ls in net.labels) == 3 for l in net.dims)  # degree-3 hyperedges
+    lz = log_z(net, planner.greedy_tree(net.labels, net.dims, net.open))
+    assert abs(lz - ising.log_z_enumerate(n, edges, J, 0.3)) < 1e-12
+    copy_form = inputs.random_ising(n, seed)
+    assert abs(lz - log_z(copy_form, planner.greedy_tree(copy_form.labels, copy_form.dims,
+                                                         copy_form.open))) < 1e-12
+
+
 def test_ising_closed_forms():
     # beta = 0: Z = 2^N exactly
     edges = inputs.random_regular_graph(40, 3, seed=4)
