@@ -121,3 +121,33 @@ def test_sliced_cost_formula():
         expect += 2.0 ** base.vc[k] / (2.0 if e in u else 1.0)
     assert info.C == pytest.approx(expect)
     assert info.C_s == pytest.approx(2 * expect)
+
+
+def test_hyper_greedy_is_seeded_valid_and_no_worse_than_greedy():
+    """Hyper-Greedy (Sec. 3.4): the same seed gives the same tree; the tree
+    is valid, never costlier than the plain greedy tree it starts from, and
+    gives the network's value (tree independence, oracle)."""
+    from oracle import tree
+    circ = inputs.random_circuit(3, 3, 6, seed=2)
+    net = inputs.circuit_network(circ, inputs.random_bitstrings(9, 1, seed=7)[0])
+    p1, s1, i1 = planner.hyper_greedy(net.labels, net.dims, net.open, trials=8, seed=5)
+    p2, s2, i2 = planner.hyper_greedy(net.labels, net.dims, net.open, trials=8, seed=5)
+    assert p1 == p2 and s1 == s2 and s1 == []
+    planner.validate_tree(net.n_tensors, p1)
+    g = planner.greedy_tree(net.labels, net.dims, net.open)
+    assert i1.C <= planner.tree_info(net.labels, net.dims, g, net.open).C
+    v_h = complex(tree.value(net.tensors, net.labels, net.dims, net.open, p1))
+    v_g = complex(tree.value(net.tensors, net.labels, net.dims, net.open, g))
+    assert abs(v_h - v_g) <= 1e-12 * abs(v_g)
+
+
+def test_hyper_greedy_with_slicing_meets_the_width_target():
+    net = inputs.random_ising(60, seed=3)
+    g = planner.greedy_tree(net.labels, net.dims, net.open)
+    target = planner.tree_info(net.labels, net.dims, g, net.open).W - 4
+    pairs, sliced, info = planner.hyper_greedy(net.labels, net.dims, net.open, trials=6, seed=1,
+                                               target_width=target)
+    assert info.W <= target + 1e-9 and len(sliced) > 0
+    # the reported cost is the sliced cost of that tree and slicing
+    again = planner.tree_info(net.labels, net.dims, pairs, net.open, sliced)
+    assert again.C_s == info.C_s and again.d_sliced == info.d_sliced
