@@ -62,6 +62,7 @@ WORKLOAD_NAMES = {
     "batch": "batch_6x6_12cyc_amplitudes_plus_256_ising",
     "grad5x4": "grad_5x4_12cyc_fsim_params_64_bitstrings",
     "node": "single_complex_node",
+    "sample": "sample_5x4_12cyc_open6_fidelity_mixture",
 }
 MODES = ["fp32", "tf32_split", "bf16_split", "tf32_3m"]
 # accuracy each mode is held to (relative, against the FP64 oracle)
@@ -933,6 +934,74 @@ def run_grad(args, torch, dist, rank, world, local):
     return 0
 
 
+def run_sample(args, torch, dist, rank, world, local):
+    """Bitstring samples of a 5x4, 12-cycle circuit (Sec. 5's sampling
+    procedure): 14 fixed qubits drawn uniformly, the 2^6 amplitudes over
+    the other 6 qubits from one open-output contraction on the GPU, x_f drawn
+    from them.  value = contraction FLOP/s; s_per_sample beside it."""
+    import numpy as np
+    from oracle import tree as otree
+    from paper_2002_01935_gb300 import inputs, planner, sampling
+
+    R, C, T = 5, 4, 12
+    circ = inputs.random_circuit(R, C, T, seed=rank)
+    open_q = list(range(R * C - 6, R * C))
+    prov = sampling.OpenAmplitudes(circ, open_q, mode=args.mode)
+    net0 = inputs.circuit_network(circ, [0] * (R * C), open_qubits=open_q)
+    info = planner.tree_info(net0.labels, net0.dims, prov.pairs, net0.open)
+    sampling.sample(R * C, open_q, prov, args.warmup, seed=99)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    clk.start()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s = sampling.sample(R * C, open_q, prov, args.steps, fidelity=1.0, seed=1000 + rank)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    total = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        tt = torch.tensor([total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = float(tt.item())
+    flops = 8.0 * info.C * args.steps
+    rel, cpu = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        x_u = [s[0][0][q] for q in prov.fixed]
+        got = prov(x_u)
+        bits = [0] * (R * C)
+        for q, b in zip(prov.fixed, x_u):
+            bits[q] = b
+        t0 = time.perf_counter()
+        m, e = otree.contract_net(inputs.circuit_network(circ, bits, open_qubits=open_q), prov.pairs)
+        t_or = time.perf_counter() - t0
+        ref = np.asarray(m) * 2.0 ** e
+        rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        cpu = {"value": 8.0 * info.C / t_or / 1e12, "unit": "TFLOP/s", "cores": otree.max_threads(),
+               "kind": "oracle", "s_per_contraction": t_or,
+               "sample": "one open-output contraction (2^6 amplitudes) of the first sample's x_u"}
+    prov.close()
+    line = {
+        "metric": METRIC, "value": flops * world / total / 1e12, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES[args.workload], "mode": args.mode, "qubits": R * C,
+                   "cycles": T, "open_qubits": open_q, "amplitudes_per_contraction": 64,
+                   "fidelity": 1.0, "W": info.W, "C": info.C, "tree": "greedy (alpha=1, tau=0)",
+                   "step": "one sample: uniform x_u, one contraction, x_f drawn on the host"},
+        "s_per_sample": total / args.steps,
+        "rel_err_vs_oracle": rel,
+        "roofline": None, "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_node(args, torch, dist, rank, world, local):
     import numpy as np
     from paper_2002_01935_gb300 import binding, inputs
@@ -1066,6 +1135,8 @@ def main():
         rc = run_grad(args, torch, dist, rank, world, local)
     elif args.workload == "node":
         rc = run_node(args, torch, dist, rank, world, local)
+    elif args.workload == "sample":
+        rc = run_sample(args, torch, dist, rank, world, local)
     else:
         rc = run_network(args, torch, dist, rank, world, local)
     if dist:
