@@ -80,9 +80,11 @@ MODE_PASSES = {"tf32_split": 3, "bf16_split": 3, "tf32_3m": 1}
 # workloads
 # --------------------------------------------------------------------------
 
-def wl_ising(seed: int, n: int = 100, target: float = 24.0, hyper: bool = False):
-    from paper_2002_01935_gb300 import inputs, planner
+def wl_ising(seed: int, n: int = 100, target: float = 24.0, hyper: bool = False, simplified: bool = False):
+    from paper_2002_01935_gb300 import inputs, planner, simplify
     net = inputs.random_ising_hyper(n, seed) if hyper else inputs.random_ising(n, seed)
+    if simplified:
+        net, _ = simplify.simplify(net)
     pairs = planner.greedy_tree(net.labels, net.dims, net.open)
     info = planner.tree_info(net.labels, net.dims, pairs, net.open)
     sliced = planner.slice_greedy(net.labels, net.dims, pairs, net.open, target) if info.W > target else []
@@ -91,20 +93,24 @@ def wl_ising(seed: int, n: int = 100, target: float = 24.0, hyper: bool = False)
             "slice_begin": 0, "slice_count": int(info.d_sliced), "oracle": "full",
             "config": {"n_vertices": n, "beta": 0.3, "J": "+-1", "graph_seed": seed,
                        "form": "hyperedge (one label per spin)" if hyper else "COPY tensor per vertex",
+                       "simplified": net.meta.get("simplified"),
                        "tree": "greedy (alpha=1, tau=0)", "target_W_s": target}}
 
 
-def wl_circuit(rows: int, cols: int, cycles: int, seed: int):
-    from paper_2002_01935_gb300 import inputs, planner
+def wl_circuit(rows: int, cols: int, cycles: int, seed: int, simplified: bool = False):
+    from paper_2002_01935_gb300 import inputs, planner, simplify
     circ = inputs.random_circuit(rows, cols, cycles, seed=seed)
     bits = inputs.random_bitstrings(rows * cols, 1, seed=1000 + seed)[0]
     net = inputs.circuit_network(circ, bits)
+    if simplified:
+        net, _ = simplify.simplify(net)
     pairs = planner.greedy_tree(net.labels, net.dims, net.open)
     info = planner.tree_info(net.labels, net.dims, pairs, net.open)
     return {"net": net, "pairs": pairs, "sliced": [], "info": info, "slice_begin": 0,
             "slice_count": 1, "oracle": "full",
             "config": {"qubits": rows * cols, "grid": f"{rows}x{cols}", "cycles": cycles,
                        "circuit_seed": seed, "bitstring_seed": 1000 + seed,
+                       "simplified": net.meta.get("simplified"),
                        "tree": "greedy (alpha=1, tau=0)"}}
 
 
@@ -279,9 +285,11 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "unavailable":
                           f"the FP64 oracle needs hours per step on the {args.workload} workload"}))
         return 0
-    w = (wl_ising(0) if args.workload == "ising100" else
+    simp = bool(getattr(args, "simplify", False))
+    w = (wl_ising(0, simplified=simp) if args.workload == "ising100" else
          wl_ising(0, hyper=True) if args.workload == "ising100_hyper" else
-         wl_circuit(4, 4, 8, 0) if args.workload == "circuit4x4" else wl_circuit(5, 5, 10, 0))
+         wl_circuit(4, 4, 8, 0, simplified=simp) if args.workload == "circuit4x4" else
+         wl_circuit(5, 5, 10, 0, simplified=simp))
     net, pairs, sliced, info = w["net"], w["pairs"], w["sliced"], w["info"]
     for _ in range(1 if args.warmup > 0 else 0):
         tree.contract_net(net, pairs, sliced)
@@ -296,7 +304,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": dict(workload=WORKLOAD_NAMES[args.workload], W_s=info.W, C=info.C,
+            "config": dict(workload=WORKLOAD_NAMES[args.workload] + ("_simplified" if simp else ""),
+                           W_s=info.W, C=info.C,
                            d_sliced=info.d_sliced, **w["config"]),
             "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": tree.max_threads(),
                              "kind": "oracle", "sample": f"{args.steps} full contractions"},
@@ -413,13 +422,13 @@ def run_network(args, torch, dist, rank, world, local):
     from paper_2002_01935_gb300 import binding
 
     if args.workload == "ising100":
-        w = wl_ising(rank)
+        w = wl_ising(rank, simplified=args.simplify)
     elif args.workload == "ising100_hyper":
         w = wl_ising(rank, hyper=True)
     elif args.workload == "circuit4x4":
-        w = wl_circuit(4, 4, 8, rank)
+        w = wl_circuit(4, 4, 8, rank, simplified=args.simplify)
     elif args.workload == "circuit5x5":
-        w = wl_circuit(5, 5, 10, rank)
+        w = wl_circuit(5, 5, 10, rank, simplified=args.simplify)
     else:
         w = wl_circuit7x7(rank, args.slices)
     net, pairs, sliced, info = w["net"], w["pairs"], w["sliced"], w["info"]
@@ -574,7 +583,8 @@ def run_network(args, torch, dist, rank, world, local):
     # (which also advances the slice counter when it is one block)
     n_out = math.prod(net.dims[l] for l in net.open)
     launches_per_call = 2 + groups * (1 + (n_out > 256) + sum(s.get("launches", 1) for s in steps))
-    cfg = {"workload": WORKLOAD_NAMES[args.workload], "mode": mode, "W_s": info.W, "C": info.C,
+    cfg = {"workload": WORKLOAD_NAMES[args.workload] + ("_simplified" if args.simplify else ""),
+           "mode": mode, "W_s": info.W, "C": info.C,
            "d_sliced": info.d_sliced, "slices_per_step": sc,
            "flops_per_step": flops_step, "nodes": len(pairs),
            "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
@@ -1105,6 +1115,9 @@ def main():
     ap.add_argument("--ising-max-n", type=int, default=100,
                     help="batch: largest Ising N (even N uniform in [40, this])")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--simplify", action="store_true",
+                    help="structure simplifications (Sec. 3.7) of the network before planning "
+                         "(ising100, circuit4x4, circuit5x5; not the configs' plain method)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip the per-mode comparison")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planner's kernel choices")

@@ -1,0 +1,229 @@
+"""Structure simplifications of a tensor network before path search
+(Sec. 3.7), applied on the host: they change the network the GPU executes,
+never its value.
+
+Rules, each applied where it finds something to do, cycled in the order
+antidiagonal-gauging, diagonal-reduction, column-reduction,
+rank-simplification until none changes the network:
+
+- column-reduction: a tensor that vanishes unless index i_x takes one value
+  c projects that label onto c in every tensor carrying it (the label
+  leaves the network);
+- diagonal-reduction: a tensor that vanishes unless i_x == i_y keeps only
+  its diagonal, and label i_y becomes i_x everywhere (i_x turns into a
+  hyperedge; tensors that then carry i_x twice keep their diagonal);
+- antidiagonal-gauging: a tensor that vanishes unless i_x == d - 1 - i_y has
+  the order of label i_y reversed in every tensor carrying it, which makes
+  it diagonal for the rule above;
+- rank-simplification: pairs of tensors sharing a label are contracted
+  (numpy, FP64 or complex128) when the result's rank is at most the larger
+  of their two ranks -- for networks without hyperedges, absorbing every
+  rank-1 and rank-2 tensor into a neighbour -- smallest result first.
+
+Zero tests are relative: |entry| <= rtol * max |entry| of the tensor.  Open
+labels are never projected, merged away or reversed, so the simplified
+network has the same output axes.  ``frozen`` names leaves whose entries
+may change between calls with the same simplified structure (e.g. the
+output states of sampled bitstrings): the sparsity rules do not inspect
+them, and rank-simplification leaves them alone, so that a tree found for
+one bitstring serves all.  Split-simplification (Sec. 3.7's SVD rule) is
+not implemented.
+"""
+from __future__ import annotations
+
+from typing import Dict, Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from .inputs import Network
+
+
+def _zero(t: np.ndarray, mask: np.ndarray, rtol: float) -> bool:
+    m = float(np.max(np.abs(t))) if t.size else 0.0
+    return bool(np.all(np.abs(t[mask]) <= rtol * m))
+
+
+class _Net:
+    def __init__(self, net: Network, frozen: Iterable[int]):
+        self.t: List[Optional[np.ndarray]] = [np.asarray(x) for x in net.tensors]
+        self.l: List[List[int]] = [list(x) for x in net.labels]
+        self.dims: Dict[int, int] = dict(net.dims)
+        self.open = list(net.open)
+        self.frozen = set(frozen)
+
+    def live(self) -> List[int]:
+        return [v for v, t in enumerate(self.t) if t is not None]
+
+    def carriers(self, label: int) -> List[int]:
+        return [v for v in self.live() if label in self.l[v]]
+
+    # --- column-reduction
+    def column(self, rtol: float) -> bool:
+        for v in self.live():
+            if v in self.frozen:
+                continue
+            t, ls = self.t[v], self.l[v]
+            for x, lab in enumerate(ls):
+                if lab in self.open or self.dims[lab] == 1:
+                    continue
+                for c in range(self.dims[lab]):
+                    mask = np.ones(t.shape, dtype=bool)
+                    idx = [slice(None)] * t.ndim
+                    idx[x] = c
+                    mask[tuple(idx)] = False
+                    if _zero(t, mask, rtol):
+                        if any(w in self.frozen for w in self.carriers(lab)):
+                            break
+                        for w in self.carriers(lab):
+                            ax = self.l[w].index(lab)
+                            self.t[w] = np.take(self.t[w], c, axis=ax)
+                            del self.l[w][ax]
+                        del self.dims[lab]
+                        return True
+        return False
+
+    # --- diagonal-reduction (and the diagonal of tensors that carry a label twice)
+    def _dedupe(self, w: int) -> None:
+        while True:
+            ls = self.l[w]
+            dup = next((l for l in ls if ls.count(l) > 1), None)
+            if dup is None:
+                return
+            a = ls.index(dup)
+            b = ls.index(dup, a + 1)
+            self.t[w] = np.diagonal(self.t[w], axis1=a, axis2=b)  # diagonal axis goes last
+            self.l[w] = [l for i, l in enumerate(ls) if i not in (a, b)] + [dup]
+
+    def diagonal(self, rtol: float) -> bool:
+        for v in self.live():
+            if v in self.frozen:
+                continue
+            t, ls = self.t[v], self.l[v]
+            for x in range(len(ls)):
+                for y in range(x + 1, len(ls)):
+                    lx, ly = ls[x], ls[y]
+                    if self.dims[lx] != self.dims[ly] or self.dims[lx] == 1 or ly in self.open:
+                        continue
+                    ix = np.arange(self.dims[lx])
+                    shape = [1] * t.ndim
+                    shape[x] = shape[y] = self.dims[lx]
+                    off = (ix[:, None] != ix[None, :])
+                    mask = np.broadcast_to(off.reshape([self.dims[lx] if i in (x, y) else 1
+                                                        for i in range(t.ndim)]), t.shape)
+                    if not _zero(t, mask, rtol):
+                        continue
+                    if any(w in self.frozen for w in self.carriers(ly)):
+                        continue
+                    for w in self.carriers(ly):
+                        self.l[w] = [lx if l == ly else l for l in self.l[w]]
+                        self._dedupe(w)
+                    del self.dims[ly]
+                    return True
+        return False
+
+    # --- antidiagonal-gauging
+    def antidiagonal(self, rtol: float) -> bool:
+        for v in self.live():
+            if v in self.frozen:
+                continue
+            t, ls = self.t[v], self.l[v]
+            for x in range(len(ls)):
+                for y in range(x + 1, len(ls)):
+                    lx, ly = ls[x], ls[y]
+                    d = self.dims[lx]
+                    if d != self.dims[ly] or d == 1:
+                        continue
+                    ix = np.arange(d)
+                    off = ix[:, None] != (d - 1 - ix[None, :])
+                    mask = np.broadcast_to(off.reshape([d if i in (x, y) else 1 for i in range(t.ndim)]), t.shape)
+                    if not _zero(t, mask, rtol):
+                        continue
+                    diag = ix[:, None] != ix[None, :]
+                    dmask = np.broadcast_to(diag.reshape([d if i in (x, y) else 1 for i in range(t.ndim)]), t.shape)
+                    if _zero(t, dmask, rtol):
+                        continue  # already diagonal (d = 1 or a zero tensor)
+                    flip = ly if ly not in self.open else (lx if lx not in self.open else None)
+                    if flip is None or any(w in self.frozen for w in self.carriers(flip)):
+                        continue
+                    for w in self.carriers(flip):
+                        ax = self.l[w].index(flip)
+                        self.t[w] = np.flip(self.t[w], axis=ax).copy()
+                    return True
+        return False
+
+    # --- rank-simplification
+    def rank(self) -> bool:
+        best = None
+        live = [v for v in self.live() if v not in self.frozen]
+        count: Dict[int, int] = {}
+        for v in self.live():
+            for l in self.l[v]:
+                count[l] = count.get(l, 0) + 1
+        for i, a in enumerate(live):
+            for b in live[i + 1:]:
+                shared = set(self.l[a]) & set(self.l[b])
+                if not shared:
+                    continue
+                out = [l for l in self.l[a] + [l for l in self.l[b] if l not in self.l[a]]
+                       if l in self.open or count[l] > (l in self.l[a]) + (l in self.l[b])]
+                if len(out) > max(len(self.l[a]), len(self.l[b])):
+                    continue
+                size = int(np.prod([self.dims[l] for l in out])) if out else 1
+                key = (size, len(out), a, b)
+                if best is None or key < best[0]:
+                    best = (key, a, b, out)
+        if best is None:
+            return False
+        _, a, b, out = best
+        sym = {}
+        for l in set(self.l[a]) | set(self.l[b]) | set(out):
+            sym[l] = len(sym)
+        letters = "abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ"
+        if len(sym) > len(letters):
+            return False
+        spec = ("".join(letters[sym[l]] for l in self.l[a]) + "," +
+                "".join(letters[sym[l]] for l in self.l[b]) + "->" +
+                "".join(letters[sym[l]] for l in out))
+        self.t[a] = np.einsum(spec, self.t[a], self.t[b])
+        self.l[a] = out
+        self.t[b] = None
+        for l in list(self.dims):
+            if not any(l in self.l[v] for v in self.live()) and l not in self.open:
+                del self.dims[l]
+        return True
+
+    def result(self, meta: dict) -> Network:
+        live = self.live()
+        tensors = [self.t[v] for v in live]
+        labels = [self.l[v] for v in live]
+        if not tensors:
+            tensors, labels = [np.array(1.0)], [[]]
+        used = {l for ls in labels for l in ls} | set(self.open)
+        dims = {l: d for l, d in self.dims.items() if l in used}
+        return Network(tensors, labels, dims, list(self.open), meta=meta)
+
+
+def simplify(net: Network, frozen: Sequence[int] = (), rtol: float = 1e-12,
+             max_rounds: int = 10000) -> Tuple[Network, Dict[str, int]]:
+    """The simplified network (same value, same open labels) and counts of
+    the operations applied.  ``frozen``: leaf indices left out (see module
+    docstring); in the result they come first, in their original order, so
+    that callers can keep addressing them."""
+    w = _Net(net, frozen)
+    done = {"antidiagonal": 0, "diagonal": 0, "column": 0, "rank": 0}
+    for _ in range(max_rounds):
+        changed = False
+        for name in ("antidiagonal", "diagonal", "column", "rank"):
+            fn = getattr(w, name)
+            while (fn(rtol) if name != "rank" else fn()):
+                done[name] += 1
+                changed = True
+        if not changed:
+            break
+    order = [v for v in sorted(w.frozen) if w.t[v] is not None] + \
+        [v for v in w.live() if v not in w.frozen]
+    w.t = [w.t[v] for v in order]
+    w.l = [w.l[v] for v in order]
+    meta = dict(net.meta)
+    meta["simplified"] = dict(done, leaves_before=net.n_tensors)
+    return w.result(meta), done

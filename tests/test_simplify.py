@@ -1,0 +1,87 @@
+"""Structure simplifications (Sec. 3.7) on the host: every rule keeps the
+network's value (FP64 oracle) and its output axes, and does what the paper
+describes on small hand-made cases."""
+import numpy as np
+import pytest
+
+from oracle import tree
+from paper_2002_01935_gb300 import inputs, planner, simplify
+
+
+def _value(net):
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    m, e = tree.contract_net(net, pairs)
+    return np.asarray(m) * 2.0 ** e
+
+
+@pytest.mark.parametrize("case", ["circuit", "circuit_open", "ising", "random", "random_open"])
+def test_simplification_keeps_the_value(case):
+    if case == "circuit":
+        net = inputs.circuit_network(inputs.random_circuit(3, 3, 6, seed=3),
+                                     inputs.random_bitstrings(9, 1, seed=4)[0])
+    elif case == "circuit_open":
+        net = inputs.circuit_network(inputs.random_circuit(3, 3, 5, seed=5), [0] * 9, open_qubits=[7, 2])
+    elif case == "ising":
+        net = inputs.random_ising(24, seed=6)
+    elif case == "random":
+        net = inputs.random_network(9, 14, 31, n_open=0)
+    else:
+        net = inputs.random_network(9, 14, 32, n_open=2)
+    s, done = simplify.simplify(net)
+    assert s.open == net.open
+    assert s.n_tensors <= net.n_tensors
+    a, b = _value(net), _value(s)
+    assert np.shape(a) == np.shape(b)
+    assert np.max(np.abs(a - b)) <= 1e-12 * max(np.max(np.abs(a)), 1e-300)
+
+
+def test_circuit_shrinks_and_ising_becomes_hyperedge_form():
+    c = inputs.circuit_network(inputs.random_circuit(4, 4, 8, seed=0), inputs.random_bitstrings(16, 1, seed=1000)[0])
+    s, done = simplify.simplify(c)
+    assert s.n_tensors < c.n_tensors // 2 and done["rank"] > 0 and done["column"] > 0
+    ising = inputs.random_ising(20, seed=1)
+    s2, done2 = simplify.simplify(ising)
+    # every COPY tensor reduced to its diagonal: each spin is one label in three edge matrices
+    assert done2["diagonal"] == 2 * 20 and s2.n_tensors == 30
+    assert all(len(ls) == 2 for ls in s2.labels)
+
+
+def test_column_reduction_projects_the_label():
+    t = np.array([[1.0, 0.0], [2.0, 0.0]])          # vanishes unless b == 0
+    u = np.array([[3.0, 4.0], [5.0, 6.0]])           # labels (b, c)
+    net = inputs.Network([t, u, np.array([1.0, 1.0]), np.array([1.0, 2.0])],
+                         [[0, 1], [1, 2], [0], [2]], {0: 2, 1: 2, 2: 2}, [])
+    w = simplify._Net(net, ())
+    assert w.column(1e-12)
+    assert 1 not in w.dims and w.l[1] == [2] and np.allclose(w.t[1], [3.0, 4.0])
+
+
+def test_diagonal_reduction_makes_a_hyperedge():
+    d = np.diag([2.0, -1.0])                          # labels (a, b): zero off the diagonal
+    net = inputs.Network([d, np.array([1.0, 3.0]), np.array([5.0, 7.0])], [[0, 1], [0], [1]],
+                         {0: 2, 1: 2}, [])
+    w = simplify._Net(net, ())
+    assert w.diagonal(1e-12)
+    assert 1 not in w.dims and w.l == [[0], [0], [0]]
+    s, _ = simplify.simplify(net)
+    assert np.isclose(float(_value(s)), 2.0 * 1 * 5 - 1.0 * 3 * 7)
+
+
+def test_antidiagonal_gauging_then_diagonal():
+    x = np.array([[0.0, 2.0], [3.0, 0.0]])           # vanishes unless a == 1 - b
+    net = inputs.Network([x, np.array([1.0, 4.0]), np.array([2.0, 5.0])], [[0, 1], [0], [1]],
+                         {0: 2, 1: 2}, [])
+    w = simplify._Net(net, ())
+    assert w.antidiagonal(1e-12) and w.diagonal(1e-12)
+    s, done = simplify.simplify(net)
+    assert np.isclose(float(_value(s)), float(_value(net)))
+
+
+def test_frozen_leaves_are_kept_first_and_untouched():
+    circ = inputs.random_circuit(3, 3, 4, seed=9)
+    net = inputs.circuit_network(circ, [1, 0, 1, 1, 0, 0, 1, 0, 1])
+    out_leaves = list(range(net.n_tensors - 9, net.n_tensors))
+    s, _ = simplify.simplify(net, frozen=out_leaves)
+    for i, v in enumerate(out_leaves):
+        assert np.array_equal(s.tensors[i], net.tensors[v]) and s.labels[i] == net.labels[v]
+    assert np.max(np.abs(_value(s) - _value(net))) <= 1e-12 * np.max(np.abs(_value(net)))
