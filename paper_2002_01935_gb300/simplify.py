@@ -4,7 +4,8 @@ never its value.
 
 Rules, each applied where it finds something to do, cycled in the order
 antidiagonal-gauging, diagonal-reduction, column-reduction,
-rank-simplification until none changes the network:
+rank-simplification, split-simplification until none changes the
+network:
 
 - column-reduction: a tensor that vanishes unless index i_x takes one value
   c projects that label onto c in every tensor carrying it (the label
@@ -18,16 +19,20 @@ rank-simplification until none changes the network:
 - rank-simplification: pairs of tensors sharing a label are contracted
   (numpy, FP64 or complex128) when the result's rank is at most the larger
   of their two ranks -- for networks without hyperedges, absorbing every
-  rank-1 and rank-2 tensor into a neighbour -- smallest result first.
+  rank-1 and rank-2 tensor into a neighbour -- and its size at most the
+  larger of their sizes, smallest result first;
+- split-simplification: a tensor with an exact low-rank decomposition
+  across a bipartition of its labels (SVD, singular values above rtol of
+  the largest), whose two factors are both smaller than the tensor, is
+  replaced by the factors joined by a new label.
 
 Zero tests are relative: |entry| <= rtol * max |entry| of the tensor.  Open
 labels are never projected, merged away or reversed, so the simplified
 network has the same output axes.  ``frozen`` names leaves whose entries
 may change between calls with the same simplified structure (e.g. the
 output states of sampled bitstrings): the sparsity rules do not inspect
-them, and rank-simplification leaves them alone, so that a tree found for
-one bitstring serves all.  Split-simplification (Sec. 3.7's SVD rule) is
-not implemented.
+them, and rank- and split-simplification leave them alone, so that a tree
+found for one bitstring serves all.
 """
 from __future__ import annotations
 
@@ -169,6 +174,10 @@ class _Net:
                 if len(out) > max(len(self.l[a]), len(self.l[b])):
                     continue
                 size = int(np.prod([self.dims[l] for l in out])) if out else 1
+                # never larger than the larger input: this also keeps the
+                # factors of a split from being merged back
+                if size > max(self.t[a].size, self.t[b].size):
+                    continue
                 key = (size, len(out), a, b)
                 if best is None or key < best[0]:
                     best = (key, a, b, out)
@@ -192,6 +201,47 @@ class _Net:
                 del self.dims[l]
         return True
 
+    # --- split-simplification
+    def split(self, rtol: float) -> bool:
+        """A tensor with an exact low-rank decomposition across a bipartition
+        of its labels, t = l r with max(size(l), size(r)) < size(t), is
+        replaced by l and r joined by a new label (SVD; singular values
+        above rtol times the largest are kept)."""
+        for v in self.live():
+            if v in self.frozen:
+                continue
+            t, ls = self.t[v], self.l[v]
+            k = len(ls)
+            if k < 3 or k > 12:
+                continue
+            size = t.size
+            for mask in range(1, 1 << (k - 1)):  # bipartitions (label 0 on the left... or not)
+                left = [i for i in range(k) if (mask >> i) & 1]
+                right = [i for i in range(k) if not (mask >> i) & 1]
+                if not left or not right:
+                    continue
+                dl = int(np.prod([t.shape[i] for i in left]))
+                dr = int(np.prod([t.shape[i] for i in right]))
+                if min(dl, dr) < 2:
+                    continue
+                mat = np.transpose(t, left + right).reshape(dl, dr)
+                u, s, vh = np.linalg.svd(mat, full_matrices=False)
+                if s.size == 0 or not s[0] > 0:
+                    continue
+                r = int(np.sum(s > rtol * s[0]))
+                if max(dl * r, dr * r) >= size:
+                    continue
+                new = max(self.dims) + 1 if self.dims else 0
+                lt = (u[:, :r] * s[:r]).reshape([t.shape[i] for i in left] + [r])
+                rt = vh[:r, :].reshape([r] + [t.shape[i] for i in right])
+                self.t[v] = lt
+                self.l[v] = [ls[i] for i in left] + [new]
+                self.t.append(rt)
+                self.l.append([new] + [ls[i] for i in right])
+                self.dims[new] = r
+                return True
+        return False
+
     def result(self, meta: dict) -> Network:
         live = self.live()
         tensors = [self.t[v] for v in live]
@@ -204,16 +254,16 @@ class _Net:
 
 
 def simplify(net: Network, frozen: Sequence[int] = (), rtol: float = 1e-12,
-             max_rounds: int = 10000) -> Tuple[Network, Dict[str, int]]:
+             max_rounds: int = 10000, split: bool = True) -> Tuple[Network, Dict[str, int]]:
     """The simplified network (same value, same open labels) and counts of
     the operations applied.  ``frozen``: leaf indices left out (see module
     docstring); in the result they come first, in their original order, so
     that callers can keep addressing them."""
     w = _Net(net, frozen)
-    done = {"antidiagonal": 0, "diagonal": 0, "column": 0, "rank": 0}
+    done = {"antidiagonal": 0, "diagonal": 0, "column": 0, "rank": 0, "split": 0}
     for _ in range(max_rounds):
         changed = False
-        for name in ("antidiagonal", "diagonal", "column", "rank"):
+        for name in ("antidiagonal", "diagonal", "column", "rank") + (("split",) if split else ()):
             fn = getattr(w, name)
             while (fn(rtol) if name != "rank" else fn()):
                 done[name] += 1

@@ -85,3 +85,26 @@ def test_frozen_leaves_are_kept_first_and_untouched():
     for i, v in enumerate(out_leaves):
         assert np.array_equal(s.tensors[i], net.tensors[v]) and s.labels[i] == net.labels[v]
     assert np.max(np.abs(_value(s) - _value(net))) <= 1e-12 * np.max(np.abs(_value(net)))
+
+
+def test_split_simplification_factors_a_low_rank_tensor():
+    rng = np.random.default_rng(5)
+    a, b = rng.standard_normal((2, 2)), rng.standard_normal((2, 2, 2))
+    t = np.einsum("ij,klm->ijklm", a, b)             # rank 1 across {i, j} | {k, l, m}
+    others = [rng.standard_normal(2) for _ in range(5)]
+    net = inputs.Network([t] + others, [[0, 1, 2, 3, 4], [0], [1], [2], [3], [4]],
+                         {l: 2 for l in range(5)}, [])
+    w = simplify._Net(net, ())
+    assert w.split(1e-12)
+    assert sorted(len(x) for x in w.l[:1] + w.l[-1:]) == [3, 4]  # {i, j, new} and {new, k, l, m}
+    s, done = simplify.simplify(net, frozen=[1, 2, 3, 4, 5])  # the vectors stay, t is split
+    assert done["split"] >= 1 and s.n_tensors == net.n_tensors + 1
+    assert np.isclose(float(_value(s)), float(_value(net)), rtol=1e-12)
+
+
+def test_simplify_terminates_with_split_on_random_networks():
+    for seed in range(5):
+        net = inputs.random_network(8, 12, 200 + seed, n_open=1)
+        s, done = simplify.simplify(net, max_rounds=200)
+        a, b = _value(net), _value(s)
+        assert np.max(np.abs(a - b)) <= 1e-11 * np.max(np.abs(a))
