@@ -36,6 +36,7 @@ __all__ = [
     "TreeInfo",
     "greedy_tree_sampled",
     "hyper_greedy",
+    "slice_repeats",
     "node_labels",
     "tree_info",
     "greedy_tree",
@@ -352,11 +353,13 @@ def greedy_tree_sampled(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, in
 
 def hyper_greedy(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
                  open_labels: Iterable[int] = (), trials: int = 32, seed: int = 0,
-                 target_width: Optional[float] = None):
+                 target_width: Optional[float] = None, slicer_repeats: int = 0):
     """Hyper-Greedy (Sec. 3.4): repeated Boltzmann-sampled greedy trees with
     alpha ~ U(0, 2) and tau ~ logU(0.01, 3), keeping the lowest cost -- the
     sliced cost C_s at target_width when given (slicing inside the search,
-    Sec. 4.7.1).  Returns (pairs, sliced, TreeInfo); seeded."""
+    Sec. 4.7.1; with ``slicer_repeats`` > 0 each tree gets the best of that
+    many randomised slicer runs besides the greedy one).  Returns (pairs,
+    sliced, TreeInfo); seeded."""
     opn = list(open_labels)
     rng = np.random.Generator(np.random.PCG64(seed))
     best = None
@@ -374,7 +377,10 @@ def hyper_greedy(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
             info0 = tree_info(leaf_labels, dims, pairs, opn)
             if info0.W > target_width:
                 try:
-                    sliced = slice_greedy(leaf_labels, dims, pairs, opn, target_width)
+                    sliced = (slice_repeats(leaf_labels, dims, pairs, opn, target_width, slicer_repeats,
+                                            seed=seed + 7919 * (sd or 0))
+                              if slicer_repeats > 0 else
+                              slice_greedy(leaf_labels, dims, pairs, opn, target_width))
                 except RuntimeError:
                     continue  # too wide to slice down: not a candidate
         info = tree_info(leaf_labels, dims, pairs, opn, sliced)
@@ -402,12 +408,16 @@ def left_deep_tree(n_leaves: int, order: Optional[Sequence[int]] = None) -> List
 
 def slice_greedy(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
                  pairs: Sequence[Tuple[int, int]], open_labels: Iterable[int],
-                 target_width: float, max_sliced: int = 64) -> List[int]:
+                 target_width: float, max_sliced: int = 64, temperature: float = 0.0,
+                 rng: Optional[np.random.Generator] = None) -> List[int]:
     """Greedy index slicing to a target sliced width W_s.
 
     Each step considers the summed labels of tensors wider than the target
     and removes the one minimising d_sliced * C(tree without it); ties go to
-    the smallest label id.  Stops when W_s <= target_width.
+    the smallest label id.  Stops when W_s <= target_width.  With a
+    temperature > 0 (and ``rng``) each step instead draws a label with
+    weight exp(-(log2 score - log2 min score) / temperature): the "slight
+    randomization" of the paper's slicer (Sec. 4.7.1), for repeats.
     """
     opn = set(open_labels)
     sliced: List[int] = []
@@ -433,8 +443,35 @@ def slice_greedy(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
                     red[i] += node_cost[k] * (1.0 - 1.0 / dims[l])
         w = np.array([dims[l] for l in cands], dtype=np.float64)
         score = info.d_sliced * w * (info.C - red)
-        best = int(np.flatnonzero(score <= score.min() * (1 + 1e-12))[0])
+        if temperature > 0.0 and rng is not None and len(cands) > 1:
+            ls = np.log2(np.maximum(score, 1e-300))
+            wgt = np.exp(-(ls - ls.min()) / temperature)
+            best = int(rng.choice(len(cands), p=wgt / wgt.sum()))
+        else:
+            best = int(np.flatnonzero(score <= score.min() * (1 + 1e-12))[0])
         sliced.append(cands[best])
+
+
+def slice_repeats(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
+                  pairs: Sequence[Tuple[int, int]], open_labels: Iterable[int],
+                  target_width: float, repeats: int = 8, temperature: float = 0.5,
+                  seed: int = 0) -> List[int]:
+    """The greedy slicer, then ``repeats`` randomised runs of it (seeded),
+    keeping the slicing with the lowest sliced cost C_s (Sec. 4.7.1: the
+    search targets C_s; W_s <= target for every candidate)."""
+    opn = list(open_labels)
+    best = slice_greedy(leaf_labels, dims, pairs, opn, target_width)
+    best_c = tree_info(leaf_labels, dims, pairs, opn, best).C_s
+    rng = np.random.Generator(np.random.PCG64(seed))
+    for _ in range(repeats):
+        try:
+            cand = slice_greedy(leaf_labels, dims, pairs, opn, target_width, temperature=temperature, rng=rng)
+        except RuntimeError:
+            continue
+        c_s = tree_info(leaf_labels, dims, pairs, opn, cand).C_s
+        if c_s < best_c:
+            best, best_c = cand, c_s
+    return best
 
 
 def plan(net, target_width: Optional[float] = None, alpha: float = 1.0):

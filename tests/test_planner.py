@@ -151,3 +151,24 @@ def test_hyper_greedy_with_slicing_meets_the_width_target():
     # the reported cost is the sliced cost of that tree and slicing
     again = planner.tree_info(net.labels, net.dims, pairs, net.open, sliced)
     assert again.C_s == info.C_s and again.d_sliced == info.d_sliced
+
+
+def test_randomised_slicer_repeats_never_worse_and_seeded():
+    net = inputs.random_ising(60, seed=8)
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    target = planner.tree_info(net.labels, net.dims, pairs, net.open).W - 5
+    g = planner.slice_greedy(net.labels, net.dims, pairs, net.open, target)
+    r1 = planner.slice_repeats(net.labels, net.dims, pairs, net.open, target, repeats=6, seed=3)
+    r2 = planner.slice_repeats(net.labels, net.dims, pairs, net.open, target, repeats=6, seed=3)
+    assert r1 == r2
+    i_g = planner.tree_info(net.labels, net.dims, pairs, net.open, g)
+    i_r = planner.tree_info(net.labels, net.dims, pairs, net.open, r1)
+    assert i_r.W <= target + 1e-9 and i_r.C_s <= i_g.C_s
+    # slicing never changes the value (oracle), whichever labels were chosen
+    from oracle import tree
+    m1, e1 = tree.contract_net(net, pairs, g)
+    m2, e2 = tree.contract_net(net, pairs, r1)
+    assert abs(math.log(float(m1)) + e1 * math.log(2) - math.log(float(m2)) - e2 * math.log(2)) < 1e-12
+    p3, s3, i3 = planner.hyper_greedy(net.labels, net.dims, net.open, trials=3, seed=2,
+                                      target_width=target, slicer_repeats=3)
+    assert i3.W <= target + 1e-9
