@@ -154,6 +154,14 @@ def tn_set_tensor(h: int, v: int, ptr: int, mem: int = TN_MEM_DEVICE) -> None:
     _check(_lib.tn_set_tensor(h, v, ptr, mem))
 
 
+def _hold(t, stream) -> None:
+    """A temporary device tensor read by work queued on ``stream`` (a torch
+    stream, or None for the current one): tell the caching allocator, so that
+    its memory is not handed out again before that work has run."""
+    if stream is not None and getattr(t, "is_cuda", False):
+        t.record_stream(stream)
+
+
 def _tree(pairs):
     return _arr([x for p in pairs for x in p] or [0], np.int32)
 
@@ -247,7 +255,7 @@ def tn_contract_noalloc(h: int, pairs, sliced, out_ptr: int, out_mem: int, exp_p
 def tn_autotune(h: int, pairs, sliced, mode: int, reps: int = 3, stream: int = 0) -> List[int]:
     """Time every candidate kernel per node and keep the fastest in the
     cached plan; returns the per-node choice (0 untuned, 1..4 and 6 tile shape,
-    8 tensor core)."""
+    8 tensor core, 9 tensor core with 128-column tiles)."""
     tr = _tree(pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     ch = np.zeros(max(len(pairs), 1), dtype=np.int32)
@@ -344,6 +352,48 @@ class TensorNetwork:
     def out_shape(self) -> Tuple[int, ...]:
         return tuple(self.dims[l] for l in self.open)
 
+    # The library sees plain pointers: the extents it will read or write are
+    # checked here, before any call, so that an undersized buffer raises
+    # instead of being accessed out of bounds.
+
+    def _leaf_numel(self, v: int) -> int:
+        n = 1
+        for l in self.labels[v]:
+            n *= int(self.dims[l])
+        return n
+
+    def _extent(self, v: int, n_inst: int, strides) -> int:
+        """Elements from leaf v's pointer that n_inst copies touch."""
+        st = int(strides[v]) if strides is not None else 0
+        return max(int(n_inst) - 1, 0) * st + self._leaf_numel(v)
+
+    def _check_strides(self, n_inst: int, strides) -> None:
+        if strides is not None and len(strides) != len(self.labels):
+            raise TNError(TN_EINVAL, f"leaf_inst_stride needs {len(self.labels)} entries, got {len(strides)}")
+        for v, t in enumerate(self._keep):
+            if strides is not None and int(strides[v]) < 0:
+                raise TNError(TN_EINVAL, f"leaf {v}: negative instance stride")
+            need = self._extent(v, n_inst, strides)
+            if t.numel() < need:
+                raise TNError(TN_EINVAL, f"leaf {v}: {t.numel()} elements attached, "
+                                         f"{n_inst} copies read {need}")
+
+    def _check_grads(self, grads, n_inst: int = 1, strides=None) -> None:
+        import torch
+        if len(grads) != len(self.labels):
+            raise TNError(TN_EINVAL, f"grads needs {len(self.labels)} entries (None to skip), got {len(grads)}")
+        want = torch.complex64 if self.dtype == TN_C64 else torch.float32
+        for v, g in enumerate(grads):
+            if g is None:
+                continue
+            if g.dtype != want:
+                raise TypeError(f"grads[{v}]: dtype {g.dtype}, expected {want}")
+            if not g.is_cuda or not g.is_contiguous():
+                raise TNError(TN_EINVAL, f"grads[{v}] must be a contiguous CUDA tensor")
+            need = self._extent(v, n_inst, strides)
+            if g.numel() < need:
+                raise TNError(TN_EINVAL, f"grads[{v}]: {g.numel()} elements, {need} written")
+
     def contract(self, pairs, sliced=(), mode="fp32", out=None, out_exp=None, stream=None,
                  slice_begin=0, slice_count=0, no_graph=False,
                  prof_events=None, prof_first=0, slice_batch=0):
@@ -359,6 +409,13 @@ class TensorNetwork:
             out = torch.empty(self.out_shape, dtype=odt, device=dev)
         if out_exp is None:
             out_exp = torch.empty((), dtype=torch.int64, device=out.device)
+        if out.dtype != odt or out_exp.dtype != torch.int64:
+            raise TypeError(f"out must be {odt} and out_exp torch.int64")
+        n_out = int(np.prod(self.out_shape))
+        if out.numel() != n_out or not out.is_contiguous() or out_exp.numel() != 1:
+            raise TNError(TN_EINVAL, f"out must be a contiguous tensor of {n_out} elements, out_exp a scalar")
+        if out_exp.is_cuda != out.is_cuda:
+            raise TNError(TN_EINVAL, "out and out_exp must both be device or both host tensors")
         mem = TN_MEM_DEVICE if out.is_cuda else TN_MEM_HOST
         s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
         evp = [e.cuda_event for e in prof_events] if prof_events else None
@@ -405,11 +462,16 @@ class TensorNetwork:
         if isinstance(adj_exp2, torch.Tensor):
             if adj_mem != TN_MEM_DEVICE or not adj_exp2.is_cuda or adj_exp2.dtype != torch.int64:
                 raise TypeError("a tensor adj_exp2 must be a CUDA int64 scalar, with a CUDA adjoint")
+            if adj_exp2.numel() != 1:
+                raise TNError(TN_EINVAL, "a tensor adj_exp2 must hold one exponent")
             exp_dev = adj_exp2.data_ptr()
         else:
             exp_host = int(adj_exp2)
         if grads is None:
             grads = [torch.empty_like(t, device="cuda") for t in self._keep]
+        self._check_grads(grads)
+        if keep is not adjoint:
+            _hold(keep, stream)
         s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
         tn_contract_grad_ex(self.h, pairs, sliced, m, adj_ptr, adj_mem, exp_host, exp_dev,
                             [g.data_ptr() if g is not None else 0 for g in grads],
@@ -425,6 +487,7 @@ class TensorNetwork:
         grad_instances(kept_forward=token)."""
         import torch
         m = MODES[mode] if isinstance(mode, str) else int(mode)
+        self._check_strides(n_inst, leaf_inst_stride)
         out = torch.empty((n_inst, 2), dtype=torch.float64, device="cuda")
         ex = torch.empty(n_inst, dtype=torch.int64, device="cuda")
         st = _arr(list(leaf_inst_stride), np.int64) if leaf_inst_stride is not None else None
@@ -450,6 +513,7 @@ class TensorNetwork:
         Returns ``grads``."""
         import torch
         m = MODES[mode] if isinstance(mode, str) else int(mode)
+        self._check_strides(n_inst, leaf_inst_stride)
         cplx = self.dtype == TN_C64
         n_out = int(np.prod(self.out_shape))
         if isinstance(adjoint, torch.Tensor) and adjoint.is_cuda:
@@ -472,11 +536,17 @@ class TensorNetwork:
             if adj_mem != TN_MEM_DEVICE or not adj_exp2.is_cuda or adj_exp2.dtype != torch.int64 \
                     or adj_exp2.numel() != n_inst:
                 raise TypeError("a tensor adj_exp2 must hold n_inst CUDA int64s, with a CUDA adjoint")
-            exp_dev = adj_exp2.contiguous().data_ptr()
+            exp_keep = adj_exp2.contiguous()
+            if exp_keep is not adj_exp2:
+                _hold(exp_keep, stream)
+            exp_dev = exp_keep.data_ptr()
         else:
             exp_host = int(adj_exp2)
         if grads is None:  # attached tensors: stacked copies for varying leaves
             grads = [torch.empty_like(t, device="cuda") for t in self._keep]
+        self._check_grads(grads, n_inst, leaf_inst_stride)
+        if keep is not adjoint:
+            _hold(keep, stream)
         s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
         flags = TN_GRAD_ACCUMULATE if accumulate else 0
         if kept_forward is not None and kept_forward == getattr(self, "_grad_epoch", 0) and not sliced:
@@ -506,6 +576,7 @@ class TensorNetwork:
         Returns device tensors (mantissa (n_inst, 2) float64, exp2 (n_inst,))."""
         import torch
         m = MODES[mode] if isinstance(mode, str) else int(mode)
+        self._check_strides(n_inst, leaf_inst_stride)
         out = torch.empty((n_inst, 2), dtype=torch.float64, device="cuda")
         ex = torch.empty(n_inst, dtype=torch.int64, device="cuda")
         strides = None

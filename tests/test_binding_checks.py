@@ -1,0 +1,75 @@
+"""The binding's argument checks (no GPU needed: every case is refused
+before any device call).
+
+The library sees plain pointers, so the extents it reads and writes are
+checked in the binding: caller gradient buffers, leaves read by several
+copies, output buffers.  Undersized or malformed buffers raise TNError
+(TN_EINVAL) or TypeError instead of being accessed out of bounds.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2002_01935_gb300 import binding, inputs, planner  # noqa: E402
+
+
+@pytest.fixture()
+def tnw():
+    net = inputs.random_network(5, 7, 3, n_open=1, max_dim=2)
+    ts = [torch.from_numpy(np.array(t, order="C")).to(torch.complex64) for t in net.tensors]
+    h = binding.TensorNetwork(net.labels, net.dims, net.open, ts, complex_=True)
+    h.test_pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    h.test_leaves = ts
+    yield h
+    h.close()
+
+
+def _einval(fn):
+    with pytest.raises(binding.TNError) as e:
+        fn()
+    assert e.value.status == binding.TN_EINVAL
+
+
+def test_gradient_buffers_are_checked(tnw):
+    ts = tnw.test_leaves
+    _einval(lambda: tnw._check_grads([None] * (len(ts) - 1)))  # one entry per leaf
+    _einval(lambda: tnw._check_grads([torch.empty_like(t) for t in ts]))  # host memory
+    with pytest.raises(TypeError):
+        tnw._check_grads([torch.empty(t.shape, dtype=torch.complex128) for t in ts])
+    tnw._check_grads([None] * len(ts))  # all skipped: nothing to check
+
+
+def test_instance_extents_are_checked(tnw):
+    ts = tnw.test_leaves
+    n = len(ts)
+    tnw._check_strides(4, [0] * n)  # shared leaves: one copy's extent
+    tnw._check_strides(1, [ts[0].numel()] + [0] * (n - 1))  # one copy reads one leaf
+    _einval(lambda: tnw._check_strides(2, [ts[0].numel()] + [0] * (n - 1)))  # second copy past the end
+    _einval(lambda: tnw._check_strides(2, [-1] + [0] * (n - 1)))
+    _einval(lambda: tnw._check_strides(2, [0] * (n - 1)))
+    # a stacked leaf holds exactly what its copies read
+    stacked = list(ts)
+    stacked[0] = torch.stack([ts[0]] * 3)
+    tnw.set_tensors(stacked)
+    tnw._check_strides(3, [ts[0].numel()] + [0] * (n - 1))
+    _einval(lambda: tnw._check_strides(4, [ts[0].numel()] + [0] * (n - 1)))
+    # instance gradients: varying leaves need every copy's extent
+    with pytest.raises(binding.TNError):
+        tnw.grad_instances(tnw.test_pairs, [], "fp32", 4, [ts[0].numel()] + [0] * (n - 1),
+                           np.zeros((4,) + tnw.out_shape, dtype=np.complex128))
+
+
+def test_output_buffers_are_checked(tnw):
+    pairs = tnw.test_pairs
+    ex = torch.empty((), dtype=torch.int64)
+    n_out = int(np.prod(tnw.out_shape))
+    _einval(lambda: tnw.contract(pairs, [], "fp32", out=torch.empty(n_out + 2, dtype=torch.complex128),
+                                 out_exp=ex))
+    with pytest.raises(TypeError):
+        tnw.contract(pairs, [], "fp32", out=torch.empty(tnw.out_shape, dtype=torch.complex64), out_exp=ex)
+    with pytest.raises(TypeError):
+        tnw.contract(pairs, [], "fp32", out=torch.empty(tnw.out_shape, dtype=torch.complex128),
+                     out_exp=torch.empty((), dtype=torch.int32))
+    _einval(lambda: tnw.contract(pairs, [], "fp32", out=torch.empty(tnw.out_shape, dtype=torch.complex128),
+                                 out_exp=torch.empty(2, dtype=torch.int64)))
