@@ -94,7 +94,7 @@ enum { TN_MEM_DEVICE = 0, TN_MEM_HOST = 1 };
  * The arrays are copied; the caller keeps ownership.  On success *out owns a
  * handle to be released with tn_destroy.  Errors: TN_EINVAL (unknown or
  * duplicate label, repeated label in a tensor, open label not in any tensor,
- * size < 1), TN_ENOMEM.
+ * size < 1), TN_EUNSUPPORTED (a tensor of more than 2^40 entries), TN_ENOMEM.
  */
 tn_status tn_create(tn_net **out, tn_dtype dt, int32_t n_tensors, const int32_t *ranks,
                     const int64_t *labels, int32_t n_labels, const int64_t *label_ids,
@@ -176,8 +176,9 @@ typedef struct {
  * The first call with a new (tree, slicing, mode) plans the nodes and
  * allocates the workspace (cached in the handle; a call during stream
  * capture must reuse a cached plan).  Errors: TN_EINVAL (malformed tree,
- * sliced label open or unknown, a leaf without data), TN_ENOMEM, TN_ECUDA,
- * TN_ETIMEOUT.
+ * sliced label open or unknown, a leaf without data), TN_EUNSUPPORTED (an
+ * intermediate of the sliced tree with more than 2^40 entries, or a node of
+ * more than 2^62 multiply-adds), TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT.
  */
 tn_status tn_contract(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
                       const int64_t *sliced_labels, tn_mode mode, void *out, int32_t out_mem,

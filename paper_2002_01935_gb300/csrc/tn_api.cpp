@@ -101,6 +101,9 @@ tn_status tn_create(tn_net** out, tn_dtype dt, int32_t n_tensors, const int32_t*
             used[it->second]++;
         }
         off += ranks[v];
+        double lg = 0;
+        for (int l : lf.lab) lg += std::log2((double)d.dims[l]);
+        if (lg > tn::kMaxLog2Entries) return fail(TN_EUNSUPPORTED, "tn_create: a tensor has more than 2^40 entries");
         lf.size = 1;
         lf.stride.assign(lf.lab.size(), 1);
         for (int i = (int)lf.lab.size() - 1; i >= 0; --i) {

@@ -14,6 +14,13 @@ constexpr int kMaxDigits = 40;
 constexpr int kMaxSliceDigits = 16;
 // Maximum number of bits per index group of the tiled kernels.
 constexpr int kMaxBits = 40;
+// Largest tensor (leaf or intermediate of a sliced tree), as log2 of its
+// entry count: 2^40 entries are far beyond any device memory, so every size,
+// offset and byte count derived from one stays well inside int64.
+constexpr int kMaxLog2Entries = 40;
+// Largest number of multiply-adds of one node (log2): summed-entry counts
+// stay inside int64.
+constexpr int kMaxLog2Work = 62;
 
 // Device-side control block of one contraction call (one per plan).
 struct Control {

@@ -428,6 +428,18 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
             };
             visit(a, b);
             visit(b, a);
+            // sizes are formed in int64 below: refuse what could overflow them
+            std::vector<int> uni = p.vlab[a];
+            for (int l : p.vlab[b])
+                if (std::find(uni.begin(), uni.end(), l) == uni.end()) uni.push_back(l);
+            if (log2size(keep) > kMaxLog2Entries) {
+                err = "an intermediate of the sliced tree has more than 2^40 entries";
+                return TN_EUNSUPPORTED;
+            }
+            if (log2size(uni) > kMaxLog2Work) {
+                err = "a node of the sliced tree needs more than 2^62 multiply-adds";
+                return TN_EUNSUPPORTED;
+            }
             sub[me] = sc;
             sub[a].c.clear();
             sub[b].c.clear();

@@ -62,6 +62,40 @@ def test_create_rejects_malformed_networks(lib, case):
     assert lib.tn_last_error()
 
 
+def test_tensors_beyond_the_size_limit_are_refused(lib):
+    """Entry counts are formed in int64: a leaf or an intermediate of more
+    than 2^40 entries is refused on the host (TN_EUNSUPPORTED) instead of
+    overflowing; a leaf of exactly 2^40 entries is accepted."""
+    big = {i: 2 for i in range(41)}
+    with pytest.raises(lib.TNError) as e:
+        lib.tn_create(lib.TN_C64, [list(range(41))], big, [])
+    assert e.value.status == lib.TN_EUNSUPPORTED
+    wide = {i: 4 for i in range(21)}  # 4^21 = 2^42
+    with pytest.raises(lib.TNError) as e:
+        lib.tn_create(lib.TN_C64, [list(range(21))], wide, [])
+    assert e.value.status == lib.TN_EUNSUPPORTED
+    h = lib.tn_create(lib.TN_C64, [list(range(40))], {i: 2 for i in range(40)}, [])
+    lib.tn_destroy(h)
+    # two leaves of 2^21 entries whose outer product (all labels open) has 2^42
+    dims = {i: 2 for i in range(42)}
+    h = lib.tn_create(lib.TN_C64, [list(range(21)), list(range(21, 42))], dims, list(range(42)))
+    try:
+        with pytest.raises(lib.TNError) as e:
+            lib.tn_plan_info(h, [(0, 1)], [])
+        assert e.value.status == lib.TN_EUNSUPPORTED
+        assert "2^40" in lib.tn_last_error()
+        # sliced down to 2^40 it plans
+        h2 = lib.tn_create(lib.TN_C64, [list(range(21)), list(range(21, 42)), [0], [21]], dims,
+                           list(range(1, 21)) + list(range(22, 42)))
+        try:
+            info = lib.tn_plan_info(h2, [(0, 2), (1, 3), (4, 5)], [0, 21])
+            assert info["W"] == 40
+        finally:
+            lib.tn_destroy(h2)
+    finally:
+        lib.tn_destroy(h)
+
+
 @pytest.mark.parametrize("pairs", [[(0, 1)], [(0, 1), (1, 3)], [(0, 4), (1, 2)], [(0, 0), (1, 2)]])
 def test_malformed_trees_are_rejected(lib, pairs):
     h = lib.tn_create(lib.TN_C64, [[0], [0, 1], [1]], {0: 2, 1: 2}, [])
