@@ -249,6 +249,42 @@ def test_ising_hyperedge_form_matches_enumeration(n, seed):
                                                          copy_form.open))) < 1e-12
 
 
+def _copy(rank):
+    t = np.zeros((2,) * rank)
+    t[(0,) * rank] = t[(1,) * rank] = 1.0
+    return t
+
+
+@pytest.mark.parametrize("n,seed", [(10, 5), (14, 6)])
+def test_ising_copy_tensors_rewired(n, seed):
+    """Sec. 3.5: a COPY tensor may be replaced by any connected network of
+    COPY tensors over the same open labels without changing the value.
+    Every vertex's rank-3 COPY tensor becomes a random connected COPY
+    subgraph (a chain through two new labels, or a rank-3 tensor joined to a
+    rank-2 one); Z stays that of the enumeration."""
+    net = inputs.random_ising(n, seed)
+    rng = np.random.default_rng(seed)
+    tensors, labels = list(net.tensors[n:]), [list(l) for l in net.labels[n:]]
+    nxt = max(net.dims) + 1
+    for v in range(n):
+        a, b, c = [net.labels[v][i] for i in rng.permutation(3)]
+        if rng.random() < 0.5:  # chain a - x - b - y - c
+            x, y = nxt, nxt + 1
+            nxt += 2
+            tensors += [_copy(2), _copy(3), _copy(2)]
+            labels += [[a, x], [x, b, y], [y, c]]
+        else:  # (a, b, x) joined to (x, c)
+            x = nxt
+            nxt += 1
+            tensors += [_copy(3), _copy(2)]
+            labels += [[a, b, x], [x, c]]
+    dims = {l: 2 for ls in labels for l in ls}
+    rewired = inputs.Network(tensors, labels, dims, [])
+    rewired.validate()
+    lz = log_z(rewired, planner.greedy_tree(labels, dims, []))
+    assert abs(lz - ising.log_z_enumerate(n, net.meta["edges"], net.meta["J"], net.meta["beta"])) < 1e-12
+
+
 def test_ising_closed_forms():
     # beta = 0: Z = 2^N exactly
     edges = inputs.random_regular_graph(40, 3, seed=4)
