@@ -183,3 +183,46 @@ def test_combine_grads_rejects_strided_buffers():
     import torch
     with pytest.raises(ValueError):
         shard.combine_grads([torch.zeros(4, 4)[:, 1]])
+
+
+def _leaving_worker(rank, world, port, q):
+    """The last rank leaves between steps (nothing in flight); the others'
+    next exchange must end with an error instead of waiting forever."""
+    import datetime
+    import torch
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == world - 1:
+        os._exit(0)
+    try:
+        shard.combine(torch.zeros(2, dtype=torch.complex128), 0)
+        q.put((rank, "completed"))
+    except Exception as e:  # the backend reports the lost peer
+        q.put((rank, type(e).__name__))
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_exchange_fails_cleanly_when_a_rank_leaves(world):
+    import time
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_leaving_worker, args=(r, world, port, q)) for r in range(world)]
+    t0 = time.monotonic()
+    for p in procs:
+        p.start()
+    try:
+        res = sorted(q.get(timeout=120) for _ in range(world - 1))
+    finally:
+        for p in procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.kill()
+                p.join()
+    assert [r for r, _ in res] == list(range(world - 1))
+    assert all(outcome != "completed" for _, outcome in res), res
+    assert time.monotonic() - t0 < 120
