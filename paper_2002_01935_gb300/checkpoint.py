@@ -1,0 +1,114 @@
+"""Checkpoint and resume of a sliced contraction.
+
+Slices are independent contractions whose values are summed (Sec. 4.7.1),
+so a long sliced run can be cut into consecutive blocks of the slice range.
+Each finished block leaves a partial result -- an FP64 mantissa (scalar or
+open-output tensor) m and an int64 power-of-two exponent e, value m * 2^e --
+which is written to a checkpoint file before the next block starts.  A
+resumed run reads the file and contracts only the blocks still missing.
+The partials are folded in block order with exponents aligned to the
+largest one, so the result does not depend on where (or whether) the run
+was interrupted.
+
+The contraction of one block is a callable ``contract_block(begin, count)
+-> (mantissa, exp2)``; ``library_block`` builds it from a network handle of
+the binding (device contraction of that slice range, result copied to the
+host).
+"""
+from __future__ import annotations
+
+import os
+from typing import Callable, List, Optional, Tuple
+
+import numpy as np
+
+# exponent of an exactly-zero partial: never the common exponent
+ZERO_EXP = -(1 << 60)
+
+
+def blocks(d_sliced: int, block: int) -> List[Tuple[int, int]]:
+    """The (begin, count) blocks covering [0, d_sliced) in order."""
+    if d_sliced < 1 or block < 1:
+        raise ValueError("need d_sliced >= 1 and block >= 1")
+    return [(b, min(block, d_sliced - b)) for b in range(0, d_sliced, block)]
+
+
+def fold(partials) -> Tuple[np.ndarray, int]:
+    """Sum of (mantissa, exp2) partials, in the given order, as one
+    (mantissa, exp2): every mantissa is scaled exactly by a power of two to
+    the largest exponent among the non-zero partials, then added in FP64."""
+    parts = [(np.asarray(m), int(e)) for m, e in partials]
+    if not parts:
+        raise ValueError("nothing to fold")
+    live = [e for m, e in parts if np.any(m != 0)]
+    if not live:
+        return np.zeros_like(parts[0][0]), 0
+    e_max = max(live)
+    acc = np.zeros_like(parts[0][0])
+    for m, e in parts:
+        if np.any(m != 0):
+            # contributions more than 1100 binades down underflow, as in FP64
+            shift = max(e - e_max, -1100)
+            if np.iscomplexobj(m):
+                acc = acc + (np.ldexp(m.real, shift) + 1j * np.ldexp(m.imag, shift))
+            else:
+                acc = acc + np.ldexp(m, shift)
+    return acc, e_max
+
+
+class SliceCheckpoint:
+    """The finished blocks of one sliced contraction, kept in ``path``
+    (an ``.npz`` file, replaced atomically after every block).  ``key``
+    names the problem (network, tree, sliced labels, mode): a file written
+    for another key, slice count or block size is refused, never mixed in."""
+
+    def __init__(self, path: str, key: str, d_sliced: int, block: int):
+        self.path, self.key, self.d_sliced, self.block = path, str(key), int(d_sliced), int(block)
+        self.done: dict = {}  # block index -> (mantissa, exp2)
+        if os.path.exists(path):
+            with np.load(path, allow_pickle=False) as z:
+                meta = (str(z["key"]), int(z["d_sliced"]), int(z["block"]))
+                if meta != (self.key, self.d_sliced, self.block):
+                    raise ValueError(f"checkpoint {path} belongs to {meta}, not "
+                                     f"{(self.key, self.d_sliced, self.block)}")
+                for i, m, e in zip(z["index"], z["mantissa"], z["exp2"]):
+                    self.done[int(i)] = (np.array(m), int(e))
+
+    def record(self, index: int, mantissa, exp2: int) -> None:
+        self.done[int(index)] = (np.array(mantissa), int(exp2))
+        idx = sorted(self.done)
+        tmp = self.path + ".tmp.npz"
+        np.savez(tmp, key=np.array(self.key), d_sliced=np.array(self.d_sliced),
+                 block=np.array(self.block), index=np.array(idx, dtype=np.int64),
+                 mantissa=np.stack([self.done[i][0] for i in idx]),
+                 exp2=np.array([self.done[i][1] for i in idx], dtype=np.int64))
+        os.replace(tmp, self.path)
+
+
+def run(contract_block: Callable[[int, int], Tuple[np.ndarray, int]], d_sliced: int, block: int,
+        path: str, key: str, on_block: Optional[Callable[[int], None]] = None) -> Tuple[np.ndarray, int]:
+    """Contract every block of [0, d_sliced) not yet in the checkpoint at
+    ``path`` (recording each as it finishes) and return the folded
+    (mantissa, exp2) of all of them.  ``on_block(i)`` is called after block
+    i is recorded."""
+    ck = SliceCheckpoint(path, key, d_sliced, block)
+    bl = blocks(d_sliced, block)
+    for i, (b, c) in enumerate(bl):
+        if i in ck.done:
+            continue
+        m, e = contract_block(b, c)
+        m = np.asarray(m)
+        ck.record(i, m, ZERO_EXP if not np.any(m != 0) else int(e))
+        if on_block is not None:
+            on_block(i)
+    return fold(ck.done[i] for i in range(len(bl)))
+
+
+def library_block(tnw, pairs, sliced, mode: str = "fp32"):
+    """``contract_block`` for a network handle of the binding: the slice
+    range [begin, begin + count) contracted on the device, the
+    (mantissa, exp2) copied to the host."""
+    def contract_block(begin: int, count: int):
+        m, e = tnw.contract(pairs, sliced, mode, slice_begin=begin, slice_count=count)
+        return m.cpu().numpy(), int(e.cpu())
+    return contract_block
