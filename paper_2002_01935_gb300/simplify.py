@@ -14,8 +14,10 @@ network:
   its diagonal, and label i_y becomes i_x everywhere (i_x turns into a
   hyperedge; tensors that then carry i_x twice keep their diagonal);
 - antidiagonal-gauging: a tensor that vanishes unless i_x == d - 1 - i_y has
-  the order of label i_y reversed in every tensor carrying it, which makes
-  it diagonal for the rule above;
+  the order of label i_y (or i_x) reversed in every tensor carrying it,
+  which makes it diagonal for the rule above; a reversal is taken only if
+  it makes more axis pairs diagonal than it makes antidiagonal among the
+  label's tensors, so that the rule cannot undo itself;
 - rank-simplification: pairs of tensors sharing a label are contracted
   (numpy, FP64 or complex128) when the result's rank is at most the larger
   of their two ranks -- for networks without hyperedges, absorbing every
@@ -127,7 +129,40 @@ class _Net:
         return False
 
     # --- antidiagonal-gauging
+    def _pair_kind(self, t: np.ndarray, x: int, y: int, rtol: float) -> Tuple[bool, bool]:
+        """(diagonal, antidiagonal): whether t vanishes off the diagonal,
+        and off the antidiagonal, of its axes x and y (equal sizes)."""
+        d = t.shape[x]
+        ix = np.arange(d)
+        shape = [d if i in (x, y) else 1 for i in range(t.ndim)]
+        res = []
+        for keep in (ix[:, None] == ix[None, :], ix[:, None] == d - 1 - ix[None, :]):
+            off = ~keep if x < y else ~keep.T
+            res.append(_zero(t, np.broadcast_to(off.reshape(shape), t.shape), rtol))
+        return res[0], res[1]
+
+    def _flip_gain(self, label: int, rtol: float) -> int:
+        """Reversing ``label`` everywhere turns every antidiagonal axis pair
+        containing it diagonal and every diagonal one antidiagonal: the net
+        number of antidiagonal-only pairs it removes."""
+        gain = 0
+        for w in self.carriers(label):
+            t, ls = self.t[w], self.l[w]
+            a = ls.index(label)
+            for b, other in enumerate(ls):
+                if b == a or self.dims[other] != self.dims[label]:
+                    continue
+                diag, anti = self._pair_kind(t, a, b, rtol)
+                gain += int(anti and not diag) - int(diag and not anti)
+        return gain
+
     def antidiagonal(self, rtol: float) -> bool:
+        """Reverse one label that makes an antidiagonal axis pair diagonal.
+        A reversal is taken only if it removes more antidiagonal pairs than
+        it creates over all tensors carrying the label, so the number of
+        antidiagonal pairs falls with every step and the rule terminates
+        (a label shared by two tensors, antidiagonal in one and diagonal in
+        the other, is left alone rather than flipped back and forth)."""
         for v in self.live():
             if v in self.frozen:
                 continue
@@ -138,22 +173,18 @@ class _Net:
                     d = self.dims[lx]
                     if d != self.dims[ly] or d == 1:
                         continue
-                    ix = np.arange(d)
-                    off = ix[:, None] != (d - 1 - ix[None, :])
-                    mask = np.broadcast_to(off.reshape([d if i in (x, y) else 1 for i in range(t.ndim)]), t.shape)
-                    if not _zero(t, mask, rtol):
-                        continue
-                    diag = ix[:, None] != ix[None, :]
-                    dmask = np.broadcast_to(diag.reshape([d if i in (x, y) else 1 for i in range(t.ndim)]), t.shape)
-                    if _zero(t, dmask, rtol):
-                        continue  # already diagonal (d = 1 or a zero tensor)
-                    flip = ly if ly not in self.open else (lx if lx not in self.open else None)
-                    if flip is None or any(w in self.frozen for w in self.carriers(flip)):
-                        continue
-                    for w in self.carriers(flip):
-                        ax = self.l[w].index(flip)
-                        self.t[w] = np.flip(self.t[w], axis=ax).copy()
-                    return True
+                    diag, anti = self._pair_kind(t, x, y, rtol)
+                    if not anti or diag:
+                        continue  # not antidiagonal, or already diagonal (d = 1 or a zero tensor)
+                    for flip in (ly, lx):
+                        if flip in self.open or any(w in self.frozen for w in self.carriers(flip)):
+                            continue
+                        if self._flip_gain(flip, rtol) <= 0:
+                            continue
+                        for w in self.carriers(flip):
+                            ax = self.l[w].index(flip)
+                            self.t[w] = np.flip(self.t[w], axis=ax).copy()
+                        return True
         return False
 
     # --- rank-simplification

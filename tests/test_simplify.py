@@ -108,3 +108,54 @@ def test_simplify_terminates_with_split_on_random_networks():
         s, done = simplify.simplify(net, max_rounds=200)
         a, b = _value(net), _value(s)
         assert np.max(np.abs(a - b)) <= 1e-11 * np.max(np.abs(a))
+
+
+def _planted(seed):
+    """A random network (hyperedges, open labels, sizes 1..3) whose tensors
+    carry planted structure for every rule: diagonal or antidiagonal pairs
+    of axes, an axis supported on one value, low rank across a split."""
+    rng = np.random.default_rng(seed)
+    net = inputs.random_network(8, 12, 700 + seed, n_open=int(seed % 3), max_dim=3)
+    tensors = [np.array(t, dtype=complex) for t in net.tensors]
+    for v, t in enumerate(tensors):
+        ls = net.labels[v]
+        kind = rng.integers(0, 5)
+        if kind in (0, 1) and len(ls) >= 2:
+            pairs = [(x, y) for x in range(len(ls)) for y in range(x + 1, len(ls))
+                     if net.dims[ls[x]] == net.dims[ls[y]] > 1]
+            if pairs:
+                x, y = pairs[rng.integers(len(pairs))]
+                d = net.dims[ls[x]]
+                i = np.arange(d)
+                keep = (i[:, None] == i[None, :]) if kind == 0 else (i[:, None] == d - 1 - i[None, :])
+                shape = [d if a in (x, y) else 1 for a in range(t.ndim)]
+                tensors[v] = t * keep.reshape(shape)
+        elif kind == 2 and len(ls) >= 1:
+            x = int(rng.integers(len(ls)))
+            d = net.dims[ls[x]]
+            if d > 1:
+                mask = np.zeros(d)
+                mask[rng.integers(d)] = 1.0
+                shape = [d if a == x else 1 for a in range(t.ndim)]
+                tensors[v] = t * mask.reshape(shape)
+        elif kind == 3 and len(ls) >= 3:
+            k = len(ls) // 2
+            left = [net.dims[l] for l in ls[:k]]
+            right = [net.dims[l] for l in ls[k:]]
+            r = 1 + int(rng.integers(2))
+            u = rng.standard_normal((int(np.prod(left)), r)) + 1j * rng.standard_normal((int(np.prod(left)), r))
+            w = rng.standard_normal((r, int(np.prod(right)))) + 1j * rng.standard_normal((r, int(np.prod(right))))
+            tensors[v] = (u @ w).reshape(left + right)
+    return inputs.Network(tensors, net.labels, net.dims, net.open)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_planted_structure_is_simplified_without_changing_the_value(seed):
+    net = _planted(seed)
+    s, done = simplify.simplify(net)
+    assert s.open == net.open
+    assert all(len(set(ls)) == len(ls) for ls in s.labels)  # no label twice in a tensor
+    a, b = _value(net), _value(s)
+    assert np.shape(a) == np.shape(b)
+    scale = _value(inputs.Network([np.abs(t) for t in net.tensors], net.labels, net.dims, net.open))
+    assert np.max(np.abs(a - b)) <= 1e-11 * max(np.max(np.abs(scale)), 1e-300), done
