@@ -204,3 +204,54 @@ def test_wave_steps_hold_only_small_nodes(lib):
             assert size <= 16 and vc <= 22 and vc - size <= 14, (k, size, vc)
         biggest = max(range(len(pairs)), key=lambda k: info.vc[k])
         assert biggest not in in_wave
+
+
+def _random_tree(n, rng):
+    """A uniformly shuffled valid SSA tree: any two live ids are joined (so
+    outer products of unconnected parts occur too)."""
+    live = list(range(n))
+    pairs = []
+    for k in range(n - 1):
+        i, j = sorted(rng.choice(len(live), size=2, replace=False))
+        a, b = live[i], live[j]
+        pairs.append((int(a), int(b)))
+        live = [x for x in live if x not in (a, b)] + [n + k]
+    return pairs
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_plans_match_the_cost_model_and_schedule_every_node(lib, seed):
+    """Host plan only, on random networks (hyperedges, open and summed-only
+    labels, sizes 1..4, real and complex), random trees and random sliced
+    labels, in every mode: the library's W_s, C, d_sliced and FLOPs equal
+    the Python cost model's, and the launch steps hold every node once, each
+    after its children."""
+    from paper_2002_01935_gb300 import inputs, planner
+    rng = np.random.default_rng(seed)
+    net = inputs.random_network(int(rng.integers(2, 10)), int(rng.integers(3, 16)), 4000 + seed,
+                                n_open=int(rng.integers(0, 3)), max_dim=4)
+    cplx = bool(seed % 2)
+    if not cplx:
+        net = inputs.Network([np.real(t) for t in net.tensors], net.labels, net.dims, net.open)
+    pairs = _random_tree(net.n_tensors, rng) if seed % 3 else planner.greedy_tree(net.labels, net.dims, net.open)
+    summed = [l for l in sorted(net.dims) if l not in net.open]
+    k = int(rng.integers(0, min(3, len(summed)) + 1))
+    sliced = [int(x) for x in rng.choice(summed, size=k, replace=False)] if k else []
+    ref = planner.tree_info(net.labels, net.dims, pairs, net.open, sliced)
+    n = net.n_tensors
+    for mode in ("fp32", "tf32_split", "tf32_3m", "bf16_split"):
+        steps, info = _steps(lib, net, pairs, sliced, mode)
+        assert info["W"] == pytest.approx(ref.W)
+        assert info["C"] == pytest.approx(ref.C, rel=1e-12)
+        assert info["d_sliced"] == ref.d_sliced
+        assert info["flops"] == pytest.approx(ref.flops(cplx), rel=1e-12)
+        seen = {}
+        for s, st in enumerate(steps):
+            for pos, node in enumerate(st["nodes"]):
+                assert node not in seen
+                seen[node] = (s, pos)
+        assert sorted(seen) == list(range(n - 1))
+        for node, (a, b) in enumerate(pairs):
+            for c in (a, b):
+                if c >= n:
+                    assert seen[c - n] < seen[node]
