@@ -149,13 +149,34 @@ def _planted(seed):
     return inputs.Network(tensors, net.labels, net.dims, net.open)
 
 
-@pytest.mark.parametrize("seed", range(24))
+def _error_scale(net):
+    """Rounding scale of the network's value: its value on |T|, or, for a
+    structurally zero network (that value 0), the bound prod_v max|T_v| times
+    the number of summed assignments."""
+    absnet = inputs.Network([np.abs(t) for t in net.tensors], net.labels, net.dims, net.open)
+    scale = float(np.max(np.abs(_value(absnet))))
+    if scale > 0:
+        return scale
+    bound = float(np.prod([np.max(np.abs(t)) if np.size(t) else 0.0 for t in net.tensors]))
+    summed = [l for l in net.dims if l not in net.open]
+    return bound * float(np.prod([net.dims[l] for l in summed]))
+
+
+@pytest.mark.parametrize("seed", range(48))
 def test_planted_structure_is_simplified_without_changing_the_value(seed):
+    """Odd seeds freeze a random subset of the leaves: they come first in the
+    result, unchanged, and the value still holds."""
     net = _planted(seed)
-    s, done = simplify.simplify(net)
+    frozen = []
+    if seed % 2:
+        rng = np.random.default_rng(seed + 5)
+        frozen = sorted(int(x) for x in rng.choice(net.n_tensors, size=int(rng.integers(1, net.n_tensors)),
+                                                   replace=False))
+    s, done = simplify.simplify(net, frozen=frozen)
     assert s.open == net.open
+    for i, v in enumerate(frozen):
+        assert s.labels[i] == list(net.labels[v]) and np.array_equal(s.tensors[i], net.tensors[v])
     assert all(len(set(ls)) == len(ls) for ls in s.labels)  # no label twice in a tensor
     a, b = _value(net), _value(s)
     assert np.shape(a) == np.shape(b)
-    scale = _value(inputs.Network([np.abs(t) for t in net.tensors], net.labels, net.dims, net.open))
-    assert np.max(np.abs(a - b)) <= 1e-11 * max(np.max(np.abs(scale)), 1e-300), done
+    assert np.max(np.abs(a - b)) <= 1e-11 * max(_error_scale(net), 1e-300), done
