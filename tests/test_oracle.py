@@ -387,3 +387,45 @@ def test_environment_of_plain_product():
     env = gradient.environment([a, b], [[0], [0]], {0: 3}, 0,
                                lambda l, d, o: planner.greedy_tree(l, d, o))
     assert rel(env, b) < 1e-15
+
+
+def _random_ssa_tree(n, rng):
+    live, pairs = list(range(n)), []
+    for k in range(n - 1):
+        i, j = sorted(rng.choice(len(live), size=2, replace=False))
+        a, b = live[i], live[j]
+        pairs.append((int(a), int(b)))
+        live = [x for x in live if x not in (a, b)] + [n + k]
+    return pairs
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_trees_scalars_and_slice_ranges_match_nested_sum(seed):
+    """Brute force on tiny random networks with any tree (outer products of
+    unconnected parts included), a scalar leaf now and then, random sliced
+    labels, and the slice range cut in two: the two partial sums add up to
+    the nested sum of products."""
+    rng = np.random.default_rng(seed)
+    net = inputs.random_network(int(rng.integers(1, 7)), int(rng.integers(1, 9)), 12000 + seed,
+                                n_open=int(rng.integers(0, 3)), max_dim=int(rng.integers(1, 4)))
+    tensors, labels = list(net.tensors), [list(l) for l in net.labels]
+    if rng.random() < 0.3:
+        tensors.append(np.array(rng.standard_normal() + 1j * rng.standard_normal()))
+        labels.append([])
+    n = len(tensors)
+    pairs = _random_ssa_tree(n, rng) if n > 1 else []
+    summed = [l for l in sorted(net.dims) if l not in net.open]
+    k = int(rng.integers(0, min(2, len(summed)) + 1))
+    sliced = [int(x) for x in rng.choice(summed, size=k, replace=False)] if k else []
+    ref = brute.nested_sum(tensors, labels, net.dims, net.open)
+    scale = np.abs(brute.nested_sum([np.abs(t) for t in tensors], labels, net.dims, net.open))
+    m, e = tree.contract(tensors, labels, net.dims, net.open, pairs, sliced)
+    assert np.all(np.abs(np.asarray(m) * 2.0 ** e - ref) <= 1e-12 * scale + 1e-300)
+    d = int(np.prod([net.dims[l] for l in sliced])) if sliced else 1
+    cut = int(rng.integers(0, d + 1))
+    total = 0
+    for b, c in ((0, cut), (cut, d - cut)):
+        if c:
+            mm, ee = tree.contract(tensors, labels, net.dims, net.open, pairs, sliced, slice_begin=b, slice_count=c)
+            total = total + np.asarray(mm) * 2.0 ** ee
+    assert np.all(np.abs(total - ref) <= 1e-12 * scale + 1e-300)
