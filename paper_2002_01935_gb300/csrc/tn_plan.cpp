@@ -407,7 +407,8 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
         p.vlab.push_back(nd.lab);
         p.vstride.push_back(nd.stride);
         W = std::max(W, log2size(nd.lab));
-        C += std::pow(2.0, nd.vc);
+        // one leaf has no contraction vertex, so C = 0 (Sec. 2); the node
+        // only sums the leaf's own summed labels and orders the open axes
         p.nodes.push_back(nd);
     } else {
         for (int k = 0; k < n - 1; ++k) {
