@@ -12,6 +12,7 @@ tn_last_error); ``TensorNetwork`` wraps a handle for use with torch tensors.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from typing import Dict, List, Optional, Sequence, Tuple
 
@@ -162,8 +163,24 @@ def _hold(t, stream) -> None:
         t.record_stream(stream)
 
 
+# Flattened trees of recent calls: most callers contract one tree many
+# times, and flattening a few hundred pairs costs more than the device work
+# of a small network.  An entry is reused only if the call's pair list
+# equals the kept tuple copy (tuples are immutable, so any change is seen).
+_tree_cache: Dict[int, Tuple[list, np.ndarray]] = {}
+
+
 def _tree(pairs):
-    return _arr([x for p in pairs for x in p] or [0], np.int32)
+    if not isinstance(pairs, list):
+        return _arr([x for p in pairs for x in p] or [0], np.int32)
+    hit = _tree_cache.get(id(pairs))
+    if hit is not None and hit[0] == pairs:
+        return hit[1]
+    arr = _arr([x for p in pairs for x in p] or [0], np.int32)
+    if len(_tree_cache) >= 64:
+        _tree_cache.clear()
+    _tree_cache[id(pairs)] = ([tuple(p) for p in pairs], arr)
+    return arr
 
 
 def tn_contract_ex(h: int, pairs, sliced, mode: int, out_ptr: int, out_mem: int, exp_ptr: int,
@@ -411,7 +428,7 @@ class TensorNetwork:
             out_exp = torch.empty((), dtype=torch.int64, device=out.device)
         if out.dtype != odt or out_exp.dtype != torch.int64:
             raise TypeError(f"out must be {odt} and out_exp torch.int64")
-        n_out = int(np.prod(self.out_shape))
+        n_out = math.prod(self.out_shape)
         if out.numel() != n_out or not out.is_contiguous() or out_exp.numel() != 1:
             raise TNError(TN_EINVAL, f"out must be a contiguous tensor of {n_out} elements, out_exp a scalar")
         if out_exp.is_cuda != out.is_cuda:
@@ -440,7 +457,7 @@ class TensorNetwork:
         import torch
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         cplx = self.dtype == TN_C64
-        n_out = int(np.prod(self.out_shape))
+        n_out = math.prod(self.out_shape)
         keep = None
         if isinstance(adjoint, torch.Tensor) and adjoint.is_cuda:
             want = torch.complex128 if cplx else torch.float64
@@ -515,7 +532,7 @@ class TensorNetwork:
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         self._check_strides(n_inst, leaf_inst_stride)
         cplx = self.dtype == TN_C64
-        n_out = int(np.prod(self.out_shape))
+        n_out = math.prod(self.out_shape)
         if isinstance(adjoint, torch.Tensor) and adjoint.is_cuda:
             want = torch.complex128 if cplx else torch.float64
             if adjoint.dtype != want:

@@ -73,3 +73,20 @@ def test_output_buffers_are_checked(tnw):
                      out_exp=torch.empty((), dtype=torch.int32))
     _einval(lambda: tnw.contract(pairs, [], "fp32", out=torch.empty(tnw.out_shape, dtype=torch.complex128),
                                  out_exp=torch.empty(2, dtype=torch.int64)))
+
+
+def test_flattened_trees_follow_the_pair_list():
+    """The flattened tree is reused only for an equal pair list: replacing
+    a pair, lists of lists and non-list inputs all give the current pairs."""
+    pairs = [(0, 1), (2, 3), (4, 5)]
+    a = binding._tree(pairs)
+    assert a.tolist() == [0, 1, 2, 3, 4, 5]
+    assert binding._tree(pairs) is a  # unchanged: reused
+    pairs[1] = (3, 2)
+    assert binding._tree(pairs).tolist() == [0, 1, 3, 2, 4, 5]
+    lol = [[0, 1], [2, 3]]
+    assert binding._tree(lol).tolist() == [0, 1, 2, 3]
+    lol[0][1] = 9
+    assert binding._tree(lol).tolist() == [0, 9, 2, 3]
+    assert binding._tree(np.array([[1, 0]])).tolist() == [1, 0]
+    assert binding._tree([]).tolist() == [0]
