@@ -148,6 +148,7 @@ def tn_create(dtype: int, labels: Sequence[Sequence[int]], dims: Dict[int, int],
     _check(_lib.tn_create(ctypes.byref(h), dtype, len(labels), _p(ranks, ctypes.c_int32),
                           _p(flat, ctypes.c_int64), len(ids), _p(lid, ctypes.c_int64),
                           _p(ldim, ctypes.c_int64), len(open_labels), _p(opn, ctypes.c_int64)))
+    _n_leaves[h.value] = len(labels)
     return h.value
 
 
@@ -170,6 +171,19 @@ def _hold(t, stream) -> None:
 _tree_cache: Dict[int, Tuple[list, np.ndarray]] = {}
 
 
+# leaves per handle made here: the library reads 2 * (n_tensors - 1) tree
+# ids, so a pair list of another length is refused before the call (a short
+# one would be read past its end)
+_n_leaves: Dict[int, int] = {}
+
+
+def _tree_of(h: int, pairs):
+    n = _n_leaves.get(h)
+    if n is not None and len(pairs) != n - 1:
+        raise TNError(TN_EINVAL, f"the tree needs n_tensors - 1 = {n - 1} pairs, got {len(pairs)}")
+    return _tree(pairs)
+
+
 def _tree(pairs):
     if not isinstance(pairs, list):
         return _arr([x for p in pairs for x in p] or [0], np.int32)
@@ -188,7 +202,7 @@ def tn_contract_ex(h: int, pairs, sliced, mode: int, out_ptr: int, out_mem: int,
                    no_graph: bool = False,
                    prof_events: Optional[Sequence[int]] = None, prof_first: int = 0,
                    slice_batch: int = 0) -> None:
-    tr = _tree(pairs)
+    tr = _tree_of(h, pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     opt = tn_options(slice_begin, slice_count, int(no_graph), 0)
     opt.slice_batch = slice_batch
@@ -204,7 +218,7 @@ def tn_contract_ex(h: int, pairs, sliced, mode: int, out_ptr: int, out_mem: int,
 
 def tn_contract(h: int, pairs, sliced, mode: int, out_ptr: int, out_mem: int, exp_ptr: int,
                 stream: int = 0) -> None:
-    tr = _tree(pairs)
+    tr = _tree_of(h, pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     _check(_lib.tn_contract(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
                             out_ptr, out_mem, ctypes.cast(exp_ptr, _i64p), stream))
@@ -212,7 +226,7 @@ def tn_contract(h: int, pairs, sliced, mode: int, out_ptr: int, out_mem: int, ex
 
 def tn_contract_grad(h: int, pairs, sliced, mode: int, adjoint: np.ndarray, adj_exp2: int,
                      grad_ptrs: Sequence[int], stream: int = 0) -> None:
-    tr = _tree(pairs)
+    tr = _tree_of(h, pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     adj = np.ascontiguousarray(adjoint)
     gp = (_vp * len(grad_ptrs))(*[g or None for g in grad_ptrs])
@@ -230,7 +244,7 @@ def tn_contract_grad_ex(h: int, pairs, sliced, mode: int, adj_ptr: int, adj_mem:
                         stream: int = 0, slice_begin: int = 0, slice_count: int = 0) -> None:
     """tn_contract_grad with a host or device adjoint (pointer to FP64) and
     optional accumulation (flags = TN_GRAD_ACCUMULATE)."""
-    tr = _tree(pairs)
+    tr = _tree_of(h, pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     gp = (_vp * len(grad_ptrs))(*[g or None for g in grad_ptrs])
     _check(_lib.tn_contract_grad_ex(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
@@ -244,7 +258,7 @@ def tn_contract_grad_instances(h: int, pairs, sliced, mode: int, n_inst: int, le
                                slice_begin: int = 0, slice_count: int = 0) -> None:
     """Reverse sweep of n_inst copies (leaf v of copy i at + i *
     leaf_inst_stride[v] elements; None: all shared) in one launch sequence."""
-    tr = _tree(pairs)
+    tr = _tree_of(h, pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     st = _arr(list(leaf_inst_stride), np.int64) if leaf_inst_stride is not None else None
     gp = (_vp * len(grad_ptrs))(*[g or None for g in grad_ptrs])
@@ -263,7 +277,7 @@ def tn_selftest_flow_timeout(stream: int = 0) -> int:
 def tn_contract_noalloc(h: int, pairs, sliced, out_ptr: int, out_mem: int, exp_ptr: int,
                         stream: int = 0) -> None:
     """The contraction without any device allocation (fixed 8 MiB scratch)."""
-    tr = _tree(pairs)
+    tr = _tree_of(h, pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     _check(_lib.tn_contract_noalloc(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64),
                                     out_ptr, out_mem, ctypes.cast(exp_ptr, _i64p), stream))
@@ -273,7 +287,7 @@ def tn_autotune(h: int, pairs, sliced, mode: int, reps: int = 3, stream: int = 0
     """Time every candidate kernel per node and keep the fastest in the
     cached plan; returns the per-node choice (0 untuned, 1..4 and 6 tile shape,
     8 tensor core, 9 tensor core with 128-column tiles)."""
-    tr = _tree(pairs)
+    tr = _tree_of(h, pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     ch = np.zeros(max(len(pairs), 1), dtype=np.int32)
     _check(_lib.tn_autotune(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode, reps,
@@ -282,7 +296,7 @@ def tn_autotune(h: int, pairs, sliced, mode: int, reps: int = 3, stream: int = 0
 
 
 def tn_plan_info(h: int, pairs, sliced, mode: int = TN_MODE_FP32) -> Dict[str, float]:
-    tr = _tree(pairs)
+    tr = _tree_of(h, pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     out = np.zeros(8, dtype=np.float64)
     _check(_lib.tn_plan_info(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
@@ -294,7 +308,7 @@ def tn_plan_info(h: int, pairs, sliced, mode: int = TN_MODE_FP32) -> Dict[str, f
 def tn_plan_steps(h: int, pairs, sliced, mode: int = TN_MODE_FP32):
     """Launch steps of the per-slice sequence: list of dicts
     (wave, kind, cfg, launches, nodes)."""
-    tr = _tree(pairs)
+    tr = _tree_of(h, pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     ns = ctypes.c_int32(0)
     _check(_lib.tn_plan_steps(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
@@ -314,6 +328,7 @@ def tn_plan_steps(h: int, pairs, sliced, mode: int = TN_MODE_FP32):
 
 
 def tn_destroy(h: int) -> None:
+    _n_leaves.pop(h, None)
     _lib.tn_destroy(h)
 
 
@@ -509,7 +524,7 @@ class TensorNetwork:
         ex = torch.empty(n_inst, dtype=torch.int64, device="cuda")
         st = _arr(list(leaf_inst_stride), np.int64) if leaf_inst_stride is not None else None
         s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
-        _check(_lib.tn_contract_instances_keep(self.h, _p(_tree(pairs), ctypes.c_int32), m, n_inst,
+        _check(_lib.tn_contract_instances_keep(self.h, _p(_tree_of(self.h, pairs), ctypes.c_int32), m, n_inst,
                                                _p(st, ctypes.c_int64) if st is not None else None,
                                                out.data_ptr(), ex.data_ptr(), TN_MEM_DEVICE, s))
         self._grad_epoch = getattr(self, "_grad_epoch", 0) + 1
@@ -601,7 +616,7 @@ class TensorNetwork:
             self._strides = _arr(list(leaf_inst_stride), np.int64)
             strides = _p(self._strides, ctypes.c_int64)
         s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
-        tr = _tree(pairs)
+        tr = _tree_of(self.h, pairs)
         _check(_lib.tn_contract_instances(self.h, _p(tr, ctypes.c_int32), m, n_inst, strides,
                                           out.data_ptr(), ex.data_ptr(), TN_MEM_DEVICE, s))
         return out, ex
@@ -621,7 +636,9 @@ class Batch:
         import torch  # noqa: F401
         self.nets = list(networks)
         m = MODES[mode] if isinstance(mode, str) else int(mode)
-        self._trees = [_tree(t) for t in trees]
+        if len(trees) != len(self.nets):
+            raise TNError(TN_EINVAL, "one tree per network")
+        self._trees = [_tree_of(n.h, t) for n, t in zip(self.nets, trees)]
         hs = (_vp * len(self.nets))(*[n.h for n in self.nets])
         tp = (_i32p * len(self.nets))(*[t.ctypes.data_as(_i32p) for t in self._trees])
         h = _vp()

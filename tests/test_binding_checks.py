@@ -90,3 +90,21 @@ def test_flattened_trees_follow_the_pair_list():
     assert binding._tree(lol).tolist() == [0, 9, 2, 3]
     assert binding._tree(np.array([[1, 0]])).tolist() == [1, 0]
     assert binding._tree([]).tolist() == [0]
+
+
+def test_pair_lists_of_the_wrong_length_are_refused():
+    """The library reads n_tensors - 1 pairs: shorter or longer lists are
+    refused by the binding (a short one would be read past its end)."""
+    h = binding.tn_create(binding.TN_C64, [[0], [0, 1], [1]], {0: 2, 1: 2}, [])
+    try:
+        for pairs in ([(0, 1)], [(0, 1), (2, 3), (4, 0)], []):
+            _einval(lambda: binding.tn_plan_info(h, pairs, []))
+        assert binding.tn_plan_info(h, [(0, 1), (2, 3)], [])["C"] > 0
+    finally:
+        binding.tn_destroy(h)
+    one = binding.tn_create(binding.TN_C64, [[0]], {0: 2}, [0])
+    try:
+        _einval(lambda: binding.tn_plan_info(one, [(0, 0)], []))
+        binding.tn_plan_info(one, [], [])
+    finally:
+        binding.tn_destroy(one)
