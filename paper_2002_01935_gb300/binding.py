@@ -184,6 +184,14 @@ def _tree_of(h: int, pairs):
     return _tree(pairs)
 
 
+def _per_leaf(h: int, seq, name: str) -> None:
+    """Arrays with one entry per leaf (gradient pointers, instance strides)
+    are read n_tensors entries long by the library."""
+    n = _n_leaves.get(h)
+    if n is not None and seq is not None and len(seq) != n:
+        raise TNError(TN_EINVAL, f"{name} needs n_tensors = {n} entries, got {len(seq)}")
+
+
 def _tree(pairs):
     if not isinstance(pairs, list):
         return _arr([x for p in pairs for x in p] or [0], np.int32)
@@ -227,6 +235,7 @@ def tn_contract(h: int, pairs, sliced, mode: int, out_ptr: int, out_mem: int, ex
 def tn_contract_grad(h: int, pairs, sliced, mode: int, adjoint: np.ndarray, adj_exp2: int,
                      grad_ptrs: Sequence[int], stream: int = 0) -> None:
     tr = _tree_of(h, pairs)
+    _per_leaf(h, grad_ptrs, "grad_ptrs")
     sl = _arr(list(sliced) or [0], np.int64)
     adj = np.ascontiguousarray(adjoint)
     gp = (_vp * len(grad_ptrs))(*[g or None for g in grad_ptrs])
@@ -245,6 +254,7 @@ def tn_contract_grad_ex(h: int, pairs, sliced, mode: int, adj_ptr: int, adj_mem:
     """tn_contract_grad with a host or device adjoint (pointer to FP64) and
     optional accumulation (flags = TN_GRAD_ACCUMULATE)."""
     tr = _tree_of(h, pairs)
+    _per_leaf(h, grad_ptrs, "grad_ptrs")
     sl = _arr(list(sliced) or [0], np.int64)
     gp = (_vp * len(grad_ptrs))(*[g or None for g in grad_ptrs])
     _check(_lib.tn_contract_grad_ex(h, _p(tr, ctypes.c_int32), len(sliced), _p(sl, ctypes.c_int64), mode,
@@ -259,6 +269,8 @@ def tn_contract_grad_instances(h: int, pairs, sliced, mode: int, n_inst: int, le
     """Reverse sweep of n_inst copies (leaf v of copy i at + i *
     leaf_inst_stride[v] elements; None: all shared) in one launch sequence."""
     tr = _tree_of(h, pairs)
+    _per_leaf(h, grad_ptrs, "grad_ptrs")
+    _per_leaf(h, leaf_inst_stride, "leaf_inst_stride")
     sl = _arr(list(sliced) or [0], np.int64)
     st = _arr(list(leaf_inst_stride), np.int64) if leaf_inst_stride is not None else None
     gp = (_vp * len(grad_ptrs))(*[g or None for g in grad_ptrs])
