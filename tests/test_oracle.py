@@ -429,3 +429,25 @@ def test_random_trees_scalars_and_slice_ranges_match_nested_sum(seed):
             mm, ee = tree.contract(tensors, labels, net.dims, net.open, pairs, sliced, slice_begin=b, slice_count=c)
             total = total + np.asarray(mm) * 2.0 ** ee
     assert np.all(np.abs(total - ref) <= 1e-12 * scale + 1e-300)
+
+
+@pytest.mark.parametrize("n,seed", [(10, 2), (14, 3)])
+def test_environments_give_the_ising_energy(n, seed):
+    """d ln Z / d beta from the edge matrices' environments (chain rule
+    through M_e = exp(beta J_e s s')) equals the central difference of the
+    enumerated ln Z: a pin of the gradient oracle on a real network."""
+    beta = 0.3
+    net = inputs.random_ising(n, seed, beta=beta)
+    edges, J = net.meta["edges"], net.meta["J"]
+    tf = lambda l, d, o: planner.greedy_tree(l, d, o)
+    z = float(np.real(tree.value(net.tensors, net.labels, net.dims, net.open, tf(net.labels, net.dims, net.open))))
+    spin = np.array([1.0, -1.0])
+    dz = 0.0
+    for e in range(len(edges)):
+        v = n + e  # edge matrices follow the COPY tensors
+        env = gradient.environment(net.tensors, net.labels, net.dims, v, tf)
+        dm = J[e] * np.outer(spin, spin) * net.tensors[v]
+        dz += float(np.real(np.sum(env * dm)))
+    h = 1e-4
+    fd = (ising.log_z_enumerate(n, edges, J, beta + h) - ising.log_z_enumerate(n, edges, J, beta - h)) / (2 * h)
+    assert abs(dz / z - fd) <= 1e-6 * max(abs(fd), 1.0)
