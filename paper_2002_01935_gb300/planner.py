@@ -44,6 +44,9 @@ __all__ = [
     "slice_greedy",
     "plan",
     "validate_tree",
+    "structure_fingerprint",
+    "save_tree",
+    "load_tree",
 ]
 
 
@@ -484,3 +487,64 @@ def plan(net, target_width: Optional[float] = None, alpha: float = 1.0):
         sliced = slice_greedy(net.labels, net.dims, pairs, net.open, target_width)
     info = tree_info(net.labels, net.dims, pairs, net.open, sliced)
     return pairs, sliced, info
+
+
+# --------------------------------------------------------------------------
+# tree files: a tree found once serves every later contraction of networks
+# with the same structure (other bitstrings, other runs)
+# --------------------------------------------------------------------------
+
+TREE_FORMAT = 1
+
+
+def structure_fingerprint(leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
+                          open_labels: Iterable[int] = ()) -> str:
+    """Digest of what a tree depends on: the leaves' label tuples, the
+    label sizes and the open labels (not the tensor entries)."""
+    import hashlib
+    import json
+    doc = {"labels": [[int(x) for x in ls] for ls in leaf_labels],
+           "dims": sorted([int(k), int(v)] for k, v in dims.items()),
+           "open": [int(x) for x in open_labels]}
+    return hashlib.sha256(json.dumps(doc, separators=(",", ":")).encode()).hexdigest()
+
+
+def save_tree(path: str, leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
+              open_labels: Iterable[int], pairs: Sequence[Tuple[int, int]],
+              sliced: Sequence[int] = ()) -> None:
+    """Write a tree and its sliced labels as JSON, with the network's
+    structure fingerprint and the tree's W_s and C_s (for reading only)."""
+    import json
+    import os
+    opn = list(open_labels)
+    validate_tree(len(leaf_labels), pairs)
+    info = tree_info(leaf_labels, dims, pairs, opn, sliced)
+    doc = {"format": TREE_FORMAT, "n_leaves": len(leaf_labels),
+           "fingerprint": structure_fingerprint(leaf_labels, dims, opn),
+           "pairs": [[int(a), int(b)] for a, b in pairs], "sliced": [int(x) for x in sliced],
+           "W_s": info.W, "C_s": info.C_s, "d_sliced": info.d_sliced}
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(doc, f)
+    os.replace(tmp, path)
+
+
+def load_tree(path: str, leaf_labels: Sequence[Sequence[int]], dims: Dict[int, int],
+              open_labels: Iterable[int] = ()) -> Tuple[List[Tuple[int, int]], List[int]]:
+    """(pairs, sliced) from a tree file written for a network of this
+    structure; a file for another structure, another format or holding an
+    invalid tree raises ValueError."""
+    import json
+    with open(path) as f:
+        doc = json.load(f)
+    if doc.get("format") != TREE_FORMAT:
+        raise ValueError(f"{path}: unknown tree file format {doc.get('format')!r}")
+    if doc.get("fingerprint") != structure_fingerprint(leaf_labels, dims, open_labels):
+        raise ValueError(f"{path}: the tree was found for a network of another structure")
+    pairs = [(int(a), int(b)) for a, b in doc["pairs"]]
+    validate_tree(len(leaf_labels), pairs)
+    sliced = [int(x) for x in doc["sliced"]]
+    summed = set(dims) - set(int(x) for x in open_labels)
+    if len(set(sliced)) != len(sliced) or not set(sliced) <= summed:
+        raise ValueError(f"{path}: sliced labels must be distinct summed labels")
+    return pairs, sliced

@@ -172,3 +172,34 @@ def test_randomised_slicer_repeats_never_worse_and_seeded():
     p3, s3, i3 = planner.hyper_greedy(net.labels, net.dims, net.open, trials=3, seed=2,
                                       target_width=target, slicer_repeats=3)
     assert i3.W <= target + 1e-9
+
+
+def test_tree_files_round_trip_and_refuse_other_structures(tmp_path):
+    """A saved tree loads back unchanged for a network of the same structure
+    (other tensor entries: another bitstring), and is refused for another
+    structure, a broken tree or bad sliced labels."""
+    import json
+    circ = inputs.random_circuit(3, 3, 6, seed=3)
+    a = inputs.circuit_network(circ, [0] * 9)
+    b = inputs.circuit_network(circ, [1] * 9)  # same structure, other entries
+    pairs = planner.greedy_tree(a.labels, a.dims, a.open)
+    info = planner.tree_info(a.labels, a.dims, pairs, a.open)
+    sliced = planner.slice_greedy(a.labels, a.dims, pairs, a.open, info.W - 1)
+    path = str(tmp_path / "tree.json")
+    planner.save_tree(path, a.labels, a.dims, a.open, pairs, sliced)
+    got_pairs, got_sliced = planner.load_tree(path, b.labels, b.dims, b.open)
+    assert got_pairs == [tuple(p) for p in pairs] and got_sliced == list(sliced)
+    doc = json.load(open(path))
+    ref = planner.tree_info(a.labels, a.dims, pairs, a.open, sliced)
+    assert doc["W_s"] == ref.W and doc["C_s"] == ref.C_s and doc["d_sliced"] == ref.d_sliced
+    other = inputs.circuit_network(inputs.random_circuit(3, 3, 7, seed=3), [0] * 9)
+    with pytest.raises(ValueError):
+        planner.load_tree(path, other.labels, other.dims, other.open)
+    with pytest.raises(ValueError):  # the same leaves with an open label is another structure
+        planner.load_tree(path, a.labels, a.dims, [a.labels[-1][0]])
+    for key, bad in (("pairs", doc["pairs"][:-1]), ("sliced", [doc["sliced"][0]] * 2 if doc["sliced"] else [10 ** 9]),
+                     ("format", 99)):
+        broken = dict(doc, **{key: bad})
+        json.dump(broken, open(path, "w"))
+        with pytest.raises(ValueError):
+            planner.load_tree(path, a.labels, a.dims, a.open)
