@@ -203,3 +203,31 @@ def test_tree_files_round_trip_and_refuse_other_structures(tmp_path):
         json.dump(broken, open(path, "w"))
         with pytest.raises(ValueError):
             planner.load_tree(path, a.labels, a.dims, a.open)
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_slicing_never_widens_and_never_saves_work(seed):
+    """Sec. 4.7.1 on random networks, trees and sliced label sets: W_s <= W
+    and C_s = d_sliced * C(sliced tree) >= C, with equality of the costs
+    exactly when every contraction's label union holds every sliced label
+    of size > 1."""
+    rng = np.random.default_rng(seed)
+    net = inputs.random_network(int(rng.integers(2, 9)), int(rng.integers(2, 14)), 31000 + seed,
+                                n_open=int(rng.integers(0, 3)), max_dim=3)
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    base = planner.tree_info(net.labels, net.dims, pairs, net.open)
+    summed = [l for l in sorted(net.dims) if l not in net.open]
+    if not summed:
+        pytest.skip("no summed label")
+    k = int(rng.integers(1, min(3, len(summed)) + 1))
+    sliced = [int(x) for x in rng.choice(summed, size=k, replace=False)]
+    s = planner.tree_info(net.labels, net.dims, pairs, net.open, sliced)
+    assert s.W <= base.W + 1e-12
+    assert s.C_s >= base.C * (1 - 1e-12)
+    n = net.n_tensors
+    sets = planner.node_labels(net.labels, pairs, net.open)
+    unions = []
+    for a, b in pairs:
+        unions.append(set(sets[a]) | set(sets[b]))
+    every = all(l in u or net.dims[l] == 1 for u in unions for l in sliced)  # size-1 labels change nothing
+    assert (abs(s.C_s - base.C) <= 1e-9 * base.C) == every
