@@ -377,6 +377,12 @@ class TensorNetwork:
     def set_tensors(self, tensors) -> None:
         import torch
         want = torch.complex64 if self.dtype == TN_C64 else torch.float32
+        if len(tensors) > len(self.labels):
+            raise TNError(TN_EINVAL, f"{len(tensors)} tensors for {len(self.labels)} leaves")
+        for v, t in enumerate(tensors):
+            # every call reads a whole leaf (stacked copies may hold more)
+            if t.numel() < self._leaf_numel(v):
+                raise TNError(TN_EINVAL, f"leaf {v}: {t.numel()} elements, the leaf has {self._leaf_numel(v)}")
         self._keep = []
         attached = getattr(self, "_attached", None) or [None] * len(tensors)
         for v, t in enumerate(tensors):

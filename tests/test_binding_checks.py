@@ -108,3 +108,13 @@ def test_pair_lists_of_the_wrong_length_are_refused():
         binding.tn_plan_info(one, [], [])
     finally:
         binding.tn_destroy(one)
+
+
+def test_undersized_or_surplus_leaves_are_refused(tnw):
+    ts = tnw.test_leaves
+    v = max(range(len(ts)), key=lambda i: ts[i].numel())
+    short = list(ts)
+    short[v] = ts[v].reshape(-1)[:-1].contiguous()
+    _einval(lambda: tnw.set_tensors(short))
+    _einval(lambda: tnw.set_tensors(list(ts) + [ts[0]]))
+    tnw.set_tensors(ts)  # the full leaves still attach
