@@ -217,7 +217,8 @@ tn_status tn_contract_ex(tn_net* net, const int32_t* tree_pairs, int32_t n_slice
         begin = 0;
         count = p->d_sliced;
     }
-    if (begin < 0 || begin + count > p->d_sliced) return fail(TN_EINVAL, "slice range out of bounds");
+    // (count > 0 here: written so that no sum can overflow)
+    if (begin < 0 || begin > p->d_sliced - count) return fail(TN_EINVAL, "slice range out of bounds");
     if (o.slice_batch < 0) return fail(TN_EINVAL, "negative slice_batch");
     const int G = (int)std::max<int64_t>(1, std::min<int64_t>(o.slice_batch, count));
     st = ensure_instances(net, p, G, (cudaStream_t)stream);

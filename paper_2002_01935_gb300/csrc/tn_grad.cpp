@@ -893,7 +893,7 @@ tn_status run_grad(NetDesc& d, Plan& p, void* unit, const double* adj, int adj_m
         slice_begin = 0;
         slice_count = p.d_sliced;
     }
-    if (slice_begin < 0 || slice_begin + slice_count > p.d_sliced) {
+    if (slice_begin < 0 || slice_begin > p.d_sliced - slice_count) {  // no overflowing sum
         err = "tn_contract_grad: slice range out of bounds";
         return TN_EINVAL;
     }
