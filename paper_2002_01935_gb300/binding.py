@@ -196,8 +196,13 @@ def _tree(pairs):
     if not isinstance(pairs, list):
         return _arr([x for p in pairs for x in p] or [0], np.int32)
     hit = _tree_cache.get(id(pairs))
-    if hit is not None and hit[0] == pairs:
-        return hit[1]
+    if hit is not None:
+        try:
+            same = bool(hit[0] == pairs)
+        except ValueError:  # e.g. pairs given as numpy rows: not comparable, no reuse
+            same = False
+        if same:
+            return hit[1]
     arr = _arr([x for p in pairs for x in p] or [0], np.int32)
     if len(_tree_cache) >= 64:
         _tree_cache.clear()

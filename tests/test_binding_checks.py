@@ -89,6 +89,10 @@ def test_flattened_trees_follow_the_pair_list():
     lol[0][1] = 9
     assert binding._tree(lol).tolist() == [0, 9, 2, 3]
     assert binding._tree(np.array([[1, 0]])).tolist() == [1, 0]
+    rows = list(np.array([[0, 1], [2, 3]]))  # a list of numpy rows
+    assert binding._tree(rows).tolist() == [0, 1, 2, 3]
+    rows[0] = np.array([1, 0])
+    assert binding._tree(rows).tolist() == [1, 0, 2, 3]
     assert binding._tree([]).tolist() == [0]
 
 
