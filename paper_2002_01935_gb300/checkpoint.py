@@ -4,8 +4,8 @@ Slices are independent contractions whose values are summed (Sec. 4.7.1),
 so a long sliced run can be cut into consecutive blocks of the slice range.
 Each finished block leaves a partial result -- an FP64 mantissa (scalar or
 open-output tensor) m and an int64 power-of-two exponent e, value m * 2^e --
-which is written to a checkpoint file before the next block starts.  A
-resumed run reads the file and contracts only the blocks still missing.
+which is written to a checkpoint directory before the next block starts.  A
+resumed run reads the directory and contracts only the blocks still missing.
 The partials are folded in block order with exponents aligned to the
 largest one, so the result does not depend on where (or whether) the run
 was interrupted.
@@ -57,38 +57,47 @@ def fold(partials) -> Tuple[np.ndarray, int]:
 
 
 class SliceCheckpoint:
-    """The finished blocks of one sliced contraction, kept in ``path``
-    (an ``.npz`` file, replaced atomically after every block).  ``key``
-    names the problem (network, tree, sliced labels, mode): a file written
-    for another key, slice count or block size is refused, never mixed in."""
+    """The finished blocks of one sliced contraction, kept in the directory
+    ``path``: ``meta.json`` names the problem, and each finished block is one
+    small ``block_<i>.npz`` written atomically (a rename), so recording costs
+    the same for the first block and the ten-thousandth.  ``key`` names the
+    problem (network, tree, sliced labels, mode): a directory written for
+    another key, slice count or block size is refused, never mixed in."""
 
     def __init__(self, path: str, key: str, d_sliced: int, block: int):
+        import json
         self.path, self.key, self.d_sliced, self.block = path, str(key), int(d_sliced), int(block)
         self.done: dict = {}  # block index -> (mantissa, exp2)
-        if os.path.exists(path):
-            with np.load(path, allow_pickle=False) as z:
-                meta = (str(z["key"]), int(z["d_sliced"]), int(z["block"]))
-                if meta != (self.key, self.d_sliced, self.block):
-                    raise ValueError(f"checkpoint {path} belongs to {meta}, not "
-                                     f"{(self.key, self.d_sliced, self.block)}")
-                for i, m, e in zip(z["index"], z["mantissa"], z["exp2"]):
-                    self.done[int(i)] = (np.array(m), int(e))
+        meta = {"key": self.key, "d_sliced": self.d_sliced, "block": self.block}
+        mpath = os.path.join(path, "meta.json")
+        if os.path.exists(mpath):
+            with open(mpath) as f:
+                have = json.load(f)
+            if have != meta:
+                raise ValueError(f"checkpoint {path} belongs to {have}, not {meta}")
+            for name in os.listdir(path):
+                if name.startswith("block_") and name.endswith(".npz"):
+                    with np.load(os.path.join(path, name), allow_pickle=False) as z:
+                        self.done[int(z["index"])] = (np.array(z["mantissa"]), int(z["exp2"]))
+        else:
+            os.makedirs(path, exist_ok=True)
+            tmp = mpath + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(meta, f)
+            os.replace(tmp, mpath)
 
     def record(self, index: int, mantissa, exp2: int) -> None:
         self.done[int(index)] = (np.array(mantissa), int(exp2))
-        idx = sorted(self.done)
-        tmp = self.path + ".tmp.npz"
-        np.savez(tmp, key=np.array(self.key), d_sliced=np.array(self.d_sliced),
-                 block=np.array(self.block), index=np.array(idx, dtype=np.int64),
-                 mantissa=np.stack([self.done[i][0] for i in idx]),
-                 exp2=np.array([self.done[i][1] for i in idx], dtype=np.int64))
-        os.replace(tmp, self.path)
+        final = os.path.join(self.path, f"block_{int(index)}.npz")
+        tmp = os.path.join(self.path, f"tmp_{int(index)}.npz")
+        np.savez(tmp, index=np.array(int(index)), mantissa=np.array(mantissa), exp2=np.array(int(exp2)))
+        os.replace(tmp, final)
 
 
 def run(contract_block: Callable[[int, int], Tuple[np.ndarray, int]], d_sliced: int, block: int,
         path: str, key: str, on_block: Optional[Callable[[int], None]] = None) -> Tuple[np.ndarray, int]:
-    """Contract every block of [0, d_sliced) not yet in the checkpoint at
-    ``path`` (recording each as it finishes) and return the folded
+    """Contract every block of [0, d_sliced) not yet in the checkpoint
+    directory ``path`` (recording each as it finishes) and return the folded
     (mantissa, exp2) of all of them.  ``on_block(i)`` is called after block
     i is recorded."""
     ck = SliceCheckpoint(path, key, d_sliced, block)

@@ -53,7 +53,7 @@ def test_fold_aligns_exponents():
 @pytest.mark.parametrize("open_out", [False, True])
 def test_blocks_sum_to_the_full_contraction(tmp_path, open_out):
     net, pairs, sliced, d = _case(open_out)
-    m, e = checkpoint.run(_oracle_block(net, pairs, sliced), d, 3, str(tmp_path / "ck.npz"), "case")
+    m, e = checkpoint.run(_oracle_block(net, pairs, sliced), d, 3, str(tmp_path / "ck"), "case")
     rm, re = tree.contract_net(net, pairs, sliced)
     got, ref = np.asarray(m) * 2.0 ** e, np.asarray(rm) * 2.0 ** re
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
@@ -62,8 +62,8 @@ def test_blocks_sum_to_the_full_contraction(tmp_path, open_out):
 @pytest.mark.parametrize("open_out", [False, True])
 def test_interrupted_run_resumes_missing_blocks_only(tmp_path, open_out):
     net, pairs, sliced, d = _case(open_out)
-    ref = checkpoint.run(_oracle_block(net, pairs, sliced), d, 3, str(tmp_path / "ref.npz"), "case")
-    path = str(tmp_path / "ck.npz")
+    ref = checkpoint.run(_oracle_block(net, pairs, sliced), d, 3, str(tmp_path / "ref"), "case")
+    path = str(tmp_path / "ck")
     first = []
     with pytest.raises(RuntimeError):
         checkpoint.run(_oracle_block(net, pairs, sliced, first, fail_after=2), d, 3, path, "case")
@@ -80,8 +80,19 @@ def test_interrupted_run_resumes_missing_blocks_only(tmp_path, open_out):
 
 def test_checkpoint_of_another_problem_is_refused(tmp_path):
     net, pairs, sliced, d = _case(False)
-    path = str(tmp_path / "ck.npz")
+    path = str(tmp_path / "ck")
     checkpoint.run(_oracle_block(net, pairs, sliced), d, 4, path, "ising-20")
     for key, block in (("other", 4), ("ising-20", 2)):
         with pytest.raises(ValueError):
             checkpoint.run(_oracle_block(net, pairs, sliced), d, block, path, key)
+
+
+def test_each_block_is_its_own_file(tmp_path):
+    """Recording a block writes that block only: the directory holds the
+    metadata and one file per finished block."""
+    import os
+    net, pairs, sliced, d = _case(False)
+    path = str(tmp_path / "ck")
+    checkpoint.run(_oracle_block(net, pairs, sliced), d, 3, path, "case")
+    names = set(os.listdir(path))
+    assert names == {"meta.json"} | {f"block_{i}.npz" for i in range(len(checkpoint.blocks(d, 3)))}
