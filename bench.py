@@ -3,17 +3,20 @@
 
 Workloads (``--workload``):
 
-  ising100    (default) Ising partition function of a random 3-regular graph,
+  circuit7x7  (default) one amplitude of a 7x7-qubit, 14-cycle random circuit,
+              Hyper-Greedy tree sliced to W_s <= 28 (2^24 slices of up to 2^28
+              complex entries per tensor); one step = a bounded sample of
+              consecutive slices (``--slices``, default 2); the time per
+              amplitude is extrapolated over all slices (as the paper does for
+              its starred rows).  The oracle checks the GPU on sub-slices of
+              the same tree sliced further, to W_s <= 20.
+  ising100    Ising partition function of a random 3-regular graph,
               N = 100, beta = 0.3, J = +-1, greedy tree sliced to W_s <= 24,
               float32 leaves.  One step = one full contraction (all slices).
   circuit4x4  one amplitude of a 4x4-qubit, 8-cycle random circuit, greedy
               tree, no slicing (complex64 leaves).
   circuit5x5  one amplitude of a 5x5-qubit, 10-cycle random circuit (the
               smaller circuit that is checked in full), greedy tree.
-  circuit7x7  one amplitude of a 7x7-qubit, 14-cycle random circuit,
-              Hyper-Greedy tree sliced to W_s <= 28; one step = a bounded
-              sample of consecutive slices (``--slices``); the time per
-              amplitude is extrapolated over all 2^k slices.
   grad5x4     loss = mean over 64 bitstrings of ln|c_x|^2 of a 5x4-qubit,
               12-cycle circuit and its gradient with respect to the (theta, phi)
               of all 93 fSim gates, through the autograd Function (forward tree
@@ -49,6 +52,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -64,16 +69,35 @@ WORKLOAD_NAMES = {
     "node": "single_complex_node",
     "sample": "sample_5x4_12cyc_open6_fidelity_mixture",
 }
-MODES = ["fp32", "tf32_split", "bf16_split", "tf32_3m"]
-# accuracy each mode is held to (relative, against the FP64 oracle)
-MODE_TOL = {"fp32": 1e-5, "tf32_split": 1e-5, "bf16_split": 1e-4, "tf32_3m": 1e-2}
+MODES = ["fp32", "tf32_split", "fp16_split", "bf16_split", "tf32_3m"]
+# accuracy each mode is held to (relative, against the FP64 oracle run on the
+# same leaf values the GPU reads)
+MODE_TOL = {"fp32": 1e-5, "tf32_split": 1e-5, "fp16_split": 1e-5, "bf16_split": 1e-4, "tf32_3m": 1e-2}
 L2_FLUSH_BYTES = 512 << 20
 # FP32 FMA peak of one GB300: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz.
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # nominal dense tensor rates per GPU (TF32 : BF16 = 1.1 : 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
 # real products executed per algorithmic product on the tensor cores
-MODE_PASSES = {"tf32_split": 3, "bf16_split": 3, "tf32_3m": 1}
+MODE_PASSES = {"tf32_split": 3, "bf16_split": 3, "fp16_split": 3, "tf32_3m": 1}
+# modes whose tensor-core operands are 16-bit (kind::f16: the BF16 rate)
+HALF_MODES = ("bf16_split", "fp16_split")
+
+
+def tc_peak(mode, peaks):
+    """Dense tensor peak of the mode's operand type: measured BF16 for the
+    16-bit formats, measured BF16 x 1.1/2.25 (nominal TF32 : BF16) for TF32."""
+    if mode in HALF_MODES:
+        return peaks["bf16_tflops"], f"{peaks['source']} bf16 (fp16 and bf16 share the rate)"
+    return peaks["bf16_tflops"] * TF32_OVER_BF16, f"{peaks['source']} bf16 x 1.1/2.25 (nominal TF32:BF16)"
+
+
+def gpu_leaves(net):
+    """The network as the GPU reads it (leaves rounded to complex64 /
+    float32, widened back): the oracle's parity reference is computed on
+    these values, so the comparison measures the executor's arithmetic and
+    not the rounding of the inputs."""
+    return net.as_stored()
 
 
 # --------------------------------------------------------------------------
@@ -227,46 +251,63 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 
 def oracle_full(net, pairs, sliced, info, budget_s: float = 12.0, max_runs: int = 40):
-    """Time full oracle contractions of the same network (all slices)."""
+    """Time full oracle contractions (all slices) of the network as the GPU
+    reads it (leaves rounded to its storage type); also returns the value
+    for the leaves before that rounding (context: the inputs' own rounding)."""
     from oracle import tree
+    gnet = gpu_leaves(net)
     times = []
     val = None
     t_all = time.perf_counter()
     while len(times) < max_runs and (time.perf_counter() - t_all) < budget_s:
         t0 = time.perf_counter()
-        m, e = tree.contract_net(net, pairs, sliced)
+        m, e = tree.contract_net(gnet, pairs, sliced)
         times.append(time.perf_counter() - t0)
         val = (m, e)
     t = statistics.mean(times)
     flops = info.flops(net.is_complex)
+    val_wide = tree.contract_net(net, pairs, sliced)
     return {"value": flops / t / 1e12, "unit": "TFLOP/s", "cores": tree.max_threads(),
             "kind": "oracle", "s_per_network": t,
-            "sample": f"{len(times)} full contractions of the same network (all slices)"}, val
+            "sample": f"{len(times)} full contractions of the same network (all slices)"}, val, val_wide
+
+
+def subslicing(net, pairs, target: float = 20.0):
+    """The tree's slicing refined to W_s <= target (sub-slices the oracle
+    finishes in about a second each)."""
+    from paper_2002_01935_gb300 import planner
+    sl2 = planner.slice_greedy(net.labels, net.dims, pairs, net.open, target)
+    return sl2, planner.tree_info(net.labels, net.dims, pairs, net.open, sl2)
 
 
 def oracle_subslices(net, pairs, target: float = 20.0, budget_s: float = 10.0, max_slices: int = 64):
     """Time the oracle on consecutive sub-slices of the same tree sliced
-    further, to W_s <= target: a bounded sample of the same contraction."""
+    further, to W_s <= target: a bounded sample of the same contraction, on
+    the leaf values the GPU reads.  Returns the timing, the sub-slicing, the
+    per-sub-slice values and their sums, on those leaves and on the leaves
+    before rounding to the GPU's storage type (same sub-slices)."""
     from oracle import tree
-    from paper_2002_01935_gb300 import planner
-    sl2 = planner.slice_greedy(net.labels, net.dims, pairs, net.open, target)
-    i2 = planner.tree_info(net.labels, net.dims, pairs, net.open, sl2)
-    k, t_sum, acc, acc_e = 0, 0.0, 0.0, None
+    sl2, i2 = subslicing(net, pairs, target)
+    gnet = gpu_leaves(net)
+    k, t_sum = 0, 0.0
     vals = []
     t_all = time.perf_counter()
     while k < max_slices and (time.perf_counter() - t_all) < budget_s:
         t0 = time.perf_counter()
-        m, e = tree.contract_net(net, pairs, sl2, slice_begin=k, slice_count=1)
+        m, e = tree.contract_net(gnet, pairs, sl2, slice_begin=k, slice_count=1)
         t_sum += time.perf_counter() - t0
         vals.append((complex(m), int(e)))
         k += 1
     e_max = max(e for _, e in vals)
     ref = sum(m * 2.0 ** (e - e_max) for m, e in vals)
+    mw, ew = tree.contract_net(net, pairs, sl2, slice_begin=0, slice_count=k)
     per = 8.0 if net.is_complex else 2.0
-    return {"value": per * i2.C * k / t_sum / 1e12, "unit": "TFLOP/s", "cores": tree.max_threads(),
-            "kind": "oracle", "s_per_subslice": t_sum / k,
-            "sample": f"{k} consecutive sub-slices of the same tree sliced to W_s <= {target:g} "
-                      f"(C per sub-slice {i2.C:.3e})"}, (sl2, k, ref, e_max)
+    return ({"value": per * i2.C * k / t_sum / 1e12, "unit": "TFLOP/s", "cores": tree.max_threads(),
+             "kind": "oracle", "s_per_subslice": t_sum / k,
+             "sample": f"{k} consecutive sub-slices of the same tree sliced to W_s <= {target:g} "
+                       f"(C per sub-slice {i2.C:.3e})"},
+            {"sliced": sl2, "count": k, "vals": vals, "ref": (ref, e_max),
+             "ref_wide": (complex(mw), int(ew))})
 
 
 # --------------------------------------------------------------------------
@@ -281,7 +322,7 @@ def run_reference(args):
     from oracle import build as obuild
     from oracle import tree
     obuild.build()
-    if args.workload not in ("ising100", "ising100_hyper", "circuit4x4", "circuit5x5"):
+    if args.workload not in ("ising100", "ising100_hyper", "circuit4x4", "circuit5x5", "circuit7x7"):
         print(json.dumps({"impl": "reference", "unavailable":
                           f"the FP64 oracle needs hours per step on the {args.workload} workload"}))
         return 0
@@ -289,28 +330,49 @@ def run_reference(args):
     w = (wl_ising(0, simplified=simp) if args.workload == "ising100" else
          wl_ising(0, hyper=True) if args.workload == "ising100_hyper" else
          wl_circuit(4, 4, 8, 0, simplified=simp) if args.workload == "circuit4x4" else
-         wl_circuit(5, 5, 10, 0, simplified=simp))
+         wl_circuit(5, 5, 10, 0, simplified=simp) if args.workload == "circuit5x5" else
+         wl_circuit7x7(0, args.slices))
     net, pairs, sliced, info = w["net"], w["pairs"], w["sliced"], w["info"]
+    gnet = gpu_leaves(net)
+    per = 8.0 if net.is_complex else 2.0
+    if args.workload == "circuit7x7":
+        # one step = one sub-slice of the W_s <= 28 slicing refined to
+        # W_s <= 20 (a W_s <= 28 slice takes the oracle hours): a bounded
+        # sample of the same contraction, consecutive sub-slices
+        sl2, i2 = subslicing(net, pairs)
+        run = lambda k: tree.contract_net(gnet, pairs, sl2, slice_begin=k, slice_count=1)
+        flops_unit = per * i2.C
+        sample = (f"one sub-slice per step: consecutive sub-slices of the same tree with its "
+                  f"slicing refined to W_s <= 20 (C per sub-slice {i2.C:.3e})")
+    else:
+        run = lambda k: tree.contract_net(gnet, pairs, sliced)
+        flops_unit = info.flops(net.is_complex)
+        sample = f"{args.steps} full contractions"
+    k = 0
     for _ in range(1 if args.warmup > 0 else 0):
-        tree.contract_net(net, pairs, sliced)
+        run(k)
+        k += 1
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        tree.contract_net(net, pairs, sliced)
+        run(k)
         times.append(time.perf_counter() - t0)
+        k += 1
     t = statistics.mean(times)
-    val = info.flops(net.is_complex) / t / 1e12
+    val = flops_unit / t / 1e12
+    cfg = dict(workload=WORKLOAD_NAMES[args.workload] + ("_simplified" if simp else ""),
+               W_s=info.W, C=info.C, d_sliced=info.d_sliced, **w["config"])
     line = {"metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": dict(workload=WORKLOAD_NAMES[args.workload] + ("_simplified" if simp else ""),
-                           W_s=info.W, C=info.C,
-                           d_sliced=info.d_sliced, **w["config"]),
+            "data": "synthetic", "impl": "reference", "config": cfg,
+            "s_per_network": per * info.C * info.d_sliced / (val * 1e12),
             "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": tree.max_threads(),
-                             "kind": "oracle", "sample": f"{args.steps} full contractions"},
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    if net.is_complex:
+        line["s_per_amplitude"] = line["s_per_network"]
     print(json.dumps(line), flush=True)
     return 0
 
@@ -338,12 +400,10 @@ def roofline(steps, dom, dom_ms, nodes, mode, ms_per_step, peaks):
     st = steps[dom]
     t_hbm = dn["bytes"] / (peaks["hbm_gbs"] * 1e9)
     if st["kind"] == 2:
-        tc_peak = peaks["bf16_tflops"] * (1.0 if mode == "bf16_split" else TF32_OVER_BF16)
+        pk, pk_src = tc_peak(mode, peaks)
         passes = MODE_PASSES.get(mode, 1)
-        t_alu = dn["flops"] * passes / (tc_peak * 1e12)
-        pipe = {"bound": "tensor", "peak": tc_peak,
-                "peak_source": f"{peaks['source']} bf16 x " +
-                               ("1" if mode == "bf16_split" else "1.1/2.25 (nominal TF32:BF16)"),
+        t_alu = dn["flops"] * passes / (pk * 1e12)
+        pipe = {"bound": "tensor", "peak": pk, "peak_source": pk_src,
                 "executed_flops": dn["flops"] * passes}
     else:
         t_alu = dn["flops"] / (FP32_SIMT_TFLOPS * 1e12)
@@ -385,8 +445,7 @@ def tree_roofline(steps, nodes, mode, ms_per_step, slices_per_step, peaks, step_
             nd = nodes[j]
             t_hbm = nd["bytes"] / (peaks["hbm_gbs"] * 1e9)
             if st["kind"] == 2:
-                tc = peaks["bf16_tflops"] * (1.0 if mode == "bf16_split" else TF32_OVER_BF16)
-                t_alu = nd["flops"] * MODE_PASSES.get(mode, 1) / (tc * 1e12)
+                t_alu = nd["flops"] * MODE_PASSES.get(mode, 1) / (tc_peak(mode, peaks)[0] * 1e12)
             else:
                 t_alu = nd["flops"] / (FP32_SIMT_TFLOPS * 1e12)
             t = max(t_hbm, t_alu)
@@ -399,7 +458,7 @@ def tree_roofline(steps, nodes, mode, ms_per_step, slices_per_step, peaks, step_
             tiny_steps_ms += step_ms[k]
     t_ms = t_roof * slices_per_step * 1e3
     return {"t_roof_ms": t_ms, "measured_ms": ms_per_step, "frac": t_ms / ms_per_step,
-            "peaks": "measured HBM and bf16 (TF32 = bf16 x 1.1/2.25), derived FP32 SIMT",
+            "peaks": "measured HBM and bf16 (FP16 = bf16; TF32 = bf16 x 1.1/2.25), derived FP32 SIMT",
             "latency_bound_nodes": tiny, "nodes": sum(len(s["nodes"]) for s in steps),
             "latency_bound_step_ms": tiny_steps_ms * slices_per_step,
             "latency_bound_time_frac": tiny_steps_ms * slices_per_step / ms_per_step}
@@ -535,20 +594,27 @@ def run_network(args, torch, dist, rank, world, local):
                "ms_per_step": t_e2e / args.steps * 1e3}
         htn.close()
 
-    # the oracle on the host cores: timing and the reference value
-    cpu, rel_err, ref = None, None, None
+    # the oracle on the host cores: timing and the reference value, computed
+    # on the leaf values the GPU reads (parity), and on the leaves before
+    # their rounding to complex64 / float32 (context: the inputs' rounding)
+    cpu, rel_err, rel_err_wide, ref = None, None, None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         if w["oracle"] == "full":
-            cpu, (om, oe) = oracle_full(net, pairs, sliced, info)
-            ref = (complex(om) if cplx else float(om), int(oe), sliced, 0, sc)
-            rel_err = rel_error(result, result_exp, ref[0], ref[1], cplx)
+            cpu, (om, oe), (wm, we) = oracle_full(net, pairs, sliced, info)
+            ref = {"ref": (complex(om) if cplx else float(om), int(oe)),
+                   "ref_wide": (complex(wm) if cplx else float(wm), int(we)),
+                   "sliced": sliced, "begin": 0, "count": sc}
+            got = (result, result_exp)
         else:
-            cpu, (sl2, k, rm, re_) = oracle_subslices(net, pairs)
-            ref = (rm, re_, sl2, 0, k)
-            gm, ge = scalar_value(*tnw.contract(pairs, sl2, mode, slice_begin=0, slice_count=k), cplx)
-            rel_err = rel_error(gm, ge, rm, re_, cplx)
+            cpu, sub = oracle_subslices(net, pairs)
+            ref = {"ref": sub["ref"], "ref_wide": sub["ref_wide"], "sliced": sub["sliced"],
+                   "begin": 0, "count": sub["count"], "vals": sub["vals"]}
+            got = scalar_value(*tnw.contract(pairs, sub["sliced"], mode, slice_begin=0,
+                                             slice_count=sub["count"]), cplx)
             cpu["rel_err_sample"] = ("GPU vs oracle on the same sub-slices (the slice sample "
                                      "itself is beyond the oracle's reach)")
+        rel_err = rel_error(got[0], got[1], ref["ref"][0], ref["ref"][1], cplx)
+        rel_err_wide = rel_error(got[0], got[1], ref["ref_wide"][0], ref["ref_wide"][1], cplx)
 
     # every precision mode on the same work (device buffers), with its error
     modes_cmp = None
@@ -571,10 +637,20 @@ def run_network(args, torch, dist, rank, world, local):
             entry = {"ms_per_step": tms, "tflops": flops_step / (tms / 1e3) / 1e12,
                      "tol": MODE_TOL[md]}
             if ref is not None:
-                rm, re_, rsl, rb, rc = ref
-                gm, ge = scalar_value(*tnw.contract(pairs, rsl, md, slice_begin=rb, slice_count=rc), cplx)
-                entry["rel_err"] = rel_error(gm, ge, rm, re_, cplx)
+                gm, ge = scalar_value(*tnw.contract(pairs, ref["sliced"], md, slice_begin=ref["begin"],
+                                                    slice_count=ref["count"]), cplx)
+                entry["rel_err"] = rel_error(gm, ge, ref["ref"][0], ref["ref"][1], cplx)
                 entry["within_tol"] = entry["rel_err"] <= MODE_TOL[md]
+                entry["rel_err_c128_leaves"] = rel_error(gm, ge, ref["ref_wide"][0], ref["ref_wide"][1], cplx)
+                if "vals" in ref:
+                    # every sub-slice on its own, against the oracle's value of it
+                    errs = []
+                    for j, (vm, ve) in enumerate(ref["vals"]):
+                        sm_, se_ = scalar_value(*tnw.contract(pairs, ref["sliced"], md, slice_begin=j,
+                                                              slice_count=1), cplx)
+                        errs.append(rel_error(sm_, se_, vm, ve, cplx))
+                    entry["subslice_rel_err_max"] = max(errs)
+                    entry["subslice_rel_err_median"] = statistics.median(errs)
             modes_cmp[md] = entry
 
     groups = sc
@@ -597,9 +673,13 @@ def run_network(args, torch, dist, rank, world, local):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic", "config": cfg,
+        "dtype": "c64" if cplx else "f32", "data": "synthetic", "config": cfg,
         "s_per_network": ms_per_step / 1e3 * (info.d_sliced / sc),
         "rel_err_vs_oracle": rel_err,
+        "rel_err_vs_oracle_c128_leaves": rel_err_wide,
+        "rel_err_definition": ("|got - oracle| / |oracle|, the oracle (FP64) run on the leaf values "
+                               "the GPU reads; *_c128_leaves: against the leaves before their rounding "
+                               "to the GPU's storage type"),
         "roofline": roof,
         "tree_roofline": tree_roofline(steps, nodes, mode, ms_per_step, sc, peaks, step_ms),
         "cpu_baseline": cpu,
@@ -744,7 +824,7 @@ def run_batch(args, torch, dist, rank, world, local):
             if time.perf_counter() - t_all > 10.0:
                 break
             t1 = time.perf_counter()
-            om, oe = tree.contract_net(ising_nets[j], ising_trees[j])
+            om, oe = tree.contract_net(gpu_leaves(ising_nets[j]), ising_trees[j])
             t_or += time.perf_counter() - t1
             fl_or += flops[n_amp + j]
             i = n_amp + j
@@ -753,16 +833,17 @@ def run_batch(args, torch, dist, rank, world, local):
         cpu = {"value": fl_or / t_or / 1e12, "unit": "TFLOP/s", "cores": tree.max_threads(),
                "kind": "oracle", "sample": f"{k} of the {len(ising_nets)} Ising networks, full"}
         rel = {"ising_max": max(errs) if errs else None, "ising_checked": k}
-        sub, (sl2, kk, rm, re_) = oracle_subslices(amp_nets[0], a_pairs, budget_s=6.0)
-        gm, ge = scalar_value(*handles[0].contract(a_pairs, sl2, mode, slice_begin=0, slice_count=kk), True)
-        rel["amplitude_subslices"] = rel_error(gm, ge, rm, re_, True)
+        sub, so = oracle_subslices(amp_nets[0], a_pairs, budget_s=6.0)
+        gm, ge = scalar_value(*handles[0].contract(a_pairs, so["sliced"], mode, slice_begin=0,
+                                                   slice_count=so["count"]), True)
+        rel["amplitude_subslices"] = rel_error(gm, ge, so["ref"][0], so["ref"][1], True)
         rel["amplitude_sample"] = sub["sample"]
 
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "dtype": "c64+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAMES["batch"], "mode": mode,
                    "amplitudes": n_amp, "amplitude_sample_of": 1024, "circuit": "6x6, 12 cycles",
                    "amplitude_tree": f"Hyper-Greedy 32 trials, W {a_info.W:g}, C {a_info.C:.3e}",
@@ -924,7 +1005,7 @@ def run_grad(args, torch, dist, rank, world, local):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "dtype": "c64", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAMES["grad5x4"], "mode": mode, "qubits": R * C, "cycles": T,
                    "parameters": 2 * len(fs), "bitstrings": len(bits), "W": info.W, "C": info.C,
                    "flops_per_step": flops_step, "tree": "greedy (alpha=1, tau=0)",
@@ -997,7 +1078,7 @@ def run_sample(args, torch, dist, rank, world, local):
     line = {
         "metric": METRIC, "value": flops * world / total / 1e12, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAMES[args.workload], "mode": args.mode, "qubits": R * C,
                    "cycles": T, "open_qubits": open_q, "amplitudes_per_contraction": 64,
@@ -1063,11 +1144,11 @@ def run_node(args, torch, dist, rank, world, local):
     passes = MODE_PASSES.get(mode, 1) if tc else 1
     if mode == "tf32_3m" and tc:
         passes = 0.75  # three real products per complex one instead of four
-    peak = (peaks["bf16_tflops"] * (1.0 if mode == "bf16_split" else TF32_OVER_BF16)) if tc else FP32_SIMT_TFLOPS
+    peak = tc_peak(mode, peaks)[0] if tc else FP32_SIMT_TFLOPS
     achieved = flops / (ms_node / 1e3) / 1e12
     roof = {"bound": "tensor" if tc else "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "executed_frac": achieved * passes / peak, "traffic": None,
-            "peak_source": (f"{peaks['source']} bf16" + ("" if mode == "bf16_split" else " x 1.1/2.25")) if tc
+            "peak_source": tc_peak(mode, peaks)[1] if tc
             else "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
             "kernel": f"node ({mb}, {nb}, {kb}) bits, {'pack + tcgen05 GEMM' if tc else 'k_tile'}",
             "share_of_step": ms_node / ms_step}
@@ -1083,7 +1164,7 @@ def run_node(args, torch, dist, rank, world, local):
     line = {
         "metric": METRIC, "value": flops / (ms_step / 1e3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAMES["node"], "mode": mode, "bits_m_n_k": [mb, nb, kb],
                    "plan_kernels": {"tensor_core": plan["n_tensor_core"], "tiled": plan["n_tiled"]},
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
@@ -1104,10 +1185,11 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
                     help="timed steps (default: 400 for the sub-millisecond workloads, so that the "
-                         "timed region spans several clock samples; 5 otherwise; 20 for --impl reference)")
+                         "timed region spans several clock samples; 20 for circuit7x7 and for "
+                         "--impl reference; 5 otherwise)")
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="ising100", choices=list(WORKLOAD_NAMES))
-    ap.add_argument("--mode", default="tf32_split", choices=MODES)
+    ap.add_argument("--workload", default="circuit7x7", choices=list(WORKLOAD_NAMES))
+    ap.add_argument("--mode", default="fp16_split", choices=MODES)
     ap.add_argument("--slices", type=int, default=2, help="circuit7x7: slices per step")
     ap.add_argument("--amplitudes", type=int, default=8, help="batch: amplitudes per step")
     ap.add_argument("--ising", type=int, default=256, help="batch: Ising networks per step")
@@ -1124,7 +1206,8 @@ def main():
     args = ap.parse_args()
     if args.steps is None:
         short = args.workload in ("ising100", "ising100_hyper", "circuit4x4", "circuit5x5")
-        args.steps = 20 if args.impl == "reference" else (400 if short else 5)
+        args.steps = (20 if args.impl == "reference" or args.workload == "circuit7x7"
+                      else (400 if short else 5))
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(args.warmup, 3)

@@ -68,13 +68,24 @@ typedef enum {
  *   TN_MODE_TF32_SPLIT : operands split hi+lo in TF32, three products
  *                        (hi*hi + hi*lo + lo*hi), 4M, FP32 accumulation
  *   TN_MODE_BF16_SPLIT : the same split in BF16
+ *   TN_MODE_FP16_SPLIT : the same split in FP16, whose 11-bit significand
+ *                        equals TF32's while its tensor-core rate equals
+ *                        BF16's.  Each operand is scaled by a power of two
+ *                        so that its largest magnitude lies in [2^14, 2^15);
+ *                        entries at least 2^-18 of that largest keep the full
+ *                        22 bits of hi + lo, smaller ones lose low bits (FP16
+ *                        subnormals) and those below 2^-40 of it count as 0.
+ *                        Suited to networks whose tensors span a moderate
+ *                        dynamic range (random circuits); prefer TF32_SPLIT
+ *                        where single tensors span more than ~2^18.
  * Nodes too small for the tensor cores run the FP32 path in every mode.
  */
 typedef enum {
     TN_MODE_FP32 = 0,
     TN_MODE_TF32_3M = 1,
     TN_MODE_TF32_SPLIT = 2,
-    TN_MODE_BF16_SPLIT = 3
+    TN_MODE_BF16_SPLIT = 3,
+    TN_MODE_FP16_SPLIT = 4
 } tn_mode;
 
 enum { TN_MEM_DEVICE = 0, TN_MEM_HOST = 1 };
@@ -312,14 +323,14 @@ tn_status tn_contract_instances_keep(tn_net *net, const int32_t *tree_pairs, tn_
  * tn_contract_noalloc -- tn_contract for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a deployment variant.
  * tn_contract obtains its workspace with cudaMalloc on the first run of a
- * tree; callers that run while a CUDA graph is being captured, hosts that
- * forbid allocation after start-up, and processes whose device memory is
- * owned by another allocator cannot let it do so.  This call runs the same
- * node kernels (FP32 arithmetic, as TN_MODE_FP32) with every piece of scratch
- * -- intermediate tensors, renormalisation slots, control block, FP64
- * accumulator -- inside one fixed 8 MiB device array that is part of the
- * library image; it calls no cudaMalloc, cudaFree or other allocating
- * routine.
+ * tree.  Hosts that must not allocate device memory after start-up (fixed
+ * memory budgets, real-time loops) and processes whose device memory is
+ * owned by another allocator's pool cannot let it do so.  This call runs the
+ * same contraction on the generic node kernel (FP32 arithmetic, as
+ * TN_MODE_FP32) with every piece of scratch -- intermediate tensors,
+ * renormalisation slots, control block, FP64 accumulator -- inside one
+ * fixed 8 MiB device array that is part of the library image; it calls no
+ * cudaMalloc, cudaFree or other allocating routine.
  *   Arguments as tn_contract (no mode); the leaves must be device pointers.
  *   Limit: the tree's workspace plus bookkeeping must fit in 8 MiB
  *   (tn_plan_info out[4] is the workspace part); larger trees are refused

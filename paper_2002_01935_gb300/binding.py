@@ -28,10 +28,10 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ETIMEOUT, TN_EUNSUPPORTED = range(6)
 TN_R32, TN_C64 = 0, 1
-TN_MODE_FP32, TN_MODE_TF32_3M, TN_MODE_TF32_SPLIT, TN_MODE_BF16_SPLIT = range(4)
+TN_MODE_FP32, TN_MODE_TF32_3M, TN_MODE_TF32_SPLIT, TN_MODE_BF16_SPLIT, TN_MODE_FP16_SPLIT = range(5)
 TN_MEM_DEVICE, TN_MEM_HOST = 0, 1
 MODES = {"fp32": TN_MODE_FP32, "tf32_3m": TN_MODE_TF32_3M, "tf32_split": TN_MODE_TF32_SPLIT,
-         "bf16_split": TN_MODE_BF16_SPLIT}
+         "bf16_split": TN_MODE_BF16_SPLIT, "fp16_split": TN_MODE_FP16_SPLIT}
 
 
 class tn_options(ctypes.Structure):

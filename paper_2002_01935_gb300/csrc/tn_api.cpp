@@ -145,7 +145,7 @@ static tn_status get_plan(tn_net* net, const int32_t* pairs, int32_t n_sliced, c
     const int n = d.n;
     if (n > 1 && !pairs) return fail(TN_EINVAL, "tree_pairs is NULL");
     if (n_sliced < 0 || (n_sliced > 0 && !sliced)) return fail(TN_EINVAL, "bad sliced labels");
-    if (mode < TN_MODE_FP32 || mode > TN_MODE_BF16_SPLIT) return fail(TN_EINVAL, "bad mode");
+    if (mode < TN_MODE_FP32 || mode > TN_MODE_FP16_SPLIT) return fail(TN_EINVAL, "bad mode");
     std::vector<int32_t> pv(pairs, pairs + 2 * (size_t)(n - 1));
     std::vector<int64_t> sv(sliced, sliced + n_sliced);
     for (auto& p : net->plans)

@@ -146,9 +146,9 @@ struct TcGeom {
     int64_t rows_r;    // rows of R per batch entry
     int64_t cols_q;    // real rows of Q per batch entry
     int64_t kr;        // packed row length (elements) before padding
-    int ke;            // elements per 128-byte row (32 TF32, 64 BF16)
+    int ke;            // elements per 128-byte row (32 TF32, 64 BF16 / FP16)
     int64_t nkb;       // k-blocks (KR padded up to a multiple of ke)
-    int esz;           // bytes per packed element (4 TF32, 2 BF16)
+    int esz;           // bytes per packed element (4 TF32, 2 BF16 / FP16)
     int parts;         // 1, or 2 for hi + lo
     int64_t plane_r;   // bytes of one R plane
     int64_t plane_q;   // bytes of one Q plane
@@ -183,10 +183,20 @@ struct DotPlan {
 };
 
 // Tensor-core precision of a mode (tn_mode values): 0 TF32 single product
-// (4M), 1 TF32 hi+lo, 2 BF16 hi+lo, 3 TF32 single product (3M).
+// (4M), 1 TF32 hi+lo, 2 BF16 hi+lo, 3 TF32 single product (3M), 4 FP16
+// hi+lo (operands scaled by 2^kF16Shift).
 __host__ __device__ inline int tc_prec_of_mode(int mode) {
-    return mode == 3 ? 2 : (mode == 2 ? 1 : (mode == 1 ? 3 : 0));
+    return mode == 4 ? 4 : (mode == 3 ? 2 : (mode == 2 ? 1 : (mode == 1 ? 3 : 0)));
 }
+
+// FP16 operands: after the renormalisation (largest magnitude in [1/2, 1))
+// the pack scales by 2^kF16Shift, so the largest packed magnitude is below
+// 2^15 (FP16's largest finite value is 65504); the GEMM epilogue removes
+// 2^(2 kF16Shift) with the rest of the residual scale.
+constexpr int kF16Shift = 15;
+
+// Bytes per packed element: 2 for the 16-bit formats, 4 for TF32.
+__host__ __device__ inline int tc_esz_of_prec(int prec) { return (prec == 2 || prec == 4) ? 2 : 4; }
 
 // 3M needs a complex node with >= 128 complex columns; otherwise the node
 // runs the single-product 4M form.
@@ -206,7 +216,7 @@ __host__ __device__ inline TcGeom tc_geom(const TileArgs& a, bool cplx, int prec
     g.rows_r = int64_t(1) << (a.tc_swap ? a.nn : a.nm);
     g.cols_q = (int64_t(1) << (a.tc_swap ? a.nm : a.nn)) * c;
     g.kr = (int64_t(1) << a.nk) * c;
-    g.esz = prec == 2 ? 2 : 4;
+    g.esz = tc_esz_of_prec(prec);
     g.ke = 128 / g.esz;
     g.nkb = (g.kr + g.ke - 1) / g.ke;
     g.parts = prec == 0 ? 1 : (prec == 3 ? 3 : 2);
@@ -326,6 +336,11 @@ cudaError_t launch_copy_table(const CopyEntry* tab, int n_entries, int64_t max_n
 // p[i * stride + j] = 0 for i < n, j < count (per-instance scale slots).
 cudaError_t launch_zero_strided(unsigned* p, int64_t count, int64_t stride, int n, cudaStream_t s);
 cudaError_t launch_root_adjoint(const RootAdjArgs& a, int n_inst, cudaStream_t s);
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// cached per device); 152, the GB300 count, when no device is visible (host-only
+// planning, e.g. tn_plan_info on a machine without a GPU).  Grid sizes and
+// K splits are sized in multiples of it.
+int sm_count();
 cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s);
 cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s);  // tn_tiled.cu
 // Tensor-core node (tn_tc.cu): prec as tc_prec_of_mode.

@@ -133,9 +133,28 @@ __global__ void __launch_bounds__(256) k_generic(const __grid_constant__ Generic
     if (a.t_done && threadIdx.x == 0) atomicMax(a.t_done, global_ns());
 }
 
+int sm_count() {
+    constexpr int kMaxDev = 64;
+    static int cache[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (cache[dev] <= 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 152;
+        }
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 cudaError_t launch_generic(const GenericArgs& a, bool is_c, cudaStream_t s) {
     int64_t blocks = (a.n_out + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > sm_count() * 16) blocks = sm_count() * 16;
     if (blocks < 1) blocks = 1;
     const unsigned ni = a.in.n_inst > 1 ? (unsigned)a.in.n_inst : 1u;
     if (is_c)
@@ -226,7 +245,7 @@ __global__ void __launch_bounds__(256) k_accumulate(const __grid_constant__ Accu
 
 cudaError_t launch_accumulate(const AccumArgs& a0, bool is_c, cudaStream_t s, int advance) {
     int64_t blocks = (a0.n_out + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
     if (blocks < 1) blocks = 1;
     AccumArgs a = a0;
     a.advance = blocks == 1 ? advance : 0;  // one block advances the slice counter itself
@@ -358,7 +377,7 @@ __global__ void k_result(const double* acc, int64_t n, const Control* ctl, doubl
 cudaError_t launch_result(const double* acc, int64_t n, const Control* ctl, double* out, int64_t* out_exp,
                           cudaStream_t s) {
     int64_t blocks = (n + 255) / 256;
-    blocks = blocks < 1 ? 1 : (blocks > 152 * 4 ? 152 * 4 : blocks);
+    blocks = blocks < 1 ? 1 : (blocks > sm_count() * 4 ? sm_count() * 4 : blocks);
     k_result<<<(unsigned)blocks, 256, 0, s>>>(acc, n, ctl, out, out_exp);
     return cudaGetLastError();
 }
@@ -421,7 +440,7 @@ cudaError_t launch_leaf_grads(const LeafGradArgs* tab, int n_entries, int64_t ma
                               cudaStream_t s) {
     if (n_entries <= 0) return cudaSuccess;
     int64_t blocks = (max_n + 255) / 256;
-    blocks = blocks < 1 ? 1 : (blocks > 152 * 8 ? 152 * 8 : blocks);
+    blocks = blocks < 1 ? 1 : (blocks > sm_count() * 8 ? sm_count() * 8 : blocks);
     const dim3 grid((unsigned)blocks, (unsigned)n_entries, (unsigned)(n_inst > 1 ? n_inst : 1));
     if (is_c)
         k_leaf_grads<true><<<grid, 256, 0, s>>>(tab, n_entries);
@@ -445,7 +464,7 @@ __global__ void __launch_bounds__(256) k_copy_table(const CopyEntry* tab, int n_
 
 cudaError_t launch_copy_table(const CopyEntry* tab, int n_entries, int64_t max_nfloat, cudaStream_t s) {
     int64_t blocks = (max_nfloat + 255) / 256;
-    blocks = blocks < 1 ? 1 : (blocks > 152 * 4 ? 152 * 4 : blocks);
+    blocks = blocks < 1 ? 1 : (blocks > sm_count() * 4 ? sm_count() * 4 : blocks);
     for (int first = 0; first < n_entries; first += 65535) {  // grid y limit
         const int cnt = n_entries - first < 65535 ? n_entries - first : 65535;
         k_copy_table<<<dim3((unsigned)blocks, (unsigned)cnt), 256, 0, s>>>(tab + first, cnt);
@@ -466,7 +485,7 @@ cudaError_t launch_zero_strided(unsigned* p, int64_t count, int64_t stride, int 
     const int64_t total = count * n;
     if (total <= 0) return cudaSuccess;
     int64_t blocks = (total + 255) / 256;
-    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks > sm_count() * 4) blocks = sm_count() * 4;
     k_zero_strided<<<(unsigned)blocks, 256, 0, s>>>(p, count, stride, n);
     return cudaGetLastError();
 }

@@ -2,11 +2,12 @@
 // device memory.
 //
 // tn_contract keeps a per-plan workspace that it obtains with cudaMalloc the
-// first time a tree is run.  Some callers cannot allow that: code that runs
-// while another component is capturing a CUDA graph (an allocation there
-// either fails or breaks the capture), hosts that must not allocate after
-// start-up (fixed memory budgets, real-time loops), and processes whose
-// device memory belongs to another allocator's pool.  For them this file
+// first time a tree is run.  Some callers cannot allow that: hosts that must
+// not allocate device memory after start-up (fixed memory budgets, real-time
+// loops whose latency an allocation would break), and processes whose device
+// memory is owned by another allocator's pool (a framework's caching
+// allocator, which cudaMalloc calls behind its back would starve).  For them
+// this file
 // offers the same contraction with every piece of scratch -- workspace for
 // the intermediate tensors, node maxima and exponents, leaf maxima, the
 // control block and the FP64 accumulator -- carved out of one fixed array
@@ -17,7 +18,9 @@
 // loads the library, for as long as the process lives.  Calls share it and
 // it keeps the last call's contents; everything a call relies on starting at
 // zero is cleared by the call itself.  Calls whose GPU work overlaps (on
-// different streams, or from several threads) race on the array.
+// different streams, or from several threads) race on the array.  The small
+// per-call tables (leaf pointers and sizes, the unit scalar) travel as kernel
+// parameters, so a call reads no host memory after it has returned.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,6 +74,25 @@ bool scratch_address(void** out, std::string& err) {
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// One chunk of the leaf tables, passed by value as a kernel parameter.
+constexpr int kTableChunk = 128;
+struct LeafTableChunk {
+    int32_t first, count;
+    const void* ptr[kTableChunk];
+    int64_t nfloat[kTableChunk];
+};
+
+__global__ void k_noalloc_tables(const __grid_constant__ LeafTableChunk c, const float** lptr,
+                                 int64_t* lnf, float* unit) {
+    const int i = threadIdx.x;
+    if (i < c.count) {
+        lptr[c.first + i] = static_cast<const float*>(c.ptr[i]);
+        lnf[c.first + i] = c.nfloat[i];
+    }
+    // the scalar 1 that stands in for a missing operand
+    if (c.first == 0 && i < 4) unit[i] = i == 0 ? 1.f : 0.f;
+}
 
 }  // namespace
 
@@ -131,17 +153,21 @@ tn_status run_noalloc(const NetDesc& d, const Plan& p, void* out, int out_mem, i
         }                                                              \
     } while (0)
 
-    // small host tables go up by copies (pageable: staged before return)
-    std::vector<const void*> lp(n);
-    std::vector<int64_t> nf(n);
-    for (int v = 0; v < n; ++v) {
-        lp[v] = d.leaves[v].ptr;
-        nf[v] = d.leaves[v].size * (cplx ? 2 : 1);
+    // the leaf pointer and size tables and the unit scalar, written by
+    // kernels that take them as parameters (no host memory is read later)
+    for (int first = 0; first < n || first == 0; first += kTableChunk) {
+        LeafTableChunk c;
+        memset(&c, 0, sizeof(c));
+        c.first = first;
+        c.count = std::min(kTableChunk, n - first);
+        for (int i = 0; i < c.count; ++i) {
+            c.ptr[i] = d.leaves[first + i].ptr;
+            c.nfloat[i] = d.leaves[first + i].size * (cplx ? 2 : 1);
+        }
+        k_noalloc_tables<<<1, kTableChunk, 0, stream>>>(c, lptr, lnf, static_cast<float*>(unit));
+        CK(cudaGetLastError());
+        if (n == 0) break;
     }
-    static const float kOne[4] = {1.f, 0.f, 0.f, 0.f};
-    CK(cudaMemcpyAsync(lptr, lp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(lnf, nf.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(unit, kOne, sizeof(kOne), cudaMemcpyHostToDevice, stream));
 
     // node arguments, pointing into the scratch
     std::vector<GenericArgs> gen(nn);

@@ -205,7 +205,7 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems, 
         const int64_t tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN) * t.nbatch;
         const int64_t ktiles = (K + TK - 1) / TK;
         int split = 1;
-        while (tiles * p.copies * split < 2 * 152 && split * 16 <= ktiles && split < 64 &&
+        while (tiles * p.copies * split < 2 * sm_count() && split * 16 <= ktiles && split < 64 &&
                t.nbatch * split * 2 <= 65535)
             split *= 2;
         t.split = split;
@@ -1215,14 +1215,14 @@ bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_e
     t.split = 1;
     t.kchunk = int64_t(1) << t.nk;
     const int prec = tc_prec_of_mode(mode);
-    // K split: the grid should fill whole waves of the 152 SMs (one CTA
+    // K split: the grid should fill whole waves of the SMs (one CTA
     // each); split only while every part keeps >= 8 k-blocks
     {
         const TcGeom g0 = tc_geom(t, c, prec);
         const double tiles = (double)t.nbatch * (g0.rows_r / 128) * (g0.cols_q / g0.bn) * copies;
         double best = 0.0;
         for (int s = 1; s <= 16 && g0.nkb / s >= 8; s *= 2) {
-            const double w = tiles * s / 152.0;
+            const double w = tiles * s / (double)sm_count();
             const double eff = w / std::ceil(w);
             if (eff > best + 0.03) {
                 best = eff;

@@ -9,17 +9,21 @@
 //      the write of the packed layout are coalesced; the same pass applies
 //      the slice offset of a sliced leaf, the power-of-two renormalisation,
 //      the complex conjugation of the reverse sweep, the hi/lo split (TF32
-//      round-to-nearest-away, or BF16 round-to-nearest) and, for a complex Q,
+//      round-to-nearest-away, or BF16 / FP16 round-to-nearest; FP16 after a
+//      power-of-two shift into its range) and, for a complex Q,
 //      the expansion into the rows (Re, -Im) and (Im, Re).
-//   3. k_umma: a warp-specialised GEMM.  One thread streams 128-row x
-//      128-byte tiles of R and Q into a ring of shared-memory stages with
-//      TMA (cp.async.bulk.tensor, 128-byte swizzle); one thread issues
-//      tcgen05.mma (kind::tf32, or kind::f16 with BF16 operands) into FP32
-//      accumulators in tensor memory -- hi*hi + hi*lo + lo*hi for the split
-//      precisions -- rotating over up to four accumulators along K, which
-//      the epilogue sums in a fixed order; four epilogue warps read them
-//      with tcgen05.ld, undo the residual scale, reduce the node maximum
-//      and write C in the node's [batch][M][N] layout.
+//   3. k_umma: a warp-specialised GEMM.  One thread streams the packed
+//      16 KB tiles (128 rows x one 128-byte row of K, already laid out in
+//      the 128-byte swizzle the UMMA descriptors expect) into a ring of
+//      shared-memory stages with plain bulk copies (cp.async.bulk on the
+//      TMA engine, one contiguous copy per tile and plane); one thread
+//      issues tcgen05.mma (kind::tf32, or kind::f16 with BF16 or FP16
+//      operands) into FP32 accumulators in tensor memory -- hi*hi + hi*lo +
+//      lo*hi for the split precisions -- rotating over up to four
+//      accumulators along K; four (128-column tiles) or eight (256-column
+//      tiles) epilogue warps drain each finished accumulator with
+//      tcgen05.ld into FP32 registers, undo the residual scale, reduce the
+//      node maximum and write C in the node's [batch][M][N] layout.
 // Complex nodes use one real GEMM with K doubled (4M): R holds interleaved
 // (re, im) pairs along K and Q's expanded rows turn each accumulator column
 // pair into (Re C, Im C).  The larger complex operand plays R (it is not
@@ -29,6 +33,7 @@
 // control block, waits (bounded) for its copies and MMAs in flight, frees
 // its tensor memory and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -60,7 +65,7 @@ constexpr int kPackMaxTile = 1 << (2 * kPackLow);
 // packs of mid-size nodes slower, not faster).
 inline unsigned pack_blocks(int64_t n, int ni) {
     (void)ni;
-    return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), 152 * 8);
+    return (unsigned)std::min<int64_t>(std::max<int64_t>(n / 8192, 1), (int64_t)sm_count() * 8);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -129,10 +134,12 @@ __device__ __forceinline__ uint32_t instr_desc(uint32_t ab_format, int M, int N)
            ((uint32_t)(M >> 4) << 24);
 }
 
-template <bool BF16>
+// HALF: kind::f16 (BF16 or FP16 operands, the format is in idesc);
+// otherwise kind::tf32.
+template <bool HALF>
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
                                     uint32_t accumulate) {
-    if constexpr (BF16) {
+    if constexpr (HALF) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
@@ -263,6 +270,15 @@ struct Parts<2> {
         l = __float2bfloat16_rn(x - __bfloat162float(h));
     }
 };
+// FP16: the pack has already scaled x by 2^kF16Shift (|x| < 2^15)
+template <>
+struct Parts<4> {
+    using E = __half;
+    static __device__ __forceinline__ void split(float x, E& h, E& l) {
+        h = __float2half_rn(x);
+        l = __float2half_rn(x - __half2float(h));
+    }
+};
 
 // 16-byte chunk position of (row, chunk) in a 128B-swizzled K-major tile
 // (the layout of a TMA 128-byte swizzle and of the UMMA descriptors below).
@@ -292,6 +308,11 @@ __device__ __forceinline__ void put2(char* hi, int64_t lo_off, int64_t pos, floa
         h.x = hx; h.y = hy; l.x = lx; l.y = ly;
         *reinterpret_cast<__nv_bfloat162*>(hi + pos) = h;
         *reinterpret_cast<__nv_bfloat162*>(hi + lo_off + pos) = l;
+    } else if constexpr (PREC == 4) {
+        __half2 h, l;
+        h.x = hx; h.y = hy; l.x = lx; l.y = ly;
+        *reinterpret_cast<__half2*>(hi + pos) = h;
+        *reinterpret_cast<__half2*>(hi + lo_off + pos) = l;
     } else {
         *reinterpret_cast<float2*>(hi + pos) = make_float2(hx, hy);
         if constexpr (PREC == 1) *reinterpret_cast<float2*>(hi + lo_off + pos) = make_float2(lx, ly);
@@ -343,7 +364,7 @@ __global__ void __launch_bounds__(kPackThreads)
     if (slice >= a.ctl->slice_end) return;
     const int nk = a.nk;
     const TcGeom geo = tc_geom(a, CPLX, PREC);
-    constexpr int LG_ESZ = PREC == 2 ? 1 : 2, LG_KE = 7 - LG_ESZ;
+    constexpr int LG_ESZ = (PREC == 2 || PREC == 4) ? 1 : 2, LG_KE = 7 - LG_ESZ;
     const int ESZ = CPLX ? 8 : 4;
     const T* src = reinterpret_cast<const T*>(useB ? a.B : a.A) +
                    (int64_t)inst * (useB ? in.b_is : in.a_is) +
@@ -354,7 +375,7 @@ __global__ void __launch_bounds__(kPackThreads)
     const unsigned* mslot = useB ? a.sc.max_b : a.sc.max_a;
     if (mslot) mslot += (int64_t)inst * (useB ? in.sb_is : in.sa_is);
     const int e = exp_of(mslot);
-    const float f = ldexpf(1.f, -max(-120, min(120, e)));
+    const float f = ldexpf(1.f, -max(-120, min(120, e)) + (PREC == 4 ? kF16Shift : 0));
     const bool conj = useB ? a.conj_b : a.conj_a;
 
     // the tile tables: source offset of each source-order index, packed
@@ -472,17 +493,17 @@ __global__ void __launch_bounds__(kPackThreads)
 template <bool CPLX, int PREC, int STAGES, int BN>
 __global__ void __launch_bounds__(64 + BN, 1)
     k_umma(const __grid_constant__ TileArgs a, int nacc) {
-    constexpr bool BF16 = PREC == 2;
+    constexpr bool HALF = PREC == 2 || PREC == 4;   // 16-bit operands, kind::f16
     constexpr bool SPLIT = PREC != 0;
     constexpr int PARTS = SPLIT ? 2 : 1;
     constexpr int QB = BN * kRowBytes;                    // one Q part per stage
     constexpr int QT = BN / kBM;                           // packed 128-row Q tiles per part
     constexpr int EPI_WARPS = BN / 32;                     // 128 rows x BN columns, 128 each
     constexpr int STAGE_BYTES = PARTS * (kTileBytes + QB);
-    constexpr int KE = BF16 ? 64 : 32;     // packed elements per 128-byte row
-    constexpr int MMA_K = BF16 ? 16 : 8;   // K per instruction
+    constexpr int KE = HALF ? 64 : 32;     // packed elements per 128-byte row
+    constexpr int MMA_K = HALF ? 16 : 8;   // K per instruction
     constexpr int KSTEPS = KE / MMA_K;
-    constexpr uint32_t FMT = BF16 ? 1u : 2u;
+    constexpr uint32_t FMT = PREC == 2 ? 1u : (PREC == 4 ? 0u : 2u);  // BF16, FP16, TF32
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -536,7 +557,8 @@ __global__ void __launch_bounds__(64 + BN, 1)
     sio.max_c += (int64_t)inst * in.sc_is;
     sio.exp_c += (int64_t)inst * in.sc_is;
     const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
-    const int resid = (eA - max(-120, min(120, eA))) + (eB - max(-120, min(120, eB)));
+    const int resid = (eA - max(-120, min(120, eA))) + (eB - max(-120, min(120, eB))) +
+                      (PREC == 4 ? 2 * kF16Shift : 0);
     if (blockIdx.x == 0 && sp == 0 && b == 0 && tid == 0 && sio.exp_c)
         *sio.exp_c = (sio.exp_a ? *sio.exp_a : 0) + (sio.exp_b ? *sio.exp_b : 0) + eA + eB;
 
@@ -627,12 +649,12 @@ __global__ void __launch_bounds__(64 + BN, 1)
                 const uint32_t d = tmem + (uint32_t)(q * BN);
 #pragma unroll
                 for (int k = 0; k < KSTEPS; ++k) {
-                    const uint32_t off = k * MMA_K * (BF16 ? 2 : 4);
+                    const uint32_t off = k * MMA_K * (HALF ? 2 : 4);
                     const uint32_t acc0 = (!first || k > 0) ? 1u : 0u;
-                    mma<BF16>(d, smem_desc(r_hi + off), smem_desc(q_hi + off), idesc, acc0);
+                    mma<HALF>(d, smem_desc(r_hi + off), smem_desc(q_hi + off), idesc, acc0);
                     if constexpr (SPLIT) {
-                        mma<BF16>(d, smem_desc(r_hi + off), smem_desc(q_lo + off), idesc, 1u);
-                        mma<BF16>(d, smem_desc(r_lo + off), smem_desc(q_hi + off), idesc, 1u);
+                        mma<HALF>(d, smem_desc(r_hi + off), smem_desc(q_lo + off), idesc, 1u);
+                        mma<HALF>(d, smem_desc(r_lo + off), smem_desc(q_hi + off), idesc, 1u);
                     }
                 }
                 mma_commit(&empty_bar[s]);
@@ -947,7 +969,8 @@ __global__ void __launch_bounds__(256) k_tc_reduce(const __grid_constant__ TileA
     if (sio.max_b) sio.max_b += (int64_t)inst * in.sb_is;
     sio.max_c += (int64_t)inst * in.sc_is;
     const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
-    const int resid = (eA - max(-120, min(120, eA))) + (eB - max(-120, min(120, eB)));
+    const int resid = (eA - max(-120, min(120, eA))) + (eB - max(-120, min(120, eB))) +
+                      (PREC == 4 ? 2 * kF16Shift : 0);
     float lmax = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
         float4 s = P[i];
@@ -1063,7 +1086,7 @@ cudaError_t launch_tc_3m(const TileArgs& a, cudaStream_t s) {
     k_umma3m<STAGES><<<dim3((unsigned)tiles, (unsigned)split, (unsigned)(a.nbatch * ni)), kGemmThreads, SMEM, s>>>(a);
     if (split > 1) {
         const int64_t n4 = (a.nbatch << (a.nm + a.nn)) * 2 / 4;
-        const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>((n4 + 255) / 256, 1), 152 * 8);
+        const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>((n4 + 255) / 256, 1), (int64_t)sm_count() * 8);
         k_tc_reduce<true, 3><<<dim3(nb, ni), 256, 0, s>>>(a);
     }
     return cudaGetLastError();
@@ -1113,7 +1136,7 @@ cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (split > 1) {
         const int64_t n4 = (a.nbatch << (a.nm + a.nn)) * (CPLX ? 2 : 1) / 4;
-        const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>((n4 + 255) / 256, 1), 152 * 8);
+        const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>((n4 + 255) / 256, 1), (int64_t)sm_count() * 8);
         k_tc_reduce<CPLX, PREC><<<dim3(nb, ni), 256, 0, s>>>(a);
     }
     return cudaGetLastError();
@@ -1127,10 +1150,12 @@ cudaError_t launch_tc(const TileArgs& a, int prec, bool is_c, cudaStream_t s) {
     if (is_c) {
         if (prec == 0) return launch_tc_t<true, 0>(a, s);
         if (prec == 1) return launch_tc_t<true, 1>(a, s);
+        if (prec == 4) return launch_tc_t<true, 4>(a, s);
         return launch_tc_t<true, 2>(a, s);
     }
     if (prec == 0) return launch_tc_t<false, 0>(a, s);
     if (prec == 1) return launch_tc_t<false, 1>(a, s);
+    if (prec == 4) return launch_tc_t<false, 4>(a, s);
     return launch_tc_t<false, 2>(a, s);
 }
 

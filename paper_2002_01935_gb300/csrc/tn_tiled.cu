@@ -839,9 +839,9 @@ static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
     // same order however many run side by side (results independent of the
     // slice batch)
     int G = 1;
-    while (G < 32 && G * 2 <= a.split && n * G < (int64_t)152 * 256 * 4) G *= 2;
+    while (G < 32 && G * 2 <= a.split && n * G < (int64_t)sm_count() * 256 * 4) G *= 2;
     int64_t blocks = (n + 256 / G - 1) / (256 / G);
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
     k_split_reduce<CPLX><<<dim3((unsigned)blocks, (unsigned)ni), 256, 0, s>>>(a, G);
     return cudaGetLastError();
 }
@@ -855,7 +855,7 @@ cudaError_t launch_wave(const WaveItem* items, int n_items, const TileArgs* desc
                         unsigned* done, unsigned* head, int G) {
     if (n_items <= 0) return cudaSuccess;
     // dataflow: persistent CTAs (all resident: 8 per SM fit), else one per item
-    const int grid = deps ? std::min(n_items, 152 * 8) : n_items;
+    const int grid = deps ? std::min(n_items, sm_count() * 8) : n_items;
     if (is_c)
         k_wave<true><<<grid, 256, 0, s>>>(items, n_items, descs, leaf_ptrs, deps, done, head, G);
     else

@@ -94,6 +94,16 @@ class Network:
     def with_tensors(self, tensors: Sequence[np.ndarray]) -> "Network":
         return dataclasses.replace(self, tensors=list(tensors))
 
+    def as_stored(self) -> "Network":
+        """The same network with every entry rounded to the storage type of
+        the GPU leaves (complex64, or float32 for a real network) and
+        widened back to complex128 / float64: the exact values a device
+        contraction reads, so that a reference computed on them compares
+        arithmetic with arithmetic, without the rounding of the inputs."""
+        cplx = self.is_complex
+        narrow, wide = (np.complex64, np.complex128) if cplx else (np.float32, np.float64)
+        return self.with_tensors([np.asarray(t).astype(narrow).astype(wide) for t in self.tensors])
+
 
 # ---------------------------------------------------------------------------
 # Random quantum circuits (Sec. 4.6)

@@ -2,9 +2,12 @@
 
 Large nodes run on tcgen05 tensor cores in the reduced-precision modes:
 TF32 single pass, TF32 hi+lo split and BF16 hi+lo split (three products,
-FP32 accumulation).  Tolerances (relative to the cancellation-free scale,
-i.e. the same contraction on |A|, |B|): 1e-5 for the TF32 split, 1e-4 for
-the BF16 split, 2e-3 for a single TF32 pass (10-bit mantissa).
+FP32 accumulation) and FP16 hi+lo split.  Single nodes: tolerances
+relative to the cancellation-free scale of each entry (the same contraction
+on |A|, |B|): 1e-5 for the TF32 and FP16 splits, 1e-4 for the BF16 split,
+2e-3 for a single TF32 pass (10-bit mantissa).  Whole networks: relative
+error of the value against the oracle run on the leaf values the GPU reads
+(complex64 / float32), at the mode's bound (1e-2 for the single pass).
 """
 import math
 
@@ -16,7 +19,8 @@ from paper_2002_01935_gb300 import inputs, planner
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"tf32_split": 1e-5, "bf16_split": 1e-4, "tf32_3m": 2e-3, "fp32": 1e-5}
+TOL = {"tf32_split": 1e-5, "fp16_split": 1e-5, "bf16_split": 1e-4, "tf32_3m": 2e-3, "fp32": 1e-5}
+NET_TOL = dict(TOL, tf32_3m=1e-2)
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +71,7 @@ def gemm_net(mb, nb, kb, batch=0, cplx=True, seed=0, interleave=True):
     return inputs.Network([ta, tb], [la, lb], dims, bl + ml + nl)
 
 
-@pytest.mark.parametrize("mode", ["tf32_split", "bf16_split", "tf32_3m"])
+@pytest.mark.parametrize("mode", ["tf32_split", "fp16_split", "bf16_split", "tf32_3m"])
 @pytest.mark.parametrize("shape", [(8, 8, 8, 0, True), (7, 9, 6, 0, False), (9, 7, 10, 0, True),
                                    (7, 7, 4, 1, True), (8, 8, 7, 0, False), (7, 8, 3, 0, True),
                                    (6, 9, 5, 0, True), (6, 10, 6, 1, True), (10, 6, 5, 0, True),
@@ -90,29 +94,28 @@ def test_single_gemm_node(torch, mode, shape):
     assert err <= TOL[mode], err
 
 
-@pytest.mark.parametrize("mode", ["tf32_split", "bf16_split", "tf32_3m"])
+@pytest.mark.parametrize("mode", ["tf32_split", "fp16_split", "bf16_split", "tf32_3m"])
 def test_cfg1_ising_modes(torch, mode):
     net = inputs.random_ising(100, seed=0)
     pairs = planner.greedy_tree(net.labels, net.dims, net.open)
     m, e, info = run(torch, net, pairs, mode=mode)
     assert info["n_tensor_core"] >= 1
-    mo, eo = tree.contract_net(net, pairs)
+    mo, eo = tree.contract_net(net.as_stored(), pairs)
     d = math.log(float(m)) + e * math.log(2) - (math.log(float(mo)) + eo * math.log(2))
-    assert abs(math.expm1(d)) <= TOL[mode], d
+    assert abs(math.expm1(d)) <= NET_TOL[mode], d
 
 
-@pytest.mark.parametrize("mode", ["tf32_split", "bf16_split", "tf32_3m"])
+@pytest.mark.parametrize("mode", ["fp32", "tf32_split", "fp16_split", "bf16_split", "tf32_3m"])
 def test_circuit_5x5_modes(torch, mode):
     """Complex 4M on the tensor cores over a whole circuit network; the
-    amplitude's error against the FP64 oracle is within the mode's bound."""
+    amplitude's error against the FP64 oracle (run on the complex64 leaf
+    values the GPU reads) is within the mode's bound."""
     circ = inputs.random_circuit(5, 5, 10, seed=0)
     net = inputs.circuit_network(circ, inputs.random_bitstrings(25, 1, seed=1000)[0])
     pairs = planner.greedy_tree(net.labels, net.dims, net.open)
     m, e, info = run(torch, net, pairs, mode=mode)
-    assert info["n_tensor_core"] >= 1
-    mo, eo = tree.contract_net(net, pairs)
+    assert (info["n_tensor_core"] >= 1) == (mode != "fp32")
+    mo, eo = tree.contract_net(net.as_stored(), pairs)
     ref = complex(mo) * 2.0 ** eo
     err = abs(complex(m) * 2.0 ** e - ref) / abs(ref)
-    # the amplitude (~2^-12.5) results from heavy cancellation: allow a
-    # growth factor of 10 over the per-contraction bound
-    assert err <= 10 * TOL[mode], err
+    assert err <= NET_TOL[mode], err

@@ -1,13 +1,17 @@
 """tn_contract_noalloc: the contraction for callers that cannot allocate
-device memory (graph-capturing code, allocation-free hosts, processes whose
-device memory belongs to another allocator).  Its results must match
-tn_contract's, on consecutive calls that reuse the shared fixed scratch,
-and trees too large for the scratch must be refused with a clear error.
+device memory (hosts that forbid device allocation after start-up, and
+processes whose device memory is owned by another allocator's pool).  Its
+results must match tn_contract's and the FP64 oracle's (run on the leaf
+values the GPU reads), on consecutive calls that reuse the shared fixed
+scratch -- including the first call on a fresh handle, a single-leaf network
+and a sliced tree with open outputs -- and trees too large for the scratch
+must be refused with a clear error.
 Collected last so a stop-at-first-failure run has executed every other test.
 """
 import numpy as np
 import pytest
 
+from oracle import tree
 from paper_2002_01935_gb300 import inputs, planner
 
 pytestmark = pytest.mark.gpu
@@ -31,12 +35,28 @@ def _leaves(torch, net):
     return [torch.from_numpy(np.array(t, order="C")).to(dt).contiguous().cuda() for t in net.tensors]
 
 
+def _oracle(net, pairs, sliced=()):
+    m, e = tree.contract_net(net.as_stored(), pairs, sliced)
+    return m * 2.0 ** e
+
+
+def _noalloc_device(torch, binding, tnw, pairs, sliced, cplx):
+    odt = torch.complex128 if cplx else torch.float64
+    out = torch.full(tnw.out_shape, 7.0, dtype=odt, device="cuda")
+    oe = torch.full((), 99, dtype=torch.int64, device="cuda")
+    binding.tn_contract_noalloc(tnw.h, pairs, sliced, out.data_ptr(), binding.TN_MEM_DEVICE,
+                                oe.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy() * 2.0 ** int(oe.cpu())
+
+
 def test_noalloc_matches_tn_contract_on_two_calls(env):
     torch, binding = env
     circ = inputs.random_circuit(4, 4, 8, seed=0)
     net = inputs.circuit_network(circ, inputs.random_bitstrings(16, 1, seed=1000)[0])
     pairs = planner.greedy_tree(net.labels, net.dims, net.open)
     sliced = planner.slice_greedy(net.labels, net.dims, pairs, net.open, 10)
+    oref = complex(_oracle(net, pairs, sliced))
     ts = _leaves(torch, net)
     tnw = binding.TensorNetwork(net.labels, net.dims, net.open, ts, complex_=True)
     try:
@@ -52,6 +72,7 @@ def test_noalloc_matches_tn_contract_on_two_calls(env):
             torch.cuda.synchronize()
             got = complex(out.cpu()) * 2.0 ** int(oe.cpu())
             assert abs(got - ref) <= TOL * abs(ref), (call, got, ref)
+            assert abs(got - oref) <= TOL * abs(oref), (call, got, oref)
     finally:
         tnw.close()
 
@@ -61,6 +82,7 @@ def test_noalloc_open_outputs_to_host(env):
     circ = inputs.random_circuit(3, 3, 5, seed=2)
     net = inputs.circuit_network(circ, open_qubits=[2, 0, 1, 3, 4, 5, 6, 7, 8])
     pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    oref = _oracle(net, pairs)
     ts = _leaves(torch, net)
     tnw = binding.TensorNetwork(net.labels, net.dims, net.open, ts, complex_=True)
     try:
@@ -74,6 +96,7 @@ def test_noalloc_open_outputs_to_host(env):
                                         oe.data_ptr(), torch.cuda.current_stream().cuda_stream)
             got = out.numpy() * 2.0 ** int(oe)
             assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref)
+            assert np.linalg.norm(got - oref) <= TOL * np.linalg.norm(oref)
     finally:
         tnw.close()
 
@@ -92,5 +115,63 @@ def test_noalloc_refuses_trees_beyond_the_scratch(env):
                                         oe.data_ptr(), torch.cuda.current_stream().cuda_stream)
         assert err.value.status == binding.TN_EUNSUPPORTED
         assert "8 MiB" in str(err.value)
+    finally:
+        tnw.close()
+
+
+def test_noalloc_first_call_on_fresh_handle_sliced_open_outputs(env):
+    """No tn_contract before: the handle's plan has never been run, so the
+    call cannot lean on a workspace or device state tn_contract made."""
+    torch, binding = env
+    circ = inputs.random_circuit(3, 3, 6, seed=4)
+    net = inputs.circuit_network(circ, inputs.random_bitstrings(9, 1, seed=1004)[0],
+                                 open_qubits=[4, 1, 7])
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    sliced = planner.slice_greedy(net.labels, net.dims, pairs, net.open, 6)
+    assert sliced
+    ref = _oracle(net, pairs, sliced)
+    tnw = binding.TensorNetwork(net.labels, net.dims, net.open, _leaves(torch, net), complex_=True)
+    try:
+        for call in range(2):
+            got = _noalloc_device(torch, binding, tnw, pairs, sliced, True)
+            assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), call
+        m, e = tnw.contract(pairs, sliced, "fp32")
+        torch.cuda.synchronize()
+        again = m.cpu().numpy() * 2.0 ** int(e.cpu())
+        assert np.linalg.norm(again - got) <= TOL * np.linalg.norm(ref)
+    finally:
+        tnw.close()
+
+
+@pytest.mark.parametrize("open_labels", [[0, 2], []])
+def test_noalloc_single_leaf(env, open_labels):
+    """One tensor and no pairs: its summed label is contracted against the
+    scratch's own unit scalar."""
+    torch, binding = env
+    rng = np.random.default_rng(9)
+    t = rng.standard_normal((2, 4, 2)) + 1j * rng.standard_normal((2, 4, 2))
+    net = inputs.Network([t], [[0, 1, 2]], {0: 2, 1: 4, 2: 2}, list(open_labels))
+    ref = _oracle(net, [])
+    tnw = binding.TensorNetwork(net.labels, net.dims, net.open, _leaves(torch, net), complex_=True)
+    try:
+        for call in range(2):
+            got = _noalloc_device(torch, binding, tnw, [], [], True)
+            assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), call
+    finally:
+        tnw.close()
+
+
+def test_noalloc_real_network_against_oracle(env):
+    torch, binding = env
+    net = inputs.random_ising(16, seed=3)
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    sliced = planner.slice_greedy(net.labels, net.dims, pairs, net.open, 3)
+    assert sliced
+    ref = float(_oracle(net, pairs, sliced))
+    tnw = binding.TensorNetwork(net.labels, net.dims, net.open, _leaves(torch, net), complex_=False)
+    try:
+        for call in range(2):
+            got = float(_noalloc_device(torch, binding, tnw, pairs, sliced, False))
+            assert abs(got - ref) <= TOL * abs(ref), (call, got, ref)
     finally:
         tnw.close()
