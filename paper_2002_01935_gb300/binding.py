@@ -196,17 +196,20 @@ def _tree(pairs):
     if not isinstance(pairs, list):
         return _arr([x for p in pairs for x in p] or [0], np.int32)
     hit = _tree_cache.get(id(pairs))
-    if hit is not None:
+    if hit is not None and len(hit[0]) == len(pairs):
+        # element by element, so that a list of lists (e.g. pairs read from
+        # JSON) or of numpy rows is reused like a list of tuples
         try:
-            same = bool(hit[0] == pairs)
-        except ValueError:  # e.g. pairs given as numpy rows: not comparable, no reuse
+            same = all(len(p) == 2 and int(p[0]) == q[0] and int(p[1]) == q[1]
+                       for p, q in zip(pairs, hit[0]))
+        except (TypeError, ValueError):
             same = False
         if same:
             return hit[1]
     arr = _arr([x for p in pairs for x in p] or [0], np.int32)
     if len(_tree_cache) >= 64:
         _tree_cache.clear()
-    _tree_cache[id(pairs)] = ([tuple(p) for p in pairs], arr)
+    _tree_cache[id(pairs)] = ([(int(p[0]), int(p[1])) for p in pairs], arr)
     return arr
 
 

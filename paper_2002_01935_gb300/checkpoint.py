@@ -56,9 +56,23 @@ def fold(partials) -> Tuple[np.ndarray, int]:
     return acc, e_max
 
 
+def _fsync_dir(path: str) -> None:
+    try:
+        fd = os.open(path, os.O_RDONLY)
+    except OSError:
+        return
+    try:
+        os.fsync(fd)
+    except OSError:
+        pass
+    finally:
+        os.close(fd)
+
+
 class SliceCheckpoint:
     """The finished blocks of one sliced contraction, kept in the directory
-    ``path``: ``meta.json`` names the problem, and each finished block is one
+    ``path``: ``meta.json`` names the problem (and, once a block is recorded,
+    the partials' shape), and each finished block is one
     small ``block_<i>.npz`` written atomically (a rename), so recording costs
     the same for the first block and the ten-thousandth.  ``key`` names the
     problem (network, tree, sliced labels, mode): a directory written for
@@ -68,30 +82,67 @@ class SliceCheckpoint:
         import json
         self.path, self.key, self.d_sliced, self.block = path, str(key), int(d_sliced), int(block)
         self.done: dict = {}  # block index -> (mantissa, exp2)
+        self.shape = None     # mantissa shape, recorded with the first block
         meta = {"key": self.key, "d_sliced": self.d_sliced, "block": self.block}
-        mpath = os.path.join(path, "meta.json")
+        self._mpath = mpath = os.path.join(path, "meta.json")
         if os.path.exists(mpath):
             with open(mpath) as f:
                 have = json.load(f)
+            shape = have.pop("shape", None)
             if have != meta:
                 raise ValueError(f"checkpoint {path} belongs to {have}, not {meta}")
-            for name in os.listdir(path):
-                if name.startswith("block_") and name.endswith(".npz"):
+            self.shape = tuple(shape) if shape is not None else None
+            n_blocks = len(blocks(self.d_sliced, self.block))
+            for name in sorted(os.listdir(path)):
+                if not (name.startswith("block_") and name.endswith(".npz")):
+                    continue
+                # a damaged or foreign file counts as a missing block: that
+                # block is contracted again instead of failing the run
+                try:
                     with np.load(os.path.join(path, name), allow_pickle=False) as z:
-                        self.done[int(z["index"])] = (np.array(z["mantissa"]), int(z["exp2"]))
+                        idx, m, e = int(z["index"]), np.array(z["mantissa"]), int(z["exp2"])
+                except Exception:
+                    continue
+                if not (0 <= idx < n_blocks) or name != f"block_{idx}.npz":
+                    continue
+                if self.shape is None or m.shape != self.shape:
+                    continue
+                self.done[idx] = (m, e)
         else:
             os.makedirs(path, exist_ok=True)
-            tmp = mpath + ".tmp"
-            with open(tmp, "w") as f:
-                json.dump(meta, f)
-            os.replace(tmp, mpath)
+            self._write_meta(meta)
+        self._meta = meta
+
+    def _write_meta(self, meta: dict) -> None:
+        import json
+        tmp = self._mpath + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(meta, f)
+            f.flush()
+            os.fsync(f.fileno())
+        os.replace(tmp, self._mpath)
+        _fsync_dir(self.path)
 
     def record(self, index: int, mantissa, exp2: int) -> None:
-        self.done[int(index)] = (np.array(mantissa), int(exp2))
+        m = np.array(mantissa)
+        if self.shape is None:
+            # the first recorded block fixes the partials' shape; files of
+            # another shape found later are not this problem's
+            self.shape = m.shape
+            self._write_meta(dict(self._meta, shape=list(m.shape)))
+        elif m.shape != self.shape:
+            raise ValueError(f"block {index}: mantissa shape {m.shape}, expected {self.shape}")
+        self.done[int(index)] = (m, int(exp2))
         final = os.path.join(self.path, f"block_{int(index)}.npz")
         tmp = os.path.join(self.path, f"tmp_{int(index)}.npz")
-        np.savez(tmp, index=np.array(int(index)), mantissa=np.array(mantissa), exp2=np.array(int(exp2)))
+        # written, flushed to the disk, then renamed (and the rename made
+        # durable): a crash leaves either no file or a complete one
+        with open(tmp, "wb") as f:
+            np.savez(f, index=np.array(int(index)), mantissa=np.array(mantissa), exp2=np.array(int(exp2)))
+            f.flush()
+            os.fsync(f.fileno())
         os.replace(tmp, final)
+        _fsync_dir(self.path)
 
 
 def run(contract_block: Callable[[int, int], Tuple[np.ndarray, int]], d_sliced: int, block: int,

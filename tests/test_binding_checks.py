@@ -85,7 +85,9 @@ def test_flattened_trees_follow_the_pair_list():
     pairs[1] = (3, 2)
     assert binding._tree(pairs).tolist() == [0, 1, 3, 2, 4, 5]
     lol = [[0, 1], [2, 3]]
-    assert binding._tree(lol).tolist() == [0, 1, 2, 3]
+    b = binding._tree(lol)
+    assert b.tolist() == [0, 1, 2, 3]
+    assert binding._tree(lol) is b  # a list of lists is reused too
     lol[0][1] = 9
     assert binding._tree(lol).tolist() == [0, 9, 2, 3]
     assert binding._tree(np.array([[1, 0]])).tolist() == [1, 0]

@@ -96,3 +96,24 @@ def test_each_block_is_its_own_file(tmp_path):
     checkpoint.run(_oracle_block(net, pairs, sliced), d, 3, path, "case")
     names = set(os.listdir(path))
     assert names == {"meta.json"} | {f"block_{i}.npz" for i in range(len(checkpoint.blocks(d, 3)))}
+
+
+def test_damaged_or_foreign_block_files_are_recomputed(tmp_path):
+    """A truncated block file, one whose index lies outside the slice range,
+    and one whose mantissa has another shape are treated as missing blocks:
+    the resumed run contracts those blocks again and gives the same result."""
+    import os
+    net, pairs, sliced, d = _case(False)
+    ref = checkpoint.run(_oracle_block(net, pairs, sliced), d, 3, str(tmp_path / "ref"), "case")
+    path = str(tmp_path / "ck")
+    checkpoint.run(_oracle_block(net, pairs, sliced), d, 3, path, "case")
+    n = len(checkpoint.blocks(d, 3))
+    with open(os.path.join(path, "block_1.npz"), "r+b") as f:
+        f.truncate(20)
+    np.savez(os.path.join(path, "block_2.npz"), index=np.array(n + 5), mantissa=np.array(1.0),
+             exp2=np.array(0))
+    np.savez(os.path.join(path, "block_0.npz"), index=np.array(0), mantissa=np.ones(3), exp2=np.array(0))
+    again = []
+    got = checkpoint.run(_oracle_block(net, pairs, sliced, again), d, 3, path, "case")
+    assert sorted(again) == [checkpoint.blocks(d, 3)[i] for i in (0, 1, 2)]
+    assert got[1] == ref[1] and np.array_equal(got[0], ref[0])

@@ -162,3 +162,65 @@ def test_cfg3_fsim_parameter_gradients(torch):
             p_minus[which][i] -= h
             fd = (loss_sv(*p_plus) - loss_sv(*p_minus)) / (2 * h)
             assert abs(gvec[i] - fd) <= 2e-3 * scale, (i, which, gvec[i], fd)
+
+
+def _fsim_stack(torch, theta, phi):
+    n = theta.shape[0]
+    c, s = torch.cos(theta).to(torch.complex128), torch.sin(theta).to(torch.complex128)
+    g = torch.zeros((n, 4, 4), dtype=torch.complex128, device=theta.device)
+    g[:, 0, 0] = 1
+    g[:, 1, 1] = c
+    g[:, 2, 2] = c
+    g[:, 1, 2] = -1j * s
+    g[:, 2, 1] = -1j * s
+    g[:, 3, 3] = torch.exp(-1j * phi.to(torch.complex128))
+    return g.to(torch.complex64).reshape(n, 2, 2, 2, 2)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "tf32_split", "fp16_split"])
+def test_cfg3_all_fsim_gradients_against_adjoint_state(torch, mode):
+    """All 186 fSim parameters of the 5x4, 12-cycle circuit, L = mean over
+    64 seeded bitstrings of ln|c_x|^2, through the batched autograd Function
+    (one forward for the 64 copies, one reverse sweep): the gradient vector
+    against the state-vector adjoint gradient of the same L (gates as the
+    GPU reads them, complex64; their derivatives exact), norm-relative."""
+    from paper_2002_01935_gb300 import autograd, binding
+    R, C, T = 5, 4, 12
+    circ = inputs.random_circuit(R, C, T, seed=0)
+    bits = inputs.random_bitstrings(R * C, 64, seed=1000)
+    fs = circ.fsim_gates()
+    nets = [inputs.circuit_network(circ, b) for b in bits]
+    net0 = nets[0]
+    pairs = planner.greedy_tree(net0.labels, net0.dims, net0.open)
+    n = net0.n_tensors
+    first_out = n - R * C
+    base = [torch.from_numpy(np.array(t, order="C")).to(torch.complex64).cuda() for t in net0.tensors]
+    outs = torch.stack([torch.stack([torch.from_numpy(np.array(nt.tensors[v], order="C")).to(torch.complex64)
+                                     for v in range(first_out, n)]) for nt in nets]).cuda()
+    batch = {first_out + q: outs[:, q].contiguous() for q in range(R * C)}
+    leaf_of = [net0.meta["gate_leaf"][g] for g in fs]
+    theta = torch.tensor([circ.gates[g].params[0] for g in fs], dtype=torch.float64, device="cuda",
+                         requires_grad=True)
+    phi = torch.tensor([circ.gates[g].params[1] for g in fs], dtype=torch.float64, device="cuda",
+                       requires_grad=True)
+    tnw = binding.TensorNetwork(net0.labels, net0.dims, net0.open, base, complex_=True)
+    try:
+        G = _fsim_stack(torch, theta, phi)
+        leaves = list(base)
+        for i, v in enumerate(leaf_of):
+            leaves[v] = G[i]
+        vals = autograd.contract_batch(tnw, pairs, mode, leaves[:first_out] + [None] * (R * C), batch)
+        loss = torch.mean(torch.log(torch.abs(vals) ** 2))
+        loss.backward()
+        got = np.concatenate([theta.grad.cpu().numpy(), phi.grad.cpu().numpy()])
+        got_loss = float(loss.detach().cpu())
+    finally:
+        tnw.close()
+    gates = [inputs.Gate(g.name, g.qubits, np.asarray(g.matrix).astype(np.complex64).astype(np.complex128),
+                         g.params) for g in circ.gates]
+    dg = {g: list(statevector.fsim_derivatives(*circ.gates[g].params)) for g in fs}
+    L, grads = statevector.mean_log_prob_grad(R * C, gates, bits, dg)
+    ref = np.concatenate([[grads[g][0] for g in fs], [grads[g][1] for g in fs]])
+    assert abs(got_loss - L) <= 1e-5 * abs(L)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= 1e-5, err

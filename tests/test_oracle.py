@@ -451,3 +451,47 @@ def test_environments_give_the_ising_energy(n, seed):
     h = 1e-4
     fd = (ising.log_z_enumerate(n, edges, J, beta + h) - ising.log_z_enumerate(n, edges, J, beta - h)) / (2 * h)
     assert abs(dz / z - fd) <= 1e-6 * max(abs(fd), 1.0)
+
+
+# --------------------------------------------------------------------------
+# loss gradient of the differentiation workload (state-vector adjoint)
+# --------------------------------------------------------------------------
+
+def test_fsim_derivatives_match_finite_differences():
+    h = 1e-6
+    for theta, phi in [(0.3, 1.1), (1.2, 2.9), (0.0, 0.0)]:
+        dt, dp = statevector.fsim_derivatives(theta, phi)
+        fd_t = (inputs.fsim(theta + h, phi) - inputs.fsim(theta - h, phi)) / (2 * h)
+        fd_p = (inputs.fsim(theta, phi + h) - inputs.fsim(theta, phi - h)) / (2 * h)
+        assert np.max(np.abs(dt - fd_t)) < 1e-9
+        assert np.max(np.abs(dp - fd_p)) < 1e-9
+
+
+def test_mean_log_prob_grad_matches_finite_differences():
+    """Every fSim (theta, phi) of a 3x3, 5-cycle circuit: the adjoint-state
+    gradient of L = mean ln|c_x|^2 against central differences of L computed
+    by plain forward simulation."""
+    circ = inputs.random_circuit(3, 3, 5, seed=6)
+    bits = inputs.random_bitstrings(9, 5, seed=1006)
+    fs = circ.fsim_gates()
+    dg = {g: list(statevector.fsim_derivatives(*circ.gates[g].params)) for g in fs}
+    L, grads = statevector.mean_log_prob_grad(9, circ.gates, bits, dg)
+
+    def loss(gates):
+        psi = statevector.final_state(9, gates)
+        return float(np.mean([math.log(abs(psi[tuple(int(b) for b in x)]) ** 2) for x in bits]))
+
+    assert abs(L - loss(circ.gates)) < 1e-12
+    h = 1e-5
+    for g in fs:
+        th, ph = circ.gates[g].params
+        for which in (0, 1):
+            vals = []
+            for sgn in (1, -1):
+                p = [th, ph]
+                p[which] += sgn * h
+                gates = list(circ.gates)
+                gates[g] = inputs.Gate("fsim", gates[g].qubits, inputs.fsim(*p), tuple(p))
+                vals.append(loss(gates))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(grads[g][which] - fd) <= 1e-6 * max(1.0, abs(fd)), (g, which, grads[g][which], fd)
