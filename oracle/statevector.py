@@ -39,12 +39,11 @@ def amplitude(n_qubits: int, gates, bitstring: Sequence[int]) -> complex:
 
 def _apply(psi: np.ndarray, m: np.ndarray, qubits) -> np.ndarray:
     """Gate matrix m [out, in] applied to the state array on ``qubits``."""
-    if len(qubits) == 1:
-        (q,) = qubits
-        return np.moveaxis(np.tensordot(m, psi, axes=([1], [q])), 0, q)
-    a, b = qubits
-    out = np.tensordot(m.reshape(2, 2, 2, 2), psi, axes=([2, 3], [a, b]))
-    return np.moveaxis(out, [0, 1], [a, b])
+    k = len(qubits)
+    # contract the gate's input axes with the state's qubit axes, then put
+    # the gate's output axes where those qubits were
+    out = np.tensordot(m.reshape((2,) * (2 * k)), psi, axes=(tuple(range(k, 2 * k)), tuple(qubits)))
+    return np.moveaxis(out, tuple(range(k)), tuple(qubits))
 
 
 def fsim_derivatives(theta: float, phi: float):

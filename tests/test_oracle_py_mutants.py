@@ -1,6 +1,7 @@
 """The pins of the oracle's Python modules catch plausible mistakes.
 
-Each case plants one mistake in a copy of ``oracle/statevector.py`` or
+Each case plants one mistake in a copy of ``oracle/statevector.py`` (its
+state vector, or its adjoint gradient of the mean log-probability) or
 ``oracle/gradient.py`` (a gate read transposed, qubits swapped on output, a
 bitstring read backwards, environment axes in the wrong order, the exponent
 of a renormalised environment dropped, dangling labels not closed), loads the
@@ -34,6 +35,21 @@ GRAD_MUTANTS = [
     ("environment axes reversed", "open_l = list(labels[v])", "open_l = list(labels[v])[::-1]"),
     ("renormalisation exponent dropped", "return m * (2.0 ** e)", "return m"),
     ("dangling labels left unclosed", "for l in missing:", "for l in missing[:0]:"),
+]
+
+
+LOSS_GRAD_MUTANTS = [
+    ("adjoint carried by G instead of its conjugate transpose",
+     "lam = _apply(lam, np.conj(m).T, gate.qubits)", "lam = _apply(lam, m, gate.qubits)"),
+    ("adjoint state not conjugated", "lam[idx] += np.conj(1.0 / c) / B", "lam[idx] += (1.0 / c) / B"),
+    ("imaginary part taken for the real part", "2.0 * float(np.real(np.sum(M * d)))",
+     "2.0 * float(np.imag(np.sum(M * d)))"),
+    ("state taken after the gate instead of before",
+     "        if g in dgates:\n            before[g] = psi\n"
+     "        psi = _apply(psi, np.asarray(gate.matrix, dtype=np.complex128), gate.qubits)\n",
+     "        psi = _apply(psi, np.asarray(gate.matrix, dtype=np.complex128), gate.qubits)\n"
+     "        if g in dgates:\n            before[g] = psi\n"),
+    ("fSim theta derivative sign", "dt[1, 1] = dt[2, 2] = -np.sin(theta)", "dt[1, 1] = dt[2, 2] = np.sin(theta)"),
 ]
 
 
@@ -131,3 +147,50 @@ def test_planted_gradient_mistake_is_caught(name, orig, mutated):
     assert src.count(orig) == 1, f"mutation anchor not found: {name}"
     mod = _load("gradient.py", src.replace(orig, mutated), "gradient_mutant")
     assert not _grad_pins_pass(mod), f"pins did not catch: {name}"
+
+
+def _loss_grad_pins_pass(sv) -> bool:
+    """Every fSim (theta, phi) of a small circuit: the module's adjoint loss
+    gradient against central differences of the loss from forward
+    simulation (the unmutated final_state of the oracle)."""
+    from oracle import statevector as ref_sv
+    circ = inputs.random_circuit(2, 3, 5, seed=31)
+    bits = inputs.random_bitstrings(6, 3, seed=1031)
+    fs = circ.fsim_gates()
+    try:
+        dg = {g: list(sv.fsim_derivatives(*circ.gates[g].params)) for g in fs}
+        _, grads = sv.mean_log_prob_grad(6, circ.gates, bits, dg)
+
+        def loss(gates):
+            psi = ref_sv.final_state(6, gates)
+            return float(np.mean([np.log(abs(psi[tuple(int(b) for b in x)]) ** 2) for x in bits]))
+
+        h = 1e-5
+        for g in fs:
+            for which in (0, 1):
+                vals = []
+                for sgn in (1, -1):
+                    p = list(circ.gates[g].params)
+                    p[which] += sgn * h
+                    gates = list(circ.gates)
+                    gates[g] = inputs.Gate("fsim", gates[g].qubits, inputs.fsim(*p), tuple(p))
+                    vals.append(loss(gates))
+                fd = (vals[0] - vals[1]) / (2 * h)
+                if not abs(grads[g][which] - fd) <= 1e-6 * max(1.0, abs(fd)):
+                    return False
+    except (ValueError, IndexError):
+        return False
+    return True
+
+
+def test_unmodified_loss_gradient_passes_pins():
+    from oracle import statevector
+    assert _loss_grad_pins_pass(statevector)
+
+
+@pytest.mark.parametrize("name,orig,mutated", LOSS_GRAD_MUTANTS, ids=[m[0] for m in LOSS_GRAD_MUTANTS])
+def test_planted_loss_gradient_mistake_is_caught(name, orig, mutated):
+    src = open(os.path.join(ORACLE, "statevector.py")).read()
+    assert src.count(orig) == 1, f"mutation anchor not found: {name}"
+    mod = _load("statevector.py", src.replace(orig, mutated), "statevector_grad_mutant")
+    assert not _loss_grad_pins_pass(mod), f"pins did not catch: {name}"
