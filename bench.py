@@ -25,10 +25,11 @@ Workloads (``--workload``):
               K x N by --node-bits, default 15,13,10 = the largest node of
               the 7x7x14 slice), open M x N output: the tensor-core kernel
               measured on its own; sampled outputs checked in FP64.
-  batch       a bounded sample of amplitudes of a 6x6-qubit, 12-cycle circuit
-              (one shared tree) plus 256 Ising networks with N even in
-              [40, --ising-max-n], all in one captured launch sequence (unsliced);
-              per-network completion latency p50 / p99.
+  batch       1024 amplitudes of a 6x6-qubit, 12-cycle circuit (one shared
+              tree, blocks of copies per launch sequence) plus 256 Ising
+              networks with N even in [40, 160] in one batch (networks wider
+              than 24 sliced to W_s <= 24 inside it); per-network completion
+              latency p50 / p99.
 
 Throughput = algorithmic FLOPs (8 C complex, 2 C real per slice, Eq.
 vertexcon) over device time.
@@ -589,7 +590,7 @@ def run_network(args, torch, dist, rank, world, local):
             t_e2e += time.perf_counter() - t0
         h2d = sum(int(t.numel()) * elem for t in hl)
         d2h = hout.numel() * hout.element_size() + 8
-        e2e = {"value": flops_step * args.steps / t_e2e / 1e12, "unit": "TFLOP/s",
+        e2e = {"value": flops_step / t_e2e / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": t_e2e / args.steps * 1e3}
         htn.close()
@@ -704,65 +705,104 @@ def run_network(args, torch, dist, rank, world, local):
 # --------------------------------------------------------------------------
 
 def run_batch(args, torch, dist, rank, world, local):
+    """Config 4: 1024 distinct amplitudes of one 6x6-qubit, 12-cycle circuit
+    (one shared Hyper-Greedy tree) plus 256 Ising networks with N even,
+    uniform in [40, 160].  The Ising networks run as one batch: those whose
+    greedy width is at most 24 in the merged forest (one captured launch
+    sequence), wider ones sliced to W_s <= 24 (config 1's rule) as sliced
+    members of the same batch.  The amplitudes run in blocks of copies, each
+    block one launch sequence of tn_contract_instances (every node launch
+    covers the block).  One step = all of it; per-network latency from the
+    step's start (Ising: the batch's completion timestamps; amplitudes: the
+    completion of their block)."""
     import numpy as np
     from paper_2002_01935_gb300 import binding, inputs, planner
 
     mode = args.mode
     t0 = time.perf_counter()
     circ = inputs.random_circuit(6, 6, 12, seed=0)
-    bits = inputs.random_bitstrings(36, 1024, seed=1000)
     n_amp = min(args.amplitudes, 1024)
-    sel = bits[rank * n_amp:(rank + 1) * n_amp] if (rank + 1) * n_amp <= 1024 else bits[:n_amp]
-    amp_nets = [inputs.circuit_network(circ, b) for b in sel]
+    bits = inputs.random_bitstrings(36, 1024, seed=1000 + rank)[:n_amp]
+    amp_nets = [inputs.circuit_network(circ, b) for b in bits[:1]]
     a_pairs, _, a_info = planner.hyper_greedy(amp_nets[0].labels, amp_nets[0].dims, amp_nets[0].open,
                                               trials=32, seed=0, target_width=None)
     rng = np.random.default_rng(4242 + rank)
     ising_n = [int(x) for x in rng.choice(np.arange(40, args.ising_max_n + 1, 2), size=args.ising)]
     ising_nets = [inputs.random_ising(n, seed=7000 + 1000 * rank + j) for j, n in enumerate(ising_n)]
-    ising_trees = [planner.greedy_tree(nt.labels, nt.dims, nt.open) for nt in ising_nets]
-    ising_info = [planner.tree_info(nt.labels, nt.dims, p, nt.open) for nt, p in zip(ising_nets, ising_trees)]
+    ising_trees, ising_sliced, ising_info = [], [], []
+    for nt in ising_nets:
+        pr = planner.greedy_tree(nt.labels, nt.dims, nt.open)
+        inf = planner.tree_info(nt.labels, nt.dims, pr, nt.open)
+        sl = planner.slice_greedy(nt.labels, nt.dims, pr, nt.open, 24.0) if inf.W > 24 else []
+        ising_trees.append(pr)
+        ising_sliced.append(sl)
+        ising_info.append(planner.tree_info(nt.labels, nt.dims, pr, nt.open, sl))
     t_plan = time.perf_counter() - t0
-    nets = amp_nets + ising_nets
-    trees = [a_pairs] * n_amp + ising_trees
-    flops = [8.0 * a_info.C] * n_amp + [2.0 * i.C for i in ising_info]
-    flops_step = sum(flops)
-    # every leaf of the batch lives in one flat device buffer per dtype (16-byte
-    # aligned views), so the end-to-end leg needs one host->device copy each
-    flat = {}
-    for dt in (torch.complex64, torch.float32):
-        sizes = [-(-int(np.prod(np.shape(t))) // (2 if dt == torch.complex64 else 4)) *
-                 (2 if dt == torch.complex64 else 4)
-                 for nt in nets if (nt.is_complex == (dt == torch.complex64)) for t in nt.tensors]
-        flat[dt] = [torch.zeros(max(sum(sizes), 1), dtype=dt, device="cuda"),
-                    torch.zeros(max(sum(sizes), 1), dtype=dt).pin_memory(), 0]
-    handles, keep = [], []
-    for nt in nets:
-        dt = torch.complex64 if nt.is_complex else torch.float32
-        align = 2 if nt.is_complex else 4
-        dev, host, pos = flat[dt]
+    flops_ising = [2.0 * i.C * i.d_sliced for i in ising_info]
+    flops_amp = 8.0 * a_info.C * n_amp
+    flops_step = flops_amp + sum(flops_ising)
+
+    # Ising leaves in one flat device buffer (one host->device copy for e2e)
+    sizes = [int(np.prod(np.shape(t))) for nt in ising_nets for t in nt.tensors]
+    i_dev = torch.zeros(sum(-(-x // 4) * 4 for x in sizes), dtype=torch.float32, device="cuda")
+    i_host = torch.zeros(i_dev.numel(), dtype=torch.float32).pin_memory()
+    handles, keep, pos = [], [], 0
+    for nt in ising_nets:
         ts = []
         for t in nt.tensors:
             a = np.array(t, order="C")
-            sz = int(a.size)
-            host[pos:pos + sz] = torch.from_numpy(a.reshape(-1)).to(dt)
-            ts.append(dev[pos:pos + sz].view(a.shape))
-            pos += -(-sz // align) * align
-        flat[dt][2] = pos
+            i_host[pos:pos + a.size] = torch.from_numpy(a.reshape(-1)).float()
+            ts.append(i_dev[pos:pos + a.size].view(a.shape))
+            pos += -(-a.size // 4) * 4
         keep.append(ts)
-    for dt in flat:
-        flat[dt][0].copy_(flat[dt][1])
-    for nt, ts in zip(nets, keep):
-        handles.append(binding.TensorNetwork(nt.labels, nt.dims, nt.open, ts, complex_=nt.is_complex))
+    i_dev.copy_(i_host)
+    for nt, ts in zip(ising_nets, keep):
+        handles.append(binding.TensorNetwork(nt.labels, nt.dims, nt.open, ts, complex_=False))
     if not args.no_autotune:
-        for h, tr in zip(handles, trees):
-            h.autotune(tr, [], mode, reps=2)
-    batch = binding.Batch(handles, trees, mode)
+        for h, tr, sl in zip(handles, ising_trees, ising_sliced):
+            if not sl:
+                h.autotune(tr, [], mode, reps=2)
+    batch = binding.Batch(handles, ising_trees, mode, sliced=ising_sliced)
+
+    # amplitudes: shared leaves once, the output states of all bitstrings
+    # stacked [n_amp, 2] per qubit; a block reads rows [b0, b0 + B)
+    net0 = amp_nets[0]
+    n = net0.n_tensors
+    first_out = n - 36
+    a_leaves = [torch.from_numpy(np.array(t, order="C")).to(torch.complex64).cuda() for t in net0.tensors]
+    outs_host = torch.zeros((36, n_amp, 2), dtype=torch.complex64).pin_memory()
+    for q in range(36):
+        outs_host[q, torch.arange(n_amp), torch.from_numpy(bits[:, q].astype(np.int64))] = 1.0
+    outs_dev = outs_host.cuda()
+    atn = binding.TensorNetwork(net0.labels, net0.dims, net0.open, a_leaves, complex_=True)
+    ws1 = atn.plan_info(a_pairs, [], mode)["ws_bytes"]
+    B = int(max(1, min(args.amp_block, n_amp, (48 << 30) // max(ws1, 1))))
+    strides = [0] * first_out + [2] * 36
+    blocks = [(b0, min(B, n_amp - b0)) for b0 in range(0, n_amp, B)]
+
+    def run_amplitudes(evs=None):
+        res = []
+        for j, (b0, cnt) in enumerate(blocks):
+            leaves = list(a_leaves)
+            for q in range(36):
+                leaves[first_out + q] = outs_dev[q, b0:b0 + cnt]
+            atn.set_tensors(leaves)
+            res.append(atn.contract_instances(a_pairs, mode, cnt, strides))
+            if evs is not None:
+                evs[j].record(stream)
+        return res
+
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    # warm-up: the Ising batch W times; the amplitude blocks once (a
+    # minute of work: the first pass builds every plan and graph, later
+    # passes repeat it unchanged)
     for _ in range(args.warmup):
-        out, ex, lat = batch.contract()
+        batch.contract()
+    run_amplitudes()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    blk_ev = [device_events(torch, stream, len(blocks)) for _ in range(args.steps)]
     lats = []
     clk = ClockSampler(local)
     if dist:
@@ -774,6 +814,7 @@ def run_batch(args, torch, dist, rank, world, local):
         flush.zero_()
         starts[i].record(stream)
         out, ex, lat = batch.contract()
+        amp_res = run_amplitudes(blk_ev[i])
         ends[i].record(stream)
         lats.append(lat)
     torch.cuda.nvtx.range_pop()
@@ -787,75 +828,91 @@ def run_batch(args, torch, dist, rank, world, local):
         dist.barrier()
     ms_per_step = total_ms / args.steps
     value = flops_step * world * args.steps / (total_ms / 1e3) / 1e12
-    L = np.stack([x.cpu().numpy() for x in lats]).astype(np.float64) / 1e6  # ms
-    la, li = L[:, :n_amp].ravel(), L[:, n_amp:].ravel()
+    li = np.stack([x.cpu().numpy() for x in lats]).astype(np.float64).ravel() / 1e6  # ms
+    la = np.array([starts[i].elapsed_time(blk_ev[i][j]) for i in range(args.steps)
+                   for j, (b0, cnt) in enumerate(blocks) for _ in range(cnt)])
     pct = lambda x, q: float(np.percentile(x, q)) if x.size else None
     out, ex = out.cpu().numpy(), ex.cpu().numpy()
+    amp_m = torch.cat([r[0] for r in amp_res]).cpu().numpy()
+    amp_e = torch.cat([r[1] for r in amp_res]).cpu().numpy()
 
-    # e2e: the same batch with every leaf copied from pinned host memory per step
+    # e2e: every leaf copied from pinned host memory per step, results read back
     e2e = None
     if rank == 0:
-        h2d = sum(int(f[2]) * f[1].element_size() for f in flat.values())
+        h2d = int(pos) * 4 + int(outs_host.numel()) * 8
         t_e2e = 0.0
-        for i in range(args.warmup + args.steps):
+        for i in range(2):  # one untimed pass, one timed
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for dev, host, pos in flat.values():
-                if pos:
-                    dev[:pos].copy_(host[:pos], non_blocking=True)
+            t1 = time.perf_counter()
+            i_dev.copy_(i_host, non_blocking=True)
+            outs_dev.copy_(outs_host, non_blocking=True)
             o2, x2, _ = batch.contract()
+            r2 = run_amplitudes()
             o2h, x2h = o2.cpu(), x2.cpu()
-            if i >= args.warmup:
-                t_e2e += time.perf_counter() - t0
-        e2e = {"value": flops_step * args.steps / t_e2e / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(o2h.numel() * 8 + x2h.numel() * 8),
-               "ms_per_step": t_e2e / args.steps * 1e3,
-               "path": "all leaves copied host->device (one copy per dtype), one batch call, "
-                       "results read back"}
+            rh = [(a.cpu(), b_.cpu()) for a, b_ in r2]
+            if i >= 1:
+                t_e2e += time.perf_counter() - t1
+        e2e = {"value": flops_step / t_e2e / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": int(o2h.numel() * 8 + x2h.numel() * 8 + n_amp * 24),
+               "ms_per_step": t_e2e * 1e3,
+               "path": "Ising leaves and the amplitudes' output states copied host->device, "
+                       "the batch call and the amplitude blocks, results read back"}
 
-    # the oracle: a sample of the Ising networks in full (amplitudes of 36 qubits
-    # are beyond its reach in a bench run; the sub-slice check covers them)
+    # the oracle: a sample of the Ising networks (same sliced trees, on the
+    # leaf values the GPU reads) and sub-slices of one amplitude
     cpu, rel = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import tree
         errs, t_or, fl_or, k = [], 0.0, 0.0, 0
         t_all = time.perf_counter()
-        for j in range(len(ising_nets)):
+        order = sorted(range(len(ising_nets)), key=lambda j: flops_ising[j])
+        for j in order:
             if time.perf_counter() - t_all > 10.0:
                 break
             t1 = time.perf_counter()
-            om, oe = tree.contract_net(gpu_leaves(ising_nets[j]), ising_trees[j])
+            om, oe = tree.contract_net(gpu_leaves(ising_nets[j]), ising_trees[j], ising_sliced[j])
             t_or += time.perf_counter() - t1
-            fl_or += flops[n_amp + j]
-            i = n_amp + j
-            errs.append(rel_error(float(out[i, 0]), int(ex[i]), float(om), int(oe), False))
+            fl_or += flops_ising[j]
+            errs.append(rel_error(float(out[j, 0]), int(ex[j]), float(om), int(oe), False))
             k += 1
         cpu = {"value": fl_or / t_or / 1e12, "unit": "TFLOP/s", "cores": tree.max_threads(),
-               "kind": "oracle", "sample": f"{k} of the {len(ising_nets)} Ising networks, full"}
+               "kind": "oracle", "sample": f"the {k} smallest of the {len(ising_nets)} Ising networks, full"}
         rel = {"ising_max": max(errs) if errs else None, "ising_checked": k}
-        sub, so = oracle_subslices(amp_nets[0], a_pairs, budget_s=6.0)
-        gm, ge = scalar_value(*handles[0].contract(a_pairs, so["sliced"], mode, slice_begin=0,
-                                                   slice_count=so["count"]), True)
+        a0 = binding.TensorNetwork(net0.labels, net0.dims, net0.open, a_leaves, complex_=True)
+        sub, so = oracle_subslices(net0, a_pairs, budget_s=6.0)
+        gm, ge = scalar_value(*a0.contract(a_pairs, so["sliced"], mode, slice_begin=0,
+                                           slice_count=so["count"]), True)
         rel["amplitude_subslices"] = rel_error(gm, ge, so["ref"][0], so["ref"][1], True)
         rel["amplitude_sample"] = sub["sample"]
+        # block copy 0 is bitstring 0: against the single-network call
+        sm_, se_ = scalar_value(*a0.contract(a_pairs, [], mode), True)
+        a0.close()
+        rel["amplitude_block_vs_single_call"] = rel_error(
+            complex(amp_m[0, 0], amp_m[0, 1]), int(amp_e[0]), sm_, se_, True)
 
+    n_sl = sum(1 for sl in ising_sliced if sl)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAMES["batch"], "mode": mode,
-                   "amplitudes": n_amp, "amplitude_sample_of": 1024, "circuit": "6x6, 12 cycles",
+                   "amplitudes": n_amp, "amplitude_block": B, "amplitude_blocks": len(blocks),
+                   "circuit": "6x6, 12 cycles",
                    "amplitude_tree": f"Hyper-Greedy 32 trials, W {a_info.W:g}, C {a_info.C:.3e}",
                    "ising_networks": len(ising_nets),
                    "ising_N": f"even, uniform in [40, {args.ising_max_n}]",
+                   "ising_sliced": f"{n_sl} networks with greedy width > 24 sliced to W_s <= 24",
+                   "ising_flops": sum(flops_ising), "amplitude_flops": flops_amp,
                    "flops_per_step": flops_step, "planning_s": round(t_plan, 2),
+                   "warmup": f"the Ising batch {args.warmup} times, the amplitude blocks once",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
-        "s_per_amplitude": (pct(la, 50) / 1e3) if n_amp else None,
+        "s_per_amplitude": ms_per_step / 1e3 / max(n_amp, 1),
         "latency_ms": {"amplitude_p50": pct(la, 50), "amplitude_p99": pct(la, 99),
                        "ising_p50": pct(li, 50), "ising_p99": pct(li, 99),
-                       "all_p50": pct(L.ravel(), 50), "all_p99": pct(L.ravel(), 99)},
-        "extrapolated_1024_amplitudes_s": ms_per_step / 1e3 * 1024 / max(n_amp, 1),
+                       "all_p50": pct(np.concatenate([la, li]), 50),
+                       "all_p99": pct(np.concatenate([la, li]), 99)},
         "rel_err_vs_oracle": rel,
         "roofline": None,
         "cpu_baseline": cpu,
@@ -866,6 +923,7 @@ def run_batch(args, torch, dist, rank, world, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     batch.close()
+    atn.close()
     for h in handles:
         h.close()
     return 0
@@ -1191,10 +1249,11 @@ def main():
     ap.add_argument("--workload", default="circuit7x7", choices=list(WORKLOAD_NAMES))
     ap.add_argument("--mode", default="fp16_split", choices=MODES)
     ap.add_argument("--slices", type=int, default=2, help="circuit7x7: slices per step")
-    ap.add_argument("--amplitudes", type=int, default=8, help="batch: amplitudes per step")
+    ap.add_argument("--amplitudes", type=int, default=1024, help="batch: amplitudes per step")
+    ap.add_argument("--amp-block", type=int, default=32, help="batch: amplitudes per instances launch")
     ap.add_argument("--ising", type=int, default=256, help="batch: Ising networks per step")
     ap.add_argument("--node-bits", default="15,13,10", help="node: M,N,K label bits")
-    ap.add_argument("--ising-max-n", type=int, default=100,
+    ap.add_argument("--ising-max-n", type=int, default=160,
                     help="batch: largest Ising N (even N uniform in [40, this])")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--simplify", action="store_true",
@@ -1207,7 +1266,7 @@ def main():
     if args.steps is None:
         short = args.workload in ("ising100", "ising100_hyper", "circuit4x4", "circuit5x5")
         args.steps = (20 if args.impl == "reference" or args.workload == "circuit7x7"
-                      else (400 if short else 5))
+                      else (400 if short else (1 if args.workload == "batch" else 5)))
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(args.warmup, 3)

@@ -445,12 +445,29 @@ tn_status tn_plan_steps(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced
  *                     time from the start of the batch until its root
  *                     contraction completed (%globaltimer, nanoseconds).
  *                     out_mem: TN_MEM_DEVICE or TN_MEM_HOST for all three.
- *   Errors: TN_EINVAL, TN_EUNSUPPORTED (open labels, slicing, host leaves),
- *   TN_ENOMEM, TN_ECUDA.
+ *   Errors: TN_EINVAL, TN_EUNSUPPORTED (open labels, slicing -- see
+ *   tn_batch_create_sliced --, host leaves), TN_ENOMEM, TN_ECUDA.
  */
 typedef struct tn_batch tn_batch;
 tn_status tn_batch_create(tn_batch **out, int32_t n_nets, tn_net *const *nets,
                           const int32_t *const *tree_pairs, tn_mode mode);
+
+/*
+ * tn_batch_create_sliced -- tn_batch_create with a slicing per network
+ * (Sec. 4.7.1): network i sums the n_sliced[i] labels sliced_labels[i]
+ * outside its tree (n_sliced[i] = 0: unsliced).  Unsliced networks form the
+ * merged forest as in tn_batch_create.  A sliced network stays out of it:
+ * after the forest, on the same stream, its slices run through its own plan
+ * -- up to 8 slices side by side per launch (fewer when their workspace
+ * would exceed 2 GiB), folded in FP64 in slice order -- and its value,
+ * exponent and latency (the time from the batch start until its last slice
+ * was folded) go to the same outputs of tn_batch_contract.  Its device state
+ * is that of its handle's plan (kept by the handle).  Errors as
+ * tn_batch_create; TN_EINVAL for bad sliced labels (as tn_contract).
+ */
+tn_status tn_batch_create_sliced(tn_batch **out, int32_t n_nets, tn_net *const *nets,
+                                 const int32_t *const *tree_pairs, const int32_t *n_sliced,
+                                 const int64_t *const *sliced_labels, tn_mode mode);
 tn_status tn_batch_contract(tn_batch *batch, double *out, int64_t *out_exp2, uint64_t *latency_ns,
                             int32_t out_mem, void *stream);
 void tn_batch_destroy(tn_batch *batch);

@@ -90,6 +90,9 @@ _lib.tn_plan_steps.argtypes = [_vp, _i32p, ctypes.c_int32, _i64p, ctypes.c_int, 
 _lib.tn_batch_create.restype = ctypes.c_int
 _lib.tn_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp),
                                  ctypes.POINTER(_i32p), ctypes.c_int]
+_lib.tn_batch_create_sliced.restype = ctypes.c_int
+_lib.tn_batch_create_sliced.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp),
+                                        ctypes.POINTER(_i32p), _i32p, ctypes.POINTER(_i64p), ctypes.c_int]
 _lib.tn_batch_contract.restype = ctypes.c_int
 _lib.tn_batch_contract.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, _vp]
 _lib.tn_batch_destroy.restype = None
@@ -105,7 +108,7 @@ EXPORTS = ["tn_create", "tn_set_tensor", "tn_contract", "tn_contract_ex", "tn_co
            "tn_contract_grad_ex", "tn_contract_grad_instances", "tn_contract_instances_keep",
            "tn_selftest_flow_timeout",
            "tn_contract_noalloc", "tn_contract_instances", "tn_autotune", "tn_plan_info", "tn_plan_steps",
-           "tn_batch_create",
+           "tn_batch_create", "tn_batch_create_sliced",
            "tn_batch_contract", "tn_batch_destroy", "tn_destroy", "tn_last_error", "tn_version"]
 
 
@@ -654,11 +657,14 @@ class TensorNetwork:
 
 class Batch:
     """Many scalar networks (TensorNetwork handles, each with its tree) run
-    as one captured launch sequence.  ``contract`` returns (mantissa, exp2,
-    latency_ns) device tensors: mantissa (n, 2) float64, exp2 (n,) int64,
-    per-network completion time since the batch started."""
+    as one captured launch sequence.  ``sliced`` (optional) gives each
+    network's sliced labels (empty: unsliced); sliced networks run their
+    slice loops after the merged forest (tn_batch_create_sliced).
+    ``contract`` returns (mantissa, exp2, latency_ns) device tensors:
+    mantissa (n, 2) float64, exp2 (n,) int64, per-network completion time
+    since the batch started."""
 
-    def __init__(self, networks, trees, mode="fp32"):
+    def __init__(self, networks, trees, mode="fp32", sliced=None):
         import torch  # noqa: F401
         self.nets = list(networks)
         m = MODES[mode] if isinstance(mode, str) else int(mode)
@@ -668,7 +674,16 @@ class Batch:
         hs = (_vp * len(self.nets))(*[n.h for n in self.nets])
         tp = (_i32p * len(self.nets))(*[t.ctypes.data_as(_i32p) for t in self._trees])
         h = _vp()
-        _check(_lib.tn_batch_create(ctypes.byref(h), len(self.nets), hs, tp, m))
+        if sliced is None or not any(len(s) for s in sliced):
+            _check(_lib.tn_batch_create(ctypes.byref(h), len(self.nets), hs, tp, m))
+        else:
+            if len(sliced) != len(self.nets):
+                raise TNError(TN_EINVAL, "one sliced-label list per network")
+            self._sliced = [_arr(list(s) or [0], np.int64) for s in sliced]
+            ns = _arr([len(s) for s in sliced], np.int32)
+            sp = (_i64p * len(self.nets))(*[a.ctypes.data_as(_i64p) for a in self._sliced])
+            _check(_lib.tn_batch_create_sliced(ctypes.byref(h), len(self.nets), hs, tp,
+                                               ns.ctypes.data_as(_i32p), sp, m))
         self.h = h.value
 
     def contract(self, stream=None):

@@ -476,8 +476,9 @@ struct tn_batch {
     tn::BatchPlan b;
 };
 
-tn_status tn_batch_create(tn_batch** out, int32_t n_nets, tn_net* const* nets,
-                          const int32_t* const* tree_pairs, tn_mode mode) {
+static tn_status batch_create(tn_batch** out, int32_t n_nets, tn_net* const* nets,
+                              const int32_t* const* tree_pairs, const int32_t* n_sliced,
+                              const int64_t* const* sliced_labels, tn_mode mode) {
     if (!out || n_nets < 1 || !nets || !tree_pairs) return fail(TN_EINVAL, "tn_batch_create: bad arguments");
     *out = nullptr;
     std::unique_ptr<tn_batch> b(new (std::nothrow) tn_batch);
@@ -485,11 +486,30 @@ tn_status tn_batch_create(tn_batch** out, int32_t n_nets, tn_net* const* nets,
     b->b.mode = mode;
     for (int i = 0; i < n_nets; ++i) {
         if (!nets[i]) return fail(TN_EINVAL, "tn_batch_create: NULL network");
+        const int32_t ns = n_sliced ? n_sliced[i] : 0;
+        if (ns < 0 || (ns > 0 && (!sliced_labels || !sliced_labels[i])))
+            return fail(TN_EINVAL, "tn_batch_create_sliced: bad sliced labels");
         Plan* p = nullptr;
-        tn_status st = get_plan(nets[i], tree_pairs[i], 0, nullptr, mode, &p);
+        tn_status st = get_plan(nets[i], tree_pairs[i], ns, ns ? sliced_labels[i] : nullptr, mode, &p);
         if (st != TN_OK) return st;
         b->b.nets.push_back(&nets[i]->d);
         b->b.plans.push_back(p);
+        if (p->d_sliced > 1) {
+            // device state for G slices side by side: as many as fit a 2 GiB
+            // workspace budget, at most 8
+            const int64_t ws = p->ws_elems * (int64_t)nets[i]->d.elem_bytes() + p->split_bytes;
+            int G = 1;
+            while (G < 8 && 2 * (int64_t)G <= p->d_sliced && 2 * (int64_t)G * ws <= (int64_t(2) << 30)) G *= 2;
+            st = ensure_instances(nets[i], p, G, nullptr);
+            if (st != TN_OK) return st;
+            tn::SlicedMember m;
+            m.index = i;
+            m.d = &nets[i]->d;
+            m.p = p;
+            m.unit = nets[i]->unit;
+            m.G = G;
+            b->b.sliced.push_back(m);
+        }
     }
     std::string err;
     tn_status st = tn::build_batch(b->b, err);
@@ -500,6 +520,18 @@ tn_status tn_batch_create(tn_batch** out, int32_t n_nets, tn_net* const* nets,
     }
     *out = b.release();
     return TN_OK;
+}
+
+tn_status tn_batch_create(tn_batch** out, int32_t n_nets, tn_net* const* nets,
+                          const int32_t* const* tree_pairs, tn_mode mode) {
+    return batch_create(out, n_nets, nets, tree_pairs, nullptr, nullptr, mode);
+}
+
+tn_status tn_batch_create_sliced(tn_batch** out, int32_t n_nets, tn_net* const* nets,
+                                 const int32_t* const* tree_pairs, const int32_t* n_sliced,
+                                 const int64_t* const* sliced_labels, tn_mode mode) {
+    if (!n_sliced) return fail(TN_EINVAL, "tn_batch_create_sliced: n_sliced is NULL");
+    return batch_create(out, n_nets, nets, tree_pairs, n_sliced, sliced_labels, mode);
 }
 
 tn_status tn_batch_contract(tn_batch* batch, double* out, int64_t* out_exp2, uint64_t* latency_ns,

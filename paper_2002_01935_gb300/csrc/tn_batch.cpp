@@ -7,7 +7,12 @@
 // one wave launch per storage type runs every small node of every network,
 // then the large nodes launch one by one.  A final kernel writes every
 // network's (mantissa, exponent) and the time its root completed.  The
-// whole sequence is captured once as a CUDA graph and replayed.
+// whole sequence is captured once as a CUDA graph and replayed.  Sliced
+// networks (Sec. 4.7.1: a tree sliced to a width cap) stay out of the forest:
+// after the graph, each runs its own slice loop -- its per-slice graph
+// replayed over its slices, several side by side, folded in FP64 -- on the
+// same stream, and writes its value and completion latency into the batch's
+// outputs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,6 +34,8 @@ tn_status build_batch(BatchPlan& b, std::string& err) {
     int max_level = 0;
     b.level.assign(N, {});
     b.small.assign(N, {});
+    b.is_sliced.assign(N, 0);
+    for (const SlicedMember& m : b.sliced) b.is_sliced[m.index] = 1;
     for (int i = 0; i < N; ++i) {
         const NetDesc& d = *b.nets[i];
         const Plan& p = *b.plans[i];
@@ -36,10 +43,11 @@ tn_status build_batch(BatchPlan& b, std::string& err) {
             err = "tn_batch: every network must be scalar (no open labels)";
             return TN_EUNSUPPORTED;
         }
-        if (p.d_sliced != 1) {
-            err = "tn_batch: sliced trees are not supported in a batch";
+        if (p.d_sliced != 1 && !b.is_sliced[i]) {
+            err = "tn_batch: a sliced tree must be given as a sliced member";
             return TN_EUNSUPPORTED;
         }
+        if (b.is_sliced[i]) continue;  // runs its own slice loop after the forest
         b.ws_base[i] = ws;
         ws += (p.ws_elems * (int64_t)d.elem_bytes() + 255) / 256 * 256;
         b.slot_base[i] = slots;
@@ -79,7 +87,7 @@ tn_status build_batch(BatchPlan& b, std::string& err) {
             w.cplx = cp == 1;
             w.item_begin = (int)b.items.size();
             for (int i = 0; i < N; ++i) {
-                if (b.nets[i]->is_complex() != w.cplx) continue;
+                if (b.is_sliced[i] || b.nets[i]->is_complex() != w.cplx) continue;
                 const Plan& p = *b.plans[i];
                 for (size_t k = 0; k < p.nodes.size(); ++k) {
                     if (b.level[i][k] != L || !b.small[i][k]) continue;
@@ -99,6 +107,7 @@ tn_status build_batch(BatchPlan& b, std::string& err) {
             if (w.item_count) b.steps.push_back(w);
         }
         for (int i = 0; i < N; ++i) {
+            if (b.is_sliced[i]) continue;
             const Plan& p = *b.plans[i];
             for (size_t k = 0; k < p.nodes.size(); ++k) {
                 if (b.level[i][k] != L || b.small[i][k]) continue;
@@ -127,9 +136,10 @@ tn_status alloc_batch(BatchPlan& b, std::string& err) {
     if (!ck(cudaMalloc(&b.maxabs, sizeof(unsigned) * std::max(b.n_slots, 1)), "cudaMalloc")) return TN_ENOMEM;
     if (!ck(cudaMalloc(&b.exps, sizeof(int64_t) * std::max(b.n_slots, 1)), "cudaMalloc")) return TN_ENOMEM;
     if (!ck(cudaMalloc(&b.ctl, sizeof(Control)), "cudaMalloc")) return TN_ENOMEM;
-    if (!ck(cudaMalloc(&b.leafmax, sizeof(unsigned) * b.n_leaves), "cudaMalloc")) return TN_ENOMEM;
-    if (!ck(cudaMalloc((void**)&b.leaf_ptr_dev, sizeof(void*) * b.n_leaves), "cudaMalloc")) return TN_ENOMEM;
-    if (!ck(cudaMalloc(&b.leaf_nfloat_dev, sizeof(int64_t) * b.n_leaves), "cudaMalloc")) return TN_ENOMEM;
+    const size_t nl = (size_t)std::max(b.n_leaves, 1);
+    if (!ck(cudaMalloc(&b.leafmax, sizeof(unsigned) * nl), "cudaMalloc")) return TN_ENOMEM;
+    if (!ck(cudaMalloc((void**)&b.leaf_ptr_dev, sizeof(void*) * nl), "cudaMalloc")) return TN_ENOMEM;
+    if (!ck(cudaMalloc(&b.leaf_nfloat_dev, sizeof(int64_t) * nl), "cudaMalloc")) return TN_ENOMEM;
     if (!ck(cudaMalloc(&b.t_start, sizeof(unsigned long long)), "cudaMalloc")) return TN_ENOMEM;
     if (!ck(cudaMalloc(&b.t_done, sizeof(unsigned long long) * N), "cudaMalloc")) return TN_ENOMEM;
     if (!ck(cudaMalloc(&b.lat_dev, sizeof(unsigned long long) * N), "cudaMalloc")) return TN_ENOMEM;
@@ -144,6 +154,10 @@ tn_status alloc_batch(BatchPlan& b, std::string& err) {
     std::vector<int64_t> nf(b.n_leaves);
     std::vector<BatchRoot> roots(N);
     for (int i = 0; i < N; ++i) {
+        if (b.is_sliced[i]) {
+            memset(&roots[i], 0, sizeof(roots[i]));  // root NULL: written by its slice loop
+            continue;
+        }
         const NetDesc& d = *b.nets[i];
         const Plan& p = *b.plans[i];
         const int n = d.n;
@@ -277,7 +291,7 @@ tn_status run_batch(BatchPlan& b, double* out, int64_t* out_exp2, uint64_t* late
                 err = "tn_batch: every leaf must be a device pointer";
                 return TN_EINVAL;
             }
-            lp[b.leaf_base[i] + v] = d.leaves[v].ptr;
+            if (!b.is_sliced[i]) lp[b.leaf_base[i] + v] = d.leaves[v].ptr;
         }
     }
     if (!b.gexec || lp != b.graph_ptrs) {
@@ -286,6 +300,7 @@ tn_status run_batch(BatchPlan& b, double* out, int64_t* out_exp2, uint64_t* late
                            stream));
         CK(cudaStreamSynchronize(stream));
         for (int i = 0; i < N; ++i) {
+            if (b.is_sliced[i]) continue;
             const Plan& p = *b.plans[i];
             const int n = b.nets[i]->n;
             for (size_t k = 0; k < p.nodes.size(); ++k) {
@@ -309,6 +324,18 @@ tn_status run_batch(BatchPlan& b, double* out, int64_t* out_exp2, uint64_t* late
         b.graph_ptrs = lp;
     }
     CK(cudaGraphLaunch(b.gexec, stream));
+    // the sliced members, one after another: all their slices (G side by
+    // side per launch, FP64 fold in slice order), value and exponent into
+    // the batch's outputs, then their completion latency
+    for (const SlicedMember& m : b.sliced) {
+        tn_options o;
+        memset(&o, 0, sizeof(o));
+        o.slice_batch = m.G;
+        tn_status st = run_plan(*m.d, *m.p, m.unit, 0, m.p->d_sliced, o, b.out_dev + 2 * m.index,
+                                TN_MEM_DEVICE, b.exp_dev + m.index, stream, err);
+        if (st != TN_OK) return st;
+        CK(launch_batch_mark(b.t_start, b.lat_dev + m.index, stream));
+    }
     cudaMemcpyKind kind = out_mem == TN_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     CK(cudaMemcpyAsync(out, b.out_dev, sizeof(double) * 2 * N, kind, stream));
     CK(cudaMemcpyAsync(out_exp2, b.exp_dev, sizeof(int64_t) * N, kind, stream));

@@ -17,10 +17,23 @@ struct BatchStep {
     int net = -1, node = -1;  // single-node step
 };
 
+// A sliced network of the batch: not part of the merged forest; its slices
+// run after the forest, on the same stream, through its own plan (device
+// state owned by its handle), G slices side by side per launch.
+struct SlicedMember {
+    int index = -1;
+    NetDesc* d = nullptr;
+    Plan* p = nullptr;
+    void* unit = nullptr;
+    int G = 1;
+};
+
 struct BatchPlan {
     tn_mode mode = TN_MODE_FP32;
     std::vector<const NetDesc*> nets;
     std::vector<Plan*> plans;  // host plans, owned by the network handles
+    std::vector<SlicedMember> sliced;  // members with d_sliced > 1
+    std::vector<char> is_sliced;       // per network
     std::vector<std::vector<int>> level, small;
     std::vector<int64_t> ws_base;  // bytes
     std::vector<int> slot_base, leaf_base, desc_base;

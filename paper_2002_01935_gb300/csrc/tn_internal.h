@@ -316,7 +316,8 @@ struct RootAdjArgs {
 
 // Batched networks: where each network's root lives and where its result goes.
 struct BatchRoot {
-    const void* root;           // scalar root value (float2 or float)
+    const void* root;           // scalar root value (float2 or float); NULL: a
+                                // sliced member that writes its own result
     const int64_t* exp;         // root exponent slot
     const unsigned* max;        // root max slot (0: the value is exactly zero)
     int is_c;
@@ -325,6 +326,8 @@ struct BatchRoot {
 
 // Launchers (tn_kernels.cu).  is_c: complex64 data.
 cudaError_t launch_batch_start(unsigned long long* t_start, cudaStream_t s);
+// latency = now - *t_start (%globaltimer), written after a batch member's own launches
+cudaError_t launch_batch_mark(const unsigned long long* t_start, unsigned long long* latency, cudaStream_t s);
 cudaError_t launch_batch_finish(const BatchRoot* roots, int n, double* out, int64_t* out_exp,
                                 const unsigned long long* t_start, const unsigned long long* t_done,
                                 unsigned long long* latency, cudaStream_t s);

@@ -545,6 +545,15 @@ __global__ void k_batch_finish(const BatchRoot* roots, int n, double* out, int64
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const BatchRoot r = roots[i];
+    if (r.root == nullptr) {
+        // a sliced network: its slice loop runs after this kernel and writes
+        // its value, exponent and latency itself
+        out[2 * i] = 0.0;
+        out[2 * i + 1] = 0.0;
+        out_exp[i] = 0;
+        if (latency) latency[i] = 0;
+        return;
+    }
     const bool zero = !(__uint_as_float(*r.max) > 0.f);
     if (r.is_c) {
         const float2 v = *reinterpret_cast<const float2*>(r.root);
@@ -556,6 +565,16 @@ __global__ void k_batch_finish(const BatchRoot* roots, int n, double* out, int64
     }
     out_exp[i] = zero ? 0 : *r.exp;
     if (latency) latency[i] = t_done[i] > *t_start ? t_done[i] - *t_start : 0;
+}
+
+__global__ void k_batch_mark(const unsigned long long* t_start, unsigned long long* latency) {
+    const unsigned long long t = global_ns();
+    *latency = t > *t_start ? t - *t_start : 0;
+}
+
+cudaError_t launch_batch_mark(const unsigned long long* t_start, unsigned long long* latency, cudaStream_t s) {
+    k_batch_mark<<<1, 1, 0, s>>>(t_start, latency);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_finish(const BatchRoot* roots, int n, double* out, int64_t* out_exp,

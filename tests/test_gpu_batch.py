@@ -68,3 +68,56 @@ def test_mixed_batch_matches_oracle(torch, mode):
         batch.close()
         for h in handles:
             h.close()
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp16_split"])
+def test_mixed_batch_with_sliced_members(torch, mode):
+    """Circuit amplitudes and Ising networks of N in [12, 60] in the merged
+    forest, plus Ising networks sliced to a width cap as members that run
+    their own slice loops: an N = 152 network (greedy width 24, sliced to
+    W_s <= 22) and an N = 100 one (width 21, sliced to W_s <= 16).  Every
+    value against the oracle's contraction of the same sliced tree (on the
+    leaf values the GPU reads); the sliced members complete after the forest."""
+    from paper_2002_01935_gb300 import binding
+    nets = make_nets(6, 6)
+    trees = [planner.greedy_tree(n.labels, n.dims, n.open) for n in nets]
+    sliced = [[] for _ in nets]
+    for n_v, seed, cap in ((152, 15, 22.0), (100, 0, 16.0)):
+        net = inputs.random_ising(n_v, seed=seed)
+        pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+        sl = planner.slice_greedy(net.labels, net.dims, pairs, net.open, cap)
+        assert sl
+        nets.append(net)
+        trees.append(pairs)
+        sliced.append(sl)
+    handles, keep = [], []
+    for net in nets:
+        dt = torch.complex64 if net.is_complex else torch.float32
+        ts = [torch.from_numpy(np.array(t, order="C")).to(dt).cuda() for t in net.tensors]
+        keep.append(ts)
+        handles.append(binding.TensorNetwork(net.labels, net.dims, net.open, ts, complex_=net.is_complex))
+    refs = [tree.contract_net(net.as_stored(), trees[i], sliced[i]) for i, net in enumerate(nets)]
+    batch = binding.Batch(handles, trees, mode, sliced=sliced)
+    tol = 1e-5
+    try:
+        for call in range(2):
+            out, ex, lat = batch.contract()
+            torch.cuda.synchronize()
+            out, ex, lat = out.cpu().numpy(), ex.cpu().numpy(), lat.cpu().numpy()
+            for i, net in enumerate(nets):
+                mo, eo = refs[i]
+                if net.is_complex:
+                    got = complex(out[i, 0], out[i, 1]) * 2.0 ** (int(ex[i]) - eo)
+                    ref = complex(mo)
+                    assert abs(got - ref) <= tol * abs(ref), (call, i)
+                else:
+                    assert out[i, 1] == 0.0
+                    d = math.log(out[i, 0]) + (int(ex[i]) - eo) * math.log(2) - math.log(float(mo))
+                    assert abs(math.expm1(d)) <= tol, (call, i, d)
+            assert np.all(lat > 0) and np.all(lat < 60 * 10**9)
+            # the sliced members run after the forest, the second after the first
+            assert lat[-2] >= lat[:-2].max() and lat[-1] >= lat[-2]
+    finally:
+        batch.close()
+        for h in handles:
+            h.close()
