@@ -503,7 +503,9 @@ def run_network(args, torch, dist, rank, world, local):
     if not args.no_autotune:
         t0 = time.perf_counter()
         ch = tnw.autotune(pairs, sliced, mode, reps=10)
-        tuned = {"seconds": round(time.perf_counter() - t0, 3), "tensor_core": ch.count(8) + ch.count(9), "tensor_core_128col": ch.count(9),
+        tuned = {"seconds": round(time.perf_counter() - t0, 3),
+                 "tensor_core": ch.count(8) + ch.count(9) + ch.count(10), "tensor_core_128col": ch.count(9),
+                 "tensor_core_planar": ch.count(10),
                  "tile_shapes": {n: ch.count(v) for v, n in
                                  ((1, "64x64"), (2, "16x256"), (3, "4x1024"), (4, "256x16"), (6, "128x64"))
                                  if ch.count(v)}}
@@ -590,7 +592,7 @@ def run_network(args, torch, dist, rank, world, local):
             t_e2e += time.perf_counter() - t0
         h2d = sum(int(t.numel()) * elem for t in hl)
         d2h = hout.numel() * hout.element_size() + 8
-        e2e = {"value": flops_step / t_e2e / 1e12, "unit": "TFLOP/s",
+        e2e = {"value": flops_step * args.steps / t_e2e / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": t_e2e / args.steps * 1e3}
         htn.close()

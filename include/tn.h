@@ -393,9 +393,13 @@ tn_status tn_plan_info(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,
  * can run skip the CUDA-core shapes.  The leaves must be attached; their
  * values do not matter.  choice (NULL or n_tensors-1 entries) receives per
  * node 0 (not tuned), 1..4 or 6 (tile shapes 64x64, 16x256, 4x1024,
- * 256x16, 128x64), 8 (tensor core) or 9 (tensor core with 128-column
+ * 256x16, 128x64), 8 (tensor core), 9 (tensor core with 128-column
  * tiles where the planner's 256-column tiles fit: twice the CTAs, for
- * nodes with few tiles).  Synchronises `stream`.  Errors as tn_contract.
+ * nodes with few tiles) or 10 (tensor core on the planar complex layout:
+ * Re and Im planes of both operands, four real products per complex one
+ * without interleaving or expanding either operand; complex nodes in a
+ * split precision with at least 128 complex rows and columns).
+ * Synchronises `stream`.  Errors as tn_contract.
  * Not in the paper: its executor has no kernel choices to tune.
  */
 tn_status tn_autotune(tn_net *net, const int32_t *tree_pairs, int32_t n_sliced,

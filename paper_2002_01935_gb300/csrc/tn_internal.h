@@ -127,6 +127,8 @@ struct alignas(16) TileArgs {
     unsigned long long* t_done;  // root of a batched network: completion time (ns)
     int tc_swap;          // tensor-core node: B plays the row role (see TcGeom)
     int tc_bn128;         // tensor-core node: 128-column GEMM tiles even where 256 fit
+    int tc_planar;        // tensor-core node: planar complex layout (see TcGeom)
+    int pad_tc;
     InstanceInfo in;
 };
 
@@ -142,6 +144,16 @@ struct alignas(16) TileArgs {
 // one k-block of one operand is a single contiguous bulk copy.  Split
 // precisions store a hi plane then a lo plane.  With a K split (split > 1)
 // the FP32 partial products [split][batch][M][N] follow the packed planes.
+//
+// Planar layout (tc_planar: complex nodes in a split precision with at least
+// 128 complex rows and columns): neither operand is interleaved or expanded.
+// R and Q each hold four planes -- Re hi, Re lo, Im hi, Im lo -- of
+// [batch x rows] x K complex entries, cut into 8 KB tiles of 128 rows x one
+// 64-byte swizzled row of K; the GEMM forms Re C = Re R Re Q - Im R Im Q and
+// Im C = Re R Im Q + Im R Re Q as real products (the minus sign by the MMA's
+// negate-A bit) into two accumulators.  Per unit of work this moves two
+// thirds of the 4M layout's operand bytes, and the smaller stages leave room
+// for a deeper pipeline.
 struct TcGeom {
     int64_t rows_r;    // rows of R per batch entry
     int64_t cols_q;    // real rows of Q per batch entry
@@ -156,19 +168,29 @@ struct TcGeom {
     int64_t part_off;  // bytes: start of the split-K partials
     int64_t total;     // bytes per instance, 1 KB aligned
     int bn;            // GEMM tile columns: 256 where the columns allow, else 128
+                       // (planar: 128 complex columns)
+    int row_bytes;     // bytes of one K row of a tile: 128, or 64 (planar)
+    int planar;        // planar complex layout
 };
 
 // Tile plan of one operand pack (tensor-core path), computed on the host:
 // a tile is 2^t entries (t <= 10), enumerated in source order by the
-// src_add offsets and in packed order by dst_add (packed index) and
-// idx_add (stage index); the u remaining bits step between tiles.
+// src_add offsets and in packed order by dst_pos (byte position in the
+// packed planes) and idx_add (stage index); the u remaining bits step
+// between tiles.  The byte position of an entry in the packed planes is the
+// XOR of one constant per set bit of its packed index (K bits, then row
+// bits, then batch bits): every size is a power of two, so tiles and rows
+// are bit fields and the swizzle XORs row bits into chunk bits.  pos_row1:
+// the position XOR from a complex column's first expanded row to its second
+// (4M layout of Q).
 struct PackPlan {
     int t, u;
     int64_t src_add[10];
-    int64_t dst_add[10];
+    int64_t dst_pos[10];
     int32_t idx_add[10];
     int64_t rest_src[kMaxBits];  // an operand has at most 2^40 entries
-    int64_t rest_dst[kMaxBits];
+    int64_t rest_pos[kMaxBits];
+    int64_t pos_row1;
 };
 
 // Tile plan of an inner-product node (k_dot), computed on the host: a tile
@@ -212,22 +234,24 @@ __host__ __device__ inline int tc_prec_of_node(const TileArgs& a, bool cplx, int
 __host__ __device__ inline TcGeom tc_geom(const TileArgs& a, bool cplx, int prec) {
     TcGeom g;
     prec = tc_prec_of_node(a, cplx, prec);
-    const int c = cplx && prec != 3 ? 2 : 1;
+    g.planar = a.tc_planar ? 1 : 0;
+    const int c = cplx && prec != 3 && !g.planar ? 2 : 1;
     g.rows_r = int64_t(1) << (a.tc_swap ? a.nn : a.nm);
     g.cols_q = (int64_t(1) << (a.tc_swap ? a.nm : a.nn)) * c;
     g.kr = (int64_t(1) << a.nk) * c;
     g.esz = tc_esz_of_prec(prec);
-    g.ke = 128 / g.esz;
+    g.row_bytes = g.planar ? 64 : 128;
+    g.ke = g.row_bytes / g.esz;
     g.nkb = (g.kr + g.ke - 1) / g.ke;
-    g.parts = prec == 0 ? 1 : (prec == 3 ? 3 : 2);
-    g.plane_r = a.nbatch * g.rows_r * g.nkb * 128;
-    g.plane_q = a.nbatch * g.cols_q * g.nkb * 128;
+    g.parts = g.planar ? 4 : (prec == 0 ? 1 : (prec == 3 ? 3 : 2));
+    g.plane_r = a.nbatch * g.rows_r * g.nkb * g.row_bytes;
+    g.plane_q = a.nbatch * g.cols_q * g.nkb * g.row_bytes;
     g.region_r = (g.parts * g.plane_r + 1023) / 1024 * 1024;
     g.part_off = g.region_r + (g.parts * g.plane_q + 1023) / 1024 * 1024;
     const int64_t parts_bytes =
         a.split > 1 ? (int64_t)a.split * a.nbatch * (int64_t(1) << (a.nm + a.nn)) * 4 * (cplx ? 2 : 1) : 0;
     g.total = g.part_off + (parts_bytes + 1023) / 1024 * 1024;
-    g.bn = (prec != 3 && g.cols_q % 256 == 0 && !a.tc_bn128) ? 256 : 128;
+    g.bn = g.planar ? 128 : ((prec != 3 && g.cols_q % 256 == 0 && !a.tc_bn128) ? 256 : 128);
     return g;
 }
 

@@ -215,8 +215,11 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems, 
         if (t.nbatch > 65535) return false;
         const int64_t outs = M * N * t.nbatch;
         int split = 1;
-        // one K tile (1024 entries) or more per part; about 256 parts in all
-        while (outs * p.copies * split < 256 && (K / (split * 2)) >= 1024 && split < 1024) split *= 2;
+        // one K tile (1024 entries) or more per part; at least four parts per
+        // SM in all (several CTAs per SM keep enough loads in flight for HBM)
+        while (outs * p.copies * split < 4 * (int64_t)sm_count() && (K / (split * 2)) >= 1024 &&
+               split < 4096 && (int64_t)split * 2 * p.copies <= 65535)
+            split *= 2;
         t.split = split;
         t.kchunk = ((K / split + 255) / 256) * 256;
         if (split > 1) split_elems = std::max(split_elems, (int64_t)split * outs);
@@ -1215,6 +1218,14 @@ bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_e
     t.split = 1;
     t.kchunk = int64_t(1) << t.nk;
     const int prec = tc_prec_of_mode(mode);
+    // the planar layout (asked for by the autotuner's planar variant, or for
+    // every eligible node by the diagnostic switch TN_PLANAR=1, read when a
+    // plan is built) needs a complex node in a split precision with >= 128
+    // complex rows and columns
+    if (const char* e = getenv("TN_PLANAR"))
+        if (e[0] == '1') t.tc_planar = 1;
+    t.tc_planar = (t.tc_planar && c && (prec == 1 || prec == 2 || prec == 4) && t.nm >= 7 && t.nn >= 7 &&
+                   !t.tc_bn128) ? 1 : 0;
     // K split: the grid should fill whole waves of the SMs (one CTA
     // each); split only while every part keeps >= 8 k-blocks
     {
@@ -1252,9 +1263,10 @@ static bool make_variant(const NetDesc& d, const Plan& p, int k, int v, Node& ou
                          int split_mult = 1) {
     const Node& nd = p.nodes[k];
     Node t = nd;
-    const bool tcv = v == kVariantTC || v == kVariantTC128;
+    const bool tcv = v == kVariantTC || v == kVariantTC128 || v == kVariantTCPlanar;
     if (!plan_tile(d, p, t, split_elems, tcv ? 0 : v)) return false;
     if (v == kVariantTC128) t.tile.tc_bn128 = 1;
+    if (v == kVariantTCPlanar) t.tile.tc_planar = 1;
     if (t.tile.cfg == kTileDot) return false;
     t.kind = kTiled;
     if (tcv && !make_tensor_core(d, p.mode, t, split_elems)) return false;
@@ -1324,9 +1336,20 @@ tn_status autotune_plan(NetDesc& d, Plan& p, int reps, int32_t* choice, cudaStre
                 t1.tile.split = 1;
                 cand[k].push_back({kVariantTC, t1});
             }
+            // the planar layout (complex nodes in a split precision)
+            Node tpl;
+            if (make_variant(d, p, k, kVariantTCPlanar, tpl, split_elems) && tpl.tile.tc_planar) {
+                cand[k].push_back({kVariantTCPlanar, tpl});
+                if (tpl.tile.split > 1) {
+                    Node t1 = tpl;
+                    t1.tile.split = 1;
+                    cand[k].push_back({kVariantTCPlanar, t1});
+                }
+            }
             // 128-column tiles where 256 were chosen: twice the CTAs
             Node tn;
-            if (tc_geom(tc.tile, d.is_complex(), tc_prec_of_mode(p.mode)).bn == 256 &&
+            const TcGeom g_tc = tc_geom(tc.tile, d.is_complex(), tc_prec_of_mode(p.mode));
+            if (g_tc.bn == 256 &&
                 make_variant(d, p, k, kVariantTC128, tn, split_elems)) {
                 cand[k].push_back({kVariantTC128, tn});
                 if (tn.tile.split > 1) {

@@ -171,6 +171,9 @@ constexpr int kVariantTC = 8;
 // ... and of the tensor-core kernel with 128-column tiles (twice the tiles:
 // a fuller grid for nodes with few).
 constexpr int kVariantTC128 = 9;
+// ... and of the tensor-core kernel on the planar complex layout (split
+// precisions, >= 128 complex rows and columns).
+constexpr int kVariantTCPlanar = 10;
 // Times every candidate kernel of the nodes that run alone in a launch step
 // and keeps the fastest in the plan (device state must be allocated).
 tn_status autotune_plan(NetDesc& d, Plan& p, int reps, int32_t* choice, cudaStream_t s, std::string& err);

@@ -295,6 +295,31 @@ __device__ __forceinline__ int64_t tile_pos(int64_t row, int64_t k, int64_t nkb,
     return tile * kTileBytes + swz((int)(row & 127), byte >> 4) + (byte & 15);
 }
 
+// The same for the planar layout's 8 KB tiles: 128 rows x one 64-byte row
+// of K in the 64-byte swizzle (16-byte chunk c of row r stored at chunk
+// c ^ ((r >> 1) & 3); 8-row atoms of 512 bytes).
+__device__ __forceinline__ uint32_t swz64(int row, int chunk) {
+    return (uint32_t)((row >> 3) * 512 + (row & 7) * 64 + ((chunk ^ ((row >> 1) & 3)) << 4));
+}
+
+__device__ __forceinline__ int64_t tile_pos64(int64_t row, int64_t k, int64_t nkb, int lg_ke, int lg_esz) {
+    const int64_t tile = (row >> 7) * nkb + (k >> lg_ke);
+    const int byte = (int)(k & ((1 << lg_ke) - 1)) << lg_esz;
+    return tile * (kTileBytes / 2) + swz64((int)(row & 127), byte >> 4) + (byte & 15);
+}
+
+// UMMA shared-memory descriptor for the planar tiles: K-major, 64-byte
+// swizzle, 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)4 << 61;              // SWIZZLE_64B
+    return d;
+}
+
 // Write the packed elements (x, y) (adjacent along K) at byte position pos
 // of the hi plane and of the lo plane lo_off bytes later.
 template <int PREC>
@@ -379,7 +404,7 @@ __global__ void __launch_bounds__(kPackThreads)
     const bool conj = useB ? a.conj_b : a.conj_a;
 
     // the tile tables: source offset of each source-order index, packed
-    // index and (padded) stage index of each packed-order index
+    // byte position and (padded) stage index of each packed-order index
     const int t = pp.t, u = pp.u;
     const int tsz = 1 << t;
     for (int i = threadIdx.x; i < tsz; i += blockDim.x) {
@@ -388,7 +413,7 @@ __global__ void __launch_bounds__(kPackThreads)
         for (int j = 0; j < t; ++j)
             if ((i >> j) & 1) {
                 so += pp.src_add[j];
-                dg += pp.dst_add[j];
+                dg ^= pp.dst_pos[j];
                 idx += pp.idx_add[j];
             }
         tsrc[i] = so;
@@ -406,7 +431,7 @@ __global__ void __launch_bounds__(kPackThreads)
         for (int j = 0; j < u; ++j)
             if ((tile >> j) & 1) {
                 sb += pp.rest_src[j];
-                gb += pp.rest_dst[j];
+                gb ^= pp.rest_pos[j];
             }
     };
     constexpr int R = kPackMaxTile / kPackThreads;
@@ -443,42 +468,27 @@ __global__ void __launch_bounds__(kPackThreads)
             const int i = threadIdx.x + r * kPackThreads;
             if (i >= tsz) break;
             const T v = stage[tidx[i]];
-            const int64_t g = gbase + tdst[i];
-            const int64_t row = g >> nk, k = g & (K - 1);
+            const int64_t pos = gbase ^ tdst[i];  // byte position in the first plane
             if constexpr (CPLX && PREC == 3) {
                 // 3M: planes Re, Im, Re + Im of either operand, K not doubled
                 const float re = v.x * f, im = (conj ? -v.y : v.y) * f;
-                const int64_t pos = tile_pos(row, k, geo.nkb, LG_KE, LG_ESZ);
                 put1<0>(hi, 0, pos, re);
                 put1<0>(hi + lo_off, 0, pos, im);
                 put1<0>(hi + 2 * lo_off, 0, pos, re + im);
-                for (int64_t z = k + geo.kr; z < (int64_t)1 << LG_KE; z += geo.kr) {
-                    const int64_t pz = tile_pos(row, z, geo.nkb, LG_KE, LG_ESZ);
-                    put1<0>(hi, 0, pz, 0.f);
-                    put1<0>(hi + lo_off, 0, pz, 0.f);
-                    put1<0>(hi + 2 * lo_off, 0, pz, 0.f);
-                }
             } else if constexpr (CPLX) {
                 const float re = v.x * f, im = (conj ? -v.y : v.y) * f;
-                if (role == 0) {
-                    put2<PREC>(hi, lo_off, tile_pos(row, 2 * k, geo.nkb, LG_KE, LG_ESZ), re, im);
+                if (geo.planar) {
+                    // planes Re hi, Re lo, Im hi, Im lo of either operand
+                    put1<PREC>(hi, lo_off, pos, re);
+                    put1<PREC>(hi + 2 * lo_off, lo_off, pos, im);
+                } else if (role == 0) {
+                    put2<PREC>(hi, lo_off, pos, re, im);
                 } else {
-                    put2<PREC>(hi, lo_off, tile_pos(2 * row, 2 * k, geo.nkb, LG_KE, LG_ESZ), re, -im);
-                    put2<PREC>(hi, lo_off, tile_pos(2 * row + 1, 2 * k, geo.nkb, LG_KE, LG_ESZ), im, re);
-                }
-                // K shorter than one 128-byte row: zero the rest of the row
-                for (int64_t z = 2 * k + geo.kr; z < (int64_t)1 << LG_KE; z += geo.kr) {
-                    if (role == 0) {
-                        put2<PREC>(hi, lo_off, tile_pos(row, z, geo.nkb, LG_KE, LG_ESZ), 0.f, 0.f);
-                    } else {
-                        put2<PREC>(hi, lo_off, tile_pos(2 * row, z, geo.nkb, LG_KE, LG_ESZ), 0.f, 0.f);
-                        put2<PREC>(hi, lo_off, tile_pos(2 * row + 1, z, geo.nkb, LG_KE, LG_ESZ), 0.f, 0.f);
-                    }
+                    put2<PREC>(hi, lo_off, pos, re, -im);
+                    put2<PREC>(hi, lo_off, pos ^ pp.pos_row1, im, re);
                 }
             } else {
-                put1<PREC>(hi, lo_off, tile_pos(row, k, geo.nkb, LG_KE, LG_ESZ), v * f);
-                for (int64_t z = k + geo.kr; z < (int64_t)1 << LG_KE; z += geo.kr)
-                    put1<PREC>(hi, lo_off, tile_pos(row, z, geo.nkb, LG_KE, LG_ESZ), 0.f);
+                put1<PREC>(hi, lo_off, pos, v * f);
             }
         }
         __syncthreads();
@@ -752,6 +762,259 @@ __global__ void __launch_bounds__(64 + BN, 1)
 }
 
 // ---------------------------------------------------------------------------
+// k_umma_planar: complex node in a split precision over the planar layout.
+// A tile is 128 complex rows x 128 complex columns; each stage holds one
+// 64-byte K row of the four planes of R and of Q (8 KB each).  Per K step
+// the MMA thread issues the three split products of Re R Re Q and of
+// Im R Im Q (negated) into the Re C accumulator and of Re R Im Q and Im R
+// Re Q into the Im C accumulator; the accumulator pair rotates between two
+// TMEM halves along K, and the eight epilogue warps drain each finished pair
+// into FP32 registers as k_umma does.  blockIdx.x: output tile (grouped
+// raster), y: K split, z: batch entry and instance.
+// ---------------------------------------------------------------------------
+template <int PREC, int STAGES>
+__global__ void __launch_bounds__(320, 1)
+    k_umma_planar(const __grid_constant__ TileArgs a) {
+    constexpr bool HALF = PREC == 2 || PREC == 4;
+    constexpr int PT = kTileBytes / 2;                   // 8 KB: one plane of one operand
+    constexpr int STAGE_BYTES = 8 * PT;                  // 4 planes of R, 4 of Q
+    constexpr int MMA_K = HALF ? 16 : 8;                 // K per instruction
+    constexpr int KSTEPS = 64 / (MMA_K * (HALF ? 2 : 4));  // 2
+    constexpr uint32_t FMT = PREC == 2 ? 1u : (PREC == 4 ? 0u : 2u);
+    constexpr int NACC = 2;                              // accumulator pairs in rotation
+    constexpr int BNC = 128;                             // complex columns per tile
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ uint64_t acc_full[NACC], acc_empty[NACC];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ int consumed;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int64_t b = blockIdx.z % a.nbatch;
+    const int inst = (int)(blockIdx.z / a.nbatch);
+    const int sp = blockIdx.y, nsplit = gridDim.y;
+    const InstanceInfo& in = a.in;
+    const int64_t slice = a.ctl->slice + (int64_t)inst * in.slice_step;
+    if (slice >= a.ctl->slice_end) return;  // idle instance: before any barrier or TMEM
+    const TcGeom geo = tc_geom(a, true, PREC);
+    const int nkl = (int)(geo.nkb / nsplit);   // k-blocks of this K part
+    const int64_t kb0 = (int64_t)sp * nkl;
+    const int tiles_m = (int)(geo.rows_r / kBM), tiles_n = (int)(geo.cols_q / BNC);
+    int tm, tn;
+    {
+        const int per_group = kGroupRows * tiles_n;
+        const int grp = (int)blockIdx.x / per_group;
+        const int first = grp * kGroupRows;
+        const int gsz = min(kGroupRows, tiles_m - first);
+        const int r = (int)blockIdx.x - grp * per_group;
+        tm = first + r % gsz;
+        tn = r / gsz;
+    }
+    const int row0 = tm * kBM, col0 = tn * BNC;
+    const char* pk = reinterpret_cast<const char*>(a.P) + (int64_t)inst * in.p_is * 8;
+
+    ScaleIO sio = a.sc;
+    if (sio.max_a) sio.max_a += (int64_t)inst * in.sa_is;
+    if (sio.exp_a) sio.exp_a += (int64_t)inst * in.sa_is;
+    if (sio.max_b) sio.max_b += (int64_t)inst * in.sb_is;
+    if (sio.exp_b) sio.exp_b += (int64_t)inst * in.sb_is;
+    sio.max_c += (int64_t)inst * in.sc_is;
+    sio.exp_c += (int64_t)inst * in.sc_is;
+    const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
+    const int resid = (eA - max(-120, min(120, eA))) + (eB - max(-120, min(120, eB))) +
+                      (PREC == 4 ? 2 * kF16Shift : 0);
+    if (blockIdx.x == 0 && sp == 0 && b == 0 && tid == 0 && sio.exp_c)
+        *sio.exp_c = (sio.exp_a ? *sio.exp_a : 0) + (sio.exp_b ? *sio.exp_b : 0) + eA + eB;
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        for (int q = 0; q < NACC; ++q) {
+            mbar_init(&acc_full[q], 1);
+            mbar_init(&acc_empty[q], 8);  // one arrival per epilogue warp
+        }
+        abort_flag = 0;
+        consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(512u));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        // ---------------- bulk-copy producer ----------------
+        if (tid == 0) {
+            const char* r_src = pk + ((b * tiles_m + tm) * geo.nkb + kb0) * PT;
+            const char* q_src = pk + geo.region_r + ((b * tiles_n + tn) * geo.nkb + kb0) * PT;
+            int issued = 0;
+            for (int j = 0; j < nkl; ++j) {
+                const int s = j % STAGES;
+                if (j >= STAGES &&
+                    !mbar_wait(&empty_bar[s], (uint32_t)(((j / STAGES) + 1) & 1), &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                uint8_t* st = smem + s * STAGE_BYTES;
+                mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+                const int64_t o = (int64_t)j * PT;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    bulk_load(st + p * PT, r_src + p * geo.plane_r + o, PT, &full_bar[s]);
+                    bulk_load(st + (4 + p) * PT, q_src + p * geo.plane_q + o, PT, &full_bar[s]);
+                }
+                ++issued;
+            }
+            if (abort_flag) {
+                int dummy = 0;
+                for (int j = *(volatile int*)&consumed; j < issued; ++j)
+                    mbar_wait(&full_bar[j % STAGES], (uint32_t)((j / STAGES) & 1), &dummy);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (tid == 32) {
+            const uint32_t idesc = instr_desc(FMT, kBM, BNC);
+            const uint32_t idesc_neg = idesc | (1u << 13);  // negate A: - Im R Im Q
+            for (int j = 0; j < nkl; ++j) {
+                const int s = j % STAGES;
+                if (!mbar_wait(&full_bar[s], (uint32_t)((j / STAGES) & 1), &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                const int q = j % NACC;
+                // an accumulator pair is reused once the epilogue has drained it
+                if (j >= NACC && !mbar_wait(&acc_empty[q], (uint32_t)(((j / NACC) + 1) & 1), &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+                const uint32_t d_re = tmem + (uint32_t)(q * 2 * BNC), d_im = d_re + (uint32_t)BNC;
+#pragma unroll
+                for (int k = 0; k < KSTEPS; ++k) {
+                    const uint32_t off = k * 32;
+                    const uint64_t rrh = smem_desc64(base + 0 * PT + off), rrl = smem_desc64(base + 1 * PT + off);
+                    const uint64_t rih = smem_desc64(base + 2 * PT + off), ril = smem_desc64(base + 3 * PT + off);
+                    const uint64_t qrh = smem_desc64(base + 4 * PT + off), qrl = smem_desc64(base + 5 * PT + off);
+                    const uint64_t qih = smem_desc64(base + 6 * PT + off), qil = smem_desc64(base + 7 * PT + off);
+                    const uint32_t acc0 = k > 0 ? 1u : 0u;
+                    mma<HALF>(d_re, rrh, qrh, idesc, acc0);
+                    mma<HALF>(d_im, rrh, qih, idesc, acc0);
+                    mma<HALF>(d_re, rrh, qrl, idesc, 1u);
+                    mma<HALF>(d_im, rrh, qil, idesc, 1u);
+                    mma<HALF>(d_re, rrl, qrh, idesc, 1u);
+                    mma<HALF>(d_im, rrl, qih, idesc, 1u);
+                    mma<HALF>(d_re, rih, qih, idesc_neg, 1u);
+                    mma<HALF>(d_im, rih, qrh, idesc, 1u);
+                    mma<HALF>(d_re, rih, qil, idesc_neg, 1u);
+                    mma<HALF>(d_im, rih, qrl, idesc, 1u);
+                    mma<HALF>(d_re, ril, qih, idesc_neg, 1u);
+                    mma<HALF>(d_im, ril, qrh, idesc, 1u);
+                }
+                mma_commit(&empty_bar[s]);
+                mma_commit(&acc_full[q]);
+                *(volatile int*)&consumed = j + 1;
+            }
+            mma_commit(&done_bar);  // arrives once every MMA issued above has completed
+        }
+    } else {
+        // ---------------- epilogue (warps 2..9) ----------------
+        float lmax = 0.f;
+        const int quad = warp & 3;                 // TMEM lanes 32*quad.. belong to this warp
+        const int cbase = ((warp - 2) >> 2) * 64;  // this warp's 64 of the 128 complex columns
+        float sre[64], sim[64];
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+            sre[i] = 0.f;
+            sim[i] = 0.f;
+        }
+        bool ok = true;
+        for (int j = 0; j < nkl && ok; ++j) {
+            const int q = j % NACC;
+            const bool got = mbar_wait(&acc_full[q], (uint32_t)((j / NACC) & 1), &abort_flag);
+            ok = __all_sync(0xffffffffu, got && !abort_flag);  // tcgen05.ld is warp-collective
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(q * 2 * BNC + cbase);
+            tmem_add32(ta, sre);
+            tmem_add32(ta + 32u, sre + 32);
+            tmem_add32(ta + (uint32_t)BNC, sim);
+            tmem_add32(ta + (uint32_t)BNC + 32u, sim + 32);
+            tc_fence_before();
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(&acc_empty[q]);
+        }
+        if (ok) {
+            const int row = row0 + quad * 32 + (tid & 31);
+            const int64_t M = int64_t(1) << a.nm, N = int64_t(1) << a.nn;
+            float* C = nsplit > 1
+                           ? reinterpret_cast<float*>(const_cast<char*>(pk) + geo.part_off) +
+                                 (int64_t)sp * a.nbatch * M * N * 2
+                           : reinterpret_cast<float*>(a.C) + (int64_t)inst * in.c_is * 2;
+            const int rs = nsplit > 1 ? 0 : resid;
+#pragma unroll
+            for (int i = 0; i < 64; ++i) {
+                if (rs) {
+                    sre[i] = ldexpf(sre[i], -rs);
+                    sim[i] = ldexpf(sim[i], -rs);
+                }
+                lmax = fmaxf(lmax, fmaxf(fabsf(sre[i]), fabsf(sim[i])));
+            }
+            const int64_t j0 = col0 + cbase;  // first complex column of this warp
+            if (!a.tc_swap) {
+                float* crow = C + ((b * M + row) * N + j0) * 2;
+#pragma unroll
+                for (int i = 0; i < 64; i += 2)
+                    *reinterpret_cast<float4*>(crow + 2 * i) = make_float4(sre[i], sim[i], sre[i + 1], sim[i + 1]);
+            } else {
+                // rows run over N, complex columns over M
+#pragma unroll
+                for (int i = 0; i < 64; ++i)
+                    *reinterpret_cast<float2*>(C + ((b * M + j0 + i) * N + row) * 2) = make_float2(sre[i], sim[i]);
+            }
+        } else if ((tid & 31) == 0) {
+            atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
+        }
+        if (nsplit == 1) {
+            for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+            if ((tid & 31) == 0 && lmax > 0.f) atomicMax(sio.max_c, __float_as_uint(lmax));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        // no MMA may still write the accumulators when they are freed
+        int dummy = 0;
+        bool quiet = true;
+        if (tid == 32) quiet = mbar_wait(&done_bar, 0u, &dummy);
+        quiet = __shfl_sync(0xffffffffu, quiet, 0);
+        tc_fence_after();
+        if (!quiet && tid == 32) atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
+    }
+    if (a.t_done && tid == 0 && nsplit == 1) {
+        unsigned long long tnow;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tnow));
+        atomicMax(a.t_done, tnow);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_umma3m: complex node as three real TF32 GEMMs (3M) over the Re, Im and
 // Re + Im planes of R and Q, one accumulator each (128 complex columns per
 // tile); the epilogue forms Re C = T1 - T2 and Im C = T3 - T1 - T2.
@@ -999,15 +1262,55 @@ __global__ void __launch_bounds__(256) k_tc_reduce(const __grid_constant__ TileA
 // ---------------------------------------------------------------------------
 namespace {
 
+// Host copies of the tile layouts (swz, swz64 above).
+inline int64_t host_swz128(int64_t row, int64_t chunk) {
+    return (row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4);
+}
+inline int64_t host_swz64(int64_t row, int64_t chunk) {
+    return (row >> 3) * 512 + (row & 7) * 64 + ((chunk ^ ((row >> 1) & 3)) << 4);
+}
+
+// Byte position in the first packed plane of operand entry (row, k) (row
+// counts batch entries x rows, k the complex or real K index), for the
+// layout the kernels read: planar, 3M, 4M (R interleaves (re, im) along K,
+// Q's column c becomes rows 2c and 2c + 1) or real.
+int64_t packed_pos(const TcGeom& g, int prec, bool cplx, int role, int64_t row, int64_t k) {
+    const int lg_esz = g.esz == 2 ? 1 : 2;
+    if (g.planar) {
+        const int lg_ke = 6 - lg_esz;
+        const int64_t tile = (row >> 7) * g.nkb + (k >> lg_ke);
+        const int64_t byte = (k & ((int64_t(1) << lg_ke) - 1)) << lg_esz;
+        return tile * (kTileBytes / 2) + host_swz64(row & 127, byte >> 4) + (byte & 15);
+    }
+    int64_t rr = row, kk = k;
+    if (cplx && prec != 3) {
+        kk = 2 * k;
+        if (role == 1) rr = 2 * row;
+    }
+    const int lg_ke = 7 - lg_esz;
+    const int64_t tile = (rr >> 7) * g.nkb + (kk >> lg_ke);
+    const int64_t byte = (kk & ((int64_t(1) << lg_ke) - 1)) << lg_esz;
+    return tile * kTileBytes + host_swz128(rr & 127, byte >> 4) + (byte & 15);
+}
+
 // Tile bits of a pack (role 0: R, 1: Q): the kPackLow lowest packed
 // positions and the kPackLow lowest source strides, filled up with the next
 // packed positions to 2 * kPackLow bits; the other bits enumerate tiles.
-PackPlan make_pack_plan(const TileArgs& a, int role) {
+// Destination byte positions: one XOR constant per packed-index bit.
+PackPlan make_pack_plan(const TileArgs& a, int role, int prec, bool cplx) {
     PackPlan pp;
     memset(&pp, 0, sizeof(pp));
     const bool useB = (role == 0) == (a.tc_swap != 0);
     const int nk = a.nk, no = useB ? a.nn : a.nm, nb = a.nb;
     const int nbits = nk + no + nb;
+    const TcGeom geo = tc_geom(a, cplx, prec);
+    int64_t lpos[3 * kMaxBits];
+    for (int p = 0; p < nbits; ++p) {
+        const int64_t row = p >= nk ? int64_t(1) << (p - nk) : 0;
+        const int64_t k = p < nk ? int64_t(1) << p : 0;
+        lpos[p] = packed_pos(geo, prec, cplx, role, row, k);
+    }
+    pp.pos_row1 = host_swz128(1, 0);  // row 2c + 1 of the 4M layout from row 2c
     const uint8_t* xk = useB ? a.b_k : a.a_k;
     const uint8_t* xo = useB ? a.b_n : a.a_m;
     const uint8_t* xb = useB ? a.b_b : a.a_b;
@@ -1038,7 +1341,7 @@ PackPlan make_pack_plan(const TileArgs& a, int role) {
             td[t++] = p;
         } else {
             pp.rest_src[u] = shift[p] < 64 ? int64_t(1) << shift[p] : 0;
-            pp.rest_dst[u] = int64_t(1) << p;
+            pp.rest_pos[u] = lpos[p];
             ++u;
         }
     }
@@ -1051,7 +1354,7 @@ PackPlan make_pack_plan(const TileArgs& a, int role) {
         if (shift[td[i]] >= 64) ts[w++] = td[i];
     for (int j = 0; j < t; ++j) {
         pp.src_add[j] = shift[ts[j]] < 64 ? int64_t(1) << shift[ts[j]] : 0;
-        pp.dst_add[j] = int64_t(1) << td[j];
+        pp.dst_pos[j] = lpos[td[j]];
         int r = 0;
         while (ts[r] != td[j]) ++r;
         pp.idx_add[j] = 1 << r;
@@ -1077,10 +1380,16 @@ cudaError_t launch_tc_3m(const TileArgs& a, cudaStream_t s) {
     const int64_t elems_a = int64_t(1) << (a.nk + a.nm + a.nb);
     const int64_t elems_b = int64_t(1) << (a.nk + a.nn + a.nb);
     auto blocks = [ni](int64_t n) { return pack_blocks(n, ni); };
+    if (g.kr < g.ke) {
+        // K shorter than one packed row: the rest of every row must be zero
+        const size_t pitch = (size_t)(a.in.n_inst > 1 ? a.in.p_is * 8 : g.part_off);
+        cudaError_t e0 = cudaMemset2DAsync(a.P, pitch, 0, (size_t)g.part_off, (size_t)ni, s);
+        if (e0 != cudaSuccess) return e0;
+    }
     {
         const unsigned br = blocks(a.tc_swap ? elems_b : elems_a), bq = blocks(a.tc_swap ? elems_a : elems_b);
-        k_pack<true, 3><<<dim3(br + bq, ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 0), make_pack_plan(a, 1),
-                                                                 (int)br);
+        k_pack<true, 3><<<dim3(br + bq, ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 0, 3, true),
+                                                                 make_pack_plan(a, 1, 3, true), (int)br);
     }
     const int64_t tiles = (g.rows_r / kBM) * (g.cols_q / kBN);
     k_umma3m<STAGES><<<dim3((unsigned)tiles, (unsigned)split, (unsigned)(a.nbatch * ni)), kGemmThreads, SMEM, s>>>(a);
@@ -1113,6 +1422,22 @@ cudaError_t launch_umma(const TileArgs& a, dim3 grid, int nacc, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+// planar layout: 64 KB stages, three in flight
+template <int PREC>
+cudaError_t launch_umma_planar(const TileArgs& a, dim3 grid, cudaStream_t s) {
+    constexpr int STAGES = 3;
+    constexpr int SMEM = STAGES * 8 * (kTileBytes / 2) + 1024;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_umma_planar<PREC, STAGES>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_umma_planar<PREC, STAGES><<<grid, 320, SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <bool CPLX, int PREC>
 cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     const TcGeom g = tc_geom(a, CPLX, PREC);
@@ -1123,16 +1448,32 @@ cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     const int64_t elems_b = int64_t(1) << (a.nk + a.nn + a.nb);
     auto blocks = [ni](int64_t n) { return pack_blocks(n, ni); };
     const int64_t n_r = a.tc_swap ? elems_b : elems_a, n_q = a.tc_swap ? elems_a : elems_b;
+    if (g.kr < g.ke) {
+        // K shorter than one packed row: the rest of every row must be zero
+        const size_t pitch = (size_t)(a.in.n_inst > 1 ? a.in.p_is * (CPLX ? 8 : 4) : g.part_off);
+        cudaError_t e0 = cudaMemset2DAsync(a.P, pitch, 0, (size_t)g.part_off, (size_t)ni, s);
+        if (e0 != cudaSuccess) return e0;
+    }
     k_pack<CPLX, PREC><<<dim3(blocks(n_r) + blocks(n_q), ni), kPackThreads, 0, s>>>(
-        a, make_pack_plan(a, 0), make_pack_plan(a, 1), (int)blocks(n_r));
+        a, make_pack_plan(a, 0, PREC, CPLX), make_pack_plan(a, 1, PREC, CPLX), (int)blocks(n_r));
     const int nkl = (int)(g.nkb / split);
     const int chains = PREC == 0 ? (nkl + 3) / 4 : nkl;
     const int max_acc = 512 / g.bn;
     const int nacc = chains >= max_acc ? max_acc : (chains >= 2 ? 2 : 1);
     const int64_t tiles = (g.rows_r / kBM) * (g.cols_q / g.bn);
     dim3 grid((unsigned)tiles, (unsigned)split, (unsigned)(a.nbatch * ni));
-    cudaError_t e = g.bn == 256 ? launch_umma<CPLX, PREC, 256>(a, grid, nacc, s)
-                                : launch_umma<CPLX, PREC, 128>(a, grid, nacc, s);
+    cudaError_t e;
+    if constexpr (CPLX && (PREC == 1 || PREC == 2 || PREC == 4)) {
+        if (g.planar) {
+            e = launch_umma_planar<PREC>(a, grid, s);
+        } else {
+            e = g.bn == 256 ? launch_umma<CPLX, PREC, 256>(a, grid, nacc, s)
+                            : launch_umma<CPLX, PREC, 128>(a, grid, nacc, s);
+        }
+    } else {
+        e = g.bn == 256 ? launch_umma<CPLX, PREC, 256>(a, grid, nacc, s)
+                        : launch_umma<CPLX, PREC, 128>(a, grid, nacc, s);
+    }
     if (e != cudaSuccess) return e;
     if (split > 1) {
         const int64_t n4 = (a.nbatch << (a.nm + a.nn)) * (CPLX ? 2 : 1) / 4;

@@ -468,14 +468,21 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a,
     const int64_t per = (n_tiles + a.split - 1) / a.split;
     const int64_t t0 = (int64_t)sp * per, t1 = min64(n_tiles, t0 + per);
     T acc0 = zero<T>(), acc1 = zero<T>();
-    for (int64_t tile = t0; tile < t1; ++tile) {
-        int64_t ba = baseA, bb = baseB;
+    // the loads of the next tile are issued before the current one is
+    // multiplied (two tiles of reads in flight per thread)
+    auto tile_base = [&](int64_t tile, int64_t& ba, int64_t& bb) {
+        ba = baseA;
+        bb = baseB;
         for (int j = 0; j < u; ++j)
             if ((tile >> j) & 1) {
                 ba += dp.rest_a[j];
                 bb += dp.rest_b[j];
             }
-        T xa[kDotTile / 256], xb[kDotTile / 256];
+    };
+    T xa[kDotTile / 256], xb[kDotTile / 256];
+    if (t0 < t1) {
+        int64_t ba, bb;
+        tile_base(t0, ba, bb);
 #pragma unroll
         for (int r = 0; r < kDotTile / 256; ++r) {
             const int e = threadIdx.x + r * 256;
@@ -484,6 +491,8 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a,
                 xb[r] = B[bb + offB[e]];
             }
         }
+    }
+    for (int64_t tile = t0; tile < t1; ++tile) {
 #pragma unroll
         for (int r = 0; r < kDotTile / 256; ++r) {
             const int e = threadIdx.x + r * 256;
@@ -493,6 +502,18 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a,
             }
         }
         __syncthreads();
+        if (tile + 1 < t1) {
+            int64_t ba, bb;
+            tile_base(tile + 1, ba, bb);
+#pragma unroll
+            for (int r = 0; r < kDotTile / 256; ++r) {
+                const int e = threadIdx.x + r * 256;
+                if (e < tsz) {
+                    xa[r] = A[ba + offA[e]];
+                    xb[r] = B[bb + offB[e]];
+                }
+            }
+        }
 #pragma unroll
         for (int r = 0; r < kDotTile / 256; ++r) {
             const int i = threadIdx.x + r * 256;

@@ -119,3 +119,36 @@ def test_circuit_5x5_modes(torch, mode):
     ref = complex(mo) * 2.0 ** eo
     err = abs(complex(m) * 2.0 ** e - ref) / abs(ref)
     assert err <= NET_TOL[mode], err
+
+
+@pytest.mark.parametrize("mode", ["tf32_split", "fp16_split", "bf16_split"])
+@pytest.mark.parametrize("shape", [(8, 8, 8, 0, True), (9, 7, 10, 0, True), (7, 7, 4, 1, True),
+                                   (7, 9, 6, 1, True), (10, 7, 5, 0, True)])
+def test_single_gemm_node_planar_layout(torch, mode, shape, monkeypatch):
+    """The planar complex layout (Re and Im planes, negated Im x Im product)
+    on single complex nodes, incl. batch labels, the swapped orientation and
+    K shorter than one 64-byte row (K = 16)."""
+    monkeypatch.setenv("TN_PLANAR", "1")
+    mb, nb, kb, batch, cplx = shape
+    net = gemm_net(mb, nb, kb, batch, cplx, seed=100 + sum(shape))
+    pairs = [(0, 1)]
+    m, e, info = run(torch, net, pairs, mode=mode)
+    assert info["n_tensor_core"] == 1
+    got = m * 2.0 ** e
+    ref = tree.value(net.tensors, net.labels, net.dims, net.open, pairs)
+    scale = tree.value([np.abs(x) for x in net.tensors], net.labels, net.dims, net.open, pairs)
+    err = float(np.max(np.abs(got - ref) / scale))
+    assert err <= TOL[mode], err
+
+
+@pytest.mark.parametrize("mode", ["tf32_split", "fp16_split"])
+def test_circuit_5x5_planar_layout(torch, mode, monkeypatch):
+    monkeypatch.setenv("TN_PLANAR", "1")
+    circ = inputs.random_circuit(5, 5, 10, seed=0)
+    net = inputs.circuit_network(circ, inputs.random_bitstrings(25, 1, seed=1000)[0])
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    m, e, info = run(torch, net, pairs, mode=mode)
+    mo, eo = tree.contract_net(net.as_stored(), pairs)
+    ref = complex(mo) * 2.0 ** eo
+    err = abs(complex(m) * 2.0 ** e - ref) / abs(ref)
+    assert err <= NET_TOL[mode], err
