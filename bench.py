@@ -482,7 +482,7 @@ def run_network(args, torch, dist, rank, world, local):
     from paper_2002_01935_gb300 import binding
 
     if args.workload == "ising100":
-        w = wl_ising(rank, simplified=args.simplify)
+        w = wl_ising(rank, target=args.target_ws, simplified=args.simplify)
     elif args.workload == "ising100_hyper":
         w = wl_ising(rank, hyper=True)
     elif args.workload == "circuit4x4":
@@ -517,9 +517,12 @@ def run_network(args, torch, dist, rank, world, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def call(md=mode, **kw):
-        return tnw.contract(pairs, sliced, md, slice_begin=sb, slice_count=sc, **kw)
+        return tnw.contract(pairs, sliced, md, slice_begin=sb, slice_count=sc, persistent=args.persistent, **kw)
 
     steps = tnw.plan_steps(pairs, sliced, mode)
+    if args.persistent:
+        # the persistent plan is one dataflow launch over every node
+        steps = [{"wave": True, "kind": 1, "cfg": 0, "nodes": list(range(len(pairs))), "launches": 1}]
     n_steps = len(steps)
     for _ in range(args.warmup):
         m, e = call()
@@ -582,13 +585,15 @@ def run_network(args, torch, dist, rank, world, local):
         hout = torch.empty(tnw.out_shape, dtype=odt).pin_memory()
         hexp = torch.empty((), dtype=torch.int64).pin_memory()
         for _ in range(args.warmup):
-            htn.contract(pairs, sliced, mode, out=hout, out_exp=hexp, slice_begin=sb, slice_count=sc)
+            htn.contract(pairs, sliced, mode, out=hout, out_exp=hexp, slice_begin=sb, slice_count=sc,
+                         persistent=args.persistent)
         t_e2e = 0.0
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            htn.contract(pairs, sliced, mode, out=hout, out_exp=hexp, slice_begin=sb, slice_count=sc)
+            htn.contract(pairs, sliced, mode, out=hout, out_exp=hexp, slice_begin=sb, slice_count=sc,
+                         persistent=args.persistent)
             t_e2e += time.perf_counter() - t0
         h2d = sum(int(t.numel()) * elem for t in hl)
         d2h = hout.numel() * hout.element_size() + 8
@@ -656,7 +661,7 @@ def run_network(args, torch, dist, rank, world, local):
                     entry["subslice_rel_err_median"] = statistics.median(errs)
             modes_cmp[md] = entry
 
-    groups = sc
+    groups = 1 if args.persistent else sc
     # our kernels per call: call setup (leaf maxima + control block) and the
     # result copy; per slice group the steps' launches and the accumulation
     # (which also advances the slice counter when it is one block)
@@ -670,7 +675,8 @@ def run_network(args, torch, dist, rank, world, local):
            "plan_kernels": {"generic": plan["n_generic"], "tiled": plan["n_tiled"],
                             "tensor_core": plan["n_tensor_core"]},
            "launch_steps": n_steps, "wave_steps": sum(1 for s in steps if s["wave"]),
-           "workspace_bytes": plan["ws_bytes"], "autotune": tuned}
+           "workspace_bytes": plan["ws_bytes"], "autotune": tuned,
+           "persistent": bool(args.persistent)}
     cfg.update(w["config"])
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
@@ -1264,6 +1270,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="skip the per-mode comparison")
     ap.add_argument("--no-autotune", action="store_true", help="keep the planner's kernel choices")
+    ap.add_argument("--target-ws", type=float, default=24.0,
+                    help="ising100: slice the greedy tree to this width (config 1: 24)")
+    ap.add_argument("--persistent", action="store_true",
+                    help="network workloads: every node of every slice in one persistent launch")
     args = ap.parse_args()
     if args.steps is None:
         short = args.workload in ("ising100", "ising100_hyper", "circuit4x4", "circuit5x5")

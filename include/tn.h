@@ -150,6 +150,19 @@ tn_status tn_set_tensor(tn_net *net, int32_t v, const void *ptr, int32_t mem);
  *       so memory grows by this factor); their results are folded into the
  *       FP64 sum in slice order, so the result does not depend on it.
  *       0 or 1: one slice per launch.
+ *   persistent
+ *       1: the whole call in one persistent dataflow launch (Sec. 4.7.1:
+ *       the slices are independent): every node of every slice of the call
+ *       side by side -- small or narrow nodes as chunks of outputs, nodes
+ *       with >= 32 rows and columns and >= 4096 outputs as 64 x 64 output
+ *       tiles over all of K -- taken in tree order by resident CTAs that
+ *       wait (bounded) for their inputs' completion counters; then one fold
+ *       of the slices' roots, in slice order, into the FP64 result on the
+ *       device.  Every node runs in FP32 on the CUDA cores (the mode's tensor
+ *       cores are not used); slice_batch is ignored (all slices of the call
+ *       run side by side, as many as 8 GiB of workspace copies hold; more
+ *       slices take several such launches).  Needs power-of-two label sizes
+ *       (else TN_EUNSUPPORTED).  0: the per-step launch sequence.
  */
 typedef struct {
     int64_t slice_begin;
@@ -160,7 +173,8 @@ typedef struct {
     int32_t prof_first;
     int32_t prof_count;
     int32_t slice_batch;      /* slices run side by side per launch (>= 1) */
-    int32_t reserved[5];
+    int32_t persistent;       /* 1: one persistent launch for the whole call */
+    int32_t reserved[4];
 } tn_options;
 
 /*

@@ -39,7 +39,7 @@ class tn_options(ctypes.Structure):
                 ("no_graph", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("prof_events", ctypes.POINTER(ctypes.c_void_p)), ("prof_first", ctypes.c_int32),
                 ("prof_count", ctypes.c_int32), ("slice_batch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("persistent", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -220,11 +220,12 @@ def tn_contract_ex(h: int, pairs, sliced, mode: int, out_ptr: int, out_mem: int,
                    stream: int = 0, slice_begin: int = 0, slice_count: int = 0,
                    no_graph: bool = False,
                    prof_events: Optional[Sequence[int]] = None, prof_first: int = 0,
-                   slice_batch: int = 0) -> None:
+                   slice_batch: int = 0, persistent: bool = False) -> None:
     tr = _tree_of(h, pairs)
     sl = _arr(list(sliced) or [0], np.int64)
     opt = tn_options(slice_begin, slice_count, int(no_graph), 0)
     opt.slice_batch = slice_batch
+    opt.persistent = int(bool(persistent))
     if prof_events:
         evs = (ctypes.c_void_p * len(prof_events))(*prof_events)
         opt.prof_events = ctypes.cast(evs, ctypes.POINTER(ctypes.c_void_p))
@@ -457,11 +458,13 @@ class TensorNetwork:
 
     def contract(self, pairs, sliced=(), mode="fp32", out=None, out_exp=None, stream=None,
                  slice_begin=0, slice_count=0, no_graph=False,
-                 prof_events=None, prof_first=0, slice_batch=0):
+                 prof_events=None, prof_first=0, slice_batch=0, persistent=False):
         """Return (mantissa, exp2) torch tensors; value = mantissa * 2**exp2.
 
         Device outputs by default (asynchronous on ``stream``); pass CPU
-        ``out``/``out_exp`` tensors to receive host outputs (synchronous)."""
+        ``out``/``out_exp`` tensors to receive host outputs (synchronous).
+        ``persistent``: the whole call (every node of every slice) in one
+        persistent dataflow launch (FP32 on the CUDA cores)."""
         import torch
         m = MODES[mode] if isinstance(mode, str) else int(mode)
         dev = torch.device("cuda")
@@ -481,7 +484,7 @@ class TensorNetwork:
         s = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
         evp = [e.cuda_event for e in prof_events] if prof_events else None
         tn_contract_ex(self.h, pairs, sliced, m, out.data_ptr(), mem, out_exp.data_ptr(), s,
-                       slice_begin, slice_count, no_graph, evp, prof_first, slice_batch)
+                       slice_begin, slice_count, no_graph, evp, prof_first, slice_batch, persistent)
         return out, out_exp
 
     def grad(self, pairs, sliced, mode, adjoint, adj_exp2=0, grads=None, stream=None,

@@ -140,7 +140,7 @@ tn_status tn_set_tensor(tn_net* net, int32_t v, const void* ptr, int32_t mem) {
 // choices and K splits count the copies (and which the autotuner, timing
 // single copies, leaves alone).
 static tn_status get_plan(tn_net* net, const int32_t* pairs, int32_t n_sliced, const int64_t* sliced,
-                          tn_mode mode, Plan** out, int copies = 1) {
+                          tn_mode mode, Plan** out, int copies = 1, bool persistent = false) {
     NetDesc& d = net->d;
     const int n = d.n;
     if (n > 1 && !pairs) return fail(TN_EINVAL, "tree_pairs is NULL");
@@ -149,7 +149,8 @@ static tn_status get_plan(tn_net* net, const int32_t* pairs, int32_t n_sliced, c
     std::vector<int32_t> pv(pairs, pairs + 2 * (size_t)(n - 1));
     std::vector<int64_t> sv(sliced, sliced + n_sliced);
     for (auto& p : net->plans)
-        if (p->mode == mode && p->pairs == pv && p->sliced_ids == sv && p->copies == copies) {
+        if (p->mode == mode && p->pairs == pv && p->sliced_ids == sv && p->copies == copies &&
+            p->persistent == persistent) {
             *out = p.get();
             return TN_OK;
         }
@@ -159,6 +160,7 @@ static tn_status get_plan(tn_net* net, const int32_t* pairs, int32_t n_sliced, c
     p->pairs = pv;
     p->sliced_ids = sv;
     p->copies = copies;
+    p->persistent = persistent;
     std::string err;
     tn_status st = tn::build_plan(d, *p, err);
     if (st != TN_OK) return fail(st, err);
@@ -207,11 +209,12 @@ tn_status tn_contract_ex(tn_net* net, const int32_t* tree_pairs, int32_t n_slice
     if (out_mem != TN_MEM_DEVICE && out_mem != TN_MEM_HOST) return fail(TN_EINVAL, "bad out_mem");
     for (int v = 0; v < net->d.n; ++v)
         if (!net->d.leaves[v].ptr) return fail(TN_EINVAL, "tn_contract: tensor without data");
-    Plan* p = nullptr;
-    tn_status st = get_plan(net, tree_pairs, n_sliced, sliced_labels, mode, &p);
-    if (st != TN_OK) return st;
     tn_options o{};
     if (opt) o = *opt;
+    if (o.persistent != 0 && o.persistent != 1) return fail(TN_EINVAL, "persistent must be 0 or 1");
+    Plan* p = nullptr;
+    tn_status st = get_plan(net, tree_pairs, n_sliced, sliced_labels, mode, &p, 1, o.persistent == 1);
+    if (st != TN_OK) return st;
     int64_t begin = o.slice_begin, count = o.slice_count;
     if (count <= 0) {
         begin = 0;
@@ -220,7 +223,17 @@ tn_status tn_contract_ex(tn_net* net, const int32_t* tree_pairs, int32_t n_slice
     // (count > 0 here: written so that no sum can overflow)
     if (begin < 0 || begin > p->d_sliced - count) return fail(TN_EINVAL, "slice range out of bounds");
     if (o.slice_batch < 0) return fail(TN_EINVAL, "negative slice_batch");
-    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(o.slice_batch, count));
+    int G = (int)std::max<int64_t>(1, std::min<int64_t>(o.slice_batch, count));
+    if (o.persistent) {
+        // every slice of the call side by side in the one launch, as far as
+        // 8 GiB of workspace copies and 2^31 work items allow (else several)
+        const int64_t ws = std::max<int64_t>(p->ws_elems * (int64_t)net->d.elem_bytes(), 1);
+        const int64_t items = std::max<int64_t>((int64_t)p->items.size(), 1);
+        int64_t g = std::min<int64_t>(count, (int64_t(8) << 30) / ws);
+        g = std::min<int64_t>(g, ((int64_t(1) << 31) - 1) / items);
+        g = std::min<int64_t>(g, 1 << 20);
+        G = (int)std::max<int64_t>(1, g);
+    }
     st = ensure_instances(net, p, G, (cudaStream_t)stream);
     if (st != TN_OK) return st;
     std::string err;

@@ -255,7 +255,8 @@ __host__ __device__ inline TcGeom tc_geom(const TileArgs& a, bool cplx, int prec
     return g;
 }
 
-// One CTA of a wave launch: outputs [o_begin, o_begin + o_count) of node.
+// One CTA of a wave launch: outputs [o_begin, o_begin + o_count) of node;
+// o_count < 0: a 64 x 64 tile item (o_begin = batch entry x tiles + tile).
 struct WaveItem {
     int node;
     int pad;
@@ -382,7 +383,7 @@ inline int tc_launches(const TileArgs& a) { return a.split > 1 ? 3 : 2; }
 cudaError_t launch_wave(const WaveItem* items, int n_items, const TileArgs* descs,
                         const void* const* leaf_ptrs, bool is_c, cudaStream_t s,
                         const int4* deps = nullptr, unsigned* done = nullptr, unsigned* head = nullptr,
-                        int G = 1);
+                        int G = 1, bool tiles = false);
 // Folds the slice group's roots into the FP64 accumulator, leaves the
 // result's exponent after the last group, and advances the slice counter by
 // `advance` (in the same launch when it is one block).

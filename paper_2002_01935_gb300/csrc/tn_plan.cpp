@@ -297,6 +297,16 @@ Node build_node(const NetDesc& d, const Plan& p, int id, int a, int b, const std
     return nd;
 }
 
+// Work items of a node in the persistent launch (per instance).
+static int64_t persistent_items(const Node& nd) {
+    if (nd.tile.cfg == kTile64x64 && tile_item_node(nd)) {
+        const int64_t M = int64_t(1) << nd.tile.nm, N = int64_t(1) << nd.tile.nn;
+        return ((M + 63) / 64) * ((N + 63) / 64) * nd.tile.nbatch;
+    }
+    const int64_t chunk = wave_chunk(nd, 2);
+    return (nd.size + chunk - 1) / chunk;
+}
+
 tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
     const int n = d.n;
     // diagnostics: TN_FORCE_GENERIC=1 runs every node on the generic kernel,
@@ -470,7 +480,26 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
     for (size_t k = 0; k < p.nodes.size(); ++k) {
         Node& nd = p.nodes[k];
         nd.kind = kGeneric;
-        if (p.force_generic || !plan_tile(d, p, nd, split_elems)) continue;
+        if (p.force_generic || !plan_tile(d, p, nd, split_elems)) {
+            if (p.persistent) {
+                err = "the persistent launch needs power-of-two label sizes on every node";
+                return TN_EUNSUPPORTED;
+            }
+            continue;
+        }
+        if (p.persistent) {
+            // tile items: 64 x 64 tiles, all of K in one item (no K split)
+            if (tile_item_node(nd)) {
+                int64_t unused = 0;
+                Node t = nd;
+                if (plan_tile(d, p, t, unused, kTile64x64)) {
+                    t.tile.split = 1;
+                    t.tile.kchunk = int64_t(1) << t.tile.nk;
+                    nd = t;
+                }
+            }
+            continue;
+        }
         if (!p.no_tensor_cores) make_tensor_core(d, p.mode, nd, split_elems, p.copies);
     }
     p.split_bytes = (split_elems * (int64_t)d.elem_bytes() + 1023) / 1024 * 1024;
@@ -486,7 +515,41 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
     }
     p.steps.clear();
     p.items.clear();
-    for (int L = 1; L <= max_level; ++L) {
+    if (p.persistent) {
+        // one dataflow launch over the whole tree, level by level
+        Step w;
+        w.wave = 1;
+        w.flow = 1;
+        w.item_begin = 0;
+        for (int L = 1; L <= max_level; ++L)
+            for (size_t k = 0; k < p.nodes.size(); ++k) {
+                if (level[n + k] != L) continue;
+                const Node& nd = p.nodes[k];
+                const int64_t cnt = persistent_items(nd);
+                for (int64_t i = 0; i < cnt; ++i) {
+                    WaveItem it;
+                    it.node = (int)k;
+                    it.pad = 0;
+                    if (nd.tile.cfg == kTile64x64 && tile_item_node(nd)) {
+                        it.o_begin = i;
+                        it.o_count = -1;
+                    } else {
+                        const int64_t chunk = wave_chunk(nd, 2);
+                        it.o_begin = i * chunk;
+                        it.o_count = std::min(chunk, nd.size - i * chunk);
+                    }
+                    p.items.push_back(it);
+                }
+                w.nodes.push_back((int)k);
+            }
+        w.item_count = (int)p.items.size();
+        if ((int64_t)p.items.size() > (int64_t(1) << 30)) {
+            err = "the persistent launch would need more than 2^30 work items";
+            return TN_EUNSUPPORTED;
+        }
+        p.steps.push_back(w);
+    }
+    for (int L = 1; L <= max_level && !p.persistent; ++L) {
         Step w;
         w.wave = 1;
         w.item_begin = (int)p.items.size();
@@ -521,7 +584,7 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
     }
     // ---- consecutive wave levels become one dataflow launch (their items
     // are contiguous); a node waits for its children in the same launch
-    if (!p.no_flow) {
+    if (!p.no_flow && !p.persistent) {
         std::vector<Step> merged;
         for (Step& st : p.steps) {
             if (st.wave && !merged.empty() && merged.back().wave &&
@@ -549,7 +612,8 @@ tn_status build_plan(const NetDesc& d, Plan& p, std::string& err) {
                     const Node& ch = p.nodes[c - n];
                     const int64_t chunk = wave_chunk(ch, p.copies);
                     p.flow_deps[4 * k + 2 * slot] = c - n;
-                    p.flow_deps[4 * k + 2 * slot + 1] = (int)((ch.size + chunk - 1) / chunk);
+                    p.flow_deps[4 * k + 2 * slot + 1] =
+                        p.persistent ? (int)persistent_items(ch) : (int)((ch.size + chunk - 1) / chunk);
                 }
                 ++slot;
             }
@@ -776,7 +840,7 @@ static tn_status configure_instances(const NetDesc& d, Plan& p, int G, int step,
         nd.tile.in = in;
         // the launch grid's z extent (batch x K splits x instances) is at most
         // 65535: fewer K splits when many instances run side by side
-        if (nd.kind == kTiled || nd.kind == kTensorCore) {
+        if (!p.persistent && (nd.kind == kTiled || nd.kind == kTensorCore)) {
             TileArgs& t = nd.tile;
             if (t.nbatch * (int64_t)G > 65535) {
                 err = "too many instances for a node with " + std::to_string(t.nbatch) + " batch entries";
@@ -792,7 +856,7 @@ static tn_status configure_instances(const NetDesc& d, Plan& p, int G, int step,
                 t.kchunk = ((units + split - 1) / split) * gran;
             }
         }
-        if (nd.kind == kGeneric && G > 65535) {
+        if (!p.persistent && nd.kind == kGeneric && G > 65535) {
             err = "too many instances";
             return TN_EUNSUPPORTED;
         }
@@ -873,7 +937,7 @@ static cudaError_t enqueue_slice(const NetDesc& d, Plan& p, cudaStream_t s, cons
                 e = launch_wave(p.items_dev + p.inst_items_begin[k], st.item_count * G, p.descs_dev,
                                 reinterpret_cast<const void* const*>(p.leaf_ptr_dev), c, s,
                                 reinterpret_cast<const int4*>(p.flow_deps_dev), p.flow_cnt_dev,
-                                p.flow_cnt_dev + (size_t)nn * G + k, G);
+                                p.flow_cnt_dev + (size_t)nn * G + k, G, p.persistent);
             else
                 e = launch_wave(p.items_dev + p.inst_items_begin[k], st.item_count * G, p.descs_dev,
                                 reinterpret_cast<const void* const*>(p.leaf_ptr_dev), c, s);

@@ -82,6 +82,11 @@ inline bool wave_node(const Node& nd, int copies = 1) {
 // independent loads: on the dataflow's critical path an item's latency must
 // not grow with K), 2^12 when several copies share the launch (there
 // throughput counts), and at most 1024 outputs.
+// Persistent plans: nodes with >= 32 rows and columns and >= 4096 outputs
+// run as 64 x 64 tile items.
+inline bool tile_item_node(const Node& nd) {
+    return nd.kind == kTiled && nd.tile.nm >= 5 && nd.tile.nn >= 5 && nd.size >= 4096;
+}
 inline int64_t wave_chunk(const Node& nd, int copies = 1) {
     const int bits = copies > 1 ? 12 : 10;
     const int sh = nd.tile.nk >= bits ? 0 : bits - nd.tile.nk;
@@ -94,6 +99,10 @@ struct GradState;  // reverse-sweep plan and device state (tn_grad.cpp)
 
 struct Plan {
     tn_mode mode = TN_MODE_FP32;
+    // persistent launch: every node (every slice of a call side by side) in
+    // one dataflow launch -- wave items for the small or narrow nodes, 64 x 64
+    // tile items over all of K for the others; FP32 on the CUDA cores
+    bool persistent = false;
     bool tuned = false;             // kernels chosen by autotune_plan
     bool no_flow = false;           // one launch per wave level (env TN_NO_FLOW)
     std::vector<int> flow_deps;     // per node: child a, its chunks, child b, its chunks

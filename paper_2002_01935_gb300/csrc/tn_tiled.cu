@@ -190,33 +190,40 @@ __device__ __forceinline__ Scales scales_from(unsigned ma, unsigned mb, int64_t 
 
 }  // namespace
 
+template <bool CPLX>
+__device__ __forceinline__ typename VT<CPLX>::T ld_cg(const typename VT<CPLX>::T* p) {
+    if constexpr (CPLX) return __ldcg(reinterpret_cast<const float2*>(p));
+    else return __ldcg(reinterpret_cast<const float*>(p));
+}
+
 // --------------------------------------------------------------------------
-// Register-blocked tile kernel: one CTA = TM x TN outputs of one batch
-// index and one K split; TK-deep steps through shared memory.
+// Register-blocked tile: TM x TN outputs of one batch index and one K split;
+// TK-deep steps through shared memory.  The body serves the tile kernel
+// (one CTA per tile) and the tile items of the persistent dataflow launch
+// (CG: operands read through L2 only -- they may have been written earlier
+// in the same launch by other CTAs).  A and B are the instance's operand
+// bases; the epilogue writes C (or the K part's partial) and the maximum.
 // --------------------------------------------------------------------------
-template <bool CPLX, int TM, int TN, int TK, int RM, int RN>
-__global__ void __launch_bounds__((TM / RM) * (TN / RN))
-    k_tile(const __grid_constant__ TileArgs a) {
+template <bool CPLX, int TM, int TN, int TK, int RM, int RN, bool CG>
+__device__ __forceinline__ void tile_body(const TileArgs& a, int64_t tile_x, int split_id, int64_t b,
+                                          const View& vw, const typename VT<CPLX>::T* A,
+                                          const typename VT<CPLX>::T* B, const Scales& sc) {
     using T = typename VT<CPLX>::T;
     constexpr int TX = TN / RN, TY = TM / RM, NT = TX * TY;
     constexpr int PB = CPLX ? 2 : 4;  // keeps sB rows 16-byte aligned
     __shared__ T sA[TK][TM + 1];
     __shared__ __align__(16) T sB[TK][TN + PB];
     __shared__ int64_t rowA[TM], colB[TN], kA[TK], kB[TK];
+    auto ldx = [](const T* p) -> T {
+        if constexpr (CG) return ld_cg<CPLX>(p);
+        else return *p;
+    };
 
     const int tid = threadIdx.x;
     const int64_t M = 1ll << a.nm, N = 1ll << a.nn, K = 1ll << a.nk;
     const int64_t tiles_n = (N + TN - 1) / TN;
-    const int64_t m0 = ((int64_t)blockIdx.x / tiles_n) * TM;
-    const int64_t n0 = ((int64_t)blockIdx.x % tiles_n) * TN;
-    const int per_inst = (int)(a.nbatch * a.split);
-    const int inst = blockIdx.z / per_inst;
-    const int zz = blockIdx.z % per_inst;
-    const int split_id = zz % a.split;
-    const int64_t b = zz / a.split;
-    const View vw = inst_view(a, inst, (int)sizeof(T));
-    if (!vw.live) return;
-    const Scales sc = node_scales(vw.sc, blockIdx.x == 0 && zz == 0 && tid == 0);
+    const int64_t m0 = (tile_x / tiles_n) * TM;
+    const int64_t n0 = (tile_x % tiles_n) * TN;
     const int64_t slice = vw.slice;
     const int64_t baseA =
         slice_off(a.sla, slice) + scatter_bits(b, a.a_b, a.nb) + scatter_bits(m0, a.a_m, a.nm);
@@ -233,8 +240,6 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
     const int nlim = (int)min64(N - n0, TN);
     const int64_t kbeg = (int64_t)split_id * a.kchunk;
     const int64_t kend = min64(K, kbeg + a.kchunk);
-    const T* A = reinterpret_cast<const T*>(vw.A);
-    const T* B = reinterpret_cast<const T*>(vw.B);
     const int tx = tid % TX, ty = tid / TX;
 
     T acc[RM][RN];
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
             const int i = a.a_mfast ? e % TM : e / TK;
             const int t = a.a_mfast ? e / TM : e % TK;
             const bool in = e < TM * TK && i < mlim && t < klim;
-            ra[q] = in ? cmul(A[baseA + rowA[i] + kaA + kA[t]], sc.fa, a.conj_a) : zero<T>();
+            ra[q] = in ? cmul(ldx(A + baseA + rowA[i] + kaA + kA[t]), sc.fa, a.conj_a) : zero<T>();
         }
 #pragma unroll
         for (int q = 0; q < LB; ++q) {
@@ -281,7 +286,7 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
             const int j = a.b_nfast ? e % TN : e / TK;
             const int t = a.b_nfast ? e / TN : e % TK;
             const bool in = e < TN * TK && j < nlim && t < klim;
-            rb[q] = in ? cmul(B[baseB + colB[j] + kaB + kB[t]], sc.fb, a.conj_b) : zero<T>();
+            rb[q] = in ? cmul(ldx(B + baseB + colB[j] + kaB + kB[t]), sc.fb, a.conj_b) : zero<T>();
         }
     };
     if (kbeg < kend) gload(kbeg);
@@ -357,6 +362,22 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
         block_max(lmax, vw.sc.max_c);
         if (a.t_done && threadIdx.x == 0) atomicMax(a.t_done, global_ns());
     }
+}
+
+template <bool CPLX, int TM, int TN, int TK, int RM, int RN>
+__global__ void __launch_bounds__((TM / RM) * (TN / RN))
+    k_tile(const __grid_constant__ TileArgs a) {
+    using T = typename VT<CPLX>::T;
+    const int per_inst = (int)(a.nbatch * a.split);
+    const int inst = blockIdx.z / per_inst;
+    const int zz = blockIdx.z % per_inst;
+    const int split_id = zz % a.split;
+    const int64_t b = zz / a.split;
+    const View vw = inst_view(a, inst, (int)sizeof(T));
+    if (!vw.live) return;
+    const Scales sc = node_scales(vw.sc, blockIdx.x == 0 && zz == 0 && threadIdx.x == 0);
+    tile_body<CPLX, TM, TN, TK, RM, RN, false>(a, blockIdx.x, split_id, b, vw, reinterpret_cast<const T*>(vw.A),
+                                                reinterpret_cast<const T*>(vw.B), sc);
 }
 
 // Sums the K-split partials of a node in a fixed order and applies its
@@ -567,6 +588,9 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a,
 // its own counter is raised.  Items only depend on earlier items, and every
 // taken item belongs to a running CTA, so the waits always end.  Inputs that
 // other CTAs of the launch produced are read through L2 (ld.global.cg).
+// The persistent launch (every node of every slice of a call in one
+// dataflow) adds tile items (o_count < 0): a 64 x 64 output tile of a large
+// node computed by the tile kernel's body over all of K.
 constexpr long long kFlowWaitCycles = 4000000000ll;  // ~2 s
 
 // Completion counters: the producer's release add (after a CTA barrier, so
@@ -580,13 +604,7 @@ __device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <bool CPLX>
-__device__ __forceinline__ typename VT<CPLX>::T ld_cg(const typename VT<CPLX>::T* p) {
-    if constexpr (CPLX) return __ldcg(reinterpret_cast<const float2*>(p));
-    else return __ldcg(reinterpret_cast<const float*>(p));
-}
-
-template <bool CPLX>
+template <bool CPLX, bool TILES>
 __global__ void __launch_bounds__(256)
     k_wave(const WaveItem* items, int n_items, const TileArgs* descs, const void* const* leaf_ptrs,
            const int4* deps, unsigned* done, unsigned* head, int G) {
@@ -668,7 +686,18 @@ __global__ void __launch_bounds__(256)
             }
         }
         __syncthreads();
-        if (vw.live) {
+        if (TILES && vw.live && it.o_count < 0) {
+            // a tile item of the persistent launch: 64 x 64 outputs of one
+            // batch entry (o_begin = batch entry x tiles + tile), all of K
+            const unsigned rma = vw.sc.max_a ? __ldcg(vw.sc.max_a) : 0u;
+            const unsigned rmb = vw.sc.max_b ? __ldcg(vw.sc.max_b) : 0u;
+            const int64_t rea = vw.sc.exp_a ? __ldcg(vw.sc.exp_a) : 0;
+            const int64_t reb = vw.sc.exp_b ? __ldcg(vw.sc.exp_b) : 0;
+            const Scales sc = scales_from(rma, rmb, rea, reb, it.o_begin == 0 && tid == 0 ? vw.sc.exp_c : nullptr);
+            const int64_t tiles = ((1ll << d.nm) + 63) / 64 * (((1ll << d.nn) + 63) / 64);
+            if constexpr (TILES)
+                tile_body<CPLX, 64, 64, 16, 4, 4, true>(d, it.o_begin % tiles, 0, it.o_begin / tiles, vw, A, B, sc);
+        } else if (vw.live) {
             const int64_t K = 1ll << d.nk;
             const int64_t nmask = (1ll << d.nn) - 1, mmask = (1ll << d.nm) - 1;
             const int O = (int)it.o_count;
@@ -873,14 +902,20 @@ cudaError_t launch_tile(const TileArgs& a, bool is_c, cudaStream_t s) {
 
 cudaError_t launch_wave(const WaveItem* items, int n_items, const TileArgs* descs,
                         const void* const* leaf_ptrs, bool is_c, cudaStream_t s, const int4* deps,
-                        unsigned* done, unsigned* head, int G) {
+                        unsigned* done, unsigned* head, int G, bool tiles) {
     if (n_items <= 0) return cudaSuccess;
-    // dataflow: persistent CTAs (all resident: 8 per SM fit), else one per item
+    // dataflow: persistent CTAs (8 per SM for the plain waves), else one per item
     const int grid = deps ? std::min(n_items, sm_count() * 8) : n_items;
-    if (is_c)
-        k_wave<true><<<grid, 256, 0, s>>>(items, n_items, descs, leaf_ptrs, deps, done, head, G);
-    else
-        k_wave<false><<<grid, 256, 0, s>>>(items, n_items, descs, leaf_ptrs, deps, done, head, G);
+    if (tiles) {
+        if (is_c)
+            k_wave<true, true><<<grid, 256, 0, s>>>(items, n_items, descs, leaf_ptrs, deps, done, head, G);
+        else
+            k_wave<false, true><<<grid, 256, 0, s>>>(items, n_items, descs, leaf_ptrs, deps, done, head, G);
+    } else if (is_c) {
+        k_wave<true, false><<<grid, 256, 0, s>>>(items, n_items, descs, leaf_ptrs, deps, done, head, G);
+    } else {
+        k_wave<false, false><<<grid, 256, 0, s>>>(items, n_items, descs, leaf_ptrs, deps, done, head, G);
+    }
     return cudaGetLastError();
 }
 
