@@ -54,7 +54,7 @@ constexpr int kRowBytes = 128;        // one swizzle row per stage and plane
 constexpr int kTileBytes = kBM * kRowBytes;  // 16 KB per plane and operand
 constexpr int kGemmThreads = 192;     // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kNumAcc = 4;            // TMEM accumulators (128 columns each) in rotation
-constexpr int kGroupRows = 64;        // row tiles per raster group (L2 reuse: R stays resident, Q streams)
+constexpr int kGroupRows = 32;        // row tiles per raster group (L2 reuse: R stays resident, Q streams)
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 constexpr int kPackThreads = 256;
 constexpr int kPackLow = 5;           // lowest bits of each order staged per tile

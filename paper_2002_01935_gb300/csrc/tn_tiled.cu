@@ -198,10 +198,10 @@ __device__ __forceinline__ typename VT<CPLX>::T ld_cg(const typename VT<CPLX>::T
 
 // --------------------------------------------------------------------------
 // Register-blocked tile: TM x TN outputs of one batch index and one K split;
-// TK-deep steps through shared memory.  The body serves the tile kernel
-// (one CTA per tile) and the tile items of the persistent dataflow launch
-// (CG: operands read through L2 only -- they may have been written earlier
-// in the same launch by other CTAs).  A and B are the instance's operand
+// TK-deep steps through shared memory.  This body serves the tile items of
+// the persistent dataflow launch (CG: operands read through L2 only -- they
+// may have been written earlier in the same launch by other CTAs); the tile
+// kernel below is the same computation.  A and B are the instance's operand
 // bases; the epilogue writes C (or the K part's partial) and the maximum.
 // --------------------------------------------------------------------------
 template <bool CPLX, int TM, int TN, int TK, int RM, int RN, bool CG>
@@ -364,10 +364,26 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int64_t tile_x, int
     }
 }
 
+// --------------------------------------------------------------------------
+// The tile kernel: one CTA = TM x TN outputs of one batch index and one K
+// split (the same computation as tile_body above, written out for the
+// kernel: the shared body costs the kernel registers, hence occupancy).
+// --------------------------------------------------------------------------
 template <bool CPLX, int TM, int TN, int TK, int RM, int RN>
 __global__ void __launch_bounds__((TM / RM) * (TN / RN))
     k_tile(const __grid_constant__ TileArgs a) {
     using T = typename VT<CPLX>::T;
+    constexpr int TX = TN / RN, TY = TM / RM, NT = TX * TY;
+    constexpr int PB = CPLX ? 2 : 4;  // keeps sB rows 16-byte aligned
+    __shared__ T sA[TK][TM + 1];
+    __shared__ __align__(16) T sB[TK][TN + PB];
+    __shared__ int64_t rowA[TM], colB[TN], kA[TK], kB[TK];
+
+    const int tid = threadIdx.x;
+    const int64_t M = 1ll << a.nm, N = 1ll << a.nn, K = 1ll << a.nk;
+    const int64_t tiles_n = (N + TN - 1) / TN;
+    const int64_t m0 = ((int64_t)blockIdx.x / tiles_n) * TM;
+    const int64_t n0 = ((int64_t)blockIdx.x % tiles_n) * TN;
     const int per_inst = (int)(a.nbatch * a.split);
     const int inst = blockIdx.z / per_inst;
     const int zz = blockIdx.z % per_inst;
@@ -375,9 +391,147 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN))
     const int64_t b = zz / a.split;
     const View vw = inst_view(a, inst, (int)sizeof(T));
     if (!vw.live) return;
-    const Scales sc = node_scales(vw.sc, blockIdx.x == 0 && zz == 0 && threadIdx.x == 0);
-    tile_body<CPLX, TM, TN, TK, RM, RN, false>(a, blockIdx.x, split_id, b, vw, reinterpret_cast<const T*>(vw.A),
-                                                reinterpret_cast<const T*>(vw.B), sc);
+    const Scales sc = node_scales(vw.sc, blockIdx.x == 0 && zz == 0 && tid == 0);
+    const int64_t slice = vw.slice;
+    const int64_t baseA =
+        slice_off(a.sla, slice) + scatter_bits(b, a.a_b, a.nb) + scatter_bits(m0, a.a_m, a.nm);
+    const int64_t baseB =
+        slice_off(a.slb, slice) + scatter_bits(b, a.b_b, a.nb) + scatter_bits(n0, a.b_n, a.nn);
+    for (int i = tid; i < TM; i += NT) rowA[i] = scatter_bits(i, a.a_m, a.nm);
+    for (int j = tid; j < TN; j += NT) colB[j] = scatter_bits(j, a.b_n, a.nn);
+    for (int t = tid; t < TK; t += NT) {
+        kA[t] = scatter_bits(t, a.a_k, a.nk);
+        kB[t] = scatter_bits(t, a.b_k, a.nk);
+    }
+    __syncthreads();
+    const int mlim = (int)min64(M - m0, TM);
+    const int nlim = (int)min64(N - n0, TN);
+    const int64_t kbeg = (int64_t)split_id * a.kchunk;
+    const int64_t kend = min64(K, kbeg + a.kchunk);
+    const T* A = reinterpret_cast<const T*>(vw.A);
+    const T* B = reinterpret_cast<const T*>(vw.B);
+    const int tx = tid % TX, ty = tid / TX;
+
+    T acc[RM][RN];
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int c = 0; c < RN; ++c) acc[r][c] = zero<T>();
+
+    // global -> registers for one K step (all loads issued back to back).
+    // The operand offsets of the K step's base k0 are kept incrementally:
+    // k0 advances by TK, so only the bits of its carry chain change.
+    constexpr int LA = (TM * TK + NT - 1) / NT, LB = (TN * TK + NT - 1) / NT;
+    constexpr int LG_TK = TK == 16 ? 4 : (TK == 8 ? 3 : (TK == 4 ? 2 : 0));
+    static_assert((1 << LG_TK) == TK, "TK must be a power of two");
+    T ra[LA], rb[LB];
+    int64_t cur_k = kbeg;
+    int64_t kaA = scatter_bits(kbeg, a.a_k, a.nk), kaB = scatter_bits(kbeg, a.b_k, a.nk);
+    auto step_k = [&]() {  // cur_k += TK, offsets follow
+        int i = LG_TK;
+        while (i < a.nk && ((cur_k >> i) & 1)) {
+            if (a.a_k[i] != kNoBit) kaA -= int64_t(1) << a.a_k[i];
+            if (a.b_k[i] != kNoBit) kaB -= int64_t(1) << a.b_k[i];
+            ++i;
+        }
+        if (i < a.nk) {
+            if (a.a_k[i] != kNoBit) kaA += int64_t(1) << a.a_k[i];
+            if (a.b_k[i] != kNoBit) kaB += int64_t(1) << a.b_k[i];
+        }
+        cur_k += TK;
+    };
+    auto gload = [&](int64_t k0) {
+        const int klim = (int)min64(kend - k0, TK);
+#pragma unroll
+        for (int q = 0; q < LA; ++q) {
+            const int e = tid + q * NT;
+            const int i = a.a_mfast ? e % TM : e / TK;
+            const int t = a.a_mfast ? e / TM : e % TK;
+            const bool in = e < TM * TK && i < mlim && t < klim;
+            ra[q] = in ? cmul(A[baseA + rowA[i] + kaA + kA[t]], sc.fa, a.conj_a) : zero<T>();
+        }
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+            const int e = tid + q * NT;
+            const int j = a.b_nfast ? e % TN : e / TK;
+            const int t = a.b_nfast ? e / TN : e % TK;
+            const bool in = e < TN * TK && j < nlim && t < klim;
+            rb[q] = in ? cmul(B[baseB + colB[j] + kaB + kB[t]], sc.fb, a.conj_b) : zero<T>();
+        }
+    };
+    if (kbeg < kend) gload(kbeg);
+    for (int64_t k0 = kbeg; k0 < kend; k0 += TK) {
+        // kaA/kaB describe k0 here; gload of k0 + TK needs them advanced
+#pragma unroll
+        for (int q = 0; q < LA; ++q) {
+            const int e = tid + q * NT;
+            if (e < TM * TK) {
+                const int i = a.a_mfast ? e % TM : e / TK;
+                const int t = a.a_mfast ? e / TM : e % TK;
+                sA[t][i] = ra[q];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+            const int e = tid + q * NT;
+            if (e < TN * TK) {
+                const int j = a.b_nfast ? e % TN : e / TK;
+                const int t = a.b_nfast ? e / TN : e % TK;
+                sB[t][j] = rb[q];
+            }
+        }
+        __syncthreads();
+        if (k0 + TK < kend) {
+            step_k();
+            gload(k0 + TK);  // next step's loads overlap this step's FMAs
+        }
+#pragma unroll 4
+        for (int t = 0; t < TK; ++t) {
+            T af[RM], bf[RN];
+#pragma unroll
+            for (int r = 0; r < RM; ++r) af[r] = sA[t][ty * RM + r];
+#pragma unroll
+            for (int c = 0; c < RN; ++c) bf[c] = sB[t][tx + c * TX];  // conflict-free
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int c = 0; c < RN; ++c) fma_acc(acc[r][c], af[r], bf[c]);
+        }
+        __syncthreads();
+    }
+
+    // epilogue: direct output (one split) or a partial for the reduce pass
+    float lmax = 0.f;
+    T* out = reinterpret_cast<T*>(a.split > 1 ? vw.P : vw.C);
+    const int64_t plane = (a.split > 1 ? (int64_t)split_id * ((int64_t)a.nbatch) : 0) + b;
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+        const int i = ty * RM + r;
+        if (i >= mlim) continue;
+        const int64_t rowoff = (plane * M + m0 + i) * N + n0;
+#pragma unroll
+        for (int c = 0; c < RN; ++c) {
+            const int j = tx + c * TX;
+            if (j >= nlim) continue;
+            T v = acc[r][c];
+            if (a.split == 1) {
+                if (sc.resid) {
+                    if constexpr (CPLX) {
+                        v.x = ldexpf(v.x, -sc.resid);
+                        v.y = ldexpf(v.y, -sc.resid);
+                    } else {
+                        v = ldexpf(v, -sc.resid);
+                    }
+                }
+                lmax = fmaxf(lmax, absmax(v));
+            }
+            out[rowoff + j] = v;
+        }
+    }
+    if (a.split == 1) {
+        block_max(lmax, vw.sc.max_c);
+        if (a.t_done && threadIdx.x == 0) atomicMax(a.t_done, global_ns());
+    }
 }
 
 // Sums the K-split partials of a node in a fixed order and applies its
