@@ -344,6 +344,34 @@ __device__ __forceinline__ void put2(char* hi, int64_t lo_off, int64_t pos, floa
     }
 }
 
+// Four adjacent packed elements (two K-adjacent complex entries of the 4M
+// layout) in one store per plane: 8 bytes (16-bit formats) or 16 (TF32).
+template <int PREC>
+__device__ __forceinline__ void put4(char* hi, int64_t lo_off, int64_t pos, float a, float b, float c, float d) {
+    using P = Parts<PREC>;
+    typename P::E h[4], l[4];
+    P::split(a, h[0], l[0]);
+    P::split(b, h[1], l[1]);
+    P::split(c, h[2], l[2]);
+    P::split(d, h[3], l[3]);
+    if constexpr (PREC == 2 || PREC == 4) {
+        using E2 = typename std::conditional<PREC == 2, __nv_bfloat162, __half2>::type;
+        E2 h01, h23, l01, l23;
+        h01.x = h[0]; h01.y = h[1]; h23.x = h[2]; h23.y = h[3];
+        l01.x = l[0]; l01.y = l[1]; l23.x = l[2]; l23.y = l[3];
+        uint2 hv, lv;
+        hv.x = *reinterpret_cast<uint32_t*>(&h01);
+        hv.y = *reinterpret_cast<uint32_t*>(&h23);
+        lv.x = *reinterpret_cast<uint32_t*>(&l01);
+        lv.y = *reinterpret_cast<uint32_t*>(&l23);
+        *reinterpret_cast<uint2*>(hi + pos) = hv;
+        *reinterpret_cast<uint2*>(hi + lo_off + pos) = lv;
+    } else {
+        *reinterpret_cast<float4*>(hi + pos) = make_float4(h[0], h[1], h[2], h[3]);
+        if constexpr (PREC == 1) *reinterpret_cast<float4*>(hi + lo_off + pos) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+}
+
 template <int PREC>
 __device__ __forceinline__ void put1(char* hi, int64_t lo_off, int64_t pos, float x) {
     using P = Parts<PREC>;
@@ -463,32 +491,36 @@ __global__ void __launch_bounds__(kPackThreads)
             }
         }
         const int64_t gbase = gb_cur;
+        // two K-adjacent entries per thread (tile index bit 0 is K bit 0):
+        // one store per plane for both
 #pragma unroll
-        for (int r = 0; r < kPackMaxTile / kPackThreads; ++r) {
-            const int i = threadIdx.x + r * kPackThreads;
+        for (int r = 0; r < kPackMaxTile / (2 * kPackThreads); ++r) {
+            const int i = 2 * (threadIdx.x + r * kPackThreads);
             if (i >= tsz) break;
-            const T v = stage[tidx[i]];
-            const int64_t pos = gbase ^ tdst[i];  // byte position in the first plane
+            const T v0 = stage[tidx[i]], v1 = stage[tidx[i + 1]];
+            const int64_t pos = gbase ^ tdst[i];  // byte position of the first entry (even k)
             if constexpr (CPLX && PREC == 3) {
                 // 3M: planes Re, Im, Re + Im of either operand, K not doubled
-                const float re = v.x * f, im = (conj ? -v.y : v.y) * f;
-                put1<0>(hi, 0, pos, re);
-                put1<0>(hi + lo_off, 0, pos, im);
-                put1<0>(hi + 2 * lo_off, 0, pos, re + im);
+                const float re0 = v0.x * f, im0 = (conj ? -v0.y : v0.y) * f;
+                const float re1 = v1.x * f, im1 = (conj ? -v1.y : v1.y) * f;
+                put2<0>(hi, 0, pos, re0, re1);
+                put2<0>(hi + lo_off, 0, pos, im0, im1);
+                put2<0>(hi + 2 * lo_off, 0, pos, re0 + im0, re1 + im1);
             } else if constexpr (CPLX) {
-                const float re = v.x * f, im = (conj ? -v.y : v.y) * f;
+                const float re0 = v0.x * f, im0 = (conj ? -v0.y : v0.y) * f;
+                const float re1 = v1.x * f, im1 = (conj ? -v1.y : v1.y) * f;
                 if (geo.planar) {
                     // planes Re hi, Re lo, Im hi, Im lo of either operand
-                    put1<PREC>(hi, lo_off, pos, re);
-                    put1<PREC>(hi + 2 * lo_off, lo_off, pos, im);
+                    put2<PREC>(hi, lo_off, pos, re0, re1);
+                    put2<PREC>(hi + 2 * lo_off, lo_off, pos, im0, im1);
                 } else if (role == 0) {
-                    put2<PREC>(hi, lo_off, pos, re, im);
+                    put4<PREC>(hi, lo_off, pos, re0, im0, re1, im1);
                 } else {
-                    put2<PREC>(hi, lo_off, pos, re, -im);
-                    put2<PREC>(hi, lo_off, pos ^ pp.pos_row1, im, re);
+                    put4<PREC>(hi, lo_off, pos, re0, -im0, re1, -im1);
+                    put4<PREC>(hi, lo_off, pos ^ pp.pos_row1, im0, re0, im1, re1);
                 }
             } else {
-                put1<PREC>(hi, lo_off, pos, v * f);
+                put2<PREC>(hi, lo_off, pos, v0 * f, v1 * f);
             }
         }
         __syncthreads();
