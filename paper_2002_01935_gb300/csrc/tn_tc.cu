@@ -528,10 +528,44 @@ __global__ void __launch_bounds__(kPackThreads)
 }
 
 // ---------------------------------------------------------------------------
-// k_umma: bulk-copy-fed tcgen05 GEMM over the packed planes.  blockIdx.x:
-// output tile (grouped raster), blockIdx.y: K split, blockIdx.z: batch entry
-// and instance.
+// k_umma: bulk-copy-fed tcgen05 GEMM over the packed planes, persistent: the
+// work items (output tile in grouped raster order, K part, batch entry and
+// instance; tile fastest) are dealt to the CTAs round robin, one CTA per SM.
+// The copy thread, the MMA thread and the epilogue warps each walk the same
+// item sequence; the stage ring and the accumulator rotation run on across
+// items, so the next item's copies and first MMAs overlap this item's final
+// drain and output stores, and no CTA is launched or torn down per tile.
 // ---------------------------------------------------------------------------
+struct UmmaItem {
+    int tm, tn, sp;
+    int64_t b;
+    int inst;
+    bool live;
+};
+
+__device__ __forceinline__ UmmaItem umma_item(int64_t w, int tiles_m, int tiles_n, int nsplit,
+                                              int64_t nbatch, int64_t slice0, int64_t slice_step,
+                                              int64_t slice_end) {
+    UmmaItem it;
+    const int64_t tiles = (int64_t)tiles_m * tiles_n;
+    const int x = (int)(w % tiles);
+    const int64_t rest = w / tiles;
+    it.sp = (int)(rest % nsplit);
+    const int64_t z = rest / nsplit;
+    it.b = z % nbatch;
+    it.inst = (int)(z / nbatch);
+    // grouped raster: kGroupRows row tiles share the column tiles they stream
+    const int per_group = kGroupRows * tiles_n;
+    const int grp = x / per_group;
+    const int first = grp * kGroupRows;
+    const int gsz = min(kGroupRows, tiles_m - first);
+    const int r = x - grp * per_group;
+    it.tm = first + r % gsz;
+    it.tn = r / gsz;
+    it.live = slice0 + (int64_t)it.inst * slice_step < slice_end;
+    return it;
+}
+
 template <bool CPLX, int PREC, int STAGES, int BN>
 __global__ void __launch_bounds__(64 + BN, 1)
     k_umma(const __grid_constant__ TileArgs a, int nacc) {
@@ -557,52 +591,25 @@ __global__ void __launch_bounds__(64 + BN, 1)
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
-    const int64_t b = blockIdx.z % a.nbatch;
-    const int inst = (int)(blockIdx.z / a.nbatch);
-    const int sp = blockIdx.y, nsplit = gridDim.y;
+    const int nsplit = a.split > 1 ? a.split : 1;
     // two-level accumulation: a chain of `chain` k-blocks accumulates in one
     // TMEM accumulator; the epilogue warps add every finished chain into FP32
     // registers (round to nearest), which keeps the tensor-core adder's long
     // accumulation error out of the result
     const int chain = SPLIT ? 1 : 4;
     const InstanceInfo& in = a.in;
-    const int64_t slice = a.ctl->slice + (int64_t)inst * in.slice_step;
-    if (slice >= a.ctl->slice_end) return;  // idle instance: before any barrier or TMEM
+    const int ni = in.n_inst > 1 ? in.n_inst : 1;
+    const int64_t slice0 = a.ctl->slice, slice_end = a.ctl->slice_end;
     const TcGeom geo = tc_geom(a, CPLX, PREC);
-    const int nkl = (int)(geo.nkb / nsplit);   // k-blocks of this K part
-    const int64_t kb0 = (int64_t)sp * nkl;
+    const int nkl = (int)(geo.nkb / nsplit);   // k-blocks of one K part
     const int tiles_m = (int)(geo.rows_r / kBM), tiles_n = (int)(geo.cols_q / BN);
-    // grouped raster: kGroupRows row tiles share the column tiles they stream
-    int tm, tn;
-    {
-        const int per_group = kGroupRows * tiles_n;
-        const int grp = (int)blockIdx.x / per_group;
-        const int first = grp * kGroupRows;
-        const int gsz = min(kGroupRows, tiles_m - first);
-        const int r = (int)blockIdx.x - grp * per_group;
-        tm = first + r % gsz;
-        tn = r / gsz;
-    }
-    const int row0 = tm * kBM, col0 = tn * BN;
+    const int64_t n_items = (int64_t)tiles_m * tiles_n * nsplit * a.nbatch * ni;
     const int nchain = (nkl + chain - 1) / chain;
     const int acc_cols = nacc * BN;
     const uint32_t alloc_cols = acc_cols <= 128 ? 128u : (acc_cols <= 256 ? 256u : 512u);
     const int ESZ = CPLX ? 8 : 4;
-    const char* pk = reinterpret_cast<const char*>(a.P) + (int64_t)inst * in.p_is * ESZ;
-
-    // renormalisation: the pack applied 2^-clamp(e); the rest is undone here
-    ScaleIO sio = a.sc;
-    if (sio.max_a) sio.max_a += (int64_t)inst * in.sa_is;
-    if (sio.exp_a) sio.exp_a += (int64_t)inst * in.sa_is;
-    if (sio.max_b) sio.max_b += (int64_t)inst * in.sb_is;
-    if (sio.exp_b) sio.exp_b += (int64_t)inst * in.sb_is;
-    sio.max_c += (int64_t)inst * in.sc_is;
-    sio.exp_c += (int64_t)inst * in.sc_is;
-    const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
-    const int resid = (eA - max(-120, min(120, eA))) + (eB - max(-120, min(120, eB))) +
-                      (PREC == 4 ? 2 * kF16Shift : 0);
-    if (blockIdx.x == 0 && sp == 0 && b == 0 && tid == 0 && sio.exp_c)
-        *sio.exp_c = (sio.exp_a ? *sio.exp_a : 0) + (sio.exp_b ? *sio.exp_b : 0) + eA + eB;
+    const int64_t M = int64_t(1) << a.nm, N = int64_t(1) << a.nn;
+#define UMMA_ITEM(w) umma_item((w), tiles_m, tiles_n, nsplit, a.nbatch, slice0, in.slice_step, slice_end)
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -633,31 +640,37 @@ __global__ void __launch_bounds__(64 + BN, 1)
     if (warp == 0) {
         // ---------------- bulk-copy producer ----------------
         if (tid == 0) {
-            const char* r_src = pk + ((b * tiles_m + tm) * geo.nkb + kb0) * kTileBytes;
-            const char* q_src = pk + geo.region_r + ((b * tiles_n + tn) * QT * geo.nkb + kb0) * kTileBytes;
-            int issued = 0;
-            for (int j = 0; j < nkl; ++j) {
-                const int s = j % STAGES;
-                if (j >= STAGES &&
-                    !mbar_wait(&empty_bar[s], (uint32_t)(((j / STAGES) + 1) & 1), &abort_flag)) {
-                    abort_flag = 1;
-                    break;
-                }
-                uint8_t* st = smem + s * STAGE_BYTES;
-                mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-                const int64_t o = (int64_t)j * kTileBytes;
-                bulk_load(st, r_src + o, kTileBytes, &full_bar[s]);
-                if constexpr (SPLIT) bulk_load(st + kTileBytes, r_src + geo.plane_r + o, kTileBytes, &full_bar[s]);
-                uint8_t* sq = st + PARTS * kTileBytes;
-                // BN columns: QT consecutive 128-row packed tiles, one after the other in smem
+            int issued = 0;  // k-blocks over all items (stage ring position)
+            for (int64_t w = blockIdx.x; w < n_items && !*(volatile int*)&abort_flag; w += gridDim.x) {
+                const UmmaItem it = UMMA_ITEM(w);
+                if (!it.live) continue;
+                const char* pk = reinterpret_cast<const char*>(a.P) + (int64_t)it.inst * in.p_is * ESZ;
+                const int64_t kb0 = (int64_t)it.sp * nkl;
+                const char* r_src = pk + ((it.b * tiles_m + it.tm) * geo.nkb + kb0) * kTileBytes;
+                const char* q_src = pk + geo.region_r + ((it.b * tiles_n + it.tn) * QT * geo.nkb + kb0) * kTileBytes;
+                for (int j = 0; j < nkl; ++j) {
+                    const int s = issued % STAGES;
+                    if (issued >= STAGES &&
+                        !mbar_wait(&empty_bar[s], (uint32_t)(((issued / STAGES) + 1) & 1), &abort_flag)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    uint8_t* st = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+                    const int64_t o = (int64_t)j * kTileBytes;
+                    bulk_load(st, r_src + o, kTileBytes, &full_bar[s]);
+                    if constexpr (SPLIT) bulk_load(st + kTileBytes, r_src + geo.plane_r + o, kTileBytes, &full_bar[s]);
+                    uint8_t* sq = st + PARTS * kTileBytes;
+                    // BN columns: QT consecutive 128-row packed tiles, one after the other in smem
 #pragma unroll
-                for (int h = 0; h < QT; ++h) {
-                    const int64_t oh = o + (int64_t)h * geo.nkb * kTileBytes;
-                    bulk_load(sq + h * kTileBytes, q_src + oh, kTileBytes, &full_bar[s]);
-                    if constexpr (SPLIT)
-                        bulk_load(sq + QB + h * kTileBytes, q_src + geo.plane_q + oh, kTileBytes, &full_bar[s]);
+                    for (int h = 0; h < QT; ++h) {
+                        const int64_t oh = o + (int64_t)h * geo.nkb * kTileBytes;
+                        bulk_load(sq + h * kTileBytes, q_src + oh, kTileBytes, &full_bar[s]);
+                        if constexpr (SPLIT)
+                            bulk_load(sq + QB + h * kTileBytes, q_src + geo.plane_q + oh, kTileBytes, &full_bar[s]);
+                    }
+                    ++issued;
                 }
-                ++issued;
             }
             if (abort_flag) {
                 // wait (bounded) for the copies still in flight before leaving
@@ -670,71 +683,100 @@ __global__ void __launch_bounds__(64 + BN, 1)
         // ---------------- MMA issuer ----------------
         if (tid == 32) {
             const uint32_t idesc = instr_desc(FMT, kBM, BN);
-            for (int j = 0; j < nkl; ++j) {
-                const int s = j % STAGES;
-                if (!mbar_wait(&full_bar[s], (uint32_t)((j / STAGES) & 1), &abort_flag)) {
-                    abort_flag = 1;
-                    break;
-                }
-                const int ch = j / chain, q = ch % nacc;
-                const bool first = j % chain == 0;
-                // a chain reuses accumulator q once the epilogue has drained it
-                if (first && ch >= nacc &&
-                    !mbar_wait(&acc_empty[q], (uint32_t)(((ch / nacc) + 1) & 1), &abort_flag)) {
-                    abort_flag = 1;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-                const uint32_t r_hi = base, q_hi = base + PARTS * kTileBytes;
-                const uint32_t r_lo = base + kTileBytes, q_lo = q_hi + QB;
-                const uint32_t d = tmem + (uint32_t)(q * BN);
-#pragma unroll
-                for (int k = 0; k < KSTEPS; ++k) {
-                    const uint32_t off = k * MMA_K * (HALF ? 2 : 4);
-                    const uint32_t acc0 = (!first || k > 0) ? 1u : 0u;
-                    mma<HALF>(d, smem_desc(r_hi + off), smem_desc(q_hi + off), idesc, acc0);
-                    if constexpr (SPLIT) {
-                        mma<HALF>(d, smem_desc(r_hi + off), smem_desc(q_lo + off), idesc, 1u);
-                        mma<HALF>(d, smem_desc(r_lo + off), smem_desc(q_hi + off), idesc, 1u);
+            int gj = 0, gc = 0;  // k-blocks and chains over all items
+            for (int64_t w = blockIdx.x; w < n_items && !*(volatile int*)&abort_flag; w += gridDim.x) {
+                if (!UMMA_ITEM(w).live) continue;
+                int q = 0;
+                for (int j = 0; j < nkl; ++j, ++gj) {
+                    const int s = gj % STAGES;
+                    if (!mbar_wait(&full_bar[s], (uint32_t)((gj / STAGES) & 1), &abort_flag)) {
+                        abort_flag = 1;
+                        break;
                     }
+                    const bool first = j % chain == 0;
+                    if (first) {
+                        // a chain reuses accumulator q once the epilogue has drained it
+                        q = gc % nacc;
+                        if (gc >= nacc &&
+                            !mbar_wait(&acc_empty[q], (uint32_t)(((gc / nacc) + 1) & 1), &abort_flag)) {
+                            abort_flag = 1;
+                            break;
+                        }
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t r_hi = base, q_hi = base + PARTS * kTileBytes;
+                    const uint32_t r_lo = base + kTileBytes, q_lo = q_hi + QB;
+                    const uint32_t d = tmem + (uint32_t)(q * BN);
+#pragma unroll
+                    for (int k = 0; k < KSTEPS; ++k) {
+                        const uint32_t off = k * MMA_K * (HALF ? 2 : 4);
+                        const uint32_t acc0 = (!first || k > 0) ? 1u : 0u;
+                        mma<HALF>(d, smem_desc(r_hi + off), smem_desc(q_hi + off), idesc, acc0);
+                        if constexpr (SPLIT) {
+                            mma<HALF>(d, smem_desc(r_hi + off), smem_desc(q_lo + off), idesc, 1u);
+                            mma<HALF>(d, smem_desc(r_lo + off), smem_desc(q_hi + off), idesc, 1u);
+                        }
+                    }
+                    mma_commit(&empty_bar[s]);
+                    if (j % chain == chain - 1 || j == nkl - 1) {
+                        mma_commit(&acc_full[q]);
+                        ++gc;
+                    }
+                    *(volatile int*)&consumed = gj + 1;
                 }
-                mma_commit(&empty_bar[s]);
-                if (j % chain == chain - 1 || j == nkl - 1) mma_commit(&acc_full[q]);
-                *(volatile int*)&consumed = j + 1;
             }
             mma_commit(&done_bar);  // arrives once every MMA issued above has completed
         }
     } else {
         // ---------------- epilogue (warps 2..) ----------------
-        float lmax = 0.f;
         const int quad = warp & 3;                   // TMEM lanes 32*quad.. belong to this warp
         const int cbase = ((warp - 2) >> 2) * kBM;   // this warp's 128 of the BN columns
         float sum[kBM];
-#pragma unroll
-        for (int i = 0; i < kBM; ++i) sum[i] = 0.f;
         bool ok = true;
-        for (int ch = 0; ch < nchain && ok; ++ch) {
-            const int q = ch % nacc;
-            const bool got = mbar_wait(&acc_full[q], (uint32_t)((ch / nacc) & 1), &abort_flag);
-            ok = __all_sync(0xffffffffu, got && !abort_flag);  // tcgen05.ld is warp-collective
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(q * BN + cbase);
+        int gc = 0;  // chains over all items
+        for (int64_t w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+            const UmmaItem it = UMMA_ITEM(w);
+            if (!it.live) continue;
+            // renormalisation: the pack applied 2^-clamp(e); the rest is undone here
+            ScaleIO sio = a.sc;
+            if (sio.max_a) sio.max_a += (int64_t)it.inst * in.sa_is;
+            if (sio.exp_a) sio.exp_a += (int64_t)it.inst * in.sa_is;
+            if (sio.max_b) sio.max_b += (int64_t)it.inst * in.sb_is;
+            if (sio.exp_b) sio.exp_b += (int64_t)it.inst * in.sb_is;
+            sio.max_c += (int64_t)it.inst * in.sc_is;
+            sio.exp_c += (int64_t)it.inst * in.sc_is;
+            const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
+            const int resid = (eA - max(-120, min(120, eA))) + (eB - max(-120, min(120, eB))) +
+                              (PREC == 4 ? 2 * kF16Shift : 0);
+            if (it.tm == 0 && it.tn == 0 && it.sp == 0 && it.b == 0 && tid == 64 && sio.exp_c)
+                *sio.exp_c = (sio.exp_a ? *sio.exp_a : 0) + (sio.exp_b ? *sio.exp_b : 0) + eA + eB;
 #pragma unroll
-            for (int col = 0; col < kBM; col += 32) tmem_add32(ta + (uint32_t)col, sum + col);
-            tc_fence_before();
-            __syncwarp();
-            if ((tid & 31) == 0) mbar_arrive(&acc_empty[q]);
-        }
-        if (ok) {
-            const int row = row0 + quad * 32 + (tid & 31);
-            const int64_t M = int64_t(1) << a.nm, N = int64_t(1) << a.nn;
+            for (int i = 0; i < kBM; ++i) sum[i] = 0.f;
+            for (int ch = 0; ch < nchain; ++ch, ++gc) {
+                const int q = gc % nacc;
+                const bool got = mbar_wait(&acc_full[q], (uint32_t)((gc / nacc) & 1), &abort_flag);
+                ok = __all_sync(0xffffffffu, got && !abort_flag);  // tcgen05.ld is warp-collective
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(q * BN + cbase);
+#pragma unroll
+                for (int col = 0; col < kBM; col += 32) tmem_add32(ta + (uint32_t)col, sum + col);
+                tc_fence_before();
+                __syncwarp();
+                if ((tid & 31) == 0) mbar_arrive(&acc_empty[q]);
+            }
+            if (!ok) break;
+            float lmax = 0.f;
+            const int row = it.tm * kBM + quad * 32 + (tid & 31);
+            const int col0 = it.tn * BN;
+            const int64_t b = it.b;
             // the node's output, or this part's FP32 partial product (same layout)
             float* C = nsplit > 1
-                           ? reinterpret_cast<float*>(const_cast<char*>(pk) + geo.part_off) +
-                                 (int64_t)sp * a.nbatch * M * N * (CPLX ? 2 : 1)
-                           : reinterpret_cast<float*>(a.C) + (int64_t)inst * in.c_is * (CPLX ? 2 : 1);
+                           ? reinterpret_cast<float*>(reinterpret_cast<char*>(a.P) +
+                                                      (int64_t)it.inst * in.p_is * ESZ + geo.part_off) +
+                                 (int64_t)it.sp * a.nbatch * M * N * (CPLX ? 2 : 1)
+                           : reinterpret_cast<float*>(a.C) + (int64_t)it.inst * in.c_is * (CPLX ? 2 : 1);
             const int rs = nsplit > 1 ? 0 : resid;
 #pragma unroll
             for (int cc = 0; cc < kBM; cc += 16) {
@@ -766,14 +808,14 @@ __global__ void __launch_bounds__(64 + BN, 1)
                         *reinterpret_cast<float4*>(crow + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
                 }
             }
-        } else if ((tid & 31) == 0) {
-            atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
+            if (nsplit == 1) {
+                for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+                if ((tid & 31) == 0 && lmax > 0.f) atomicMax(sio.max_c, __float_as_uint(lmax));
+            }
         }
-        if (nsplit == 1) {
-            for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-            if ((tid & 31) == 0 && lmax > 0.f) atomicMax(sio.max_c, __float_as_uint(lmax));
-        }
+        if (!ok && (tid & 31) == 0) atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
     }
+#undef UMMA_ITEM
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
@@ -1450,7 +1492,11 @@ cudaError_t launch_umma(const TileArgs& a, dim3 grid, int nacc, cudaStream_t s) 
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_umma<CPLX, PREC, STAGES, BN><<<grid, 64 + BN, SMEM, s>>>(a, nacc);
+    // persistent: at most one CTA per SM (the stages fill its shared memory),
+    // each walking every gridDim.x-th work item
+    const int64_t items = (int64_t)grid.x * grid.y * grid.z;
+    const unsigned ctas = (unsigned)std::min<int64_t>(items, (int64_t)sm_count());
+    k_umma<CPLX, PREC, STAGES, BN><<<ctas, 64 + BN, SMEM, s>>>(a, nacc);
     return cudaGetLastError();
 }
 
