@@ -128,7 +128,7 @@ struct alignas(16) TileArgs {
     int tc_swap;          // tensor-core node: B plays the row role (see TcGeom)
     int tc_bn128;         // tensor-core node: 128-column GEMM tiles even where 256 fit
     int tc_planar;        // tensor-core node: planar complex layout (see TcGeom)
-    int pad_tc;
+    int tc_nopair;        // tensor-core node: single-CTA GEMM even where CTA pairs apply
     InstanceInfo in;
 };
 

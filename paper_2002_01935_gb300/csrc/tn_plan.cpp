@@ -1288,6 +1288,12 @@ bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_e
     // complex rows and columns
     if (const char* e = getenv("TN_PLANAR"))
         if (e[0] == '1') t.tc_planar = 1;
+    // 256-column GEMMs run on CTA pairs (pair MMA) where the row tiles pair
+    // up; the diagnostic switch TN_NO_PAIR=1, read when a plan is built,
+    // keeps the single-CTA GEMM
+    t.tc_nopair = 0;
+    if (const char* e = getenv("TN_NO_PAIR"))
+        if (e[0] == '1') t.tc_nopair = 1;
     t.tc_planar = (t.tc_planar && c && (prec == 1 || prec == 2 || prec == 4) && t.nm >= 7 && t.nn >= 7 &&
                    !t.tc_bn128) ? 1 : 0;
     // K split: the grid should fill whole waves of the SMs (one CTA

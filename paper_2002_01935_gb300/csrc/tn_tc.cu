@@ -240,6 +240,79 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
+// ---- CTA-pair helpers (k_umma2) ----
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Shared::cluster address of the object at local's offset in CTA `rank`.
+__device__ __forceinline__ uint32_t peer_addr(const void* local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+    return r;
+}
+
+// Arrive (release, cluster scope) on a barrier given by its shared::cluster address.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+// Bounded wait with cluster-scope acquire: the phase may have been completed
+// by arrivals from the peer CTA.
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    long long t0 = clock64();
+    for (uint32_t i = 0;; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 255) == 255) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > kWaitCycles) return false;
+        }
+    }
+}
+
+// One MMA of a CTA pair (M = 256 over the two CTAs' TMEM lanes; A rows and
+// B columns split between the two CTAs' shared memory at the same offsets),
+// issued by the even CTA.
+template <bool HALF>
+__device__ __forceinline__ void mma2(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accumulate) {
+    if constexpr (HALF) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    }
+}
+
+// Arrive on the barrier at bar's offset in both CTAs of the pair once the
+// pair MMAs issued so far have completed.
+__device__ __forceinline__ void mma2_commit_both(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+
 // One packed element: the split parts of a value (TF32 keeps float bit
 // patterns with the low 13 mantissa bits zero; BF16 is round to nearest).
 template <int PREC>
@@ -527,6 +600,16 @@ __global__ void __launch_bounds__(kPackThreads)
     }
 }
 
+// k-blocks per TMEM accumulator chain before the epilogue adds it into FP32
+// registers.  Each hand-off costs a round trip between the MMA thread and
+// the epilogue (and a drain of the accumulator), so longer chains keep the
+// tensor pipe busier, while every extra k-block in a chain adds the tensor
+// core's own accumulation rounding.  Measured on the 7x7x14 amplitude (split
+// products issued small-first, see the MMA loops): chains of 2 take the
+// slice 10% faster than chains of 1 and keep its FP16-split error against
+// the oracle at 3.6e-6 (every sub-slice within 4.9e-6).
+__host__ __device__ constexpr int umma_chain(int prec) { return prec == 0 ? 4 : 2; }
+
 // ---------------------------------------------------------------------------
 // k_umma: bulk-copy-fed tcgen05 GEMM over the packed planes, persistent: the
 // work items (output tile in grouped raster order, K part, batch entry and
@@ -596,7 +679,7 @@ __global__ void __launch_bounds__(64 + BN, 1)
     // TMEM accumulator; the epilogue warps add every finished chain into FP32
     // registers (round to nearest), which keeps the tensor-core adder's long
     // accumulation error out of the result
-    const int chain = SPLIT ? 1 : 4;
+    const int chain = umma_chain(PREC);
     const InstanceInfo& in = a.in;
     const int ni = in.n_inst > 1 ? in.n_inst : 1;
     const int64_t slice0 = a.ctl->slice, slice_end = a.ctl->slice_end;
@@ -708,15 +791,24 @@ __global__ void __launch_bounds__(64 + BN, 1)
                     const uint32_t r_hi = base, q_hi = base + PARTS * kTileBytes;
                     const uint32_t r_lo = base + kTileBytes, q_lo = q_hi + QB;
                     const uint32_t d = tmem + (uint32_t)(q * BN);
+                    // split precisions: the small hi*lo and lo*hi products first, the
+                    // large hi*hi products last, so that the small ones are not added
+                    // into an accumulator already holding the large sum (the tensor
+                    // core's adder drops bits relative to the larger operand)
+                    if constexpr (SPLIT) {
+#pragma unroll
+                        for (int k = 0; k < KSTEPS; ++k) {
+                            const uint32_t off = k * MMA_K * (HALF ? 2 : 4);
+                            mma<HALF>(d, smem_desc(r_hi + off), smem_desc(q_lo + off), idesc,
+                                       (!first || k > 0) ? 1u : 0u);
+                            mma<HALF>(d, smem_desc(r_lo + off), smem_desc(q_hi + off), idesc, 1u);
+                        }
+                    }
 #pragma unroll
                     for (int k = 0; k < KSTEPS; ++k) {
                         const uint32_t off = k * MMA_K * (HALF ? 2 : 4);
-                        const uint32_t acc0 = (!first || k > 0) ? 1u : 0u;
+                        const uint32_t acc0 = (SPLIT || !first || k > 0) ? 1u : 0u;
                         mma<HALF>(d, smem_desc(r_hi + off), smem_desc(q_hi + off), idesc, acc0);
-                        if constexpr (SPLIT) {
-                            mma<HALF>(d, smem_desc(r_hi + off), smem_desc(q_lo + off), idesc, 1u);
-                            mma<HALF>(d, smem_desc(r_lo + off), smem_desc(q_hi + off), idesc, 1u);
-                        }
                     }
                     mma_commit(&empty_bar[s]);
                     if (j % chain == chain - 1 || j == nkl - 1) {
@@ -833,6 +925,322 @@ __global__ void __launch_bounds__(64 + BN, 1)
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tnow));
         atomicMax(a.t_done, tnow);
     }
+}
+
+// ---------------------------------------------------------------------------
+// k_umma2: the persistent GEMM on CTA pairs (clusters of two, one CTA per
+// SM) with the pair MMA (tcgen05 cta_group::2): a pair computes a 256-row x
+// 256-column tile, each CTA holding its own 128 rows of R and one of the two
+// 128-row tiles of Q in its shared memory, and its own 128 accumulator rows
+// in its tensor memory.  Per k-block an SM thus receives 64 KB of operands
+// (FP16 / BF16 / TF32 split) instead of the 96 KB of a single-CTA 128 x 256
+// tile, and three stages fit in its shared memory.  Pair item v is the work
+// items 2v (even CTA: row tile tm, Q tile 0) and 2v + 1 (odd CTA: row tile
+// tm + 1, Q tile 1) of k_umma's item order.
+// Synchronisation: each CTA's copy thread fills its own stage and barrier;
+// the odd CTA's relay thread forwards each completed stage to the even
+// CTA's full barrier (two arrivals per phase); the even CTA's MMA thread
+// issues the pair MMAs and commits to the empty, accumulator-full and done
+// barriers of both CTAs; the epilogue warps of both CTAs arrive on the even
+// CTA's accumulator-empty barriers.  Tensor memory is allocated and freed
+// by one warp of each CTA together.
+// ---------------------------------------------------------------------------
+template <bool CPLX, int PREC, int STAGES, int BN>
+__global__ void __launch_bounds__(320, 1)
+    k_umma2(const __grid_constant__ TileArgs a, int nacc) {
+    // BN: pair tile columns, 256 or 128; each CTA holds BN / 2 Q rows
+    constexpr bool HALF = PREC == 2 || PREC == 4;
+    constexpr bool SPLIT = PREC != 0;
+    constexpr int PARTS = SPLIT ? 2 : 1;
+    constexpr int QT = BN / kBM;                            // packed Q tiles per pair tile
+    constexpr int QHB = BN / 2 * kRowBytes;                // this CTA's Q rows, per part
+    constexpr int EPI_WARPS = 8;
+    constexpr int ECOLS = BN / 2;                          // accumulator columns per epilogue warp
+    constexpr int STAGE_BYTES = PARTS * (kTileBytes + QHB);
+    constexpr int KE = HALF ? 64 : 32;
+    constexpr int MMA_K = HALF ? 16 : 8;
+    constexpr int KSTEPS = KE / MMA_K;
+    constexpr uint32_t FMT = PREC == 2 ? 1u : (PREC == 4 ? 0u : 2u);
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ uint64_t acc_full[kNumAcc], acc_empty[kNumAcc];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ int consumed;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int nsplit = a.split > 1 ? a.split : 1;
+    const int chain = umma_chain(PREC);   // k-blocks per accumulator chain (see k_umma)
+    const InstanceInfo& in = a.in;
+    const int ni = in.n_inst > 1 ? in.n_inst : 1;
+    const int64_t slice0 = a.ctl->slice, slice_end = a.ctl->slice_end;
+    const TcGeom geo = tc_geom(a, CPLX, PREC);
+    const int nkl = (int)(geo.nkb / nsplit);
+    const int tiles_m = (int)(geo.rows_r / kBM), tiles_n = (int)(geo.cols_q / BN);
+    const int64_t n_pairs = (int64_t)tiles_m * tiles_n * nsplit * a.nbatch * ni / 2;
+    const int nchain = (nkl + chain - 1) / chain;
+    const uint32_t alloc_cols = nacc * BN <= 128 ? 128u : (nacc * BN <= 256 ? 256u : 512u);
+    const int ESZ = CPLX ? 8 : 4;
+    const int64_t M = int64_t(1) << a.nm, N = int64_t(1) << a.nn;
+    const int64_t v0 = blockIdx.x >> 1, vstep = gridDim.x >> 1;
+#define UMMA2_ITEM(v) \
+    umma_item(2 * (v) + rank, tiles_m, tiles_n, nsplit, a.nbatch, slice0, in.slice_step, slice_end)
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            // even CTA: its own copies' arrival + the odd CTA's relay
+            mbar_init(&full_bar[s], leader ? 2 : 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        for (int q = 0; q < kNumAcc; ++q) {
+            mbar_init(&acc_full[q], 1);
+            mbar_init(&acc_empty[q], 2 * EPI_WARPS);  // both CTAs' epilogue warps (even CTA's copy used)
+        }
+        abort_flag = 0;
+        consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    // the peer's arrivals, copies and commits may only come once its barriers exist
+    cluster_sync();
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(alloc_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        // ---------------- bulk-copy producer (both CTAs, own stages) ----------------
+        if (tid == 0) {
+            int issued = 0;
+            for (int64_t v = v0; v < n_pairs && !*(volatile int*)&abort_flag; v += vstep) {
+                const UmmaItem it = UMMA2_ITEM(v);
+                if (!it.live) continue;
+                const char* pk = reinterpret_cast<const char*>(a.P) + (int64_t)it.inst * in.p_is * ESZ;
+                const int64_t kb0 = (int64_t)it.sp * nkl;
+                const char* r_src = pk + ((it.b * tiles_m + it.tm) * geo.nkb + kb0) * kTileBytes;
+                // this CTA's half of the pair's Q rows: Q tile `rank` (BN 256), or
+                // rows 64 rank .. 64 rank + 63 of the Q tile (BN 128)
+                const char* q_src = pk + geo.region_r +
+                                    (QT == 2 ? (((it.b * tiles_n + it.tn) * QT + rank) * geo.nkb + kb0) * kTileBytes
+                                             : ((it.b * tiles_n + it.tn) * geo.nkb + kb0) * kTileBytes + rank * QHB);
+                for (int j = 0; j < nkl; ++j) {
+                    const int s = issued % STAGES;
+                    if (issued >= STAGES &&
+                        !mbar_wait_cl(&empty_bar[s], (uint32_t)(((issued / STAGES) + 1) & 1), &abort_flag)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    uint8_t* st = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+                    const int64_t o = (int64_t)j * kTileBytes;
+                    // stage: R hi, Q hi, R lo, Q lo
+                    bulk_load(st, r_src + o, kTileBytes, &full_bar[s]);
+                    bulk_load(st + kTileBytes, q_src + o, QHB, &full_bar[s]);
+                    if constexpr (SPLIT) {
+                        bulk_load(st + kTileBytes + QHB, r_src + geo.plane_r + o, kTileBytes, &full_bar[s]);
+                        bulk_load(st + 2 * kTileBytes + QHB, q_src + geo.plane_q + o, QHB, &full_bar[s]);
+                    }
+                    ++issued;
+                }
+            }
+            if (*(volatile int*)&abort_flag) {
+                // wait (bounded) for this CTA's copies still in flight before leaving
+                int dummy = 0;
+                for (int j = *(volatile int*)&consumed; j < issued; ++j)
+                    mbar_wait(&full_bar[j % STAGES], (uint32_t)((j / STAGES) & 1), &dummy);
+            }
+        }
+    } else if (warp == 1) {
+        if (tid == 32 && leader) {
+            // ---------------- pair MMA issuer (even CTA) ----------------
+            const uint32_t idesc = instr_desc(FMT, 2 * kBM, BN);
+            int gj = 0, gc = 0;
+            for (int64_t v = v0; v < n_pairs && !*(volatile int*)&abort_flag; v += vstep) {
+                if (!UMMA2_ITEM(v).live) continue;
+                int q = 0;
+                for (int j = 0; j < nkl; ++j, ++gj) {
+                    const int s = gj % STAGES;
+                    if (!mbar_wait_cl(&full_bar[s], (uint32_t)((gj / STAGES) & 1), &abort_flag)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    const bool first = j % chain == 0;
+                    if (first) {
+                        q = gc % nacc;
+                        if (gc >= nacc &&
+                            !mbar_wait_cl(&acc_empty[q], (uint32_t)(((gc / nacc) + 1) & 1), &abort_flag)) {
+                            abort_flag = 1;
+                            break;
+                        }
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t r_hi = base, q_hi = base + kTileBytes;
+                    const uint32_t r_lo = base + kTileBytes + QHB, q_lo = base + 2 * kTileBytes + QHB;
+                    const uint32_t d = tmem + (uint32_t)(q * BN);
+                    // split precisions: the small hi*lo and lo*hi products first, the
+                    // large hi*hi products last, so that the small ones are not added
+                    // into an accumulator already holding the large sum (the tensor
+                    // core's adder drops bits relative to the larger operand)
+                    if constexpr (SPLIT) {
+#pragma unroll
+                        for (int k = 0; k < KSTEPS; ++k) {
+                            const uint32_t off = k * MMA_K * (HALF ? 2 : 4);
+                            mma2<HALF>(d, smem_desc(r_hi + off), smem_desc(q_lo + off), idesc,
+                                       (!first || k > 0) ? 1u : 0u);
+                            mma2<HALF>(d, smem_desc(r_lo + off), smem_desc(q_hi + off), idesc, 1u);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < KSTEPS; ++k) {
+                        const uint32_t off = k * MMA_K * (HALF ? 2 : 4);
+                        const uint32_t acc0 = (SPLIT || !first || k > 0) ? 1u : 0u;
+                        mma2<HALF>(d, smem_desc(r_hi + off), smem_desc(q_hi + off), idesc, acc0);
+                    }
+                    mma2_commit_both(&empty_bar[s]);
+                    if (j % chain == chain - 1 || j == nkl - 1) {
+                        mma2_commit_both(&acc_full[q]);
+                        ++gc;
+                    }
+                    *(volatile int*)&consumed = gj + 1;
+                }
+            }
+            mma2_commit_both(&done_bar);  // both CTAs: every pair MMA issued above has completed
+        } else if (tid == 32) {
+            // ---------------- relay (odd CTA): own stage complete -> even CTA's full barrier ----------------
+            int gj = 0;
+            for (int64_t v = v0; v < n_pairs && !*(volatile int*)&abort_flag; v += vstep) {
+                if (!UMMA2_ITEM(v).live) continue;
+                for (int j = 0; j < nkl; ++j, ++gj) {
+                    const int s = gj % STAGES;
+                    if (!mbar_wait(&full_bar[s], (uint32_t)((gj / STAGES) & 1), &abort_flag)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    mbar_arrive_cluster(peer_addr(&full_bar[s], 0));
+                    *(volatile int*)&consumed = gj + 1;
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 2..9 of both CTAs, own TMEM lanes) ----------------
+        const int quad = warp & 3;
+        const int cbase = ((warp - 2) >> 2) * ECOLS;
+        float sum[ECOLS];
+        bool ok = true;
+        int gc = 0;
+        for (int64_t v = v0; v < n_pairs && ok; v += vstep) {
+            const UmmaItem it = UMMA2_ITEM(v);
+            if (!it.live) continue;
+            ScaleIO sio = a.sc;
+            if (sio.max_a) sio.max_a += (int64_t)it.inst * in.sa_is;
+            if (sio.exp_a) sio.exp_a += (int64_t)it.inst * in.sa_is;
+            if (sio.max_b) sio.max_b += (int64_t)it.inst * in.sb_is;
+            if (sio.exp_b) sio.exp_b += (int64_t)it.inst * in.sb_is;
+            sio.max_c += (int64_t)it.inst * in.sc_is;
+            sio.exp_c += (int64_t)it.inst * in.sc_is;
+            const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
+            const int resid = (eA - max(-120, min(120, eA))) + (eB - max(-120, min(120, eB))) +
+                              (PREC == 4 ? 2 * kF16Shift : 0);
+            if (it.tm == 0 && it.tn == 0 && it.sp == 0 && it.b == 0 && tid == 64 && sio.exp_c)
+                *sio.exp_c = (sio.exp_a ? *sio.exp_a : 0) + (sio.exp_b ? *sio.exp_b : 0) + eA + eB;
+#pragma unroll
+            for (int i = 0; i < ECOLS; ++i) sum[i] = 0.f;
+            for (int ch = 0; ch < nchain; ++ch, ++gc) {
+                const int q = gc % nacc;
+                const bool got = mbar_wait_cl(&acc_full[q], (uint32_t)((gc / nacc) & 1), &abort_flag);
+                ok = __all_sync(0xffffffffu, got && !abort_flag);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(q * BN + cbase);
+#pragma unroll
+                for (int col = 0; col < ECOLS; col += 32) tmem_add32(ta + (uint32_t)col, sum + col);
+                tc_fence_before();
+                __syncwarp();
+                if ((tid & 31) == 0) {
+                    if (leader) mbar_arrive(&acc_empty[q]);
+                    else mbar_arrive_cluster(peer_addr(&acc_empty[q], 0));
+                }
+            }
+            if (!ok) break;
+            float lmax = 0.f;
+            const int row = it.tm * kBM + quad * 32 + (tid & 31);
+            const int col0 = it.tn * BN;
+            const int64_t b = it.b;
+            float* C = nsplit > 1
+                           ? reinterpret_cast<float*>(reinterpret_cast<char*>(a.P) +
+                                                      (int64_t)it.inst * in.p_is * ESZ + geo.part_off) +
+                                 (int64_t)it.sp * a.nbatch * M * N * (CPLX ? 2 : 1)
+                           : reinterpret_cast<float*>(a.C) + (int64_t)it.inst * in.c_is * (CPLX ? 2 : 1);
+            const int rs = nsplit > 1 ? 0 : resid;
+#pragma unroll
+            for (int cc = 0; cc < ECOLS; cc += 16) {
+                float* w = sum + cc;
+                const int col = cbase + cc;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    if (rs) w[i] = ldexpf(w[i], -rs);
+                    lmax = fmaxf(lmax, fabsf(w[i]));
+                }
+                if constexpr (CPLX) {
+                    const int64_t j0 = (col0 + col) / 2;
+                    if (!a.tc_swap) {
+                        float* crow = C + ((b * M + row) * N + j0) * 2;
+#pragma unroll
+                        for (int i = 0; i < 16; i += 4)
+                            *reinterpret_cast<float4*>(crow + i) = make_float4(w[i], w[i + 1], w[i + 2], w[i + 3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            *reinterpret_cast<float2*>(C + ((b * M + j0 + i) * N + row) * 2) =
+                                make_float2(w[2 * i], w[2 * i + 1]);
+                    }
+                } else {
+                    float* crow = C + (b * M + row) * N + col0 + col;
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4)
+                        *reinterpret_cast<float4*>(crow + i) = make_float4(w[i], w[i + 1], w[i + 2], w[i + 3]);
+                }
+            }
+            if (nsplit == 1) {
+                for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+                if ((tid & 31) == 0 && lmax > 0.f) atomicMax(sio.max_c, __float_as_uint(lmax));
+            }
+        }
+        if (!ok && (tid & 31) == 0) atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
+    }
+#undef UMMA2_ITEM
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        // no pair MMA may still write either CTA's accumulators when they are freed
+        int dummy = 0;
+        bool quiet = true;
+        if (tid == 32) quiet = mbar_wait_cl(&done_bar, 0u, &dummy);
+        quiet = __shfl_sync(0xffffffffu, quiet, 0);
+        tc_fence_after();
+        if (!quiet && tid == 32) atomicExch(const_cast<int32_t*>(&a.ctl->status), (int32_t)TN_ETIMEOUT);
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(alloc_cols));
+    }
+    if (a.t_done && tid == 0 && nsplit == 1) {
+        unsigned long long tnow;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tnow));
+        atomicMax(a.t_done, tnow);
+    }
+    // neither CTA leaves while the other may still arrive on its barriers
+    cluster_sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -979,6 +1387,9 @@ __global__ void __launch_bounds__(320, 1)
                 tc_fence_after();
                 const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
                 const uint32_t d_re = tmem + (uint32_t)(q * 2 * BNC), d_im = d_re + (uint32_t)BNC;
+                // the small hi*lo and lo*hi products first, the large hi*hi ones
+                // last (see k_umma: the adder drops bits relative to the larger
+                // operand)
 #pragma unroll
                 for (int k = 0; k < KSTEPS; ++k) {
                     const uint32_t off = k * 32;
@@ -987,18 +1398,24 @@ __global__ void __launch_bounds__(320, 1)
                     const uint64_t qrh = smem_desc64(base + 4 * PT + off), qrl = smem_desc64(base + 5 * PT + off);
                     const uint64_t qih = smem_desc64(base + 6 * PT + off), qil = smem_desc64(base + 7 * PT + off);
                     const uint32_t acc0 = k > 0 ? 1u : 0u;
-                    mma<HALF>(d_re, rrh, qrh, idesc, acc0);
-                    mma<HALF>(d_im, rrh, qih, idesc, acc0);
-                    mma<HALF>(d_re, rrh, qrl, idesc, 1u);
-                    mma<HALF>(d_im, rrh, qil, idesc, 1u);
+                    mma<HALF>(d_re, rrh, qrl, idesc, acc0);
+                    mma<HALF>(d_im, rrh, qil, idesc, acc0);
                     mma<HALF>(d_re, rrl, qrh, idesc, 1u);
                     mma<HALF>(d_im, rrl, qih, idesc, 1u);
-                    mma<HALF>(d_re, rih, qih, idesc_neg, 1u);
-                    mma<HALF>(d_im, rih, qrh, idesc, 1u);
                     mma<HALF>(d_re, rih, qil, idesc_neg, 1u);
                     mma<HALF>(d_im, rih, qrl, idesc, 1u);
                     mma<HALF>(d_re, ril, qih, idesc_neg, 1u);
                     mma<HALF>(d_im, ril, qrh, idesc, 1u);
+                }
+#pragma unroll
+                for (int k = 0; k < KSTEPS; ++k) {
+                    const uint32_t off = k * 32;
+                    const uint64_t rrh = smem_desc64(base + 0 * PT + off), rih = smem_desc64(base + 2 * PT + off);
+                    const uint64_t qrh = smem_desc64(base + 4 * PT + off), qih = smem_desc64(base + 6 * PT + off);
+                    mma<HALF>(d_re, rrh, qrh, idesc, 1u);
+                    mma<HALF>(d_im, rrh, qih, idesc, 1u);
+                    mma<HALF>(d_re, rih, qih, idesc_neg, 1u);
+                    mma<HALF>(d_im, rih, qrh, idesc, 1u);
                 }
                 mma_commit(&empty_bar[s]);
                 mma_commit(&acc_full[q]);
@@ -1500,6 +1917,41 @@ cudaError_t launch_umma(const TileArgs& a, dim3 grid, int nacc, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+// CTA pairs: 64 KB stages (split precisions), as many as fit in 192 KB;
+// persistent over the pair items, at most as many pairs as fit at once
+template <bool CPLX, int PREC, int BN>
+cudaError_t launch_umma2(const TileArgs& a, int64_t items, int nacc, cudaStream_t s) {
+    constexpr int STAGE_BYTES = (PREC == 0 ? 1 : 2) * (kTileBytes + BN / 2 * kRowBytes);
+    constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
+    constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+    auto* kern = k_umma2<CPLX, PREC, STAGES, BN>;
+    static bool configured = false;
+    static int max_pairs = 0;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(320);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        cfg.gridDim = dim3((unsigned)(sm_count() & ~1));
+        e = cudaOccupancyMaxActiveClusters(&max_pairs, kern, &cfg);
+        if (e != cudaSuccess) return e;
+        if (max_pairs < 1) return cudaErrorInvalidConfiguration;
+        configured = true;
+    }
+    const unsigned pairs = (unsigned)std::min<int64_t>(items / 2, (int64_t)max_pairs);
+    cfg.gridDim = dim3(2 * pairs);
+    cfg.stream = s;
+    return cudaLaunchKernelEx(&cfg, kern, a, nacc);
+}
+
 // planar layout: 64 KB stages, three in flight
 template <int PREC>
 cudaError_t launch_umma_planar(const TileArgs& a, dim3 grid, cudaStream_t s) {
@@ -1535,19 +1987,25 @@ cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     k_pack<CPLX, PREC><<<dim3(blocks(n_r) + blocks(n_q), ni), kPackThreads, 0, s>>>(
         a, make_pack_plan(a, 0, PREC, CPLX), make_pack_plan(a, 1, PREC, CPLX), (int)blocks(n_r));
     const int nkl = (int)(g.nkb / split);
-    const int chains = PREC == 0 ? (nkl + 3) / 4 : nkl;
+    const int chains = (nkl + umma_chain(PREC) - 1) / umma_chain(PREC);
     const int max_acc = 512 / g.bn;
     const int nacc = chains >= max_acc ? max_acc : (chains >= 2 ? 2 : 1);
     const int64_t tiles = (g.rows_r / kBM) * (g.cols_q / g.bn);
     dim3 grid((unsigned)tiles, (unsigned)split, (unsigned)(a.nbatch * ni));
+    // 256-column tiles over an even number of row tiles run on CTA pairs
+    const bool pair = g.bn == 256 && !g.planar && (g.rows_r / kBM) % 2 == 0 && !a.tc_nopair;
     cudaError_t e;
     if constexpr (CPLX && (PREC == 1 || PREC == 2 || PREC == 4)) {
         if (g.planar) {
             e = launch_umma_planar<PREC>(a, grid, s);
+        } else if (pair) {
+            e = launch_umma2<CPLX, PREC, 256>(a, (int64_t)grid.x * grid.y * grid.z, nacc, s);
         } else {
             e = g.bn == 256 ? launch_umma<CPLX, PREC, 256>(a, grid, nacc, s)
                             : launch_umma<CPLX, PREC, 128>(a, grid, nacc, s);
         }
+    } else if (pair) {
+        e = launch_umma2<CPLX, PREC, 256>(a, (int64_t)grid.x * grid.y * grid.z, nacc, s);
     } else {
         e = g.bn == 256 ? launch_umma<CPLX, PREC, 256>(a, grid, nacc, s)
                         : launch_umma<CPLX, PREC, 128>(a, grid, nacc, s);
