@@ -240,6 +240,20 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
+// Output stores of the GEMM epilogues: a node's final output is written once
+// and read by a later launch step, so it is stored with the streaming
+// (evict-first) hint and does not push the packed operands, which the other
+// tiles of the node still read, out of L2; K-split partials, which the
+// reduction reads right after, keep the normal policy.
+__device__ __forceinline__ void st_out4(float* p, float4 v, bool stream) {
+    if (stream) __stcs(reinterpret_cast<float4*>(p), v);
+    else *reinterpret_cast<float4*>(p) = v;
+}
+__device__ __forceinline__ void st_out2(float* p, float2 v, bool stream) {
+    if (stream) __stcs(reinterpret_cast<float2*>(p), v);
+    else *reinterpret_cast<float2*>(p) = v;
+}
+
 // ---- CTA-pair helpers (k_umma2) ----
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -628,7 +642,7 @@ struct UmmaItem {
 
 __device__ __forceinline__ UmmaItem umma_item(int64_t w, int tiles_m, int tiles_n, int nsplit,
                                               int64_t nbatch, int64_t slice0, int64_t slice_step,
-                                              int64_t slice_end) {
+                                              int64_t slice_end, int group_rows) {
     UmmaItem it;
     const int64_t tiles = (int64_t)tiles_m * tiles_n;
     const int x = (int)(w % tiles);
@@ -637,11 +651,11 @@ __device__ __forceinline__ UmmaItem umma_item(int64_t w, int tiles_m, int tiles_
     const int64_t z = rest / nsplit;
     it.b = z % nbatch;
     it.inst = (int)(z / nbatch);
-    // grouped raster: kGroupRows row tiles share the column tiles they stream
-    const int per_group = kGroupRows * tiles_n;
+    // grouped raster: group_rows row tiles share the column tiles they stream
+    const int per_group = group_rows * tiles_n;
     const int grp = x / per_group;
-    const int first = grp * kGroupRows;
-    const int gsz = min(kGroupRows, tiles_m - first);
+    const int first = grp * group_rows;
+    const int gsz = min(group_rows, tiles_m - first);
     const int r = x - grp * per_group;
     it.tm = first + r % gsz;
     it.tn = r / gsz;
@@ -651,7 +665,7 @@ __device__ __forceinline__ UmmaItem umma_item(int64_t w, int tiles_m, int tiles_
 
 template <bool CPLX, int PREC, int STAGES, int BN>
 __global__ void __launch_bounds__(64 + BN, 1)
-    k_umma(const __grid_constant__ TileArgs a, int nacc) {
+    k_umma(const __grid_constant__ TileArgs a, int nacc, int grp_rows) {
     constexpr bool HALF = PREC == 2 || PREC == 4;   // 16-bit operands, kind::f16
     constexpr bool SPLIT = PREC != 0;
     constexpr int PARTS = SPLIT ? 2 : 1;
@@ -692,7 +706,7 @@ __global__ void __launch_bounds__(64 + BN, 1)
     const uint32_t alloc_cols = acc_cols <= 128 ? 128u : (acc_cols <= 256 ? 256u : 512u);
     const int ESZ = CPLX ? 8 : 4;
     const int64_t M = int64_t(1) << a.nm, N = int64_t(1) << a.nn;
-#define UMMA_ITEM(w) umma_item((w), tiles_m, tiles_n, nsplit, a.nbatch, slice0, in.slice_step, slice_end)
+#define UMMA_ITEM(w) umma_item((w), tiles_m, tiles_n, nsplit, a.nbatch, slice0, in.slice_step, slice_end, grp_rows)
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -885,19 +899,19 @@ __global__ void __launch_bounds__(64 + BN, 1)
                         float* crow = C + ((b * M + row) * N + j0) * 2;
 #pragma unroll
                         for (int i = 0; i < 16; i += 4)
-                            *reinterpret_cast<float4*>(crow + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                            st_out4(crow + i, make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]), nsplit == 1);
                     } else {
                         // rows run over N, complex columns over M
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
-                            *reinterpret_cast<float2*>(C + ((b * M + j0 + i) * N + row) * 2) =
-                                make_float2(v[2 * i], v[2 * i + 1]);
+                            st_out2(C + ((b * M + j0 + i) * N + row) * 2, make_float2(v[2 * i], v[2 * i + 1]),
+                                        nsplit == 1);
                     }
                 } else {
                     float* crow = C + (b * M + row) * N + col0 + col;
 #pragma unroll
                     for (int i = 0; i < 16; i += 4)
-                        *reinterpret_cast<float4*>(crow + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                        st_out4(crow + i, make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]), nsplit == 1);
                 }
             }
             if (nsplit == 1) {
@@ -947,7 +961,7 @@ __global__ void __launch_bounds__(64 + BN, 1)
 // ---------------------------------------------------------------------------
 template <bool CPLX, int PREC, int STAGES, int BN>
 __global__ void __launch_bounds__(320, 1)
-    k_umma2(const __grid_constant__ TileArgs a, int nacc) {
+    k_umma2(const __grid_constant__ TileArgs a, int nacc, int grp_rows) {
     // BN: pair tile columns, 256 or 128; each CTA holds BN / 2 Q rows
     constexpr bool HALF = PREC == 2 || PREC == 4;
     constexpr bool SPLIT = PREC != 0;
@@ -989,7 +1003,7 @@ __global__ void __launch_bounds__(320, 1)
     const int64_t M = int64_t(1) << a.nm, N = int64_t(1) << a.nn;
     const int64_t v0 = blockIdx.x >> 1, vstep = gridDim.x >> 1;
 #define UMMA2_ITEM(v) \
-    umma_item(2 * (v) + rank, tiles_m, tiles_n, nsplit, a.nbatch, slice0, in.slice_step, slice_end)
+    umma_item(2 * (v) + rank, tiles_m, tiles_n, nsplit, a.nbatch, slice0, in.slice_step, slice_end, grp_rows)
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -1200,18 +1214,18 @@ __global__ void __launch_bounds__(320, 1)
                         float* crow = C + ((b * M + row) * N + j0) * 2;
 #pragma unroll
                         for (int i = 0; i < 16; i += 4)
-                            *reinterpret_cast<float4*>(crow + i) = make_float4(w[i], w[i + 1], w[i + 2], w[i + 3]);
+                            st_out4(crow + i, make_float4(w[i], w[i + 1], w[i + 2], w[i + 3]), nsplit == 1);
                     } else {
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
-                            *reinterpret_cast<float2*>(C + ((b * M + j0 + i) * N + row) * 2) =
-                                make_float2(w[2 * i], w[2 * i + 1]);
+                            st_out2(C + ((b * M + j0 + i) * N + row) * 2, make_float2(w[2 * i], w[2 * i + 1]),
+                                        nsplit == 1);
                     }
                 } else {
                     float* crow = C + (b * M + row) * N + col0 + col;
 #pragma unroll
                     for (int i = 0; i < 16; i += 4)
-                        *reinterpret_cast<float4*>(crow + i) = make_float4(w[i], w[i + 1], w[i + 2], w[i + 3]);
+                        st_out4(crow + i, make_float4(w[i], w[i + 1], w[i + 2], w[i + 3]), nsplit == 1);
                 }
             }
             if (nsplit == 1) {
@@ -1892,6 +1906,30 @@ cudaError_t launch_tc_3m(const TileArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Row tiles per raster group of the persistent GEMMs: the group's packed R
+// rows (all of K) stay in L2 while the column tiles stream past them, so the
+// group holds at most a quarter of L2 of them (at least one row tile, two
+// for CTA pairs, at most 32).
+int group_rows(const TileArgs& a, bool cplx, int prec, bool pair) {
+    static int l2 = 0;
+    if (!l2) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
+            v > 0)
+            l2 = v;
+        else
+            l2 = 126 << 20;
+        cudaGetLastError();
+    }
+    const TcGeom g = tc_geom(a, cplx, prec);
+    const int nsplit = a.split > 1 ? a.split : 1;
+    const int64_t row_bytes = std::max<int64_t>(g.nkb / nsplit, 1) * kTileBytes * g.parts;
+    int64_t rows = (int64_t)(l2 / 4) / row_bytes;
+    rows = std::max<int64_t>(std::min<int64_t>(rows, kGroupRows), pair ? 2 : 1);
+    if (pair) rows &= ~int64_t(1);
+    return (int)rows;
+}
+
 // pipeline depth: as many stages as fit in 192 KB
 template <int PREC, int BN>
 constexpr int stages_of() {
@@ -1913,7 +1951,7 @@ cudaError_t launch_umma(const TileArgs& a, dim3 grid, int nacc, cudaStream_t s) 
     // each walking every gridDim.x-th work item
     const int64_t items = (int64_t)grid.x * grid.y * grid.z;
     const unsigned ctas = (unsigned)std::min<int64_t>(items, (int64_t)sm_count());
-    k_umma<CPLX, PREC, STAGES, BN><<<ctas, 64 + BN, SMEM, s>>>(a, nacc);
+    k_umma<CPLX, PREC, STAGES, BN><<<ctas, 64 + BN, SMEM, s>>>(a, nacc, group_rows(a, CPLX, PREC, false));
     return cudaGetLastError();
 }
 
@@ -1949,7 +1987,7 @@ cudaError_t launch_umma2(const TileArgs& a, int64_t items, int nacc, cudaStream_
     const unsigned pairs = (unsigned)std::min<int64_t>(items / 2, (int64_t)max_pairs);
     cfg.gridDim = dim3(2 * pairs);
     cfg.stream = s;
-    return cudaLaunchKernelEx(&cfg, kern, a, nacc);
+    return cudaLaunchKernelEx(&cfg, kern, a, nacc, group_rows(a, CPLX, PREC, true));
 }
 
 // planar layout: 64 KB stages, three in flight
