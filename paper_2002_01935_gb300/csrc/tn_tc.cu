@@ -435,25 +435,33 @@ __device__ __forceinline__ void put2(char* hi, int64_t lo_off, int64_t pos, floa
 // layout) in one store per plane: 8 bytes (16-bit formats) or 16 (TF32).
 template <int PREC>
 __device__ __forceinline__ void put4(char* hi, int64_t lo_off, int64_t pos, float a, float b, float c, float d) {
-    using P = Parts<PREC>;
-    typename P::E h[4], l[4];
-    P::split(a, h[0], l[0]);
-    P::split(b, h[1], l[1]);
-    P::split(c, h[2], l[2]);
-    P::split(d, h[3], l[3]);
     if constexpr (PREC == 2 || PREC == 4) {
-        using E2 = typename std::conditional<PREC == 2, __nv_bfloat162, __half2>::type;
-        E2 h01, h23, l01, l23;
-        h01.x = h[0]; h01.y = h[1]; h23.x = h[2]; h23.y = h[3];
-        l01.x = l[0]; l01.y = l[1]; l23.x = l[2]; l23.y = l[3];
+        // paired round-to-nearest conversions; the same parts as Parts<PREC>::split
         uint2 hv, lv;
-        hv.x = *reinterpret_cast<uint32_t*>(&h01);
-        hv.y = *reinterpret_cast<uint32_t*>(&h23);
-        lv.x = *reinterpret_cast<uint32_t*>(&l01);
-        lv.y = *reinterpret_cast<uint32_t*>(&l23);
+        if constexpr (PREC == 4) {
+            const __half2 h01 = __floats2half2_rn(a, b), h23 = __floats2half2_rn(c, d);
+            const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
+            const __half2 l01 = __floats2half2_rn(a - f01.x, b - f01.y);
+            const __half2 l23 = __floats2half2_rn(c - f23.x, d - f23.y);
+            hv = make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+            lv = make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+        } else {
+            const __nv_bfloat162 h01 = __floats2bfloat162_rn(a, b), h23 = __floats2bfloat162_rn(c, d);
+            const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+            const __nv_bfloat162 l01 = __floats2bfloat162_rn(a - f01.x, b - f01.y);
+            const __nv_bfloat162 l23 = __floats2bfloat162_rn(c - f23.x, d - f23.y);
+            hv = make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+            lv = make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+        }
         *reinterpret_cast<uint2*>(hi + pos) = hv;
         *reinterpret_cast<uint2*>(hi + lo_off + pos) = lv;
     } else {
+        using P = Parts<PREC>;
+        typename P::E h[4], l[4];
+        P::split(a, h[0], l[0]);
+        P::split(b, h[1], l[1]);
+        P::split(c, h[2], l[2]);
+        P::split(d, h[3], l[3]);
         *reinterpret_cast<float4*>(hi + pos) = make_float4(h[0], h[1], h[2], h[3]);
         if constexpr (PREC == 1) *reinterpret_cast<float4*>(hi + lo_off + pos) = make_float4(l[0], l[1], l[2], l[3]);
     }
@@ -538,16 +546,25 @@ __global__ void __launch_bounds__(kPackThreads)
     __syncthreads();
     const int64_t n_tiles = int64_t(1) << u;
     const int64_t K = int64_t(1) << nk;
-    // tile bases by their bits; the loads of the next tile are issued before
-    // the current one is written out (two tiles of reads in flight)
+    // tile bases by their bits, one bit per lane and a warp-wide sum (source
+    // offset) and XOR (packed position); the loads of the next tile are
+    // issued before the current one is written out (two tiles of reads in
+    // flight)
+    const int lane = threadIdx.x & 31;
     auto bases = [&](int64_t tile, int64_t& sb, int64_t& gb) {
-        sb = 0;
-        gb = 0;
-        for (int j = 0; j < u; ++j)
+        int64_t s0 = 0, g0 = 0;
+        for (int j = lane; j < u; j += 32)
             if ((tile >> j) & 1) {
-                sb += pp.rest_src[j];
-                gb ^= pp.rest_pos[j];
+                s0 += pp.rest_src[j];
+                g0 ^= pp.rest_pos[j];
             }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            g0 ^= __shfl_xor_sync(0xffffffffu, g0, o);
+        }
+        sb = s0;
+        gb = g0;
     };
     constexpr int R = kPackMaxTile / kPackThreads;
     T ld[R];
