@@ -91,8 +91,8 @@ HALF_MODES = ("bf16_split", "fp16_split")
 # while the tensor-core kernel file is the one that was measured (SHA-256).
 TRAFFIC = {
     ("circuit7x7", "fp16_split"): {
-        "bytes": 4.726e9,  # node 1067 (M 2^15, N 2^13, K 2^10): k_pack 0.678 GB + k_umma 4.048 GB
-        "tn_tc_sha256": "f927ee6b67960a9f42f7a39cf3e87fc48e0b2fc83ebdb3e08cfefc819302c2bd",
+        "bytes": 4.818e9,  # node 1067 (M 2^15, N 2^13, K 2^10): k_pack 0.679 GB + k_umma2 4.139 GB
+        "tn_tc_sha256": "997fcc2e33608f9f70437ec76d2234fc30a9ff980936aa1b8e0bc652ee636d91",
         "profile": "profiles/launches_circuit7x7_fp16split.md",
     },
 }

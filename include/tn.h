@@ -346,6 +346,8 @@ tn_status tn_contract_instances_keep(tn_net *net, const int32_t *tree_pairs, tn_
  * fixed 8 MiB device array that is part of the library image; it calls no
  * cudaMalloc, cudaFree or other allocating routine.
  *   Arguments as tn_contract (no mode); the leaves must be device pointers.
+ *   Host outputs (out_mem = TN_MEM_HOST) make the call wait for the stream;
+ *   on a stream that is capturing they are refused with TN_EUNSUPPORTED.
  *   Limit: the tree's workspace plus bookkeeping must fit in 8 MiB
  *   (tn_plan_info out[4] is the workspace part); larger trees are refused
  *   with TN_EUNSUPPORTED and a message giving the bytes needed.

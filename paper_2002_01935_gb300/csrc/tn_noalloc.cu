@@ -102,6 +102,20 @@ tn_status run_noalloc(const NetDesc& d, const Plan& p, void* out, int out_mem, i
     const int nn = (int)p.nodes.size();
     const size_t eb = d.elem_bytes();
     const bool cplx = d.is_complex();
+    if (out_mem == TN_MEM_HOST) {
+        // a host result is waited for; a capturing stream cannot be waited on
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t ce = cudaStreamIsCapturing(stream, &cs);
+        if (ce != cudaSuccess) {
+            err = std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce);
+            return TN_ECUDA;
+        }
+        if (cs != cudaStreamCaptureStatusNone) {
+            err = "tn_contract_noalloc: host outputs need a stream synchronisation, which a "
+                  "capturing stream does not allow; pass device outputs";
+            return TN_EUNSUPPORTED;
+        }
+    }
     for (int v = 0; v < n; ++v)
         if (d.leaves[v].mem != TN_MEM_DEVICE) {
             err = "tn_contract_noalloc: leaves must be device pointers (staging a host leaf "

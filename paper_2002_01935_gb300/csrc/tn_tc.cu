@@ -12,18 +12,24 @@
 //      round-to-nearest-away, or BF16 / FP16 round-to-nearest; FP16 after a
 //      power-of-two shift into its range) and, for a complex Q,
 //      the expansion into the rows (Re, -Im) and (Im, Re).
-//   3. k_umma: a warp-specialised GEMM.  One thread streams the packed
-//      16 KB tiles (128 rows x one 128-byte row of K, already laid out in
-//      the 128-byte swizzle the UMMA descriptors expect) into a ring of
-//      shared-memory stages with plain bulk copies (cp.async.bulk on the
-//      TMA engine, one contiguous copy per tile and plane); one thread
-//      issues tcgen05.mma (kind::tf32, or kind::f16 with BF16 or FP16
-//      operands) into FP32 accumulators in tensor memory -- hi*hi + hi*lo +
-//      lo*hi for the split precisions -- rotating over up to four
-//      accumulators along K; four (128-column tiles) or eight (256-column
-//      tiles) epilogue warps drain each finished accumulator with
+//   3. k_umma: a warp-specialised, persistent GEMM (one CTA per SM walking
+//      the output tiles in grouped raster order).  One thread streams the
+//      packed 16 KB tiles (128 rows x one 128-byte row of K, already laid
+//      out in the 128-byte swizzle the UMMA descriptors expect) into a ring
+//      of shared-memory stages with plain bulk copies (cp.async.bulk on the
+//      TMA engine, one contiguous copy per tile and plane: the pack has
+//      done the permutation, so no tensor map is needed); one thread issues
+//      tcgen05.mma (kind::tf32, or kind::f16 with BF16 or FP16 operands)
+//      into FP32 accumulators in tensor memory -- lo*hi, hi*lo, then hi*hi
+//      for the split precisions -- rotating over up to four accumulators
+//      along K; four (128-column tiles) or eight (256-column tiles)
+//      epilogue warps drain each finished accumulator chain with
 //      tcgen05.ld into FP32 registers, undo the residual scale, reduce the
 //      node maximum and write C in the node's [batch][M][N] layout.
+//      k_umma2 runs 256 x 256 tiles on CTA pairs (clusters of two, the
+//      pair MMA tcgen05 cta_group::2, eight epilogue warps per CTA) when
+//      the row tiles come in pairs; k_umma_planar (Re/Im planes) and
+//      k_umma3m (three real products) are the other layouts.
 // Complex nodes use one real GEMM with K doubled (4M): R holds interleaved
 // (re, im) pairs along K and Q's expanded rows turn each accumulator column
 // pair into (Re C, Im C).  The larger complex operand plays R (it is not

@@ -175,3 +175,30 @@ def test_noalloc_real_network_against_oracle(env):
             assert abs(got - ref) <= TOL * abs(ref), (call, got, ref)
     finally:
         tnw.close()
+
+
+def test_noalloc_host_outputs_refused_while_capturing(env):
+    """Host outputs make the call wait for its stream; on a stream that is
+    capturing a graph the call refuses them before it launches anything."""
+    torch, binding = env
+    net = inputs.random_ising(12, seed=5)
+    pairs = planner.greedy_tree(net.labels, net.dims, net.open)
+    tnw = binding.TensorNetwork(net.labels, net.dims, net.open, _leaves(torch, net), complex_=False)
+    try:
+        ref = float(_oracle(net, pairs))
+        got = float(_noalloc_device(torch, binding, tnw, pairs, [], False))  # set-up call
+        assert abs(got - ref) <= TOL * abs(ref)
+        out = torch.zeros((), dtype=torch.float64).pin_memory()
+        oe = torch.zeros((), dtype=torch.int64).pin_memory()
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with pytest.raises(binding.TNError) as err:
+            with torch.cuda.graph(g, stream=s):
+                binding.tn_contract_noalloc(tnw.h, pairs, [], out.data_ptr(), binding.TN_MEM_HOST,
+                                            oe.data_ptr(), s.cuda_stream)
+        assert err.value.status == binding.TN_EUNSUPPORTED
+        torch.cuda.synchronize()
+        again = float(_noalloc_device(torch, binding, tnw, pairs, [], False))
+        assert abs(again - ref) <= TOL * abs(ref)
+    finally:
+        tnw.close()
