@@ -156,7 +156,10 @@ struct alignas(16) TileArgs {
 // for a deeper pipeline.
 struct TcGeom {
     int64_t rows_r;    // rows of R per batch entry
-    int64_t cols_q;    // real rows of Q per batch entry
+    int64_t cols_q;    // real rows of Q per batch entry in the packed layout: the
+                       // node's real accumulator columns, padded up to one 128-row tile
+    int64_t cols_valid;  // the node's real accumulator columns (<= cols_q)
+    int q_pad_lg;      // log2(cols_q / cols_valid): packed Q rows beyond cols_valid are never written
     int64_t kr;        // packed row length (elements) before padding
     int ke;            // elements per 128-byte row (32 TF32, 64 BF16 / FP16)
     int64_t nkb;       // k-blocks (KR padded up to a multiple of ke)
@@ -237,7 +240,12 @@ __host__ __device__ inline TcGeom tc_geom(const TileArgs& a, bool cplx, int prec
     g.planar = a.tc_planar ? 1 : 0;
     const int c = cplx && prec != 3 && !g.planar ? 2 : 1;
     g.rows_r = int64_t(1) << (a.tc_swap ? a.nn : a.nm);
-    g.cols_q = (int64_t(1) << (a.tc_swap ? a.nm : a.nn)) * c;
+    g.cols_valid = (int64_t(1) << (a.tc_swap ? a.nm : a.nn)) * c;
+    // narrow complex nodes (64 real columns) fill half of one 128-row Q tile; the
+    // GEMM computes the whole tile and the epilogue keeps the valid columns
+    g.q_pad_lg = 0;
+    while ((g.cols_valid << g.q_pad_lg) < 128) ++g.q_pad_lg;
+    g.cols_q = g.cols_valid << g.q_pad_lg;
     g.kr = (int64_t(1) << a.nk) * c;
     g.esz = tc_esz_of_prec(prec);
     g.row_bytes = g.planar ? 64 : 128;

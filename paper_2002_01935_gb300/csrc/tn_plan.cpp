@@ -1264,16 +1264,19 @@ tn_status make_generic_args_node(const NetDesc& d, const Plan& p, const Node& nd
 
 // Tensor-core choice for a tiled node in a reduced-precision mode: the
 // GEMM tile needs >= 128 accumulator rows, >= 128 real accumulator columns
-// and K >= 16.  A complex node puts its larger operand in the row role (the
-// column operand is expanded to two real rows per column).  The packed
-// operands live in the shared P buffer, which grows to hold them.
+// (a complex node: >= 64, its 32 complex columns expand to 64 real ones that
+// fill half of the 128-column tile, the rest is padding the epilogue drops)
+// and K >= 16.  A complex node puts its larger
+// operand in the row role (the column operand is expanded to two real rows
+// per column).  The packed operands live in the shared P buffer, which
+// grows to hold them.
 bool make_tensor_core(const NetDesc& d, tn_mode mode, Node& nd, int64_t& split_elems, int copies) {
     TileArgs& t = nd.tile;
     if (mode == TN_MODE_FP32 || t.cfg == kTileDot || t.nk < 4 || t.nbatch > 65535) return false;
     const bool c = d.is_complex();
     int swap = 0;
     if (c) {
-        if (std::max(t.nm, t.nn) < 7 || std::min(t.nm, t.nn) < 6) return false;
+        if (std::max(t.nm, t.nn) < 7 || std::min(t.nm, t.nn) < 5) return false;
         swap = t.nn > t.nm ? 1 : 0;
     } else if (t.nm < 7 || t.nn < 7) {
         return false;

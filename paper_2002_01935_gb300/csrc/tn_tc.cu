@@ -911,6 +911,7 @@ __global__ void __launch_bounds__(64 + BN, 1)
             for (int cc = 0; cc < kBM; cc += 16) {
                 float* v = sum + cc;
                 const int col = cbase + cc;
+                if (col0 + col >= geo.cols_valid) continue;  // padding columns of a narrow node
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     if (rs) v[i] = ldexpf(v[i], -rs);
@@ -1834,7 +1835,9 @@ PackPlan make_pack_plan(const TileArgs& a, int role, int prec, bool cplx) {
     const TcGeom geo = tc_geom(a, cplx, prec);
     int64_t lpos[3 * kMaxBits];
     for (int p = 0; p < nbits; ++p) {
-        const int64_t row = p >= nk ? int64_t(1) << (p - nk) : 0;
+        // Q's batch entries start on whole (padded) 128-row tiles
+        const int pad = role == 1 && p >= nk + no ? geo.q_pad_lg : 0;
+        const int64_t row = p >= nk ? int64_t(1) << (p - nk + pad) : 0;
         const int64_t k = p < nk ? int64_t(1) << p : 0;
         lpos[p] = packed_pos(geo, prec, cplx, role, row, k);
     }
@@ -2055,6 +2058,8 @@ cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
     dim3 grid((unsigned)tiles, (unsigned)split, (unsigned)(a.nbatch * ni));
     // 256-column tiles over an even number of row tiles run on CTA pairs
     const bool pair = g.bn == 256 && !g.planar && (g.rows_r / kBM) % 2 == 0 && !a.tc_nopair;
+    // padded (narrow) column operands: only k_umma keeps the valid columns
+    if (g.cols_valid != g.cols_q && (g.planar || pair || g.bn != kBN)) return cudaErrorInvalidValue;
     cudaError_t e;
     if constexpr (CPLX && (PREC == 1 || PREC == 2 || PREC == 4)) {
         if (g.planar) {
