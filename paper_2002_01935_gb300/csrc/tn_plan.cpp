@@ -215,9 +215,9 @@ bool plan_tile(const NetDesc& d, const Plan& p, Node& nd, int64_t& split_elems, 
         if (t.nbatch > 65535) return false;
         const int64_t outs = M * N * t.nbatch;
         int split = 1;
-        // one K tile (1024 entries) or more per part; at least four parts per
+        // one K tile (1024 entries) or more per part; at least eight parts per
         // SM in all (several CTAs per SM keep enough loads in flight for HBM)
-        while (outs * p.copies * split < 4 * (int64_t)sm_count() && (K / (split * 2)) >= 1024 &&
+        while (outs * p.copies * split < 8 * (int64_t)sm_count() && (K / (split * 2)) >= 1024 &&
                split < 4096 && (int64_t)split * 2 * p.copies <= 65535)
             split *= 2;
         t.split = split;

@@ -44,6 +44,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <type_traits>
 
@@ -2048,8 +2049,32 @@ cudaError_t launch_tc_t(const TileArgs& a, cudaStream_t s) {
         cudaError_t e0 = cudaMemset2DAsync(a.P, pitch, 0, (size_t)g.part_off, (size_t)ni, s);
         if (e0 != cudaSuccess) return e0;
     }
-    k_pack<CPLX, PREC><<<dim3(blocks(n_r) + blocks(n_q), ni), kPackThreads, 0, s>>>(
-        a, make_pack_plan(a, 0, PREC, CPLX), make_pack_plan(a, 1, PREC, CPLX), (int)blocks(n_r));
+    // pack grid: both operands' blocks in at most one round of resident CTAs
+    // (per instance), shared in proportion to the bytes each operand moves,
+    // so that no second, partly filled round of blocks trails the launch
+    unsigned br = blocks(n_r), bq = blocks(n_q);
+    {
+        static int per_sm = 0;
+        if (!per_sm) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pack<CPLX, PREC>, kPackThreads, 0) !=
+                    cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+            cudaGetLastError();
+        }
+        const int64_t slots = std::max<int64_t>((int64_t)per_sm * sm_count() / ni, 2);
+        if ((int64_t)br + bq > slots) {
+            const int src = CPLX ? 8 : 4;
+            const double wr = (double)n_r * (src + g.parts * g.esz * (CPLX ? 2 : 1));
+            const double wq = (double)n_q * (src + g.parts * g.esz * (CPLX ? (g.planar ? 2 : 4) : 1));
+            int64_t r = (int64_t)std::llround((double)slots * wr / (wr + wq));
+            r = std::min<int64_t>(std::max<int64_t>(r, 1), slots - 1);
+            br = (unsigned)std::min<int64_t>(r, br);
+            bq = (unsigned)std::min<int64_t>(slots - r, bq);
+        }
+    }
+    k_pack<CPLX, PREC><<<dim3(br + bq, ni), kPackThreads, 0, s>>>(a, make_pack_plan(a, 0, PREC, CPLX),
+                                                                 make_pack_plan(a, 1, PREC, CPLX), (int)br);
     const int nkl = (int)(g.nkb / split);
     const int chains = (nkl + umma_chain(PREC) - 1) / umma_chain(PREC);
     const int max_acc = 512 / g.bn;
