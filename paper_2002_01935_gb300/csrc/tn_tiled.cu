@@ -593,20 +593,47 @@ __global__ void __launch_bounds__(256) k_split_reduce(const __grid_constant__ Ti
 // K range in a fixed order; with several splits the partials go to P and
 // k_split_reduce sums them in split order (deterministic).
 // Inner-product node (few outputs, long K): out[b,m,n] = sum_k A[.., k] B[.., k].
-// The K range is cut into tiles of up to 2^kDotLow2 entries holding the
+// The K range is cut into tiles of up to 2^(2 kDotLow) entries holding the
 // kDotLow lowest strides of A, the kDotLow lowest of B and the next K bits;
 // every tile is read twice in the operands' own orders (consecutive threads,
-// consecutive addresses), staged in shared memory in K order and multiplied
-// there.  blockIdx.x: output, y: batch entry, z: K part x instance.
+// consecutive addresses) by asynchronous copies straight into shared memory,
+// where each entry lands at its K position, and multiplied there.  A ring of
+// kDotStages tiles keeps two tiles of copies in flight per CTA while a third
+// is multiplied; the tile base offsets follow the tile index by its carry
+// chain.  blockIdx.x: output, y: batch entry, z: K part x instance.
 constexpr int kDotLow = 5;
 constexpr int kDotTile = 1 << (2 * kDotLow);
+constexpr int kDotPad = kDotTile + kDotTile / 32;  // one padding entry per 32: no bank conflicts
+constexpr int kDotStages = 3;
+
+template <bool CPLX>
+constexpr size_t dot_smem_bytes() {
+    using T = typename VT<CPLX>::T;
+    return (size_t)kDotStages * 2 * kDotPad * sizeof(T) + 2 * kDotTile * sizeof(int32_t) +
+           2 * kDotTile * sizeof(uint16_t);
+}
+
+// asynchronous global -> shared copy of one 4- or 8-byte element
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 template <bool CPLX>
 __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a, const __grid_constant__ DotPlan dp) {
     using T = typename VT<CPLX>::T;
-    __shared__ T sA[kDotTile + kDotTile / 32], sB[kDotTile + kDotTile / 32];
-    __shared__ int64_t offA[kDotTile], offB[kDotTile];
-    __shared__ uint16_t canA[kDotTile], canB[kDotTile];
+    extern __shared__ __align__(16) unsigned char dot_smem[];
+    T* const stg = reinterpret_cast<T*>(dot_smem);  // [stage][A, B][kDotPad]
+    int32_t* const offA = reinterpret_cast<int32_t*>(dot_smem + (size_t)kDotStages * 2 * kDotPad * sizeof(T));
+    int32_t* const offB = offA + kDotTile;
+    uint16_t* const canA = reinterpret_cast<uint16_t*>(offB + kDotTile);
+    uint16_t* const canB = canA + kDotTile;
     __shared__ T red[256];
     const int64_t N = 1ll << a.nn, M = 1ll << a.nm;
     const int64_t m = (int64_t)blockIdx.x / N, n = (int64_t)blockIdx.x % N;
@@ -626,8 +653,8 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a,
                 ca += dp.ca_add[w];
                 cb += dp.cb_add[w];
             }
-        offA[e] = xa;
-        offB[e] = xb;
+        offA[e] = (int32_t)xa;  // within one operand: the planner keeps tiled operands below 2^31 entries
+        offB[e] = (int32_t)xb;
         canA[e] = (uint16_t)(ca + (ca >> 5));
         canB[e] = (uint16_t)(cb + (cb >> 5));
     }
@@ -642,53 +669,49 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a,
     const int64_t n_tiles = int64_t(1) << u;
     const int64_t per = (n_tiles + a.split - 1) / a.split;
     const int64_t t0 = (int64_t)sp * per, t1 = min64(n_tiles, t0 + per);
-    T acc0 = zero<T>(), acc1 = zero<T>();
-    // the loads of the next tile are issued before the current one is
-    // multiplied (two tiles of reads in flight per thread)
-    auto tile_base = [&](int64_t tile, int64_t& ba, int64_t& bb) {
-        ba = baseA;
-        bb = baseB;
-        for (int j = 0; j < u; ++j)
-            if ((tile >> j) & 1) {
-                ba += dp.rest_a[j];
-                bb += dp.rest_b[j];
-            }
-    };
-    T xa[kDotTile / 256], xb[kDotTile / 256];
-    if (t0 < t1) {
-        int64_t ba, bb;
-        tile_base(t0, ba, bb);
-#pragma unroll
-        for (int r = 0; r < kDotTile / 256; ++r) {
-            const int e = threadIdx.x + r * 256;
-            if (e < tsz) {
-                xa[r] = A[ba + offA[e]];
-                xb[r] = B[bb + offB[e]];
-            }
+    // offsets of the next tile to copy; advanced tile by tile along the carry chain
+    int64_t nt = t0, ba = baseA, bb = baseB;
+    for (int j = 0; j < u; ++j)
+        if ((t0 >> j) & 1) {
+            ba += dp.rest_a[j];
+            bb += dp.rest_b[j];
         }
-    }
-    for (int64_t tile = t0; tile < t1; ++tile) {
-#pragma unroll
-        for (int r = 0; r < kDotTile / 256; ++r) {
-            const int e = threadIdx.x + r * 256;
-            if (e < tsz) {
-                sA[canA[e]] = xa[r];
-                sB[canB[e]] = xb[r];
-            }
-        }
-        __syncthreads();
-        if (tile + 1 < t1) {
-            int64_t ba, bb;
-            tile_base(tile + 1, ba, bb);
+    auto issue = [&](int stage) {
+        if (nt < t1) {
+            T* sA = stg + (size_t)stage * 2 * kDotPad;
+            T* sB = sA + kDotPad;
 #pragma unroll
             for (int r = 0; r < kDotTile / 256; ++r) {
                 const int e = threadIdx.x + r * 256;
                 if (e < tsz) {
-                    xa[r] = A[ba + offA[e]];
-                    xb[r] = B[bb + offB[e]];
+                    cp_async_elem<sizeof(T)>(sA + canA[e], A + ba + offA[e]);
+                    cp_async_elem<sizeof(T)>(sB + canB[e], B + bb + offB[e]);
                 }
             }
+            int j = 0;
+            while (j < u && ((nt >> j) & 1)) {
+                ba -= dp.rest_a[j];
+                bb -= dp.rest_b[j];
+                ++j;
+            }
+            if (j < u) {
+                ba += dp.rest_a[j];
+                bb += dp.rest_b[j];
+            }
+            ++nt;
         }
+        cp_async_commit();  // one group per call, empty or not: the wait counts stay uniform
+    };
+#pragma unroll
+    for (int q = 0; q < kDotStages - 1; ++q) issue(q);
+    T acc0 = zero<T>(), acc1 = zero<T>();
+    int stage = 0;
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        issue((stage + kDotStages - 1) % kDotStages);
+        cp_async_wait<kDotStages - 1>();  // this thread's copies of `tile` have landed
+        __syncthreads();                  // ... and every other thread's
+        const T* sA = stg + (size_t)stage * 2 * kDotPad;
+        const T* sB = sA + kDotPad;
 #pragma unroll
         for (int r = 0; r < kDotTile / 256; ++r) {
             const int i = threadIdx.x + r * 256;
@@ -698,8 +721,10 @@ __global__ void __launch_bounds__(256) k_dot(const __grid_constant__ TileArgs a,
                 else fma_acc(acc0, cmul(sA[ip], sc.fa, a.conj_a), cmul(sB[ip], sc.fb, a.conj_b));
             }
         }
-        __syncthreads();
+        __syncthreads();  // the stage is refilled by the next iteration's copies
+        stage = (stage + 1) % kDotStages;
     }
+    cp_async_wait<0>();
     // fixed-order block reduction
     red[threadIdx.x] = add(acc0, acc1);
     __syncthreads();
@@ -1028,7 +1053,14 @@ static cudaError_t launch_tile_t(const TileArgs& a, cudaStream_t s) {
         case kTileDot: {
             const int64_t outs = 1ll << (a.nm + a.nn);
             const int ni = a.in.n_inst > 1 ? a.in.n_inst : 1;
-            k_dot<CPLX><<<dim3((unsigned)outs, (unsigned)a.nbatch, (unsigned)(a.split * ni)), 256, 0, s>>>(
+            constexpr size_t smem = dot_smem_bytes<CPLX>();
+            static bool configured = false;
+            if (!configured) {
+                e = cudaFuncSetAttribute(k_dot<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                configured = true;
+            }
+            k_dot<CPLX><<<dim3((unsigned)outs, (unsigned)a.nbatch, (unsigned)(a.split * ni)), 256, smem, s>>>(
                 a, make_dot_plan(a));
             e = cudaGetLastError();
             break;
