@@ -91,8 +91,8 @@ HALF_MODES = ("bf16_split", "fp16_split")
 # while the tensor-core kernel file is the one that was measured (SHA-256).
 TRAFFIC = {
     ("circuit7x7", "fp16_split"): {
-        "bytes": 4.818e9,  # node 1067 (M 2^15, N 2^13, K 2^10): k_pack 0.679 GB + k_umma2 4.139 GB
-        "tn_tc_sha256": "997fcc2e33608f9f70437ec76d2234fc30a9ff980936aa1b8e0bc652ee636d91",
+        "bytes": 4.798e9,  # node 1067 (M 2^15, N 2^13, K 2^10): k_pack 0.687 GB + k_umma2 4.111 GB
+        "tn_tc_sha256": "7f0fb9ae8d577b371196cf51913ecf66e4ed26f029f36fc16842673446233a8f",
         "profile": "profiles/launches_circuit7x7_fp16split.md",
     },
 }
