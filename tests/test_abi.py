@@ -206,6 +206,39 @@ def test_wave_steps_hold_only_small_nodes(lib):
         assert biggest not in in_wave
 
 
+def _gemm_node(mb, nb, kb, cplx):
+    from paper_2002_01935_gb300 import inputs
+    lab = 0
+    ml = list(range(lab, lab + mb)); lab += mb
+    nl = list(range(lab, lab + nb)); lab += nb
+    kl = list(range(lab, lab + kb)); lab += kb
+    dims = {l: 2 for l in range(lab)}
+    la, lb = kl[::2] + ml + kl[1::2], nl + kl
+    z = lambda labels: np.zeros([2] * len(labels), dtype=np.complex128 if cplx else np.float64)
+    return inputs.Network([z(la), z(lb)], [la, lb], dims, ml + nl)
+
+
+@pytest.mark.parametrize("mb,nb,kb,cplx,tc", [
+    (8, 8, 6, True, True), (5, 8, 6, True, True), (8, 5, 6, True, True),   # 32 complex columns: padded tile
+    (4, 8, 6, True, False), (8, 4, 6, True, False),                        # 16 complex columns: CUDA cores
+    (6, 6, 6, True, False),                                                # no side with 128 rows
+    (5, 8, 3, True, False),                                                # K = 8 < 16
+    (8, 7, 6, False, True), (8, 6, 6, False, False), (6, 8, 6, False, False)])  # real: 128 x 128 needed
+def test_tensor_core_choice(lib, mb, nb, kb, cplx, tc):
+    """Host plan only: a single GEMM node goes to the tensor cores in a
+    reduced-precision mode exactly when it has K >= 16, >= 128 accumulator
+    rows on its larger side and >= 128 real columns (a complex node's 32
+    complex columns expand to 64 real ones, which fill half of a padded
+    128-column tile); never in the FP32 mode."""
+    net = _gemm_node(mb, nb, kb, cplx)
+    for mode in ("fp16_split", "tf32_split", "bf16_split", "tf32_3m"):
+        steps, info = _steps(lib, net, [(0, 1)], (), mode)
+        assert [s["kind"] for s in steps] == [2 if tc else 1], (mode, steps)
+        assert info["n_tensor_core"] == (1 if tc else 0)
+    steps, info = _steps(lib, net, [(0, 1)], (), "fp32")
+    assert [s["kind"] for s in steps] == [1] and info["n_tensor_core"] == 0
+
+
 def _random_tree(n, rng):
     """A uniformly shuffled valid SSA tree: any two live ids are joined (so
     outer products of unconnected parts occur too)."""
