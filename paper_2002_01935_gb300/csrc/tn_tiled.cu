@@ -66,8 +66,6 @@ __device__ __forceinline__ int64_t slice_off(const SliceDigits& d, int64_t slice
 
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 
-__device__ __forceinline__ float2 cmul(float2 x, float f) { return make_float2(x.x * f, x.y * f); }
-__device__ __forceinline__ float cmul(float x, float f) { return x * f; }
 // scaled load value, complex-conjugated when cj != 0 (a sign flip of Im)
 __device__ __forceinline__ float2 cmul(float2 x, float f, int cj) {
     return make_float2(x.x * f, cj ? -x.y * f : x.y * f);
@@ -152,8 +150,6 @@ __device__ __forceinline__ View inst_view(const TileArgs& a, int inst, int esz) 
     v.live = v.slice < a.ctl->slice_end;
     return v;
 }
-
-__device__ __forceinline__ int n_inst(const TileArgs& a) { return a.in.n_inst > 1 ? a.in.n_inst : 1; }
 
 __device__ __forceinline__ Scales node_scales(const ScaleIO& sio, bool write_exp) {
     const int eA = exp_of(sio.max_a), eB = exp_of(sio.max_b);
